@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Benchmark of the WPCD Faddeev hot path on GB300.
+
+One step = one pass of the whole hot path over the 3-channel workload
+(three identical bosons, V = -3 exp(-r^2), l = lambda <= 2 coupled to L = 0,
+N = M = 200 packet bins, 8 x 8 p,q nodes and 32 y nodes per cell, dimension
+120 000): assemble P0 (count, scan, fill), build G1, and solve the matrix
+Faddeev equation at the step's energies (Krylov summation of the iterates,
+FP64).  Inputs are resident in HBM before the timed region; L2 is flushed
+(512 MB write) before every timed step, outside its events.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on the host cores on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "P assembly Gnodes/s; energies solved/s vs plain FP64 GPU at rel 1e-6"
+WORKLOAD_DESC = ("3 identical bosons, V=-3exp(-r^2), l=lambda<=2 -> L=0 (3 channels), N=M=200 "
+                 "tangent bins to 20, GL 8x8 p,q + 32 y nodes per cell (81.9M nodes), dim 120000")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="cfg2")
+    ap.add_argument("--energies", type=float, nargs="*", default=[0.5])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle-check", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# GB300: 152 SMs; FP64 issue rate 2 DFMA per SM per clock (about 1.25 TFLOP/s
+# at 2.07 GHz), FP32 128 FMA per SM per clock.
+N_SM = 152
+FP64_FMA_PER_SM_CLK = 2
+FP32_FMA_PER_SM_CLK = 128
+
+
+def fill_flops_per_node(n_ch: int, n_pairs: int) -> int:
+    """FP64 operations of one node in the fill pass (algorithmic count):
+    recoupled momenta 2 FMA, y' 1 FMA + 2 MUL + rsqrt (counted as 4),
+    Legendre recurrence 3 per order above 1, and per (l, l') pair two
+    products and one accumulation."""
+    return 4 + (2 + 2 + 4) + 3 * max(n_ch - 2, 0) + 3 * n_pairs
+
+
+def run_reference(args):
+    """The oracle (FP64 C, OpenMP) on the host cores: the same workload and
+    metric; each step assembles P0 for the full lattice."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+
+    import oracle
+    from paper_1508_07441_gb300 import inputs
+
+    oracle.build()
+    w = inputs.workload(args.workload)
+    nodes = w["N"] * w["M"] * int(np.prod(w["nodes"]))
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        P = oracle.P0(w["p_edges"], w["q_edges"], *w["nodes"], w["n_ch"])
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+        del P
+    ms = 1e3 * statistics.mean(times)
+    value = nodes / (ms * 1e-3) / 1e9
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gnodes/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "step": "oracle P0 assembly (count + fill), full lattice"},
+        "cpu_baseline": {"value": value, "unit": "Gnodes/s", "cores": cores, "kind": "oracle",
+                         "sample": "full 200x200 lattice, all 81.9M nodes, per step"},
+        "e2e": {"value": value, "unit": "Gnodes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1508_07441_gb300 import inputs
+    from paper_1508_07441_gb300 import wpcd as W
+
+    w = inputs.workload(args.workload)
+    energies = list(args.energies)
+    n_nodes = w["N"] * w["M"] * int(np.prod(w["nodes"]))
+    stream = torch.cuda.Stream()
+    pr = W.Problem(w["p_edges"], w["q_edges"], *w["nodes"], w["n_ch"], w["V"], w["a"],
+                   n_pair_nodes=8, device=local)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def one_step():
+        with torch.cuda.stream(stream):
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            P = pr.wpcd_assemble_P(W.WPCD_FP64, stream=stream)
+            U, stats, st = pr.wpcd_solve(P, energies, method=W.WPCD_SUM_KRYLOV, tol=1e-10,
+                                         max_iter=200, check_every=4, stream=stream)
+            ev1.record(stream)
+            ev1.synchronize()
+            rec = dict(step_ms=ev0.elapsed_time(ev1), asm_ms=P.ms, phases=P.wpcd_P_timing(),
+                       solve_ms=sum(s.ms for s in stats), U=U.copy(), nnz=P.nnz,
+                       n_kapply=sum(s.n_kapply for s in stats), status=st)
+            P.close()
+            return rec
+
+    for _ in range(args.warmup):
+        one_step()
+    recs = []
+    barrier()
+    l0 = W.wpcd_launch_count()
+    t_wall = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)  # L2 flush, outside the step's events
+            torch.cuda.synchronize()
+            recs.append(one_step())
+        barrier()
+    wall = time.perf_counter() - t_wall
+    launches = W.wpcd_launch_count() - l0
+
+    def maxr(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    step_ms = maxr(statistics.mean(r["step_ms"] for r in recs))
+    asm_ms = maxr(statistics.mean(r["asm_ms"] for r in recs))
+    solve_ms = maxr(statistics.mean(r["solve_ms"] for r in recs))
+    phases = [statistics.mean(r["phases"][k] for r in recs) for k in range(3)]
+    value = world * n_nodes / (asm_ms * 1e-3) / 1e9
+    energies_per_s = world * len(energies) / (solve_ms * 1e-3)
+
+    # ---- end to end through the public API with host buffers -------------
+    barrier()
+    t0 = time.perf_counter()
+    n_e2e = 2
+    for _ in range(n_e2e):
+        pr2 = W.Problem(w["p_edges"], w["q_edges"], *w["nodes"], w["n_ch"], w["V"], w["a"],
+                        n_pair_nodes=8, device=local)
+        P2 = pr2.wpcd_assemble_P(W.WPCD_FP64, stream=stream)
+        U2, st2, _ = pr2.wpcd_solve(P2, energies, tol=1e-10, max_iter=200, stream=stream)
+        P2.close()
+        pr2.close()
+    torch.cuda.synchronize()
+    e2e_s = maxr((time.perf_counter() - t0) / n_e2e)
+    N, M, n_ch = w["N"], w["M"], w["n_ch"]
+    nn = w["nodes"]
+    h2d = 8 * ((N + 1) + (M + 1) + N * nn[0] * 2 + M * nn[1] * 2 + nn[2] * 2 + N * M + (M + 1)
+               + n_ch * N + 2 * n_ch * N * N) + 8 * (2 * len(energies) + 64)
+    d2h = 8 + sum(48 + 8 * (s.n_kapply // 4 + 2) for s in st2)
+
+    # ---- roofline of the dominant kernel (from the live phase timings) ----
+    peaks, peak_src = measured_peaks()
+    clocks = clk.summary()
+    f_sm = (clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    fp64_peak = 2 * FP64_FMA_PER_SM_CLK * N_SM * f_sm / 1e12  # TFLOP/s
+    n_pairs = pr.n_pairs
+    fill_flops = n_nodes * fill_flops_per_node(n_ch, n_pairs)
+    fill_ms = phases[2]
+    achieved = fill_flops / (fill_ms * 1e-3) / 1e12
+    roofline = {"kernel": "fill_kernel<FP64,3> (node values + segmented reduction)",
+                "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": None,
+                "peak_source": f"FP64 pipe: {FP64_FMA_PER_SM_CLK} DFMA/SM/clk x {N_SM} SMs x "
+                               f"{f_sm / 1e6:.0f} MHz (median SM clock under load)",
+                "flops_per_node": fill_flops_per_node(n_ch, n_pairs)}
+
+    # ---- accuracy against the oracle and the CPU baseline -----------------
+    cpu = None
+    acc = None
+    if rank == 0 and world == 1 and not (args.no_cpu_baseline and args.no_oracle_check):
+        import oracle
+
+        oracle.build()
+        t0 = time.perf_counter()
+        Pref = oracle.P0(w["p_edges"], w["q_edges"], *w["nodes"], n_ch)
+        t_asm = time.perf_counter() - t0
+        cpu = {"value": n_nodes / t_asm / 1e9, "unit": "Gnodes/s", "cores": oracle.num_threads(),
+               "kind": "oracle",
+               "sample": "P0 assembly (count + fill) of the full 200x200 lattice, 81.9M nodes, once"}
+        if not args.no_oracle_check:
+            opr = oracle.Problem(dict(pe=w["p_edges"], qe=w["q_edges"], n_p=nn[0], n_q=nn[1],
+                                      n_x=nn[2], n_ch=n_ch, V=list(w["V"]), a=list(w["a"]),
+                                      n_pair_nodes=8), P=Pref)
+            t0 = time.perf_counter()
+            refs = [opr.solve_gmres(E, tol=1e-12, max_iter=300)["U00"] for E in energies]
+            t_solve = time.perf_counter() - t0
+            cpu["solve_energies_per_s"] = len(energies) / t_solve
+            errs = [abs(u - r) / abs(r) for u, r in zip(recs[-1]["U"], refs)]
+            acc = {"max_rel_err_U00": max(errs), "within_1e-6": int(sum(e < 1e-6 for e in errs)),
+                   "n": len(errs)}
+
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "Gnodes/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": step_ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "energies": energies, "assembly": "FP64",
+                   "solve": "Krylov (vector Pade) FP64, rel residual 1e-10",
+                   "l2": "flushed (512 MB write) before every timed step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "assembly": {"ms": asm_ms, "count_ms": phases[0], "scan_ms": phases[1], "fill_ms": phases[2],
+                     "nnz_cells": recs[-1]["nnz"]},
+        "solve": {"value": energies_per_s, "unit": "energies/s", "ms": solve_ms,
+                  "k_applications": recs[-1]["n_kapply"], "accuracy_vs_oracle": acc},
+        "roofline": roofline,
+        "roofline_peak_source": peak_src,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * n_nodes / e2e_s / 1e9, "unit": "Gnodes/s",
+                "s_per_step": e2e_s, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "what": "Problem create (host setup + uploads) + assemble + solve with host "
+                        "energies and host U00, per step"},
+        "gpu_launches": launches // max(args.steps, 1) * args.steps,
+        "gpu_launches_per_step": launches / max(args.steps, 1),
+        "clocks": clocks,
+        "wall_s_timed": wall,
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,209 @@
+/*
+ * wpcd.h -- C ABI of the GB300 (sm_103a) library for the hot path of the
+ * wave-packet continuum-discretisation (WPCD) Faddeev method of
+ * Pomerantsev, Kukulin, Rubtsova and Sakhiev, "Fast GPU-based calculations
+ * in few-body quantum scattering" (arXiv:1508.07441).
+ *
+ * The calls follow the paper's statement of the problem (Sec. 3.3, the four
+ * steps of the numerical scheme): build the packet grids and the pair
+ * quantities (step 1), assemble the lattice permutation matrix P0 (step 2),
+ * build the channel resolvent G1 (step 3) and solve the matrix Faddeev
+ * equation by iterating K = O P0 Vt G1 and summing the iterates (step 4).
+ *
+ * System: three identical spinless bosons, hbar = m = 1, pair potential
+ * V(r) = sum_k V_k exp(-r^2 / a_k), total orbital momentum L = 0, channels
+ * alpha = (l, lambda = l) for l = 0 .. n_ch-1.  Momenta are Jacobi momenta p
+ * (pair) and q (spectator); the free energy is p^2 + 3 q^2 / 4.
+ *
+ * Conventions used by every call:
+ *   - cell index c = i*M + j for p-bin i in [0, N) and q-bin j in [0, M);
+ *   - channel-basis vector index r = ch*N*M + k*M + j (k: pair eigenstate,
+ *     ascending energy, k = 0 the dimer); complex vectors are interleaved
+ *     (re, im) doubles (or floats where stated);
+ *   - (l, l') channel pairs with l + l' even, ordered by l then l'
+ *     (n_pairs of them: 1, 5, 13 for n_ch = 1, 3, 5);
+ *   - P0 is block-CSR over cells: row_ptr[N*M + 1] (int64), col[nnz]
+ *     (int32, ascending within a row), val[n_pairs][nnz] (pair-major), one
+ *     value per (l, l') pair of each nonzero cell pair.
+ *
+ * Ownership: the library allocates and owns everything behind a handle
+ * (device memory via cudaMalloc on the problem's device) until the matching
+ * *_destroy.  Caller arrays are never retained.  Pointers documented as
+ * "device" must be device (or managed) memory on the problem's device;
+ * "host" pointers are ordinary host memory.  `stream` is a cudaStream_t
+ * (NULL: the legacy default stream); calls that return results to host
+ * memory synchronise that stream before returning.
+ *
+ * Errors: every call returns a wpcd_status (0 on success, < 0 on failure) and
+ * leaves a message for wpcd_last_error() (thread-local).  No call aborts or
+ * lets a C++ exception escape.  Invalid sizes, non-monotone edges, NaN
+ * inputs, energies without an open elastic channel and out-of-range
+ * channels are rejected with WPCD_EINVAL / WPCD_ENOBOUND before any launch.
+ */
+#ifndef WPCD_H
+#define WPCD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int wpcd_status;
+
+#define WPCD_OK 0
+#define WPCD_EINVAL -1      /* invalid argument */
+#define WPCD_ENOMEM -2      /* allocation failed */
+#define WPCD_ECUDA -3       /* CUDA runtime error (message has the detail) */
+#define WPCD_ENOCONV -4     /* summation did not reach the tolerance */
+#define WPCD_EBREAKDOWN -5  /* zero divisor in the Pade table / Krylov basis */
+#define WPCD_ETIMEOUT -6    /* a device-side wait ran out of its budget */
+#define WPCD_ENOBOUND -7    /* no bound pair state / energy below threshold */
+
+/* arithmetic of the assembled values and of the solve */
+#define WPCD_FP64 0   /* all node values and sums in FP64 */
+#define WPCD_FP32C 1  /* FP64 binning, FP32 node values, compensated sums */
+
+/* summation of the iterates */
+#define WPCD_SUM_KRYLOV 0 /* vector form: minimal-residual extrapolation of
+                             the iterates through an orthonormal basis */
+#define WPCD_SUM_WYNN 1   /* scalar Pade approximants of sum_n c_n by
+                             Wynn's epsilon algorithm (the paper's route) */
+
+/* Thread-local text of the last error on this thread ("" if none). */
+const char *wpcd_last_error(void);
+
+/* ABI version (major * 10000 + minor * 100 + patch). */
+int wpcd_version(void);
+
+/* Number of CUDA kernel launches this library has issued in this process
+ * (all devices, all threads); lets a caller count the device work of a
+ * region by differencing. */
+int64_t wpcd_launch_count(void);
+
+/* Step 1, packet grid (Sec. 2.2 Eq. ip, Sec. 2.4 Eq. xij): n_bins + 1 edges
+ * of the tangent map k_n = s tan(pi n / (2 (n_bins + 1))), s chosen so that
+ * the last edge is k_max; edges[0] = 0.  edges: host, n_bins + 1 doubles.
+ * EINVAL if n_bins < 1 or k_max is not positive and finite. */
+wpcd_status wpcd_tangent_edges(int n_bins, double k_max, double *edges);
+
+/* Description of one three-body problem (all pointers host, read during
+ * wpcd_problem_create only). */
+typedef struct {
+  int N, M;               /* number of p-bins and q-bins */
+  const double *p_edges;  /* N + 1 strictly increasing, p_edges[0] = 0 */
+  const double *q_edges;  /* M + 1 strictly increasing, q_edges[0] = 0 */
+  int n_p, n_q, n_x;      /* GL nodes per p-bin, per q-bin, and in y on [-1, 1] */
+  int n_ch;               /* channels l = 0 .. n_ch - 1 (1 <= n_ch <= 5) */
+  int n_terms;            /* Gaussian terms of V(r) */
+  const double *V;        /* strengths V_k */
+  const double *a;        /* ranges a_k > 0 (V_k exp(-r^2 / a_k)) */
+  int n_pair_nodes;       /* GL nodes per bin for the pair double integrals */
+  int device;             /* CUDA device ordinal */
+} wpcd_problem_desc;
+
+typedef struct wpcd_problem wpcd_problem;
+typedef struct wpcd_P wpcd_P;
+
+/* Step 1 (Sec. 3.3, "processing of the input data"; Sec. 2.2 Eq. vpot and
+ * Eq. exp_z): free-packet potential matrices v_l, diagonalisation of
+ * h1 = h0 + v in every channel (rotation matrices O, energies eps),
+ * Vt = O^T V1 = v O^T, node and edge tables, all uploaded to the device.
+ * Runs on the host in FP64 (the paper calls this step negligible).
+ * ENOBOUND if channel 0 has no bound pair state. */
+wpcd_status wpcd_problem_create(const wpcd_problem_desc *desc, wpcd_problem **out);
+void wpcd_problem_destroy(wpcd_problem *pr);
+
+/* dim = n_ch*N*M, n_pairs, eps_bound = lowest eigenvalue of channel 0. */
+wpcd_status wpcd_problem_info(const wpcd_problem *pr, int *dim, int *n_pairs, double *eps_bound);
+
+/* Host copies of channel l's eps[N], O[N][N] (row k = eigenvector k in the
+ * free-packet basis, largest component positive) and v[N][N]; any output
+ * may be NULL. */
+wpcd_status wpcd_problem_pair(const wpcd_problem *pr, int l, double *eps, double *O, double *v);
+
+/* Step 2 (Sec. 3.2 Eqs. perm_z, perm, gal; Sec. 4.2 pre-selection and
+ * nonzero elements): assemble P0 on the device by quadrature-node binning.
+ * Every source cell's (p, q, y) GL nodes are mapped through the recoupled
+ * momenta p' = -(p/2 + 3q/4), q' = p - q/2, binned against the squared
+ * edges in FP64 (bin k holds [e_k^2, e_{k+1}^2), the last bin also e_N^2;
+ * larger values leave the grid), and summed per target cell:
+ *   P0[(l,c),(l',c')] = sqrt((2l+1)(2l'+1)) / sqrt(B_i Bq_j B_i' Bq_j')
+ *                       * sum_nodes w p^2 q^2 P_l(y) P_l'(y') [node -> c'].
+ * prec = WPCD_FP64 or WPCD_FP32C.  Two passes (count, then fill) with no
+ * atomics: the result is bit-reproducible for a given device.
+ * Runs on `stream` and returns when the assembly has completed (the stream
+ * is synchronised twice: for the nonzero count, and at the end). */
+wpcd_status wpcd_assemble_P(wpcd_problem *pr, int prec, void *stream, wpcd_P **out);
+void wpcd_P_destroy(wpcd_P *P);
+
+/* nnz (cell pairs), n_pairs, prec, and the timing of the last assembly in
+ * milliseconds (count pass + scan + fill; CUDA events); any may be NULL. */
+wpcd_status wpcd_P_info(const wpcd_P *P, int64_t *nnz, int *n_pairs, int *prec, float *ms);
+
+/* Device time of each assembly phase of P, in milliseconds, from CUDA events
+ * recorded on the assembly stream: ms[0] count pass (map, bin, sort, count),
+ * ms[1] scan, ms[2] fill pass (values and segmented reduction). */
+wpcd_status wpcd_P_timing(const wpcd_P *P, float ms[3]);
+
+/* Copy P0 out: row_ptr[N*M + 1], col[nnz], val[n_pairs][nnz] as FP64 (FP32C
+ * values are widened).  Destinations may be host or device memory; any may
+ * be NULL.  Synchronises `stream`. */
+wpcd_status wpcd_P_export(const wpcd_P *P, int64_t *row_ptr, int32_t *col, double *val,
+                          void *stream);
+
+/* Step 3 (Sec. 2.1 Eq. g_tot, Sec. 2.3 energy averaging, Sec. 2.4): the
+ * channel resolvent G1 at n_E energies, each averaged over its on-shell
+ * bin [E_lo, E_hi] = eps_b + 3/4 [q_j0^2, q_j0+1^2]:
+ *   g_kj = [Phi_j(E_hi - eps_k) - Phi_j(E_lo - eps_k)] / (D Bq_j)
+ *          - i pi / (D Bq_j) int_{bin j} q^2 dq theta(E_lo < eps_k + 3q^2/4 < E_hi),
+ *   Phi_j(a) = int_{bin j} q^2 ln|a - 3q^2/4| dq,  D = E_hi - E_lo.
+ * E: host [n_E].  g: device [n_E][dim] interleaved complex FP64.
+ * j0, D: host [n_E] (may be NULL).  ENOBOUND if some E <= eps_b; EINVAL if
+ * its on-shell momentum lies beyond the q grid. */
+wpcd_status wpcd_resolvent(const wpcd_problem *pr, const double *E, int n_E, double *g, int *j0,
+                           double *D, void *stream);
+
+/* One application of the Faddeev kernel (Sec. 3.3 Eq. kernel):
+ * y = O P0 Vt (g o x), FP64.  g: device [dim] complex or NULL (G1 = 1).
+ * x, y: device [dim] complex, distinct. */
+wpcd_status wpcd_kapply(const wpcd_problem *pr, const wpcd_P *P, const double *g, const double *x,
+                        double *y, void *stream);
+
+typedef struct {
+  int method;      /* WPCD_SUM_KRYLOV or WPCD_SUM_WYNN */
+  int max_iter;    /* cap on K applications (<= 512) */
+  int min_iter;    /* Wynn: minimum number of terms before stopping */
+  double tol;      /* Krylov: relative residual; Wynn: relative change */
+  int check_every; /* Krylov: read the residual estimate back every n steps */
+} wpcd_solve_opts;
+
+typedef struct {
+  int status;        /* per-energy status */
+  int n_kapply;      /* K applications used */
+  int j0;            /* on-shell q-bin */
+  double D;          /* on-shell energy width */
+  double relres;     /* Krylov: final relative residual estimate */
+  double U00[2];     /* on-shell element <Z_{0,0,j0}|U|Z_{0,0,j0}> */
+  double S[2];       /* S = 1 - 2 pi i U00 / D */
+  double A[2];       /* paper's amplitude (2/(3 q0)) U00 / (q_j0+1 - q_j0) */
+  float ms;          /* device time of this energy's solve (CUDA events) */
+} wpcd_solve_stats;
+
+/* Step 4 (Sec. 3.3: iterations of the matrix equation and Pade
+ * summation): for every energy, the on-shell element U00 of
+ * U = P V1 + P V1 G1 U, from the iterates of K = O P0 Vt G1 started at the
+ * Born term u0 = O P0 Vt e0.  FP64 throughout (P0 of either precision is
+ * applied with FP64 accumulation).  E: host [n_E]; U00: host [n_E] complex
+ * (interleaved); stats: host [n_E] or NULL.  Returns the worst per-energy
+ * status (ENOCONV / EBREAKDOWN still deliver the best estimate). */
+wpcd_status wpcd_solve(wpcd_problem *pr, const wpcd_P *P, const double *E, int n_E,
+                       const wpcd_solve_opts *opts, double *U00, wpcd_solve_stats *stats,
+                       void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WPCD_H */

@@ -76,7 +76,7 @@ def lib():
                 "orc_n_pairs": (c_int, [c_int]),
                 "orc_P0_count": (c_i64, [c_int, _D, c_int, _D, c_int, c_int, c_int, _I64]),
                 "orc_P0_fill": (c_int, [c_int, _D, c_int, _D, c_int, c_int, c_int, c_int, _I64,
-                                        _I32, _D, _D]),
+                                        _I32, _D, _D, _D]),
                 "orc_P0_node_totals": (c_int, [c_int, _D, c_int, _D, c_int, c_int, c_int, c_int, _D]),
                 "orc_P0_normalize": (None, [c_int, _D, c_int, _D, c_int, _I64, _I32, _D]),
                 "orc_onshell": (c_int, [c_int, _D, c_double, c_double, _INT, _D, _D, _D]),
@@ -173,11 +173,12 @@ def pair_list(n_ch: int):
     return [(l, lp) for l in range(n_ch) for lp in range(n_ch) if (l + lp) % 2 == 0]
 
 
-def P0(pe, qe, n_p, n_q, n_x, n_ch, normalize=True, with_outgrid=False):
+def P0(pe, qe, n_p, n_q, n_x, n_ch, normalize=True, with_outgrid=False, with_abs=False):
     """Node-binned lattice P0 as block-CSR over cells.
 
     Returns dict(row_ptr int64[N*M+1], col int32[nnz], val f64[nnz, n_pairs],
-    outgrid f64[N*M, n_pairs] (unnormalised, optional)).
+    outgrid f64[N*M, n_pairs] (unnormalised, optional), absval f64[nnz,
+    n_pairs] (sums of |terms|, normalised like val, optional)).
     """
     pe, qe = _f64(pe), _f64(qe)
     N, M = len(pe) - 1, len(qe) - 1
@@ -188,12 +189,17 @@ def P0(pe, qe, n_p, n_q, n_x, n_ch, normalize=True, with_outgrid=False):
     col = np.zeros(max(nnz, 1), dtype=np.int32)
     val = np.zeros((max(nnz, 1), npair))
     og = np.zeros((N * M, npair)) if with_outgrid else None
+    av = np.zeros((max(nnz, 1), npair)) if with_abs else None
     st = lib().orc_P0_fill(N, _p(pe), M, _p(qe), n_p, n_q, n_x, n_ch, _p(rp, _I64), _p(col, _I32),
-                           _p(val), _p(og))
+                           _p(val), _p(og), _p(av))
     assert st == OK, st
     if normalize:
         lib().orc_P0_normalize(N, _p(pe), M, _p(qe), n_ch, _p(rp, _I64), _p(col, _I32), _p(val))
+        if with_abs:
+            lib().orc_P0_normalize(N, _p(pe), M, _p(qe), n_ch, _p(rp, _I64), _p(col, _I32), _p(av))
     out = dict(row_ptr=rp, col=col[:nnz], val=val[:nnz], N=N, M=M, n_ch=n_ch)
+    if with_abs:
+        out["absval"] = av[:nnz]
     if with_outgrid:
         out["outgrid"] = og
     return out

@@ -493,9 +493,14 @@ static int cmp_int(const void *a, const void *b) {
 
 /* Step 2b: node-binned values, unnormalised (the bare node sums), columns
  * ascending within each row; val is [nnz][n_pairs].  outgrid (optional,
- * [N*M][n_pairs]) receives the weight of nodes that leave the grid. */
+ * [N*M][n_pairs]) receives the weight of nodes that leave the grid.  absval
+ * (optional, [nnz][n_pairs]) receives the sums of |terms|, the scale of the
+ * rounding error of each element (elements whose terms cancel exactly, e.g.
+ * l' = 0 with the GL rule integrating P_l(y) to zero, are rounding noise of
+ * that size). */
 int orc_P0_fill(int N, const double *pe, int M, const double *qe, int np_, int nq, int nx,
-                int n_ch, const int64_t *row_ptr, int32_t *col, double *val, double *outgrid) {
+                int n_ch, const int64_t *row_ptr, int32_t *col, double *val, double *outgrid,
+                double *absval) {
   lattice L;
   if (n_ch < 1) return ORC_EINVAL;
   if (lattice_init(&L, N, pe, M, qe, np_, nq, nx) != ORC_OK) return ORC_ENOMEM;
@@ -507,16 +512,17 @@ int orc_P0_fill(int N, const double *pe, int M, const double *qe, int np_, int n
 #pragma omp parallel
   {
     double *acc = calloc((size_t)ncell * npair, sizeof(double));
+    double *aacc = absval ? calloc((size_t)ncell * npair, sizeof(double)) : NULL;
     unsigned char *seen = calloc((size_t)ncell, 1);
     int *touched = malloc(sizeof(int) * (size_t)np_ * nq * nx);
     double Py[32], Pyp[32], og[64];
-    if (!acc || !seen || !touched) {
+    if (!acc || !seen || !touched || (absval && !aacc)) {
 #pragma omp atomic write
       err = 1;
     }
 #pragma omp for schedule(dynamic, 8)
     for (int c = 0; c < ncell; ++c) {
-      if (!acc || !seen || !touched) continue;
+      if (!acc || !seen || !touched || (absval && !aacc)) continue;
       int i = c / M, j = c % M, nt = 0;
       for (int k = 0; k < npair; ++k) og[k] = 0.0;
       for (int a = 0; a < np_; ++a)
@@ -533,7 +539,11 @@ int orc_P0_fill(int N, const double *pe, int M, const double *qe, int np_, int n
               continue;
             }
             if (!seen[t]) { seen[t] = 1; touched[nt++] = t; }
-            for (int k = 0; k < npair; ++k) acc[(size_t)t * npair + k] += W * Py[pl[k]] * Pyp[plp[k]];
+            for (int k = 0; k < npair; ++k) {
+              double term = W * Py[pl[k]] * Pyp[plp[k]];
+              acc[(size_t)t * npair + k] += term;
+              if (aacc) aacc[(size_t)t * npair + k] += fabs(term);
+            }
           }
       if (row_ptr[c + 1] - row_ptr[c] != nt) {
 #pragma omp atomic write
@@ -547,6 +557,10 @@ int orc_P0_fill(int N, const double *pe, int M, const double *qe, int np_, int n
         for (int m = 0; m < npair; ++m) {
           val[(o + k) * npair + m] = acc[(size_t)t * npair + m];
           acc[(size_t)t * npair + m] = 0.0;
+          if (aacc) {
+            absval[(o + k) * npair + m] = aacc[(size_t)t * npair + m];
+            aacc[(size_t)t * npair + m] = 0.0;
+          }
         }
         seen[t] = 0;
       }
@@ -554,6 +568,7 @@ int orc_P0_fill(int N, const double *pe, int M, const double *qe, int np_, int n
         for (int k = 0; k < npair; ++k) outgrid[(size_t)c * npair + k] = og[k];
     }
     free(acc);
+    free(aacc);
     free(seen);
     free(touched);
   }

@@ -1,0 +1,327 @@
+// extern "C" entry points of include/wpcd.h: argument validation, handle
+// lifetime, uploads, and error reporting.  No C++ exception crosses the ABI.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "wpcd_internal.h"
+
+namespace wpcd {
+
+static thread_local std::string g_last_error;
+static std::atomic<int64_t> g_launches{0};
+
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+wpcd_status set_error(wpcd_status st, const std::string &msg) {
+  g_last_error = msg;
+  return st;
+}
+
+wpcd_status cuda_error(cudaError_t e, const char *what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return WPCD_ECUDA;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+static void free_tables(DeviceTables &d) {
+  double **all[] = {&d.pe2, &d.qe2, &d.pn, &d.wp, &d.qn, &d.wq, &d.yn, &d.wy, &d.rsb, &d.qe, &d.eps, &d.O, &d.Vt};
+  for (double **p : all) {
+    cudaFree(*p);
+    *p = nullptr;
+  }
+}
+
+static wpcd_status upload(double **dst, const std::vector<double> &src) {
+  cudaError_t e = cudaMalloc(dst, sizeof(double) * (src.empty() ? 1 : src.size()));
+  if (e != cudaSuccess) return cuda_error(e, "cudaMalloc (problem tables)");
+  if (!src.empty()) {
+    e = cudaMemcpy(*dst, src.data(), sizeof(double) * src.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy (problem tables)");
+  }
+  return WPCD_OK;
+}
+
+static bool valid_edges(const double *e, int n) {
+  if (!e || !(e[0] == 0.0)) return false;
+  for (int k = 0; k < n; ++k)
+    if (!(e[k + 1] > e[k]) || !std::isfinite(e[k + 1])) return false;
+  return true;
+}
+
+static wpcd_status create(const wpcd_problem_desc *d, wpcd_problem **out) {
+  if (!d || !out) return set_error(WPCD_EINVAL, "null argument");
+  *out = nullptr;
+  if (d->N < 1 || d->M < 1) return set_error(WPCD_EINVAL, "N and M must be >= 1");
+  if ((int64_t)d->N * d->M > (1 << 24)) return set_error(WPCD_EINVAL, "lattice too large (N*M > 2^24)");
+  if (d->n_p < 1 || d->n_q < 1 || d->n_x < 1 || d->n_p > 64 || d->n_q > 64 || d->n_x > 256)
+    return set_error(WPCD_EINVAL, "node counts must be in [1, 64] (p, q) and [1, 256] (x)");
+  if (d->n_ch < 1 || d->n_ch > 5) return set_error(WPCD_EINVAL, "n_ch must be in [1, 5]");
+  if (d->n_terms < 1 || !d->V || !d->a) return set_error(WPCD_EINVAL, "potential needs >= 1 term");
+  for (int k = 0; k < d->n_terms; ++k)
+    if (!std::isfinite(d->V[k]) || !(d->a[k] > 0.0) || !std::isfinite(d->a[k]))
+      return set_error(WPCD_EINVAL, "potential terms must be finite with a_k > 0");
+  if (d->n_pair_nodes < 1 || d->n_pair_nodes > 64) return set_error(WPCD_EINVAL, "n_pair_nodes in [1, 64]");
+  if (!valid_edges(d->p_edges, d->N) || !valid_edges(d->q_edges, d->M))
+    return set_error(WPCD_EINVAL, "edges must start at 0 and increase strictly");
+  int ndev = 0;
+  cudaError_t ce = cudaGetDeviceCount(&ndev);
+  if (ce != cudaSuccess) return cuda_error(ce, "cudaGetDeviceCount");
+  if (d->device < 0 || d->device >= ndev) return set_error(WPCD_EINVAL, "no such CUDA device");
+  ce = cudaSetDevice(d->device);
+  if (ce != cudaSuccess) return cuda_error(ce, "cudaSetDevice");
+
+  wpcd_problem *pr = new (std::nothrow) wpcd_problem();
+  if (!pr) return set_error(WPCD_ENOMEM, "host allocation");
+  pr->device = d->device;
+  pr->N = d->N;
+  pr->M = d->M;
+  pr->n_p = d->n_p;
+  pr->n_q = d->n_q;
+  pr->n_x = d->n_x;
+  pr->n_ch = d->n_ch;
+  int np = 0;
+  for (int l = 0; l < d->n_ch; ++l)
+    for (int lp = 0; lp < d->n_ch; ++lp)
+      if (((l + lp) & 1) == 0) {
+        pr->pair_l[np] = l;
+        pr->pair_lp[np] = lp;
+        ++np;
+      }
+  pr->n_pairs = np;
+  pr->pe.assign(d->p_edges, d->p_edges + d->N + 1);
+  pr->qe.assign(d->q_edges, d->q_edges + d->M + 1);
+  const int N = d->N, M = d->M;
+  // pair quantities per channel
+  pr->eps.assign((size_t)d->n_ch * N, 0.0);
+  pr->O.assign((size_t)d->n_ch * N * N, 0.0);
+  pr->v.assign((size_t)d->n_ch * N * N, 0.0);
+  pr->Vt.assign((size_t)d->n_ch * N * N, 0.0);
+  for (int l = 0; l < d->n_ch; ++l) {
+    std::vector<double> v, eps, O;
+    pair_setup(N, d->p_edges, d->n_pair_nodes, l, d->n_terms, d->V, d->a, v, eps, O);
+    if ((int)eps.size() != N) {
+      delete pr;
+      return set_error(WPCD_EINVAL, "pair Hamiltonian eigensolver did not converge");
+    }
+    std::copy(eps.begin(), eps.end(), pr->eps.begin() + (size_t)l * N);
+    std::copy(O.begin(), O.end(), pr->O.begin() + (size_t)l * N * N);
+    std::copy(v.begin(), v.end(), pr->v.begin() + (size_t)l * N * N);
+    // Vt = O^T V1 in the channel basis = v O^T:  Vt[i][k] = sum_m v[i][m] O[k][m]
+    double *Vt = pr->Vt.data() + (size_t)l * N * N;
+    for (int i = 0; i < N; ++i)
+      for (int k = 0; k < N; ++k) {
+        double s = 0.0;
+        for (int m = 0; m < N; ++m) s += v[(size_t)i * N + m] * O[(size_t)k * N + m];
+        Vt[(size_t)i * N + k] = s;
+      }
+  }
+  pr->eps_b = pr->eps[0];
+  if (!(pr->eps_b < 0.0)) {
+    delete pr;
+    return set_error(WPCD_ENOBOUND, "channel 0 has no bound pair state on this grid");
+  }
+  // node and edge tables (canonical node placement: mid + half * t)
+  std::vector<double> tp(d->n_p), wp(d->n_p), tq(d->n_q), wq(d->n_q), ty(d->n_x), wy(d->n_x);
+  gauss_legendre(d->n_p, tp.data(), wp.data());
+  gauss_legendre(d->n_q, tq.data(), wq.data());
+  gauss_legendre(d->n_x, ty.data(), wy.data());
+  std::vector<double> pn((size_t)N * d->n_p), pw((size_t)N * d->n_p), qn((size_t)M * d->n_q),
+      qw((size_t)M * d->n_q), pe2(N + 1), qe2(M + 1), rsb((size_t)N * M);
+  for (int i = 0; i < N; ++i) {
+    double lo = pr->pe[i], hi = pr->pe[i + 1], half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
+    for (int a = 0; a < d->n_p; ++a) {
+      double p = mid + half * tp[a];
+      pn[(size_t)i * d->n_p + a] = p;
+      pw[(size_t)i * d->n_p + a] = half * wp[a] * p * p;
+    }
+  }
+  for (int j = 0; j < M; ++j) {
+    double lo = pr->qe[j], hi = pr->qe[j + 1], half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
+    for (int b = 0; b < d->n_q; ++b) {
+      double q = mid + half * tq[b];
+      qn[(size_t)j * d->n_q + b] = q;
+      qw[(size_t)j * d->n_q + b] = half * wq[b] * q * q;
+    }
+  }
+  for (int k = 0; k <= N; ++k) pe2[k] = pr->pe[k] * pr->pe[k];
+  for (int k = 0; k <= M; ++k) qe2[k] = pr->qe[k] * pr->qe[k];
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < M; ++j)
+      rsb[(size_t)i * M + j] = 1.0 / std::sqrt(shell_volume(pr->pe[i], pr->pe[i + 1]) *
+                                               shell_volume(pr->qe[j], pr->qe[j + 1]));
+  wpcd_status st = WPCD_OK;
+  DeviceTables &t = pr->d;
+  if ((st = upload(&t.pe2, pe2)) || (st = upload(&t.qe2, qe2)) || (st = upload(&t.pn, pn)) ||
+      (st = upload(&t.wp, pw)) || (st = upload(&t.qn, qn)) || (st = upload(&t.wq, qw)) ||
+      (st = upload(&t.yn, ty)) || (st = upload(&t.wy, wy)) || (st = upload(&t.rsb, rsb)) ||
+      (st = upload(&t.qe, pr->qe)) || (st = upload(&t.eps, pr->eps)) || (st = upload(&t.O, pr->O)) ||
+      (st = upload(&t.Vt, pr->Vt))) {
+    free_tables(t);
+    delete pr;
+    return st;
+  }
+  *out = pr;
+  return WPCD_OK;
+}
+
+}  // namespace wpcd
+
+using namespace wpcd;
+
+#define WPCD_GUARD_BEGIN try {
+#define WPCD_GUARD_END                                                   \
+  }                                                                      \
+  catch (const std::bad_alloc &) {                                       \
+    return set_error(WPCD_ENOMEM, "host allocation failed");             \
+  }                                                                      \
+  catch (...) {                                                          \
+    return set_error(WPCD_EINVAL, "internal error (unexpected exception)"); \
+  }
+
+extern "C" {
+
+const char *wpcd_last_error(void) { return g_last_error.c_str(); }
+
+int wpcd_version(void) { return 100; }
+
+int64_t wpcd_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+wpcd_status wpcd_tangent_edges(int n_bins, double k_max, double *edges) {
+  if (n_bins < 1 || !(k_max > 0.0) || !std::isfinite(k_max) || !edges)
+    return set_error(WPCD_EINVAL, "tangent edges need n_bins >= 1, finite k_max > 0");
+  const double half_pi = 1.5707963267948966192;
+  double span = half_pi / (n_bins + 1.0);
+  double scale = k_max / std::tan(span * n_bins);
+  edges[0] = 0.0;
+  for (int n = 1; n < n_bins; ++n) edges[n] = scale * std::tan(span * n);
+  edges[n_bins] = k_max;
+  return WPCD_OK;
+}
+
+wpcd_status wpcd_problem_create(const wpcd_problem_desc *desc, wpcd_problem **out) {
+  WPCD_GUARD_BEGIN
+  clear_error();
+  return create(desc, out);
+  WPCD_GUARD_END
+}
+
+void wpcd_problem_destroy(wpcd_problem *pr) {
+  if (!pr) return;
+  cudaSetDevice(pr->device);
+  free_tables(pr->d);
+  delete pr;
+}
+
+wpcd_status wpcd_problem_info(const wpcd_problem *pr, int *dim, int *n_pairs, double *eps_bound) {
+  if (!pr) return set_error(WPCD_EINVAL, "null problem");
+  if (dim) *dim = pr->n_ch * pr->N * pr->M;
+  if (n_pairs) *n_pairs = pr->n_pairs;
+  if (eps_bound) *eps_bound = pr->eps_b;
+  return WPCD_OK;
+}
+
+wpcd_status wpcd_problem_pair(const wpcd_problem *pr, int l, double *eps, double *O, double *v) {
+  if (!pr || l < 0 || l >= pr->n_ch) return set_error(WPCD_EINVAL, "bad problem or channel");
+  const size_t N = pr->N;
+  if (eps) std::memcpy(eps, pr->eps.data() + l * N, sizeof(double) * N);
+  if (O) std::memcpy(O, pr->O.data() + l * N * N, sizeof(double) * N * N);
+  if (v) std::memcpy(v, pr->v.data() + l * N * N, sizeof(double) * N * N);
+  return WPCD_OK;
+}
+
+wpcd_status wpcd_assemble_P(wpcd_problem *pr, int prec, void *stream, wpcd_P **out) {
+  WPCD_GUARD_BEGIN
+  clear_error();
+  if (!pr || !out) return set_error(WPCD_EINVAL, "null argument");
+  *out = nullptr;
+  return assemble(pr, prec, static_cast<cudaStream_t>(stream), out);
+  WPCD_GUARD_END
+}
+
+void wpcd_P_destroy(wpcd_P *P) {
+  if (!P) return;
+  cudaSetDevice(P->pr->device);
+  cudaFree(P->row_ptr);
+  cudaFree(P->col);
+  cudaFree(P->val64);
+  cudaFree(P->val32);
+  delete P;
+}
+
+wpcd_status wpcd_P_info(const wpcd_P *P, int64_t *nnz, int *n_pairs, int *prec, float *ms) {
+  if (!P) return set_error(WPCD_EINVAL, "null P");
+  if (nnz) *nnz = P->nnz;
+  if (n_pairs) *n_pairs = P->n_pairs;
+  if (prec) *prec = P->prec;
+  if (ms) *ms = P->ms;
+  return WPCD_OK;
+}
+
+wpcd_status wpcd_P_timing(const wpcd_P *P, float ms[3]) {
+  if (!P || !ms) return set_error(WPCD_EINVAL, "null argument");
+  for (int i = 0; i < 3; ++i) ms[i] = P->ms_phase[i];
+  return WPCD_OK;
+}
+
+wpcd_status wpcd_P_export(const wpcd_P *P, int64_t *row_ptr, int32_t *col, double *val, void *stream) {
+  WPCD_GUARD_BEGIN
+  if (!P) return set_error(WPCD_EINVAL, "null P");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  WPCD_CUDA_TRY(cudaSetDevice(P->pr->device));
+  const size_t ncell = (size_t)P->pr->N * P->pr->M;
+  if (row_ptr) WPCD_CUDA_TRY(cudaMemcpyAsync(row_ptr, P->row_ptr, sizeof(int64_t) * (ncell + 1), cudaMemcpyDefault, s));
+  if (col && P->nnz) WPCD_CUDA_TRY(cudaMemcpyAsync(col, P->col, sizeof(int32_t) * P->nnz, cudaMemcpyDefault, s));
+  if (val && P->nnz) {
+    const size_t n = (size_t)P->nnz * P->n_pairs;
+    if (P->prec == WPCD_FP64) {
+      WPCD_CUDA_TRY(cudaMemcpyAsync(val, P->val64, sizeof(double) * n, cudaMemcpyDefault, s));
+    } else {
+      std::vector<float> tmp(n);
+      WPCD_CUDA_TRY(cudaMemcpyAsync(tmp.data(), P->val32, sizeof(float) * n, cudaMemcpyDeviceToHost, s));
+      WPCD_CUDA_TRY(cudaStreamSynchronize(s));
+      std::vector<double> wide(tmp.begin(), tmp.end());
+      WPCD_CUDA_TRY(cudaMemcpy(val, wide.data(), sizeof(double) * n, cudaMemcpyDefault));
+    }
+  }
+  WPCD_CUDA_TRY(cudaStreamSynchronize(s));
+  return WPCD_OK;
+  WPCD_GUARD_END
+}
+
+wpcd_status wpcd_resolvent(const wpcd_problem *pr, const double *E, int n_E, double *g, int *j0,
+                           double *D, void *stream) {
+  WPCD_GUARD_BEGIN
+  clear_error();
+  if (!pr) return set_error(WPCD_EINVAL, "null problem");
+  return resolvent(pr, E, n_E, g, j0, D, static_cast<cudaStream_t>(stream));
+  WPCD_GUARD_END
+}
+
+wpcd_status wpcd_kapply(const wpcd_problem *pr, const wpcd_P *P, const double *g, const double *x,
+                        double *y, void *stream) {
+  WPCD_GUARD_BEGIN
+  clear_error();
+  if (!pr || !P || !x || !y || x == y) return set_error(WPCD_EINVAL, "bad kapply arguments");
+  if (P->pr != pr) return set_error(WPCD_EINVAL, "P was assembled for another problem");
+  return kapply(pr, P, g, x, y, static_cast<cudaStream_t>(stream));
+  WPCD_GUARD_END
+}
+
+wpcd_status wpcd_solve(wpcd_problem *pr, const wpcd_P *P, const double *E, int n_E,
+                       const wpcd_solve_opts *opts, double *U00, wpcd_solve_stats *stats, void *stream) {
+  WPCD_GUARD_BEGIN
+  clear_error();
+  if (!pr || !P) return set_error(WPCD_EINVAL, "null problem or P");
+  if (P->pr != pr) return set_error(WPCD_EINVAL, "P was assembled for another problem");
+  return solve(pr, P, E, n_E, opts, U00, stats, static_cast<cudaStream_t>(stream));
+  WPCD_GUARD_END
+}
+
+}  // extern "C"

@@ -1,0 +1,257 @@
+// Host mathematics of step 1 of the numerical scheme (Sec. 3.3): packet
+// grids, Gauss-Legendre tables, the pair potential in the free-packet basis
+// (Sec. 2.2 Eq. vpot) and the diagonalisation of h1 (Eq. exp_z).  FP64,
+// negligible time; everything here feeds the device kernels.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "wpcd_internal.h"
+
+namespace wpcd {
+
+// Gauss-Legendre nodes (ascending) and weights on [-1, 1]: Newton's method on
+// P_n with the derivative from P_n' = n (x P_n - P_{n-1}) / (x^2 - 1), started
+// from Tricomi's asymptotic node estimate, iterated in long double and
+// rounded once.
+void gauss_legendre(int n, double *t, double *w) {
+  const long double pi = 3.14159265358979323846264338327950288L;
+  for (int k = 1; k <= n; ++k) {
+    long double th = pi * (4.0L * k - 1.0L) / (4.0L * n + 2.0L);
+    long double x = (1.0L - (n - 1.0L) / (8.0L * n * n * n)) * cosl(th);
+    long double d = 0.0L;
+    for (int it = 0; it < 64; ++it) {
+      long double pm1 = 1.0L, p = x;  // P_0, P_1
+      for (int m = 2; m <= n; ++m) {
+        long double pn = ((2.0L * m - 1.0L) * x * p - (m - 1.0L) * pm1) / m;
+        pm1 = p;
+        p = pn;
+      }
+      if (n == 1) { p = x; pm1 = 1.0L; }
+      d = n * (x * p - pm1) / (x * x - 1.0L);
+      long double step = p / d;
+      x -= step;
+      if (fabsl(step) < 1e-28L) break;
+    }
+    long double pm1 = 1.0L, p = x;
+    for (int m = 2; m <= n; ++m) {
+      long double pn = ((2.0L * m - 1.0L) * x * p - (m - 1.0L) * pm1) / m;
+      pm1 = p;
+      p = pn;
+    }
+    if (n == 1) { p = x; pm1 = 1.0L; }
+    d = n * (x * p - pm1) / (x * x - 1.0L);
+    // k = 1 is the largest node
+    t[n - k] = (double)x;
+    w[n - k] = (double)(2.0L / ((1.0L - x * x) * d * d));
+  }
+}
+
+// exp(-z) i_l(z) for the modified spherical Bessel function i_l.
+// Small z: leading power-series terms.  Moderate z: Miller's downward
+// recurrence i_{n-1} = i_{n+1} + (2n+1)/z i_n (stable: i_n is the minimal
+// solution) normalised by exp(-z) i_0 = (1 - exp(-2z)) / (2z).  Large z: the
+// terminating expansion of i_l in powers of 1/(2z).
+double bessel_i_scaled(int l, double z) {
+  if (z == 0.0) return l == 0 ? 1.0 : 0.0;
+  if (z < 1e-3) {
+    double df = 1.0;
+    for (int m = 3; m <= 2 * l + 1; m += 2) df *= m;
+    double lead = std::pow(z, l) / df;
+    return lead * (1.0 + z * z / (2.0 * (2 * l + 3))) * std::exp(-z);
+  }
+  if (z > 40.0) {
+    double inv = 1.0 / (2.0 * z), term = 1.0, s_alt = 0.0, s_pos = 0.0;
+    for (int k = 0; k <= l; ++k) {
+      if (k > 0) term *= (double)(l + k) * (l - k + 1) / k * inv;  // (l+k)!/(k!(l-k)!) (2z)^-k
+      s_alt += (k % 2 ? -term : term);
+      s_pos += term;
+    }
+    double tail = ((l + 1) % 2 ? -1.0 : 1.0) * std::exp(-2.0 * z) * s_pos;
+    return (s_alt + tail) / (2.0 * z);
+  }
+  int top = l + 30 + (int)(2.0 * z);
+  double up = 0.0, cur = 1e-300, want = 0.0;
+  for (int n = top; n >= 1; --n) {
+    double down = up + (2.0 * n + 1.0) / z * cur;  // i_{n-1}
+    up = cur;
+    cur = down;
+    if (n - 1 == l) want = cur;
+    if (std::fabs(cur) > 1e250) {  // rescale to stay in range
+      cur *= 1e-250;
+      up *= 1e-250;
+      want *= 1e-250;
+    }
+  }
+  // cur = i_0 (unnormalised)
+  double i0s = -std::expm1(-2.0 * z) / (2.0 * z);
+  return want / cur * i0s;
+}
+
+// v_l(p, p') = (2/pi) int r^2 j_l(pr) V(r) j_l(p'r) dr for a sum of
+// Gaussians, partial-wave states normalised to delta(p - p')/p^2:
+//   sum_k V_k / (2 sqrt(pi) alpha^{3/2}) exp(-(p-p')^2/(4 alpha)) e^{-z} i_l(z),
+// alpha = 1/a_k, z = p p' / (2 alpha).
+double v_partial_wave(int l, double p, double pp, int n_terms, const double *V, const double *a) {
+  const double two_sqrt_pi = 3.5449077018110320546;
+  double s = 0.0;
+  for (int k = 0; k < n_terms; ++k) {
+    double alpha = 1.0 / a[k];
+    double z = 0.5 * p * pp * a[k];
+    double gauss = std::exp(-0.25 * (p - pp) * (p - pp) * a[k]);
+    s += V[k] / (two_sqrt_pi * alpha * std::sqrt(alpha)) * gauss * bessel_i_scaled(l, z);
+  }
+  return s;
+}
+
+// Symmetric eigenproblem: Householder reduction to tridiagonal form, then
+// implicit symmetric QR steps with Wilkinson shifts on the tridiagonal,
+// accumulating the orthogonal transformations.
+bool sym_eig(int n, std::vector<double> A, std::vector<double> &evals, std::vector<double> &rows) {
+  std::vector<double> Q((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
+  auto a = [&](int i, int j) -> double & { return A[(size_t)i * n + j]; };
+  auto q = [&](int i, int j) -> double & { return Q[(size_t)i * n + j]; };
+  std::vector<double> u(n), pvec(n), kvec(n);
+  // Householder: zero column k below the subdiagonal, A <- H A H, Q <- Q H
+  for (int k = 0; k + 2 < n; ++k) {
+    double alpha = 0.0;
+    for (int i = k + 1; i < n; ++i) alpha += a(i, k) * a(i, k);
+    alpha = std::sqrt(alpha);
+    if (alpha == 0.0) continue;
+    if (a(k + 1, k) > 0) alpha = -alpha;
+    std::fill(u.begin(), u.end(), 0.0);
+    u[k + 1] = a(k + 1, k) - alpha;
+    for (int i = k + 2; i < n; ++i) u[i] = a(i, k);
+    double unorm2 = 0.0;
+    for (int i = k + 1; i < n; ++i) unorm2 += u[i] * u[i];
+    if (unorm2 == 0.0) continue;
+    double beta = 2.0 / unorm2;
+    // p = beta A u ; K = p - (beta/2)(u.p) u ; A <- A - u K^T - K u^T
+    double up = 0.0;
+    for (int i = k; i < n; ++i) {
+      double s = 0.0;
+      for (int j = k + 1; j < n; ++j) s += a(i, j) * u[j];
+      pvec[i] = beta * s;
+    }
+    for (int i = 0; i < k; ++i) pvec[i] = 0.0;
+    for (int i = k + 1; i < n; ++i) up += u[i] * pvec[i];
+    for (int i = k; i < n; ++i) kvec[i] = pvec[i] - 0.5 * beta * up * u[i];
+    for (int i = k; i < n; ++i)
+      for (int j = k; j < n; ++j) a(i, j) -= u[i] * kvec[j] + kvec[i] * u[j];
+    for (int i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (int j = k + 1; j < n; ++j) s += q(i, j) * u[j];
+      s *= beta;
+      for (int j = k + 1; j < n; ++j) q(i, j) -= s * u[j];
+    }
+  }
+  std::vector<double> d(n), e(n, 0.0);
+  for (int i = 0; i < n; ++i) d[i] = a(i, i);
+  for (int i = 0; i + 1 < n; ++i) e[i] = a(i + 1, i);
+  // implicit symmetric QR on (d, e), deflating from the bottom
+  auto small = [&](int i) { return std::fabs(e[i]) <= 2.3e-16 * (std::fabs(d[i]) + std::fabs(d[i + 1])); };
+  int hi = n - 1, iters = 0;
+  while (hi > 0) {
+    if (small(hi - 1)) {
+      e[hi - 1] = 0.0;
+      --hi;
+      continue;
+    }
+    int st = hi - 1;
+    while (st > 0 && !small(st - 1)) --st;
+    if (st > 0) e[st - 1] = 0.0;
+    if (++iters > 100 * n) return false;
+    // Wilkinson shift from the trailing 2x2 block
+    double dd = 0.5 * (d[hi - 1] - d[hi]);
+    double ee = e[hi - 1];
+    double mu = d[hi] - ee * ee / (dd + (dd >= 0 ? 1.0 : -1.0) * std::hypot(dd, ee));
+    double x = d[st] - mu, z = e[st];
+    for (int k = st; k < hi; ++k) {
+      double r = std::hypot(x, z);
+      double c = r == 0.0 ? 1.0 : x / r, s = r == 0.0 ? 0.0 : z / r;
+      if (k > st) e[k - 1] = r;
+      double d0 = d[k], d1 = d[k + 1], e0 = e[k];
+      d[k] = c * c * d0 + 2 * c * s * e0 + s * s * d1;
+      d[k + 1] = s * s * d0 - 2 * c * s * e0 + c * c * d1;
+      e[k] = c * s * (d1 - d0) + (c * c - s * s) * e0;
+      if (k + 1 < hi) {
+        x = e[k];
+        z = s * e[k + 1];
+        e[k + 1] *= c;
+      }
+      for (int i = 0; i < n; ++i) {
+        double qk = q(i, k), qk1 = q(i, k + 1);
+        q(i, k) = c * qk + s * qk1;
+        q(i, k + 1) = -s * qk + c * qk1;
+      }
+    }
+  }
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return d[x] < d[y]; });
+  evals.assign(n, 0.0);
+  rows.assign((size_t)n * n, 0.0);
+  for (int k = 0; k < n; ++k) {
+    int c = order[k];
+    evals[k] = d[c];
+    int imax = 0;
+    double big = -1.0;
+    for (int i = 0; i < n; ++i)
+      if (std::fabs(q(i, c)) > big) { big = std::fabs(q(i, c)); imax = i; }
+    double sg = q(imax, c) < 0 ? -1.0 : 1.0;
+    for (int i = 0; i < n; ++i) rows[(size_t)k * n + i] = sg * q(i, c);
+  }
+  return true;
+}
+
+// Pair quantities of channel l: free-packet potential matrix v (Eq. vpot
+// with unit weight functions in the p^2 dp measure, n_nodes GL points per
+// bin), h1 = diag(<p^2>) + v and its eigen-decomposition (Eq. exp_z).
+void pair_setup(int N, const double *edges, int n_nodes, int l, int n_terms, const double *V,
+                const double *a, std::vector<double> &v, std::vector<double> &eps,
+                std::vector<double> &O) {
+  std::vector<double> t(n_nodes), w(n_nodes);
+  gauss_legendre(n_nodes, t.data(), w.data());
+  std::vector<double> pn((size_t)N * n_nodes), pw((size_t)N * n_nodes), rsB(N);
+  for (int i = 0; i < N; ++i) {
+    double lo = edges[i], hi = edges[i + 1];
+    double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
+    for (int a_ = 0; a_ < n_nodes; ++a_) {
+      double p = mid + half * t[a_];
+      pn[(size_t)i * n_nodes + a_] = p;
+      pw[(size_t)i * n_nodes + a_] = half * w[a_] * p * p;
+    }
+    rsB[i] = 1.0 / std::sqrt(shell_volume(lo, hi));
+  }
+  v.assign((size_t)N * N, 0.0);
+  for (int i = 0; i < N; ++i)
+    for (int k = i; k < N; ++k) {
+      double s = 0.0;
+      for (int x = 0; x < n_nodes; ++x) {
+        double px = pn[(size_t)i * n_nodes + x], wx = pw[(size_t)i * n_nodes + x];
+        double row = 0.0;
+        for (int y = 0; y < n_nodes; ++y)
+          row += pw[(size_t)k * n_nodes + y] *
+                 v_partial_wave(l, px, pn[(size_t)k * n_nodes + y], n_terms, V, a);
+        s += wx * row;
+      }
+      s *= rsB[i] * rsB[k];
+      v[(size_t)i * N + k] = s;
+      v[(size_t)k * N + i] = s;
+    }
+  std::vector<double> h(v);
+  for (int i = 0; i < N; ++i) {
+    double lo = edges[i], hi = edges[i + 1];
+    // <p^2>_i = int p^4 dp / B_i
+    double lo2 = lo * lo, hi2 = hi * hi;
+    double p5 = (hi - lo) * (hi2 * hi2 + hi2 * hi * lo + hi2 * lo2 + hi * lo * lo2 + lo2 * lo2) / 5.0;
+    h[(size_t)i * N + i] += p5 / shell_volume(lo, hi);
+  }
+  if (!sym_eig(N, h, eps, O)) {
+    eps.clear();
+    O.clear();
+  }
+}
+
+}  // namespace wpcd

@@ -1,0 +1,124 @@
+// Internal declarations of the WPCD library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "wpcd.h"
+
+namespace wpcd {
+
+constexpr int kMaxCh = 8;
+constexpr int kMaxPairs = kMaxCh * kMaxCh;
+
+// (l, l') channel pairs with l + l' even, ordered by l then l' (compile-time
+// versions, so that unrolled loops index register arrays statically)
+__host__ __device__ constexpr int pair_count(int nch) {
+  int n = 0;
+  for (int l = 0; l < nch; ++l)
+    for (int lp = 0; lp < nch; ++lp)
+      if (((l + lp) & 1) == 0) ++n;
+  return n;
+}
+__host__ __device__ constexpr int pair_first(int nch, int m) {
+  int n = 0;
+  for (int l = 0; l < nch; ++l)
+    for (int lp = 0; lp < nch; ++lp)
+      if (((l + lp) & 1) == 0) {
+        if (n == m) return l;
+        ++n;
+      }
+  return 0;
+}
+__host__ __device__ constexpr int pair_second(int nch, int m) {
+  int n = 0;
+  for (int l = 0; l < nch; ++l)
+    for (int lp = 0; lp < nch; ++lp)
+      if (((l + lp) & 1) == 0) {
+        if (n == m) return lp;
+        ++n;
+      }
+  return 0;
+}
+
+// Kernel launch counter (wpcd_launch_count); every launch site bumps it.
+void count_launches(int n);
+
+// Status plumbing: every entry point funnels errors through set_error.
+wpcd_status set_error(wpcd_status st, const std::string &msg);
+wpcd_status cuda_error(cudaError_t e, const char *what);
+void clear_error();
+
+#define WPCD_CUDA_TRY(expr)                                  \
+  do {                                                       \
+    cudaError_t _e = (expr);                                 \
+    if (_e != cudaSuccess) return ::wpcd::cuda_error(_e, #expr); \
+  } while (0)
+
+// ---- host mathematics of step 1 (setup.cpp) -------------------------------
+void gauss_legendre(int n, double *t, double *w);
+double bessel_i_scaled(int l, double z);  // exp(-z) i_l(z)
+double v_partial_wave(int l, double p, double pp, int n_terms, const double *V, const double *a);
+// symmetric eigensolver: A (n x n, row-major) -> eigenvalues ascending,
+// vectors as rows with the largest-magnitude component positive.
+bool sym_eig(int n, std::vector<double> A, std::vector<double> &evals, std::vector<double> &rows);
+void pair_setup(int N, const double *edges, int n_nodes, int l, int n_terms, const double *V,
+                const double *a, std::vector<double> &v, std::vector<double> &eps,
+                std::vector<double> &O);
+inline double shell_volume(double lo, double hi) {
+  // int_lo^hi p^2 dp, written to avoid cancellation for narrow bins
+  return (hi - lo) * (hi * hi + hi * lo + lo * lo) / 3.0;
+}
+
+// ---- handles -----------------------------------------------------------------
+struct DeviceTables {
+  double *pe2 = nullptr, *qe2 = nullptr;        // squared edges [N+1], [M+1]
+  double *pn = nullptr, *wp = nullptr;          // p nodes / weights*p^2 [N*n_p]
+  double *qn = nullptr, *wq = nullptr;          // q nodes / weights*q^2 [M*n_q]
+  double *yn = nullptr, *wy = nullptr;          // y nodes / weights [n_x]
+  double *rsb = nullptr;                        // 1/sqrt(B_i Bq_j) per cell [N*M]
+  double *qe = nullptr;                         // q edges [M+1]
+  double *eps = nullptr;                        // [n_ch][N]
+  double *O = nullptr, *Vt = nullptr;           // [n_ch][N][N]
+};
+
+}  // namespace wpcd
+
+struct wpcd_problem {
+  int device = 0;
+  int N = 0, M = 0, n_p = 0, n_q = 0, n_x = 0, n_ch = 0, n_pairs = 0;
+  int pair_l[wpcd::kMaxPairs], pair_lp[wpcd::kMaxPairs];
+  std::vector<double> pe, qe;                   // host edges
+  std::vector<double> eps, O, v, Vt;            // host [n_ch][N](*N)
+  double eps_b = 0.0;
+  wpcd::DeviceTables d;
+};
+
+struct wpcd_P {
+  const wpcd_problem *pr = nullptr;
+  int prec = WPCD_FP64;
+  int n_pairs = 0;
+  int64_t nnz = 0;
+  int64_t *row_ptr = nullptr;   // device [N*M+1]
+  int32_t *col = nullptr;       // device [nnz]
+  double *val64 = nullptr;      // device [n_pairs][nnz] (FP64 assembly)
+  float *val32 = nullptr;       // device [n_pairs][nnz] (FP32C assembly)
+  float ms = 0.f;
+  float ms_phase[3] = {0.f, 0.f, 0.f};  // count, scan, fill
+};
+
+namespace wpcd {
+// assemble.cu
+wpcd_status assemble(wpcd_problem *pr, int prec, cudaStream_t s, wpcd_P **out);
+// solve.cu
+wpcd_status resolvent(const wpcd_problem *pr, const double *E, int n_E, double *g, int *j0,
+                      double *D, cudaStream_t s);
+wpcd_status onshell(const wpcd_problem *pr, double E, int *j0, double *Elo, double *Ehi, double *q0);
+wpcd_status kapply(const wpcd_problem *pr, const wpcd_P *P, const double *g, const double *x,
+                   double *y, cudaStream_t s);
+wpcd_status solve(wpcd_problem *pr, const wpcd_P *P, const double *E, int n_E,
+                  const wpcd_solve_opts *o, double *U00, wpcd_solve_stats *st, cudaStream_t s);
+}  // namespace wpcd

@@ -1,0 +1,251 @@
+"""Thin ctypes binding of the C ABI in include/wpcd.h (argument marshalling only).
+
+Every computation happens in ``libwpcd.so`` (sm_103a CUDA kernels and the
+library's host setup).  Loading fails loudly when the library is missing: there
+is no CPU fallback.  Device buffers are torch tensors (``data_ptr()``); streams
+are torch streams (``cuda_stream``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libwpcd.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "wpcd.h")
+
+WPCD_OK, WPCD_EINVAL, WPCD_ENOMEM, WPCD_ECUDA = 0, -1, -2, -3
+WPCD_ENOCONV, WPCD_EBREAKDOWN, WPCD_ETIMEOUT, WPCD_ENOBOUND = -4, -5, -6, -7
+WPCD_FP64, WPCD_FP32C = 0, 1
+WPCD_SUM_KRYLOV, WPCD_SUM_WYNN = 0, 1
+
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+_I64 = ctypes.POINTER(ctypes.c_int64)
+_I32 = ctypes.POINTER(ctypes.c_int32)
+_F = ctypes.POINTER(ctypes.c_float)
+
+
+class wpcd_problem_desc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("M", ctypes.c_int), ("p_edges", _D), ("q_edges", _D),
+                ("n_p", ctypes.c_int), ("n_q", ctypes.c_int), ("n_x", ctypes.c_int),
+                ("n_ch", ctypes.c_int), ("n_terms", ctypes.c_int), ("V", _D), ("a", _D),
+                ("n_pair_nodes", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+class wpcd_solve_opts(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("max_iter", ctypes.c_int), ("min_iter", ctypes.c_int),
+                ("tol", ctypes.c_double), ("check_every", ctypes.c_int)]
+
+
+class wpcd_solve_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("n_kapply", ctypes.c_int), ("j0", ctypes.c_int),
+                ("D", ctypes.c_double), ("relres", ctypes.c_double),
+                ("U00", ctypes.c_double * 2), ("S", ctypes.c_double * 2), ("A", ctypes.c_double * 2),
+                ("ms", ctypes.c_float)]
+
+
+_SIGS = {
+    "wpcd_last_error": (ctypes.c_char_p, []),
+    "wpcd_version": (ctypes.c_int, []),
+    "wpcd_launch_count": (ctypes.c_int64, []),
+    "wpcd_P_timing": (ctypes.c_int, [_P, _F]),
+    "wpcd_tangent_edges": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, _D]),
+    "wpcd_problem_create": (ctypes.c_int, [ctypes.POINTER(wpcd_problem_desc), ctypes.POINTER(_P)]),
+    "wpcd_problem_destroy": (None, [_P]),
+    "wpcd_problem_info": (ctypes.c_int, [_P, _I, _I, _D]),
+    "wpcd_problem_pair": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, _D]),
+    "wpcd_assemble_P": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.POINTER(_P)]),
+    "wpcd_P_destroy": (None, [_P]),
+    "wpcd_P_info": (ctypes.c_int, [_P, _I64, _I, _I, _F]),
+    "wpcd_P_export": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "wpcd_resolvent": (ctypes.c_int, [_P, _D, ctypes.c_int, _P, _I, _D, _P]),
+    "wpcd_kapply": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "wpcd_solve": (ctypes.c_int, [_P, _P, _D, ctypes.c_int, ctypes.POINTER(wpcd_solve_opts), _D,
+                                  ctypes.POINTER(wpcd_solve_stats), _P]),
+}
+
+_lib = None
+
+
+class WpcdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"wpcd status {status}: {msg}")
+        self.status = status
+
+
+def lib():
+    """Load libwpcd.so (raises if it has not been built: no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() "
+                               "(the CUDA library is required; there is no CPU path)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def header_functions():
+    """Names of the functions declared in include/wpcd.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(wpcd_\w+)\s*\(", txt)))
+
+
+def last_error() -> str:
+    return lib().wpcd_last_error().decode()
+
+
+def check(status: int, allow=()):
+    if status != WPCD_OK and status not in allow:
+        raise WpcdError(status, last_error())
+    return status
+
+
+def _dp(a):
+    return a.ctypes.data_as(_D)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _tensor_ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------------------
+# same names as the C ABI
+# ---------------------------------------------------------------------------
+def wpcd_launch_count() -> int:
+    return int(lib().wpcd_launch_count())
+
+
+def wpcd_tangent_edges(n_bins: int, k_max: float) -> np.ndarray:
+    e = np.zeros(n_bins + 1)
+    check(lib().wpcd_tangent_edges(n_bins, k_max, _dp(e)))
+    return e
+
+
+class Problem:
+    """Handle of wpcd_problem (step 1 of the scheme, done by the library)."""
+
+    def __init__(self, p_edges, q_edges, n_p, n_q, n_x, n_ch, V, a, n_pair_nodes=8, device=0):
+        self._keep = [np.ascontiguousarray(x, dtype=np.float64) for x in (p_edges, q_edges, V, a)]
+        pe, qe, Vv, av = self._keep
+        d = wpcd_problem_desc(len(pe) - 1, len(qe) - 1, _dp(pe), _dp(qe), n_p, n_q, n_x, n_ch,
+                              len(Vv), _dp(Vv), _dp(av), n_pair_nodes, device)
+        h = _P()
+        self._h = None
+        check(lib().wpcd_problem_create(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+        self.N, self.M, self.n_ch = len(pe) - 1, len(qe) - 1, n_ch
+        self.pe, self.qe = pe, qe
+        dim, npair, eb = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        check(lib().wpcd_problem_info(h, ctypes.byref(dim), ctypes.byref(npair), ctypes.byref(eb)))
+        self.dim, self.n_pairs, self.eps_bound = dim.value, npair.value, eb.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None:
+            lib().wpcd_problem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def wpcd_problem_pair(self, l: int):
+        N = self.N
+        eps, O, v = np.zeros(N), np.zeros((N, N)), np.zeros((N, N))
+        check(lib().wpcd_problem_pair(self._h, l, _dp(eps), _dp(O), _dp(v)))
+        return eps, O, v
+
+    def wpcd_assemble_P(self, prec=WPCD_FP64, stream=None) -> "PMatrix":
+        h = _P()
+        check(lib().wpcd_assemble_P(self._h, prec, _stream_ptr(stream), ctypes.byref(h)))
+        return PMatrix(h, self)
+
+    def wpcd_resolvent(self, E, g, stream=None):
+        """g: device tensor (float64) of >= 2 * len(E) * dim elements."""
+        E = np.ascontiguousarray(np.atleast_1d(E), dtype=np.float64)
+        j0 = np.zeros(len(E), dtype=np.int32)
+        D = np.zeros(len(E))
+        check(lib().wpcd_resolvent(self._h, _dp(E), len(E), _tensor_ptr(g),
+                                   j0.ctypes.data_as(_I), _dp(D), _stream_ptr(stream)))
+        return j0, D
+
+    def wpcd_kapply(self, P, g, x, y, stream=None):
+        check(lib().wpcd_kapply(self._h, P.handle, _tensor_ptr(g), _tensor_ptr(x), _tensor_ptr(y),
+                                _stream_ptr(stream)))
+
+    def wpcd_solve(self, P, E, method=WPCD_SUM_KRYLOV, max_iter=100, min_iter=4, tol=1e-10,
+                   check_every=4, stream=None, allow=(WPCD_ENOCONV, WPCD_EBREAKDOWN)):
+        E = np.ascontiguousarray(np.atleast_1d(E), dtype=np.float64)
+        U = np.zeros(2 * len(E))
+        stats = (wpcd_solve_stats * len(E))()
+        opts = wpcd_solve_opts(method, max_iter, min_iter, tol, check_every)
+        st = lib().wpcd_solve(self._h, P.handle, _dp(E), len(E), ctypes.byref(opts), _dp(U), stats,
+                              _stream_ptr(stream))
+        check(st, allow=allow)
+        return U.view(np.complex128), list(stats), st
+
+
+class PMatrix:
+    """Handle of wpcd_P (block-CSR P0 on the device)."""
+
+    def __init__(self, h, problem):
+        self._h = h
+        self.problem = problem
+        nnz, npair, prec, ms = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        check(lib().wpcd_P_info(h, ctypes.byref(nnz), ctypes.byref(npair), ctypes.byref(prec),
+                                ctypes.byref(ms)))
+        self.nnz, self.n_pairs, self.prec, self.ms = nnz.value, npair.value, prec.value, ms.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None:
+            lib().wpcd_P_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def wpcd_P_timing(self):
+        """(count, scan, fill) device milliseconds of this assembly."""
+        ms = (ctypes.c_float * 3)()
+        check(lib().wpcd_P_timing(self._h, ms))
+        return tuple(ms)
+
+    def wpcd_P_export(self):
+        """Host copies: row_ptr int64[N*M+1], col int32[nnz], val f64[n_pairs, nnz]."""
+        pr = self.problem
+        rp = np.zeros(pr.N * pr.M + 1, dtype=np.int64)
+        col = np.zeros(max(self.nnz, 1), dtype=np.int32)
+        val = np.zeros((self.n_pairs, max(self.nnz, 1)))
+        check(lib().wpcd_P_export(self._h, ctypes.c_void_p(rp.ctypes.data),
+                                  ctypes.c_void_p(col.ctypes.data), ctypes.c_void_p(val.ctypes.data),
+                                  None))
+        return rp, col[: self.nnz], val[:, : self.nnz]

@@ -1,0 +1,90 @@
+"""The C ABI library (include/wpcd.h): it builds for sm_103a, loads, exports
+every declared symbol, and rejects invalid input on the host before any
+device work (no GPU needed for these)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+
+@pytest.fixture(scope="module")
+def W():
+    from paper_1508_07441_gb300 import build, wpcd
+
+    build.build()
+    return wpcd
+
+
+def test_exports_every_declared_symbol(W):
+    L = W.lib()
+    names = W.header_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(L, n), n
+    assert L.wpcd_version() >= 100
+
+
+def test_struct_layouts_match_header(W):
+    # desc: 2 ints, 2 ptrs, 5 ints, 2 ptrs, 2 ints (LP64 padding)
+    assert ctypes.sizeof(W.wpcd_problem_desc) == 72
+    assert ctypes.sizeof(W.wpcd_solve_opts) == 32
+    assert ctypes.sizeof(W.wpcd_solve_stats) == 88
+
+
+def _desc(W, N=4, M=4, **kw):
+    pe = np.linspace(0, 3, N + 1)
+    qe = np.linspace(0, 3, M + 1)
+    args = dict(n_p=2, n_q=2, n_x=4, n_ch=1, V=np.array([-3.0]), a=np.array([1.0]), n_pair_nodes=4,
+                device=0)
+    args.update(kw)
+    keep = [pe, qe, args["V"], args["a"]]
+    d = W.wpcd_problem_desc(N, M, keep[0].ctypes.data_as(W._D), keep[1].ctypes.data_as(W._D),
+                            args["n_p"], args["n_q"], args["n_x"], args["n_ch"], len(args["V"]),
+                            keep[2].ctypes.data_as(W._D), keep[3].ctypes.data_as(W._D),
+                            args["n_pair_nodes"], args["device"])
+    return d, keep
+
+
+@pytest.mark.parametrize("kw,needle", [
+    (dict(n_ch=0), "n_ch"), (dict(n_ch=9), "n_ch"), (dict(n_p=0), "node"), (dict(n_x=300), "node"),
+    (dict(a=np.array([-1.0])), "a_k"), (dict(V=np.array([np.nan])), "finite"),
+    (dict(n_pair_nodes=0), "n_pair_nodes"),
+])
+def test_create_rejects_invalid_input(W, kw, needle):
+    d, keep = _desc(W, **kw)
+    h = ctypes.c_void_p()
+    st = W.lib().wpcd_problem_create(ctypes.byref(d), ctypes.byref(h))
+    assert st == W.WPCD_EINVAL
+    assert needle in W.last_error()
+    assert not h.value
+
+
+def test_create_rejects_bad_edges(W):
+    d, keep = _desc(W)
+    keep[0][2] = keep[0][1]  # not strictly increasing
+    h = ctypes.c_void_p()
+    assert W.lib().wpcd_problem_create(ctypes.byref(d), ctypes.byref(h)) == W.WPCD_EINVAL
+    assert "edges" in W.last_error()
+
+
+def test_tangent_edges_host_call(W):
+    e = W.wpcd_tangent_edges(30, 20.0)
+    assert e[0] == 0 and e[-1] == 20.0 and np.all(np.diff(e) > 0)
+    with pytest.raises(W.WpcdError):
+        W.wpcd_tangent_edges(0, 20.0)
+
+
+def test_null_handles_are_rejected(W):
+    L = W.lib()
+    assert L.wpcd_problem_info(None, None, None, None) == W.WPCD_EINVAL
+    assert L.wpcd_P_info(None, None, None, None, None) == W.WPCD_EINVAL
+    assert L.wpcd_solve(None, None, None, 0, None, None, None, None) == W.WPCD_EINVAL
+    L.wpcd_problem_destroy(None)
+    L.wpcd_P_destroy(None)
+
+
+def test_no_cpu_fallback_when_library_missing(W, monkeypatch, tmp_path):
+    monkeypatch.setattr(W, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(W, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU path"):
+        W.lib()
