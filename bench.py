@@ -244,6 +244,18 @@ def main():
     value = world * n_nodes / (asm_ms * 1e-3) / 1e9
     energies_per_s = world * len(energies) / (solve_ms * 1e-3)
 
+    # ---- FP32C assembly (FP64 binning, FP32 node values), same lattice ----
+    f32 = []
+    for it in range(max(args.steps, 2) + 1):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        P3 = pr.wpcd_assemble_P(W.WPCD_FP32C, stream=stream)
+        if it > 0:
+            f32.append((P3.ms, P3.wpcd_P_timing()))
+        P3.close()
+    f32_ms = maxr(statistics.mean(m for m, _ in f32))
+    f32_phases = [statistics.mean(ph[k] for _, ph in f32) for k in range(3)]
+
     # ---- end to end through the public API with host buffers -------------
     barrier()
     t0 = time.perf_counter()
@@ -325,6 +337,9 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "assembly": {"ms": asm_ms, "count_ms": phases[0], "scan_ms": phases[1], "fill_ms": phases[2],
                      "nnz_cells": recs[-1]["nnz"]},
+        "assembly_fp32c": {"value": world * n_nodes / (f32_ms * 1e-3) / 1e9, "unit": "Gnodes/s",
+                           "ms": f32_ms, "count_ms": f32_phases[0], "scan_ms": f32_phases[1],
+                           "fill_ms": f32_phases[2]},
         "solve": {"value": energies_per_s, "unit": "energies/s", "ms": solve_ms,
                   "k_applications": recs[-1]["n_kapply"], "accuracy_vs_oracle": acc},
         "roofline": roofline,

@@ -178,7 +178,8 @@ def P0(pe, qe, n_p, n_q, n_x, n_ch, normalize=True, with_outgrid=False, with_abs
 
     Returns dict(row_ptr int64[N*M+1], col int32[nnz], val f64[nnz, n_pairs],
     outgrid f64[N*M, n_pairs] (unnormalised, optional), absval f64[nnz,
-    n_pairs] (sums of |terms|, normalised like val, optional)).
+    n_pairs] (sum over the element's nodes of W |P_l(y)|, the magnitude that
+    bounds every node term, normalised like val, optional)).
     """
     pe, qe = _f64(pe), _f64(qe)
     N, M = len(pe) - 1, len(qe) - 1

@@ -494,10 +494,12 @@ static int cmp_int(const void *a, const void *b) {
 /* Step 2b: node-binned values, unnormalised (the bare node sums), columns
  * ascending within each row; val is [nnz][n_pairs].  outgrid (optional,
  * [N*M][n_pairs]) receives the weight of nodes that leave the grid.  absval
- * (optional, [nnz][n_pairs]) receives the sums of |terms|, the scale of the
- * rounding error of each element (elements whose terms cancel exactly, e.g.
- * l' = 0 with the GL rule integrating P_l(y) to zero, are rounding noise of
- * that size). */
+ * (optional, [nnz][n_pairs]) receives sum_nodes W |P_l(y)|, the magnitude
+ * that bounds every node term (|P_l'| <= 1) and so sets the scale of the
+ * rounding error of each element: elements whose terms cancel exactly (e.g.
+ * l' = 0 with the GL rule integrating P_l(y) to zero) are rounding noise of
+ * that size, and a node evaluated in FP32 carries an absolute error of order
+ * eps_32 times its W |P_l(y)| even where P_l'(y') passes through zero. */
 int orc_P0_fill(int N, const double *pe, int M, const double *qe, int np_, int nq, int nx,
                 int n_ch, const int64_t *row_ptr, int32_t *col, double *val, double *outgrid,
                 double *absval) {
@@ -542,7 +544,7 @@ int orc_P0_fill(int N, const double *pe, int M, const double *qe, int np_, int n
             for (int k = 0; k < npair; ++k) {
               double term = W * Py[pl[k]] * Pyp[plp[k]];
               acc[(size_t)t * npair + k] += term;
-              if (aacc) aacc[(size_t)t * npair + k] += fabs(term);
+              if (aacc) aacc[(size_t)t * npair + k] += W * fabs(Py[pl[k]]);
             }
           }
       if (row_ptr[c + 1] - row_ptr[c] != nt) {

@@ -56,24 +56,10 @@ __device__ __forceinline__ int bin_search(const long long *e2, int n, long long 
   return lo;
 }
 
-__device__ __forceinline__ void node_coords(const AsmParams &P, int i, int j, int node, double &p,
-                                            double &q, int &x) {
-  x = node % P.n_x;
-  int ab = node / P.n_x;
-  int b = ab % P.n_q, a = ab / P.n_q;
-  p = P.pn[i * P.n_p + a];
-  q = P.qn[j * P.n_q + b];
-}
-
-// p'^2 and q'^2 in the canonical rounding order (no contraction)
-__device__ __forceinline__ void recoupled(double p, double q, double y, double &p2, double &q2) {
-  double A = __dmul_rn(__dmul_rn(0.75, p), q);
-  double Bp = __dadd_rn(__dmul_rn(__dmul_rn(p, p), 0.25), __dmul_rn(__dmul_rn(q, q), 0.5625));
-  double C = -__dmul_rn(p, q);
-  double D = __dadd_rn(__dmul_rn(p, p), __dmul_rn(__dmul_rn(q, q), 0.25));
-  p2 = __fma_rn(A, y, Bp);
-  q2 = __fma_rn(C, y, D);
-}
+// p'^2 = A y + Bp and q'^2 = C y + D for one (p, q) node pair
+struct BinConst {
+  double A, Bp, C, D;
+};
 
 template <int NT>
 __device__ void bitonic_sort(uint32_t *s, int n) {
@@ -100,24 +86,35 @@ __global__ void __launch_bounds__(kThreads) count_kernel(AsmParams P, int64_t *c
   extern __shared__ __align__(16) unsigned char smem[];
   long long *pe2 = reinterpret_cast<long long *>(smem);
   long long *qe2 = pe2 + (P.N + 1);
-  uint32_t *keys = reinterpret_cast<uint32_t *>(qe2 + (P.M + 1));
+  BinConst *abk = reinterpret_cast<BinConst *>(qe2 + (P.M + 1));  // per (a, b)
+  double *ys = reinterpret_cast<double *>(abk + P.n_p * P.n_q);
+  uint32_t *keys = reinterpret_cast<uint32_t *>(ys + P.n_x);
   __shared__ int red[kThreads / 32];
 
   const int c = blockIdx.x;
   const int i = c / P.M, j = c % P.M;
   for (int k = threadIdx.x; k <= P.N; k += kThreads) pe2[k] = __double_as_longlong(P.pe2[k]);
   for (int k = threadIdx.x; k <= P.M; k += kThreads) qe2[k] = __double_as_longlong(P.qe2[k]);
+  for (int ab = threadIdx.x; ab < P.n_p * P.n_q; ab += kThreads) {
+    int a = ab / P.n_q, b = ab % P.n_q;
+    double p = P.pn[i * P.n_p + a], q = P.qn[j * P.n_q + b];
+    // canonical rounding order of the recoupled squares (no contraction)
+    double A = __dmul_rn(__dmul_rn(0.75, p), q);
+    double Bp = __dadd_rn(__dmul_rn(__dmul_rn(p, p), 0.25), __dmul_rn(__dmul_rn(q, q), 0.5625));
+    double C = -__dmul_rn(p, q);
+    double D = __dadd_rn(__dmul_rn(p, p), __dmul_rn(__dmul_rn(q, q), 0.25));
+    abk[ab] = BinConst{A, Bp, C, D};
+  }
+  for (int x = threadIdx.x; x < P.n_x; x += kThreads) ys[x] = P.yn[x];
   __syncthreads();
   const long long pmax2 = pe2[P.N], qmax2 = qe2[P.M];
   for (int n = threadIdx.x; n < P.np2; n += kThreads) {
     uint32_t key = kInvalid;
     if (n < P.n_nodes) {
-      double p, q;
-      int x;
-      node_coords(P, i, j, n, p, q, x);
-      double p2, q2;
-      recoupled(p, q, P.yn[x], p2, q2);
-      long long ip2 = __double_as_longlong(p2), iq2 = __double_as_longlong(q2);
+      const BinConst k = abk[n / P.n_x];
+      const double y = ys[n % P.n_x];
+      long long ip2 = __double_as_longlong(__fma_rn(k.A, y, k.Bp));
+      long long iq2 = __double_as_longlong(__fma_rn(k.C, y, k.D));
       if (ip2 <= pmax2 && iq2 <= qmax2) {
         int ib = bin_search(pe2, P.N, ip2);
         int jb = bin_search(qe2, P.M, iq2);
@@ -194,7 +191,6 @@ struct AccFF {
     hi = s;
     lo = __fadd_rn(lo, e);
   }
-  __device__ void add(double x) { add((float)x); }
   __device__ void add(const AccFF &o) {
     float s, e;
     two_sum(hi, o.hi, s, e);
@@ -233,36 +229,12 @@ __device__ __forceinline__ void legendre_n(real y, real *P) {
     P[n + 1] = (real(2 * n + 1) / real(n + 1)) * y * P[n] - (real(n) / real(n + 1)) * P[n - 1];
 }
 
-// Values of one node: W and y' (per precision)
-template <bool F64>
-__device__ __forceinline__ void node_value(const AsmParams &P, int i, int j, int node,
-                                           typename NodeVal<F64>::real &W,
-                                           typename NodeVal<F64>::real &yp, int &x) {
-  using real = typename NodeVal<F64>::real;
-  int ab = node / P.n_x;
-  x = node % P.n_x;
-  int b = ab % P.n_q, a = ab / P.n_q;
-  double p = P.pn[i * P.n_p + a], q = P.qn[j * P.n_q + b], y = P.yn[x];
-  double Wd = P.wp[i * P.n_p + a] * P.wq[j * P.n_q + b] * P.wy[x];
-  if (F64) {
-    double p2, q2;
-    recoupled(p, q, y, p2, q2);
-    double num = fma(-0.5 * p * q, y, 0.375 * q * q - 0.5 * p * p);
-    double den2 = fmax(p2, 0.0) * fmax(q2, 0.0);
-    double c = den2 > 0.0 ? num * rsqrt(den2) : 0.0;
-    W = (real)Wd;
-    yp = (real)fmin(1.0, fmax(-1.0, c));
-  } else {
-    float pf = (float)p, qf = (float)q, yf = (float)y;
-    float p2 = fmaf(0.75f * pf * qf, yf, 0.25f * pf * pf + 0.5625f * qf * qf);
-    float q2 = fmaf(-pf * qf, yf, pf * pf + 0.25f * qf * qf);
-    float num = fmaf(-0.5f * pf * qf, yf, 0.375f * qf * qf - 0.5f * pf * pf);
-    float den2 = fmaxf(p2, 0.f) * fmaxf(q2, 0.f);
-    float c = den2 > 0.f ? num * rsqrtf(den2) : 0.f;
-    W = (real)Wd;
-    yp = (real)fminf(1.f, fmaxf(-1.f, c));
-  }
-}
+// Per (p, q) node pair constants of one source cell (FP64):
+//   p'^2 = A y + Bp,  q'^2 = C y + D,  p'.q' = nA y + nB,  and the weight
+//   wp wq.  Shared by the n_x y-nodes of the pair.
+struct PairConst {
+  double A, Bp, C, D, nA, nB, W;
+};
 
 template <bool F64, int NCH>
 __global__ void __launch_bounds__(kThreads) fill_kernel(AsmParams P, const uint32_t *sorted,
@@ -273,10 +245,10 @@ __global__ void __launch_bounds__(kThreads) fill_kernel(AsmParams P, const uint3
   using Acc = typename NodeVal<F64>::Acc;
   constexpr int NPAIR = pair_count(NCH);
   extern __shared__ __align__(16) unsigned char smem[];
-  uint32_t *keys = reinterpret_cast<uint32_t *>(smem);
-  real *Wn = reinterpret_cast<real *>(keys + P.np2);        // per sorted element
-  real *Yp = Wn + P.np2;
-  real *Py = Yp + P.np2;                                    // [n_x][n_ch]
+  PairConst *pc = reinterpret_cast<PairConst *>(smem);           // [n_p * n_q]
+  real *Py = reinterpret_cast<real *>(pc + P.n_p * P.n_q);      // [n_x][NCH]
+  real *wy = Py + P.n_x * NCH;                                   // [n_x]
+  uint32_t *keys = reinterpret_cast<uint32_t *>(wy + P.n_x + 2); // [np2]
   __shared__ Acc wtot[kThreads / 32][NPAIR];
   __shared__ int wflag[kThreads / 32];
   __shared__ int whead[kThreads / 32];
@@ -286,133 +258,114 @@ __global__ void __launch_bounds__(kThreads) fill_kernel(AsmParams P, const uint3
   const int R = P.np2 / kThreads;  // consecutive sorted elements per thread
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t mask = (1u << P.nbits) - 1u;
+  const int nbits = P.nbits;
 
+  for (int ab = threadIdx.x; ab < P.n_p * P.n_q; ab += kThreads) {
+    int a = ab / P.n_q, b = ab % P.n_q;
+    double p = P.pn[i * P.n_p + a], q = P.qn[j * P.n_q + b];
+    PairConst k;
+    k.A = __dmul_rn(__dmul_rn(0.75, p), q);
+    k.Bp = __dadd_rn(__dmul_rn(__dmul_rn(p, p), 0.25), __dmul_rn(__dmul_rn(q, q), 0.5625));
+    k.C = -__dmul_rn(p, q);
+    k.D = __dadd_rn(__dmul_rn(p, p), __dmul_rn(__dmul_rn(q, q), 0.25));
+    k.nA = -0.5 * p * q;
+    k.nB = 0.375 * q * q - 0.5 * p * p;
+    k.W = P.wp[i * P.n_p + a] * P.wq[j * P.n_q + b];
+    pc[ab] = k;
+  }
   for (int x = threadIdx.x; x < P.n_x; x += kThreads) {
     real Pl[NCH];
     legendre_n<real, NCH>((real)P.yn[x], Pl);
 #pragma unroll
     for (int l = 0; l < NCH; ++l) Py[x * NCH + l] = Pl[l];
+    wy[x] = (real)P.wy[x];
   }
-  for (int n = threadIdx.x; n < P.np2; n += kThreads) {
-    uint32_t k = sorted[(size_t)c * P.np2 + n];
-    keys[n] = k;
-    real W = 0, yp = 0;
-    if (k != kInvalid) {
-      int x;
-      node_value<F64>(P, i, j, (int)(k & mask), W, yp, x);
-    }
-    Wn[n] = W;
-    Yp[n] = yp;
-  }
+  for (int n = threadIdx.x; n < P.np2; n += kThreads) keys[n] = sorted[(size_t)c * P.np2 + n];
   __syncthreads();
 
-  // contribution of sorted element e to pair m
-  auto contrib = [&](int e, real *out) {
+  auto is_head = [&](int e) {
     uint32_t k = keys[e];
-    int x = (int)(k & mask) % P.n_x;
+    return k != kInvalid && (e == 0 || (keys[e - 1] >> nbits) != (k >> nbits));
+  };
+  auto is_tail = [&](int e) {
+    uint32_t k = keys[e];
+    return k != kInvalid &&
+           (e + 1 == P.np2 || keys[e + 1] == kInvalid || (keys[e + 1] >> nbits) != (k >> nbits));
+  };
+  // contribution of sorted element e to every (l, l') pair
+  auto contrib = [&](int e, real *out) {
+    int node = (int)(keys[e] & mask);
+    int x = node % P.n_x;
+    const PairConst &k = pc[node / P.n_x];
+    double y = P.yn[x];
+    real yp;
+    if (F64) {
+      double p2 = fma(k.A, y, k.Bp), q2 = fma(k.C, y, k.D), num = fma(k.nA, y, k.nB);
+      double den2 = fmax(p2, 0.0) * fmax(q2, 0.0);
+      double cc = den2 > 0.0 ? num * rsqrt(den2) : 0.0;
+      yp = (real)fmin(1.0, fmax(-1.0, cc));
+    } else {
+      // recoupled squares and p'.q' in FP64 (three FMAs), the rest in FP32
+      float p2 = (float)fma(k.A, y, k.Bp), q2 = (float)fma(k.C, y, k.D);
+      float num = (float)fma(k.nA, y, k.nB);
+      float den2 = fmaxf(p2, 0.f) * fmaxf(q2, 0.f);
+      float cc = den2 > 0.f ? num * rsqrtf(den2) : 0.f;
+      yp = (real)fminf(1.f, fmaxf(-1.f, cc));
+    }
     real Pl2[NCH];
-    legendre_n<real, NCH>(Yp[e], Pl2);
-    real W = Wn[e];
+    legendre_n<real, NCH>(yp, Pl2);
+    real W = (real)k.W * wy[x];
 #pragma unroll
     for (int m = 0; m < NPAIR; ++m)
       out[m] = W * Py[x * NCH + pair_first(NCH, m)] * Pl2[pair_second(NCH, m)];
   };
-  auto is_head = [&](int e) {
-    uint32_t k = keys[e];
-    return k != kInvalid && (e == 0 || (keys[e - 1] >> P.nbits) != (k >> P.nbits));
-  };
 
-  // pass 1: thread aggregate = (any head in my range, sum since my last head)
+  // step A: segment ranks from an integer scan of the head flags
   const int e0 = threadIdx.x * R;
-  Acc agg[NPAIR];
-#pragma unroll
-  for (int m = 0; m < NPAIR; ++m) agg[m].zero();
-  int flag = 0, nhead = 0;
-  for (int r = 0; r < R; ++r) {
-    int e = e0 + r;
-    if (keys[e] == kInvalid) break;
-    if (is_head(e)) {
-      flag = 1;
-      ++nhead;
-#pragma unroll
-      for (int m = 0; m < NPAIR; ++m) agg[m].zero();
-    }
-    real v[NPAIR];
-    contrib(e, v);
-#pragma unroll
-    for (int m = 0; m < NPAIR; ++m) agg[m].add(v[m]);
-  }
-  // inclusive segmented scan over threads (operator: (f1,s1)+(f2,s2) =
-  // (f1|f2, f2 ? s2 : s1+s2)), plus a plain scan of the head counts
+  int nhead = 0;
+  for (int r = 0; r < R; ++r) nhead += is_head(e0 + r) ? 1 : 0;
   int hscan = nhead;
   for (int d = 1; d < 32; d <<= 1) {
-    int fu = __shfl_up_sync(0xffffffffu, flag, d);
     int hu = __shfl_up_sync(0xffffffffu, hscan, d);
-    Acc su[NPAIR];
-#pragma unroll
-    for (int m = 0; m < NPAIR; ++m) su[m] = agg[m].shfl_up(d);
-    if (lane >= d) {
-      if (!flag) {
-#pragma unroll
-        for (int m = 0; m < NPAIR; ++m) agg[m].add(su[m]);
-      }
-      flag |= fu;
-      hscan += hu;
-    }
+    if (lane >= d) hscan += hu;
   }
-  if (lane == 31) {
-#pragma unroll
-    for (int m = 0; m < NPAIR; ++m) wtot[warp][m] = agg[m];
-    wflag[warp] = flag;
-    whead[warp] = hscan;
-  }
+  if (lane == 31) whead[warp] = hscan;
   __syncthreads();
-  // carry into this warp from the warps before it
-  Acc carry[NPAIR];
-#pragma unroll
-  for (int m = 0; m < NPAIR; ++m) carry[m].zero();
-  int cflag = 0, hbase = 0;
-  for (int w = warp - 1; w >= 0; --w) {
-    if (!cflag) {
-#pragma unroll
-      for (int m = 0; m < NPAIR; ++m) carry[m].add(wtot[w][m]);
-      cflag = wflag[w];
-    }
-    hbase += whead[w];
-  }
-  // combine: inclusive value for this thread, then shift to exclusive
-  if (!flag) {
-#pragma unroll
-    for (int m = 0; m < NPAIR; ++m) agg[m].add(carry[m]);
-  }
-  Acc excl[NPAIR];
-  int hexcl = hbase + hscan - nhead;
-  {
-    // exclusive = inclusive of the previous thread
-#pragma unroll
-    for (int m = 0; m < NPAIR; ++m) excl[m] = agg[m].shfl_up(1);
-    if (lane == 0) {
-#pragma unroll
-      for (int m = 0; m < NPAIR; ++m) excl[m] = carry[m];
-    }
-  }
-  // pass 2: walk my elements again, write completed segments
+  int hbase = 0;
+  for (int w = 0; w < warp; ++w) hbase += whead[w];
+  const int seg0 = hbase + hscan - nhead;  // heads before this thread
   const int64_t base = row_ptr[c];
-  Acc run[NPAIR];
-#pragma unroll
-  for (int m = 0; m < NPAIR; ++m) run[m] = excl[m];
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int m = 0; m < NPAIR; ++m) run[m].zero();
-  }
-  int seg = hexcl - 1;
+  const int64_t lim = row_ptr[c + 1];
   const double rs_src = P.rsb[c];
+
+  auto write_seg = [&](int seg, uint32_t k, const Acc *sum) {
+    int64_t o = base + seg;
+    if (o < lim) {
+      int t = (int)(k >> nbits);
+      col[o] = t;
+      double nrm = rs_src * P.rsb[t];
+#pragma unroll
+      for (int m = 0; m < NPAIR; ++m) val[(size_t)m * nnz + o] = (real)(sum[m].value() * nrm * P.cnorm[m]);
+    }
+  };
+
+  // step B: one pass over my elements; segments that open and close here are
+  // written at once, the leading one (continuing from earlier threads) waits
+  Acc run[NPAIR], lead[NPAIR];
+#pragma unroll
+  for (int m = 0; m < NPAIR; ++m) {
+    run[m].zero();
+    lead[m].zero();
+  }
+  int flag = 0, local_heads = 0, lead_tail = 0;
+  uint32_t lead_key = 0;
   for (int r = 0; r < R; ++r) {
-    int e = e0 + r;
-    uint32_t k = keys[e];
+    const int e = e0 + r;
+    const uint32_t k = keys[e];
     if (k == kInvalid) break;
     if (is_head(e)) {
-      ++seg;
+      flag = 1;
+      ++local_heads;
 #pragma unroll
       for (int m = 0; m < NPAIR; ++m) run[m].zero();
     }
@@ -420,18 +373,67 @@ __global__ void __launch_bounds__(kThreads) fill_kernel(AsmParams P, const uint3
     contrib(e, v);
 #pragma unroll
     for (int m = 0; m < NPAIR; ++m) run[m].add(v[m]);
-    bool tail = (e + 1 == P.np2) || keys[e + 1] == kInvalid ||
-                (keys[e + 1] >> P.nbits) != (k >> P.nbits);
-    if (tail) {
-      int t = (int)(k >> P.nbits);
-      int64_t o = base + seg;
-      if (o < row_ptr[c + 1]) {
-        col[o] = t;
-        double nrm = rs_src * P.rsb[t];
+    if (is_tail(e)) {
+      if (flag) {
+        write_seg(seg0 + local_heads - 1, k, run);
+      } else {
 #pragma unroll
-        for (int m = 0; m < NPAIR; ++m) val[(size_t)m * nnz + o] = (real)(run[m].value() * nrm * P.cnorm[m]);
+        for (int m = 0; m < NPAIR; ++m) lead[m] = run[m];
+        lead_tail = 1;
+        lead_key = k;
       }
     }
+  }
+  // step C: segmented scan of (flag, sum of the segment open at my end)
+  Acc agg[NPAIR];
+#pragma unroll
+  for (int m = 0; m < NPAIR; ++m) agg[m] = run[m];
+  int f = flag;
+  for (int d = 1; d < 32; d <<= 1) {
+    int fu = __shfl_up_sync(0xffffffffu, f, d);
+    Acc su[NPAIR];
+#pragma unroll
+    for (int m = 0; m < NPAIR; ++m) su[m] = agg[m].shfl_up(d);
+    if (lane >= d) {
+      if (!f) {
+#pragma unroll
+        for (int m = 0; m < NPAIR; ++m) agg[m].add(su[m]);
+      }
+      f |= fu;
+    }
+  }
+  if (lane == 31) {
+#pragma unroll
+    for (int m = 0; m < NPAIR; ++m) wtot[warp][m] = agg[m];
+    wflag[warp] = f;
+  }
+  __syncthreads();
+  Acc carry[NPAIR];
+#pragma unroll
+  for (int m = 0; m < NPAIR; ++m) carry[m].zero();
+  int cflag = 0;
+  for (int w = warp - 1; w >= 0 && !cflag; --w) {
+#pragma unroll
+    for (int m = 0; m < NPAIR; ++m) carry[m].add(wtot[w][m]);
+    cflag = wflag[w];
+  }
+  if (!f) {
+#pragma unroll
+    for (int m = 0; m < NPAIR; ++m) agg[m].add(carry[m]);
+  }
+  // exclusive value for this thread = inclusive value of the previous one
+  Acc excl[NPAIR];
+#pragma unroll
+  for (int m = 0; m < NPAIR; ++m) excl[m] = agg[m].shfl_up(1);
+  if (lane == 0) {
+#pragma unroll
+    for (int m = 0; m < NPAIR; ++m) excl[m] = carry[m];
+  }
+  // step D: close the leading segment with the carry from earlier threads
+  if (lead_tail) {
+#pragma unroll
+    for (int m = 0; m < NPAIR; ++m) lead[m].add(excl[m]);
+    write_seg(seg0 - 1, lead_key, lead);
   }
 }
 
@@ -529,7 +531,8 @@ wpcd_status assemble(wpcd_problem *pr, int prec, cudaStream_t s, wpcd_P **out) {
   if ((e = cudaMalloc(&Pm->row_ptr, sizeof(int64_t) * (n_cells + 1))) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc row_ptr"));
 
   cudaEventRecord(ev0, s);
-  size_t smem_count = sizeof(long long) * (P.N + P.M + 2) + sizeof(uint32_t) * np2;
+  size_t smem_count = sizeof(long long) * (P.N + P.M + 2) + sizeof(BinConst) * P.n_p * P.n_q +
+                      sizeof(double) * P.n_x + sizeof(uint32_t) * np2;
   cudaFuncSetAttribute(count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_count);
   count_kernel<<<n_cells, kThreads, smem_count, s>>>(P, counts, sorted);
   cudaEventRecord(evc, s);
@@ -553,7 +556,8 @@ wpcd_status assemble(wpcd_problem *pr, int prec, cudaStream_t s, wpcd_P **out) {
     val = Pm->val32;
   }
   size_t rsz = prec == WPCD_FP64 ? sizeof(double) : sizeof(float);
-  size_t smem_fill = sizeof(uint32_t) * np2 + rsz * (2 * (size_t)np2 + (size_t)P.n_x * P.n_ch);
+  size_t smem_fill = sizeof(double) * 7 * (size_t)P.n_p * P.n_q +
+                     rsz * ((size_t)P.n_x * P.n_ch + P.n_x + 2) + sizeof(uint32_t) * np2;
   smem_fill = (smem_fill + 15) & ~(size_t)15;
   wpcd_status st = prec == WPCD_FP64
                        ? dispatch_fill<true>(P, n_cells, smem_fill, s, sorted, Pm->row_ptr, Pm->col, val, nnz)

@@ -114,7 +114,10 @@ __global__ void resolvent_kernel(ResParams R, double *g) {
 // B' = B, or the G1-scaled complex block (ncol = 2M, complex pairs)
 // epilogue: C = out, or C = S - out
 // ---------------------------------------------------------------------------
-constexpr int GB_M = 64, GB_N = 64, GB_K = 16, G_THREADS = 256;
+// 32 x 64 output tiles: 7 x 7 x 3 = 147 CTAs for the 200-bin, 3-channel
+// blocks, close to one wave over the 152 SMs (FP64 work is issue-bound, so
+// SM coverage matters more than data reuse here)
+constexpr int GB_M = 32, GB_N = 64, GB_K = 16, G_THREADS = 256;
 
 template <bool SCALE_G, bool SUB>
 __global__ void __launch_bounds__(G_THREADS) gemm_kernel(int n, int ncol, const double *__restrict__ A,
@@ -127,8 +130,8 @@ __global__ void __launch_bounds__(G_THREADS) gemm_kernel(int n, int ncol, const 
   const int b = blockIdx.z;
   const size_t offA = (size_t)b * n * n, offB = (size_t)b * n * ncol;
   const int row0 = blockIdx.y * GB_M, col0 = blockIdx.x * GB_N;
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  double acc[4][4] = {};
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 16 x 16 threads, 2 x 4 outputs each
+  double acc[2][4] = {};
   for (int k0 = 0; k0 < n; k0 += GB_K) {
     for (int t = threadIdx.x; t < GB_M * GB_K; t += G_THREADS) {
       int r = t / GB_K, kk = t % GB_K;
@@ -154,20 +157,20 @@ __global__ void __launch_bounds__(G_THREADS) gemm_kernel(int n, int ncol, const 
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < GB_K; ++kk) {
-      double a[4], bb[4];
+      double a[2], bb[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) a[u] = As[kk][ty + 16 * u];
+      for (int u = 0; u < 2; ++u) a[u] = As[kk][ty + 16 * u];
 #pragma unroll
       for (int u = 0; u < 4; ++u) bb[u] = Bs[kk][tx + 16 * u];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < 2; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], bb[v], acc[u][v]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < 2; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       int gr = row0 + ty + 16 * u, gc = col0 + tx + 16 * v;

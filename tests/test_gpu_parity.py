@@ -4,11 +4,13 @@ the same seeded inputs.
 Tolerances: P0 elements rel 1e-10 in FP64 and 1e-5 in FP32C.  Some
 elements are exactly zero in exact arithmetic (for l' = 0 the GL rule
 integrates P_l(y) to zero when all y-nodes of a (p, q) pair land in one
-target), so both sides return rounding noise there; the bar is therefore
-per element |d| <= rel * |ref| + abs * sum|terms|, with sum|terms| (the
-rounding scale of the node sum) from the oracle: (rel, abs) = (1e-10, 1e-13)
-in FP64 and (1e-5, 1e-6) in FP32C.  The pattern (row pointers and columns)
-must match exactly, so a misbinned node is an error.  Amplitudes rel 1e-6.
+target), and in FP32 a node term W P_l(y) P_l'(y') carries an absolute error
+of order eps_32 W |P_l(y)| even where P_l'(y') passes through a root; so the
+bar is per element |d| <= rel |ref| + abs S, with S = sum_nodes W |P_l(y)|
+(the magnitude bounding every term, |P_l'| <= 1) from the oracle:
+(rel, abs) = (1e-10, 1e-13) in FP64 and (1e-5, 1e-6) in FP32C.  The pattern
+(row pointers and columns) must match exactly, so a misbinned node is an
+error.  Amplitudes rel 1e-6.
 """
 import numpy as np
 import pytest
@@ -39,7 +41,7 @@ def _inputs(N, M, jitter=None, kmax=20.0):
 
 
 def _excess(val, ref, absref, prec):
-    """max over elements of |d| / (rel |ref| + abs sum|terms|); <= 1 passes"""
+    """max over elements of |d| / (rel |ref| + abs S); <= 1 passes"""
     rel, ab = TOL[prec]
     return np.max(np.abs(val - ref) / (rel * np.abs(ref) + ab * absref + 1e-300))
 
