@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const int64_t *counts, int n
 struct Acc64 {
   double v;
   __device__ void zero() { v = 0.0; }
-  __device__ void add(double x) { v += x; }
+  __device__ void fma(double a, double b) { v = ::fma(a, b, v); }
   __device__ void add(const Acc64 &o) { v += o.v; }
   __device__ double value() const { return v; }
   __device__ Acc64 shfl_up(int d) const { Acc64 r; r.v = __shfl_up_sync(0xffffffffu, v, d); return r; }
@@ -191,6 +191,7 @@ struct AccFF {
     hi = s;
     lo = __fadd_rn(lo, e);
   }
+  __device__ void fma(float a, float b) { add(__fmul_rn(a, b)); }
   __device__ void add(const AccFF &o) {
     float s, e;
     two_sum(hi, o.hi, s, e);
@@ -246,9 +247,8 @@ __global__ void __launch_bounds__(kThreads) fill_kernel(AsmParams P, const uint3
   constexpr int NPAIR = pair_count(NCH);
   extern __shared__ __align__(16) unsigned char smem[];
   PairConst *pc = reinterpret_cast<PairConst *>(smem);           // [n_p * n_q]
-  real *Py = reinterpret_cast<real *>(pc + P.n_p * P.n_q);      // [n_x][NCH]
-  real *wy = Py + P.n_x * NCH;                                   // [n_x]
-  uint32_t *keys = reinterpret_cast<uint32_t *>(wy + P.n_x + 2); // [np2]
+  real *Pyw = reinterpret_cast<real *>(pc + P.n_p * P.n_q);     // w_y P_l(y) [n_x][NCH]
+  uint32_t *keys = reinterpret_cast<uint32_t *>(Pyw + P.n_x * NCH + 2);  // [np2]
   __shared__ Acc wtot[kThreads / 32][NPAIR];
   __shared__ int wflag[kThreads / 32];
   __shared__ int whead[kThreads / 32];
@@ -277,8 +277,7 @@ __global__ void __launch_bounds__(kThreads) fill_kernel(AsmParams P, const uint3
     real Pl[NCH];
     legendre_n<real, NCH>((real)P.yn[x], Pl);
 #pragma unroll
-    for (int l = 0; l < NCH; ++l) Py[x * NCH + l] = Pl[l];
-    wy[x] = (real)P.wy[x];
+    for (int l = 0; l < NCH; ++l) Pyw[x * NCH + l] = (real)P.wy[x] * Pl[l];
   }
   for (int n = threadIdx.x; n < P.np2; n += kThreads) keys[n] = sorted[(size_t)c * P.np2 + n];
   __syncthreads();
@@ -292,8 +291,9 @@ __global__ void __launch_bounds__(kThreads) fill_kernel(AsmParams P, const uint3
     return k != kInvalid &&
            (e + 1 == P.np2 || keys[e + 1] == kInvalid || (keys[e + 1] >> nbits) != (k >> nbits));
   };
-  // contribution of sorted element e to every (l, l') pair
-  auto contrib = [&](int e, real *out) {
+  // add the contributions of sorted element e to every (l, l') pair:
+  // acc[m] += (W_pq w_y P_l(y)) P_l'(y'), the first factor per l
+  auto accumulate = [&](int e, Acc *acc) {
     int node = (int)(keys[e] & mask);
     int x = node % P.n_x;
     const PairConst &k = pc[node / P.n_x];
@@ -301,23 +301,24 @@ __global__ void __launch_bounds__(kThreads) fill_kernel(AsmParams P, const uint3
     real yp;
     if (F64) {
       double p2 = fma(k.A, y, k.Bp), q2 = fma(k.C, y, k.D), num = fma(k.nA, y, k.nB);
-      double den2 = fmax(p2, 0.0) * fmax(q2, 0.0);
-      double cc = den2 > 0.0 ? num * rsqrt(den2) : 0.0;
-      yp = (real)fmin(1.0, fmax(-1.0, cc));
+      double den2 = p2 * q2;  // both >= 0 up to rounding; guarded below
+      yp = den2 > 0.0 ? num * rsqrt(den2) : 0.0;
     } else {
       // recoupled squares and p'.q' in FP64 (three FMAs), the rest in FP32
       float p2 = (float)fma(k.A, y, k.Bp), q2 = (float)fma(k.C, y, k.D);
       float num = (float)fma(k.nA, y, k.nB);
-      float den2 = fmaxf(p2, 0.f) * fmaxf(q2, 0.f);
+      float den2 = p2 * q2;
       float cc = den2 > 0.f ? num * rsqrtf(den2) : 0.f;
       yp = (real)fminf(1.f, fmaxf(-1.f, cc));
     }
     real Pl2[NCH];
     legendre_n<real, NCH>(yp, Pl2);
-    real W = (real)k.W * wy[x];
+    real wl[NCH];
+    const real W = (real)k.W;
 #pragma unroll
-    for (int m = 0; m < NPAIR; ++m)
-      out[m] = W * Py[x * NCH + pair_first(NCH, m)] * Pl2[pair_second(NCH, m)];
+    for (int l = 0; l < NCH; ++l) wl[l] = W * Pyw[x * NCH + l];
+#pragma unroll
+    for (int m = 0; m < NPAIR; ++m) acc[m].fma(wl[pair_first(NCH, m)], Pl2[pair_second(NCH, m)]);
   };
 
   // step A: segment ranks from an integer scan of the head flags
@@ -369,10 +370,7 @@ __global__ void __launch_bounds__(kThreads) fill_kernel(AsmParams P, const uint3
 #pragma unroll
       for (int m = 0; m < NPAIR; ++m) run[m].zero();
     }
-    real v[NPAIR];
-    contrib(e, v);
-#pragma unroll
-    for (int m = 0; m < NPAIR; ++m) run[m].add(v[m]);
+    accumulate(e, run);
     if (is_tail(e)) {
       if (flag) {
         write_seg(seg0 + local_heads - 1, k, run);
@@ -557,7 +555,7 @@ wpcd_status assemble(wpcd_problem *pr, int prec, cudaStream_t s, wpcd_P **out) {
   }
   size_t rsz = prec == WPCD_FP64 ? sizeof(double) : sizeof(float);
   size_t smem_fill = sizeof(double) * 7 * (size_t)P.n_p * P.n_q +
-                     rsz * ((size_t)P.n_x * P.n_ch + P.n_x + 2) + sizeof(uint32_t) * np2;
+                     rsz * ((size_t)P.n_x * P.n_ch + 2) + sizeof(uint32_t) * np2;
   smem_fill = (smem_fill + 15) & ~(size_t)15;
   wpcd_status st = prec == WPCD_FP64
                        ? dispatch_fill<true>(P, n_cells, smem_fill, s, sorted, Pm->row_ptr, Pm->col, val, nnz)
