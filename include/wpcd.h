@@ -171,12 +171,29 @@ wpcd_status wpcd_resolvent(const wpcd_problem *pr, const double *E, int n_E, dou
 wpcd_status wpcd_kapply(const wpcd_problem *pr, const wpcd_P *P, const double *g, const double *x,
                         double *y, void *stream);
 
+/* precision of the solve */
+#define WPCD_SOLVE_FP64 0  /* plain FP64 iteration (the comparison baseline) */
+#define WPCD_SOLVE_MIXED 1 /* FP32 inner Krylov cycles (FP32 P0 values, FP32
+                              block GEMMs, compensated FP32 SpMM sums) inside
+                              an FP64 iterative-refinement loop whose
+                              residual b - (I - K) u is formed in FP64 */
+
 typedef struct {
-  int method;      /* WPCD_SUM_KRYLOV or WPCD_SUM_WYNN */
-  int max_iter;    /* cap on K applications (<= 512) */
+  int method;      /* WPCD_SUM_KRYLOV or WPCD_SUM_WYNN (Wynn: FP64, one energy at a time) */
+  int max_iter;    /* FP64 Krylov / Wynn: cap on K applications (<= 512) */
   int min_iter;    /* Wynn: minimum number of terms before stopping */
-  double tol;      /* Krylov: relative residual; Wynn: relative change */
-  int check_every; /* Krylov: read the residual estimate back every n steps */
+  double tol;      /* Krylov, mixed: relative residual; Wynn: relative change */
+  int check_every; /* FP64 Krylov: read the residual estimates back every n steps */
+  int precision;   /* WPCD_SOLVE_FP64 or WPCD_SOLVE_MIXED */
+  int batch;       /* energies solved together in one batched iteration
+                      (block K applications, SpMM over the batch); 0: all */
+  int inner_iter;  /* mixed: Krylov steps per refinement cycle (0: 16) */
+  int max_outer;   /* mixed: cap on refinement cycles (0: 12) */
+  int use_graph;   /* mixed: replay each inner cycle from a CUDA graph (1) or
+                      launch its kernels one by one (0) */
+  const double *u_init; /* device [n_E][dim] complex warm start, or NULL (0) */
+  double *u_out;   /* device [n_E][dim] complex solutions u = (I - K)^-1 u0,
+                      or NULL */
 } wpcd_solve_opts;
 
 typedef struct {
@@ -188,19 +205,37 @@ typedef struct {
   double U00[2];     /* on-shell element <Z_{0,0,j0}|U|Z_{0,0,j0}> */
   double S[2];       /* S = 1 - 2 pi i U00 / D */
   double A[2];       /* paper's amplitude (2/(3 q0)) U00 / (q_j0+1 - q_j0) */
-  float ms;          /* device time of this energy's solve (CUDA events) */
+  float ms;          /* device time of the batch holding this energy
+                        (CUDA events), divided by the batch size */
+  int n_kapply32;    /* mixed: FP32 K applications (n_kapply counts FP64 ones) */
+  int n_outer;       /* mixed: refinement cycles */
 } wpcd_solve_stats;
 
 /* Step 4 (Sec. 3.3: iterations of the matrix equation and Pade
  * summation): for every energy, the on-shell element U00 of
  * U = P V1 + P V1 G1 U, from the iterates of K = O P0 Vt G1 started at the
- * Born term u0 = O P0 Vt e0.  FP64 throughout (P0 of either precision is
- * applied with FP64 accumulation).  E: host [n_E]; U00: host [n_E] complex
+ * Born term u0 = O P0 Vt e0 (column e0 of U solves u = u0 + K u).
+ * Energies are processed in batches of opts->batch: one batched iteration
+ * applies K to all of them at once (the energy index innermost in device
+ * memory, so P0 is read once per batch), each energy keeping its own G1 and
+ * its own Krylov basis.  WPCD_SOLVE_FP64 runs the plain FP64 iteration;
+ * WPCD_SOLVE_MIXED runs FP32 inner cycles under an FP64 refinement loop and
+ * reaches the same FP64 tolerance.  E: host [n_E]; U00: host [n_E] complex
  * (interleaved); stats: host [n_E] or NULL.  Returns the worst per-energy
  * status (ENOCONV / EBREAKDOWN still deliver the best estimate). */
 wpcd_status wpcd_solve(wpcd_problem *pr, const wpcd_P *P, const double *E, int n_E,
                        const wpcd_solve_opts *opts, double *U00, wpcd_solve_stats *stats,
                        void *stream);
+
+/* Autotuner (batching): time the candidate SpMM launch shapes (rows per
+ * warp, energy lanes per row, energies per lane = RHS tile width) for a
+ * batch of n_rhs energies in FP64 (fp32 = 0) or FP32 (fp32 = 1) and keep the
+ * fastest in P for later solves; returns the choice.  Solves tune on first
+ * use of a (batch, precision) pair.  With WPCD_TUNE_CACHE set to a file
+ * path, choices are also read from / appended to that file (text lines
+ * "key rows_per_warp energy_lanes energies_per_lane"). */
+wpcd_status wpcd_tune_spmm(wpcd_problem *pr, wpcd_P *P, int n_rhs, int fp32, void *stream,
+                           int *rows_per_warp, int *energy_lanes, int *energies_per_lane);
 
 #ifdef __cplusplus
 }

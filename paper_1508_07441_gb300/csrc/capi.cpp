@@ -36,6 +36,20 @@ static void free_tables(DeviceTables &d) {
     cudaFree(*p);
     *p = nullptr;
   }
+  cudaFree(d.O32);
+  cudaFree(d.Vt32);
+  d.O32 = d.Vt32 = nullptr;
+}
+
+static wpcd_status upload32(float **dst, const std::vector<double> &src) {
+  std::vector<float> f(src.begin(), src.end());
+  cudaError_t e = cudaMalloc(dst, sizeof(float) * (f.empty() ? 1 : f.size()));
+  if (e != cudaSuccess) return cuda_error(e, "cudaMalloc (problem tables)");
+  if (!f.empty()) {
+    e = cudaMemcpy(*dst, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy (problem tables)");
+  }
+  return WPCD_OK;
 }
 
 static wpcd_status upload(double **dst, const std::vector<double> &src) {
@@ -162,7 +176,7 @@ static wpcd_status create(const wpcd_problem_desc *d, wpcd_problem **out) {
       (st = upload(&t.wp, pw)) || (st = upload(&t.qn, qn)) || (st = upload(&t.wq, qw)) ||
       (st = upload(&t.yn, ty)) || (st = upload(&t.wy, wy)) || (st = upload(&t.rsb, rsb)) ||
       (st = upload(&t.qe, pr->qe)) || (st = upload(&t.eps, pr->eps)) || (st = upload(&t.O, pr->O)) ||
-      (st = upload(&t.Vt, pr->Vt))) {
+      (st = upload(&t.Vt, pr->Vt)) || (st = upload32(&t.O32, pr->O)) || (st = upload32(&t.Vt32, pr->Vt))) {
     free_tables(t);
     delete pr;
     return st;
@@ -252,6 +266,7 @@ void wpcd_P_destroy(wpcd_P *P) {
   cudaFree(P->col);
   cudaFree(P->val64);
   cudaFree(P->val32);
+  cudaFree(P->val32_copy);
   delete P;
 }
 
@@ -321,6 +336,25 @@ wpcd_status wpcd_solve(wpcd_problem *pr, const wpcd_P *P, const double *E, int n
   if (!pr || !P) return set_error(WPCD_EINVAL, "null problem or P");
   if (P->pr != pr) return set_error(WPCD_EINVAL, "P was assembled for another problem");
   return solve(pr, P, E, n_E, opts, U00, stats, static_cast<cudaStream_t>(stream));
+  WPCD_GUARD_END
+}
+
+wpcd_status wpcd_tune_spmm(wpcd_problem *pr, wpcd_P *P, int n_rhs, int fp32, void *stream,
+                           int *rows_per_warp, int *energy_lanes, int *energies_per_lane) {
+  WPCD_GUARD_BEGIN
+  clear_error();
+  if (!pr || !P || P->pr != pr) return set_error(WPCD_EINVAL, "bad problem or P");
+  if (n_rhs < 1 || n_rhs > 1024) return set_error(WPCD_EINVAL, "n_rhs must be in [1, 1024]");
+  if (fp32 && !P->val32 && !P->val32_copy)
+    return set_error(WPCD_EINVAL, "FP32 tuning needs an FP32C P (or a mixed solve first)");
+  WPCD_CUDA_TRY(cudaSetDevice(pr->device));
+  SpmmConfig c;
+  wpcd_status st = tune_spmm(pr, P, n_rhs, fp32 ? 1 : 0, static_cast<cudaStream_t>(stream), &c);
+  if (st != WPCD_OK) return st;
+  if (rows_per_warp) *rows_per_warp = c.rpw;
+  if (energy_lanes) *energy_lanes = c.el;
+  if (energies_per_lane) *energies_per_lane = c.ept;
+  return WPCD_OK;
   WPCD_GUARD_END
 }
 

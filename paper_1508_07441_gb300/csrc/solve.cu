@@ -1,26 +1,37 @@
 // Steps 3 and 4 of the numerical scheme (Sec. 3.3): the channel resolvent
 // G1 and the iterative solution of the matrix Faddeev equation (Eq. m_pvg)
-// with the factorised kernel K = O P0 Vt G1 (Eq. kernel).
+// with the factorised kernel K = O P0 Vt G1 (Eq. kernel), batched over
+// energies.
 //
-// One K application (FP64):
-//   gemm_kernel<VT>  Y[ch] = Vt[ch] (G1 o X)[ch]   (G1 fused into the B load)
-//   spmv_kernel      Z[l][c] = sum_{c', l'} P0[(l,c),(l',c')] Y[l'][c']
-//   gemm_kernel<O>   X'[ch] = O[ch] Z[ch]          (optional epilogue V - .)
-// Complex vectors are interleaved, so an [N][M] complex block is an
-// [N][2M] real matrix and the (real) block matrices multiply it directly.
+// Device layout of a batch of B energies: the energy index is innermost,
+// element (r, e) of a channel-basis vector at r * B + e (complex
+// interleaved), r = ch*N*M + k*M + j.  So an [N][M][B] complex block per
+// channel is an [N][2MB] real matrix and one K application is
+//   gemm_kernel<T>   Y[ch] = Vt[ch] (G1 o X)[ch]   (G1 fused into the B load)
+//   spmm_kernel      Z[l][c][e] = sum_{c', l'} P0[(l,c),(l',c')] Y[l'][c'][e]
+//   gemm_kernel<T>   X'[ch] = O[ch] Z[ch]           (optional epilogue S - .)
+// P0 is read once for the whole batch; each energy has its own G1.
 //
 // Summation of the iterates:
-//   KRYLOV  the vector form: Arnoldi with two-pass classical Gram-Schmidt on
-//           the iterates of (I - K), the least-squares problem updated by
-//           Givens rotations on the device; equivalent to the
-//           minimal-residual (reduced-rank) extrapolation of the iterates.
-//   WYNN    the paper's scalar route: c_n = e0^T K^n u0 collected on the
-//           device and summed by Wynn's epsilon algorithm (device kernel).
+//   KRYLOV (vector form)  Arnoldi with two-pass classical Gram-Schmidt on the
+//          iterates of (I - K), one basis per energy, Givens updates on the
+//          device: the minimal-residual (reduced-rank) extrapolation of the
+//          iterates.  FP64, or MIXED: FP32 inner cycles (FP32 values,
+//          compensated SpMM sums, CUDA-graph replay) inside an FP64
+//          iterative-refinement loop r = b - (I - K) u.
+//   WYNN (the paper's scalar route)  c_n = e0^T K^n u0 summed by Wynn's
+//          epsilon algorithm on the device (FP64, one energy at a time).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <mutex>
+#include <sstream>
+#include <string>
 #include <vector>
 
 #include "wpcd_internal.h"
@@ -29,6 +40,17 @@ namespace wpcd {
 namespace {
 
 constexpr double kPi = 3.141592653589793238462643383279502884;
+
+template <typename T>
+struct Cx;
+template <>
+struct Cx<double> {
+  using t = double2;
+};
+template <>
+struct Cx<float> {
+  using t = float2;
+};
 
 // ---------------------------------------------------------------------------
 // resolvent
@@ -61,10 +83,10 @@ __device__ double phi_noconst(double qa, double qb, double a) {
 }
 
 struct ResParams {
-  int n_ch, N, M, n_E;
+  int n_ch, N, M, n_E, minor;  // minor: energy index innermost
   const double *qe, *eps;
-  const double *Elo, *Ehi;  // per energy
-  const double *gl_t, *gl_w; // 32-point GL rule
+  const double *Elo, *Ehi;     // per energy
+  const double *gl_t, *gl_w;   // 32-point GL rule
 };
 
 __global__ void resolvent_kernel(ResParams R, double *g) {
@@ -72,8 +94,14 @@ __global__ void resolvent_kernel(ResParams R, double *g) {
   const int64_t total = (int64_t)R.n_E * dim;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    int e = (int)(idx / dim);
-    int r = (int)(idx % dim);
+    int e, r;
+    if (R.minor) {
+      e = (int)(idx % R.n_E);
+      r = (int)(idx / R.n_E);
+    } else {
+      e = (int)(idx / dim);
+      r = (int)(idx % dim);
+    }
     int j = r % R.M;
     int chk = r / R.M;  // ch*N + k
     double ek = R.eps[chk];
@@ -110,43 +138,44 @@ __global__ void resolvent_kernel(ResParams R, double *g) {
 }
 
 // ---------------------------------------------------------------------------
-// dense block GEMM (FP64):  C[b] (n x ncol) = A[b] (n x n) * B'[b] (n x ncol)
-// B' = B, or the G1-scaled complex block (ncol = 2M, complex pairs)
+// dense block GEMM:  C[b] (n x ncol) = A[b] (n x n) * B'[b] (n x ncol)
+// B' = B, or the G1-scaled complex block (complex pairs along the columns)
 // epilogue: C = out, or C = S - out
 // ---------------------------------------------------------------------------
-// 32 x 64 output tiles: 7 x 7 x 3 = 147 CTAs for the 200-bin, 3-channel
-// blocks, close to one wave over the 152 SMs (FP64 work is issue-bound, so
-// SM coverage matters more than data reuse here)
+// 32 x 64 output tiles: 7 x 7 x 3 = 147 CTAs for the 200-bin, 3-channel,
+// one-energy blocks, close to one wave over the 152 SMs (FP64 work is
+// issue-bound, so SM coverage matters more than data reuse there)
 constexpr int GB_M = 32, GB_N = 64, GB_K = 16, G_THREADS = 256;
 
-template <bool SCALE_G, bool SUB>
-__global__ void __launch_bounds__(G_THREADS) gemm_kernel(int n, int ncol, const double *__restrict__ A,
-                                                         const double *__restrict__ B,
-                                                         const double *__restrict__ G,
-                                                         const double *__restrict__ S,
-                                                         double *__restrict__ C) {
-  __shared__ double As[GB_K][GB_M + 1];
-  __shared__ double Bs[GB_K][GB_N];
+template <typename T, bool SCALE_G, bool SUB>
+__global__ void __launch_bounds__(G_THREADS) gemm_kernel(int n, int64_t ncol, const T *__restrict__ A,
+                                                         const T *__restrict__ B,
+                                                         const T *__restrict__ G,
+                                                         const T *__restrict__ S, T *__restrict__ C) {
+  __shared__ T As[GB_K][GB_M + 1];
+  __shared__ T Bs[GB_K][GB_N];
   const int b = blockIdx.z;
   const size_t offA = (size_t)b * n * n, offB = (size_t)b * n * ncol;
-  const int row0 = blockIdx.y * GB_M, col0 = blockIdx.x * GB_N;
+  const int row0 = blockIdx.y * GB_M;
+  const int64_t col0 = (int64_t)blockIdx.x * GB_N;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 16 x 16 threads, 2 x 4 outputs each
-  double acc[2][4] = {};
+  T acc[2][4] = {};
   for (int k0 = 0; k0 < n; k0 += GB_K) {
     for (int t = threadIdx.x; t < GB_M * GB_K; t += G_THREADS) {
       int r = t / GB_K, kk = t % GB_K;
       int gr = row0 + r, gk = k0 + kk;
-      As[kk][r] = (gr < n && gk < n) ? A[offA + (size_t)gr * n + gk] : 0.0;
+      As[kk][r] = (gr < n && gk < n) ? A[offA + (size_t)gr * n + gk] : T(0);
     }
     for (int t = threadIdx.x; t < GB_K * GB_N; t += G_THREADS) {
       int kk = t / GB_N, cc = t % GB_N;
-      int gk = k0 + kk, gc = col0 + cc;
-      double v = 0.0;
+      int gk = k0 + kk;
+      int64_t gc = col0 + cc;
+      T v = T(0);
       if (gk < n && gc < ncol) {
         size_t o = offB + (size_t)gk * ncol + gc;
         if (SCALE_G) {
           size_t oc = o & ~(size_t)1;  // complex pair (re at even column)
-          double xr = B[oc], xi = B[oc + 1], gr_ = G[oc], gi = G[oc + 1];
+          T xr = B[oc], xi = B[oc + 1], gr_ = G[oc], gi = G[oc + 1];
           v = (gc & 1) ? (gr_ * xi + gi * xr) : (gr_ * xr - gi * xi);
         } else {
           v = B[o];
@@ -157,7 +186,7 @@ __global__ void __launch_bounds__(G_THREADS) gemm_kernel(int n, int ncol, const 
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < GB_K; ++kk) {
-      double a[2], bb[4];
+      T a[2], bb[4];
 #pragma unroll
       for (int u = 0; u < 2; ++u) a[u] = As[kk][ty + 16 * u];
 #pragma unroll
@@ -173,7 +202,8 @@ __global__ void __launch_bounds__(G_THREADS) gemm_kernel(int n, int ncol, const 
   for (int u = 0; u < 2; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      int gr = row0 + ty + 16 * u, gc = col0 + tx + 16 * v;
+      int gr = row0 + ty + 16 * u;
+      int64_t gc = col0 + tx + 16 * v;
       if (gr < n && gc < ncol) {
         size_t o = offB + (size_t)gr * ncol + gc;
         C[o] = SUB ? S[o] - acc[u][v] : acc[u][v];
@@ -182,159 +212,248 @@ __global__ void __launch_bounds__(G_THREADS) gemm_kernel(int n, int ncol, const 
 }
 
 // ---------------------------------------------------------------------------
-// block-CSR SpMV on complex vectors: Z[l][c] = sum P0 Y
-// LPR lanes per row; values pair-major (val[m][nnz]), real = double / float
+// block-CSR SpMM on complex batches: Z[l][c][e] = sum P0 Y[l'][c'][e]
+// A warp holds `rpw` rows; each row's 32/rpw lanes split into `el` energy
+// lanes times 32/(rpw el) nonzero lanes; every lane keeps EPT energies
+// (RHS tile = el * EPT, grid.y walks the tiles).  Values pair-major.
+// FP64 sums in double; FP32 sums compensated (float-float).
 // ---------------------------------------------------------------------------
-struct SpmvParams {
-  int n_cells, n_ch, n_pairs;
-  int pl[kMaxPairs], plp[kMaxPairs];
+struct SpmmParams {
+  int n_cells, B, rpw, el;
   const int64_t *row_ptr;
   const int32_t *col;
   int64_t nnz;
 };
 
-template <typename real, int NCH, int LPR>
-__global__ void __launch_bounds__(256) spmv_kernel(SpmvParams S, const real *__restrict__ val,
-                                                   const double2 *__restrict__ y, double2 *__restrict__ z) {
+struct AccD {
+  double v;
+  __device__ void zero() { v = 0.0; }
+  __device__ void fma(double a, double b) { v = ::fma(a, b, v); }
+  __device__ void add_shfl(int off) { v += __shfl_xor_sync(0xffffffffu, v, off); }
+  __device__ double value() const { return v; }
+};
+
+struct AccF {  // float-float (Knuth TwoSum on the running sum, exact products)
+  float hi, lo;
+  __device__ void zero() { hi = 0.f; lo = 0.f; }
+  __device__ void add(float x) {
+    float s = __fadd_rn(hi, x);
+    float bb = __fsub_rn(s, hi);
+    float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ void fma(float a, float b) {
+    float p = __fmul_rn(a, b);
+    float pe = fmaf(a, b, -p);  // exact product error (TwoProduct)
+    add(p);
+    lo = __fadd_rn(lo, pe);
+  }
+  __device__ void add_shfl(int off) {
+    float ohi = __shfl_xor_sync(0xffffffffu, hi, off);
+    float olo = __shfl_xor_sync(0xffffffffu, lo, off);
+    add(ohi);
+    lo = __fadd_rn(lo, olo);
+  }
+  __device__ float value() const { return __fadd_rn(hi, lo); }
+};
+
+template <typename T>
+struct AccOf;
+template <>
+struct AccOf<double> {
+  using t = AccD;
+};
+template <>
+struct AccOf<float> {
+  using t = AccF;
+};
+
+template <typename VT, typename T, int NCH, int EPT>
+__global__ void __launch_bounds__(256) spmm_kernel(SpmmParams S, const VT *__restrict__ val,
+                                                   const typename Cx<T>::t *__restrict__ y,
+                                                   typename Cx<T>::t *__restrict__ z) {
+  using C2 = typename Cx<T>::t;
+  using Acc = typename AccOf<T>::t;
   constexpr int NPAIR = pair_count(NCH);
-  constexpr int GPW = 32 / LPR;  // row groups per warp
-  const int lane = threadIdx.x % LPR;
-  const int gw = threadIdx.x / LPR % GPW;
+  const int lane = threadIdx.x & 31;
+  const int lpr = 32 / S.rpw;          // lanes per row
+  const int nl_count = lpr / S.el;     // nonzero lanes per row
+  const int r_in = lane / lpr, sub = lane % lpr;
+  const int el = sub % S.el, nl = sub / S.el;
   const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
   const int n_warps = gridDim.x * blockDim.x / 32;
+  const int e_base = blockIdx.y * S.el * EPT;
+  const int B = S.B;
   // the loop bound depends on the warp only, so every lane reaches the
   // full-mask shuffles below
-  for (int base = warp_global * GPW; base < S.n_cells; base += n_warps * GPW) {
-    const int c = base + gw;
+  for (int base = warp_global * S.rpw; base < S.n_cells; base += n_warps * S.rpw) {
+    const int c = base + r_in;
     const bool active = c < S.n_cells;
-    double2 acc[NCH];
+    Acc acc[NCH][EPT][2];
 #pragma unroll
-    for (int l = 0; l < NCH; ++l) acc[l] = make_double2(0.0, 0.0);
+    for (int l = 0; l < NCH; ++l)
+#pragma unroll
+      for (int t = 0; t < EPT; ++t) {
+        acc[l][t][0].zero();
+        acc[l][t][1].zero();
+      }
     const int64_t b = active ? S.row_ptr[c] : 0, e = active ? S.row_ptr[c + 1] : 0;
-    for (int64_t o = b + lane; o < e; o += LPR) {
-      const int t = __ldg(S.col + o);
-      double2 yv[NCH];
+    for (int64_t o = b + nl; o < e; o += nl_count) {
+      const int tc = __ldg(S.col + o);
+      T v[NPAIR];
 #pragma unroll
-      for (int l = 0; l < NCH; ++l) yv[l] = __ldg(y + (size_t)l * S.n_cells + t);
+      for (int m = 0; m < NPAIR; ++m) v[m] = (T)__ldg(val + (size_t)m * S.nnz + o);
 #pragma unroll
-      for (int m = 0; m < NPAIR; ++m) {
-        const int l = pair_first(NCH, m), lp = pair_second(NCH, m);
-        double v = (double)__ldg(val + (size_t)m * S.nnz + o);
-        acc[l].x = fma(v, yv[lp].x, acc[l].x);
-        acc[l].y = fma(v, yv[lp].y, acc[l].y);
+      for (int t = 0; t < EPT; ++t) {
+        const int en = e_base + el + S.el * t;
+        if (en < B) {
+          C2 yv[NCH];
+#pragma unroll
+          for (int l = 0; l < NCH; ++l) yv[l] = __ldg(y + ((size_t)l * S.n_cells + tc) * B + en);
+#pragma unroll
+          for (int m = 0; m < NPAIR; ++m) {
+            const int l = pair_first(NCH, m), lp = pair_second(NCH, m);
+            acc[l][t][0].fma(v[m], yv[lp].x);
+            acc[l][t][1].fma(v[m], yv[lp].y);
+          }
+        }
       }
     }
+    // reduce over the nonzero lanes of the row (xor offsets el .. lpr/2)
+    for (int off = S.el; off < lpr; off <<= 1)
 #pragma unroll
-    for (int off = LPR / 2; off > 0; off >>= 1)
+      for (int l = 0; l < NCH; ++l)
 #pragma unroll
-      for (int l = 0; l < NCH; ++l) {
-        acc[l].x += __shfl_xor_sync(0xffffffffu, acc[l].x, off, LPR);
-        acc[l].y += __shfl_xor_sync(0xffffffffu, acc[l].y, off, LPR);
+        for (int t = 0; t < EPT; ++t) {
+          acc[l][t][0].add_shfl(off);
+          acc[l][t][1].add_shfl(off);
+        }
+    if (active && nl == 0) {
+#pragma unroll
+      for (int t = 0; t < EPT; ++t) {
+        const int en = e_base + el + S.el * t;
+        if (en < B)
+#pragma unroll
+          for (int l = 0; l < NCH; ++l) {
+            C2 out;
+            out.x = (T)acc[l][t][0].value();
+            out.y = (T)acc[l][t][1].value();
+            z[((size_t)l * S.n_cells + c) * B + en] = out;
+          }
       }
-    if (active && lane == 0)
-#pragma unroll
-      for (int l = 0; l < NCH; ++l) z[(size_t)l * S.n_cells + c] = acc[l];
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
-// vector kernels for the Krylov basis (complex, interleaved)
+// batched Krylov vector kernels (energy index innermost); scalars in FP64
 // ---------------------------------------------------------------------------
 constexpr int V_THREADS = 256;
 
-// partial[j][blk] = sum_{i in blk} conj(V_j[i]) w[i], j < nv
-__global__ void __launch_bounds__(V_THREADS) multi_dot_kernel(int n, int nv, const double2 *__restrict__ V,
-                                                              size_t ld, const double2 *__restrict__ w,
-                                                              double2 *__restrict__ partial) {
-  __shared__ double2 red[V_THREADS / 32];
+// partial[(j * nblk + blk) * B + e] = sum_{rows of blk} conj(V_j[row, e]) w[row, e]
+template <typename T>
+__global__ void __launch_bounds__(V_THREADS) bdot_kernel(int rows, int B, int nv,
+                                                         const typename Cx<T>::t *__restrict__ V,
+                                                         size_t ld, const typename Cx<T>::t *__restrict__ w,
+                                                         double2 *__restrict__ partial) {
+  __shared__ double2 red[V_THREADS];
+  const int EL = blockDim.x;  // energy lanes (<= 32)
+  const int RB = blockDim.y;  // row lanes
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int e = blockIdx.y * EL + tx;
   const int nblk = gridDim.x;
   for (int j = 0; j < nv; ++j) {
-    double2 s = make_double2(0.0, 0.0);
-    for (int i = blockIdx.x * V_THREADS + threadIdx.x; i < n; i += nblk * V_THREADS) {
-      double2 a = V[(size_t)j * ld + i], b = w[i];
-      s.x += a.x * b.x + a.y * b.y;
-      s.y += a.x * b.y - a.y * b.x;
+    double sx = 0.0, sy = 0.0;
+    if (e < B) {
+      for (int r = blockIdx.x * RB + ty; r < rows; r += nblk * RB) {
+        auto a = V[(size_t)j * ld + (size_t)r * B + e];
+        auto b = w[(size_t)r * B + e];
+        sx += (double)a.x * b.x + (double)a.y * b.y;
+        sy += (double)a.x * b.y - (double)a.y * b.x;
+      }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      s.x += __shfl_down_sync(0xffffffffu, s.x, o);
-      s.y += __shfl_down_sync(0xffffffffu, s.y, o);
-    }
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    red[ty * EL + tx] = make_double2(sx, sy);
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double2 t = make_double2(0.0, 0.0);
-      for (int k = 0; k < V_THREADS / 32; ++k) { t.x += red[k].x; t.y += red[k].y; }
-      partial[(size_t)j * nblk + blockIdx.x] = t;
+    for (int h = RB / 2; h > 0; h >>= 1) {
+      if (ty < h) {
+        double2 o = red[(ty + h) * EL + tx];
+        red[ty * EL + tx].x += o.x;
+        red[ty * EL + tx].y += o.y;
+      }
+      __syncthreads();
     }
+    if (ty == 0 && e < B) partial[((size_t)j * nblk + blockIdx.x) * B + e] = red[tx];
     __syncthreads();
   }
 }
 
-// out[j] (+)= sum_blk partial[j][blk]   (accumulate: add to out)
-__global__ void reduce_partials_kernel(int nv, int nblk, const double2 *partial, double2 *out, int accumulate) {
-  int j = blockIdx.x;
-  __shared__ double2 red[256];
-  double2 s = make_double2(0.0, 0.0);
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-    s.x += partial[(size_t)j * nblk + b].x;
-    s.y += partial[(size_t)j * nblk + b].y;
+// out[j * B + e] (+)= sum_blk partial[(j * nblk + blk) * B + e]
+__global__ void breduce_kernel(int nv, int nblk, int B, const double2 *partial, double2 *out,
+                               int accumulate) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nv * B) return;
+  int j = idx / B, e = idx % B;
+  double sx = 0.0, sy = 0.0;
+  for (int b = 0; b < nblk; ++b) {
+    double2 p = partial[((size_t)j * nblk + b) * B + e];
+    sx += p.x;
+    sy += p.y;
   }
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) { red[threadIdx.x].x += red[threadIdx.x + o].x; red[threadIdx.x].y += red[threadIdx.x + o].y; }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    if (accumulate) { out[j].x += red[0].x; out[j].y += red[0].y; }
-    else out[j] = red[0];
+  if (accumulate) {
+    out[idx].x += sx;
+    out[idx].y += sy;
+  } else {
+    out[idx] = make_double2(sx, sy);
   }
 }
 
-// w[i] -= sum_j h[j] V_j[i]  (sign = -1) or w[i] += ... (sign = +1)
-__global__ void multi_axpy_kernel(int n, int nv, const double2 *__restrict__ V, size_t ld,
-                                  const double2 *__restrict__ h, double2 *__restrict__ w, double sign) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    double2 acc = w[i];
+// w[f] += sign * sum_j h[j * B + e] V_j[f]
+template <typename T>
+__global__ void baxpy_kernel(int64_t n, int B, int nv, const typename Cx<T>::t *__restrict__ V,
+                             size_t ld, const double2 *__restrict__ h, typename Cx<T>::t *__restrict__ w,
+                             double sign) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    const int e = (int)(f % B);
+    double ax = w[f].x, ay = w[f].y;
     for (int j = 0; j < nv; ++j) {
-      double2 a = V[(size_t)j * ld + i], c = h[j];
-      acc.x += sign * (c.x * a.x - c.y * a.y);
-      acc.y += sign * (c.x * a.y + c.y * a.x);
+      auto a = V[(size_t)j * ld + f];
+      double2 c = h[j * B + e];
+      ax += sign * (c.x * a.x - c.y * a.y);
+      ay += sign * (c.x * a.y + c.y * a.x);
     }
-    w[i] = acc;
+    w[f].x = (T)ax;
+    w[f].y = (T)ay;
   }
 }
 
-// dst = src * (1 / |nrm|)  where nrm is a device scalar (real part used)
-__global__ void scale_kernel(int n, const double2 *src, const double2 *nrm2, double2 *dst) {
-  double s = nrm2->x > 0.0 ? 1.0 / sqrt(nrm2->x) : 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    double2 a = src[i];
-    dst[i] = make_double2(a.x * s, a.y * s);
+// dst[f] = src[f] / sqrt(nrm2[e].x)   (0 if the norm is 0)
+template <typename T>
+__global__ void bscale_kernel(int64_t n, int B, const typename Cx<T>::t *src, const double2 *nrm2,
+                              typename Cx<T>::t *dst) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    const int e = (int)(f % B);
+    double s = nrm2[e].x > 0.0 ? 1.0 / sqrt(nrm2[e].x) : 0.0;
+    dst[f].x = (T)(src[f].x * s);
+    dst[f].y = (T)(src[f].y * s);
   }
 }
 
-// Krylov state on the device
-struct KrylovState {
-  int m;          // capacity (columns)
-  int k;          // columns done
-  int status;
-  double bnorm;
-  double relres;
-  double2 H[1];   // [(m+1) * m] column-major Hessenberg, then cs, sn, bet, y
-};
-
-// one Givens/least-squares update for column k; h[0..k] holds the Gram-Schmidt
-// coefficients (accumulated over both passes), hn2 the squared norm of the
-// new vector (real part)
-__global__ void givens_kernel(int m, int k, const double2 *h, const double2 *hn2, double2 *H,
-                              double2 *cs, double2 *sn, double2 *bet, double *resid, double bnorm) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Givens least-squares update of column k for every energy (thread e).
+// Layout per energy e: H + e*(m+1)*m column-major (ld m+1), cs/sn + e*m,
+// bet + e*(m+1); h[i * B + e], hn2[e].
+__global__ void bgivens_kernel(int B, int m, int k, const double2 *h, const double2 *hn2, double2 *Hb,
+                               double2 *csb, double2 *snb, double2 *betb, double *resid,
+                               const double *bnorm) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= B) return;
+  double2 *H = Hb + (size_t)e * (m + 1) * m, *cs = csb + (size_t)e * m, *sn = snb + (size_t)e * m;
+  double2 *bet = betb + (size_t)e * (m + 1);
   double2 *col = H + (size_t)k * (m + 1);
-  for (int i = 0; i <= k; ++i) col[i] = h[i];
-  // H stores -h for the (I - K) operator convention handled by the caller
-  double hn = sqrt(fmax(hn2->x, 0.0));
-  col[k + 1] = make_double2(hn, 0.0);
+  for (int i = 0; i <= k; ++i) col[i] = h[(size_t)i * B + e];
+  col[k + 1] = make_double2(sqrt(fmax(hn2[e].x, 0.0)), 0.0);
   for (int i = 0; i < k; ++i) {
     double2 a = col[i], b = col[i + 1], c = cs[i], s = sn[i];
     // [a'; b'] = [conj(c) conj(s); -s c] [a; b]
@@ -356,34 +475,113 @@ __global__ void givens_kernel(int m, int k, const double2 *h, const double2 *hn2
   double2 bk = bet[k];
   bet[k + 1] = make_double2(-(s.x * bk.x - s.y * bk.y), -(s.x * bk.y + s.y * bk.x));
   bet[k] = make_double2(c.x * bk.x + c.y * bk.y, c.x * bk.y - c.y * bk.x);
-  *resid = sqrt(bet[k + 1].x * bet[k + 1].x + bet[k + 1].y * bet[k + 1].y) / bnorm;
+  resid[e] = sqrt(bet[k + 1].x * bet[k + 1].x + bet[k + 1].y * bet[k + 1].y) / bnorm[e];
 }
 
-// back substitution H y = bet (k x k upper triangular)
-__global__ void backsub_kernel(int m, int k, const double2 *H, const double2 *bet, double2 *y) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// back substitution H y = bet per energy; y[j * B + e]
+__global__ void bbacksub_kernel(int B, int m, int k, const double2 *Hb, const double2 *betb, double2 *y) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= B) return;
+  const double2 *H = Hb + (size_t)e * (m + 1) * m, *bet = betb + (size_t)e * (m + 1);
   for (int i = k - 1; i >= 0; --i) {
     double2 s = bet[i];
     for (int j = i + 1; j < k; ++j) {
-      double2 h = H[(size_t)j * (m + 1) + i], yj = y[j];
+      double2 h = H[(size_t)j * (m + 1) + i], yj = y[(size_t)j * B + e];
       s.x -= h.x * yj.x - h.y * yj.y;
       s.y -= h.x * yj.y + h.y * yj.x;
     }
     double2 d = H[(size_t)i * (m + 1) + i];
     double dd = d.x * d.x + d.y * d.y;
-    y[i] = make_double2((s.x * d.x + s.y * d.y) / dd, (s.y * d.x - s.x * d.y) / dd);
+    y[(size_t)i * B + e] = dd > 0.0 ? make_double2((s.x * d.x + s.y * d.y) / dd, (s.y * d.x - s.x * d.y) / dd)
+                                    : make_double2(0.0, 0.0);
+  }
+  for (int i = k; i < m; ++i) y[(size_t)i * B + e] = make_double2(0.0, 0.0);
+}
+
+// u[f] += coef[e] * sum_j y[j * B + e] V_j[f]   (u FP64; V in T;
+// coef = sqrt(nrm2[e].x), or 1 when nrm2 is NULL)
+template <typename T>
+__global__ void bupdate_kernel(int64_t n, int B, int k, const typename Cx<T>::t *__restrict__ V,
+                               size_t ld, const double2 *__restrict__ y, const double2 *__restrict__ nrm2,
+                               double2 *__restrict__ u) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    const int e = (int)(f % B);
+    double ax = 0.0, ay = 0.0;
+    for (int j = 0; j < k; ++j) {
+      auto a = V[(size_t)j * ld + f];
+      double2 c = y[(size_t)j * B + e];
+      ax += c.x * a.x - c.y * a.y;
+      ay += c.x * a.y + c.y * a.x;
+    }
+    double s = nrm2 ? sqrt(nrm2[e].x) : 1.0;
+    u[f].x += s * ax;
+    u[f].y += s * ay;
   }
 }
 
-// amplitude from the on-shell element: S = 1 - 2 pi i U00 / D, paper's A
-__global__ void amplitude_kernel(const double2 *u, int r0, double D, double pref, double *out) {
-  double2 U = u[r0];
-  out[0] = U.x;
-  out[1] = U.y;
-  out[2] = 1.0 + 2.0 * kPi * U.y / D;   // Re S
-  out[3] = -2.0 * kPi * U.x / D;        // Im S
-  out[4] = pref * U.x;
-  out[5] = pref * U.y;
+// r = b - u + t  (FP64)
+__global__ void bresid_kernel(int64_t n, const double2 *b, const double2 *u, const double2 *t, double2 *r) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n;
+       f += (int64_t)gridDim.x * blockDim.x)
+    r[f] = make_double2(b[f].x - u[f].x + t[f].x, b[f].y - u[f].y + t[f].y);
+}
+
+// dst32[f] = (float)(src[f] / sqrt(nrm2[e].x))
+__global__ void bnormalize_f32_kernel(int64_t n, int B, const double2 *src, const double2 *nrm2, float2 *dst) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    const int e = (int)(f % B);
+    double s = nrm2[e].x > 0.0 ? 1.0 / sqrt(nrm2[e].x) : 0.0;
+    dst[f] = make_float2((float)(src[f].x * s), (float)(src[f].y * s));
+  }
+}
+
+__global__ void d2f_kernel(int64_t n, const double *src, float *dst) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n;
+       f += (int64_t)gridDim.x * blockDim.x)
+    dst[f] = (float)src[f];
+}
+
+// unit vectors: X[r0[e] * B + e] = 1
+__global__ void bunits_kernel(int64_t n, int B, const int *r0, double2 *x) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    const int e = (int)(f % B);
+    const int64_t r = f / B;
+    x[f] = make_double2(r == r0[e] ? 1.0 : 0.0, 0.0);
+  }
+}
+
+// energy-major [B][dim] <-> energy-minor [dim][B] (complex)
+__global__ void transpose_kernel(int64_t dim, int B, const double2 *src, double2 *dst, int to_minor) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < dim * B;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    if (to_minor) {
+      const int64_t r = f / B;
+      const int e = (int)(f % B);
+      dst[f] = src[(size_t)e * dim + r];
+    } else {
+      const int e = (int)(f / dim);
+      const int64_t r = f % dim;
+      dst[f] = src[(size_t)r * B + e];
+    }
+  }
+}
+
+// S = 1 - 2 pi i U00 / D, paper's A; out[e * 6 + ...]
+__global__ void bamplitude_kernel(int B, const double2 *u, const int *r0, const double *D,
+                                  const double *pref, double *out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= B) return;
+  double2 U = u[(size_t)r0[e] * B + e];
+  double *o = out + 6 * (size_t)e;
+  o[0] = U.x;
+  o[1] = U.y;
+  o[2] = 1.0 + 2.0 * kPi * U.y / D[e];
+  o[3] = -2.0 * kPi * U.x / D[e];
+  o[4] = pref[e] * U.x;
+  o[5] = pref[e] * U.y;
 }
 
 // Wynn epsilon over the partial sums of c[0..n-1] (complex); writes the
@@ -405,7 +603,10 @@ __global__ void wynn_kernel(int n, const double2 *c, double2 *work, double2 *est
     for (int i = 0; i + 1 < len; ++i) {
       double dx = cur[i + 1].x - cur[i].x, dy = cur[i + 1].y - cur[i].y;
       double d2 = dx * dx + dy * dy;
-      if (d2 == 0.0) { bd = 1; break; }
+      if (d2 == 0.0) {
+        bd = 1;
+        break;
+      }
       nxt[i] = make_double2(prev[i + 1].x + dx / d2, prev[i + 1].y - dy / d2);
     }
     if (bd) break;
@@ -423,11 +624,6 @@ __global__ void wynn_kernel(int n, const double2 *c, double2 *work, double2 *est
 
 __global__ void extract_kernel(const double2 *x, int r0, double2 *c_out) { *c_out = x[r0]; }
 
-__global__ void set_unit_kernel(int n, int r0, double2 *x) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    x[i] = make_double2(i == r0 ? 1.0 : 0.0, 0.0);
-}
-
 int grid_for(int64_t n, int threads, int cap = 152 * 8) {
   int64_t g = (n + threads - 1) / threads;
   return (int)(g < 1 ? 1 : (g > cap ? cap : g));
@@ -436,66 +632,218 @@ int grid_for(int64_t n, int threads, int cap = 152 * 8) {
 // ---------------------------------------------------------------------------
 // K application machinery
 // ---------------------------------------------------------------------------
+template <typename T>
 struct Workspace {
-  double *y = nullptr, *z = nullptr;  // [dim] complex
+  T *y = nullptr, *z = nullptr;  // [dim * B] complex
   ~Workspace() {
     cudaFree(y);
     cudaFree(z);
   }
+  cudaError_t alloc(size_t dim, int B) {
+    cudaError_t e = cudaMalloc(&y, 2 * sizeof(T) * dim * B);
+    if (e != cudaSuccess) return e;
+    return cudaMalloc(&z, 2 * sizeof(T) * dim * B);
+  }
 };
 
-wpcd_status launch_spmv(const wpcd_problem *pr, const wpcd_P *P, const double *y, double *z, cudaStream_t s) {
-  SpmvParams S{};
+template <typename VT, typename T>
+wpcd_status launch_spmm_cfg(const wpcd_problem *pr, const wpcd_P *P, const VT *val, const T *y, T *z,
+                            int B, const SpmmConfig &cfg, cudaStream_t s) {
+  SpmmParams S{};
   S.n_cells = pr->N * pr->M;
-  S.n_ch = pr->n_ch;
-  S.n_pairs = pr->n_pairs;
-  for (int m = 0; m < pr->n_pairs; ++m) {
-    S.pl[m] = pr->pair_l[m];
-    S.plp[m] = pr->pair_lp[m];
-  }
+  S.B = B;
+  S.rpw = cfg.rpw;
+  S.el = cfg.el;
   S.row_ptr = P->row_ptr;
   S.col = P->col;
   S.nnz = P->nnz;
-  const double2 *yy = reinterpret_cast<const double2 *>(y);
-  double2 *zz = reinterpret_cast<double2 *>(z);
-  constexpr int LPR = 16;
-  int grid = grid_for((int64_t)S.n_cells, 256 / LPR, 152 * 16);  // blocks of 256 threads
-  bool f64 = P->prec == WPCD_FP64;
-#define WPCD_SPMV_CASE(NCH, NPAIR)                                                                 \
-  if (pr->n_ch == NCH) {                                                                           \
-    if (f64)                                                                                       \
-      spmv_kernel<double, NCH, LPR><<<grid, 256, 0, s>>>(S, P->val64, yy, zz);                     \
-    else                                                                                           \
-      spmv_kernel<float, NCH, LPR><<<grid, 256, 0, s>>>(S, P->val32, yy, zz);                      \
-    count_launches(1);                                                                             \
-    return cudaGetLastError() == cudaSuccess ? WPCD_OK : set_error(WPCD_ECUDA, "spmv launch");    \
+  using C2 = typename Cx<T>::t;
+  const C2 *yy = reinterpret_cast<const C2 *>(y);
+  C2 *zz = reinterpret_cast<C2 *>(z);
+  const int rows_per_block = 8 * cfg.rpw;
+  dim3 grid(grid_for((int64_t)S.n_cells, rows_per_block, 152 * 16),
+            (B + cfg.el * cfg.ept - 1) / (cfg.el * cfg.ept));
+#define WPCD_SPMM_EPT(NCH, EPT) spmm_kernel<VT, T, NCH, EPT><<<grid, 256, 0, s>>>(S, val, yy, zz)
+#define WPCD_SPMM_CASE(NCH)                       \
+  case NCH:                                       \
+    if (cfg.ept == 1)                             \
+      WPCD_SPMM_EPT(NCH, 1);                      \
+    else if (cfg.ept == 2)                        \
+      WPCD_SPMM_EPT(NCH, 2);                      \
+    else                                          \
+      WPCD_SPMM_EPT(NCH, 4);                      \
+    break;
+  switch (pr->n_ch) {
+    WPCD_SPMM_CASE(1)
+    WPCD_SPMM_CASE(2)
+    WPCD_SPMM_CASE(3)
+    WPCD_SPMM_CASE(4)
+    WPCD_SPMM_CASE(5)
+    default:
+      return set_error(WPCD_EINVAL, "unsupported channel count for the SpMM");
   }
-  WPCD_SPMV_CASE(1, 1)
-  WPCD_SPMV_CASE(2, 2)
-  WPCD_SPMV_CASE(3, 5)
-  WPCD_SPMV_CASE(4, 8)
-  WPCD_SPMV_CASE(5, 13)
-#undef WPCD_SPMV_CASE
-  return set_error(WPCD_EINVAL, "unsupported channel count for the SpMV");
+#undef WPCD_SPMM_CASE
+#undef WPCD_SPMM_EPT
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? WPCD_OK : cuda_error(e, "spmm launch");
 }
 
-// y = O P0 Vt (g o x)   or, with sub, y = sub - O P0 Vt (g o x)
-wpcd_status kapply_ws(const wpcd_problem *pr, const wpcd_P *P, const double *g, const double *x,
-                      double *out, const double *sub, Workspace &ws, cudaStream_t s) {
+// launch shapes tried by the autotuner for a batch of B energies
+std::vector<SpmmConfig> candidates(int B) {
+  std::vector<SpmmConfig> c;
+  if (B == 1) {
+    for (int rpw : {1, 2, 4, 8}) c.push_back(SpmmConfig{rpw, 1, 1});
+    return c;
+  }
+  int el = 1;
+  while (el < B && el < 32) el *= 2;
+  for (int ept : {1, 2, 4}) {
+    if (ept > 1 && el * ept / 2 >= B) continue;  // tile wider than the batch
+    c.push_back(SpmmConfig{1, el, ept});
+    if (el <= 16) c.push_back(SpmmConfig{2, el, ept});
+  }
+  if (el > 1) c.push_back(SpmmConfig{1, el / 2, 1});
+  return c;
+}
+
+std::mutex g_tune_mutex;
+
+bool load_cached(int64_t key, SpmmConfig *out) {
+  const char *path = std::getenv("WPCD_TUNE_CACHE");
+  if (!path || !*path) return false;
+  std::ifstream f(path);
+  std::string line;
+  bool found = false;
+  while (std::getline(f, line)) {
+    std::istringstream is(line);
+    long long k;
+    SpmmConfig c;
+    if (is >> k >> c.rpw >> c.el >> c.ept && k == key) {
+      *out = c;
+      found = true;
+    }
+  }
+  return found;
+}
+
+void store_cached(int64_t key, const SpmmConfig &c) {
+  const char *path = std::getenv("WPCD_TUNE_CACHE");
+  if (!path || !*path) return;
+  std::ofstream f(path, std::ios::app);
+  f << (long long)key << " " << c.rpw << " " << c.el << " " << c.ept << "\n";
+}
+
+}  // namespace
+
+// Time every candidate launch shape on the real P0 (3 launches each, CUDA
+// events, the minimum kept) and remember the fastest.
+wpcd_status tune_spmm(const wpcd_problem *pr, wpcd_P *P, int B, int fp32, cudaStream_t s,
+                      SpmmConfig *out) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  // the key carries the shape so that one cache file can serve several problems
+  const int64_t key = ((((int64_t)pr->n_ch * 4096 + pr->N) * 4096 + pr->M) * 4096 + B) * 2 + (fp32 ? 1 : 0);
+  auto it = P->tuned.find(key);
+  if (it != P->tuned.end()) {
+    *out = it->second;
+    return WPCD_OK;
+  }
+  SpmmConfig cached;
+  if (load_cached(key, &cached)) {
+    P->tuned[key] = cached;
+    *out = cached;
+    return WPCD_OK;
+  }
+  if (fp32 && !P->val32 && !P->val32_copy) return set_error(WPCD_EINVAL, "no FP32 values to tune on");
+  const size_t dim = (size_t)pr->n_ch * pr->N * pr->M;
+  void *y = nullptr, *z = nullptr;
+  const size_t esz = fp32 ? sizeof(float) : sizeof(double);
+  WPCD_CUDA_TRY(cudaMalloc(&y, 2 * esz * dim * B));
+  cudaError_t ce = cudaMalloc(&z, 2 * esz * dim * B);
+  if (ce != cudaSuccess) {
+    cudaFree(y);
+    return cuda_error(ce, "cudaMalloc (tuning)");
+  }
+  cudaMemsetAsync(y, 0, 2 * esz * dim * B, s);
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  float best = 1e30f;
+  SpmmConfig pick;
+  wpcd_status st = WPCD_OK;
+  for (const SpmmConfig &c : candidates(B)) {
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 3 && st == WPCD_OK; ++rep) {
+      cudaEventRecord(a, s);
+      if (fp32) {
+        const float *v32 = P->val32 ? P->val32 : P->val32_copy;
+        st = launch_spmm_cfg<float, float>(pr, P, v32, (const float *)y, (float *)z, B, c, s);
+      } else if (P->prec == WPCD_FP64) {
+        st = launch_spmm_cfg<double, double>(pr, P, P->val64, (const double *)y, (double *)z, B, c, s);
+      } else {
+        st = launch_spmm_cfg<float, double>(pr, P, P->val32, (const double *)y, (double *)z, B, c, s);
+      }
+      cudaEventRecord(b, s);
+      cudaEventSynchronize(b);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      tmin = std::min(tmin, ms);
+    }
+    if (st != WPCD_OK) break;
+    if (tmin < best) {
+      best = tmin;
+      pick = c;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(y);
+  cudaFree(z);
+  if (st != WPCD_OK) return st;
+  P->tuned[key] = pick;
+  store_cached(key, pick);
+  *out = pick;
+  return WPCD_OK;
+}
+
+namespace {
+
+// SpMM with the tuned shape (values: the P's own precision for FP64 T, FP32
+// values for FP32 T)
+template <typename T>
+wpcd_status spmm(const wpcd_problem *pr, const wpcd_P *P, const T *y, T *z, int B, cudaStream_t s) {
+  SpmmConfig cfg;
+  wpcd_status st = tune_spmm(pr, const_cast<wpcd_P *>(P), B, sizeof(T) == 4 ? 1 : 0, s, &cfg);
+  if (st != WPCD_OK) return st;
+  if (sizeof(T) == 4) {
+    const float *v32 = P->val32 ? P->val32 : P->val32_copy;
+    return launch_spmm_cfg<float, float>(pr, P, v32, (const float *)y, (float *)z, B, cfg, s);
+  }
+  if (P->prec == WPCD_FP64)
+    return launch_spmm_cfg<double, double>(pr, P, P->val64, (const double *)y, (double *)z, B, cfg, s);
+  return launch_spmm_cfg<float, double>(pr, P, P->val32, (const double *)y, (double *)z, B, cfg, s);
+}
+
+// out = O P0 Vt (g o x)  or  out = sub - O P0 Vt (g o x), batch of B energies
+template <typename T>
+wpcd_status kapply_ws(const wpcd_problem *pr, const wpcd_P *P, const T *g, const T *x, T *out,
+                      const T *sub, int B, Workspace<T> &ws, cudaStream_t s) {
   const int N = pr->N, M = pr->M, n_ch = pr->n_ch;
-  const int ncol = 2 * M;
-  dim3 grid((ncol + GB_N - 1) / GB_N, (N + GB_M - 1) / GB_M, n_ch);
+  const int64_t ncol = 2LL * M * B;
+  const T *Vt = sizeof(T) == 8 ? (const T *)(const void *)pr->d.Vt : (const T *)(const void *)pr->d.Vt32;
+  const T *O = sizeof(T) == 8 ? (const T *)(const void *)pr->d.O : (const T *)(const void *)pr->d.O32;
+  dim3 grid((unsigned)((ncol + GB_N - 1) / GB_N), (N + GB_M - 1) / GB_M, n_ch);
   if (g)
-    gemm_kernel<true, false><<<grid, G_THREADS, 0, s>>>(N, ncol, pr->d.Vt, x, g, nullptr, ws.y);
+    gemm_kernel<T, true, false><<<grid, G_THREADS, 0, s>>>(N, ncol, Vt, x, g, nullptr, ws.y);
   else
-    gemm_kernel<false, false><<<grid, G_THREADS, 0, s>>>(N, ncol, pr->d.Vt, x, nullptr, nullptr, ws.y);
+    gemm_kernel<T, false, false><<<grid, G_THREADS, 0, s>>>(N, ncol, Vt, x, nullptr, nullptr, ws.y);
   count_launches(1);
-  wpcd_status st = launch_spmv(pr, P, ws.y, ws.z, s);
+  wpcd_status st = spmm<T>(pr, P, ws.y, ws.z, B, s);
   if (st != WPCD_OK) return st;
   if (sub)
-    gemm_kernel<false, true><<<grid, G_THREADS, 0, s>>>(N, ncol, pr->d.O, ws.z, nullptr, sub, out);
+    gemm_kernel<T, false, true><<<grid, G_THREADS, 0, s>>>(N, ncol, O, ws.z, nullptr, sub, out);
   else
-    gemm_kernel<false, false><<<grid, G_THREADS, 0, s>>>(N, ncol, pr->d.O, ws.z, nullptr, nullptr, out);
+    gemm_kernel<T, false, false><<<grid, G_THREADS, 0, s>>>(N, ncol, O, ws.z, nullptr, nullptr, out);
   count_launches(1);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? WPCD_OK : cuda_error(e, "kapply launch");
@@ -516,7 +864,10 @@ wpcd_status onshell(const wpcd_problem *pr, double E, int *j0, double *Elo, doub
   int lo = 0, hi = pr->M - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) / 2;
-    if (qe[mid] <= q) lo = mid; else hi = mid - 1;
+    if (qe[mid] <= q)
+      lo = mid;
+    else
+      hi = mid - 1;
   }
   *j0 = lo;
   *Elo = pr->eps_b + 0.75 * qe[lo] * qe[lo];
@@ -525,8 +876,10 @@ wpcd_status onshell(const wpcd_problem *pr, double E, int *j0, double *Elo, doub
   return WPCD_OK;
 }
 
-wpcd_status resolvent(const wpcd_problem *pr, const double *E, int n_E, double *g, int *j0,
-                      double *D, cudaStream_t s) {
+namespace {
+
+wpcd_status resolvent_impl(const wpcd_problem *pr, const double *E, int n_E, double *g, int minor,
+                           int *j0, double *D, cudaStream_t s) {
   if (n_E < 0 || (n_E > 0 && (!E || !g))) return set_error(WPCD_EINVAL, "bad resolvent arguments");
   if (n_E == 0) return WPCD_OK;
   std::vector<double> lohi(2 * (size_t)n_E + 64);
@@ -550,6 +903,7 @@ wpcd_status resolvent(const wpcd_problem *pr, const double *E, int n_E, double *
   R.N = pr->N;
   R.M = pr->M;
   R.n_E = n_E;
+  R.minor = minor;
   R.qe = pr->d.qe;
   R.eps = pr->d.eps;
   R.Elo = d_lohi;
@@ -557,7 +911,8 @@ wpcd_status resolvent(const wpcd_problem *pr, const double *E, int n_E, double *
   R.gl_t = d_lohi + 2 * n_E;
   R.gl_w = d_lohi + 2 * n_E + 32;
   int64_t total = (int64_t)n_E * pr->n_ch * pr->N * pr->M;
-  resolvent_kernel<<<grid_for(total, 256, 152 * 16), 256, 0, s>>>(R, g); count_launches(1);
+  resolvent_kernel<<<grid_for(total, 256, 152 * 16), 256, 0, s>>>(R, g);
+  count_launches(1);
   cudaError_t e = cudaGetLastError();
   cudaFreeAsync(d_lohi, s);
   // the host staging buffer must outlive the copy
@@ -567,14 +922,20 @@ wpcd_status resolvent(const wpcd_problem *pr, const double *E, int n_E, double *
   return WPCD_OK;
 }
 
+}  // namespace
+
+wpcd_status resolvent(const wpcd_problem *pr, const double *E, int n_E, double *g, int *j0,
+                      double *D, cudaStream_t s) {
+  return resolvent_impl(pr, E, n_E, g, 0, j0, D, s);
+}
+
 wpcd_status kapply(const wpcd_problem *pr, const wpcd_P *P, const double *g, const double *x,
                    double *y, cudaStream_t s) {
   WPCD_CUDA_TRY(cudaSetDevice(pr->device));
   const size_t dim = (size_t)pr->n_ch * pr->N * pr->M;
-  Workspace ws;
-  WPCD_CUDA_TRY(cudaMalloc(&ws.y, 16 * dim));
-  WPCD_CUDA_TRY(cudaMalloc(&ws.z, 16 * dim));
-  wpcd_status st = kapply_ws(pr, P, g, x, y, nullptr, ws, s);
+  Workspace<double> ws;
+  WPCD_CUDA_TRY(ws.alloc(dim, 1));
+  wpcd_status st = kapply_ws<double>(pr, P, g, x, y, nullptr, 1, ws, s);
   if (st != WPCD_OK) return st;
   WPCD_CUDA_TRY(cudaStreamSynchronize(s));
   return WPCD_OK;
@@ -582,151 +943,411 @@ wpcd_status kapply(const wpcd_problem *pr, const wpcd_P *P, const double *g, con
 
 namespace {
 
-struct SolveBuffers {
-  double *g = nullptr;       // [dim] complex
-  double *V = nullptr;       // [(m+1)][dim] complex basis (or iterates)
-  double *w = nullptr;       // [dim] complex
-  double *u = nullptr;       // [dim] complex solution
-  double2 *small = nullptr;  // Krylov scalars
-  double2 *partial = nullptr;
-  double *resid = nullptr;
-  int *flag = nullptr;
-  double *amp = nullptr;
-  ~SolveBuffers() {
-    cudaFree(g); cudaFree(V); cudaFree(w); cudaFree(u); cudaFree(small); cudaFree(partial);
-    cudaFree(resid); cudaFree(flag); cudaFree(amp);
+// Krylov basis and least-squares state for a batch of B energies
+template <typename T>
+struct Krylov {
+  int m = 0, B = 0;
+  size_t dim = 0;
+  T *V = nullptr;  // [(m+1)][dim][B] complex
+  T *w = nullptr;  // [dim][B] complex
+  double2 *H = nullptr, *cs = nullptr, *sn = nullptr, *bet = nullptr;
+  double2 *h = nullptr, *h2 = nullptr, *nrm = nullptr, *y = nullptr, *partial = nullptr;
+  double *resid = nullptr, *bnorm = nullptr;
+  int nblk = 0;
+  ~Krylov() {
+    cudaFree(V); cudaFree(w); cudaFree(H); cudaFree(cs); cudaFree(sn); cudaFree(bet); cudaFree(h);
+    cudaFree(h2); cudaFree(nrm); cudaFree(y); cudaFree(partial); cudaFree(resid); cudaFree(bnorm);
+  }
+  cudaError_t alloc(int m_, int B_, size_t dim_, bool vectors = true) {
+    m = m_;
+    B = B_;
+    dim = dim_;
+    nblk = 152 * 2;
+    cudaError_t e;
+    if (vectors) {
+      if ((e = cudaMalloc(&V, 2 * sizeof(T) * dim * B * (m + 1))) != cudaSuccess) return e;
+      if ((e = cudaMalloc(&w, 2 * sizeof(T) * dim * B)) != cudaSuccess) return e;
+    }
+    if ((e = cudaMalloc(&H, sizeof(double2) * (size_t)B * (m + 1) * m)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&cs, sizeof(double2) * (size_t)B * m)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&sn, sizeof(double2) * (size_t)B * m)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&bet, sizeof(double2) * (size_t)B * (m + 1))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&h, sizeof(double2) * (size_t)B * (m + 1))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&h2, sizeof(double2) * (size_t)B * (m + 1))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&nrm, sizeof(double2) * (size_t)B)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&y, sizeof(double2) * (size_t)B * m)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&partial, sizeof(double2) * (size_t)B * (m + 1) * nblk)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&resid, sizeof(double) * B)) != cudaSuccess) return e;
+    return cudaMalloc(&bnorm, sizeof(double) * B);
+  }
+  using C2 = typename Cx<T>::t;
+  C2 *vec(int j) { return reinterpret_cast<C2 *>(V) + (size_t)j * dim * B; }
+  C2 *wv() { return reinterpret_cast<C2 *>(w); }
+  dim3 dot_block() const {
+    int el = 1;
+    while (el < B && el < 32) el *= 2;
+    return dim3(el, V_THREADS / el);
+  }
+  dim3 dot_grid() const {
+    dim3 b = dot_block();
+    return dim3(nblk, (B + b.x - 1) / b.x);
+  }
+  // out[j * B + e] = <V_j, x>, j < nv
+  template <typename U>
+  void dots(int nv, const typename Cx<U>::t *base, size_t ld, const typename Cx<U>::t *x, double2 *out,
+            int accumulate, cudaStream_t s) {
+    bdot_kernel<U><<<dot_grid(), dot_block(), 0, s>>>((int)dim, B, nv, base, ld, x, partial);
+    breduce_kernel<<<(nv * B + 255) / 256, 256, 0, s>>>(nv, nblk, B, partial, out, accumulate);
+    count_launches(2);
+  }
+  template <typename U>
+  void norms(const typename Cx<U>::t *x, cudaStream_t s) {
+    dots<U>(1, x, 0, x, nrm, 0, s);
+  }
+  // one Arnoldi step from column k (w holds (I - K) v_k on entry)
+  void step(int k, cudaStream_t s) {
+    const int64_t n = (int64_t)dim * B;
+    const size_t ld = dim * B;
+    const int vg = grid_for(n, 256);
+    dots<T>(k + 1, vec(0), ld, wv(), h, 0, s);
+    baxpy_kernel<T><<<vg, 256, 0, s>>>(n, B, k + 1, vec(0), ld, h, wv(), -1.0);
+    dots<T>(k + 1, vec(0), ld, wv(), h2, 0, s);
+    baxpy_kernel<T><<<vg, 256, 0, s>>>(n, B, k + 1, vec(0), ld, h2, wv(), -1.0);
+    breduce_kernel<<<((k + 1) * B + 255) / 256, 256, 0, s>>>(k + 1, nblk, B, partial, h, 1);  // h += h2
+    norms<T>(wv(), s);
+    bscale_kernel<T><<<vg, 256, 0, s>>>(n, B, wv(), nrm, vec(k + 1));
+    bgivens_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, m, k, h, nrm, H, cs, sn, bet, resid, bnorm);
+    count_launches(5);
   }
 };
 
-// Krylov solve of (I - K) u = b with u0 = 0; b = Born term.  Returns U00 etc.
-wpcd_status solve_krylov(const wpcd_problem *pr, const wpcd_P *P, double E, const wpcd_solve_opts &o,
-                         SolveBuffers &B, Workspace &ws, wpcd_solve_stats &out, cudaStream_t s) {
-  const int dim = pr->n_ch * pr->N * pr->M;
-  const int m = o.max_iter;
-  int j0;
-  double Elo, Ehi, q0;
-  wpcd_status st = onshell(pr, E, &j0, &Elo, &Ehi, &q0);
-  if (st != WPCD_OK) return st;
-  double D = Ehi - Elo;
-  st = resolvent(pr, &E, 1, B.g, nullptr, nullptr, s);
-  if (st != WPCD_OK) return st;
-  const int r0 = j0;
-  double2 *V = reinterpret_cast<double2 *>(B.V);
-  double2 *w = reinterpret_cast<double2 *>(B.w);
-  const size_t ld = (size_t)dim;
-  double2 *H = B.small;                       // (m+1) * m
-  double2 *cs = H + (size_t)(m + 1) * m;
-  double2 *sn = cs + m;
-  double2 *bet = sn + m;                      // m + 1
-  double2 *h = bet + (m + 1);                 // m + 1
-  double2 *h2 = h + (m + 1);                  // m + 1
-  double2 *nrm = h2 + (m + 1);                // 1
-  double2 *yv = nrm + 1;                      // m
-  const int nblk = 152 * 2;
-  const int vgrid = grid_for(dim, 256, 152 * 8);
-  cudaEvent_t e0, e1;
-  WPCD_CUDA_TRY(cudaEventCreate(&e0));
-  WPCD_CUDA_TRY(cudaEventCreate(&e1));
-  cudaEventRecord(e0, s);
-  // b = O P0 Vt e0  (into w), then v0 = b / |b|
-  set_unit_kernel<<<vgrid, 256, 0, s>>>(dim, r0, reinterpret_cast<double2 *>(B.u)); count_launches(1);
-  st = kapply_ws(pr, P, nullptr, B.u, B.w, nullptr, ws, s);
-  if (st != WPCD_OK) return st;
-  multi_dot_kernel<<<nblk, V_THREADS, 0, s>>>(dim, 1, w, ld, w, B.partial); count_launches(1);
-  reduce_partials_kernel<<<1, 256, 0, s>>>(1, nblk, B.partial, nrm, 0); count_launches(1);
-  scale_kernel<<<vgrid, 256, 0, s>>>(dim, w, nrm, V); count_launches(1);
-  double2 nrm_h;
-  WPCD_CUDA_TRY(cudaMemcpyAsync(&nrm_h, nrm, sizeof(double2), cudaMemcpyDeviceToHost, s));
-  WPCD_CUDA_TRY(cudaMemsetAsync(B.small, 0, sizeof(double2) * ((size_t)(m + 1) * m + 5 * (m + 1) + 2), s));
-  WPCD_CUDA_TRY(cudaStreamSynchronize(s));
-  double bnorm = std::sqrt(nrm_h.x);
-  if (!(bnorm > 0.0)) return set_error(WPCD_EBREAKDOWN, "Born term is zero");
-  double2 bet0 = make_double2(bnorm, 0.0);
-  WPCD_CUDA_TRY(cudaMemcpyAsync(bet, &bet0, sizeof(double2), cudaMemcpyHostToDevice, s));
-  int k = 0, status = WPCD_ENOCONV;
-  double resid = 1.0;
-  for (k = 0; k < m; ++k) {
-    // w = (I - K) v_k = v_k - O P0 Vt G1 v_k
-    st = kapply_ws(pr, P, B.g, reinterpret_cast<double *>(V + (size_t)k * ld), B.w,
-                   reinterpret_cast<double *>(V + (size_t)k * ld), ws, s);
+struct SolveCtx {
+  int B = 0;
+  size_t dim = 0;
+  double *g = nullptr;  // [dim][B] complex FP64 resolvent
+  float *g32 = nullptr; // FP32 copy (mixed)
+  double *b = nullptr, *u = nullptr, *r = nullptr, *t = nullptr;  // FP64 [dim][B] complex
+  int *r0 = nullptr;    // [B]
+  double *Dd = nullptr, *pref = nullptr, *amp = nullptr;
+  ~SolveCtx() {
+    cudaFree(g); cudaFree(g32); cudaFree(b); cudaFree(u); cudaFree(r); cudaFree(t); cudaFree(r0);
+    cudaFree(Dd); cudaFree(pref); cudaFree(amp);
+  }
+};
+
+struct BatchInfo {
+  std::vector<int> j0;
+  std::vector<double> D, pref;
+};
+
+wpcd_status batch_setup(const wpcd_problem *pr, const double *E, int B, SolveCtx &cx, BatchInfo &bi,
+                        bool need32, cudaStream_t s) {
+  const size_t dim = (size_t)pr->n_ch * pr->N * pr->M;
+  bi.j0.assign(B, 0);
+  bi.D.assign(B, 0.0);
+  bi.pref.assign(B, 0.0);
+  for (int e = 0; e < B; ++e) {
+    double lo, hi, q0;
+    wpcd_status st = onshell(pr, E[e], &bi.j0[e], &lo, &hi, &q0);
     if (st != WPCD_OK) return st;
-    // two-pass classical Gram-Schmidt
-    multi_dot_kernel<<<nblk, V_THREADS, 0, s>>>(dim, k + 1, V, ld, w, B.partial); count_launches(1);
-    reduce_partials_kernel<<<k + 1, 256, 0, s>>>(k + 1, nblk, B.partial, h, 0); count_launches(1);
-    multi_axpy_kernel<<<vgrid, 256, 0, s>>>(dim, k + 1, V, ld, h, w, -1.0); count_launches(1);
-    multi_dot_kernel<<<nblk, V_THREADS, 0, s>>>(dim, k + 1, V, ld, w, B.partial); count_launches(1);
-    reduce_partials_kernel<<<k + 1, 256, 0, s>>>(k + 1, nblk, B.partial, h2, 0); count_launches(1);
-    multi_axpy_kernel<<<vgrid, 256, 0, s>>>(dim, k + 1, V, ld, h2, w, -1.0); count_launches(1);
-    reduce_partials_kernel<<<k + 1, 256, 0, s>>>(k + 1, nblk, B.partial, h, 1);  // h += h2
-    multi_dot_kernel<<<nblk, V_THREADS, 0, s>>>(dim, 1, w, ld, w, B.partial); count_launches(1);
-    reduce_partials_kernel<<<1, 256, 0, s>>>(1, nblk, B.partial, nrm, 0); count_launches(1);
-    scale_kernel<<<vgrid, 256, 0, s>>>(dim, w, nrm, V + (size_t)(k + 1) * ld); count_launches(1);
-    givens_kernel<<<1, 1, 0, s>>>(m, k, h, nrm, H, cs, sn, bet, B.resid, bnorm); count_launches(1);
-    cudaError_t ce = cudaGetLastError();
-    if (ce != cudaSuccess) return cuda_error(ce, "krylov step launch");
-    bool check = ((k + 1) % (o.check_every > 0 ? o.check_every : 1) == 0) || k + 1 == m;
-    if (check) {
-      WPCD_CUDA_TRY(cudaMemcpyAsync(&resid, B.resid, sizeof(double), cudaMemcpyDeviceToHost, s));
-      WPCD_CUDA_TRY(cudaStreamSynchronize(s));
-      if (!std::isfinite(resid)) { status = WPCD_EBREAKDOWN; ++k; break; }
-      if (resid <= o.tol) { status = WPCD_OK; ++k; break; }
-    }
+    bi.D[e] = hi - lo;
+    bi.pref[e] = 2.0 / (3.0 * q0) / (pr->qe[bi.j0[e] + 1] - pr->qe[bi.j0[e]]);
   }
-  if (k > m) k = m;
-  // u = V y
-  backsub_kernel<<<1, 1, 0, s>>>(m, k, H, bet, yv); count_launches(1);
-  WPCD_CUDA_TRY(cudaMemsetAsync(B.u, 0, 16 * (size_t)dim, s));
-  multi_axpy_kernel<<<vgrid, 256, 0, s>>>(dim, k, V, ld, yv, reinterpret_cast<double2 *>(B.u), 1.0); count_launches(1);
-  double pref = 2.0 / (3.0 * q0) / (pr->qe[j0 + 1] - pr->qe[j0]);
-  amplitude_kernel<<<1, 1, 0, s>>>(reinterpret_cast<double2 *>(B.u), r0, D, pref, B.amp); count_launches(1);
-  cudaEventRecord(e1, s);
-  double amp[6];
-  WPCD_CUDA_TRY(cudaMemcpyAsync(amp, B.amp, sizeof(amp), cudaMemcpyDeviceToHost, s));
-  WPCD_CUDA_TRY(cudaMemcpyAsync(&resid, B.resid, sizeof(double), cudaMemcpyDeviceToHost, s));
-  WPCD_CUDA_TRY(cudaStreamSynchronize(s));
-  cudaEventElapsedTime(&out.ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  out.status = status;
-  out.n_kapply = k + 1;  // including the Born term
-  out.j0 = j0;
-  out.D = D;
-  out.relres = resid;
-  for (int i = 0; i < 2; ++i) {
-    out.U00[i] = amp[i];
-    out.S[i] = amp[2 + i];
-    out.A[i] = amp[4 + i];
+  wpcd_status st = resolvent_impl(pr, E, B, cx.g, 1, nullptr, nullptr, s);
+  if (st != WPCD_OK) return st;
+  if (need32) {
+    d2f_kernel<<<grid_for(2 * (int64_t)dim * B, 256), 256, 0, s>>>(2 * (int64_t)dim * B, cx.g, cx.g32);
+    count_launches(1);
   }
+  // e0 = channel 0, k = 0 (the dimer), q-bin j0: vector index j0
+  WPCD_CUDA_TRY(cudaMemcpyAsync(cx.r0, bi.j0.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
+  WPCD_CUDA_TRY(cudaMemcpyAsync(cx.Dd, bi.D.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
+  WPCD_CUDA_TRY(cudaMemcpyAsync(cx.pref, bi.pref.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
   return WPCD_OK;
 }
 
-// Paper's route: iterate x_{n+1} = K x_n from the Born term, collect
-// c_n = x_n[r0], Wynn epsilon on the device.  Stops on two successive
-// estimates within tol (relative), else returns the best (least changing)
-// estimate with ENOCONV.
+// Born term b = O P0 Vt e0 for every energy of the batch (FP64)
+wpcd_status born(const wpcd_problem *pr, const wpcd_P *P, SolveCtx &cx, Workspace<double> &ws, cudaStream_t s) {
+  const int64_t n = (int64_t)cx.dim * cx.B;
+  bunits_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, cx.B, cx.r0, reinterpret_cast<double2 *>(cx.t));
+  count_launches(1);
+  return kapply_ws<double>(pr, P, nullptr, cx.t, cx.b, nullptr, cx.B, ws, s);
+}
+
+// Plain FP64 Krylov on (I - K) u = b, started from u (0 or a warm start)
+wpcd_status solve_fp64(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solve_opts &o, SolveCtx &cx,
+                       Krylov<double> &kr, Workspace<double> &ws, std::vector<int> &status,
+                       std::vector<double> &relres, int &n_apply, bool warm, cudaStream_t s) {
+  const int B = cx.B, m = kr.m;
+  const int64_t n = (int64_t)cx.dim * B;
+  const int vg = grid_for(n, 256);
+  n_apply = 0;
+  if (warm) {  // r = b - (I - K) u
+    wpcd_status st = kapply_ws<double>(pr, P, cx.g, cx.u, cx.t, nullptr, B, ws, s);
+    if (st != WPCD_OK) return st;
+    ++n_apply;
+    bresid_kernel<<<vg, 256, 0, s>>>(n, (double2 *)cx.b, (double2 *)cx.u, (double2 *)cx.t, (double2 *)cx.r);
+    count_launches(1);
+  } else {
+    WPCD_CUDA_TRY(cudaMemcpyAsync(cx.r, cx.b, 16 * n, cudaMemcpyDeviceToDevice, s));
+    WPCD_CUDA_TRY(cudaMemsetAsync(cx.u, 0, 16 * n, s));
+  }
+  // |b| is the reference of the relative residual
+  kr.norms<double>((const double2 *)cx.b, s);
+  std::vector<double2> nb(B), nr(B);
+  WPCD_CUDA_TRY(cudaMemcpyAsync(nb.data(), kr.nrm, sizeof(double2) * B, cudaMemcpyDeviceToHost, s));
+  kr.norms<double>((const double2 *)cx.r, s);
+  WPCD_CUDA_TRY(cudaMemcpyAsync(nr.data(), kr.nrm, sizeof(double2) * B, cudaMemcpyDeviceToHost, s));
+  WPCD_CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<double> bn(B);
+  std::vector<double2> bet0((size_t)B * (m + 1), make_double2(0.0, 0.0));
+  for (int e = 0; e < B; ++e) {
+    bn[e] = std::sqrt(nb[e].x);
+    if (!(bn[e] > 0.0)) return set_error(WPCD_EBREAKDOWN, "Born term is zero");
+    bet0[(size_t)e * (m + 1)] = make_double2(std::sqrt(nr[e].x), 0.0);
+  }
+  // v0 = r / |r| ; bet = |r| e1
+  bscale_kernel<double><<<vg, 256, 0, s>>>(n, B, (const double2 *)cx.r, kr.nrm, kr.vec(0));
+  count_launches(1);
+  WPCD_CUDA_TRY(cudaMemsetAsync(kr.H, 0, sizeof(double2) * (size_t)B * (m + 1) * m, s));
+  WPCD_CUDA_TRY(cudaMemcpyAsync(kr.bet, bet0.data(), sizeof(double2) * bet0.size(), cudaMemcpyHostToDevice, s));
+  WPCD_CUDA_TRY(cudaMemcpyAsync(kr.bnorm, bn.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
+  status.assign(B, WPCD_ENOCONV);
+  relres.assign(B, 1.0);
+  std::vector<double> res(B);
+  for (int e = 0; e < B; ++e) relres[e] = std::sqrt(nr[e].x) / bn[e];
+  int k = 0;
+  bool done = true;
+  for (int e = 0; e < B; ++e)
+    if (relres[e] > o.tol) done = false;
+  for (k = 0; k < m && !done; ++k) {
+    // w = (I - K) v_k
+    wpcd_status st = kapply_ws<double>(pr, P, cx.g, (double *)kr.vec(k), kr.w, (double *)kr.vec(k), B, ws, s);
+    if (st != WPCD_OK) return st;
+    ++n_apply;
+    kr.step(k, s);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) return cuda_error(ce, "krylov step launch");
+    bool check = ((k + 1) % std::max(o.check_every, 1) == 0) || k + 1 == m;
+    if (check) {
+      WPCD_CUDA_TRY(cudaMemcpyAsync(res.data(), kr.resid, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+      WPCD_CUDA_TRY(cudaStreamSynchronize(s));
+      done = true;
+      for (int e = 0; e < B; ++e) {
+        relres[e] = res[e];
+        if (!std::isfinite(res[e]))
+          status[e] = WPCD_EBREAKDOWN;
+        else if (res[e] <= o.tol)
+          status[e] = WPCD_OK;
+        else
+          done = false;
+      }
+    }
+  }
+  if (k == 0)
+    for (int e = 0; e < B; ++e) status[e] = WPCD_OK;  // the start already met the tolerance
+  bbacksub_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, m, k, kr.H, kr.bet, kr.y);
+  bupdate_kernel<double><<<vg, 256, 0, s>>>(n, B, k, kr.vec(0), cx.dim * B, kr.y, nullptr, (double2 *)cx.u);
+  count_launches(2);
+  return WPCD_OK;
+}
+
+// Mixed precision: FP64 refinement around FP32 inner Krylov cycles
+wpcd_status solve_mixed(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solve_opts &o, SolveCtx &cx,
+                        Krylov<float> &kr, Krylov<double> &k64, Workspace<double> &ws64,
+                        Workspace<float> &ws32, std::vector<int> &status, std::vector<double> &relres,
+                        int &n64, int &n32, int &n_outer, bool warm, cudaStream_t s) {
+  const int B = cx.B, m = kr.m;
+  const int64_t n = (int64_t)cx.dim * B;
+  const int vg = grid_for(n, 256);
+  n64 = n32 = n_outer = 0;
+  if (!warm) WPCD_CUDA_TRY(cudaMemsetAsync(cx.u, 0, 16 * n, s));
+  // |b|
+  k64.norms<double>((const double2 *)cx.b, s);
+  std::vector<double2> nb(B);
+  WPCD_CUDA_TRY(cudaMemcpyAsync(nb.data(), k64.nrm, sizeof(double2) * B, cudaMemcpyDeviceToHost, s));
+  WPCD_CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<double> bn(B);
+  for (int e = 0; e < B; ++e) {
+    bn[e] = std::sqrt(nb[e].x);
+    if (!(bn[e] > 0.0)) return set_error(WPCD_EBREAKDOWN, "Born term is zero");
+  }
+  // inner right-hand sides are normalised: bet = e1, reference norm 1
+  std::vector<double> ones(B, 1.0);
+  std::vector<double2> bet0((size_t)B * (m + 1), make_double2(0.0, 0.0));
+  for (int e = 0; e < B; ++e) bet0[(size_t)e * (m + 1)] = make_double2(1.0, 0.0);
+  double2 *d_bet0 = nullptr;
+  WPCD_CUDA_TRY(cudaMalloc(&d_bet0, sizeof(double2) * bet0.size()));
+  WPCD_CUDA_TRY(cudaMemcpyAsync(kr.bnorm, ones.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
+  WPCD_CUDA_TRY(cudaMemcpyAsync(d_bet0, bet0.data(), sizeof(double2) * bet0.size(), cudaMemcpyHostToDevice, s));
+  WPCD_CUDA_TRY(cudaStreamSynchronize(s));  // host staging vectors
+
+  // the inner cycle: fixed sizes and pointers, so it can be captured once
+  // and replayed as a CUDA graph
+  auto inner_cycle = [&]() -> wpcd_status {
+    cudaMemsetAsync(kr.H, 0, sizeof(double2) * (size_t)B * (m + 1) * m, s);
+    cudaMemcpyAsync(kr.bet, d_bet0, sizeof(double2) * bet0.size(), cudaMemcpyDeviceToDevice, s);
+    for (int k = 0; k < m; ++k) {
+      wpcd_status st = kapply_ws<float>(pr, P, cx.g32, (float *)kr.vec(k), kr.w, (float *)kr.vec(k), B, ws32, s);
+      if (st != WPCD_OK) return st;
+      kr.step(k, s);
+    }
+    bbacksub_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, m, m, kr.H, kr.bet, kr.y);
+    // u += |r| (V y)   (FP64 accumulation of the FP32 correction)
+    bupdate_kernel<float><<<vg, 256, 0, s>>>(n, B, m, kr.vec(0), cx.dim * B, kr.y, k64.nrm, (double2 *)cx.u);
+    count_launches(2);
+    return WPCD_OK;
+  };
+  // the SpMM shapes are tuned before any capture (tuning synchronises)
+  {
+    SpmmConfig c;
+    wpcd_status st = tune_spmm(pr, const_cast<wpcd_P *>(P), B, 1, s, &c);
+    if (st == WPCD_OK) st = tune_spmm(pr, const_cast<wpcd_P *>(P), B, 0, s, &c);
+    if (st != WPCD_OK) {
+      cudaFree(d_bet0);
+      return st;
+    }
+  }
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches0 = 0;
+  int graph_kernels = 0;
+  status.assign(B, WPCD_ENOCONV);
+  relres.assign(B, 1.0);
+  std::vector<double2> nr(B);
+  const int max_outer = o.max_outer > 0 ? o.max_outer : 12;
+  wpcd_status result = WPCD_OK;
+  for (int outer = 0; outer <= max_outer; ++outer) {
+    // r = b - (I - K) u in FP64
+    if (outer > 0 || warm) {
+      wpcd_status st = kapply_ws<double>(pr, P, cx.g, cx.u, cx.t, nullptr, B, ws64, s);
+      if (st != WPCD_OK) {
+        result = st;
+        break;
+      }
+      ++n64;
+      bresid_kernel<<<vg, 256, 0, s>>>(n, (double2 *)cx.b, (double2 *)cx.u, (double2 *)cx.t, (double2 *)cx.r);
+      count_launches(1);
+    } else {
+      cudaMemcpyAsync(cx.r, cx.b, 16 * n, cudaMemcpyDeviceToDevice, s);
+    }
+    k64.norms<double>((const double2 *)cx.r, s);
+    cudaMemcpyAsync(nr.data(), k64.nrm, sizeof(double2) * B, cudaMemcpyDeviceToHost, s);
+    cudaError_t ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) {
+      result = cuda_error(ce, "refinement residual");
+      break;
+    }
+    bool done = true;
+    for (int e = 0; e < B; ++e) {
+      relres[e] = std::sqrt(nr[e].x) / bn[e];
+      if (!std::isfinite(relres[e])) {
+        status[e] = WPCD_EBREAKDOWN;
+      } else if (relres[e] <= o.tol) {
+        status[e] = WPCD_OK;
+      } else {
+        status[e] = WPCD_ENOCONV;
+        done = false;
+      }
+    }
+    if (done || outer == max_outer) break;
+    ++n_outer;
+    // v0 = (float)(r / |r|)
+    bnormalize_f32_kernel<<<vg, 256, 0, s>>>(n, B, (const double2 *)cx.r, k64.nrm, kr.vec(0));
+    count_launches(1);
+    if (o.use_graph && s != nullptr) {  // the legacy default stream cannot be captured
+      if (!exec) {
+        cudaGraph_t graph;
+        launches0 = wpcd_launch_count();
+        ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (ce != cudaSuccess) {
+          result = cuda_error(ce, "begin capture");
+          break;
+        }
+        wpcd_status st = inner_cycle();
+        ce = cudaStreamEndCapture(s, &graph);
+        if (st != WPCD_OK) {
+          result = st;
+          break;
+        }
+        if (ce != cudaSuccess) {
+          result = cuda_error(ce, "end capture");
+          break;
+        }
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+          result = cuda_error(ce, "graph instantiate");
+          break;
+        }
+        // captured kernels run at each replay, not at capture
+        graph_kernels = (int)(wpcd_launch_count() - launches0);
+        count_launches(-graph_kernels);
+      }
+      ce = cudaGraphLaunch(exec, s);
+      if (ce != cudaSuccess) {
+        result = cuda_error(ce, "graph launch");
+        break;
+      }
+      count_launches(graph_kernels);
+    } else {
+      wpcd_status st = inner_cycle();
+      if (st != WPCD_OK) {
+        result = st;
+        break;
+      }
+    }
+    n32 += m;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  cudaFree(d_bet0);
+  return result;
+}
+
+// Paper's route, one energy: x_{n+1} = K x_n from the Born term, c_n =
+// x_n[r0], Wynn epsilon on the device.
 wpcd_status solve_wynn(const wpcd_problem *pr, const wpcd_P *P, double E, const wpcd_solve_opts &o,
-                       SolveBuffers &B, Workspace &ws, wpcd_solve_stats &out, cudaStream_t s) {
-  const int dim = pr->n_ch * pr->N * pr->M;
+                       wpcd_solve_stats &out, cudaStream_t s) {
+  const size_t dim = (size_t)pr->n_ch * pr->N * pr->M;
   const int m = o.max_iter;
   int j0;
   double Elo, Ehi, q0;
   wpcd_status st = onshell(pr, E, &j0, &Elo, &Ehi, &q0);
   if (st != WPCD_OK) return st;
   double D = Ehi - Elo;
-  st = resolvent(pr, &E, 1, B.g, nullptr, nullptr, s);
+  Workspace<double> ws;
+  WPCD_CUDA_TRY(ws.alloc(dim, 1));
+  struct Free {
+    std::vector<void *> p;
+    ~Free() {
+      for (void *q : p) cudaFree(q);
+    }
+  } fr;
+  double *g = nullptr, *x0d = nullptr, *x1d = nullptr;
+  double2 *small = nullptr;
+  int *flag = nullptr;
+  WPCD_CUDA_TRY(cudaMalloc(&g, 16 * dim));
+  fr.p.push_back(g);
+  WPCD_CUDA_TRY(cudaMalloc(&x0d, 16 * dim));
+  fr.p.push_back(x0d);
+  WPCD_CUDA_TRY(cudaMalloc(&x1d, 16 * dim));
+  fr.p.push_back(x1d);
+  WPCD_CUDA_TRY(cudaMalloc(&small, sizeof(double2) * (5 * (size_t)m + 8)));
+  fr.p.push_back(small);
+  WPCD_CUDA_TRY(cudaMalloc(&flag, 2 * sizeof(int)));
+  fr.p.push_back(flag);
+  st = resolvent_impl(pr, &E, 1, g, 1, nullptr, nullptr, s);
   if (st != WPCD_OK) return st;
-  const int r0 = j0;
-  double2 *c = B.small;              // m
-  double2 *est = c + m;              // m
-  double2 *work = est + m;           // 3 (m + 1)
-  double2 *x0 = reinterpret_cast<double2 *>(B.u), *x1 = reinterpret_cast<double2 *>(B.w);
-  const int vgrid = grid_for(dim, 256, 152 * 8);
+  double2 *c = small, *est = c + m, *work = est + m;  // work: 3 (m + 1)
+  double2 *x0 = reinterpret_cast<double2 *>(x0d), *x1 = reinterpret_cast<double2 *>(x1d);
+  int *r0d = flag + 1;
   cudaEvent_t e0, e1;
   WPCD_CUDA_TRY(cudaEventCreate(&e0));
   WPCD_CUDA_TRY(cudaEventCreate(&e1));
   cudaEventRecord(e0, s);
-  set_unit_kernel<<<vgrid, 256, 0, s>>>(dim, r0, x1); count_launches(1);
-  st = kapply_ws(pr, P, nullptr, B.w, B.u, nullptr, ws, s);  // x0 = Born
+  WPCD_CUDA_TRY(cudaMemcpyAsync(r0d, &j0, sizeof(int), cudaMemcpyHostToDevice, s));
+  bunits_kernel<<<grid_for((int64_t)dim, 256), 256, 0, s>>>((int64_t)dim, 1, r0d, x1);
+  count_launches(1);
+  st = kapply_ws<double>(pr, P, nullptr, x1d, x0d, nullptr, 1, ws, s);  // x0 = Born
   if (st != WPCD_OK) return st;
   std::vector<double2> est_h(m);
   int n = 0, status = WPCD_ENOCONV, bd = 0, checked = 0, used = 0;
@@ -735,37 +1356,39 @@ wpcd_status solve_wynn(const wpcd_problem *pr, const wpcd_P *P, double E, const 
   int best_n = 0;
   const int every = o.check_every > 0 ? o.check_every : 1;
   for (n = 0; n < m; ++n) {
-    extract_kernel<<<1, 1, 0, s>>>(x0, r0, c + n); count_launches(1);
-    wynn_kernel<<<1, 1, 0, s>>>(n + 1, c, work, est, B.flag); count_launches(1);
+    extract_kernel<<<1, 1, 0, s>>>(x0, j0, c + n);
+    wynn_kernel<<<1, 1, 0, s>>>(n + 1, c, work, est, flag);
+    count_launches(2);
     if (n + 1 < m) {
-      st = kapply_ws(pr, P, B.g, reinterpret_cast<double *>(x0), reinterpret_cast<double *>(x1), nullptr, ws, s);
+      st = kapply_ws<double>(pr, P, g, reinterpret_cast<double *>(x0), reinterpret_cast<double *>(x1), nullptr, 1,
+                             ws, s);
       if (st != WPCD_OK) return st;
       std::swap(x0, x1);
     }
     if ((n + 1) % every != 0 && n + 1 != m) continue;
     WPCD_CUDA_TRY(cudaMemcpyAsync(est_h.data(), est, sizeof(double2) * (n + 1), cudaMemcpyDeviceToHost, s));
-    WPCD_CUDA_TRY(cudaMemcpyAsync(&bd, B.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    WPCD_CUDA_TRY(cudaMemcpyAsync(&bd, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     WPCD_CUDA_TRY(cudaStreamSynchronize(s));
     bool done = false;
     for (int t = checked; t <= n; ++t) {
-      double2 e = est_h[t];
+      double2 ev = est_h[t];
       used = t + 1;
       if (t > 0) {
         double2 p = est_h[t - 1];
-        double d = std::hypot(e.x - p.x, e.y - p.y) / std::hypot(e.x, e.y);
+        double d = std::hypot(ev.x - p.x, ev.y - p.y) / std::hypot(ev.x, ev.y);
         if (t + 1 >= o.min_iter && d <= o.tol) {
-          best = e;
+          best = ev;
           status = WPCD_OK;
           done = true;
           break;
         }
         if (d < best_d) {
           best_d = d;
-          best = e;
+          best = ev;
           best_n = t + 1;
         }
       }
-      last = e;
+      last = ev;
     }
     checked = n + 1;
     if (done) break;
@@ -782,6 +1405,8 @@ wpcd_status solve_wynn(const wpcd_problem *pr, const wpcd_P *P, double E, const 
   if (status != WPCD_OK && best_n == 0) best = last;
   out.status = status;
   out.n_kapply = (status == WPCD_OK) ? used : (best_n > 0 ? best_n : used);
+  out.n_kapply32 = 0;
+  out.n_outer = 0;
   out.j0 = j0;
   out.D = D;
   out.relres = status == WPCD_OK ? 0.0 : best_d;
@@ -797,13 +1422,29 @@ wpcd_status solve_wynn(const wpcd_problem *pr, const wpcd_P *P, double E, const 
 
 }  // namespace
 
-wpcd_status solve(wpcd_problem *pr, const wpcd_P *P, const double *E, int n_E,
+wpcd_status solve(wpcd_problem *pr, const wpcd_P *Pc, const double *E, int n_E,
                   const wpcd_solve_opts *o, double *U00, wpcd_solve_stats *st_out, cudaStream_t s) {
-  wpcd_solve_opts opt{WPCD_SUM_KRYLOV, 100, 4, 1e-10, 4};
+  wpcd_solve_opts opt{};
+  opt.method = WPCD_SUM_KRYLOV;
+  opt.max_iter = 100;
+  opt.min_iter = 4;
+  opt.tol = 1e-10;
+  opt.check_every = 4;
+  opt.precision = WPCD_SOLVE_FP64;
+  opt.use_graph = 1;
   if (o) opt = *o;
+  wpcd_P *P = const_cast<wpcd_P *>(Pc);
   if (opt.max_iter < 2 || opt.max_iter > 512) return set_error(WPCD_EINVAL, "max_iter must be in [2, 512]");
   if (!(opt.tol > 0.0)) return set_error(WPCD_EINVAL, "tol must be positive");
   if (opt.method != WPCD_SUM_KRYLOV && opt.method != WPCD_SUM_WYNN) return set_error(WPCD_EINVAL, "unknown method");
+  if (opt.precision != WPCD_SOLVE_FP64 && opt.precision != WPCD_SOLVE_MIXED)
+    return set_error(WPCD_EINVAL, "unknown precision");
+  if (opt.method == WPCD_SUM_WYNN && opt.precision != WPCD_SOLVE_FP64)
+    return set_error(WPCD_EINVAL, "the Wynn summation runs in FP64 only");
+  if (opt.method == WPCD_SUM_WYNN && (opt.u_init || opt.u_out))
+    return set_error(WPCD_EINVAL, "the Wynn summation takes no vectors");
+  if (opt.batch < 0 || opt.batch > 1024) return set_error(WPCD_EINVAL, "batch must be in [0, 1024]");
+  if (opt.inner_iter < 0 || opt.inner_iter > 128) return set_error(WPCD_EINVAL, "inner_iter must be in [0, 128]");
   if (n_E < 0 || (n_E > 0 && (!E || !U00))) return set_error(WPCD_EINVAL, "bad energies / output");
   for (int e = 0; e < n_E; ++e) {
     int j0;
@@ -812,32 +1453,119 @@ wpcd_status solve(wpcd_problem *pr, const wpcd_P *P, const double *E, int n_E,
     if (st != WPCD_OK) return st;
   }
   WPCD_CUDA_TRY(cudaSetDevice(pr->device));
-  const size_t dim = (size_t)pr->n_ch * pr->N * pr->M;
-  const int m = opt.max_iter;
-  SolveBuffers B;
-  Workspace ws;
-  const size_t nvec = opt.method == WPCD_SUM_KRYLOV ? (size_t)m + 1 : 1;
-  WPCD_CUDA_TRY(cudaMalloc(&ws.y, 16 * dim));
-  WPCD_CUDA_TRY(cudaMalloc(&ws.z, 16 * dim));
-  WPCD_CUDA_TRY(cudaMalloc(&B.g, 16 * dim));
-  WPCD_CUDA_TRY(cudaMalloc(&B.V, 16 * dim * nvec));
-  WPCD_CUDA_TRY(cudaMalloc(&B.w, 16 * dim));
-  WPCD_CUDA_TRY(cudaMalloc(&B.u, 16 * dim));
-  WPCD_CUDA_TRY(cudaMalloc(&B.small, sizeof(double2) * ((size_t)(m + 1) * (m + 8) + 16)));
-  WPCD_CUDA_TRY(cudaMalloc(&B.partial, sizeof(double2) * (size_t)(m + 1) * 152 * 2));
-  WPCD_CUDA_TRY(cudaMalloc(&B.resid, sizeof(double)));
-  WPCD_CUDA_TRY(cudaMalloc(&B.flag, sizeof(int)));
-  WPCD_CUDA_TRY(cudaMalloc(&B.amp, sizeof(double) * 8));
+  if (n_E == 0) return WPCD_OK;
   wpcd_status worst = WPCD_OK;
-  for (int e = 0; e < n_E; ++e) {
-    wpcd_solve_stats one{};
-    wpcd_status st = opt.method == WPCD_SUM_KRYLOV ? solve_krylov(pr, P, E[e], opt, B, ws, one, s)
-                                                   : solve_wynn(pr, P, E[e], opt, B, ws, one, s);
-    if (st != WPCD_OK) return st;
-    U00[2 * e] = one.U00[0];
-    U00[2 * e + 1] = one.U00[1];
-    if (st_out) st_out[e] = one;
-    if (one.status < worst) worst = one.status;
+  if (opt.method == WPCD_SUM_WYNN) {
+    for (int e = 0; e < n_E; ++e) {
+      wpcd_solve_stats one{};
+      wpcd_status st = solve_wynn(pr, P, E[e], opt, one, s);
+      if (st != WPCD_OK) return st;
+      U00[2 * e] = one.U00[0];
+      U00[2 * e + 1] = one.U00[1];
+      if (st_out) st_out[e] = one;
+      if (one.status < worst) worst = one.status;
+    }
+  } else {
+    const bool mixed = opt.precision == WPCD_SOLVE_MIXED;
+    const int Bmax = opt.batch > 0 ? std::min(opt.batch, n_E) : n_E;
+    const size_t dim = (size_t)pr->n_ch * pr->N * pr->M;
+    if (mixed && !P->val32 && !P->val32_copy) {
+      WPCD_CUDA_TRY(cudaMalloc(&P->val32_copy, sizeof(float) * (size_t)P->nnz * P->n_pairs + 4));
+      int64_t nv = (int64_t)P->nnz * P->n_pairs;
+      d2f_kernel<<<grid_for(nv, 256), 256, 0, s>>>(nv, P->val64, P->val32_copy);
+      count_launches(1);
+    }
+    for (int e0 = 0; e0 < n_E; e0 += Bmax) {
+      const int B = std::min(Bmax, n_E - e0);
+      SolveCtx cx;
+      cx.B = B;
+      cx.dim = dim;
+      const size_t nb = 16 * dim * B;
+      WPCD_CUDA_TRY(cudaMalloc(&cx.g, nb));
+      if (mixed) WPCD_CUDA_TRY(cudaMalloc(&cx.g32, nb / 2));
+      WPCD_CUDA_TRY(cudaMalloc(&cx.b, nb));
+      WPCD_CUDA_TRY(cudaMalloc(&cx.u, nb));
+      WPCD_CUDA_TRY(cudaMalloc(&cx.r, nb));
+      WPCD_CUDA_TRY(cudaMalloc(&cx.t, nb));
+      WPCD_CUDA_TRY(cudaMalloc(&cx.r0, sizeof(int) * B));
+      WPCD_CUDA_TRY(cudaMalloc(&cx.Dd, sizeof(double) * B));
+      WPCD_CUDA_TRY(cudaMalloc(&cx.pref, sizeof(double) * B));
+      WPCD_CUDA_TRY(cudaMalloc(&cx.amp, sizeof(double) * 6 * B));
+      BatchInfo bi;
+      cudaEvent_t ev0, ev1;
+      WPCD_CUDA_TRY(cudaEventCreate(&ev0));
+      WPCD_CUDA_TRY(cudaEventCreate(&ev1));
+      cudaEventRecord(ev0, s);
+      wpcd_status st = batch_setup(pr, E + e0, B, cx, bi, mixed, s);
+      if (st != WPCD_OK) return st;
+      Workspace<double> ws64;
+      WPCD_CUDA_TRY(ws64.alloc(dim, B));
+      st = born(pr, P, cx, ws64, s);
+      if (st != WPCD_OK) return st;
+      const bool warm = opt.u_init != nullptr;
+      const int64_t n = (int64_t)dim * B;
+      if (warm) {
+        transpose_kernel<<<grid_for(n, 256), 256, 0, s>>>((int64_t)dim, B,
+                                                          (const double2 *)opt.u_init + (size_t)e0 * dim,
+                                                          (double2 *)cx.u, 1);
+        count_launches(1);
+      }
+      std::vector<int> status;
+      std::vector<double> relres;
+      int n64 = 0, n32 = 0, n_outer = 0;
+      if (mixed) {
+        const int m_in = opt.inner_iter > 0 ? opt.inner_iter : 16;
+        Krylov<float> kr;
+        Krylov<double> k64;
+        WPCD_CUDA_TRY(kr.alloc(m_in, B, dim));
+        WPCD_CUDA_TRY(k64.alloc(1, B, dim, false));  // norms only
+        Workspace<float> ws32;
+        WPCD_CUDA_TRY(ws32.alloc(dim, B));
+        st = solve_mixed(pr, P, opt, cx, kr, k64, ws64, ws32, status, relres, n64, n32, n_outer, warm, s);
+      } else {
+        Krylov<double> kr;
+        WPCD_CUDA_TRY(kr.alloc(opt.max_iter, B, dim));
+        st = solve_fp64(pr, P, opt, cx, kr, ws64, status, relres, n64, warm, s);
+      }
+      if (st != WPCD_OK) return st;
+      n64 += 1;  // the Born term
+      bamplitude_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, (const double2 *)cx.u, cx.r0, cx.Dd, cx.pref, cx.amp);
+      count_launches(1);
+      if (opt.u_out) {
+        transpose_kernel<<<grid_for(n, 256), 256, 0, s>>>((int64_t)dim, B, (const double2 *)cx.u,
+                                                          (double2 *)opt.u_out + (size_t)e0 * dim, 0);
+        count_launches(1);
+      }
+      cudaEventRecord(ev1, s);
+      std::vector<double> amp(6 * (size_t)B);
+      WPCD_CUDA_TRY(cudaMemcpyAsync(amp.data(), cx.amp, sizeof(double) * 6 * B, cudaMemcpyDeviceToHost, s));
+      WPCD_CUDA_TRY(cudaStreamSynchronize(s));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev0, ev1);
+      cudaEventDestroy(ev0);
+      cudaEventDestroy(ev1);
+      for (int e = 0; e < B; ++e) {
+        U00[2 * (e0 + e)] = amp[6 * e];
+        U00[2 * (e0 + e) + 1] = amp[6 * e + 1];
+        if (st_out) {
+          wpcd_solve_stats &so = st_out[e0 + e];
+          so.status = status[e];
+          so.n_kapply = n64;
+          so.n_kapply32 = n32;
+          so.n_outer = n_outer;
+          so.j0 = bi.j0[e];
+          so.D = bi.D[e];
+          so.relres = relres[e];
+          for (int i = 0; i < 2; ++i) {
+            so.U00[i] = amp[6 * e + i];
+            so.S[i] = amp[6 * e + 2 + i];
+            so.A[i] = amp[6 * e + 4 + i];
+          }
+          so.ms = ms / B;
+        }
+        if (status[e] < worst) worst = status[e];
+      }
+    }
   }
   if (worst != WPCD_OK)
     set_error(worst, worst == WPCD_ENOCONV ? "summation did not reach the tolerance for some energy"

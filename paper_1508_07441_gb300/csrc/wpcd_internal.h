@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -83,6 +84,7 @@ struct DeviceTables {
   double *qe = nullptr;                         // q edges [M+1]
   double *eps = nullptr;                        // [n_ch][N]
   double *O = nullptr, *Vt = nullptr;           // [n_ch][N][N]
+  float *O32 = nullptr, *Vt32 = nullptr;        // FP32 copies for the inner solve
 };
 
 }  // namespace wpcd
@@ -97,6 +99,12 @@ struct wpcd_problem {
   wpcd::DeviceTables d;
 };
 
+// SpMM launch shape chosen by the autotuner: rows per warp, energy lanes per
+// row, energies per lane (RHS tile = el * ept)
+struct SpmmConfig {
+  int rpw = 1, el = 1, ept = 1;
+};
+
 struct wpcd_P {
   const wpcd_problem *pr = nullptr;
   int prec = WPCD_FP64;
@@ -108,6 +116,8 @@ struct wpcd_P {
   float *val32 = nullptr;       // device [n_pairs][nnz] (FP32C assembly)
   float ms = 0.f;
   float ms_phase[3] = {0.f, 0.f, 0.f};  // count, scan, fill
+  float *val32_copy = nullptr;          // FP32 values made from FP64 ones (mixed solve)
+  std::map<int64_t, SpmmConfig> tuned;  // autotuner choices keyed by (B, precision)
 };
 
 namespace wpcd {
@@ -121,4 +131,6 @@ wpcd_status kapply(const wpcd_problem *pr, const wpcd_P *P, const double *g, con
                    double *y, cudaStream_t s);
 wpcd_status solve(wpcd_problem *pr, const wpcd_P *P, const double *E, int n_E,
                   const wpcd_solve_opts *o, double *U00, wpcd_solve_stats *st, cudaStream_t s);
+wpcd_status tune_spmm(const wpcd_problem *pr, wpcd_P *P, int B, int fp32, cudaStream_t s,
+                      SpmmConfig *out);
 }  // namespace wpcd

@@ -21,6 +21,7 @@ WPCD_OK, WPCD_EINVAL, WPCD_ENOMEM, WPCD_ECUDA = 0, -1, -2, -3
 WPCD_ENOCONV, WPCD_EBREAKDOWN, WPCD_ETIMEOUT, WPCD_ENOBOUND = -4, -5, -6, -7
 WPCD_FP64, WPCD_FP32C = 0, 1
 WPCD_SUM_KRYLOV, WPCD_SUM_WYNN = 0, 1
+WPCD_SOLVE_FP64, WPCD_SOLVE_MIXED = 0, 1
 
 _P = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
@@ -39,14 +40,16 @@ class wpcd_problem_desc(ctypes.Structure):
 
 class wpcd_solve_opts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("max_iter", ctypes.c_int), ("min_iter", ctypes.c_int),
-                ("tol", ctypes.c_double), ("check_every", ctypes.c_int)]
+                ("tol", ctypes.c_double), ("check_every", ctypes.c_int), ("precision", ctypes.c_int),
+                ("batch", ctypes.c_int), ("inner_iter", ctypes.c_int), ("max_outer", ctypes.c_int),
+                ("use_graph", ctypes.c_int), ("u_init", _P), ("u_out", _P)]
 
 
 class wpcd_solve_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("n_kapply", ctypes.c_int), ("j0", ctypes.c_int),
                 ("D", ctypes.c_double), ("relres", ctypes.c_double),
                 ("U00", ctypes.c_double * 2), ("S", ctypes.c_double * 2), ("A", ctypes.c_double * 2),
-                ("ms", ctypes.c_float)]
+                ("ms", ctypes.c_float), ("n_kapply32", ctypes.c_int), ("n_outer", ctypes.c_int)]
 
 
 _SIGS = {
@@ -67,6 +70,7 @@ _SIGS = {
     "wpcd_kapply": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "wpcd_solve": (ctypes.c_int, [_P, _P, _D, ctypes.c_int, ctypes.POINTER(wpcd_solve_opts), _D,
                                   ctypes.POINTER(wpcd_solve_stats), _P]),
+    "wpcd_tune_spmm": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P, _I, _I, _I]),
 }
 
 _lib = None
@@ -196,15 +200,29 @@ class Problem:
                                 _stream_ptr(stream)))
 
     def wpcd_solve(self, P, E, method=WPCD_SUM_KRYLOV, max_iter=100, min_iter=4, tol=1e-10,
-                   check_every=4, stream=None, allow=(WPCD_ENOCONV, WPCD_EBREAKDOWN)):
+                   check_every=4, precision=WPCD_SOLVE_FP64, batch=0, inner_iter=0, max_outer=0,
+                   use_graph=1, u_init=None, u_out=None, stream=None,
+                   allow=(WPCD_ENOCONV, WPCD_EBREAKDOWN)):
+        """U00 per energy (complex array), per-energy stats, status.  u_init /
+        u_out: device float64 tensors of 2 * len(E) * dim (energy-major)."""
         E = np.ascontiguousarray(np.atleast_1d(E), dtype=np.float64)
         U = np.zeros(2 * len(E))
         stats = (wpcd_solve_stats * len(E))()
-        opts = wpcd_solve_opts(method, max_iter, min_iter, tol, check_every)
+        opts = wpcd_solve_opts(method, max_iter, min_iter, tol, check_every, precision, batch,
+                               inner_iter, max_outer, use_graph,
+                               None if u_init is None else u_init.data_ptr(),
+                               None if u_out is None else u_out.data_ptr())
         st = lib().wpcd_solve(self._h, P.handle, _dp(E), len(E), ctypes.byref(opts), _dp(U), stats,
                               _stream_ptr(stream))
         check(st, allow=allow)
         return U.view(np.complex128), list(stats), st
+
+    def wpcd_tune_spmm(self, P, n_rhs, fp32=False, stream=None):
+        """(rows_per_warp, energy_lanes, energies_per_lane) chosen by timing."""
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(lib().wpcd_tune_spmm(self._h, P.handle, n_rhs, 1 if fp32 else 0, _stream_ptr(stream),
+                                   ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
 
 
 class PMatrix:

@@ -24,11 +24,23 @@ def test_exports_every_declared_symbol(W):
     assert L.wpcd_version() >= 100
 
 
-def test_struct_layouts_match_header(W):
-    # desc: 2 ints, 2 ptrs, 5 ints, 2 ptrs, 2 ints (LP64 padding)
-    assert ctypes.sizeof(W.wpcd_problem_desc) == 72
-    assert ctypes.sizeof(W.wpcd_solve_opts) == 32
-    assert ctypes.sizeof(W.wpcd_solve_stats) == 88
+def test_struct_layouts_match_header(W, tmp_path):
+    """ctypes mirrors of the ABI structs have the C compiler's sizes."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include "wpcd.h"\nint main(void){printf("%zu %zu %zu",'
+                   'sizeof(wpcd_problem_desc), sizeof(wpcd_solve_opts), sizeof(wpcd_solve_stats));}\n')
+    exe = tmp_path / "sz"
+    inc = W.HEADER.rsplit("/", 1)[0]
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    sizes = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    assert sizes == [ctypes.sizeof(W.wpcd_problem_desc), ctypes.sizeof(W.wpcd_solve_opts),
+                     ctypes.sizeof(W.wpcd_solve_stats)]
 
 
 def _desc(W, N=4, M=4, **kw):

@@ -1,0 +1,142 @@
+"""GPU parity of the batched and mixed-precision solves (through the C ABI)
+against the FP64 oracle: amplitudes rel 1e-6, residuals at the requested
+FP64 tolerance, identical results with and without CUDA-graph replay."""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def W():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1508_07441_gb300 import build, wpcd
+
+    build.build()
+    return wpcd
+
+
+@pytest.fixture(scope="module")
+def sys3(W, orc):
+    """3-channel system, 30 x 28 lattice, 4x4x16 nodes, V = -6 exp(-r^2)."""
+    from paper_1508_07441_gb300 import inputs
+
+    pe, qe = inputs.tangent_edges(30, 20.0), inputs.tangent_edges(28, 20.0)
+    pr = W.Problem(pe, qe, 4, 4, 16, 3, (-6.0,), (1.0,))
+    P64 = pr.wpcd_assemble_P(W.WPCD_FP64)
+    P32 = pr.wpcd_assemble_P(W.WPCD_FP32C)
+    opr = orc.Problem(dict(pe=pe, qe=qe, n_p=4, n_q=4, n_x=16, n_ch=3, V=[-6.0], a=[1.0],
+                           n_pair_nodes=8))
+    return pr, P64, P32, opr
+
+
+ENERGIES = [-0.3, 0.25, 0.9, 2.0, 4.5]
+
+
+def _ref(opr, E):
+    return np.array([opr.solve_gmres(e, tol=1e-13, max_iter=300)["U00"] for e in E])
+
+
+def test_batched_fp64_matches_oracle(W, sys3):
+    pr, P64, _, opr = sys3
+    U, stats, st = pr.wpcd_solve(P64, ENERGIES, tol=1e-12, max_iter=200, batch=len(ENERGIES))
+    assert st == W.WPCD_OK
+    ref = _ref(opr, ENERGIES)
+    assert np.max(np.abs(U - ref) / np.abs(ref)) < 1e-9
+    # one batch of 5 applies K to all five energies at once
+    assert len({s.n_kapply for s in stats}) == 1
+
+
+@pytest.mark.parametrize("pname", ["P64", "P32"])
+def test_mixed_matches_oracle(W, sys3, pname):
+    pr, P64, P32, opr = sys3
+    P = P64 if pname == "P64" else P32
+    U, stats, st = pr.wpcd_solve(P, ENERGIES, tol=1e-10, precision=W.WPCD_SOLVE_MIXED,
+                                 batch=len(ENERGIES))
+    assert st == W.WPCD_OK
+    for s in stats:
+        assert s.status == W.WPCD_OK and s.relres <= 1e-10
+        assert s.n_outer >= 1 and s.n_kapply32 >= 16
+    ref = _ref(opr, ENERGIES)
+    err = np.max(np.abs(U - ref) / np.abs(ref))
+    # FP64 values: refined to the FP64 system; FP32C values: the FP32 rounding
+    # of P0 (relative 6e-8) bounds the distance to the FP64 oracle
+    assert err < (1e-9 if pname == "P64" else 1e-6), err
+
+
+def test_mixed_graph_and_eager_identical(W, sys3):
+    pr, P64, _, _ = sys3
+    Ug, sg, _ = pr.wpcd_solve(P64, ENERGIES, precision=W.WPCD_SOLVE_MIXED, use_graph=1,
+                              stream=__import__("torch").cuda.Stream())
+    Ue, se, _ = pr.wpcd_solve(P64, ENERGIES, precision=W.WPCD_SOLVE_MIXED, use_graph=0)
+    assert np.array_equal(Ug, Ue)
+    assert [s.n_outer for s in sg] == [s.n_outer for s in se]
+
+
+def test_batch_of_128_energies(W, orc):
+    """The batching workload's energy grid (128 energies uniform in
+    [-0.9 |E_d|, 5]) solved in one batch, mixed precision, on a 3-channel
+    lattice; a sample of energies checked against the oracle."""
+    from paper_1508_07441_gb300 import inputs
+
+    pe, qe = inputs.tangent_edges(36, 20.0), inputs.tangent_edges(36, 20.0)
+    pr = W.Problem(pe, qe, 4, 4, 16, 3, (-3.0,), (1.0,))
+    P = pr.wpcd_assemble_P(W.WPCD_FP32C)
+    E = inputs.batch_energies(pr.eps_bound, 128)
+    U, stats, st = pr.wpcd_solve(P, E, precision=W.WPCD_SOLVE_MIXED, batch=128, tol=1e-10)
+    assert st == W.WPCD_OK and all(s.status == W.WPCD_OK for s in stats)
+    opr = orc.Problem(dict(pe=pe, qe=qe, n_p=4, n_q=4, n_x=16, n_ch=3, V=[-3.0], a=[1.0],
+                           n_pair_nodes=8))
+    for k in [0, 1, 40, 90, 127]:
+        ref = opr.solve_gmres(E[k], tol=1e-13, max_iter=400)["U00"]
+        assert abs(U[k] - ref) / abs(ref) < 1e-6, (k, E[k])
+
+
+def test_solution_vectors_and_warm_start(W, sys3):
+    import torch
+
+    pr, P64, _, opr = sys3
+    E = [0.9, 2.0]
+    u = torch.zeros(2 * len(E) * pr.dim, dtype=torch.float64, device="cuda")
+    U, s1, _ = pr.wpcd_solve(P64, E, tol=1e-12, max_iter=200, u_out=u)
+    for k, e in enumerate(E):
+        ref = opr.solve_gmres(e, tol=1e-13, max_iter=300)["u"]
+        got = u[2 * k * pr.dim:2 * (k + 1) * pr.dim].cpu().numpy().view(np.complex128)
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-9
+    # restarting from the solution needs no Krylov step
+    U2, s2, st = pr.wpcd_solve(P64, E, tol=1e-10, max_iter=200, u_init=u)
+    assert st == W.WPCD_OK
+    assert all(s.n_kapply <= 2 for s in s2)  # Born term + one residual
+    assert np.max(np.abs(U2 - U) / np.abs(U)) < 1e-10
+    # the mixed solve from the same warm start needs no refinement cycle
+    U3, s3, st = pr.wpcd_solve(P64, E, tol=1e-10, precision=W.WPCD_SOLVE_MIXED, u_init=u)
+    assert st == W.WPCD_OK and all(s.n_outer == 0 for s in s3)
+
+
+def test_autotuner(W, sys3, tmp_path, monkeypatch):
+    pr, P64, P32, _ = sys3
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("WPCD_TUNE_CACHE", str(cache))
+    for B in (1, 3, 8, 64):
+        for fp32, P in ((0, P64), (1, P32)):
+            rpw, el, ept = pr.wpcd_tune_spmm(P, B, fp32=bool(fp32))
+            assert rpw * el <= 32 and 32 % (rpw * el) == 0
+            assert ept in (1, 2, 4)
+            if B == 1:
+                assert el == 1
+    assert cache.exists() and len(cache.read_text().splitlines()) >= 1
+
+
+def test_invalid_solve_options(W, sys3):
+    pr, P64, _, _ = sys3
+    with pytest.raises(W.WpcdError):
+        pr.wpcd_solve(P64, [1.0], method=W.WPCD_SUM_WYNN, precision=W.WPCD_SOLVE_MIXED)
+    with pytest.raises(W.WpcdError):
+        pr.wpcd_solve(P64, [1.0], batch=5000)
+    with pytest.raises(W.WpcdError):
+        pr.wpcd_solve(P64, [1.0], inner_iter=500)
