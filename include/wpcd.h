@@ -183,7 +183,8 @@ typedef struct {
   int max_iter;    /* FP64 Krylov / Wynn: cap on K applications (<= 512) */
   int min_iter;    /* Wynn: minimum number of terms before stopping */
   double tol;      /* Krylov, mixed: relative residual; Wynn: relative change */
-  int check_every; /* FP64 Krylov: read the residual estimates back every n steps */
+  int check_every; /* FP64 Krylov: read the residual estimates back every n
+                      steps (1 gives exact per-energy step counts) */
   int precision;   /* WPCD_SOLVE_FP64 or WPCD_SOLVE_MIXED */
   int batch;       /* energies solved together in one batched iteration
                       (block K applications, SpMM over the batch); 0: all */
@@ -209,6 +210,8 @@ typedef struct {
                         (CUDA events), divided by the batch size */
   int n_kapply32;    /* mixed: FP32 K applications (n_kapply counts FP64 ones) */
   int n_outer;       /* mixed: refinement cycles */
+  int warm_fallback; /* FP64 Krylov: 1 if this energy's warm start was not
+                        better than the zero start and was replaced by it */
 } wpcd_solve_stats;
 
 /* Step 4 (Sec. 3.3: iterations of the matrix equation and Pade
@@ -236,6 +239,70 @@ wpcd_status wpcd_solve(wpcd_problem *pr, const wpcd_P *P, const double *E, int n
  * "key rows_per_warp energy_lanes energies_per_lane"). */
 wpcd_status wpcd_tune_spmm(wpcd_problem *pr, wpcd_P *P, int n_rhs, int fp32, void *stream,
                            int *rows_per_warp, int *energy_lanes, int *energies_per_lane);
+
+/* Born terms u0 = O P0 Vt e0 (the first iterate, Eq. kernel with G1
+ * removed) for n_E energies: b device [n_E][dim] complex FP64. */
+wpcd_status wpcd_born(wpcd_problem *pr, const wpcd_P *P, const double *E, int n_E, double *b, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned warm start.  The paper has no learned component: this is a growth
+ * line around its iteration, which stays the fallback and the judge.  A
+ * 3-layer MLP (n_in -> width -> width -> n_out, tanh hidden layers) is
+ * trained on the GPU by the library's own FP32 forward, backward and Adam
+ * kernels and inferred with BF16 weights (FP32 arithmetic); its outputs are
+ * coefficients of the solution in a projected basis Phi built from the
+ * method's own solutions.  All arrays named device are device memory.
+ * ------------------------------------------------------------------------- */
+typedef struct wpcd_mlp wpcd_mlp;
+
+/* Glorot-uniform weights (counter-based splitmix64 stream from `seed`),
+ * zero biases, identity input/output affine maps. */
+wpcd_status wpcd_mlp_create(int n_in, int width, int n_out, uint64_t seed, int device, wpcd_mlp **out);
+void wpcd_mlp_destroy(wpcd_mlp *m);
+wpcd_status wpcd_mlp_info(const wpcd_mlp *m, int64_t *n_params, int *n_in, int *width, int *n_out);
+
+/* Flat FP32 parameters [W1 (width x n_in), b1, W2 (width x width), b2,
+ * W3 (n_out x width), b3], weights row-major (output x input); `get` and
+ * `set` (either may be NULL) are host or device arrays of n_params. */
+wpcd_status wpcd_mlp_params(wpcd_mlp *m, float *get, const float *set);
+
+/* Input map x -> x * in_scale + in_shift before layer 1 and output map
+ * z -> z * out_scale + out_shift after layer 3 (training fits z to the
+ * targets mapped back by the inverse of the output map).  Host or device
+ * arrays; NULL leaves a map unchanged. */
+wpcd_status wpcd_mlp_set_affine(wpcd_mlp *m, const float *in_scale, const float *in_shift,
+                                const float *out_scale, const float *out_shift);
+
+/* Y [n][n_out] = MLP(X [n][n_in]) (device FP32); bf16 != 0 uses BF16 weights. */
+wpcd_status wpcd_mlp_forward(wpcd_mlp *m, const float *X, int n, float *Y, int bf16, void *stream);
+
+/* Mean squared error of the normalised outputs against targets T [n][n_out]
+ * (host *loss) and its gradient (device grad [n_params], may be NULL). */
+wpcd_status wpcd_mlp_loss_grad(wpcd_mlp *m, const float *X, const float *T, int n, float *loss, float *grad,
+                               void *stream);
+
+/* Minibatch Adam (lr, beta 0.9 / 0.999, eps 1e-8) over `epochs` shuffles of
+ * the n rows (X, T), batches of `batch` (a trailing partial batch is
+ * skipped); loss_hist: host [epochs] mean batch loss per epoch, or NULL. */
+wpcd_status wpcd_mlp_train(wpcd_mlp *m, const float *X, const float *T, int n, int epochs, int batch, float lr,
+                           uint64_t seed, float *loss_hist, void *stream);
+
+/* Projected basis: C [n][k] = <Phi_j, U_e> (complex FP64, device) for
+ * Phi [k][dim] and U [n][dim]. */
+wpcd_status wpcd_basis_project(const double *Phi, int k, int dim, const double *U, int n, double *C,
+                               void *stream);
+/* U [n][dim] = sum_j C[e][j] Phi_j with C as FP32 (re, im) pairs [n][k][2]. */
+wpcd_status wpcd_basis_expand(const double *Phi, int k, int dim, const float *C, int n, double *U,
+                              void *stream);
+/* Orthonormalise the k rows of Phi [k][dim] in place (two-pass modified
+ * Gram-Schmidt). */
+wpcd_status wpcd_basis_orthonormalize(double *Phi, int k, int dim, void *stream);
+/* X [n][1 + 2 kf] = [(E - e_lo)/(e_hi - e_lo), Re/Im Cb[e][0..kf)] (FP32),
+ * E_dev device [n], Cb [n][k] complex FP64 (the Born term's coefficients). */
+wpcd_status wpcd_warm_features(const double *E_dev, int n, double e_lo, double e_hi, const double *Cb, int k,
+                               int kf, float *X, void *stream);
+/* dst [2n] FP32 (re, im) pairs from src [n] complex FP64 (device). */
+wpcd_status wpcd_complex_to_f32(const double *src, int64_t n, float *dst, void *stream);
 
 #ifdef __cplusplus
 }

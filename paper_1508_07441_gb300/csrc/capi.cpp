@@ -28,7 +28,14 @@ wpcd_status cuda_error(cudaError_t e, const char *what) {
   return WPCD_ECUDA;
 }
 
-void clear_error() { g_last_error.clear(); }
+// Called on entry to the ABI calls that launch work: clears this thread's
+// message and any CUDA error another component left pending in the runtime
+// (cudaGetLastError is per host thread), so that the launch checks below
+// report this library's own failures only.
+void clear_error() {
+  g_last_error.clear();
+  (void)cudaGetLastError();
+}
 
 static void free_tables(DeviceTables &d) {
   double **all[] = {&d.pe2, &d.qe2, &d.pn, &d.wp, &d.qn, &d.wq, &d.yn, &d.wy, &d.rsb, &d.qe, &d.eps, &d.O, &d.Vt};
@@ -287,6 +294,7 @@ wpcd_status wpcd_P_timing(const wpcd_P *P, float ms[3]) {
 
 wpcd_status wpcd_P_export(const wpcd_P *P, int64_t *row_ptr, int32_t *col, double *val, void *stream) {
   WPCD_GUARD_BEGIN
+  clear_error();
   if (!P) return set_error(WPCD_EINVAL, "null P");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   WPCD_CUDA_TRY(cudaSetDevice(P->pr->device));
@@ -336,6 +344,14 @@ wpcd_status wpcd_solve(wpcd_problem *pr, const wpcd_P *P, const double *E, int n
   if (!pr || !P) return set_error(WPCD_EINVAL, "null problem or P");
   if (P->pr != pr) return set_error(WPCD_EINVAL, "P was assembled for another problem");
   return solve(pr, P, E, n_E, opts, U00, stats, static_cast<cudaStream_t>(stream));
+  WPCD_GUARD_END
+}
+
+wpcd_status wpcd_born(wpcd_problem *pr, const wpcd_P *P, const double *E, int n_E, double *b, void *stream) {
+  WPCD_GUARD_BEGIN
+  clear_error();
+  if (!pr || !P || P->pr != pr) return set_error(WPCD_EINVAL, "bad problem or P");
+  return born_vectors(pr, P, E, n_E, b, static_cast<cudaStream_t>(stream));
   WPCD_GUARD_END
 }
 

@@ -87,6 +87,7 @@ struct ResParams {
   const double *qe, *eps;
   const double *Elo, *Ehi;     // per energy
   const double *gl_t, *gl_w;   // 32-point GL rule
+  const double *gl8_t, *gl8_w; // 8-point GL rule
 };
 
 __global__ void resolvent_kernel(ResParams R, double *g) {
@@ -115,11 +116,24 @@ __global__ void resolvent_kernel(ResParams R, double *g) {
     double dist = fmin(fabs(lo_a), fabs(lo_b));
     double re;
     if (no_sign_change && fabs(D) < 0.05 * dist) {
-      // smooth integrand: q^2 log(1 + D / (E_lo - eps - 3q^2/4)) by 32-point GL
+      // smooth integrand q^2 log(1 + D / (E_lo - eps - 3q^2/4)); its
+      // singularities sit at q^2 = (E_lo - eps)/(3/4) and (E_hi - eps)/(3/4),
+      // outside the bin.  Measured in half bin widths from the bin centre,
+      // a distance rho > 4 makes the 8-point GL error ~ rho^-16 < 1e-14
+      // (Bernstein ellipse bound); otherwise 32 points.
       double half = 0.5 * (qb - qa), mid = 0.5 * (qb + qa), s = 0.0;
-      for (int m = 0; m < 32; ++m) {
-        double q = mid + half * R.gl_t[m];
-        s += R.gl_w[m] * q * q * log1p(D / (Elo - ek - 0.75 * q * q));
+      double rho = 1e300;
+      for (double a2 : {(Elo - ek) / 0.75, (Ehi - ek) / 0.75}) {
+        double qs = sqrt(fabs(a2));
+        // a real singular point at qs (a2 > 0), or a complex pair +-i qs
+        double d = a2 > 0.0 ? fabs(qs - mid) : sqrt(mid * mid + qs * qs);
+        rho = fmin(rho, d / half);
+      }
+      const int npts = rho > 4.0 ? 8 : 32;
+      const double *t = npts == 8 ? R.gl8_t : R.gl_t, *wg = npts == 8 ? R.gl8_w : R.gl_w;
+      for (int m = 0; m < npts; ++m) {
+        double q = mid + half * t[m];
+        s += wg[m] * q * q * log1p(D / (Elo - ek - 0.75 * q * q));
       }
       re = half * s;
     } else {
@@ -352,38 +366,55 @@ __global__ void __launch_bounds__(256) spmm_kernel(SpmmParams S, const VT *__res
 constexpr int V_THREADS = 256;
 
 // partial[(j * nblk + blk) * B + e] = sum_{rows of blk} conj(V_j[row, e]) w[row, e]
+// One pass over w per chunk of JC basis vectors; per-thread sums in the
+// vector type T, block sums in FP64.
+constexpr int JC = 8;
+
 template <typename T>
 __global__ void __launch_bounds__(V_THREADS) bdot_kernel(int rows, int B, int nv,
                                                          const typename Cx<T>::t *__restrict__ V,
                                                          size_t ld, const typename Cx<T>::t *__restrict__ w,
                                                          double2 *__restrict__ partial) {
-  __shared__ double2 red[V_THREADS];
+  __shared__ double2 red[JC][V_THREADS];
   const int EL = blockDim.x;  // energy lanes (<= 32)
   const int RB = blockDim.y;  // row lanes
-  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * EL + tx;
   const int e = blockIdx.y * EL + tx;
   const int nblk = gridDim.x;
-  for (int j = 0; j < nv; ++j) {
-    double sx = 0.0, sy = 0.0;
+  for (int j0 = 0; j0 < nv; j0 += JC) {
+    T sx[JC], sy[JC];
+#pragma unroll
+    for (int c = 0; c < JC; ++c) sx[c] = sy[c] = T(0);
     if (e < B) {
       for (int r = blockIdx.x * RB + ty; r < rows; r += nblk * RB) {
-        auto a = V[(size_t)j * ld + (size_t)r * B + e];
-        auto b = w[(size_t)r * B + e];
-        sx += (double)a.x * b.x + (double)a.y * b.y;
-        sy += (double)a.x * b.y - (double)a.y * b.x;
+        const auto b = w[(size_t)r * B + e];
+#pragma unroll
+        for (int c = 0; c < JC; ++c) {
+          if (j0 + c < nv) {
+            const auto a = V[(size_t)(j0 + c) * ld + (size_t)r * B + e];
+            sx[c] = fma(a.x, b.x, fma(a.y, b.y, sx[c]));
+            sy[c] = fma(a.x, b.y, fma(-a.y, b.x, sy[c]));
+          }
+        }
       }
     }
-    red[ty * EL + tx] = make_double2(sx, sy);
+#pragma unroll
+    for (int c = 0; c < JC; ++c) red[c][tid] = make_double2((double)sx[c], (double)sy[c]);
     __syncthreads();
     for (int h = RB / 2; h > 0; h >>= 1) {
-      if (ty < h) {
-        double2 o = red[(ty + h) * EL + tx];
-        red[ty * EL + tx].x += o.x;
-        red[ty * EL + tx].y += o.y;
-      }
+      if (ty < h)
+#pragma unroll
+        for (int c = 0; c < JC; ++c) {
+          double2 o = red[c][(ty + h) * EL + tx];
+          red[c][tid].x += o.x;
+          red[c][tid].y += o.y;
+        }
       __syncthreads();
     }
-    if (ty == 0 && e < B) partial[((size_t)j * nblk + blockIdx.x) * B + e] = red[tx];
+    if (ty == 0 && e < B)
+#pragma unroll
+      for (int c = 0; c < JC; ++c)
+        if (j0 + c < nv) partial[((size_t)(j0 + c) * nblk + blockIdx.x) * B + e] = red[c][tx];
     __syncthreads();
   }
 }
@@ -416,15 +447,17 @@ __global__ void baxpy_kernel(int64_t n, int B, int nv, const typename Cx<T>::t *
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n;
        f += (int64_t)gridDim.x * blockDim.x) {
     const int e = (int)(f % B);
-    double ax = w[f].x, ay = w[f].y;
+    T ax = w[f].x, ay = w[f].y;
+    const T sg = (T)sign;
     for (int j = 0; j < nv; ++j) {
-      auto a = V[(size_t)j * ld + f];
-      double2 c = h[j * B + e];
-      ax += sign * (c.x * a.x - c.y * a.y);
-      ay += sign * (c.x * a.y + c.y * a.x);
+      const auto a = V[(size_t)j * ld + f];
+      const double2 c = h[j * B + e];
+      const T cx = sg * (T)c.x, cy = sg * (T)c.y;
+      ax = fma(cx, a.x, fma(-cy, a.y, ax));
+      ay = fma(cx, a.y, fma(cy, a.x, ay));
     }
-    w[f].x = (T)ax;
-    w[f].y = (T)ay;
+    w[f].x = ax;
+    w[f].y = ay;
   }
 }
 
@@ -435,9 +468,9 @@ __global__ void bscale_kernel(int64_t n, int B, const typename Cx<T>::t *src, co
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n;
        f += (int64_t)gridDim.x * blockDim.x) {
     const int e = (int)(f % B);
-    double s = nrm2[e].x > 0.0 ? 1.0 / sqrt(nrm2[e].x) : 0.0;
-    dst[f].x = (T)(src[f].x * s);
-    dst[f].y = (T)(src[f].y * s);
+    const T s = (T)(nrm2[e].x > 0.0 ? 1.0 / sqrt(nrm2[e].x) : 0.0);
+    dst[f].x = src[f].x * s;
+    dst[f].y = src[f].y * s;
   }
 }
 
@@ -507,16 +540,17 @@ __global__ void bupdate_kernel(int64_t n, int B, int k, const typename Cx<T>::t 
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n;
        f += (int64_t)gridDim.x * blockDim.x) {
     const int e = (int)(f % B);
-    double ax = 0.0, ay = 0.0;
+    T ax = T(0), ay = T(0);  // the correction in the basis precision
     for (int j = 0; j < k; ++j) {
-      auto a = V[(size_t)j * ld + f];
-      double2 c = y[(size_t)j * B + e];
-      ax += c.x * a.x - c.y * a.y;
-      ay += c.x * a.y + c.y * a.x;
+      const auto a = V[(size_t)j * ld + f];
+      const double2 c = y[(size_t)j * B + e];
+      const T cx = (T)c.x, cy = (T)c.y;
+      ax = fma(cx, a.x, fma(-cy, a.y, ax));
+      ay = fma(cx, a.y, fma(cy, a.x, ay));
     }
-    double s = nrm2 ? sqrt(nrm2[e].x) : 1.0;
-    u[f].x += s * ax;
-    u[f].y += s * ay;
+    const double s = nrm2 ? sqrt(nrm2[e].x) : 1.0;
+    u[f].x += s * (double)ax;
+    u[f].y += s * (double)ay;
   }
 }
 
@@ -525,6 +559,18 @@ __global__ void bresid_kernel(int64_t n, const double2 *b, const double2 *u, con
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n;
        f += (int64_t)gridDim.x * blockDim.x)
     r[f] = make_double2(b[f].x - u[f].x + t[f].x, b[f].y - u[f].y + t[f].y);
+}
+
+// warm-start fallback: energies flagged get u = 0, r = b
+__global__ void bfallback_kernel(int64_t n, int B, const int *flag, const double2 *b, double2 *u, double2 *r) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    const int e = (int)(f % B);
+    if (flag[e]) {
+      u[f] = make_double2(0.0, 0.0);
+      r[f] = b[f];
+    }
+  }
 }
 
 // dst32[f] = (float)(src[f] / sqrt(nrm2[e].x))
@@ -882,7 +928,7 @@ wpcd_status resolvent_impl(const wpcd_problem *pr, const double *E, int n_E, dou
                            int *j0, double *D, cudaStream_t s) {
   if (n_E < 0 || (n_E > 0 && (!E || !g))) return set_error(WPCD_EINVAL, "bad resolvent arguments");
   if (n_E == 0) return WPCD_OK;
-  std::vector<double> lohi(2 * (size_t)n_E + 64);
+  std::vector<double> lohi(2 * (size_t)n_E + 80);
   for (int e = 0; e < n_E; ++e) {
     int jj;
     double lo, hi;
@@ -894,6 +940,7 @@ wpcd_status resolvent_impl(const wpcd_problem *pr, const double *E, int n_E, dou
     if (D) D[e] = hi - lo;
   }
   gauss_legendre(32, lohi.data() + 2 * n_E, lohi.data() + 2 * n_E + 32);
+  gauss_legendre(8, lohi.data() + 2 * n_E + 64, lohi.data() + 2 * n_E + 72);
   WPCD_CUDA_TRY(cudaSetDevice(pr->device));
   double *d_lohi = nullptr;
   WPCD_CUDA_TRY(cudaMallocAsync(&d_lohi, sizeof(double) * lohi.size(), s));
@@ -910,6 +957,8 @@ wpcd_status resolvent_impl(const wpcd_problem *pr, const double *E, int n_E, dou
   R.Ehi = d_lohi + n_E;
   R.gl_t = d_lohi + 2 * n_E;
   R.gl_w = d_lohi + 2 * n_E + 32;
+  R.gl8_t = d_lohi + 2 * n_E + 64;
+  R.gl8_w = d_lohi + 2 * n_E + 72;
   int64_t total = (int64_t)n_E * pr->n_ch * pr->N * pr->M;
   resolvent_kernel<<<grid_for(total, 256, 152 * 16), 256, 0, s>>>(R, g);
   count_launches(1);
@@ -1074,14 +1123,20 @@ wpcd_status born(const wpcd_problem *pr, const wpcd_P *P, SolveCtx &cx, Workspac
   return kapply_ws<double>(pr, P, nullptr, cx.t, cx.b, nullptr, cx.B, ws, s);
 }
 
-// Plain FP64 Krylov on (I - K) u = b, started from u (0 or a warm start)
+// Plain FP64 Krylov on (I - K) u = b, started from u (0 or a warm start).
+// A warm start whose residual is not below |b| is replaced by u = 0 for that
+// energy (the plain iteration is the fallback).  conv[e] receives the number
+// of Krylov steps after which energy e met the tolerance (checked every
+// check_every steps; m + 1 if it never did).
 wpcd_status solve_fp64(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solve_opts &o, SolveCtx &cx,
                        Krylov<double> &kr, Workspace<double> &ws, std::vector<int> &status,
-                       std::vector<double> &relres, int &n_apply, bool warm, cudaStream_t s) {
+                       std::vector<double> &relres, std::vector<int> &conv, std::vector<int> &fallback,
+                       int &n_apply, bool warm, cudaStream_t s) {
   const int B = cx.B, m = kr.m;
   const int64_t n = (int64_t)cx.dim * B;
   const int vg = grid_for(n, 256);
   n_apply = 0;
+  fallback.assign(B, 0);
   if (warm) {  // r = b - (I - K) u
     wpcd_status st = kapply_ws<double>(pr, P, cx.g, cx.u, cx.t, nullptr, B, ws, s);
     if (st != WPCD_OK) return st;
@@ -1099,6 +1154,25 @@ wpcd_status solve_fp64(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solve
   kr.norms<double>((const double2 *)cx.r, s);
   WPCD_CUDA_TRY(cudaMemcpyAsync(nr.data(), kr.nrm, sizeof(double2) * B, cudaMemcpyDeviceToHost, s));
   WPCD_CUDA_TRY(cudaStreamSynchronize(s));
+  if (warm) {
+    bool any = false;
+    for (int e = 0; e < B; ++e)
+      if (!(nr[e].x < nb[e].x)) {  // not better than the zero start (also NaN)
+        fallback[e] = 1;
+        any = true;
+      }
+    if (any) {
+      int *d_flag = nullptr;
+      WPCD_CUDA_TRY(cudaMalloc(&d_flag, sizeof(int) * B));
+      WPCD_CUDA_TRY(cudaMemcpy(d_flag, fallback.data(), sizeof(int) * B, cudaMemcpyHostToDevice));
+      bfallback_kernel<<<vg, 256, 0, s>>>(n, B, d_flag, (const double2 *)cx.b, (double2 *)cx.u, (double2 *)cx.r);
+      count_launches(1);
+      kr.norms<double>((const double2 *)cx.r, s);
+      WPCD_CUDA_TRY(cudaMemcpyAsync(nr.data(), kr.nrm, sizeof(double2) * B, cudaMemcpyDeviceToHost, s));
+      WPCD_CUDA_TRY(cudaStreamSynchronize(s));
+      cudaFree(d_flag);
+    }
+  }
   std::vector<double> bn(B);
   std::vector<double2> bet0((size_t)B * (m + 1), make_double2(0.0, 0.0));
   for (int e = 0; e < B; ++e) {
@@ -1114,12 +1188,19 @@ wpcd_status solve_fp64(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solve
   WPCD_CUDA_TRY(cudaMemcpyAsync(kr.bnorm, bn.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
   status.assign(B, WPCD_ENOCONV);
   relres.assign(B, 1.0);
+  conv.assign(B, m + 1);
   std::vector<double> res(B);
-  for (int e = 0; e < B; ++e) relres[e] = std::sqrt(nr[e].x) / bn[e];
-  int k = 0;
   bool done = true;
-  for (int e = 0; e < B; ++e)
-    if (relres[e] > o.tol) done = false;
+  for (int e = 0; e < B; ++e) {
+    relres[e] = std::sqrt(nr[e].x) / bn[e];
+    if (relres[e] <= o.tol) {
+      status[e] = WPCD_OK;
+      conv[e] = 0;
+    } else {
+      done = false;
+    }
+  }
+  int k = 0;
   for (k = 0; k < m && !done; ++k) {
     // w = (I - K) v_k
     wpcd_status st = kapply_ws<double>(pr, P, cx.g, (double *)kr.vec(k), kr.w, (double *)kr.vec(k), B, ws, s);
@@ -1134,18 +1215,19 @@ wpcd_status solve_fp64(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solve
       WPCD_CUDA_TRY(cudaStreamSynchronize(s));
       done = true;
       for (int e = 0; e < B; ++e) {
+        if (status[e] == WPCD_OK) continue;  // keeps its count and residual
         relres[e] = res[e];
-        if (!std::isfinite(res[e]))
+        if (!std::isfinite(res[e])) {
           status[e] = WPCD_EBREAKDOWN;
-        else if (res[e] <= o.tol)
+        } else if (res[e] <= o.tol) {
           status[e] = WPCD_OK;
-        else
+          conv[e] = k + 1;
+        } else {
           done = false;
+        }
       }
     }
   }
-  if (k == 0)
-    for (int e = 0; e < B; ++e) status[e] = WPCD_OK;  // the start already met the tolerance
   bbacksub_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, m, k, kr.H, kr.bet, kr.y);
   bupdate_kernel<double><<<vg, 256, 0, s>>>(n, B, k, kr.vec(0), cx.dim * B, kr.y, nullptr, (double2 *)cx.u);
   count_launches(2);
@@ -1422,6 +1504,35 @@ wpcd_status solve_wynn(const wpcd_problem *pr, const wpcd_P *P, double E, const 
 
 }  // namespace
 
+wpcd_status born_vectors(wpcd_problem *pr, const wpcd_P *P, const double *E, int n_E, double *b_major,
+                         cudaStream_t s) {
+  if (n_E < 1 || !E || !b_major) return set_error(WPCD_EINVAL, "bad Born arguments");
+  const size_t dim = (size_t)pr->n_ch * pr->N * pr->M;
+  std::vector<int> j0(n_E);
+  for (int e = 0; e < n_E; ++e) {
+    double lo, hi;
+    wpcd_status st = onshell(pr, E[e], &j0[e], &lo, &hi, nullptr);
+    if (st != WPCD_OK) return st;
+  }
+  WPCD_CUDA_TRY(cudaSetDevice(pr->device));
+  SolveCtx cx;
+  cx.B = n_E;
+  cx.dim = dim;
+  WPCD_CUDA_TRY(cudaMalloc(&cx.b, 16 * dim * n_E));
+  WPCD_CUDA_TRY(cudaMalloc(&cx.t, 16 * dim * n_E));
+  WPCD_CUDA_TRY(cudaMalloc(&cx.r0, sizeof(int) * n_E));
+  WPCD_CUDA_TRY(cudaMemcpyAsync(cx.r0, j0.data(), sizeof(int) * n_E, cudaMemcpyHostToDevice, s));
+  Workspace<double> ws;
+  WPCD_CUDA_TRY(ws.alloc(dim, n_E));
+  wpcd_status st = born(pr, P, cx, ws, s);
+  if (st != WPCD_OK) return st;
+  const int64_t n = (int64_t)dim * n_E;
+  transpose_kernel<<<grid_for(n, 256), 256, 0, s>>>((int64_t)dim, n_E, (const double2 *)cx.b, (double2 *)b_major, 0);
+  count_launches(1);
+  WPCD_CUDA_TRY(cudaStreamSynchronize(s));
+  return WPCD_OK;
+}
+
 wpcd_status solve(wpcd_problem *pr, const wpcd_P *Pc, const double *E, int n_E,
                   const wpcd_solve_opts *o, double *U00, wpcd_solve_stats *st_out, cudaStream_t s) {
   wpcd_solve_opts opt{};
@@ -1510,7 +1621,7 @@ wpcd_status solve(wpcd_problem *pr, const wpcd_P *Pc, const double *E, int n_E,
                                                           (double2 *)cx.u, 1);
         count_launches(1);
       }
-      std::vector<int> status;
+      std::vector<int> status, conv, fallback;
       std::vector<double> relres;
       int n64 = 0, n32 = 0, n_outer = 0;
       if (mixed) {
@@ -1525,7 +1636,7 @@ wpcd_status solve(wpcd_problem *pr, const wpcd_P *Pc, const double *E, int n_E,
       } else {
         Krylov<double> kr;
         WPCD_CUDA_TRY(kr.alloc(opt.max_iter, B, dim));
-        st = solve_fp64(pr, P, opt, cx, kr, ws64, status, relres, n64, warm, s);
+        st = solve_fp64(pr, P, opt, cx, kr, ws64, status, relres, conv, fallback, n64, warm, s);
       }
       if (st != WPCD_OK) return st;
       n64 += 1;  // the Born term
@@ -1550,7 +1661,10 @@ wpcd_status solve(wpcd_problem *pr, const wpcd_P *Pc, const double *E, int n_E,
         if (st_out) {
           wpcd_solve_stats &so = st_out[e0 + e];
           so.status = status[e];
-          so.n_kapply = n64;
+          // FP64 K applications: the batch's total, or for the plain solve
+          // this energy's own count to convergence (+ Born, + warm residual)
+          so.n_kapply = conv.empty() ? n64 : std::min(conv[e], n64) + 1 + (warm ? 1 : 0);
+          so.warm_fallback = fallback.empty() ? 0 : fallback[e];
           so.n_kapply32 = n32;
           so.n_outer = n_outer;
           so.j0 = bi.j0[e];

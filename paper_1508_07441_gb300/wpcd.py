@@ -49,7 +49,8 @@ class wpcd_solve_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("n_kapply", ctypes.c_int), ("j0", ctypes.c_int),
                 ("D", ctypes.c_double), ("relres", ctypes.c_double),
                 ("U00", ctypes.c_double * 2), ("S", ctypes.c_double * 2), ("A", ctypes.c_double * 2),
-                ("ms", ctypes.c_float), ("n_kapply32", ctypes.c_int), ("n_outer", ctypes.c_int)]
+                ("ms", ctypes.c_float), ("n_kapply32", ctypes.c_int), ("n_outer", ctypes.c_int),
+                ("warm_fallback", ctypes.c_int)]
 
 
 _SIGS = {
@@ -71,6 +72,23 @@ _SIGS = {
     "wpcd_solve": (ctypes.c_int, [_P, _P, _D, ctypes.c_int, ctypes.POINTER(wpcd_solve_opts), _D,
                                   ctypes.POINTER(wpcd_solve_stats), _P]),
     "wpcd_tune_spmm": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P, _I, _I, _I]),
+    "wpcd_born": (ctypes.c_int, [_P, _P, _D, ctypes.c_int, _P, _P]),
+    "wpcd_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                       ctypes.c_int, ctypes.POINTER(_P)]),
+    "wpcd_mlp_destroy": (None, [_P]),
+    "wpcd_mlp_info": (ctypes.c_int, [_P, _I64, _I, _I, _I]),
+    "wpcd_mlp_params": (ctypes.c_int, [_P, _P, _P]),
+    "wpcd_mlp_set_affine": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "wpcd_mlp_forward": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int, _P]),
+    "wpcd_mlp_loss_grad": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _F, _P, _P]),
+    "wpcd_mlp_train": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_float, ctypes.c_uint64, _F, _P]),
+    "wpcd_basis_project": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P]),
+    "wpcd_basis_expand": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P]),
+    "wpcd_basis_orthonormalize": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P]),
+    "wpcd_warm_features": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double, _P,
+                                          ctypes.c_int, ctypes.c_int, _P, _P]),
+    "wpcd_complex_to_f32": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P]),
 }
 
 _lib = None
@@ -217,6 +235,11 @@ class Problem:
         check(st, allow=allow)
         return U.view(np.complex128), list(stats), st
 
+    def wpcd_born(self, P, E, b, stream=None):
+        """Born terms into device tensor b (float64, 2 * len(E) * dim)."""
+        E = np.ascontiguousarray(np.atleast_1d(E), dtype=np.float64)
+        check(lib().wpcd_born(self._h, P.handle, _dp(E), len(E), _tensor_ptr(b), _stream_ptr(stream)))
+
     def wpcd_tune_spmm(self, P, n_rhs, fp32=False, stream=None):
         """(rows_per_warp, energy_lanes, energies_per_lane) chosen by timing."""
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
@@ -267,3 +290,81 @@ class PMatrix:
                                   ctypes.c_void_p(col.ctypes.data), ctypes.c_void_p(val.ctypes.data),
                                   None))
         return rp, col[: self.nnz], val[:, : self.nnz]
+
+
+class MLP:
+    """Handle of wpcd_mlp (3-layer tanh MLP; training and inference kernels
+    in the library)."""
+
+    def __init__(self, n_in, width, n_out, seed=2026, device=0):
+        h = _P()
+        self._h = None
+        check(lib().wpcd_mlp_create(n_in, width, n_out, seed, device, ctypes.byref(h)))
+        self._h = h
+        n = ctypes.c_int64()
+        check(lib().wpcd_mlp_info(h, ctypes.byref(n), None, None, None))
+        self.n_params, self.n_in, self.width, self.n_out = n.value, n_in, width, n_out
+
+    def close(self):
+        if self._h is not None:
+            lib().wpcd_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def wpcd_mlp_params(self, get=None, set=None):
+        """get / set: numpy float32 arrays or torch tensors of n_params."""
+        def ptr(a):
+            if a is None:
+                return None
+            return ctypes.c_void_p(a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data)
+        check(lib().wpcd_mlp_params(self._h, ptr(get), ptr(set)))
+
+    def wpcd_mlp_set_affine(self, in_scale=None, in_shift=None, out_scale=None, out_shift=None):
+        arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float32)
+                for a in (in_scale, in_shift, out_scale, out_shift)]
+        check(lib().wpcd_mlp_set_affine(self._h, *[None if a is None else ctypes.c_void_p(a.ctypes.data)
+                                                   for a in arrs]))
+
+    def wpcd_mlp_forward(self, X, Y, bf16=False, stream=None):
+        check(lib().wpcd_mlp_forward(self._h, _tensor_ptr(X), X.shape[0], _tensor_ptr(Y),
+                                     1 if bf16 else 0, _stream_ptr(stream)))
+
+    def wpcd_mlp_loss_grad(self, X, T, grad=None, stream=None):
+        loss = ctypes.c_float()
+        check(lib().wpcd_mlp_loss_grad(self._h, _tensor_ptr(X), _tensor_ptr(T), X.shape[0],
+                                       ctypes.byref(loss), _tensor_ptr(grad), _stream_ptr(stream)))
+        return loss.value
+
+    def wpcd_mlp_train(self, X, T, epochs, batch, lr, seed=2026, stream=None):
+        hist = np.zeros(epochs, dtype=np.float32)
+        check(lib().wpcd_mlp_train(self._h, _tensor_ptr(X), _tensor_ptr(T), X.shape[0], epochs, batch,
+                                   lr, seed, hist.ctypes.data_as(_F), _stream_ptr(stream)))
+        return hist
+
+
+def wpcd_basis_project(Phi, k, dim, U, n, C, stream=None):
+    check(lib().wpcd_basis_project(_tensor_ptr(Phi), k, dim, _tensor_ptr(U), n, _tensor_ptr(C),
+                                   _stream_ptr(stream)))
+
+
+def wpcd_basis_expand(Phi, k, dim, C, n, U, stream=None):
+    check(lib().wpcd_basis_expand(_tensor_ptr(Phi), k, dim, _tensor_ptr(C), n, _tensor_ptr(U),
+                                  _stream_ptr(stream)))
+
+
+def wpcd_basis_orthonormalize(Phi, k, dim, stream=None):
+    check(lib().wpcd_basis_orthonormalize(_tensor_ptr(Phi), k, dim, _stream_ptr(stream)))
+
+
+def wpcd_warm_features(E_dev, n, e_lo, e_hi, Cb, k, kf, X, stream=None):
+    check(lib().wpcd_warm_features(_tensor_ptr(E_dev), n, e_lo, e_hi, _tensor_ptr(Cb), k, kf,
+                                   _tensor_ptr(X), _stream_ptr(stream)))
+
+
+def wpcd_complex_to_f32(src, n, dst, stream=None):
+    check(lib().wpcd_complex_to_f32(_tensor_ptr(src), n, _tensor_ptr(dst), _stream_ptr(stream)))
