@@ -297,10 +297,14 @@ wpcd_status wpcd_basis_expand(const double *Phi, int k, int dim, const float *C,
 /* Orthonormalise the k rows of Phi [k][dim] in place (two-pass modified
  * Gram-Schmidt). */
 wpcd_status wpcd_basis_orthonormalize(double *Phi, int k, int dim, void *stream);
-/* X [n][1 + 2 kf] = [(E - e_lo)/(e_hi - e_lo), Re/Im Cb[e][0..kf)] (FP32),
- * E_dev device [n], Cb [n][k] complex FP64 (the Born term's coefficients). */
-wpcd_status wpcd_warm_features(const double *E_dev, int n, double e_lo, double e_hi, const double *Cb, int k,
-                               int kf, float *X, void *stream);
+/* X [n][1 + 2 kf] = [(Ebin - e_lo)/(e_hi - e_lo), Re/Im Cb[e][0..kf)]
+ * (FP32, device), Ebin the centre of E's on-shell energy bin (G1 depends on E
+ * through that bin only), E host [n], Cb [n][k] complex FP64 device (the Born
+ * term's coefficients in the basis). */
+wpcd_status wpcd_warm_features(const wpcd_problem *pr, const double *E, int n, double e_lo, double e_hi,
+                               const double *Cb, int k, int kf, float *X, void *stream);
+/* y += alpha x over n reals (device FP64). */
+wpcd_status wpcd_vec_axpy(double alpha, const double *x, double *y, int64_t n, void *stream);
 /* dst [2n] FP32 (re, im) pairs from src [n] complex FP64 (device). */
 wpcd_status wpcd_complex_to_f32(const double *src, int64_t n, float *dst, void *stream);
 

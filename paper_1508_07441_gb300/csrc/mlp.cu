@@ -308,19 +308,26 @@ __global__ void normalize_one_kernel(int dim, const double2 *nrm2, double2 *v) {
   }
 }
 
-// X[e] = [E_s, Re/Im of Cb[e][0..kf)] as floats
-__global__ void features_kernel(int n, int k, int kf, const double *E, double e_lo, double e_hi, const double2 *Cb,
-                                float *X) {
+// X[e] = [Ebin_s, Re/Im of Cb[e][0..kf)] as floats (Ebin: centre of the
+// on-shell energy bin, the only way E enters G1)
+__global__ void features_kernel(int n, int k, int kf, const double *Ebin, double e_lo, double e_hi,
+                                const double2 *Cb, float *X) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
   const int cols = 1 + 2 * kf;
   float *x = X + (size_t)e * cols;
-  x[0] = (float)((E[e] - e_lo) / (e_hi - e_lo));
+  x[0] = (float)((Ebin[e] - e_lo) / (e_hi - e_lo));
   for (int j = 0; j < kf; ++j) {
     double2 c = Cb[(size_t)e * k + j];
     x[1 + 2 * j] = (float)c.x;
     x[2 + 2 * j] = (float)c.y;
   }
+}
+
+// y += alpha x  (n reals)
+__global__ void axpy_real_kernel(int64_t n, double alpha, const double *x, double *y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = fma(alpha, x[i], y[i]);
 }
 
 __global__ void c2f_kernel(int64_t n, const double2 *src, float *dst) {
@@ -615,19 +622,44 @@ wpcd_status wpcd_basis_orthonormalize(double *Phi, int k, int dim, void *stream)
   return e == cudaSuccess ? WPCD_OK : cuda_error(e, "orthonormalisation");
 }
 
-// Features of the warm-start network: X[e] = [(E - e_lo) / (e_hi - e_lo),
+// Features of the warm-start network: X[e] = [(Ebin - e_lo) / (e_hi - e_lo),
 // Re/Im of the first kf coefficients Cb[e][0..kf) of the Born term in the
-// basis] as FP32 (device)
-wpcd_status wpcd_warm_features(const double *E_dev, int n, double e_lo, double e_hi, const double *Cb, int k,
-                               int kf, float *X, void *stream) {
+// basis] as FP32 (device); Ebin = centre of E's on-shell energy bin.
+wpcd_status wpcd_warm_features(const wpcd_problem *pr, const double *E, int n, double e_lo, double e_hi,
+                               const double *Cb, int k, int kf, float *X, void *stream) {
   clear_error();
-  if (!E_dev || !Cb || !X || n < 1 || kf < 0 || kf > k || !(e_hi > e_lo))
+  if (!pr || !E || !Cb || !X || n < 1 || kf < 0 || kf > k || !(e_hi > e_lo))
     return set_error(WPCD_EINVAL, "bad feature arguments");
+  std::vector<double> eb(n);
+  for (int i = 0; i < n; ++i) {
+    int j0;
+    double lo, hi;
+    wpcd_status st = onshell(pr, E[i], &j0, &lo, &hi, nullptr);
+    if (st != WPCD_OK) return st;
+    eb[i] = 0.5 * (lo + hi);
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  features_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, k, kf, E_dev, e_lo, e_hi, (const double2 *)Cb, X);
+  double *d_eb = nullptr;
+  WPCD_CUDA_TRY(cudaMalloc(&d_eb, sizeof(double) * n));
+  WPCD_CUDA_TRY(cudaMemcpy(d_eb, eb.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+  features_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, k, kf, d_eb, e_lo, e_hi, (const double2 *)Cb, X);
   count_launches(1);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = cudaStreamSynchronize(s);
+  cudaFree(d_eb);
   return e == cudaSuccess ? WPCD_OK : cuda_error(e, "features");
+}
+
+// y += alpha x over n reals (device FP64), e.g. u - u0 or u0 + Phi c
+wpcd_status wpcd_vec_axpy(double alpha, const double *x, double *y, int64_t n, void *stream) {
+  clear_error();
+  if (!x || !y || n < 0) return set_error(WPCD_EINVAL, "bad axpy arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (n > 0) {
+    axpy_real_kernel<<<gridn(n), 256, 0, s>>>(n, alpha, x, y);
+    count_launches(1);
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? WPCD_OK : cuda_error(e, "axpy");
 }
 
 // FP64 complex -> FP32 (re, im) pairs (device), e.g. projection

@@ -1,18 +1,23 @@
 """Learned warm start for the Faddeev iteration (argument marshalling around
 the library's kernels).
 
+G1 depends on the energy only through its on-shell bin, so u(E) is constant
+across a bin and its source u0 (the Born term, the first iterate) is specific
+to the bin.  The network therefore predicts the part of the solution beyond
+the first iterate, u - u0, in a basis built from that part.
+
 Pipeline, every arithmetic step in libwpcd:
-  1. snapshots: the method's own solutions u(E) at n_basis energies (batched
-     mixed solve), orthonormalised on the GPU into a projected basis Phi;
-  2. data: for each training energy, the target is the solution's
-     coefficients Phi^H u (k complex = 2k reals) and the features are the
-     scaled energy and the first kf coefficients of the Born term (the first
-     iterate) Phi^H u0;
+  1. snapshots: u(E) - u0(E) at k energies spread evenly over the on-shell
+     bins of the range (batched mixed solves), orthonormalised on the GPU
+     into a projected basis Phi;
+  2. data: for each training energy the target is Phi^H (u - u0) (k complex
+     = 2k reals) and the features are the scaled centre of the on-shell bin
+     and the first kf coefficients Phi^H u0 of the first iterate;
   3. the MLP is trained by the library's FP32 forward / backward / Adam
      kernels and inferred with BF16 weights;
-  4. warm start u_g = Phi c_hat; the solve starts from u_g and falls back to
-     u = 0 for any energy whose warm residual is not below |u0|; the plain
-     iteration's FP64 residual judges convergence.
+  4. warm start u_g = u0 + Phi c_hat; the solve starts from u_g and falls
+     back to u = 0 for any energy whose warm residual is not below |u0|; the
+     plain iteration's FP64 residual judges convergence.
 """
 from __future__ import annotations
 
@@ -44,10 +49,28 @@ class WarmStart:
                            stream=self.stream)
         return U
 
+    def born(self, E):
+        E = np.asarray(E, dtype=np.float64)
+        b = self._dev(2 * len(E) * self.dim, self.torch.float64)
+        self.pr.wpcd_born(self.P, E, b, stream=self.stream)
+        return b
+
+    def snapshot_energies(self, e_lo, e_hi):
+        """k energies at the centres of on-shell bins spread evenly (in bin
+        index) over the bins that [e_lo, e_hi] reaches."""
+        qe, eb = self.pr.qe, self.pr.eps_bound
+        q_lo, q_hi = np.sqrt((e_lo - eb) / 0.75), np.sqrt((e_hi - eb) / 0.75)
+        j_lo = int(np.searchsorted(qe, q_lo, side="right") - 1)
+        j_hi = int(np.searchsorted(qe, q_hi, side="right") - 1)
+        js = np.unique(np.round(np.linspace(j_lo, j_hi, self.k)).astype(int))
+        E = eb + 0.75 * (0.5 * (qe[js] + qe[js + 1])) ** 2
+        return np.clip(E, e_lo, e_hi)  # fewer than k when the range has fewer bins
+
     def build_basis(self, E_snap, batch=128):
         E_snap = np.asarray(E_snap, dtype=np.float64)
-        assert len(E_snap) == self.k
+        self.k = len(E_snap)
         U = self.solve_vectors(E_snap, batch=batch)
+        W.wpcd_vec_axpy(-1.0, self.born(E_snap), U, stream=self.stream)  # u - u0
         W.wpcd_basis_orthonormalize(U, self.k, self.dim, stream=self.stream)
         self.Phi = U
         return U
@@ -57,16 +80,16 @@ class WarmStart:
         W.wpcd_basis_project(self.Phi, self.k, self.dim, U, n, C, stream=self.stream)
         return C
 
-    def features(self, E):
-        """X [n][1 + 2 kf] (device float32) from the energy and the Born term."""
+    def features(self, E, b=None):
+        """X [n][1 + 2 kf] (device float32) from the on-shell bin and the
+        Born term."""
         E = np.asarray(E, dtype=np.float64)
         n = len(E)
-        b = self._dev(2 * n * self.dim, self.torch.float64)
-        self.pr.wpcd_born(self.P, E, b, stream=self.stream)
+        if b is None:
+            b = self.born(E)
         Cb = self.coefficients(b, n)
-        Ed = self.torch.from_numpy(E.copy()).to(f"cuda:{self.device}")
         X = self._dev(n * (1 + 2 * self.kf), self.torch.float32)
-        W.wpcd_warm_features(Ed, n, self.e_lo, self.e_hi, Cb, self.k, self.kf, X, stream=self.stream)
+        W.wpcd_warm_features(self.pr, E, self.e_lo, self.e_hi, Cb, self.k, self.kf, X, stream=self.stream)
         return X.view(n, 1 + 2 * self.kf)
 
     def dataset(self, E, batch=128):
@@ -76,10 +99,12 @@ class WarmStart:
         for i in range(0, len(E), batch):
             Eb = E[i:i + batch]
             U = self.solve_vectors(Eb, batch=batch)
+            b = self.born(Eb)
+            W.wpcd_vec_axpy(-1.0, b, U, stream=self.stream)  # u - u0
             C = self.coefficients(U, len(Eb))
             T = self._dev(2 * len(Eb) * self.k, self.torch.float32)
             W.wpcd_complex_to_f32(C, len(Eb) * self.k, T, stream=self.stream)
-            Xs.append(self.features(Eb))
+            Xs.append(self.features(Eb, b))
             Ts.append(T.view(len(Eb), 2 * self.k))
             del U
         return self.torch.cat(Xs), self.torch.cat(Ts)
@@ -98,14 +123,16 @@ class WarmStart:
                                        stream=self.stream)
 
     def predict(self, E, bf16=True):
-        """Warm starts u_g = Phi c_hat (device float64 [len(E)][2 dim])."""
+        """Warm starts u_g = u0 + Phi c_hat (device float64 [len(E)][2 dim])."""
         E = np.asarray(E, dtype=np.float64)
         n = len(E)
-        X = self.features(E)
+        b = self.born(E)
+        X = self.features(E, b)
         Y = self._dev(n * 2 * self.k, self.torch.float32)
         self.mlp.wpcd_mlp_forward(X.contiguous(), Y, bf16=bf16, stream=self.stream)
         U = self._dev(2 * n * self.dim, self.torch.float64)
         W.wpcd_basis_expand(self.Phi, self.k, self.dim, Y, n, U, stream=self.stream)
+        W.wpcd_vec_axpy(1.0, b, U, stream=self.stream)
         return U
 
     def iterations(self, E, u_init=None, tol=1e-8, batch=64, max_iter=200):

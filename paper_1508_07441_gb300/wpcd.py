@@ -86,8 +86,9 @@ _SIGS = {
     "wpcd_basis_project": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P]),
     "wpcd_basis_expand": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P]),
     "wpcd_basis_orthonormalize": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P]),
-    "wpcd_warm_features": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double, _P,
+    "wpcd_warm_features": (ctypes.c_int, [_P, _D, ctypes.c_int, ctypes.c_double, ctypes.c_double, _P,
                                           ctypes.c_int, ctypes.c_int, _P, _P]),
+    "wpcd_vec_axpy": (ctypes.c_int, [ctypes.c_double, _P, _P, ctypes.c_int64, _P]),
     "wpcd_complex_to_f32": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P]),
 }
 
@@ -361,9 +362,15 @@ def wpcd_basis_orthonormalize(Phi, k, dim, stream=None):
     check(lib().wpcd_basis_orthonormalize(_tensor_ptr(Phi), k, dim, _stream_ptr(stream)))
 
 
-def wpcd_warm_features(E_dev, n, e_lo, e_hi, Cb, k, kf, X, stream=None):
-    check(lib().wpcd_warm_features(_tensor_ptr(E_dev), n, e_lo, e_hi, _tensor_ptr(Cb), k, kf,
+def wpcd_warm_features(problem, E, e_lo, e_hi, Cb, k, kf, X, stream=None):
+    E = np.ascontiguousarray(np.atleast_1d(E), dtype=np.float64)
+    check(lib().wpcd_warm_features(problem.handle, _dp(E), len(E), e_lo, e_hi, _tensor_ptr(Cb), k, kf,
                                    _tensor_ptr(X), _stream_ptr(stream)))
+
+
+def wpcd_vec_axpy(alpha, x, y, stream=None):
+    """y += alpha x (device float64 tensors of equal size)."""
+    check(lib().wpcd_vec_axpy(float(alpha), _tensor_ptr(x), _tensor_ptr(y), y.numel(), _stream_ptr(stream)))
 
 
 def wpcd_complex_to_f32(src, n, dst, stream=None):

@@ -89,10 +89,10 @@ def test_warm_start_saves_iterations(W, orc):
     pe, qe = inputs.tangent_edges(48, 20.0), inputs.tangent_edges(48, 20.0)
     pr = W.Problem(pe, qe, 4, 4, 16, 3, (-3.0,), (1.0,))
     P = pr.wpcd_assemble_P(W.WPCD_FP64)
-    ws = WarmStart(pr, P, k=32, kf=12, width=128, seed=2026)
+    ws = WarmStart(pr, P, k=48, kf=12, width=128, seed=2026)
     lo, hi = -0.9 * abs(pr.eps_bound), 5.0
     ws.e_lo, ws.e_hi = lo, hi
-    ws.build_basis(np.linspace(lo, hi, 32))
+    ws.build_basis(ws.snapshot_energies(lo, hi))
     X, T = ws.dataset(inputs.random_energies(pr.eps_bound, 384, seed=2026))
     hist = ws.fit(X, T, epochs=400, batch=128, lr=2e-3)
     assert hist[-1] < 0.2 * hist[0]

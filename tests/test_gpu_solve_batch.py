@@ -48,8 +48,9 @@ def test_batched_fp64_matches_oracle(W, sys3):
     assert st == W.WPCD_OK
     ref = _ref(opr, ENERGIES)
     assert np.max(np.abs(U - ref) / np.abs(ref)) < 1e-9
-    # one batch of 5 applies K to all five energies at once
-    assert len({s.n_kapply for s in stats}) == 1
+    # one batch of 5 applies K to all five energies at once; each energy
+    # reports its own count of steps to the tolerance (+ the Born term)
+    assert all(2 <= s.n_kapply <= 201 for s in stats)
 
 
 @pytest.mark.parametrize("pname", ["P64", "P32"])
