@@ -978,6 +978,33 @@ wpcd_status resolvent(const wpcd_problem *pr, const double *E, int n_E, double *
   return resolvent_impl(pr, E, n_E, g, 0, j0, D, s);
 }
 
+// One FP64 K application into caller-provided intermediates (two [dim]
+// complex buffers) with the SpMM shape already tuned for one right-hand side
+// if there is one, else a fixed shape: no allocation, no tuning, no sync.
+wpcd_status kapply_scratch(const wpcd_problem *pr, const wpcd_P *P, const double *g, const double *x,
+                           double *y, double *scratch_y, double *scratch_z, cudaStream_t s) {
+  const int N = pr->N, M = pr->M, n_ch = pr->n_ch;
+  const int64_t ncol = 2LL * M;
+  dim3 grid((unsigned)((ncol + GB_N - 1) / GB_N), (N + GB_M - 1) / GB_M, n_ch);
+  if (g)
+    gemm_kernel<double, true, false><<<grid, G_THREADS, 0, s>>>(N, ncol, pr->d.Vt, x, g, nullptr, scratch_y);
+  else
+    gemm_kernel<double, false, false><<<grid, G_THREADS, 0, s>>>(N, ncol, pr->d.Vt, x, nullptr, nullptr, scratch_y);
+  count_launches(1);
+  SpmmConfig cfg{2, 1, 1};
+  const int64_t key = ((((int64_t)pr->n_ch * 4096 + pr->N) * 4096 + pr->M) * 4096 + 1) * 2;
+  auto it = P->tuned.find(key);
+  if (it != P->tuned.end()) cfg = it->second;
+  wpcd_status st = P->prec == WPCD_FP64
+                       ? launch_spmm_cfg<double, double>(pr, P, P->val64, scratch_y, scratch_z, 1, cfg, s)
+                       : launch_spmm_cfg<float, double>(pr, P, P->val32, scratch_y, scratch_z, 1, cfg, s);
+  if (st != WPCD_OK) return st;
+  gemm_kernel<double, false, false><<<grid, G_THREADS, 0, s>>>(N, ncol, pr->d.O, scratch_z, nullptr, nullptr, y);
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? WPCD_OK : cuda_error(e, "kapply launch");
+}
+
 wpcd_status kapply(const wpcd_problem *pr, const wpcd_P *P, const double *g, const double *x,
                    double *y, cudaStream_t s) {
   WPCD_CUDA_TRY(cudaSetDevice(pr->device));

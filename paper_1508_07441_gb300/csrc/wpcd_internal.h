@@ -133,6 +133,8 @@ wpcd_status solve(wpcd_problem *pr, const wpcd_P *P, const double *E, int n_E,
                   const wpcd_solve_opts *o, double *U00, wpcd_solve_stats *st, cudaStream_t s);
 wpcd_status tune_spmm(const wpcd_problem *pr, wpcd_P *P, int B, int fp32, cudaStream_t s,
                       SpmmConfig *out);
+wpcd_status kapply_scratch(const wpcd_problem *pr, const wpcd_P *P, const double *g, const double *x,
+                           double *y, double *scratch_y, double *scratch_z, cudaStream_t s);
 wpcd_status born_vectors(wpcd_problem *pr, const wpcd_P *P, const double *E, int n_E, double *b_major,
                          cudaStream_t s);
 }  // namespace wpcd

@@ -73,6 +73,7 @@ _SIGS = {
                                   ctypes.POINTER(wpcd_solve_stats), _P]),
     "wpcd_tune_spmm": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P, _I, _I, _I]),
     "wpcd_born": (ctypes.c_int, [_P, _P, _D, ctypes.c_int, _P, _P]),
+    "wpcd_kapply_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "wpcd_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                        ctypes.c_int, ctypes.POINTER(_P)]),
     "wpcd_mlp_destroy": (None, [_P]),
@@ -217,6 +218,12 @@ class Problem:
     def wpcd_kapply(self, P, g, x, y, stream=None):
         check(lib().wpcd_kapply(self._h, P.handle, _tensor_ptr(g), _tensor_ptr(x), _tensor_ptr(y),
                                 _stream_ptr(stream)))
+
+    def wpcd_kapply_noalloc(self, P, g, x, y, stream=None):
+        """K application with the library's fixed device scratch (no device
+        allocation); enqueued, not synchronised."""
+        check(lib().wpcd_kapply_noalloc(self._h, P.handle, _tensor_ptr(g), _tensor_ptr(x),
+                                        _tensor_ptr(y), _stream_ptr(stream)))
 
     def wpcd_solve(self, P, E, method=WPCD_SUM_KRYLOV, max_iter=100, min_iter=4, tol=1e-10,
                    check_every=4, precision=WPCD_SOLVE_FP64, batch=0, inner_iter=0, max_outer=0,

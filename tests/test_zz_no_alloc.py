@@ -1,0 +1,66 @@
+"""wpcd_kapply_noalloc: the K application for callers that cannot allocate
+device memory (code inside stream capture, applications whose device memory
+belongs to a fixed pool or a foreign allocator).  Its intermediates live in
+the library's fixed device array; its result must equal wpcd_kapply's, on
+two calls in a row (the array keeps the previous call's contents).  This
+file is collected last, so a run that stops at the first failure has
+already run every other test; it also passes alone in a fresh process."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def W():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1508_07441_gb300 import build, wpcd
+
+    build.build()
+    return wpcd
+
+
+def test_noalloc_matches_kapply_on_two_calls(W):
+    import torch
+    from paper_1508_07441_gb300 import inputs
+
+    pe, qe = inputs.tangent_edges(28, 20.0), inputs.tangent_edges(24, 20.0)
+    pr = W.Problem(pe, qe, 4, 4, 16, 3, (-6.0,), (1.0,))
+    P = pr.wpcd_assemble_P(W.WPCD_FP64)
+    g = torch.zeros(2 * pr.dim, dtype=torch.float64, device="cuda")
+    pr.wpcd_resolvent([0.7], g)
+    for call, seed in enumerate((7, 8)):  # two calls in a row, different inputs
+        x = inputs.random_complex(pr.dim, seed)
+        xd = torch.from_numpy(x.view(np.float64).copy()).cuda()
+        ref = torch.zeros_like(xd)
+        got = torch.full_like(xd, float("nan"))
+        pr.wpcd_kapply(P, g, xd, ref)
+        pr.wpcd_kapply_noalloc(P, g, xd, got)
+        torch.cuda.synchronize()
+        r, o = ref.cpu().numpy(), got.cpu().numpy()
+        assert np.all(np.isfinite(o)), call
+        assert np.linalg.norm(o - r) / np.linalg.norm(r) < 1e-11, call
+    # and with G1 = 1
+    pr.wpcd_kapply(P, None, xd, ref)
+    pr.wpcd_kapply_noalloc(P, None, xd, got)
+    torch.cuda.synchronize()
+    assert np.linalg.norm(got.cpu().numpy() - ref.cpu().numpy()) / np.linalg.norm(ref.cpu().numpy()) < 1e-11
+
+
+def test_noalloc_rejects_dimension_above_limit(W):
+    import torch
+    from paper_1508_07441_gb300 import inputs
+
+    n = 210  # 3 * 210 * 210 = 132 300 > 131 072
+    pe = inputs.tangent_edges(n, 20.0)
+    pr = W.Problem(pe, pe, 2, 2, 4, 3, (-6.0,), (1.0,))
+    assert pr.dim > 131072
+    P = pr.wpcd_assemble_P(W.WPCD_FP64)
+    x = torch.zeros(2 * pr.dim, dtype=torch.float64, device="cuda")
+    y = torch.zeros_like(x)
+    with pytest.raises(W.WpcdError) as ei:
+        pr.wpcd_kapply_noalloc(P, None, x, y)
+    assert ei.value.status == W.WPCD_EINVAL and "WPCD_NOALLOC_MAX_DIM" in str(ei.value)
