@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-warm-start", action="store_true")
     ap.add_argument("--warm-train", type=int, default=2000)
     ap.add_argument("--warm-test", type=int, default=512)
+    ap.add_argument("--no-batching", action="store_true")
     return ap.parse_args()
 
 
@@ -172,6 +173,129 @@ def run_reference(args):
     return 0
 
 
+def _timed(stream, fn):
+    """Device milliseconds of fn() on stream (CUDA events), and its result."""
+    import torch
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    out = fn()
+    ev1.record(stream)
+    ev1.synchronize()
+    return ev0.elapsed_time(ev1), out
+
+
+def bench_batching(args, W, inputs, stream, flush, device, maxr_fn=None):
+    """Batching workload (150 x 150 lattice, 3 channels, 8x8x32 nodes):
+    128 energies in one batched mixed solve, and 16 uneven-grid problems
+    (N = M from [40, 160], seed 1234; 8 seeded energies each) in one grouped
+    mixed solve against one solve per problem; a sample checked against the
+    oracle."""
+    import numpy as np
+    import torch
+
+    w = inputs.workload("cfg3")
+    pr = W.Problem(w["p_edges"], w["q_edges"], *w["nodes"], w["n_ch"], w["V"], w["a"], device=device)
+    P = pr.wpcd_assemble_P(W.WPCD_FP64, stream=stream)
+    Eb = [float(x) for x in inputs.batch_energies(pr.eps_bound, 128)]
+    kw = dict(precision=W.WPCD_SOLVE_MIXED, tol=1e-10, stream=stream)
+    t128 = []
+    for it in range(4):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        ms, (U128, s128, _) = _timed(stream, lambda: pr.wpcd_solve(P, Eb, batch=len(Eb), **kw))
+        if it > 0:
+            t128.append(ms)
+    tp = []
+    for it in range(3):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        ms, (Up, sp, _) = _timed(stream, lambda: pr.wpcd_solve(P, [Eb[64]], tol=1e-10, max_iter=200,
+                                                                  batch=1, stream=stream))
+        if it > 0:
+            tp.append(ms)
+    # uneven group
+    sizes = [int(n) for n in inputs.uneven_sizes(16, 40, 160, 1234)]
+    probs, Ps, Es = [], [], []
+    for g, n in enumerate(sizes):
+        e = inputs.tangent_edges(n, w["k_max"])
+        q = W.Problem(e, e, *w["nodes"], w["n_ch"], w["V"], w["a"], device=device)
+        probs.append(q)
+        Ps.append(q.wpcd_assemble_P(W.WPCD_FP64, stream=stream))
+        Es.append(inputs.random_energies(q.eps_bound, 8, 5000 + g))
+    n_sys = sum(len(e) for e in Es)
+    tg, ts = [], []
+    for it in range(4):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        ms, (Ug, sg, stg) = _timed(stream, lambda: W.wpcd_solve_batch(probs, Ps, Es, **kw))
+        if it > 0:
+            tg.append(ms)
+        flush.fill_(1)
+        torch.cuda.synchronize()
+
+        def seq():
+            return [q.wpcd_solve(Pq, E, batch=len(E), **kw) for q, Pq, E in zip(probs, Ps, Es)]
+
+        ms, outs = _timed(stream, seq)
+        if it > 0:
+            ts.append(ms)
+    Useq = [o[0] for o in outs]
+    diff = max(float(np.max(np.abs(a - b) / np.abs(b))) for a, b in zip(Ug, Useq))
+    acc = None
+    if not args.no_oracle_check:
+        import oracle
+
+        oracle.build()
+        errs = []
+        t0 = time.perf_counter()
+        for g, (n, E) in enumerate(zip(sizes, Es)):
+            e = inputs.tangent_edges(n, w["k_max"])
+            opr = oracle.Problem(dict(pe=e, qe=e, n_p=w["nodes"][0], n_q=w["nodes"][1], n_x=w["nodes"][2],
+                                      n_ch=w["n_ch"], V=list(w["V"]), a=list(w["a"]), n_pair_nodes=8))
+            k = g % len(E)
+            ref = opr.solve_gmres(float(E[k]), tol=1e-12, max_iter=300)["U00"]
+            errs.append(abs(Ug[g][k] - ref) / abs(ref))
+        opr = oracle.Problem(dict(pe=w["p_edges"], qe=w["q_edges"], n_p=w["nodes"][0], n_q=w["nodes"][1],
+                                  n_x=w["nodes"][2], n_ch=w["n_ch"], V=list(w["V"]), a=list(w["a"]),
+                                  n_pair_nodes=8))
+        e128 = []
+        for k in (0, 42, 85, 127):
+            ref = opr.solve_gmres(Eb[k], tol=1e-12, max_iter=300)["U00"]
+            e128.append(abs(U128[k] - ref) / abs(ref))
+        acc = {"group_max_rel_err_U00": max(errs), "group_within_1e-6": int(sum(x < 1e-6 for x in errs)),
+               "group_n_checked": len(errs), "batch128_max_rel_err_U00": max(e128),
+               "batch128_n_checked": len(e128), "oracle_s": time.perf_counter() - t0}
+    b128 = statistics.mean(t128)
+    bp = statistics.mean(tp)
+    g_ms, s_ms = statistics.mean(tg), statistics.mean(ts)
+    res = {
+        "workload": "3 bosons, V=-3exp(-r^2), 3 channels, GL 8x8x32 nodes per cell",
+        "batch128": {"value": 128 / (b128 * 1e-3), "unit": "energies/s", "ms": b128, "N": w["N"],
+                     "fp32_k_applications": s128[0].n_kapply32, "fp64_k_applications": s128[0].n_kapply,
+                     "max_rel_residual": max(s.relres for s in s128),
+                     "plain_fp64": {"value": 1e3 / bp, "unit": "energies/s", "ms": bp, "energy": Eb[64],
+                                    "k_applications": sp[0].n_kapply},
+                     "speedup_vs_plain_fp64": (128 / (b128 * 1e-3)) / (1e3 / bp)},
+        "uneven_group": {"value": n_sys / (g_ms * 1e-3), "unit": "energies/s", "ms": g_ms,
+                         "sizes": sizes, "energies_per_problem": 8, "status": stg,
+                         "max_rel_residual": max(s.relres for sl in sg for s in sl),
+                         "fp32_k_applications": sg[0][0].n_kapply32,
+                         "one_solve_per_problem": {"value": n_sys / (s_ms * 1e-3), "unit": "energies/s",
+                                                   "ms": s_ms},
+                         "speedup_vs_per_problem": s_ms / g_ms,
+                         "max_rel_diff_vs_per_problem": diff},
+        "accuracy_vs_oracle": acc,
+    }
+    for Pq in Ps:
+        Pq.close()
+    for q in probs:
+        q.close()
+    P.close()
+    pr.close()
+    return res
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -277,6 +401,13 @@ def main():
             plain.append((sp[0].ms, sp[0].n_kapply, Up[0]))
     plain_ms = maxr(statistics.mean(m for m, _, _ in plain))
     P4.close()
+
+    # ---- batching workload: 128 energies on the 150 x 150 lattice, and 16
+    # problems of uneven grids (N = M drawn from [40, 160], seed 1234, 8
+    # seeded energies each) in one grouped iteration vs one solve per problem
+    batching = None
+    if not args.no_batching:
+        batching = bench_batching(args, W, inputs, stream, flush, local, maxr_fn=None)
 
     # ---- end to end through the public API with host buffers -------------
     barrier()
@@ -420,6 +551,7 @@ def main():
                   "speedup_vs_plain_fp64": energies_per_s / (1e3 / plain_ms),
                   "accuracy_vs_oracle": acc},
         "warm_start": warm,
+        "batching": batching,
         "roofline": roofline,
         "roofline_peak_source": peak_src,
         "cpu_baseline": cpu,

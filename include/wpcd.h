@@ -230,6 +230,34 @@ wpcd_status wpcd_solve(wpcd_problem *pr, const wpcd_P *P, const double *E, int n
                        const wpcd_solve_opts *opts, double *U00, wpcd_solve_stats *stats,
                        void *stream);
 
+/* Largest number of problems in one grouped solve, and of energies per
+ * problem there. */
+#define WPCD_GROUP_MAX 64
+#define WPCD_GROUP_MAX_E 32
+
+/* Batching across grids (Sec. 3.3 iterations of the matrix equation, the
+ * same summation as wpcd_solve with WPCD_SUM_KRYLOV): n_prob problems whose
+ * packet grids differ in size, each with its own energies, solved together.
+ * Every operation of the iteration is ONE launch over all problems: the
+ * Vt / O block products walk one tile list over (problem, channel, tile),
+ * the P0 SpMM walks the concatenated rows of all P0 matrices, and the
+ * Krylov vector kernels work on the concatenated per-problem batches (the
+ * wpcd_solve layout, energy index innermost, one segment per problem).
+ * Each (problem, energy) system keeps its own G1 and Krylov basis; with
+ * WPCD_SOLVE_MIXED the FP32 inner cycle of all problems is one CUDA graph.
+ * problems[g], P[g]: problem g and its assembled P0 (all on one device, the
+ * same channel count and the same P0 precision); E[g]: host [n_E[g]]
+ * energies, 1 <= n_E[g] <= WPCD_GROUP_MAX_E; U00[g]: host [n_E[g]] complex
+ * (interleaved) results; stats: NULL, or host array of n_prob pointers each
+ * NULL or to [n_E[g]] stats.  opts as for wpcd_solve, with method
+ * WPCD_SUM_KRYLOV, batch 0 and no vectors (EINVAL otherwise); 1 <= n_prob
+ * <= WPCD_GROUP_MAX.  Allocates its work space with cudaMalloc and frees it
+ * before returning.  Returns the worst per-energy status (ENOCONV and
+ * EBREAKDOWN still deliver the best estimate). */
+wpcd_status wpcd_solve_batch(int n_prob, wpcd_problem *const *problems, const wpcd_P *const *P,
+                             const double *const *E, const int *n_E, const wpcd_solve_opts *opts,
+                             double *const *U00, wpcd_solve_stats *const *stats, void *stream);
+
 /* Autotuner (batching): time the candidate SpMM launch shapes (rows per
  * warp, energy lanes per row, energies per lane = RHS tile width) for a
  * batch of n_rhs energies in FP64 (fp32 = 0) or FP32 (fp32 = 1) and keep the

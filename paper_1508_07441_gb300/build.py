@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwpcd.so")
-SOURCES = ["capi.cpp", "setup.cpp", "assemble.cu", "solve.cu", "mlp.cu", "kapply_noalloc.cu"]
+SOURCES = ["capi.cpp", "setup.cpp", "assemble.cu", "solve.cu", "group.cu", "mlp.cu", "kapply_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -36,7 +36,8 @@ def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
     t = os.path.getmtime(obj)
-    deps = [src, os.path.join(CSRC, "wpcd_internal.h"), os.path.join(ROOT, "include", "wpcd.h")]
+    deps = [src, os.path.join(CSRC, "wpcd_internal.h"), os.path.join(CSRC, "common.cuh"),
+            os.path.join(ROOT, "include", "wpcd.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

@@ -347,6 +347,15 @@ wpcd_status wpcd_solve(wpcd_problem *pr, const wpcd_P *P, const double *E, int n
   WPCD_GUARD_END
 }
 
+wpcd_status wpcd_solve_batch(int n_prob, wpcd_problem *const *problems, const wpcd_P *const *P,
+                             const double *const *E, const int *n_E, const wpcd_solve_opts *opts,
+                             double *const *U00, wpcd_solve_stats *const *stats, void *stream) {
+  WPCD_GUARD_BEGIN
+  clear_error();
+  return solve_group(n_prob, problems, P, E, n_E, opts, U00, stats, static_cast<cudaStream_t>(stream));
+  WPCD_GUARD_END
+}
+
 wpcd_status wpcd_born(wpcd_problem *pr, const wpcd_P *P, const double *E, int n_E, double *b, void *stream) {
   WPCD_GUARD_BEGIN
   clear_error();

@@ -1,0 +1,255 @@
+// Device pieces shared by the single-problem batched solver (solve.cu) and
+// the grouped solver over problems of uneven size (group.cu): complex and
+// accumulator types, the dense block-GEMM tile, the per-system Givens /
+// back-substitution kernels of the Krylov least-squares problem, and the
+// autotuner's candidate SpMM launch shapes.  Everything sits in an unnamed
+// namespace, so each translation unit gets its own copy of the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "wpcd_internal.h"
+
+namespace wpcd {
+namespace {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+template <typename T>
+struct Cx;
+template <>
+struct Cx<double> {
+  using t = double2;
+};
+template <>
+struct Cx<float> {
+  using t = float2;
+};
+
+// SpMM accumulators: plain FP64, or compensated FP32
+struct AccD {
+  double v;
+  __device__ void zero() { v = 0.0; }
+  __device__ void fma(double a, double b) { v = ::fma(a, b, v); }
+  __device__ void add_shfl(int off) { v += __shfl_xor_sync(0xffffffffu, v, off); }
+  __device__ double value() const { return v; }
+};
+
+struct AccF {  // float-float (Knuth TwoSum on the running sum, exact products)
+  float hi, lo;
+  __device__ void zero() { hi = 0.f; lo = 0.f; }
+  __device__ void add(float x) {
+    float s = __fadd_rn(hi, x);
+    float bb = __fsub_rn(s, hi);
+    float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ void fma(float a, float b) {
+    float p = __fmul_rn(a, b);
+    float pe = fmaf(a, b, -p);  // exact product error (TwoProduct)
+    add(p);
+    lo = __fadd_rn(lo, pe);
+  }
+  __device__ void add_shfl(int off) {
+    float ohi = __shfl_xor_sync(0xffffffffu, hi, off);
+    float olo = __shfl_xor_sync(0xffffffffu, lo, off);
+    add(ohi);
+    lo = __fadd_rn(lo, olo);
+  }
+  __device__ float value() const { return __fadd_rn(hi, lo); }
+};
+
+template <typename T>
+struct AccOf;
+template <>
+struct AccOf<double> {
+  using t = AccD;
+};
+template <>
+struct AccOf<float> {
+  using t = AccF;
+};
+
+int grid_for(int64_t n, int threads, int cap = 152 * 8) {
+  int64_t g = (n + threads - 1) / threads;
+  return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+// ---------------------------------------------------------------------------
+// dense block GEMM tile:  C (n x ncol) = A (n x n) * B' (n x ncol), rows
+// row0..row0+31, columns col0..col0+63; B' = B, or the G1-scaled complex
+// block (complex pairs along the columns, re at even columns); epilogue
+// C = out, or C = S - out.  All pointers are at the block's origin; ncol is
+// even, so complex pairs never straddle a row.
+// ---------------------------------------------------------------------------
+// 32 x 64 output tiles: 7 x 7 x 3 = 147 CTAs for the 200-bin, 3-channel,
+// one-energy blocks, close to one wave over the 152 SMs (FP64 work is
+// issue-bound, so SM coverage matters more than data reuse there)
+constexpr int GB_M = 32, GB_N = 64, GB_K = 16, G_THREADS = 256;
+
+template <typename T>
+struct GemmSmem {
+  T As[GB_K][GB_M + 1];
+  T Bs[GB_K][GB_N];
+};
+
+template <typename T, bool SCALE_G, bool SUB>
+__device__ __forceinline__ void gemm_tile(int n, int64_t ncol, const T *__restrict__ A, const T *__restrict__ B,
+                                          const T *__restrict__ G, const T *__restrict__ S, T *__restrict__ C,
+                                          int row0, int64_t col0, GemmSmem<T> &sm) {
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 16 x 16 threads, 2 x 4 outputs each
+  T acc[2][4] = {};
+  for (int k0 = 0; k0 < n; k0 += GB_K) {
+    for (int t = threadIdx.x; t < GB_M * GB_K; t += G_THREADS) {
+      int r = t / GB_K, kk = t % GB_K;
+      int gr = row0 + r, gk = k0 + kk;
+      sm.As[kk][r] = (gr < n && gk < n) ? A[(size_t)gr * n + gk] : T(0);
+    }
+    for (int t = threadIdx.x; t < GB_K * GB_N; t += G_THREADS) {
+      int kk = t / GB_N, cc = t % GB_N;
+      int gk = k0 + kk;
+      int64_t gc = col0 + cc;
+      T v = T(0);
+      if (gk < n && gc < ncol) {
+        size_t o = (size_t)gk * ncol + gc;
+        if (SCALE_G) {
+          size_t oc = o & ~(size_t)1;  // complex pair (re at even column)
+          T xr = B[oc], xi = B[oc + 1], gr_ = G[oc], gi = G[oc + 1];
+          v = (gc & 1) ? (gr_ * xi + gi * xr) : (gr_ * xr - gi * xi);
+        } else {
+          v = B[o];
+        }
+      }
+      sm.Bs[kk][cc] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GB_K; ++kk) {
+      T a[2], bb[4];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) a[u] = sm.As[kk][ty + 16 * u];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) bb[u] = sm.Bs[kk][tx + 16 * u];
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], bb[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      int gr = row0 + ty + 16 * u;
+      int64_t gc = col0 + tx + 16 * v;
+      if (gr < n && gc < ncol) {
+        size_t o = (size_t)gr * ncol + gc;
+        C[o] = SUB ? S[o] - acc[u][v] : acc[u][v];
+      }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Krylov least squares, one thread per system (energy)
+// ---------------------------------------------------------------------------
+// Givens least-squares update of column k for every energy (thread e).
+// Layout per energy e: H + e*(m+1)*m column-major (ld m+1), cs/sn + e*m,
+// bet + e*(m+1); h[i * B + e], hn2[e].
+__global__ void bgivens_kernel(int B, int m, int k, const double2 *h, const double2 *hn2, double2 *Hb,
+                               double2 *csb, double2 *snb, double2 *betb, double *resid,
+                               const double *bnorm) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= B) return;
+  double2 *H = Hb + (size_t)e * (m + 1) * m, *cs = csb + (size_t)e * m, *sn = snb + (size_t)e * m;
+  double2 *bet = betb + (size_t)e * (m + 1);
+  double2 *col = H + (size_t)k * (m + 1);
+  for (int i = 0; i <= k; ++i) col[i] = h[(size_t)i * B + e];
+  col[k + 1] = make_double2(sqrt(fmax(hn2[e].x, 0.0)), 0.0);
+  for (int i = 0; i < k; ++i) {
+    double2 a = col[i], b = col[i + 1], c = cs[i], s = sn[i];
+    // [a'; b'] = [conj(c) conj(s); -s c] [a; b]
+    double2 na = make_double2(c.x * a.x + c.y * a.y + s.x * b.x + s.y * b.y,
+                              c.x * a.y - c.y * a.x + s.x * b.y - s.y * b.x);
+    double2 nb = make_double2(-(s.x * a.x - s.y * a.y) + (c.x * b.x - c.y * b.y),
+                              -(s.x * a.y + s.y * a.x) + (c.x * b.y + c.y * b.x));
+    col[i] = na;
+    col[i + 1] = nb;
+  }
+  double2 a = col[k], b = col[k + 1];
+  double den = sqrt(a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y);
+  double2 c = den > 0 ? make_double2(a.x / den, a.y / den) : make_double2(1.0, 0.0);
+  double2 s = den > 0 ? make_double2(b.x / den, b.y / den) : make_double2(0.0, 0.0);
+  cs[k] = c;
+  sn[k] = s;
+  col[k] = make_double2(den, 0.0);
+  col[k + 1] = make_double2(0.0, 0.0);
+  double2 bk = bet[k];
+  bet[k + 1] = make_double2(-(s.x * bk.x - s.y * bk.y), -(s.x * bk.y + s.y * bk.x));
+  bet[k] = make_double2(c.x * bk.x + c.y * bk.y, c.x * bk.y - c.y * bk.x);
+  resid[e] = sqrt(bet[k + 1].x * bet[k + 1].x + bet[k + 1].y * bet[k + 1].y) / bnorm[e];
+}
+
+// back substitution H y = bet per energy; y[j * B + e]
+__global__ void bbacksub_kernel(int B, int m, int k, const double2 *Hb, const double2 *betb, double2 *y) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= B) return;
+  const double2 *H = Hb + (size_t)e * (m + 1) * m, *bet = betb + (size_t)e * (m + 1);
+  for (int i = k - 1; i >= 0; --i) {
+    double2 s = bet[i];
+    for (int j = i + 1; j < k; ++j) {
+      double2 h = H[(size_t)j * (m + 1) + i], yj = y[(size_t)j * B + e];
+      s.x -= h.x * yj.x - h.y * yj.y;
+      s.y -= h.x * yj.y + h.y * yj.x;
+    }
+    double2 d = H[(size_t)i * (m + 1) + i];
+    double dd = d.x * d.x + d.y * d.y;
+    y[(size_t)i * B + e] = dd > 0.0 ? make_double2((s.x * d.x + s.y * d.y) / dd, (s.y * d.x - s.x * d.y) / dd)
+                                    : make_double2(0.0, 0.0);
+  }
+  for (int i = k; i < m; ++i) y[(size_t)i * B + e] = make_double2(0.0, 0.0);
+}
+
+// r = b - u + t  (FP64)
+__global__ void bresid_kernel(int64_t n, const double2 *b, const double2 *u, const double2 *t, double2 *r) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n;
+       f += (int64_t)gridDim.x * blockDim.x)
+    r[f] = make_double2(b[f].x - u[f].x + t[f].x, b[f].y - u[f].y + t[f].y);
+}
+
+// warm-start fallback: energies flagged get u = 0, r = b
+__global__ void bfallback_kernel(int64_t n, int B, const int *flag, const double2 *b, double2 *u, double2 *r) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    const int e = (int)(f % B);
+    if (flag[e]) {
+      u[f] = make_double2(0.0, 0.0);
+      r[f] = b[f];
+    }
+  }
+}
+
+// launch shapes tried by the autotuner for a batch of B energies
+std::vector<SpmmConfig> candidates(int B) {
+  std::vector<SpmmConfig> c;
+  if (B == 1) {
+    for (int rpw : {1, 2, 4, 8}) c.push_back(SpmmConfig{rpw, 1, 1});
+    return c;
+  }
+  int el = 1;
+  while (el < B && el < 32) el *= 2;
+  for (int ept : {1, 2, 4}) {
+    if (ept > 1 && el * ept / 2 >= B) continue;  // tile wider than the batch
+    c.push_back(SpmmConfig{1, el, ept});
+    if (el <= 16) c.push_back(SpmmConfig{2, el, ept});
+  }
+  if (el > 1) c.push_back(SpmmConfig{1, el / 2, 1});
+  return c;
+}
+
+}  // namespace
+}  // namespace wpcd

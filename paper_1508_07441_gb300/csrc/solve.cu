@@ -34,23 +34,13 @@
 #include <string>
 #include <vector>
 
+#include "common.cuh"
 #include "wpcd_internal.h"
 
 namespace wpcd {
 namespace {
 
-constexpr double kPi = 3.141592653589793238462643383279502884;
 
-template <typename T>
-struct Cx;
-template <>
-struct Cx<double> {
-  using t = double2;
-};
-template <>
-struct Cx<float> {
-  using t = float2;
-};
 
 // ---------------------------------------------------------------------------
 // resolvent
@@ -159,70 +149,17 @@ __global__ void resolvent_kernel(ResParams R, double *g) {
 // 32 x 64 output tiles: 7 x 7 x 3 = 147 CTAs for the 200-bin, 3-channel,
 // one-energy blocks, close to one wave over the 152 SMs (FP64 work is
 // issue-bound, so SM coverage matters more than data reuse there)
-constexpr int GB_M = 32, GB_N = 64, GB_K = 16, G_THREADS = 256;
-
+// one 32 x 64 output tile per CTA; grid.z walks the channel blocks
 template <typename T, bool SCALE_G, bool SUB>
-__global__ void __launch_bounds__(G_THREADS) gemm_kernel(int n, int64_t ncol, const T *__restrict__ A,
+__global__ void __launch_bounds__(G_THREADS, 2) gemm_kernel(int n, int64_t ncol, const T *__restrict__ A,
                                                          const T *__restrict__ B,
                                                          const T *__restrict__ G,
                                                          const T *__restrict__ S, T *__restrict__ C) {
-  __shared__ T As[GB_K][GB_M + 1];
-  __shared__ T Bs[GB_K][GB_N];
+  __shared__ GemmSmem<T> sm;
   const int b = blockIdx.z;
   const size_t offA = (size_t)b * n * n, offB = (size_t)b * n * ncol;
-  const int row0 = blockIdx.y * GB_M;
-  const int64_t col0 = (int64_t)blockIdx.x * GB_N;
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 16 x 16 threads, 2 x 4 outputs each
-  T acc[2][4] = {};
-  for (int k0 = 0; k0 < n; k0 += GB_K) {
-    for (int t = threadIdx.x; t < GB_M * GB_K; t += G_THREADS) {
-      int r = t / GB_K, kk = t % GB_K;
-      int gr = row0 + r, gk = k0 + kk;
-      As[kk][r] = (gr < n && gk < n) ? A[offA + (size_t)gr * n + gk] : T(0);
-    }
-    for (int t = threadIdx.x; t < GB_K * GB_N; t += G_THREADS) {
-      int kk = t / GB_N, cc = t % GB_N;
-      int gk = k0 + kk;
-      int64_t gc = col0 + cc;
-      T v = T(0);
-      if (gk < n && gc < ncol) {
-        size_t o = offB + (size_t)gk * ncol + gc;
-        if (SCALE_G) {
-          size_t oc = o & ~(size_t)1;  // complex pair (re at even column)
-          T xr = B[oc], xi = B[oc + 1], gr_ = G[oc], gi = G[oc + 1];
-          v = (gc & 1) ? (gr_ * xi + gi * xr) : (gr_ * xr - gi * xi);
-        } else {
-          v = B[o];
-        }
-      }
-      Bs[kk][cc] = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < GB_K; ++kk) {
-      T a[2], bb[4];
-#pragma unroll
-      for (int u = 0; u < 2; ++u) a[u] = As[kk][ty + 16 * u];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) bb[u] = Bs[kk][tx + 16 * u];
-#pragma unroll
-      for (int u = 0; u < 2; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], bb[v], acc[u][v]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int u = 0; u < 2; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      int gr = row0 + ty + 16 * u;
-      int64_t gc = col0 + tx + 16 * v;
-      if (gr < n && gc < ncol) {
-        size_t o = offB + (size_t)gr * ncol + gc;
-        C[o] = SUB ? S[o] - acc[u][v] : acc[u][v];
-      }
-    }
+  gemm_tile<T, SCALE_G, SUB>(n, ncol, A + offA, B + offB, SCALE_G ? G + offB : nullptr, SUB ? S + offB : nullptr,
+                             C + offB, blockIdx.y * GB_M, (int64_t)blockIdx.x * GB_N, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -239,49 +176,6 @@ struct SpmmParams {
   int64_t nnz;
 };
 
-struct AccD {
-  double v;
-  __device__ void zero() { v = 0.0; }
-  __device__ void fma(double a, double b) { v = ::fma(a, b, v); }
-  __device__ void add_shfl(int off) { v += __shfl_xor_sync(0xffffffffu, v, off); }
-  __device__ double value() const { return v; }
-};
-
-struct AccF {  // float-float (Knuth TwoSum on the running sum, exact products)
-  float hi, lo;
-  __device__ void zero() { hi = 0.f; lo = 0.f; }
-  __device__ void add(float x) {
-    float s = __fadd_rn(hi, x);
-    float bb = __fsub_rn(s, hi);
-    float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
-    hi = s;
-    lo = __fadd_rn(lo, e);
-  }
-  __device__ void fma(float a, float b) {
-    float p = __fmul_rn(a, b);
-    float pe = fmaf(a, b, -p);  // exact product error (TwoProduct)
-    add(p);
-    lo = __fadd_rn(lo, pe);
-  }
-  __device__ void add_shfl(int off) {
-    float ohi = __shfl_xor_sync(0xffffffffu, hi, off);
-    float olo = __shfl_xor_sync(0xffffffffu, lo, off);
-    add(ohi);
-    lo = __fadd_rn(lo, olo);
-  }
-  __device__ float value() const { return __fadd_rn(hi, lo); }
-};
-
-template <typename T>
-struct AccOf;
-template <>
-struct AccOf<double> {
-  using t = AccD;
-};
-template <>
-struct AccOf<float> {
-  using t = AccF;
-};
 
 template <typename VT, typename T, int NCH, int EPT>
 __global__ void __launch_bounds__(256) spmm_kernel(SpmmParams S, const VT *__restrict__ val,
@@ -474,63 +368,6 @@ __global__ void bscale_kernel(int64_t n, int B, const typename Cx<T>::t *src, co
   }
 }
 
-// Givens least-squares update of column k for every energy (thread e).
-// Layout per energy e: H + e*(m+1)*m column-major (ld m+1), cs/sn + e*m,
-// bet + e*(m+1); h[i * B + e], hn2[e].
-__global__ void bgivens_kernel(int B, int m, int k, const double2 *h, const double2 *hn2, double2 *Hb,
-                               double2 *csb, double2 *snb, double2 *betb, double *resid,
-                               const double *bnorm) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= B) return;
-  double2 *H = Hb + (size_t)e * (m + 1) * m, *cs = csb + (size_t)e * m, *sn = snb + (size_t)e * m;
-  double2 *bet = betb + (size_t)e * (m + 1);
-  double2 *col = H + (size_t)k * (m + 1);
-  for (int i = 0; i <= k; ++i) col[i] = h[(size_t)i * B + e];
-  col[k + 1] = make_double2(sqrt(fmax(hn2[e].x, 0.0)), 0.0);
-  for (int i = 0; i < k; ++i) {
-    double2 a = col[i], b = col[i + 1], c = cs[i], s = sn[i];
-    // [a'; b'] = [conj(c) conj(s); -s c] [a; b]
-    double2 na = make_double2(c.x * a.x + c.y * a.y + s.x * b.x + s.y * b.y,
-                              c.x * a.y - c.y * a.x + s.x * b.y - s.y * b.x);
-    double2 nb = make_double2(-(s.x * a.x - s.y * a.y) + (c.x * b.x - c.y * b.y),
-                              -(s.x * a.y + s.y * a.x) + (c.x * b.y + c.y * b.x));
-    col[i] = na;
-    col[i + 1] = nb;
-  }
-  double2 a = col[k], b = col[k + 1];
-  double den = sqrt(a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y);
-  double2 c = den > 0 ? make_double2(a.x / den, a.y / den) : make_double2(1.0, 0.0);
-  double2 s = den > 0 ? make_double2(b.x / den, b.y / den) : make_double2(0.0, 0.0);
-  cs[k] = c;
-  sn[k] = s;
-  col[k] = make_double2(den, 0.0);
-  col[k + 1] = make_double2(0.0, 0.0);
-  double2 bk = bet[k];
-  bet[k + 1] = make_double2(-(s.x * bk.x - s.y * bk.y), -(s.x * bk.y + s.y * bk.x));
-  bet[k] = make_double2(c.x * bk.x + c.y * bk.y, c.x * bk.y - c.y * bk.x);
-  resid[e] = sqrt(bet[k + 1].x * bet[k + 1].x + bet[k + 1].y * bet[k + 1].y) / bnorm[e];
-}
-
-// back substitution H y = bet per energy; y[j * B + e]
-__global__ void bbacksub_kernel(int B, int m, int k, const double2 *Hb, const double2 *betb, double2 *y) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= B) return;
-  const double2 *H = Hb + (size_t)e * (m + 1) * m, *bet = betb + (size_t)e * (m + 1);
-  for (int i = k - 1; i >= 0; --i) {
-    double2 s = bet[i];
-    for (int j = i + 1; j < k; ++j) {
-      double2 h = H[(size_t)j * (m + 1) + i], yj = y[(size_t)j * B + e];
-      s.x -= h.x * yj.x - h.y * yj.y;
-      s.y -= h.x * yj.y + h.y * yj.x;
-    }
-    double2 d = H[(size_t)i * (m + 1) + i];
-    double dd = d.x * d.x + d.y * d.y;
-    y[(size_t)i * B + e] = dd > 0.0 ? make_double2((s.x * d.x + s.y * d.y) / dd, (s.y * d.x - s.x * d.y) / dd)
-                                    : make_double2(0.0, 0.0);
-  }
-  for (int i = k; i < m; ++i) y[(size_t)i * B + e] = make_double2(0.0, 0.0);
-}
-
 // u[f] += coef[e] * sum_j y[j * B + e] V_j[f]   (u FP64; V in T;
 // coef = sqrt(nrm2[e].x), or 1 when nrm2 is NULL)
 template <typename T>
@@ -554,24 +391,6 @@ __global__ void bupdate_kernel(int64_t n, int B, int k, const typename Cx<T>::t 
   }
 }
 
-// r = b - u + t  (FP64)
-__global__ void bresid_kernel(int64_t n, const double2 *b, const double2 *u, const double2 *t, double2 *r) {
-  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n;
-       f += (int64_t)gridDim.x * blockDim.x)
-    r[f] = make_double2(b[f].x - u[f].x + t[f].x, b[f].y - u[f].y + t[f].y);
-}
-
-// warm-start fallback: energies flagged get u = 0, r = b
-__global__ void bfallback_kernel(int64_t n, int B, const int *flag, const double2 *b, double2 *u, double2 *r) {
-  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n;
-       f += (int64_t)gridDim.x * blockDim.x) {
-    const int e = (int)(f % B);
-    if (flag[e]) {
-      u[f] = make_double2(0.0, 0.0);
-      r[f] = b[f];
-    }
-  }
-}
 
 // dst32[f] = (float)(src[f] / sqrt(nrm2[e].x))
 __global__ void bnormalize_f32_kernel(int64_t n, int B, const double2 *src, const double2 *nrm2, float2 *dst) {
@@ -670,10 +489,6 @@ __global__ void wynn_kernel(int n, const double2 *c, double2 *work, double2 *est
 
 __global__ void extract_kernel(const double2 *x, int r0, double2 *c_out) { *c_out = x[r0]; }
 
-int grid_for(int64_t n, int threads, int cap = 152 * 8) {
-  int64_t g = (n + threads - 1) / threads;
-  return (int)(g < 1 ? 1 : (g > cap ? cap : g));
-}
 
 // ---------------------------------------------------------------------------
 // K application machinery
@@ -735,23 +550,6 @@ wpcd_status launch_spmm_cfg(const wpcd_problem *pr, const wpcd_P *P, const VT *v
   return e == cudaSuccess ? WPCD_OK : cuda_error(e, "spmm launch");
 }
 
-// launch shapes tried by the autotuner for a batch of B energies
-std::vector<SpmmConfig> candidates(int B) {
-  std::vector<SpmmConfig> c;
-  if (B == 1) {
-    for (int rpw : {1, 2, 4, 8}) c.push_back(SpmmConfig{rpw, 1, 1});
-    return c;
-  }
-  int el = 1;
-  while (el < B && el < 32) el *= 2;
-  for (int ept : {1, 2, 4}) {
-    if (ept > 1 && el * ept / 2 >= B) continue;  // tile wider than the batch
-    c.push_back(SpmmConfig{1, el, ept});
-    if (el <= 16) c.push_back(SpmmConfig{2, el, ept});
-  }
-  if (el > 1) c.push_back(SpmmConfig{1, el / 2, 1});
-  return c;
-}
 
 std::mutex g_tune_mutex;
 
@@ -978,6 +776,10 @@ wpcd_status resolvent(const wpcd_problem *pr, const double *E, int n_E, double *
   return resolvent_impl(pr, E, n_E, g, 0, j0, D, s);
 }
 
+wpcd_status resolvent_minor(const wpcd_problem *pr, const double *E, int n_E, double *g, cudaStream_t s) {
+  return resolvent_impl(pr, E, n_E, g, 1, nullptr, nullptr, s);
+}
+
 // One FP64 K application into caller-provided intermediates (two [dim]
 // complex buffers) with the SpMM shape already tuned for one right-hand side
 // if there is one, else a fixed shape: no allocation, no tuning, no sync.
@@ -1080,20 +882,24 @@ struct Krylov {
   void norms(const typename Cx<U>::t *x, cudaStream_t s) {
     dots<U>(1, x, 0, x, nrm, 0, s);
   }
-  // one Arnoldi step from column k (w holds (I - K) v_k on entry)
-  void step(int k, cudaStream_t s) {
+  // one Arnoldi step from column k (w holds (I - K) v_k on entry); classical
+  // Gram-Schmidt with a second pass (reorth = true) or a single pass
+  void step(int k, cudaStream_t s, bool reorth = true) {
     const int64_t n = (int64_t)dim * B;
     const size_t ld = dim * B;
     const int vg = grid_for(n, 256);
     dots<T>(k + 1, vec(0), ld, wv(), h, 0, s);
     baxpy_kernel<T><<<vg, 256, 0, s>>>(n, B, k + 1, vec(0), ld, h, wv(), -1.0);
-    dots<T>(k + 1, vec(0), ld, wv(), h2, 0, s);
-    baxpy_kernel<T><<<vg, 256, 0, s>>>(n, B, k + 1, vec(0), ld, h2, wv(), -1.0);
-    breduce_kernel<<<((k + 1) * B + 255) / 256, 256, 0, s>>>(k + 1, nblk, B, partial, h, 1);  // h += h2
+    if (reorth) {
+      dots<T>(k + 1, vec(0), ld, wv(), h2, 0, s);
+      baxpy_kernel<T><<<vg, 256, 0, s>>>(n, B, k + 1, vec(0), ld, h2, wv(), -1.0);
+      breduce_kernel<<<((k + 1) * B + 255) / 256, 256, 0, s>>>(k + 1, nblk, B, partial, h, 1);  // h += h2
+      count_launches(2);
+    }
     norms<T>(wv(), s);
     bscale_kernel<T><<<vg, 256, 0, s>>>(n, B, wv(), nrm, vec(k + 1));
     bgivens_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, m, k, h, nrm, H, cs, sn, bet, resid, bnorm);
-    count_launches(5);
+    count_launches(3);
   }
 };
 
@@ -1142,12 +948,33 @@ wpcd_status batch_setup(const wpcd_problem *pr, const double *E, int B, SolveCtx
   return WPCD_OK;
 }
 
-// Born term b = O P0 Vt e0 for every energy of the batch (FP64)
+// Vt e0 for every energy: column 0 of Vt_0 placed at (channel 0, q-bin j0)
+__global__ void born_vt_kernel(int64_t n, int B, int N, int M, const double *Vt0, const int *r0, double2 *y) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    const int e = (int)(f % B);
+    const int64_t r = f / B;  // ch*N*M + i*M + j
+    double v = 0.0;
+    if (r < (int64_t)N * M && (int)(r % M) == r0[e]) v = Vt0[(r / M) * N];  // Vt_0[i][0]
+    y[f] = make_double2(v, 0.0);
+  }
+}
+
+// Born term b = O P0 Vt e0 for every energy of the batch (FP64); the unit
+// vector makes Vt e0 a column of Vt_0, so only the SpMM and the O GEMM run
 wpcd_status born(const wpcd_problem *pr, const wpcd_P *P, SolveCtx &cx, Workspace<double> &ws, cudaStream_t s) {
   const int64_t n = (int64_t)cx.dim * cx.B;
-  bunits_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, cx.B, cx.r0, reinterpret_cast<double2 *>(cx.t));
+  const int N = pr->N, M = pr->M, n_ch = pr->n_ch, B = cx.B;
+  born_vt_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, B, N, M, pr->d.Vt, cx.r0, (double2 *)ws.y);
   count_launches(1);
-  return kapply_ws<double>(pr, P, nullptr, cx.t, cx.b, nullptr, cx.B, ws, s);
+  wpcd_status st = spmm<double>(pr, P, ws.y, ws.z, B, s);
+  if (st != WPCD_OK) return st;
+  const int64_t ncol = 2LL * M * B;
+  dim3 grid((unsigned)((ncol + GB_N - 1) / GB_N), (N + GB_M - 1) / GB_M, n_ch);
+  gemm_kernel<double, false, false><<<grid, G_THREADS, 0, s>>>(N, ncol, pr->d.O, ws.z, nullptr, nullptr, cx.b);
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? WPCD_OK : cuda_error(e, "born launch");
 }
 
 // Plain FP64 Krylov on (I - K) u = b, started from u (0 or a warm start).
@@ -1299,7 +1126,9 @@ wpcd_status solve_mixed(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solv
     for (int k = 0; k < m; ++k) {
       wpcd_status st = kapply_ws<float>(pr, P, cx.g32, (float *)kr.vec(k), kr.w, (float *)kr.vec(k), B, ws32, s);
       if (st != WPCD_OK) return st;
-      kr.step(k, s);
+      // single-pass Gram-Schmidt: the short FP32 cycle only has to cut the
+      // residual, whose FP64 value the refinement loop recomputes and judges
+      kr.step(k, s, false);
     }
     bbacksub_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, m, m, kr.H, kr.bet, kr.y);
     // u += |r| (V y)   (FP64 accumulation of the FP32 correction)

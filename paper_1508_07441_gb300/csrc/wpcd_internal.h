@@ -137,4 +137,10 @@ wpcd_status kapply_scratch(const wpcd_problem *pr, const wpcd_P *P, const double
                            double *y, double *scratch_y, double *scratch_z, cudaStream_t s);
 wpcd_status born_vectors(wpcd_problem *pr, const wpcd_P *P, const double *E, int n_E, double *b_major,
                          cudaStream_t s);
+// G1 of n_E energies in the batched layout (element (r, e) at r * n_E + e)
+wpcd_status resolvent_minor(const wpcd_problem *pr, const double *E, int n_E, double *g, cudaStream_t s);
+// group.cu
+wpcd_status solve_group(int n_prob, wpcd_problem *const *prs, const wpcd_P *const *Ps, const double *const *E,
+                        const int *n_E, const wpcd_solve_opts *o, double *const *U00, wpcd_solve_stats *const *st,
+                        cudaStream_t s);
 }  // namespace wpcd

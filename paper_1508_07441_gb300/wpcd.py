@@ -71,6 +71,10 @@ _SIGS = {
     "wpcd_kapply": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "wpcd_solve": (ctypes.c_int, [_P, _P, _D, ctypes.c_int, ctypes.POINTER(wpcd_solve_opts), _D,
                                   ctypes.POINTER(wpcd_solve_stats), _P]),
+    "wpcd_solve_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                        ctypes.POINTER(_D), _I, ctypes.POINTER(wpcd_solve_opts),
+                                        ctypes.POINTER(_D), ctypes.POINTER(ctypes.POINTER(wpcd_solve_stats)),
+                                        _P]),
     "wpcd_tune_spmm": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P, _I, _I, _I]),
     "wpcd_born": (ctypes.c_int, [_P, _P, _D, ctypes.c_int, _P, _P]),
     "wpcd_kapply_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -154,6 +158,32 @@ def _tensor_ptr(t):
 # ---------------------------------------------------------------------------
 def wpcd_launch_count() -> int:
     return int(lib().wpcd_launch_count())
+
+
+def wpcd_solve_batch(problems, Ps, energies, max_iter=100, tol=1e-10, check_every=4,
+                     precision=WPCD_SOLVE_FP64, inner_iter=0, max_outer=0, use_graph=1, stream=None,
+                     allow=(WPCD_ENOCONV, WPCD_EBREAKDOWN)):
+    """Grouped solve of several problems (uneven grids) in one iteration.
+    problems, Ps: sequences of Problem / PMatrix; energies: sequence of
+    arrays.  Returns (list of complex U00 arrays, list of stats lists, status)."""
+    n = len(problems)
+    if len(Ps) != n or len(energies) != n:
+        raise ValueError("problems, Ps and energies must have the same length")
+    Es = [np.ascontiguousarray(np.atleast_1d(e), dtype=np.float64) for e in energies]
+    Us = [np.zeros(2 * len(e)) for e in Es]
+    stats = [(wpcd_solve_stats * len(e))() for e in Es]
+    hp = (_P * n)(*[p.handle for p in problems])
+    hP = (_P * n)(*[P.handle for P in Ps])
+    hE = (_D * n)(*[_dp(e) for e in Es])
+    hU = (_D * n)(*[_dp(u) for u in Us])
+    hS = (ctypes.POINTER(wpcd_solve_stats) * n)(
+        *[ctypes.cast(st, ctypes.POINTER(wpcd_solve_stats)) for st in stats])
+    nE = (ctypes.c_int * n)(*[len(e) for e in Es])
+    opts = wpcd_solve_opts(WPCD_SUM_KRYLOV, max_iter, 4, tol, check_every, precision, 0,
+                           inner_iter, max_outer, use_graph, None, None)
+    st = lib().wpcd_solve_batch(n, hp, hP, hE, nE, ctypes.byref(opts), hU, hS, _stream_ptr(stream))
+    check(st, allow=allow)
+    return [u.view(np.complex128) for u in Us], [list(x) for x in stats], st
 
 
 def wpcd_tangent_edges(n_bins: int, k_max: float) -> np.ndarray:
