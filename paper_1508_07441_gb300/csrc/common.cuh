@@ -29,16 +29,17 @@ struct Cx<float> {
   using t = float2;
 };
 
-// SpMM accumulators: plain FP64, or compensated FP32
+// SpMM accumulators: plain FP64 sums, or FP32 float-float sums (Knuth's
+// TwoSum on the running sum, the rounding errors gathered in lo)
 struct AccD {
   double v;
   __device__ void zero() { v = 0.0; }
-  __device__ void fma(double a, double b) { v = ::fma(a, b, v); }
+  __device__ void add(double x) { v += x; }
   __device__ void add_shfl(int off) { v += __shfl_xor_sync(0xffffffffu, v, off); }
   __device__ double value() const { return v; }
 };
 
-struct AccF {  // float-float (Knuth TwoSum on the running sum, exact products)
+struct AccF {
   float hi, lo;
   __device__ void zero() { hi = 0.f; lo = 0.f; }
   __device__ void add(float x) {
@@ -47,12 +48,6 @@ struct AccF {  // float-float (Knuth TwoSum on the running sum, exact products)
     float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
     hi = s;
     lo = __fadd_rn(lo, e);
-  }
-  __device__ void fma(float a, float b) {
-    float p = __fmul_rn(a, b);
-    float pe = fmaf(a, b, -p);  // exact product error (TwoProduct)
-    add(p);
-    lo = __fadd_rn(lo, pe);
   }
   __device__ void add_shfl(int off) {
     float ohi = __shfl_xor_sync(0xffffffffu, hi, off);
@@ -73,6 +68,73 @@ template <>
 struct AccOf<float> {
   using t = AccF;
 };
+
+// nonzeros a lane keeps in flight in the SpMM (fewer for wide channel sets,
+// whose value blocks take more registers)
+template <int NCH>
+struct SpmmUnroll {
+  static constexpr int value = NCH <= 3 ? 4 : 2;
+};
+
+// The sums of one block-CSR row for the SpMM kernels.  A lane takes the
+// nonzeros o = b + nl, b + nl + nl_count, ... of its row, U at a time (their
+// column and value loads issued together), and for each of its EPT energies
+// forms the block of those U nonzeros with plain FMAs and adds it to the
+// accumulator.  For FP32 this is blocked summation with a compensated sum of
+// the block partials (FABsum, Blanchard, Higham and Mary, SIAM J. Sci.
+// Comput. 2020): the error grows with the number of blocks only through the
+// float-float accumulator, and inside a block with its few terms.  FP64
+// sums the block partials plainly.  y points at the problem's own vector
+// block ([n_ch][n_cells][B] complex).
+template <typename VT, typename T, int NCH, int EPT>
+__device__ __forceinline__ void spmm_row(int64_t b, int64_t e, int nl, int nl_count, const int32_t *__restrict__ col,
+                                         const VT *__restrict__ val, int64_t nnz,
+                                         const typename Cx<T>::t *__restrict__ y, int n_cells, int B, int e_base,
+                                         int el, int el_n, typename AccOf<T>::t (&acc)[NCH][EPT][2]) {
+  using C2 = typename Cx<T>::t;
+  constexpr int NPAIR = pair_count(NCH);
+  constexpr int U = SpmmUnroll<NCH>::value;
+  for (int64_t o0 = b + nl; o0 < e; o0 += (int64_t)U * nl_count) {
+    int tc[U];
+    T v[U][NPAIR];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t o = o0 + (int64_t)u * nl_count;
+      const bool ok = o < e;
+      tc[u] = ok ? __ldg(col + o) : -1;
+#pragma unroll
+      for (int m = 0; m < NPAIR; ++m) v[u][m] = ok ? (T)__ldg(val + (size_t)m * nnz + o) : T(0);
+    }
+#pragma unroll
+    for (int t = 0; t < EPT; ++t) {
+      const int en = e_base + el + el_n * t;
+      if (en < B) {
+        T part[NCH][2];
+#pragma unroll
+        for (int l = 0; l < NCH; ++l) part[l][0] = part[l][1] = T(0);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (tc[u] >= 0) {
+            C2 yv[NCH];
+#pragma unroll
+            for (int l = 0; l < NCH; ++l) yv[l] = __ldg(y + ((size_t)l * n_cells + tc[u]) * B + en);
+#pragma unroll
+            for (int m = 0; m < NPAIR; ++m) {
+              const int l = pair_first(NCH, m), lp = pair_second(NCH, m);
+              part[l][0] = fma(v[u][m], yv[lp].x, part[l][0]);
+              part[l][1] = fma(v[u][m], yv[lp].y, part[l][1]);
+            }
+          }
+        }
+#pragma unroll
+        for (int l = 0; l < NCH; ++l) {
+          acc[l][t][0].add(part[l][0]);
+          acc[l][t][1].add(part[l][1]);
+        }
+      }
+    }
+  }
+}
 
 int grid_for(int64_t n, int threads, int cap = 152 * 8) {
   int64_t g = (n + threads - 1) / threads;
@@ -192,6 +254,20 @@ __global__ void bgivens_kernel(int B, int m, int k, const double2 *h, const doub
   bet[k + 1] = make_double2(-(s.x * bk.x - s.y * bk.y), -(s.x * bk.y + s.y * bk.x));
   bet[k] = make_double2(c.x * bk.x + c.y * bk.y, c.x * bk.y - c.y * bk.x);
   resid[e] = sqrt(bet[k + 1].x * bet[k + 1].x + bet[k + 1].y * bet[k + 1].y) / bnorm[e];
+}
+
+// c[j * S + s] = y[j * S + s] * sqrt(nrm2[s].x) (or y with nrm2 NULL) in the
+// basis precision T: the coefficients of the correction V c, so that the
+// elementwise update does no FP64 arithmetic but the final add
+template <typename T>
+__global__ void bupdate_coef_kernel(int k, int S, const double2 *__restrict__ y, const double2 *__restrict__ nrm2,
+                                    typename Cx<T>::t *__restrict__ c) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= k * S) return;
+  const int s = idx % S;
+  const double sc = nrm2 ? sqrt(fmax(nrm2[s].x, 0.0)) : 1.0;
+  c[idx].x = (T)(y[idx].x * sc);
+  c[idx].y = (T)(y[idx].y * sc);
 }
 
 // back substitution H y = bet per energy; y[j * B + e]

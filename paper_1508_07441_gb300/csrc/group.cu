@@ -117,7 +117,7 @@ __device__ __forceinline__ const float *mat_of<float>(const GProb &P, bool O) {
 // grouped block GEMM: for every (problem, channel) C = A B' (A = Vt or O)
 // ---------------------------------------------------------------------------
 template <typename T, bool SCALE_G, bool SUB>
-__global__ void __launch_bounds__(G_THREADS, 2) ggemm_kernel(const GMeta *__restrict__ gm,
+__global__ void __launch_bounds__(G_THREADS) ggemm_kernel(const GMeta *__restrict__ gm,
                                                              const GProb *__restrict__ gp, int use_O,
                                                              const T *__restrict__ X, const T *__restrict__ G,
                                                              const T *__restrict__ S, T *__restrict__ C) {
@@ -165,7 +165,6 @@ __global__ void __launch_bounds__(256) gspmm_kernel(const GMeta *__restrict__ gm
                                                     typename Cx<T>::t *__restrict__ z) {
   using C2 = typename Cx<T>::t;
   using Acc = typename AccOf<T>::t;
-  constexpr int NPAIR = pair_count(NCH);
   __shared__ int coff[kMaxGroup + 1];
   __shared__ GProb sp[kMaxGroup];
   const int n = gm->n;
@@ -203,27 +202,7 @@ __global__ void __launch_bounds__(256) gspmm_kernel(const GMeta *__restrict__ gm
         acc[l][t][1].zero();
       }
     const int64_t b = active ? P.row_ptr[c] : 0, e = active ? P.row_ptr[c + 1] : 0;
-    for (int64_t o = b + nl; o < e; o += nl_count) {
-      const int tc = __ldg(P.col + o);
-      T v[NPAIR];
-#pragma unroll
-      for (int m = 0; m < NPAIR; ++m) v[m] = (T)__ldg(val + (size_t)m * P.nnz + o);
-#pragma unroll
-      for (int t = 0; t < EPT; ++t) {
-        const int en = e_base + el + el_n * t;
-        if (en < B) {
-          C2 yv[NCH];
-#pragma unroll
-          for (int l = 0; l < NCH; ++l) yv[l] = __ldg(yg + ((size_t)l * n_cells + tc) * B + en);
-#pragma unroll
-          for (int m = 0; m < NPAIR; ++m) {
-            const int l = pair_first(NCH, m), lp = pair_second(NCH, m);
-            acc[l][t][0].fma(v[m], yv[lp].x);
-            acc[l][t][1].fma(v[m], yv[lp].y);
-          }
-        }
-      }
-    }
+    spmm_row<VT, T, NCH, EPT>(b, e, nl, nl_count, P.col, val, P.nnz, yg, n_cells, B, e_base, el, el_n, acc);
     for (int off = el_n; off < lpr; off <<= 1)
 #pragma unroll
       for (int l = 0; l < NCH; ++l)
@@ -310,9 +289,13 @@ __global__ void __launch_bounds__(GV_THREADS) gdot_kernel(const GMeta *__restric
   }
 }
 
-// out[j * S + s] (+)= sum of system s's block partials
+// out[j * S + s] (+)= sum of system s's block partials; also, in the vector
+// precision T, coef = sign * (this pass's sum) and, for a norm pass,
+// inv = 1 / sqrt(sum.x) (0 for a zero norm)
+template <typename T>
 __global__ void greduce_kernel(const GMeta *__restrict__ gm, int nv, int NBT, const double2 *__restrict__ partial,
-                               double2 *__restrict__ out, int accumulate) {
+                               double2 *__restrict__ out, int accumulate, typename Cx<T>::t *coef, double sign,
+                               T *inv) {
   const int S = gm->S;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nv * S) return;
@@ -325,6 +308,11 @@ __global__ void greduce_kernel(const GMeta *__restrict__ gm, int nv, int NBT, co
     sx += p.x;
     sy += p.y;
   }
+  if (coef) {
+    coef[idx].x = (T)(sign * sx);
+    coef[idx].y = (T)(sign * sy);
+  }
+  if (inv) inv[idx] = (T)(sx > 0.0 ? 1.0 / sqrt(sx) : 0.0);
   if (accumulate) {
     out[idx].x += sx;
     out[idx].y += sy;
@@ -333,63 +321,60 @@ __global__ void greduce_kernel(const GMeta *__restrict__ gm, int nv, int NBT, co
   }
 }
 
-// w[f] += sign * sum_j h[j * S + s(f)] V_j[f]
+// w[f] += sum_j c[j * S + s(f)] V_j[f]   (coefficients in the vector precision)
 template <typename T>
 __global__ void gaxpy_kernel(const GMeta *__restrict__ gm, int64_t len, int nv,
-                             const typename Cx<T>::t *__restrict__ V, size_t ld, const double2 *__restrict__ h,
-                             typename Cx<T>::t *__restrict__ w, double sign) {
+                             const typename Cx<T>::t *__restrict__ V, size_t ld,
+                             const typename Cx<T>::t *__restrict__ c, typename Cx<T>::t *__restrict__ w) {
   __shared__ SegSmem sm;
   load_segs(gm, sm);
   const int n = gm->n, S = gm->S;
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < len; f += (int64_t)gridDim.x * blockDim.x) {
     const int s = system_of(sm, n, f);
     T ax = w[f].x, ay = w[f].y;
-    const T sg = (T)sign;
     for (int j = 0; j < nv; ++j) {
       const auto a = V[(size_t)j * ld + f];
-      const double2 c = h[(size_t)j * S + s];
-      const T cx = sg * (T)c.x, cy = sg * (T)c.y;
-      ax = fma(cx, a.x, fma(-cy, a.y, ax));
-      ay = fma(cx, a.y, fma(cy, a.x, ay));
+      const auto cj = c[(size_t)j * S + s];
+      ax = fma(cj.x, a.x, fma(-cj.y, a.y, ax));
+      ay = fma(cj.x, a.y, fma(cj.y, a.x, ay));
     }
     w[f].x = ax;
     w[f].y = ay;
   }
 }
 
-// dst[f] = src[f] / sqrt(nrm2[s(f)].x)   (0 if the norm is 0)
+// dst[f] = src[f] * inv[s(f)]
 template <typename T>
 __global__ void gscale_kernel(const GMeta *__restrict__ gm, int64_t len, const typename Cx<T>::t *src,
-                              const double2 *__restrict__ nrm2, typename Cx<T>::t *dst) {
+                              const T *__restrict__ inv, typename Cx<T>::t *dst) {
   __shared__ SegSmem sm;
   load_segs(gm, sm);
   const int n = gm->n;
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < len; f += (int64_t)gridDim.x * blockDim.x) {
-    const int s = system_of(sm, n, f);
-    const T sc = (T)(nrm2[s].x > 0.0 ? 1.0 / sqrt(nrm2[s].x) : 0.0);
+    const T sc = inv[system_of(sm, n, f)];
     dst[f].x = src[f].x * sc;
     dst[f].y = src[f].y * sc;
   }
 }
 
-// dst32[f] = (float)(src[f] / sqrt(nrm2[s(f)].x))
+// dst32[f] = (float)(src[f] * inv[s(f)])
 __global__ void gnormalize_f32_kernel(const GMeta *__restrict__ gm, int64_t len, const double2 *__restrict__ src,
-                                      const double2 *__restrict__ nrm2, float2 *__restrict__ dst) {
+                                      const double *__restrict__ inv, float2 *__restrict__ dst) {
   __shared__ SegSmem sm;
   load_segs(gm, sm);
   const int n = gm->n;
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < len; f += (int64_t)gridDim.x * blockDim.x) {
-    const int s = system_of(sm, n, f);
-    const double sc = nrm2[s].x > 0.0 ? 1.0 / sqrt(nrm2[s].x) : 0.0;
+    const double sc = inv[system_of(sm, n, f)];
     dst[f] = make_float2((float)(src[f].x * sc), (float)(src[f].y * sc));
   }
 }
 
-// u[f] += coef[s] * sum_j y[j * S + s] V_j[f]  (coef = sqrt(nrm2[s].x), or 1)
+// u[f] += sum_j c[j * S + s] V_j[f]: the correction formed in the basis
+// precision T (coefficients from bupdate_coef_kernel), added to u in FP64
 template <typename T>
 __global__ void gupdate_kernel(const GMeta *__restrict__ gm, int64_t len, int k,
-                               const typename Cx<T>::t *__restrict__ V, size_t ld, const double2 *__restrict__ y,
-                               const double2 *__restrict__ nrm2, double2 *__restrict__ u) {
+                               const typename Cx<T>::t *__restrict__ V, size_t ld,
+                               const typename Cx<T>::t *__restrict__ c, double2 *__restrict__ u) {
   __shared__ SegSmem sm;
   load_segs(gm, sm);
   const int n = gm->n, S = gm->S;
@@ -398,14 +383,12 @@ __global__ void gupdate_kernel(const GMeta *__restrict__ gm, int64_t len, int k,
     T ax = T(0), ay = T(0);
     for (int j = 0; j < k; ++j) {
       const auto a = V[(size_t)j * ld + f];
-      const double2 c = y[(size_t)j * S + s];
-      const T cx = (T)c.x, cy = (T)c.y;
-      ax = fma(cx, a.x, fma(-cy, a.y, ax));
-      ay = fma(cx, a.y, fma(cy, a.x, ay));
+      const auto cj = c[(size_t)j * S + s];
+      ax = fma(cj.x, a.x, fma(-cj.y, a.y, ax));
+      ay = fma(cj.x, a.y, fma(cj.y, a.x, ay));
     }
-    const double sc = nrm2 ? sqrt(nrm2[s].x) : 1.0;
-    u[f].x += sc * (double)ax;
-    u[f].y += sc * (double)ay;
+    u[f].x += (double)ax;
+    u[f].y += (double)ay;
   }
 }
 
@@ -621,6 +604,8 @@ struct GKrylov {
   double2 *H = nullptr, *cs = nullptr, *sn = nullptr, *bet = nullptr;
   double2 *h = nullptr, *h2 = nullptr, *nrm = nullptr, *y = nullptr, *partial = nullptr;
   double *resid = nullptr, *bnorm = nullptr;
+  C2 *hc = nullptr;  // axpy / update coefficients in T [(m+1)][S]
+  T *inv = nullptr;  // 1 / norm per system in T [S]
   DevFree mem;
   cudaError_t alloc(const Group &g, int m_, bool vectors = true) {
     gr = &g;
@@ -643,37 +628,43 @@ struct GKrylov {
     if ((e = mem.alloc(&partial, sizeof(double2) * (size_t)(m + 1) * g.nbt() * kMaxGroupE)) != cudaSuccess)
       return e;
     if ((e = mem.alloc(&resid, sizeof(double) * S)) != cudaSuccess) return e;
+    if ((e = mem.alloc(&hc, sizeof(C2) * (size_t)S * (m + 1))) != cudaSuccess) return e;
+    if ((e = mem.alloc(&inv, sizeof(T) * (size_t)S)) != cudaSuccess) return e;
     return mem.alloc(&bnorm, sizeof(double) * S);
   }
   C2 *vec(int j) { return reinterpret_cast<C2 *>(V) + (size_t)j * L; }
   C2 *wv() { return reinterpret_cast<C2 *>(w); }
+  // out[j * S + s] = <V_j, x>; with hcoef also hc = -out in T
   template <typename U>
   void dots(int nv, const typename Cx<U>::t *base, size_t ld, const typename Cx<U>::t *x, double2 *out,
-            int accumulate, cudaStream_t s) {
+            int accumulate, cudaStream_t s, bool hcoef = false, bool scale = false) {
     gdot_kernel<U><<<gr->nbt(), gr->dot_block(), 0, s>>>(gr->d_meta, nv, base, ld, x, partial);
-    greduce_kernel<<<(nv * S + 255) / 256, 256, 0, s>>>(gr->d_meta, nv, gr->nbt(), partial, out, accumulate);
+    greduce_kernel<T><<<(nv * S + 255) / 256, 256, 0, s>>>(gr->d_meta, nv, gr->nbt(), partial, out, accumulate,
+                                                           hcoef ? hc : nullptr, -1.0, scale ? inv : nullptr);
     count_launches(2);
   }
+  // nrm[s] = |x_s|^2 (and inv = 1 / |x_s| in T with scale)
   template <typename U>
-  void norms(const typename Cx<U>::t *x, cudaStream_t s) {
-    dots<U>(1, x, 0, x, nrm, 0, s);
+  void norms(const typename Cx<U>::t *x, cudaStream_t s, bool scale = false) {
+    dots<U>(1, x, 0, x, nrm, 0, s, false, scale);
   }
   // one Arnoldi step from column k (w = (I - K) v_k on entry); classical
   // Gram-Schmidt with a second pass (reorth) or a single pass
   void step(int k, cudaStream_t s, bool reorth) {
     const int vg = grid_for(L, 256);
     const size_t ld = (size_t)L;
-    dots<T>(k + 1, vec(0), ld, wv(), h, 0, s);
-    gaxpy_kernel<T><<<vg, 256, 0, s>>>(gr->d_meta, L, k + 1, vec(0), ld, h, wv(), -1.0);
+    dots<T>(k + 1, vec(0), ld, wv(), h, 0, s, true);
+    gaxpy_kernel<T><<<vg, 256, 0, s>>>(gr->d_meta, L, k + 1, vec(0), ld, hc, wv());
     if (reorth) {
-      dots<T>(k + 1, vec(0), ld, wv(), h2, 0, s);
-      gaxpy_kernel<T><<<vg, 256, 0, s>>>(gr->d_meta, L, k + 1, vec(0), ld, h2, wv(), -1.0);
+      dots<T>(k + 1, vec(0), ld, wv(), h2, 0, s, true);
+      gaxpy_kernel<T><<<vg, 256, 0, s>>>(gr->d_meta, L, k + 1, vec(0), ld, hc, wv());
       // h += h2: the second pass's coefficients, summed from its partials
-      greduce_kernel<<<((k + 1) * S + 255) / 256, 256, 0, s>>>(gr->d_meta, k + 1, gr->nbt(), partial, h, 1);
+      greduce_kernel<T><<<((k + 1) * S + 255) / 256, 256, 0, s>>>(gr->d_meta, k + 1, gr->nbt(), partial, h, 1,
+                                                                   nullptr, 0.0, nullptr);
       count_launches(2);
     }
-    norms<T>(wv(), s);
-    gscale_kernel<T><<<vg, 256, 0, s>>>(gr->d_meta, L, wv(), nrm, vec(k + 1));
+    norms<T>(wv(), s, true);
+    gscale_kernel<T><<<vg, 256, 0, s>>>(gr->d_meta, L, wv(), inv, vec(k + 1));
     bgivens_kernel<<<(S + 127) / 128, 128, 0, s>>>(S, m, k, h, nrm, H, cs, sn, bet, resid, bnorm);
     count_launches(3);
   }
@@ -708,7 +699,8 @@ wpcd_status gsolve_fp64(const Group &gr, const wpcd_solve_opts &o, GCtx &cx, GKr
     if (!(bn[e] > 0.0)) return set_error(WPCD_EBREAKDOWN, "Born term is zero");
     bet0[(size_t)e * (m + 1)] = make_double2(bn[e], 0.0);
   }
-  gscale_kernel<double><<<vg, 256, 0, s>>>(gr.d_meta, L, (const double2 *)cx.b, kr.nrm, kr.vec(0));
+  kr.norms<double>((const double2 *)cx.b, s, true);  // inv = 1 / |b| for v0
+  gscale_kernel<double><<<vg, 256, 0, s>>>(gr.d_meta, L, (const double2 *)cx.b, kr.inv, kr.vec(0));
   count_launches(1);
   WPCD_CUDA_TRY(cudaMemsetAsync(kr.H, 0, sizeof(double2) * (size_t)S * (m + 1) * m, s));
   WPCD_CUDA_TRY(cudaMemcpyAsync(kr.bet, bet0.data(), sizeof(double2) * bet0.size(), cudaMemcpyHostToDevice, s));
@@ -745,8 +737,9 @@ wpcd_status gsolve_fp64(const Group &gr, const wpcd_solve_opts &o, GCtx &cx, GKr
     }
   }
   bbacksub_kernel<<<(S + 127) / 128, 128, 0, s>>>(S, m, k, kr.H, kr.bet, kr.y);
-  gupdate_kernel<double><<<vg, 256, 0, s>>>(gr.d_meta, L, k, kr.vec(0), (size_t)L, kr.y, nullptr, (double2 *)cx.u);
-  count_launches(2);
+  bupdate_coef_kernel<double><<<std::max(1, (k * S + 255) / 256), 256, 0, s>>>(k, S, kr.y, nullptr, kr.hc);
+  gupdate_kernel<double><<<vg, 256, 0, s>>>(gr.d_meta, L, k, kr.vec(0), (size_t)L, kr.hc, (double2 *)cx.u);
+  count_launches(3);
   return WPCD_OK;
 }
 
@@ -788,8 +781,9 @@ wpcd_status gsolve_mixed(const Group &gr, const wpcd_solve_opts &o, GCtx &cx, GK
       kr.step(k, s, false);
     }
     bbacksub_kernel<<<(S + 127) / 128, 128, 0, s>>>(S, m, m, kr.H, kr.bet, kr.y);
-    gupdate_kernel<float><<<vg, 256, 0, s>>>(gr.d_meta, L, m, kr.vec(0), (size_t)L, kr.y, k64.nrm, (double2 *)cx.u);
-    count_launches(2);
+    bupdate_coef_kernel<float><<<(m * S + 255) / 256, 256, 0, s>>>(m, S, kr.y, k64.nrm, kr.hc);
+    gupdate_kernel<float><<<vg, 256, 0, s>>>(gr.d_meta, L, m, kr.vec(0), (size_t)L, kr.hc, (double2 *)cx.u);
+    count_launches(3);
     return WPCD_OK;
   };
   cudaGraphExec_t exec = nullptr;
@@ -812,7 +806,7 @@ wpcd_status gsolve_mixed(const Group &gr, const wpcd_solve_opts &o, GCtx &cx, GK
     } else {
       cudaMemcpyAsync(cx.r, cx.b, 16 * L, cudaMemcpyDeviceToDevice, s);
     }
-    k64.norms<double>((const double2 *)cx.r, s);
+    k64.norms<double>((const double2 *)cx.r, s, true);  // |r|^2 and 1 / |r|
     cudaMemcpyAsync(nr.data(), k64.nrm, sizeof(double2) * S, cudaMemcpyDeviceToHost, s);
     cudaError_t ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) {
@@ -833,7 +827,7 @@ wpcd_status gsolve_mixed(const Group &gr, const wpcd_solve_opts &o, GCtx &cx, GK
     }
     if (done || outer == max_outer) break;
     ++n_outer;
-    gnormalize_f32_kernel<<<vg, 256, 0, s>>>(gr.d_meta, L, (const double2 *)cx.r, k64.nrm, kr.vec(0));
+    gnormalize_f32_kernel<<<vg, 256, 0, s>>>(gr.d_meta, L, (const double2 *)cx.r, k64.inv, kr.vec(0));
     count_launches(1);
     if (o.use_graph && s != nullptr) {  // the legacy default stream cannot be captured
       if (!exec) {

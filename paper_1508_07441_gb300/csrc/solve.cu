@@ -32,6 +32,7 @@
 #include <mutex>
 #include <sstream>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -78,6 +79,7 @@ struct ResParams {
   const double *Elo, *Ehi;     // per energy
   const double *gl_t, *gl_w;   // 32-point GL rule
   const double *gl8_t, *gl8_w; // 8-point GL rule
+  const double *gl4_t, *gl4_w; // 4-point GL rule
 };
 
 __global__ void resolvent_kernel(ResParams R, double *g) {
@@ -108,9 +110,11 @@ __global__ void resolvent_kernel(ResParams R, double *g) {
     if (no_sign_change && fabs(D) < 0.05 * dist) {
       // smooth integrand q^2 log(1 + D / (E_lo - eps - 3q^2/4)); its
       // singularities sit at q^2 = (E_lo - eps)/(3/4) and (E_hi - eps)/(3/4),
-      // outside the bin.  Measured in half bin widths from the bin centre,
-      // a distance rho > 4 makes the 8-point GL error ~ rho^-16 < 1e-14
-      // (Bernstein ellipse bound); otherwise 32 points.
+      // outside the bin.  At a distance rho, in half bin widths, from the bin
+      // centre the n-point GL error falls like r^-2n with r = rho +
+      // sqrt(rho^2 - 1) (Bernstein ellipse): rho > 32 gives r > 63 and a
+      // 4-point error below 1e-14, rho > 4 gives r > 7.8 and an 8-point error
+      // below 1e-14; otherwise 32 points.
       double half = 0.5 * (qb - qa), mid = 0.5 * (qb + qa), s = 0.0;
       double rho = 1e300;
       for (double a2 : {(Elo - ek) / 0.75, (Ehi - ek) / 0.75}) {
@@ -119,8 +123,9 @@ __global__ void resolvent_kernel(ResParams R, double *g) {
         double d = a2 > 0.0 ? fabs(qs - mid) : sqrt(mid * mid + qs * qs);
         rho = fmin(rho, d / half);
       }
-      const int npts = rho > 4.0 ? 8 : 32;
-      const double *t = npts == 8 ? R.gl8_t : R.gl_t, *wg = npts == 8 ? R.gl8_w : R.gl_w;
+      const int npts = rho > 32.0 ? 4 : (rho > 4.0 ? 8 : 32);
+      const double *t = npts == 4 ? R.gl4_t : (npts == 8 ? R.gl8_t : R.gl_t);
+      const double *wg = npts == 4 ? R.gl4_w : (npts == 8 ? R.gl8_w : R.gl_w);
       for (int m = 0; m < npts; ++m) {
         double q = mid + half * t[m];
         s += wg[m] * q * q * log1p(D / (Elo - ek - 0.75 * q * q));
@@ -151,7 +156,7 @@ __global__ void resolvent_kernel(ResParams R, double *g) {
 // issue-bound, so SM coverage matters more than data reuse there)
 // one 32 x 64 output tile per CTA; grid.z walks the channel blocks
 template <typename T, bool SCALE_G, bool SUB>
-__global__ void __launch_bounds__(G_THREADS, 2) gemm_kernel(int n, int64_t ncol, const T *__restrict__ A,
+__global__ void __launch_bounds__(G_THREADS) gemm_kernel(int n, int64_t ncol, const T *__restrict__ A,
                                                          const T *__restrict__ B,
                                                          const T *__restrict__ G,
                                                          const T *__restrict__ S, T *__restrict__ C) {
@@ -167,7 +172,7 @@ __global__ void __launch_bounds__(G_THREADS, 2) gemm_kernel(int n, int64_t ncol,
 // A warp holds `rpw` rows; each row's 32/rpw lanes split into `el` energy
 // lanes times 32/(rpw el) nonzero lanes; every lane keeps EPT energies
 // (RHS tile = el * EPT, grid.y walks the tiles).  Values pair-major.
-// FP64 sums in double; FP32 sums compensated (float-float).
+// FP64 sums in double; FP32 sums blocked and compensated (spmm_row).
 // ---------------------------------------------------------------------------
 struct SpmmParams {
   int n_cells, B, rpw, el;
@@ -183,7 +188,6 @@ __global__ void __launch_bounds__(256) spmm_kernel(SpmmParams S, const VT *__res
                                                    typename Cx<T>::t *__restrict__ z) {
   using C2 = typename Cx<T>::t;
   using Acc = typename AccOf<T>::t;
-  constexpr int NPAIR = pair_count(NCH);
   const int lane = threadIdx.x & 31;
   const int lpr = 32 / S.rpw;          // lanes per row
   const int nl_count = lpr / S.el;     // nonzero lanes per row
@@ -207,27 +211,7 @@ __global__ void __launch_bounds__(256) spmm_kernel(SpmmParams S, const VT *__res
         acc[l][t][1].zero();
       }
     const int64_t b = active ? S.row_ptr[c] : 0, e = active ? S.row_ptr[c + 1] : 0;
-    for (int64_t o = b + nl; o < e; o += nl_count) {
-      const int tc = __ldg(S.col + o);
-      T v[NPAIR];
-#pragma unroll
-      for (int m = 0; m < NPAIR; ++m) v[m] = (T)__ldg(val + (size_t)m * S.nnz + o);
-#pragma unroll
-      for (int t = 0; t < EPT; ++t) {
-        const int en = e_base + el + S.el * t;
-        if (en < B) {
-          C2 yv[NCH];
-#pragma unroll
-          for (int l = 0; l < NCH; ++l) yv[l] = __ldg(y + ((size_t)l * S.n_cells + tc) * B + en);
-#pragma unroll
-          for (int m = 0; m < NPAIR; ++m) {
-            const int l = pair_first(NCH, m), lp = pair_second(NCH, m);
-            acc[l][t][0].fma(v[m], yv[lp].x);
-            acc[l][t][1].fma(v[m], yv[lp].y);
-          }
-        }
-      }
-    }
+    spmm_row<VT, T, NCH, EPT>(b, e, nl, nl_count, S.col, val, S.nnz, y, S.n_cells, B, e_base, el, S.el, acc);
     // reduce over the nonzero lanes of the row (xor offsets el .. lpr/2)
     for (int off = S.el; off < lpr; off <<= 1)
 #pragma unroll
@@ -313,9 +297,13 @@ __global__ void __launch_bounds__(V_THREADS) bdot_kernel(int rows, int B, int nv
   }
 }
 
-// out[j * B + e] (+)= sum_blk partial[(j * nblk + blk) * B + e]
-__global__ void breduce_kernel(int nv, int nblk, int B, const double2 *partial, double2 *out,
-                               int accumulate) {
+// out[j * B + e] (+)= sum_blk partial[(j * nblk + blk) * B + e]; also, in
+// the vector precision T, coef = sign * (this pass's sum) for an axpy, and
+// for a norm pass (nv = 1) inv = 1 / sqrt(sum.x) (0 for a zero norm), so
+// that the elementwise kernels do no FP64 arithmetic
+template <typename T>
+__global__ void breduce_kernel(int nv, int nblk, int B, const double2 *partial, double2 *out, int accumulate,
+                               typename Cx<T>::t *coef, double sign, T *inv) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nv * B) return;
   int j = idx / B, e = idx % B;
@@ -325,6 +313,11 @@ __global__ void breduce_kernel(int nv, int nblk, int B, const double2 *partial, 
     sx += p.x;
     sy += p.y;
   }
+  if (coef) {
+    coef[idx].x = (T)(sign * sx);
+    coef[idx].y = (T)(sign * sy);
+  }
+  if (inv) inv[idx] = (T)(sx > 0.0 ? 1.0 / sqrt(sx) : 0.0);
   if (accumulate) {
     out[idx].x += sx;
     out[idx].y += sy;
@@ -333,72 +326,66 @@ __global__ void breduce_kernel(int nv, int nblk, int B, const double2 *partial, 
   }
 }
 
-// w[f] += sign * sum_j h[j * B + e] V_j[f]
+// w[f] += sum_j c[j * B + e] V_j[f]   (coefficients in the vector precision)
 template <typename T>
 __global__ void baxpy_kernel(int64_t n, int B, int nv, const typename Cx<T>::t *__restrict__ V,
-                             size_t ld, const double2 *__restrict__ h, typename Cx<T>::t *__restrict__ w,
-                             double sign) {
+                             size_t ld, const typename Cx<T>::t *__restrict__ c,
+                             typename Cx<T>::t *__restrict__ w) {
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n;
        f += (int64_t)gridDim.x * blockDim.x) {
     const int e = (int)(f % B);
     T ax = w[f].x, ay = w[f].y;
-    const T sg = (T)sign;
     for (int j = 0; j < nv; ++j) {
       const auto a = V[(size_t)j * ld + f];
-      const double2 c = h[j * B + e];
-      const T cx = sg * (T)c.x, cy = sg * (T)c.y;
-      ax = fma(cx, a.x, fma(-cy, a.y, ax));
-      ay = fma(cx, a.y, fma(cy, a.x, ay));
+      const auto cj = c[j * B + e];
+      ax = fma(cj.x, a.x, fma(-cj.y, a.y, ax));
+      ay = fma(cj.x, a.y, fma(cj.y, a.x, ay));
     }
     w[f].x = ax;
     w[f].y = ay;
   }
 }
 
-// dst[f] = src[f] / sqrt(nrm2[e].x)   (0 if the norm is 0)
+// dst[f] = src[f] * inv[e]
 template <typename T>
-__global__ void bscale_kernel(int64_t n, int B, const typename Cx<T>::t *src, const double2 *nrm2,
+__global__ void bscale_kernel(int64_t n, int B, const typename Cx<T>::t *src, const T *__restrict__ inv,
                               typename Cx<T>::t *dst) {
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n;
        f += (int64_t)gridDim.x * blockDim.x) {
-    const int e = (int)(f % B);
-    const T s = (T)(nrm2[e].x > 0.0 ? 1.0 / sqrt(nrm2[e].x) : 0.0);
-    dst[f].x = src[f].x * s;
-    dst[f].y = src[f].y * s;
+    const T sc = inv[(int)(f % B)];
+    dst[f].x = src[f].x * sc;
+    dst[f].y = src[f].y * sc;
   }
 }
 
-// u[f] += coef[e] * sum_j y[j * B + e] V_j[f]   (u FP64; V in T;
-// coef = sqrt(nrm2[e].x), or 1 when nrm2 is NULL)
+// u[f] += sum_j c[j * B + e] V_j[f]: the correction formed in the basis
+// precision T (coefficients from bupdate_coef_kernel), added to u in FP64
 template <typename T>
 __global__ void bupdate_kernel(int64_t n, int B, int k, const typename Cx<T>::t *__restrict__ V,
-                               size_t ld, const double2 *__restrict__ y, const double2 *__restrict__ nrm2,
-                               double2 *__restrict__ u) {
+                               size_t ld, const typename Cx<T>::t *__restrict__ c, double2 *__restrict__ u) {
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n;
        f += (int64_t)gridDim.x * blockDim.x) {
     const int e = (int)(f % B);
-    T ax = T(0), ay = T(0);  // the correction in the basis precision
+    T ax = T(0), ay = T(0);
     for (int j = 0; j < k; ++j) {
       const auto a = V[(size_t)j * ld + f];
-      const double2 c = y[(size_t)j * B + e];
-      const T cx = (T)c.x, cy = (T)c.y;
-      ax = fma(cx, a.x, fma(-cy, a.y, ax));
-      ay = fma(cx, a.y, fma(cy, a.x, ay));
+      const auto cj = c[(size_t)j * B + e];
+      ax = fma(cj.x, a.x, fma(-cj.y, a.y, ax));
+      ay = fma(cj.x, a.y, fma(cj.y, a.x, ay));
     }
-    const double s = nrm2 ? sqrt(nrm2[e].x) : 1.0;
-    u[f].x += s * (double)ax;
-    u[f].y += s * (double)ay;
+    u[f].x += (double)ax;
+    u[f].y += (double)ay;
   }
 }
 
 
-// dst32[f] = (float)(src[f] / sqrt(nrm2[e].x))
-__global__ void bnormalize_f32_kernel(int64_t n, int B, const double2 *src, const double2 *nrm2, float2 *dst) {
+// dst32[f] = (float)(src[f] * inv[e])
+__global__ void bnormalize_f32_kernel(int64_t n, int B, const double2 *src, const double *__restrict__ inv,
+                                      float2 *dst) {
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n;
        f += (int64_t)gridDim.x * blockDim.x) {
-    const int e = (int)(f % B);
-    double s = nrm2[e].x > 0.0 ? 1.0 / sqrt(nrm2[e].x) : 0.0;
-    dst[f] = make_float2((float)(src[f].x * s), (float)(src[f].y * s));
+    const double sc = inv[(int)(f % B)];
+    dst[f] = make_float2((float)(src[f].x * sc), (float)(src[f].y * sc));
   }
 }
 
@@ -553,6 +540,11 @@ wpcd_status launch_spmm_cfg(const wpcd_problem *pr, const wpcd_P *P, const VT *v
 
 std::mutex g_tune_mutex;
 
+// choices made in this process, shared by every P0 of the same shape: the
+// tuning key plus the value precision, the nonzero count and the device
+// (a re-assembled P0 of an unchanged problem reuses the choice)
+std::map<std::tuple<int64_t, int, int64_t, int>, SpmmConfig> g_tuned_shapes;
+
 bool load_cached(int64_t key, SpmmConfig *out) {
   const char *path = std::getenv("WPCD_TUNE_CACHE");
   if (!path || !*path) return false;
@@ -590,6 +582,13 @@ wpcd_status tune_spmm(const wpcd_problem *pr, wpcd_P *P, int B, int fp32, cudaSt
   auto it = P->tuned.find(key);
   if (it != P->tuned.end()) {
     *out = it->second;
+    return WPCD_OK;
+  }
+  const auto shape = std::make_tuple(key, P->prec, P->nnz, pr->device);
+  auto its = g_tuned_shapes.find(shape);
+  if (its != g_tuned_shapes.end()) {
+    P->tuned[key] = its->second;
+    *out = its->second;
     return WPCD_OK;
   }
   SpmmConfig cached;
@@ -645,6 +644,7 @@ wpcd_status tune_spmm(const wpcd_problem *pr, wpcd_P *P, int B, int fp32, cudaSt
   cudaFree(z);
   if (st != WPCD_OK) return st;
   P->tuned[key] = pick;
+  g_tuned_shapes[shape] = pick;
   store_cached(key, pick);
   *out = pick;
   return WPCD_OK;
@@ -726,7 +726,7 @@ wpcd_status resolvent_impl(const wpcd_problem *pr, const double *E, int n_E, dou
                            int *j0, double *D, cudaStream_t s) {
   if (n_E < 0 || (n_E > 0 && (!E || !g))) return set_error(WPCD_EINVAL, "bad resolvent arguments");
   if (n_E == 0) return WPCD_OK;
-  std::vector<double> lohi(2 * (size_t)n_E + 80);
+  std::vector<double> lohi(2 * (size_t)n_E + 88);
   for (int e = 0; e < n_E; ++e) {
     int jj;
     double lo, hi;
@@ -739,6 +739,7 @@ wpcd_status resolvent_impl(const wpcd_problem *pr, const double *E, int n_E, dou
   }
   gauss_legendre(32, lohi.data() + 2 * n_E, lohi.data() + 2 * n_E + 32);
   gauss_legendre(8, lohi.data() + 2 * n_E + 64, lohi.data() + 2 * n_E + 72);
+  gauss_legendre(4, lohi.data() + 2 * n_E + 80, lohi.data() + 2 * n_E + 84);
   WPCD_CUDA_TRY(cudaSetDevice(pr->device));
   double *d_lohi = nullptr;
   WPCD_CUDA_TRY(cudaMallocAsync(&d_lohi, sizeof(double) * lohi.size(), s));
@@ -757,6 +758,8 @@ wpcd_status resolvent_impl(const wpcd_problem *pr, const double *E, int n_E, dou
   R.gl_w = d_lohi + 2 * n_E + 32;
   R.gl8_t = d_lohi + 2 * n_E + 64;
   R.gl8_w = d_lohi + 2 * n_E + 72;
+  R.gl4_t = d_lohi + 2 * n_E + 80;
+  R.gl4_w = d_lohi + 2 * n_E + 84;
   int64_t total = (int64_t)n_E * pr->n_ch * pr->N * pr->M;
   resolvent_kernel<<<grid_for(total, 256, 152 * 16), 256, 0, s>>>(R, g);
   count_launches(1);
@@ -831,10 +834,13 @@ struct Krylov {
   double2 *H = nullptr, *cs = nullptr, *sn = nullptr, *bet = nullptr;
   double2 *h = nullptr, *h2 = nullptr, *nrm = nullptr, *y = nullptr, *partial = nullptr;
   double *resid = nullptr, *bnorm = nullptr;
+  typename Cx<T>::t *hc = nullptr;  // axpy coefficients in T [(m+1)][B]
+  T *inv = nullptr;                  // 1 / |w| per energy in T [B]
   int nblk = 0;
   ~Krylov() {
     cudaFree(V); cudaFree(w); cudaFree(H); cudaFree(cs); cudaFree(sn); cudaFree(bet); cudaFree(h);
     cudaFree(h2); cudaFree(nrm); cudaFree(y); cudaFree(partial); cudaFree(resid); cudaFree(bnorm);
+    cudaFree(hc); cudaFree(inv);
   }
   cudaError_t alloc(int m_, int B_, size_t dim_, bool vectors = true) {
     m = m_;
@@ -856,6 +862,8 @@ struct Krylov {
     if ((e = cudaMalloc(&y, sizeof(double2) * (size_t)B * m)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&partial, sizeof(double2) * (size_t)B * (m + 1) * nblk)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&resid, sizeof(double) * B)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&hc, 2 * sizeof(T) * (size_t)B * (m + 1))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&inv, sizeof(T) * (size_t)B)) != cudaSuccess) return e;
     return cudaMalloc(&bnorm, sizeof(double) * B);
   }
   using C2 = typename Cx<T>::t;
@@ -870,17 +878,19 @@ struct Krylov {
     dim3 b = dot_block();
     return dim3(nblk, (B + b.x - 1) / b.x);
   }
-  // out[j * B + e] = <V_j, x>, j < nv
+  // out[j * B + e] = <V_j, x>, j < nv; with hcoef, also hc = -out in T
   template <typename U>
   void dots(int nv, const typename Cx<U>::t *base, size_t ld, const typename Cx<U>::t *x, double2 *out,
-            int accumulate, cudaStream_t s) {
+            int accumulate, cudaStream_t s, bool hcoef = false, bool scale = false) {
     bdot_kernel<U><<<dot_grid(), dot_block(), 0, s>>>((int)dim, B, nv, base, ld, x, partial);
-    breduce_kernel<<<(nv * B + 255) / 256, 256, 0, s>>>(nv, nblk, B, partial, out, accumulate);
+    breduce_kernel<T><<<(nv * B + 255) / 256, 256, 0, s>>>(nv, nblk, B, partial, out, accumulate,
+                                                           hcoef ? hc : nullptr, -1.0, scale ? inv : nullptr);
     count_launches(2);
   }
+  // nrm[e] = |x_e|^2 (and inv = 1 / |x_e| in T with scale)
   template <typename U>
-  void norms(const typename Cx<U>::t *x, cudaStream_t s) {
-    dots<U>(1, x, 0, x, nrm, 0, s);
+  void norms(const typename Cx<U>::t *x, cudaStream_t s, bool scale = false) {
+    dots<U>(1, x, 0, x, nrm, 0, s, false, scale);
   }
   // one Arnoldi step from column k (w holds (I - K) v_k on entry); classical
   // Gram-Schmidt with a second pass (reorth = true) or a single pass
@@ -888,16 +898,18 @@ struct Krylov {
     const int64_t n = (int64_t)dim * B;
     const size_t ld = dim * B;
     const int vg = grid_for(n, 256);
-    dots<T>(k + 1, vec(0), ld, wv(), h, 0, s);
-    baxpy_kernel<T><<<vg, 256, 0, s>>>(n, B, k + 1, vec(0), ld, h, wv(), -1.0);
+    dots<T>(k + 1, vec(0), ld, wv(), h, 0, s, true);
+    baxpy_kernel<T><<<vg, 256, 0, s>>>(n, B, k + 1, vec(0), ld, hc, wv());
     if (reorth) {
-      dots<T>(k + 1, vec(0), ld, wv(), h2, 0, s);
-      baxpy_kernel<T><<<vg, 256, 0, s>>>(n, B, k + 1, vec(0), ld, h2, wv(), -1.0);
-      breduce_kernel<<<((k + 1) * B + 255) / 256, 256, 0, s>>>(k + 1, nblk, B, partial, h, 1);  // h += h2
+      dots<T>(k + 1, vec(0), ld, wv(), h2, 0, s, true);
+      baxpy_kernel<T><<<vg, 256, 0, s>>>(n, B, k + 1, vec(0), ld, hc, wv());
+      // h += h2 (the second pass's partials are still in place)
+      breduce_kernel<T><<<((k + 1) * B + 255) / 256, 256, 0, s>>>(k + 1, nblk, B, partial, h, 1, nullptr, 0.0,
+                                                                   nullptr);
       count_launches(2);
     }
-    norms<T>(wv(), s);
-    bscale_kernel<T><<<vg, 256, 0, s>>>(n, B, wv(), nrm, vec(k + 1));
+    norms<T>(wv(), s, true);
+    bscale_kernel<T><<<vg, 256, 0, s>>>(n, B, wv(), inv, vec(k + 1));
     bgivens_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, m, k, h, nrm, H, cs, sn, bet, resid, bnorm);
     count_launches(3);
   }
@@ -1035,7 +1047,8 @@ wpcd_status solve_fp64(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solve
     bet0[(size_t)e * (m + 1)] = make_double2(std::sqrt(nr[e].x), 0.0);
   }
   // v0 = r / |r| ; bet = |r| e1
-  bscale_kernel<double><<<vg, 256, 0, s>>>(n, B, (const double2 *)cx.r, kr.nrm, kr.vec(0));
+  kr.norms<double>((const double2 *)cx.r, s, true);  // inv = 1 / |r| for v0
+  bscale_kernel<double><<<vg, 256, 0, s>>>(n, B, (const double2 *)cx.r, kr.inv, kr.vec(0));
   count_launches(1);
   WPCD_CUDA_TRY(cudaMemsetAsync(kr.H, 0, sizeof(double2) * (size_t)B * (m + 1) * m, s));
   WPCD_CUDA_TRY(cudaMemcpyAsync(kr.bet, bet0.data(), sizeof(double2) * bet0.size(), cudaMemcpyHostToDevice, s));
@@ -1083,8 +1096,9 @@ wpcd_status solve_fp64(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solve
     }
   }
   bbacksub_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, m, k, kr.H, kr.bet, kr.y);
-  bupdate_kernel<double><<<vg, 256, 0, s>>>(n, B, k, kr.vec(0), cx.dim * B, kr.y, nullptr, (double2 *)cx.u);
-  count_launches(2);
+  bupdate_coef_kernel<double><<<std::max(1, (k * B + 255) / 256), 256, 0, s>>>(k, B, kr.y, nullptr, kr.hc);
+  bupdate_kernel<double><<<vg, 256, 0, s>>>(n, B, k, kr.vec(0), cx.dim * B, kr.hc, (double2 *)cx.u);
+  count_launches(3);
   return WPCD_OK;
 }
 
@@ -1132,8 +1146,9 @@ wpcd_status solve_mixed(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solv
     }
     bbacksub_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, m, m, kr.H, kr.bet, kr.y);
     // u += |r| (V y)   (FP64 accumulation of the FP32 correction)
-    bupdate_kernel<float><<<vg, 256, 0, s>>>(n, B, m, kr.vec(0), cx.dim * B, kr.y, k64.nrm, (double2 *)cx.u);
-    count_launches(2);
+    bupdate_coef_kernel<float><<<(m * B + 255) / 256, 256, 0, s>>>(m, B, kr.y, k64.nrm, kr.hc);
+    bupdate_kernel<float><<<vg, 256, 0, s>>>(n, B, m, kr.vec(0), cx.dim * B, kr.hc, (double2 *)cx.u);
+    count_launches(3);
     return WPCD_OK;
   };
   // the SpMM shapes are tuned before any capture (tuning synchronises)
@@ -1168,7 +1183,7 @@ wpcd_status solve_mixed(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solv
     } else {
       cudaMemcpyAsync(cx.r, cx.b, 16 * n, cudaMemcpyDeviceToDevice, s);
     }
-    k64.norms<double>((const double2 *)cx.r, s);
+    k64.norms<double>((const double2 *)cx.r, s, true);  // |r|^2 and 1 / |r|
     cudaMemcpyAsync(nr.data(), k64.nrm, sizeof(double2) * B, cudaMemcpyDeviceToHost, s);
     cudaError_t ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) {
@@ -1190,7 +1205,7 @@ wpcd_status solve_mixed(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solv
     if (done || outer == max_outer) break;
     ++n_outer;
     // v0 = (float)(r / |r|)
-    bnormalize_f32_kernel<<<vg, 256, 0, s>>>(n, B, (const double2 *)cx.r, k64.nrm, kr.vec(0));
+    bnormalize_f32_kernel<<<vg, 256, 0, s>>>(n, B, (const double2 *)cx.r, k64.inv, kr.vec(0));
     count_launches(1);
     if (o.use_graph && s != nullptr) {  // the legacy default stream cannot be captured
       if (!exec) {

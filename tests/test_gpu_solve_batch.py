@@ -57,16 +57,18 @@ def test_batched_fp64_matches_oracle(W, sys3):
 def test_mixed_matches_oracle(W, sys3, pname):
     pr, P64, P32, opr = sys3
     P = P64 if pname == "P64" else P32
-    U, stats, st = pr.wpcd_solve(P, ENERGIES, tol=1e-10, precision=W.WPCD_SOLVE_MIXED,
+    U, stats, st = pr.wpcd_solve(P, ENERGIES, tol=1e-12, precision=W.WPCD_SOLVE_MIXED,
                                  batch=len(ENERGIES))
     assert st == W.WPCD_OK
     for s in stats:
-        assert s.status == W.WPCD_OK and s.relres <= 1e-10
+        assert s.status == W.WPCD_OK and s.relres <= 1e-12
         assert s.n_outer >= 1 and s.n_kapply32 >= 16
     ref = _ref(opr, ENERGIES)
     err = np.max(np.abs(U - ref) / np.abs(ref))
-    # FP64 values: refined to the FP64 system at residual 1e-10 (U00 within
-    # 1e-8); FP32C values: the refinement converges to the FP32C-valued
+    # FP64 values: refined to the FP64 system at residual 1e-12; the U00
+    # error is the residual times the conditioning of (I - K), about 1e2 on
+    # this strongly bound system, so 1e-8 holds with margin (at residual
+    # 1e-10 it sat at the bar); FP32C values: the refinement converges to the FP32C-valued
     # system, whose U00 differs from the FP64 one by the FP32 node-evaluation
     # error of P0 amplified by the conditioning (6e-6 measured on this
     # strongly bound test system; stated, not hidden)
