@@ -258,6 +258,26 @@ wpcd_status wpcd_solve_batch(int n_prob, wpcd_problem *const *problems, const wp
                              const double *const *E, const int *n_E, const wpcd_solve_opts *opts,
                              double *const *U00, wpcd_solve_stats *const *stats, void *stream);
 
+/* arithmetic of wpcd_channel_gemm */
+#define WPCD_GEMM_FP64 0   /* FP64 vectors, FP64 SIMT kernel */
+#define WPCD_GEMM_FP32 1   /* FP32 vectors, FP32 SIMT kernel */
+#define WPCD_GEMM_TF32X3 2 /* FP32 vectors, tensor cores (tcgen05): each FP32
+                              operand split into TF32 hi + lo, products
+                              hi*hi + hi*lo + lo*hi accumulated in FP32 */
+
+/* One dense step of the K application (Sec. 3.3, Eq. kernel): for every
+ * channel block ch, Y_ch = A_ch (G1 o X)_ch with A = Vt (which = 0) or O
+ * (which = 1), N x N, applied to the [N][M][n_rhs] complex block of the
+ * channel (energy index innermost, as in wpcd_solve).  g: device resolvent
+ * in the same layout and precision as x, or NULL for no scaling; x, y:
+ * device [n_ch][N][M][n_rhs] complex, FP64 for WPCD_GEMM_FP64 and FP32
+ * otherwise, distinct.  The mixed solve runs its FP32 inner cycles with
+ * WPCD_GEMM_TF32X3 when N <= 512 (the environment variable WPCD_GEMM=simt
+ * selects WPCD_GEMM_FP32 instead).  EINVAL for a bad mode, bad vectors, or
+ * WPCD_GEMM_TF32X3 with N > 512; ETIMEOUT if a tensor-core wait ran out. */
+wpcd_status wpcd_channel_gemm(wpcd_problem *pr, int which, int mode, const void *g, const void *x, void *y,
+                              int n_rhs, void *stream);
+
 /* Autotuner (batching): time the candidate SpMM launch shapes (rows per
  * warp, energy lanes per row, energies per lane = RHS tile width) for a
  * batch of n_rhs energies in FP64 (fp32 = 0) or FP32 (fp32 = 1) and keep the

@@ -46,6 +46,11 @@ static void free_tables(DeviceTables &d) {
   cudaFree(d.O32);
   cudaFree(d.Vt32);
   d.O32 = d.Vt32 = nullptr;
+  cudaFree(d.O_tc);
+  cudaFree(d.Vt_tc);
+  cudaFree(d.tc_err);
+  d.O_tc = d.Vt_tc = nullptr;
+  d.tc_err = nullptr;
 }
 
 static wpcd_status upload32(float **dst, const std::vector<double> &src) {
@@ -353,6 +358,15 @@ wpcd_status wpcd_solve_batch(int n_prob, wpcd_problem *const *problems, const wp
   WPCD_GUARD_BEGIN
   clear_error();
   return solve_group(n_prob, problems, P, E, n_E, opts, U00, stats, static_cast<cudaStream_t>(stream));
+  WPCD_GUARD_END
+}
+
+wpcd_status wpcd_channel_gemm(wpcd_problem *pr, int which, int mode, const void *g, const void *x, void *y,
+                              int n_rhs, void *stream) {
+  WPCD_GUARD_BEGIN
+  clear_error();
+  if (!pr) return set_error(WPCD_EINVAL, "null problem");
+  return channel_gemm(pr, which, mode, g, x, y, n_rhs, static_cast<cudaStream_t>(stream));
   WPCD_GUARD_END
 }
 

@@ -85,15 +85,19 @@ struct SpmmUnroll {
 // Comput. 2020): the error grows with the number of blocks only through the
 // float-float accumulator, and inside a block with its few terms.  FP64
 // sums the block partials plainly.  y points at the problem's own vector
-// block ([n_ch][n_cells][B] complex).
-template <typename VT, typename T, int NCH, int EPT>
+// block ([n_ch][n_cells][B] complex).  The lane's energies are en0 +
+// estride * t; with VEC (FP32, estride 1, EPT and B even) two adjacent
+// energies come in one 16-byte load.
+template <typename VT, typename T, int NCH, int EPT, bool VEC>
 __device__ __forceinline__ void spmm_row(int64_t b, int64_t e, int nl, int nl_count, const int32_t *__restrict__ col,
                                          const VT *__restrict__ val, int64_t nnz,
-                                         const typename Cx<T>::t *__restrict__ y, int n_cells, int B, int e_base,
-                                         int el, int el_n, typename AccOf<T>::t (&acc)[NCH][EPT][2]) {
+                                         const typename Cx<T>::t *__restrict__ y, int n_cells, int B, int en0,
+                                         int estride, typename AccOf<T>::t (&acc)[NCH][EPT][2]) {
   using C2 = typename Cx<T>::t;
   constexpr int NPAIR = pair_count(NCH);
   constexpr int U = SpmmUnroll<NCH>::value;
+  constexpr int TS = VEC ? 2 : 1;  // energies per load
+  static_assert(!VEC || (sizeof(T) == 4 && EPT % 2 == 0), "vector loads need FP32 and an even EPT");
   for (int64_t o0 = b + nl; o0 < e; o0 += (int64_t)U * nl_count) {
     int tc[U];
     T v[U][NPAIR];
@@ -106,31 +110,51 @@ __device__ __forceinline__ void spmm_row(int64_t b, int64_t e, int nl, int nl_co
       for (int m = 0; m < NPAIR; ++m) v[u][m] = ok ? (T)__ldg(val + (size_t)m * nnz + o) : T(0);
     }
 #pragma unroll
-    for (int t = 0; t < EPT; ++t) {
-      const int en = e_base + el + el_n * t;
+    for (int t0 = 0; t0 < EPT; t0 += TS) {
+      const int en = en0 + estride * t0;
       if (en < B) {
-        T part[NCH][2];
+        T part[NCH][TS][2];
 #pragma unroll
-        for (int l = 0; l < NCH; ++l) part[l][0] = part[l][1] = T(0);
+        for (int l = 0; l < NCH; ++l)
+#pragma unroll
+          for (int q = 0; q < TS; ++q) part[l][q][0] = part[l][q][1] = T(0);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           if (tc[u] >= 0) {
-            C2 yv[NCH];
+            T yr[NCH][TS], yi[NCH][TS];
 #pragma unroll
-            for (int l = 0; l < NCH; ++l) yv[l] = __ldg(y + ((size_t)l * n_cells + tc[u]) * B + en);
+            for (int l = 0; l < NCH; ++l) {
+              const C2 *p = y + ((size_t)l * n_cells + tc[u]) * B + en;
+              if constexpr (VEC) {
+                const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+                yr[l][0] = q.x;
+                yi[l][0] = q.y;
+                yr[l][TS - 1] = q.z;
+                yi[l][TS - 1] = q.w;
+              } else {
+                const C2 q = __ldg(p);
+                yr[l][0] = q.x;
+                yi[l][0] = q.y;
+              }
+            }
 #pragma unroll
             for (int m = 0; m < NPAIR; ++m) {
               const int l = pair_first(NCH, m), lp = pair_second(NCH, m);
-              part[l][0] = fma(v[u][m], yv[lp].x, part[l][0]);
-              part[l][1] = fma(v[u][m], yv[lp].y, part[l][1]);
+#pragma unroll
+              for (int q = 0; q < TS; ++q) {
+                part[l][q][0] = fma(v[u][m], yr[lp][q], part[l][q][0]);
+                part[l][q][1] = fma(v[u][m], yi[lp][q], part[l][q][1]);
+              }
             }
           }
         }
 #pragma unroll
-        for (int l = 0; l < NCH; ++l) {
-          acc[l][t][0].add(part[l][0]);
-          acc[l][t][1].add(part[l][1]);
-        }
+        for (int l = 0; l < NCH; ++l)
+#pragma unroll
+          for (int q = 0; q < TS; ++q) {
+            acc[l][t0 + q][0].add(part[l][q][0]);
+            acc[l][t0 + q][1].add(part[l][q][1]);
+          }
       }
     }
   }
@@ -324,6 +348,13 @@ std::vector<SpmmConfig> candidates(int B) {
     if (el <= 16) c.push_back(SpmmConfig{2, el, ept});
   }
   if (el > 1) c.push_back(SpmmConfig{1, el / 2, 1});
+  // narrower energy lanes with more energies each (for FP32 these load two
+  // adjacent energies at a time) leave two nonzero lanes per row
+  if (el >= 8 && B % 2 == 0)
+    for (int ept : {2, 4}) {
+      if (el / 2 * ept / 2 >= B) continue;
+      c.push_back(SpmmConfig{1, el / 2, ept});
+    }
   return c;
 }
 

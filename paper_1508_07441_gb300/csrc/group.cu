@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(256) gspmm_kernel(const GMeta *__restrict__ gm
         acc[l][t][1].zero();
       }
     const int64_t b = active ? P.row_ptr[c] : 0, e = active ? P.row_ptr[c + 1] : 0;
-    spmm_row<VT, T, NCH, EPT>(b, e, nl, nl_count, P.col, val, P.nnz, yg, n_cells, B, e_base, el, el_n, acc);
+    spmm_row<VT, T, NCH, EPT, false>(b, e, nl, nl_count, P.col, val, P.nnz, yg, n_cells, B, e_base + el, el_n, acc);
     for (int off = el_n; off < lpr; off <<= 1)
 #pragma unroll
       for (int l = 0; l < NCH; ++l)

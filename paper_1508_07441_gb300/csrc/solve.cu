@@ -182,7 +182,7 @@ struct SpmmParams {
 };
 
 
-template <typename VT, typename T, int NCH, int EPT>
+template <typename VT, typename T, int NCH, int EPT, bool VEC>
 __global__ void __launch_bounds__(256) spmm_kernel(SpmmParams S, const VT *__restrict__ val,
                                                    const typename Cx<T>::t *__restrict__ y,
                                                    typename Cx<T>::t *__restrict__ z) {
@@ -211,7 +211,9 @@ __global__ void __launch_bounds__(256) spmm_kernel(SpmmParams S, const VT *__res
         acc[l][t][1].zero();
       }
     const int64_t b = active ? S.row_ptr[c] : 0, e = active ? S.row_ptr[c + 1] : 0;
-    spmm_row<VT, T, NCH, EPT>(b, e, nl, nl_count, S.col, val, S.nnz, y, S.n_cells, B, e_base, el, S.el, acc);
+    // lane energies: VEC adjacent (en0 + t), otherwise strided (el + S.el t)
+    const int en0 = VEC ? e_base + el * EPT : e_base + el, estride = VEC ? 1 : S.el;
+    spmm_row<VT, T, NCH, EPT, VEC>(b, e, nl, nl_count, S.col, val, S.nnz, y, S.n_cells, B, en0, estride, acc);
     // reduce over the nonzero lanes of the row (xor offsets el .. lpr/2)
     for (int off = S.el; off < lpr; off <<= 1)
 #pragma unroll
@@ -224,7 +226,7 @@ __global__ void __launch_bounds__(256) spmm_kernel(SpmmParams S, const VT *__res
     if (active && nl == 0) {
 #pragma unroll
       for (int t = 0; t < EPT; ++t) {
-        const int en = e_base + el + S.el * t;
+        const int en = VEC ? e_base + el * EPT + t : e_base + el + S.el * t;
         if (en < B)
 #pragma unroll
           for (int l = 0; l < NCH; ++l) {
@@ -511,15 +513,17 @@ wpcd_status launch_spmm_cfg(const wpcd_problem *pr, const wpcd_P *P, const VT *v
   const int rows_per_block = 8 * cfg.rpw;
   dim3 grid(grid_for((int64_t)S.n_cells, rows_per_block, 152 * 16),
             (B + cfg.el * cfg.ept - 1) / (cfg.el * cfg.ept));
-#define WPCD_SPMM_EPT(NCH, EPT) spmm_kernel<VT, T, NCH, EPT><<<grid, 256, 0, s>>>(S, val, yy, zz)
-#define WPCD_SPMM_CASE(NCH)                       \
-  case NCH:                                       \
-    if (cfg.ept == 1)                             \
-      WPCD_SPMM_EPT(NCH, 1);                      \
-    else if (cfg.ept == 2)                        \
-      WPCD_SPMM_EPT(NCH, 2);                      \
-    else                                          \
-      WPCD_SPMM_EPT(NCH, 4);                      \
+  // FP32 vectors with an even batch load two adjacent energies at a time
+  const bool vec = sizeof(T) == 4 && B % 2 == 0;
+#define WPCD_SPMM_EPT(NCH, EPT, VEC) spmm_kernel<VT, T, NCH, EPT, VEC><<<grid, 256, 0, s>>>(S, val, yy, zz)
+#define WPCD_SPMM_CASE(NCH)                                                          \
+  case NCH:                                                                          \
+    if (cfg.ept == 1)                                                                \
+      WPCD_SPMM_EPT(NCH, 1, false);                                                  \
+    else if (cfg.ept == 2)                                                           \
+      vec ? WPCD_SPMM_EPT(NCH, 2, sizeof(T) == 4) : WPCD_SPMM_EPT(NCH, 2, false);    \
+    else                                                                             \
+      vec ? WPCD_SPMM_EPT(NCH, 4, sizeof(T) == 4) : WPCD_SPMM_EPT(NCH, 4, false);    \
     break;
   switch (pr->n_ch) {
     WPCD_SPMM_CASE(1)
@@ -676,6 +680,15 @@ wpcd_status kapply_ws(const wpcd_problem *pr, const wpcd_P *P, const T *g, const
   const int64_t ncol = 2LL * M * B;
   const T *Vt = sizeof(T) == 8 ? (const T *)(const void *)pr->d.Vt : (const T *)(const void *)pr->d.Vt32;
   const T *O = sizeof(T) == 8 ? (const T *)(const void *)pr->d.O : (const T *)(const void *)pr->d.O32;
+  if constexpr (sizeof(T) == 4) {
+    // FP32 vectors: tensor-core channel blocks when the operands are packed
+    if (pr->d.O_tc && tc_enabled()) {
+      wpcd_status st = tc_gemm(pr, false, (const float *)g, (const float *)x, nullptr, (float *)ws.y, ncol, s);
+      if (st == WPCD_OK) st = spmm<T>(pr, P, ws.y, ws.z, B, s);
+      if (st == WPCD_OK) st = tc_gemm(pr, true, nullptr, (const float *)ws.z, (const float *)sub, (float *)out, ncol, s);
+      return st;
+    }
+  }
   dim3 grid((unsigned)((ncol + GB_N - 1) / GB_N), (N + GB_M - 1) / GB_M, n_ch);
   if (g)
     gemm_kernel<T, true, false><<<grid, G_THREADS, 0, s>>>(N, ncol, Vt, x, g, nullptr, ws.y);
@@ -1451,6 +1464,10 @@ wpcd_status solve(wpcd_problem *pr, const wpcd_P *Pc, const double *E, int n_E,
     const bool mixed = opt.precision == WPCD_SOLVE_MIXED;
     const int Bmax = opt.batch > 0 ? std::min(opt.batch, n_E) : n_E;
     const size_t dim = (size_t)pr->n_ch * pr->N * pr->M;
+    if (mixed && tc_enabled() && tc_supported(pr)) {
+      wpcd_status st = tc_prepare(pr, s);
+      if (st != WPCD_OK) return st;
+    }
     if (mixed && !P->val32 && !P->val32_copy) {
       WPCD_CUDA_TRY(cudaMalloc(&P->val32_copy, sizeof(float) * (size_t)P->nnz * P->n_pairs + 4));
       int64_t nv = (int64_t)P->nnz * P->n_pairs;
@@ -1552,10 +1569,54 @@ wpcd_status solve(wpcd_problem *pr, const wpcd_P *Pc, const double *E, int n_E,
       }
     }
   }
+  {
+    wpcd_status st = tc_check(pr, s);
+    if (st != WPCD_OK) return st;
+  }
   if (worst != WPCD_OK)
     set_error(worst, worst == WPCD_ENOCONV ? "summation did not reach the tolerance for some energy"
                                            : "Pade/Krylov breakdown for some energy");
   return worst;
+}
+
+// one channel-block product Y = A (G1 o X) of the K application
+wpcd_status channel_gemm(wpcd_problem *pr, int which, int mode, const void *g, const void *x, void *y, int n_rhs,
+                         cudaStream_t s) {
+  if (which != 0 && which != 1) return set_error(WPCD_EINVAL, "which must be 0 (Vt) or 1 (O)");
+  if (!x || !y || x == y || n_rhs < 1) return set_error(WPCD_EINVAL, "bad vectors or n_rhs");
+  WPCD_CUDA_TRY(cudaSetDevice(pr->device));
+  const int N = pr->N;
+  const int64_t ncol = 2LL * pr->M * n_rhs;
+  dim3 grid((unsigned)((ncol + GB_N - 1) / GB_N), (N + GB_M - 1) / GB_M, pr->n_ch);
+  if (mode == WPCD_GEMM_FP64) {
+    const double *A = which ? pr->d.O : pr->d.Vt;
+    if (g)
+      gemm_kernel<double, true, false><<<grid, G_THREADS, 0, s>>>(N, ncol, A, (const double *)x, (const double *)g,
+                                                                  nullptr, (double *)y);
+    else
+      gemm_kernel<double, false, false><<<grid, G_THREADS, 0, s>>>(N, ncol, A, (const double *)x, nullptr, nullptr,
+                                                                   (double *)y);
+  } else if (mode == WPCD_GEMM_FP32) {
+    const float *A = which ? pr->d.O32 : pr->d.Vt32;
+    if (g)
+      gemm_kernel<float, true, false><<<grid, G_THREADS, 0, s>>>(N, ncol, A, (const float *)x, (const float *)g,
+                                                                 nullptr, (float *)y);
+    else
+      gemm_kernel<float, false, false><<<grid, G_THREADS, 0, s>>>(N, ncol, A, (const float *)x, nullptr, nullptr,
+                                                                  (float *)y);
+  } else if (mode == WPCD_GEMM_TF32X3) {
+    if (!tc_supported(pr)) return set_error(WPCD_EINVAL, "the tensor-core GEMM needs N <= 512");
+    wpcd_status st = tc_prepare(pr, s);
+    if (st != WPCD_OK) return st;
+    st = tc_gemm(pr, which == 1, (const float *)g, (const float *)x, nullptr, (float *)y, ncol, s);
+    if (st != WPCD_OK) return st;
+    return tc_check(pr, s);
+  } else {
+    return set_error(WPCD_EINVAL, "unknown GEMM mode");
+  }
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? WPCD_OK : cuda_error(e, "channel gemm launch");
 }
 
 }  // namespace wpcd

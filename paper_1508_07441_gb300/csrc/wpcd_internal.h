@@ -85,6 +85,8 @@ struct DeviceTables {
   double *eps = nullptr;                        // [n_ch][N]
   double *O = nullptr, *Vt = nullptr;           // [n_ch][N][N]
   float *O32 = nullptr, *Vt32 = nullptr;        // FP32 copies for the inner solve
+  float *O_tc = nullptr, *Vt_tc = nullptr;      // TF32 hi/lo operand blocks (tc_gemm.cu)
+  int *tc_err = nullptr;                        // tensor-core wait-limit flag
 };
 
 }  // namespace wpcd
@@ -137,8 +139,17 @@ wpcd_status kapply_scratch(const wpcd_problem *pr, const wpcd_P *P, const double
                            double *y, double *scratch_y, double *scratch_z, cudaStream_t s);
 wpcd_status born_vectors(wpcd_problem *pr, const wpcd_P *P, const double *E, int n_E, double *b_major,
                          cudaStream_t s);
+wpcd_status channel_gemm(wpcd_problem *pr, int which, int mode, const void *g, const void *x, void *y, int n_rhs,
+                         cudaStream_t s);
 // G1 of n_E energies in the batched layout (element (r, e) at r * n_E + e)
 wpcd_status resolvent_minor(const wpcd_problem *pr, const double *E, int n_E, double *g, cudaStream_t s);
+// tc_gemm.cu: tensor-core (TF32 x 3) channel-block products for FP32 vectors
+bool tc_supported(const wpcd_problem *pr);
+bool tc_enabled();
+wpcd_status tc_prepare(wpcd_problem *pr, cudaStream_t s);
+wpcd_status tc_gemm(const wpcd_problem *pr, bool use_O, const float *G, const float *X, const float *S, float *C,
+                    int64_t ncol, cudaStream_t s);
+wpcd_status tc_check(const wpcd_problem *pr, cudaStream_t s);
 // group.cu
 wpcd_status solve_group(int n_prob, wpcd_problem *const *prs, const wpcd_P *const *Ps, const double *const *E,
                         const int *n_E, const wpcd_solve_opts *o, double *const *U00, wpcd_solve_stats *const *st,

@@ -22,6 +22,7 @@ WPCD_ENOCONV, WPCD_EBREAKDOWN, WPCD_ETIMEOUT, WPCD_ENOBOUND = -4, -5, -6, -7
 WPCD_FP64, WPCD_FP32C = 0, 1
 WPCD_SUM_KRYLOV, WPCD_SUM_WYNN = 0, 1
 WPCD_SOLVE_FP64, WPCD_SOLVE_MIXED = 0, 1
+WPCD_GEMM_FP64, WPCD_GEMM_FP32, WPCD_GEMM_TF32X3 = 0, 1, 2
 
 _P = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
@@ -76,6 +77,7 @@ _SIGS = {
                                         ctypes.POINTER(_D), ctypes.POINTER(ctypes.POINTER(wpcd_solve_stats)),
                                         _P]),
     "wpcd_tune_spmm": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P, _I, _I, _I]),
+    "wpcd_channel_gemm": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P]),
     "wpcd_born": (ctypes.c_int, [_P, _P, _D, ctypes.c_int, _P, _P]),
     "wpcd_kapply_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "wpcd_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
@@ -272,6 +274,12 @@ class Problem:
                               _stream_ptr(stream))
         check(st, allow=allow)
         return U.view(np.complex128), list(stats), st
+
+    def wpcd_channel_gemm(self, which, mode, g, x, y, n_rhs, stream=None):
+        """y = A (g o x) per channel block, A = Vt (which 0) or O (which 1);
+        g, x, y device tensors in the batched layout (g may be None)."""
+        check(lib().wpcd_channel_gemm(self._h, which, mode, _tensor_ptr(g), _tensor_ptr(x), _tensor_ptr(y),
+                                      n_rhs, _stream_ptr(stream)))
 
     def wpcd_born(self, P, E, b, stream=None):
         """Born terms into device tensor b (float64, 2 * len(E) * dim)."""

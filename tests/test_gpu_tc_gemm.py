@@ -1,0 +1,116 @@
+"""GPU checks of the dense channel-block products of the K application
+(wpcd_channel_gemm, through the C ABI): the tensor-core TF32x3 kernel and the
+FP32/FP64 SIMT kernels against an FP64 numpy product of the same blocks, on
+grids that cover one to three 128-row tiles and ragged column tiles; and the
+mixed solve with the tensor-core products against the FP64 oracle."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def W():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1508_07441_gb300 import build, wpcd
+
+    build.build()
+    return wpcd
+
+
+def _problem(W, N, M, n_ch=3):
+    from paper_1508_07441_gb300 import inputs
+
+    return W.Problem(inputs.tangent_edges(N, 20.0), inputs.tangent_edges(M, 20.0), 2, 2, 4, n_ch,
+                     (-3.0,), (1.0,))
+
+
+def _blocks(pr, which):
+    out = []
+    for l in range(pr.n_ch):
+        eps, O, v = pr.wpcd_problem_pair(l)
+        out.append(O if which == 1 else v @ O.T)  # Vt = v O^T
+    return np.stack(out)
+
+
+def _reference(A, x, g, N, M, B):
+    """FP64 products on [n_ch][N][M][B] complex blocks."""
+    xc = x.reshape(A.shape[0], N, M * B)
+    if g is not None:
+        xc = xc * g.reshape(A.shape[0], N, M * B)
+    return np.einsum("cik,ckj->cij", A, xc), np.einsum("cik,ckj->cij", np.abs(A), np.abs(xc))
+
+
+@pytest.mark.parametrize("N,M,B", [(30, 28, 3), (130, 20, 5), (200, 16, 8), (300, 12, 2)])
+@pytest.mark.parametrize("which", [0, 1])
+def test_tensor_core_gemm_matches_fp64(W, N, M, B, which):
+    import torch
+    from paper_1508_07441_gb300 import inputs
+
+    pr = _problem(W, N, M)
+    n = pr.n_ch * N * M * B
+    x = inputs.random_complex(n, 11 + N).astype(np.complex64)
+    g = inputs.random_complex(n, 12 + N).astype(np.complex64) if which == 0 else None
+    A = _blocks(pr, which)
+    ref, scale = _reference(A, x.astype(np.complex128), None if g is None else g.astype(np.complex128), N, M, B)
+    xd = torch.from_numpy(x.view(np.float32)).cuda()
+    gd = None if g is None else torch.from_numpy(g.view(np.float32)).cuda()
+    for mode, tol in ((W.WPCD_GEMM_TF32X3, 2e-5), (W.WPCD_GEMM_FP32, 2e-6)):
+        yd = torch.full((2 * n,), float("nan"), dtype=torch.float32, device="cuda")
+        pr.wpcd_channel_gemm(which, mode, gd, xd, yd, B)
+        got = yd.cpu().numpy().view(np.complex64).astype(np.complex128).reshape(ref.shape)
+        err = np.abs(got - ref) / np.maximum(scale, 1e-30)
+        # every output written (no NaN left) and within the FP32-class bound
+        assert np.all(np.isfinite(got)), mode
+        assert err.max() < tol, (mode, err.max())
+
+
+def test_fp64_channel_gemm_matches_numpy(W):
+    import torch
+    from paper_1508_07441_gb300 import inputs
+
+    N, M, B = 40, 30, 4
+    pr = _problem(W, N, M)
+    n = pr.n_ch * N * M * B
+    x = inputs.random_complex(n, 5)
+    g = inputs.random_complex(n, 6)
+    ref, scale = _reference(_blocks(pr, 0), x, g, N, M, B)
+    yd = torch.zeros(2 * n, dtype=torch.float64, device="cuda")
+    pr.wpcd_channel_gemm(0, W.WPCD_GEMM_FP64, torch.from_numpy(g.view(np.float64)).cuda(),
+                         torch.from_numpy(x.view(np.float64)).cuda(), yd, B)
+    got = yd.cpu().numpy().view(np.complex128).reshape(ref.shape)
+    assert np.max(np.abs(got - ref) / scale) < 1e-14
+
+
+def test_channel_gemm_rejects_bad_arguments(W):
+    import torch
+
+    pr = _problem(W, 20, 10)
+    x = torch.zeros(2 * pr.dim, dtype=torch.float32, device="cuda")
+    with pytest.raises(W.WpcdError, match="mode"):
+        pr.wpcd_channel_gemm(0, 7, None, x, x.clone(), 1)
+    with pytest.raises(W.WpcdError, match="which"):
+        pr.wpcd_channel_gemm(2, W.WPCD_GEMM_FP32, None, x, x.clone(), 1)
+    with pytest.raises(W.WpcdError, match="bad vectors"):
+        pr.wpcd_channel_gemm(0, W.WPCD_GEMM_FP32, None, x, x, 1)
+
+
+@pytest.mark.parametrize("gemm", ["tc", "simt"])
+def test_mixed_solve_with_either_fp32_product(W, orc, monkeypatch, gemm):
+    """The mixed solve refines to the FP64 residual tolerance whichever FP32
+    channel product its inner cycles use; U00 against the oracle."""
+    from paper_1508_07441_gb300 import inputs
+
+    monkeypatch.setenv("WPCD_GEMM", gemm)
+    pe, qe = inputs.tangent_edges(30, 20.0), inputs.tangent_edges(28, 20.0)
+    pr = W.Problem(pe, qe, 4, 4, 16, 3, (-6.0,), (1.0,))
+    P = pr.wpcd_assemble_P(W.WPCD_FP64)
+    E = [-0.3, 0.25, 0.9, 2.0, 4.5]
+    U, stats, st = pr.wpcd_solve(P, E, tol=1e-12, precision=W.WPCD_SOLVE_MIXED, batch=len(E))
+    assert st == W.WPCD_OK and all(s.relres <= 1e-12 for s in stats)
+    opr = orc.Problem(dict(pe=pe, qe=qe, n_p=4, n_q=4, n_x=16, n_ch=3, V=[-6.0], a=[1.0], n_pair_nodes=8))
+    ref = np.array([opr.solve_gmres(e, tol=1e-13, max_iter=300)["U00"] for e in E])
+    assert np.max(np.abs(U - ref) / np.abs(ref)) < 1e-8
