@@ -134,6 +134,122 @@ def fill_flops_per_node(n_ch: int, n_pairs: int) -> int:
     return 4 + (2 + 2 + 4) + 3 * max(n_ch - 2, 0) + 3 * n_pairs
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
+# of the kernel as it stands (profiles/ names the capture); None where no
+# capture of the current kernel exists
+NCU_TRAFFIC = {
+    "fill_kernel<FP64,3>": 436.3e6,
+    "spmm_kernel<float>": 372.4e6,
+    "tc_gemm_kernel<TF32x3> (Vt, G1)": 335.3e6,
+    "spmm_df_kernel": 1539.4e6,
+    "gemm_df_kernel": 1061.9e6,
+}
+
+
+def _time_kernel(stream, flush, fn, reps=3):
+    """Mean device time (ms) of the kernel fn() times (it returns the
+    library's own event timing of that kernel alone), L2 flushed before each
+    launch; the first launch (tuning, operand packing) is not counted."""
+    import torch
+
+    ts = []
+    for _ in range(reps + 1):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            ts.append(fn())
+    return statistics.mean(ts[1:])
+
+
+# FP32 instructions per float-float multiply-add (TwoProduct by FMA with the
+# two cross terms: 4; TwoSum into the accumulator: 6; the error terms: 2)
+FF_INSTR_PER_FMA = 12
+
+
+def kernel_rooflines(W, pr, w, phases, n_nodes, n_e, stream, flush, peaks, f_sm):
+    """Achieved vs peak for the kernels that make up the step, each timed on
+    its own (the library's CUDA events around that kernel, on the bench
+    stream) in the launch configuration the step uses."""
+    import torch
+
+    N, M, n_ch = w["N"], w["M"], w["n_ch"]
+    dim = n_ch * N * M
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    fp64 = 2 * FP64_FMA_PER_SM_CLK * N_SM * f_sm / 1e12
+    fp32 = 2 * FP32_FMA_PER_SM_CLK * N_SM * f_sm / 1e12
+    ff = 2 * FP32_FMA_PER_SM_CLK * N_SM * f_sm / FF_INSTR_PER_FMA / 1e12
+    clk = f"{f_sm / 1e6:.0f} MHz"
+    src64 = f"FP64 pipe: {FP64_FMA_PER_SM_CLK} DFMA/SM/clk x {N_SM} SMs x {clk}"
+    src32 = f"FP32 pipe: {FP32_FMA_PER_SM_CLK} FMA/SM/clk x {N_SM} SMs x {clk}"
+    srcff = (f"float-float on the FP32 pipe: {FP32_FMA_PER_SM_CLK} instr/SM/clk x {N_SM} SMs x {clk} / "
+             f"{FF_INSTR_PER_FMA} instr per multiply-add (FP64-equivalent flops)")
+    out = []
+
+    def entry(kernel, bound, achieved, peak, unit, ms, per_step, what, peak_source):
+        out.append({"kernel": kernel, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                    "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(kernel), "ms_per_launch": ms,
+                    "launches_per_step": per_step, "ms_per_step": ms * per_step, "work": what,
+                    "peak_source": peak_source})
+
+    fpn = fill_flops_per_node(n_ch, pr.n_pairs)
+    entry("fill_kernel<FP64,3>", "alu", n_nodes * fpn / (phases[2] * 1e-3) / 1e12, fp64, "TFLOP/s", phases[2], 1,
+          f"{fpn} FP64 flops per node x {n_nodes} nodes", src64)
+    P = pr.wpcd_assemble_P(W.WPCD_FP64, stream=stream)
+    x64 = torch.randn(2 * dim * n_e, dtype=torch.float64, device="cuda")
+    g64 = torch.randn_like(x64)
+    y64 = torch.empty_like(x64)
+    x32 = torch.randn(2 * dim * n_e, dtype=torch.float32, device="cuda")
+    g32 = torch.randn_like(x32)
+    y32 = torch.empty_like(x32)
+    gemm_flops = 2.0 * N * N * (2 * M * n_e) * n_ch
+    spmm_flops = 4.0 * pr.n_pairs * P.nnz * n_e
+    # FP32 inner cycles: P0 SpMM and the two tensor-core channel products
+    ms = _time_kernel(stream, flush, lambda: pr.wpcd_spmm(P, x32, y32, n_e, mode=W.WPCD_SPMM_FP32, stream=stream,
+                                                           timed=True))
+    entry("spmm_kernel<float>", "alu", spmm_flops / (ms * 1e-3) / 1e12, fp32, "TFLOP/s", ms, 32,
+          f"4 n_pairs nnz B = {spmm_flops:.3e} FP32 flops (one real-by-complex multiply-add per block entry and "
+          "energy; the compensated sums add issued work that is not counted)", src32)
+    tc_bytes = 3.0 * 8 * dim * n_e
+    ms = _time_kernel(stream, flush, lambda: pr.wpcd_channel_gemm(0, W.WPCD_GEMM_TF32X3, g32, x32, y32, n_e,
+                                                                   stream=stream, timed=True))
+    entry("tc_gemm_kernel<TF32x3> (Vt, G1)", "hbm", tc_bytes / (ms * 1e-3) / 1e9, hbm, "GB/s", ms, 32,
+          f"X + G1 read, Y written (FP32 complex): {tc_bytes:.3e} B; {3 * gemm_flops:.3e} TF32 MMA flops",
+          "measured HBM copy (hbm_gbs)")
+    o_bytes = 2.0 * 8 * dim * n_e
+    ms = _time_kernel(stream, flush, lambda: pr.wpcd_channel_gemm(1, W.WPCD_GEMM_TF32X3, None, x32, y32, n_e,
+                                                                   stream=stream, timed=True))
+    entry("tc_gemm_kernel<TF32x3> (O)", "hbm", o_bytes / (ms * 1e-3) / 1e9, hbm, "GB/s", ms, 32,
+          f"Z read, Y written (FP32 complex): {o_bytes:.3e} B (the solve's O step also reads S)",
+          "measured HBM copy (hbm_gbs)")
+    # refinement residual and Born term: float-float SpMM and channel products
+    ms = _time_kernel(stream, flush, lambda: pr.wpcd_spmm(P, x64, y64, n_e, mode=W.WPCD_SPMM_FF, stream=stream,
+                                                           timed=True))
+    entry("spmm_df_kernel", "alu", spmm_flops / (ms * 1e-3) / 1e12, ff, "TFLOP/s", ms, 3,
+          f"4 n_pairs nnz B = {spmm_flops:.3e} FP64-equivalent flops in float-float", srcff)
+    ms = _time_kernel(stream, flush, lambda: pr.wpcd_channel_gemm(1, W.WPCD_GEMM_FF, None, x64, y64, n_e,
+                                                                   stream=stream, timed=True))
+    entry("gemm_df_kernel", "alu", gemm_flops / (ms * 1e-3) / 1e12, ff, "TFLOP/s", ms, 5,
+          f"2 N^2 (2 M B) n_ch = {gemm_flops:.3e} FP64-equivalent flops in float-float", srcff)
+    # the plain FP64 iteration's kernels (the comparison baseline), one energy
+    x1 = torch.randn(2 * dim, dtype=torch.float64, device="cuda")
+    y1 = torch.empty_like(x1)
+    ms = _time_kernel(stream, flush, lambda: pr.wpcd_spmm(P, x1, y1, 1, mode=W.WPCD_SPMM_FP64, stream=stream,
+                                                           timed=True))
+    spmv_bytes = P.nnz * (4 + 8 * pr.n_pairs) + 8 * (N * M + 1) + 2 * 16 * dim
+    spmv_flops = 4.0 * pr.n_pairs * P.nnz
+    entry("spmm_kernel<double> (1 RHS)", "alu", spmv_flops / (ms * 1e-3) / 1e12, fp64, "TFLOP/s", ms, 0,
+          f"{spmv_flops:.3e} FP64 flops, {spmv_bytes:.3e} B (HBM fraction "
+          f"{spmv_bytes / (ms * 1e-3) / 1e9 / hbm:.3f}): at 0.45 flop/B it sits above GB300's FP64 ridge "
+          f"({fp64 * 1e3 / hbm:.2f} flop/B), so the FP64 pipe, not HBM, bounds it", src64)
+    ms = _time_kernel(stream, flush, lambda: pr.wpcd_channel_gemm(1, W.WPCD_GEMM_FP64, None, x1, y1, 1,
+                                                                   stream=stream, timed=True))
+    g1 = 2.0 * N * N * (2 * M) * n_ch
+    entry("gemm_kernel<double> (1 RHS)", "alu", g1 / (ms * 1e-3) / 1e12, fp64, "TFLOP/s", ms, 0,
+          f"2 N^2 (2 M) n_ch = {g1:.3e} FP64 flops", src64)
+    P.close()
+    return out
+
+
 def run_reference(args):
     """The oracle (FP64 C, OpenMP) on the host cores: the same workload and
     metric; each step assembles P0 for the full lattice."""
@@ -470,21 +586,16 @@ def main():
         P5.close()
         del ws
 
-    # ---- roofline of the dominant kernel (from the live phase timings) ----
+    # ---- rooflines of the step's kernels, timed live (CUDA events on the
+    # bench stream, L2 flushed before every timed launch); the dominant
+    # kernel (largest per-step time) becomes `roofline`
     peaks, peak_src = measured_peaks()
     clocks = clk.summary()
     f_sm = (clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    fp64_peak = 2 * FP64_FMA_PER_SM_CLK * N_SM * f_sm / 1e12  # TFLOP/s
-    n_pairs = pr.n_pairs
-    fill_flops = n_nodes * fill_flops_per_node(n_ch, n_pairs)
-    fill_ms = phases[2]
-    achieved = fill_flops / (fill_ms * 1e-3) / 1e12
-    roofline = {"kernel": "fill_kernel<FP64,3> (node values + segmented reduction)",
-                "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak, "traffic": None,
-                "peak_source": f"FP64 pipe: {FP64_FMA_PER_SM_CLK} DFMA/SM/clk x {N_SM} SMs x "
-                               f"{f_sm / 1e6:.0f} MHz (median SM clock under load)",
-                "flops_per_node": fill_flops_per_node(n_ch, n_pairs)}
+    rl = kernel_rooflines(W, pr, w, phases, n_nodes, len(energies), stream, flush, peaks, f_sm)
+    dom = max(rl, key=lambda r: r["ms_per_step"])  # the kernel with the largest share of the step
+    roofline = {k: dom[k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac", "traffic")}
+    roofline["peak_source"] = dom["peak_source"]
 
     # ---- accuracy against the oracle and the CPU baseline -----------------
     cpu = None
@@ -554,6 +665,7 @@ def main():
         "batching": batching,
         "roofline": roofline,
         "roofline_peak_source": peak_src,
+        "kernel_rooflines": rl,
         "cpu_baseline": cpu,
         "e2e": {"value": world * n_nodes / e2e_s / 1e9, "unit": "Gnodes/s",
                 "s_per_step": e2e_s, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

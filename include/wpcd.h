@@ -173,10 +173,15 @@ wpcd_status wpcd_kapply(const wpcd_problem *pr, const wpcd_P *P, const double *g
 
 /* precision of the solve */
 #define WPCD_SOLVE_FP64 0  /* plain FP64 iteration (the comparison baseline) */
-#define WPCD_SOLVE_MIXED 1 /* FP32 inner Krylov cycles (FP32 P0 values, FP32
-                              block GEMMs, compensated FP32 SpMM sums) inside
-                              an FP64 iterative-refinement loop whose
-                              residual b - (I - K) u is formed in FP64 */
+#define WPCD_SOLVE_MIXED 1 /* FP32 inner Krylov cycles (FP32 P0 values,
+                              tensor-core TF32x3 block products, compensated
+                              FP32 SpMM sums) inside an iterative-refinement
+                              loop whose Born term and residual
+                              b - (I - K) u are formed in float-float
+                              arithmetic on the FP32 pipe (FP64-class, about
+                              48 significant bits; the single-problem solve) */
+#define WPCD_SOLVE_MIXED_FP64 2 /* the same with the Born term and residual
+                              in native FP64 */
 
 typedef struct {
   int method;      /* WPCD_SUM_KRYLOV or WPCD_SUM_WYNN (Wynn: FP64, one energy at a time) */
@@ -185,7 +190,9 @@ typedef struct {
   double tol;      /* Krylov, mixed: relative residual; Wynn: relative change */
   int check_every; /* FP64 Krylov: read the residual estimates back every n
                       steps (1 gives exact per-energy step counts) */
-  int precision;   /* WPCD_SOLVE_FP64 or WPCD_SOLVE_MIXED */
+  int precision;   /* WPCD_SOLVE_FP64, WPCD_SOLVE_MIXED or WPCD_SOLVE_MIXED_FP64
+                      (the grouped solve forms its residual in FP64 in both
+                      mixed modes) */
   int batch;       /* energies solved together in one batched iteration
                       (block K applications, SpMM over the batch); 0: all */
   int inner_iter;  /* mixed: Krylov steps per refinement cycle (0: 16) */
@@ -258,25 +265,48 @@ wpcd_status wpcd_solve_batch(int n_prob, wpcd_problem *const *problems, const wp
                              const double *const *E, const int *n_E, const wpcd_solve_opts *opts,
                              double *const *U00, wpcd_solve_stats *const *stats, void *stream);
 
+/* arithmetic of wpcd_spmm */
+#define WPCD_SPMM_FP64 0 /* FP64 vectors, the P's own value precision */
+#define WPCD_SPMM_FP32 1 /* FP32 vectors and values (FP32 values made from FP64
+                            ones on first use), blocked compensated sums */
+#define WPCD_SPMM_FF 2   /* FP64 vectors in and out, float-float arithmetic on
+                            the FP32 pipe (about 48 significant bits), as in
+                            the refinement residual of WPCD_SOLVE_MIXED */
+
+/* The sparse step of the K application (Sec. 3.3, Eq. kernel; P0 of
+ * Eq. perm): z = P0 y for n_rhs vectors in the batched layout (device
+ * [n_ch][N][M][n_rhs] complex, energy index innermost, y and z distinct;
+ * FP32 for WPCD_SPMM_FP32, FP64 otherwise).  The launch shape is the
+ * autotuner's choice for the batch, tuned on first use (which synchronises
+ * the stream).  kernel_ms: NULL, or receives the device time of the SpMM
+ * kernel alone (CUDA events on the stream; the call then synchronises). */
+wpcd_status wpcd_spmm(wpcd_problem *pr, wpcd_P *P, int mode, const void *y, void *z, int n_rhs, float *kernel_ms,
+                      void *stream);
+
 /* arithmetic of wpcd_channel_gemm */
 #define WPCD_GEMM_FP64 0   /* FP64 vectors, FP64 SIMT kernel */
 #define WPCD_GEMM_FP32 1   /* FP32 vectors, FP32 SIMT kernel */
 #define WPCD_GEMM_TF32X3 2 /* FP32 vectors, tensor cores (tcgen05): each FP32
                               operand split into TF32 hi + lo, products
                               hi*hi + hi*lo + lo*hi accumulated in FP32 */
+#define WPCD_GEMM_FF 3     /* FP64 vectors in and out, float-float arithmetic on
+                              the FP32 pipe (about 48 significant bits) */
 
 /* One dense step of the K application (Sec. 3.3, Eq. kernel): for every
  * channel block ch, Y_ch = A_ch (G1 o X)_ch with A = Vt (which = 0) or O
  * (which = 1), N x N, applied to the [N][M][n_rhs] complex block of the
  * channel (energy index innermost, as in wpcd_solve).  g: device resolvent
  * in the same layout and precision as x, or NULL for no scaling; x, y:
- * device [n_ch][N][M][n_rhs] complex, FP64 for WPCD_GEMM_FP64 and FP32
- * otherwise, distinct.  The mixed solve runs its FP32 inner cycles with
- * WPCD_GEMM_TF32X3 when N <= 512 (the environment variable WPCD_GEMM=simt
- * selects WPCD_GEMM_FP32 instead).  EINVAL for a bad mode, bad vectors, or
- * WPCD_GEMM_TF32X3 with N > 512; ETIMEOUT if a tensor-core wait ran out. */
+ * device [n_ch][N][M][n_rhs] complex, FP32 for WPCD_GEMM_FP32 and
+ * WPCD_GEMM_TF32X3, FP64 otherwise, distinct.  The mixed solve runs its FP32
+ * inner cycles with WPCD_GEMM_TF32X3 when N <= 512 (the environment
+ * variable WPCD_GEMM=simt selects WPCD_GEMM_FP32 instead) and its residual
+ * with WPCD_GEMM_FF.  kernel_ms: NULL, or receives the device time of the
+ * product kernel alone (the call then synchronises).  EINVAL for a bad
+ * mode, bad vectors, or WPCD_GEMM_TF32X3 with N > 512; ETIMEOUT if a
+ * tensor-core wait ran out. */
 wpcd_status wpcd_channel_gemm(wpcd_problem *pr, int which, int mode, const void *g, const void *x, void *y,
-                              int n_rhs, void *stream);
+                              int n_rhs, float *kernel_ms, void *stream);
 
 /* Autotuner (batching): time the candidate SpMM launch shapes (rows per
  * warp, energy lanes per row, energies per lane = RHS tile width) for a

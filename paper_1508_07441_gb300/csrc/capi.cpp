@@ -48,6 +48,11 @@ static void free_tables(DeviceTables &d) {
   d.O32 = d.Vt32 = nullptr;
   cudaFree(d.O_tc);
   cudaFree(d.Vt_tc);
+  cudaFree(d.O_h);
+  cudaFree(d.O_l);
+  cudaFree(d.Vt_h);
+  cudaFree(d.Vt_l);
+  d.O_h = d.O_l = d.Vt_h = d.Vt_l = nullptr;
   cudaFree(d.tc_err);
   d.O_tc = d.Vt_tc = nullptr;
   d.tc_err = nullptr;
@@ -279,6 +284,8 @@ void wpcd_P_destroy(wpcd_P *P) {
   cudaFree(P->val64);
   cudaFree(P->val32);
   cudaFree(P->val32_copy);
+  cudaFree(P->val_h);
+  cudaFree(P->val_l);
   delete P;
 }
 
@@ -361,12 +368,22 @@ wpcd_status wpcd_solve_batch(int n_prob, wpcd_problem *const *problems, const wp
   WPCD_GUARD_END
 }
 
+wpcd_status wpcd_spmm(wpcd_problem *pr, wpcd_P *P, int mode, const void *y, void *z, int n_rhs, float *kernel_ms,
+                      void *stream) {
+  WPCD_GUARD_BEGIN
+  clear_error();
+  if (!pr || !P) return set_error(WPCD_EINVAL, "null problem or P");
+  if (P->pr != pr) return set_error(WPCD_EINVAL, "P was assembled for another problem");
+  return spmm_apply(pr, P, mode, y, z, n_rhs, kernel_ms, static_cast<cudaStream_t>(stream));
+  WPCD_GUARD_END
+}
+
 wpcd_status wpcd_channel_gemm(wpcd_problem *pr, int which, int mode, const void *g, const void *x, void *y,
-                              int n_rhs, void *stream) {
+                              int n_rhs, float *kernel_ms, void *stream) {
   WPCD_GUARD_BEGIN
   clear_error();
   if (!pr) return set_error(WPCD_EINVAL, "null problem");
-  return channel_gemm(pr, which, mode, g, x, y, n_rhs, static_cast<cudaStream_t>(stream));
+  return channel_gemm(pr, which, mode, g, x, y, n_rhs, kernel_ms, static_cast<cudaStream_t>(stream));
   WPCD_GUARD_END
 }
 

@@ -29,6 +29,14 @@ struct Cx<float> {
   using t = float2;
 };
 
+// one block-CSR P0 and the SpMM launch shape (rows per warp, energy lanes)
+struct SpmmParams {
+  int n_cells, B, rpw, el;
+  const int64_t *row_ptr;
+  const int32_t *col;
+  int64_t nnz;
+};
+
 // SpMM accumulators: plain FP64 sums, or FP32 float-float sums (Knuth's
 // TwoSum on the running sum, the rounding errors gathered in lo)
 struct AccD {
@@ -239,6 +247,33 @@ __device__ __forceinline__ void gemm_tile(int n, int64_t ncol, const T *__restri
       }
     }
 }
+
+// device time of the launches between start() and stop() (optional)
+struct LaunchTimer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaStream_t s;
+  float *out;
+  LaunchTimer(float *ms, cudaStream_t st) : s(st), out(ms) {
+    if (out) {
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+    }
+  }
+  void start() {
+    if (out) cudaEventRecord(a, s);
+  }
+  void stop() {
+    if (out) cudaEventRecord(b, s);
+  }
+  ~LaunchTimer() {
+    if (out) {
+      cudaEventSynchronize(b);
+      cudaEventElapsedTime(out, a, b);
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  }
+};
 
 // ---------------------------------------------------------------------------
 // Krylov least squares, one thread per system (energy)

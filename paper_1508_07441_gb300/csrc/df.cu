@@ -1,0 +1,454 @@
+// Float-float K application for the refinement residual of the mixed solve
+// (Sec. 3.3, Eq. kernel: K = O P0 Vt G1).
+//
+// GB300 runs FP64 at 1/64 of its FP32 rate, so in the mixed solve the FP64
+// K applications (Born term, refinement residuals) cost more than all the
+// FP32 inner cycles.  Here they run on the FP32 pipe in float-float
+// arithmetic: every FP64 operand x is held as an unevaluated sum hi + lo of
+// two floats (hi = fl(x), lo = fl(x - hi); about 48 significant bits), a
+// product a b as p + e with p = fl(a_h b_h) and e the exact error of p
+// (TwoProduct with an FMA) plus the cross terms a_h b_l + a_l b_h, and sums
+// are carried with Knuth's TwoSum.  The result is FP64-class: relative
+// error ~1e-14, far below the 1e-10 residual tolerance of the refinement.
+//
+//   df_split_scaled_kernel  (G1 o x) in FP64 -> float-float panel
+//   gemm_df_kernel          C = A B for every channel block, A = Vt or O
+//                           pre-split once per problem
+//   spmm_df_kernel          z = P0 y, P0 values pre-split once per matrix
+// The intermediates stay float-float; the last product writes FP64.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "common.cuh"
+#include "wpcd_internal.h"
+
+namespace wpcd {
+namespace {
+
+// Knuth's TwoSum of (hi, p) with the error folded into lo together with e
+__device__ __forceinline__ void df_add(float &hi, float &lo, float p, float e) {
+  const float s = __fadd_rn(hi, p);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+
+// (ah + al)(bh + bl) = p + e: p the rounded product, e its exact error
+// (TwoProduct by FMA) plus the cross terms; al bl is below the precision
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &p, float &e) {
+  p = __fmul_rn(ah, bh);
+  e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+}
+
+// renormalise (hi, lo) so that |lo| <= ulp(hi) / 2 (Fast2Sum)
+__device__ __forceinline__ void df_norm(float &hi, float &lo) {
+  const float s = __fadd_rn(hi, lo);
+  lo = __fsub_rn(lo, __fsub_rn(s, hi));
+  hi = s;
+}
+
+__global__ void df_split_kernel(int64_t n, const double *__restrict__ x, float *__restrict__ hi,
+                                float *__restrict__ lo) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n; f += (int64_t)gridDim.x * blockDim.x) {
+    const double v = x[f];
+    const float h = (float)v;
+    hi[f] = h;
+    lo[f] = (float)(v - (double)h);
+  }
+}
+
+// panel = G1 o x (complex, FP64), split into float-float real arrays
+__global__ void df_split_scaled_kernel(int64_t nc, const double2 *__restrict__ x, const double2 *__restrict__ g,
+                                       float *__restrict__ hi, float *__restrict__ lo) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nc; f += (int64_t)gridDim.x * blockDim.x) {
+    const double2 a = x[f];
+    double2 v = a;
+    if (g) {
+      const double2 b = g[f];
+      v = make_double2(b.x * a.x - b.y * a.y, b.x * a.y + b.y * a.x);
+    }
+    const float hr = (float)v.x, hm = (float)v.y;
+    hi[2 * f] = hr;
+    hi[2 * f + 1] = hm;
+    lo[2 * f] = (float)(v.x - (double)hr);
+    lo[2 * f + 1] = (float)(v.y - (double)hm);
+  }
+}
+
+// C[b] (n x ncol) = A[b] (n x n) B[b] (n x ncol) in float-float; the tiling
+// of the FP64 block product (32 x 64 outputs per CTA, 2 x 4 per thread).
+// OUT_DF: C as a float-float pair (Ch, Cl); otherwise FP64 C.
+template <bool OUT_DF>
+__global__ void __launch_bounds__(G_THREADS) gemm_df_kernel(int n, int64_t ncol, const float *__restrict__ Ah,
+                                                            const float *__restrict__ Al,
+                                                            const float *__restrict__ Bh,
+                                                            const float *__restrict__ Bl, double *__restrict__ C,
+                                                            float *__restrict__ Ch, float *__restrict__ Cl) {
+  __shared__ float sAh[GB_K][GB_M + 1], sAl[GB_K][GB_M + 1];
+  __shared__ float sBh[GB_K][GB_N], sBl[GB_K][GB_N];
+  const int b = blockIdx.z;
+  const size_t offA = (size_t)b * n * n, offB = (size_t)b * n * ncol;
+  const int row0 = blockIdx.y * GB_M;
+  const int64_t col0 = (int64_t)blockIdx.x * GB_N;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  float hi[2][4], lo[2][4];
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) hi[u][v] = lo[u][v] = 0.f;
+  for (int k0 = 0; k0 < n; k0 += GB_K) {
+    for (int t = threadIdx.x; t < GB_M * GB_K; t += G_THREADS) {
+      const int r = t / GB_K, kk = t % GB_K;
+      const int gr = row0 + r, gk = k0 + kk;
+      const bool in = gr < n && gk < n;
+      const size_t o = offA + (size_t)gr * n + gk;
+      sAh[kk][r] = in ? Ah[o] : 0.f;
+      sAl[kk][r] = in ? Al[o] : 0.f;
+    }
+    for (int t = threadIdx.x; t < GB_K * GB_N; t += G_THREADS) {
+      const int kk = t / GB_N, cc = t % GB_N;
+      const int gk = k0 + kk;
+      const int64_t gc = col0 + cc;
+      const bool in = gk < n && gc < ncol;
+      const size_t o = offB + (size_t)gk * ncol + gc;
+      sBh[kk][cc] = in ? Bh[o] : 0.f;
+      sBl[kk][cc] = in ? Bl[o] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < GB_K; ++kk) {
+      float ah[2], al[2], bh[4], bl[4];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        ah[u] = sAh[kk][ty + 16 * u];
+        al[u] = sAl[kk][ty + 16 * u];
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        bh[v] = sBh[kk][tx + 16 * v];
+        bl[v] = sBl[kk][tx + 16 * v];
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          float p, e;
+          df_mul(ah[u], al[u], bh[v], bl[v], p, e);
+          df_add(hi[u][v], lo[u][v], p, e);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int gr = row0 + ty + 16 * u;
+      const int64_t gc = col0 + tx + 16 * v;
+      if (gr < n && gc < ncol) {
+        const size_t o = offB + (size_t)gr * ncol + gc;
+        float h = hi[u][v], l = lo[u][v];
+        df_norm(h, l);
+        if (OUT_DF) {
+          Ch[o] = h;
+          Cl[o] = l;
+        } else {
+          C[o] = (double)h + (double)l;
+        }
+      }
+    }
+}
+
+// z = P0 y in float-float: the SpMM lane layout (rows per warp, energy
+// lanes, nonzero lanes, EPT strided energies per lane); values pre-split
+// (vl NULL for FP32-valued matrices, whose values are exact in hi)
+template <int NCH, int EPT>
+__global__ void __launch_bounds__(256) spmm_df_kernel(SpmmParams S, const float *__restrict__ vh,
+                                                      const float *__restrict__ vl, const float2 *__restrict__ yh,
+                                                      const float2 *__restrict__ yl, float2 *__restrict__ zh,
+                                                      float2 *__restrict__ zl) {
+  constexpr int NPAIR = pair_count(NCH);
+  const int lane = threadIdx.x & 31;
+  const int lpr = 32 / S.rpw, nl_count = lpr / S.el;
+  const int r_in = lane / lpr, sub = lane % lpr;
+  const int el = sub % S.el, nl = sub / S.el;
+  const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int n_warps = gridDim.x * blockDim.x / 32;
+  const int e_base = blockIdx.y * S.el * EPT;
+  const int B = S.B;
+  for (int base = warp_global * S.rpw; base < S.n_cells; base += n_warps * S.rpw) {
+    const int c = base + r_in;
+    const bool active = c < S.n_cells;
+    float ah[NCH][EPT][2], al[NCH][EPT][2];
+#pragma unroll
+    for (int l = 0; l < NCH; ++l)
+#pragma unroll
+      for (int t = 0; t < EPT; ++t) ah[l][t][0] = ah[l][t][1] = al[l][t][0] = al[l][t][1] = 0.f;
+    const int64_t b = active ? S.row_ptr[c] : 0, e = active ? S.row_ptr[c + 1] : 0;
+    for (int64_t o = b + nl; o < e; o += nl_count) {
+      const int tc = __ldg(S.col + o);
+      float wh[NPAIR], wl[NPAIR];
+#pragma unroll
+      for (int m = 0; m < NPAIR; ++m) {
+        wh[m] = __ldg(vh + (size_t)m * S.nnz + o);
+        wl[m] = vl ? __ldg(vl + (size_t)m * S.nnz + o) : 0.f;
+      }
+#pragma unroll
+      for (int t = 0; t < EPT; ++t) {
+        const int en = e_base + el + S.el * t;
+        if (en < B) {
+          float2 qh[NCH], ql[NCH];
+#pragma unroll
+          for (int l = 0; l < NCH; ++l) {
+            const size_t yo = ((size_t)l * S.n_cells + tc) * B + en;
+            qh[l] = __ldg(yh + yo);
+            ql[l] = __ldg(yl + yo);
+          }
+#pragma unroll
+          for (int m = 0; m < NPAIR; ++m) {
+            const int l = pair_first(NCH, m), lp = pair_second(NCH, m);
+            float p, er;
+            df_mul(wh[m], wl[m], qh[lp].x, ql[lp].x, p, er);
+            df_add(ah[l][t][0], al[l][t][0], p, er);
+            df_mul(wh[m], wl[m], qh[lp].y, ql[lp].y, p, er);
+            df_add(ah[l][t][1], al[l][t][1], p, er);
+          }
+        }
+      }
+    }
+    for (int off = S.el; off < lpr; off <<= 1)
+#pragma unroll
+      for (int l = 0; l < NCH; ++l)
+#pragma unroll
+        for (int t = 0; t < EPT; ++t)
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const float oh = __shfl_xor_sync(0xffffffffu, ah[l][t][q], off);
+            const float ol = __shfl_xor_sync(0xffffffffu, al[l][t][q], off);
+            df_add(ah[l][t][q], al[l][t][q], oh, ol);
+          }
+    if (active && nl == 0) {
+#pragma unroll
+      for (int t = 0; t < EPT; ++t) {
+        const int en = e_base + el + S.el * t;
+        if (en < B)
+#pragma unroll
+          for (int l = 0; l < NCH; ++l) {
+            float hr = ah[l][t][0], lr = al[l][t][0], hm = ah[l][t][1], lm = al[l][t][1];
+            df_norm(hr, lr);
+            df_norm(hm, lm);
+            const size_t zo = ((size_t)l * S.n_cells + c) * B + en;
+            zh[zo] = make_float2(hr, hm);
+            zl[zo] = make_float2(lr, lm);
+          }
+      }
+    }
+  }
+}
+
+// Vt e0 per energy in float-float: column 0 of Vt_0 at (channel 0, q-bin j0)
+__global__ void df_born_vt_kernel(int64_t n, int B, int N, int M, const float *Vh, const float *Vl, const int *r0,
+                                  float2 *yh, float2 *yl) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n; f += (int64_t)gridDim.x * blockDim.x) {
+    const int e = (int)(f % B);
+    const int64_t r = f / B;
+    float h = 0.f, l = 0.f;
+    if (r < (int64_t)N * M && (int)(r % M) == r0[e]) {
+      h = Vh[(r / M) * N];
+      l = Vl[(r / M) * N];
+    }
+    yh[f] = make_float2(h, 0.f);
+    yl[f] = make_float2(l, 0.f);
+  }
+}
+
+__global__ void df_join_kernel(int64_t n, const float *__restrict__ hi, const float *__restrict__ lo,
+                               double *__restrict__ x) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n; f += (int64_t)gridDim.x * blockDim.x)
+    x[f] = (double)hi[f] + (double)lo[f];
+}
+
+template <bool OUT_DF>
+void gemm_df(const wpcd_problem *pr, bool use_O, const float *Bh, const float *Bl, double *C, float *Ch, float *Cl,
+             int64_t ncol, cudaStream_t s) {
+  const int N = pr->N;
+  dim3 grid((unsigned)((ncol + GB_N - 1) / GB_N), (N + GB_M - 1) / GB_M, pr->n_ch);
+  gemm_df_kernel<OUT_DF><<<grid, G_THREADS, 0, s>>>(N, ncol, use_O ? pr->d.O_h : pr->d.Vt_h,
+                                                    use_O ? pr->d.O_l : pr->d.Vt_l, Bh, Bl, C, Ch, Cl);
+  count_launches(1);
+}
+
+wpcd_status spmm_df(const wpcd_problem *pr, const wpcd_P *P, const float *yh, const float *yl, float *zh, float *zl,
+                    int B, cudaStream_t s) {
+  SpmmConfig cfg;  // the FP64 SpMM's tuned shape for this batch
+  wpcd_status st = tune_spmm(pr, const_cast<wpcd_P *>(P), B, 0, s, &cfg);
+  if (st != WPCD_OK) return st;
+  SpmmParams S{};
+  S.n_cells = pr->N * pr->M;
+  S.B = B;
+  S.rpw = cfg.rpw;
+  S.el = cfg.el;
+  S.row_ptr = P->row_ptr;
+  S.col = P->col;
+  S.nnz = P->nnz;
+  const float *vh = P->prec == WPCD_FP64 ? P->val_h : P->val32;
+  const float *vl = P->prec == WPCD_FP64 ? P->val_l : nullptr;
+  const float2 *y2h = reinterpret_cast<const float2 *>(yh), *y2l = reinterpret_cast<const float2 *>(yl);
+  float2 *z2h = reinterpret_cast<float2 *>(zh), *z2l = reinterpret_cast<float2 *>(zl);
+  dim3 grid(grid_for((int64_t)S.n_cells, 8 * cfg.rpw, 152 * 16), (B + cfg.el * cfg.ept - 1) / (cfg.el * cfg.ept));
+#define WPCD_DF_EPT(NCH, EPT) spmm_df_kernel<NCH, EPT><<<grid, 256, 0, s>>>(S, vh, vl, y2h, y2l, z2h, z2l)
+#define WPCD_DF_CASE(NCH)  \
+  case NCH:                \
+    if (cfg.ept == 1)      \
+      WPCD_DF_EPT(NCH, 1); \
+    else if (cfg.ept == 2) \
+      WPCD_DF_EPT(NCH, 2); \
+    else                   \
+      WPCD_DF_EPT(NCH, 4); \
+    break;
+  switch (pr->n_ch) {
+    WPCD_DF_CASE(1)
+    WPCD_DF_CASE(2)
+    WPCD_DF_CASE(3)
+    WPCD_DF_CASE(4)
+    WPCD_DF_CASE(5)
+    default:
+      return set_error(WPCD_EINVAL, "unsupported channel count for the SpMM");
+  }
+#undef WPCD_DF_CASE
+#undef WPCD_DF_EPT
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? WPCD_OK : cuda_error(e, "float-float spmm launch");
+}
+
+}  // namespace
+
+DfWork::~DfWork() {
+  cudaFree(xh);
+  cudaFree(xl);
+  cudaFree(yh);
+  cudaFree(yl);
+}
+
+cudaError_t DfWork::alloc(size_t dim, int B) {
+  const size_t bytes = 2 * sizeof(float) * dim * (size_t)B;
+  cudaError_t e;
+  if ((e = cudaMalloc(&xh, bytes)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&xl, bytes)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&yh, bytes)) != cudaSuccess) return e;
+  return cudaMalloc(&yl, bytes);
+}
+
+// split O, Vt (once per problem) and FP64 P0 values (once per matrix)
+wpcd_status df_prepare(wpcd_problem *pr, wpcd_P *P, cudaStream_t s) {
+  const int64_t nmat = (int64_t)pr->n_ch * pr->N * pr->N;
+  if (!pr->d.O_h) {
+    WPCD_CUDA_TRY(cudaMalloc(&pr->d.O_h, sizeof(float) * nmat));
+    WPCD_CUDA_TRY(cudaMalloc(&pr->d.O_l, sizeof(float) * nmat));
+    WPCD_CUDA_TRY(cudaMalloc(&pr->d.Vt_h, sizeof(float) * nmat));
+    WPCD_CUDA_TRY(cudaMalloc(&pr->d.Vt_l, sizeof(float) * nmat));
+    df_split_kernel<<<grid_for(nmat, 256), 256, 0, s>>>(nmat, pr->d.O, pr->d.O_h, pr->d.O_l);
+    df_split_kernel<<<grid_for(nmat, 256), 256, 0, s>>>(nmat, pr->d.Vt, pr->d.Vt_h, pr->d.Vt_l);
+    count_launches(2);
+  }
+  if (P && P->prec == WPCD_FP64 && !P->val_h) {
+    const int64_t nv = (int64_t)P->nnz * P->n_pairs;
+    WPCD_CUDA_TRY(cudaMalloc(&P->val_h, sizeof(float) * nv + 4));
+    WPCD_CUDA_TRY(cudaMalloc(&P->val_l, sizeof(float) * nv + 4));
+    df_split_kernel<<<grid_for(nv, 256), 256, 0, s>>>(nv, P->val64, P->val_h, P->val_l);
+    count_launches(1);
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? WPCD_OK : cuda_error(e, "float-float split");
+}
+
+// out = K x = O P0 Vt (g o x) for a batch of B energies, FP64 in and out,
+// float-float inside
+wpcd_status df_kapply(const wpcd_problem *pr, const wpcd_P *P, const double *g, const double *x, double *out, int B,
+                      DfWork &w, cudaStream_t s) {
+  const int64_t nc = (int64_t)pr->n_ch * pr->N * pr->M * B;  // complex elements
+  const int64_t ncol = 2LL * pr->M * B;
+  df_split_scaled_kernel<<<grid_for(nc, 256), 256, 0, s>>>(nc, reinterpret_cast<const double2 *>(x),
+                                                          reinterpret_cast<const double2 *>(g), w.xh, w.xl);
+  count_launches(1);
+  gemm_df<true>(pr, false, w.xh, w.xl, nullptr, w.yh, w.yl, ncol, s);
+  wpcd_status st = spmm_df(pr, P, w.yh, w.yl, w.xh, w.xl, B, s);
+  if (st != WPCD_OK) return st;
+  gemm_df<false>(pr, true, w.xh, w.xl, out, nullptr, nullptr, ncol, s);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? WPCD_OK : cuda_error(e, "float-float kapply launch");
+}
+
+// y = A (g o x) per channel block in float-float, FP64 in and out
+wpcd_status df_gemm_op(wpcd_problem *pr, bool use_O, const double *g, const double *x, double *y, int B, float *ms,
+                       cudaStream_t s) {
+  wpcd_status st = df_prepare(pr, nullptr, s);
+  if (st != WPCD_OK) return st;
+  const size_t dim = (size_t)pr->n_ch * pr->N * pr->M;
+  DfWork w;
+  WPCD_CUDA_TRY(w.alloc(dim, B));
+  const int64_t nc = (int64_t)dim * B;
+  df_split_scaled_kernel<<<grid_for(nc, 256), 256, 0, s>>>(nc, reinterpret_cast<const double2 *>(x),
+                                                          reinterpret_cast<const double2 *>(g), w.xh, w.xl);
+  count_launches(1);
+  {
+    LaunchTimer t(ms, s);
+    t.start();
+    gemm_df<false>(pr, use_O, w.xh, w.xl, y, nullptr, nullptr, 2LL * pr->M * B, s);
+    t.stop();
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "float-float gemm launch");
+  WPCD_CUDA_TRY(cudaStreamSynchronize(s));  // the work space is freed on return
+  return WPCD_OK;
+}
+
+// z = P0 y in float-float, FP64 in and out
+wpcd_status df_spmm_op(wpcd_problem *pr, wpcd_P *P, const double *y, double *z, int B, float *ms, cudaStream_t s) {
+  wpcd_status st = df_prepare(pr, P, s);
+  if (st != WPCD_OK) return st;
+  const size_t dim = (size_t)pr->n_ch * pr->N * pr->M;
+  const int64_t nr = 2LL * (int64_t)dim * B;  // reals
+  DfWork w;
+  WPCD_CUDA_TRY(w.alloc(dim, B));
+  df_split_kernel<<<grid_for(nr, 256), 256, 0, s>>>(nr, y, w.yh, w.yl);
+  count_launches(1);
+  {
+    SpmmConfig cfg;  // tune outside the timed launch
+    st = tune_spmm(pr, P, B, 0, s, &cfg);
+    if (st != WPCD_OK) return st;
+    LaunchTimer t(ms, s);
+    t.start();
+    st = spmm_df(pr, P, w.yh, w.yl, w.xh, w.xl, B, s);
+    t.stop();
+  }
+  if (st != WPCD_OK) return st;
+  df_join_kernel<<<grid_for(nr, 256), 256, 0, s>>>(nr, w.xh, w.xl, z);
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "float-float spmm launch");
+  WPCD_CUDA_TRY(cudaStreamSynchronize(s));
+  return WPCD_OK;
+}
+
+// Born terms b = O P0 Vt e0 for a batch (r0: device on-shell indices)
+wpcd_status df_born(const wpcd_problem *pr, const wpcd_P *P, const int *r0, int B, double *b, DfWork &w,
+                    cudaStream_t s) {
+  const int64_t nc = (int64_t)pr->n_ch * pr->N * pr->M * B;
+  df_born_vt_kernel<<<grid_for(nc, 256), 256, 0, s>>>(nc, B, pr->N, pr->M, pr->d.Vt_h, pr->d.Vt_l, r0,
+                                                     reinterpret_cast<float2 *>(w.yh),
+                                                     reinterpret_cast<float2 *>(w.yl));
+  count_launches(1);
+  wpcd_status st = spmm_df(pr, P, w.yh, w.yl, w.xh, w.xl, B, s);
+  if (st != WPCD_OK) return st;
+  gemm_df<false>(pr, true, w.xh, w.xl, b, nullptr, nullptr, 2LL * pr->M * B, s);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? WPCD_OK : cuda_error(e, "float-float born launch");
+}
+
+}  // namespace wpcd

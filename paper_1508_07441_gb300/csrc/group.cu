@@ -894,7 +894,8 @@ wpcd_status solve_group(int n_prob, wpcd_problem *const *prs, const wpcd_P *cons
   if (n_prob < 1 || n_prob > kMaxGroup) return set_error(WPCD_EINVAL, "n_prob must be in [1, WPCD_GROUP_MAX]");
   if (!prs || !Ps || !E || !n_E || !U00) return set_error(WPCD_EINVAL, "NULL group arrays");
   if (opt.method != WPCD_SUM_KRYLOV) return set_error(WPCD_EINVAL, "the grouped solve uses the Krylov summation");
-  if (opt.precision != WPCD_SOLVE_FP64 && opt.precision != WPCD_SOLVE_MIXED)
+  if (opt.precision != WPCD_SOLVE_FP64 && opt.precision != WPCD_SOLVE_MIXED &&
+      opt.precision != WPCD_SOLVE_MIXED_FP64)
     return set_error(WPCD_EINVAL, "unknown precision");
   if (opt.u_init || opt.u_out) return set_error(WPCD_EINVAL, "the grouped solve takes no vectors");
   if (opt.batch != 0) return set_error(WPCD_EINVAL, "the grouped solve takes every energy in one batch (batch 0)");
@@ -921,7 +922,8 @@ wpcd_status solve_group(int n_prob, wpcd_problem *const *prs, const wpcd_P *cons
     }
   }
   WPCD_CUDA_TRY(cudaSetDevice(prs[0]->device));
-  const bool mixed = opt.precision == WPCD_SOLVE_MIXED;
+  // both mixed modes run the refinement residual in native FP64 here
+  const bool mixed = opt.precision != WPCD_SOLVE_FP64;
   gr.n_ch = prs[0]->n_ch;
   gr.prec = Ps[0]->prec;
   // FP32 values of FP64-assembled matrices for the inner cycles

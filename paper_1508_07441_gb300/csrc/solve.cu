@@ -46,6 +46,11 @@ namespace {
 // ---------------------------------------------------------------------------
 // resolvent
 // ---------------------------------------------------------------------------
+// 1 / i for the Mercator series of log(1 + x)
+__constant__ double kInvInt[17] = {0.0,       1.0,        1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,
+                                   1.0 / 6,   1.0 / 7,    1.0 / 8,  1.0 / 9,  1.0 / 10, 1.0 / 11,
+                                   1.0 / 12,  1.0 / 13,   1.0 / 14, 1.0 / 15, 1.0 / 16};
+
 __device__ double f_lin(double q, double s, double sg) {
   // antiderivative of q^2 ln|q + sg s|; (q^3 + sg s^3) ln|.| -> 0 at q = -sg s
   double d = q + sg * s;
@@ -85,18 +90,19 @@ struct ResParams {
 __global__ void resolvent_kernel(ResParams R, double *g) {
   const int dim = R.n_ch * R.N * R.M;
   const int64_t total = (int64_t)R.n_E * dim;
+  const int nchk = R.n_ch * R.N;
+  // threads run over (energy, q-bin j, pseudostate ch*N + k) with the
+  // pseudostate fastest: a warp shares the energy and the bin, so its lanes
+  // mostly take the same branch below (the writes are scattered; their
+  // traffic is small next to the arithmetic)
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    int e, r;
-    if (R.minor) {
-      e = (int)(idx % R.n_E);
-      r = (int)(idx / R.n_E);
-    } else {
-      e = (int)(idx / dim);
-      r = (int)(idx % dim);
-    }
-    int j = r % R.M;
-    int chk = r / R.M;  // ch*N + k
+    const int chk = (int)(idx % nchk);
+    const int64_t rest = idx / nchk;
+    const int j = (int)(rest % R.M);
+    const int e = (int)(rest / R.M);
+    const int r = chk * R.M + j;
+    const int64_t out = R.minor ? (int64_t)r * R.n_E + e : (int64_t)e * dim + r;
     double ek = R.eps[chk];
     double Elo = R.Elo[e], Ehi = R.Ehi[e], D = Ehi - Elo;
     double qa = R.qe[j], qb = R.qe[j + 1];
@@ -126,9 +132,18 @@ __global__ void resolvent_kernel(ResParams R, double *g) {
       const int npts = rho > 32.0 ? 4 : (rho > 4.0 ? 8 : 32);
       const double *t = npts == 4 ? R.gl4_t : (npts == 8 ? R.gl8_t : R.gl_t);
       const double *wg = npts == 4 ? R.gl4_w : (npts == 8 ? R.gl8_w : R.gl_w);
+      // |x| = |D / (E_lo - eps - 3q^2/4)| <= |D| / dist < 0.05 at every node:
+      // log(1 + x) by its Mercator series, x (1 - x (1/2 - x (1/3 - ...))),
+      // with nt terms, nt the least with xmax^nt / (nt + 1) < 1e-17
+      const double xmax = fabs(D) / dist;
+      int nt = 1;
+      for (double pw = xmax; nt < 16 && pw > 1e-17 * (nt + 1); pw *= xmax) ++nt;
       for (int m = 0; m < npts; ++m) {
         double q = mid + half * t[m];
-        s += wg[m] * q * q * log1p(D / (Elo - ek - 0.75 * q * q));
+        const double x = D / (Elo - ek - 0.75 * q * q);
+        double h = 1.0 / nt;
+        for (int i = nt - 1; i >= 1; --i) h = fma(-x, h, kInvInt[i]);
+        s += wg[m] * q * q * (x * h);
       }
       re = half * s;
     } else {
@@ -141,8 +156,8 @@ __global__ void resolvent_kernel(ResParams R, double *g) {
       double a = fmax(qa, lo), b = fmin(qb, hi);
       if (b > a) im = -kPi * ((b - a) * (b * b + b * a + a * a) / 3.0) / (D * Bq);
     }
-    g[2 * idx] = re;
-    g[2 * idx + 1] = im;
+    g[2 * out] = re;
+    g[2 * out + 1] = im;
   }
 }
 
@@ -174,13 +189,6 @@ __global__ void __launch_bounds__(G_THREADS) gemm_kernel(int n, int64_t ncol, co
 // (RHS tile = el * EPT, grid.y walks the tiles).  Values pair-major.
 // FP64 sums in double; FP32 sums blocked and compensated (spmm_row).
 // ---------------------------------------------------------------------------
-struct SpmmParams {
-  int n_cells, B, rpw, el;
-  const int64_t *row_ptr;
-  const int32_t *col;
-  int64_t nnz;
-};
-
 
 template <typename VT, typename T, int NCH, int EPT, bool VEC>
 __global__ void __launch_bounds__(256) spmm_kernel(SpmmParams S, const VT *__restrict__ val,
@@ -1116,9 +1124,10 @@ wpcd_status solve_fp64(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solve
 }
 
 // Mixed precision: FP64 refinement around FP32 inner Krylov cycles
+// (dfw non-NULL: the FP64 K applications of the residual in float-float)
 wpcd_status solve_mixed(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solve_opts &o, SolveCtx &cx,
                         Krylov<float> &kr, Krylov<double> &k64, Workspace<double> &ws64,
-                        Workspace<float> &ws32, std::vector<int> &status, std::vector<double> &relres,
+                        Workspace<float> &ws32, DfWork *dfw, std::vector<int> &status, std::vector<double> &relres,
                         int &n64, int &n32, int &n_outer, bool warm, cudaStream_t s) {
   const int B = cx.B, m = kr.m;
   const int64_t n = (int64_t)cx.dim * B;
@@ -1185,7 +1194,8 @@ wpcd_status solve_mixed(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solv
   for (int outer = 0; outer <= max_outer; ++outer) {
     // r = b - (I - K) u in FP64
     if (outer > 0 || warm) {
-      wpcd_status st = kapply_ws<double>(pr, P, cx.g, cx.u, cx.t, nullptr, B, ws64, s);
+      wpcd_status st = dfw ? df_kapply(pr, P, cx.g, cx.u, cx.t, B, *dfw, s)
+                           : kapply_ws<double>(pr, P, cx.g, cx.u, cx.t, nullptr, B, ws64, s);
       if (st != WPCD_OK) {
         result = st;
         break;
@@ -1432,7 +1442,8 @@ wpcd_status solve(wpcd_problem *pr, const wpcd_P *Pc, const double *E, int n_E,
   if (opt.max_iter < 2 || opt.max_iter > 512) return set_error(WPCD_EINVAL, "max_iter must be in [2, 512]");
   if (!(opt.tol > 0.0)) return set_error(WPCD_EINVAL, "tol must be positive");
   if (opt.method != WPCD_SUM_KRYLOV && opt.method != WPCD_SUM_WYNN) return set_error(WPCD_EINVAL, "unknown method");
-  if (opt.precision != WPCD_SOLVE_FP64 && opt.precision != WPCD_SOLVE_MIXED)
+  if (opt.precision != WPCD_SOLVE_FP64 && opt.precision != WPCD_SOLVE_MIXED &&
+      opt.precision != WPCD_SOLVE_MIXED_FP64)
     return set_error(WPCD_EINVAL, "unknown precision");
   if (opt.method == WPCD_SUM_WYNN && opt.precision != WPCD_SOLVE_FP64)
     return set_error(WPCD_EINVAL, "the Wynn summation runs in FP64 only");
@@ -1461,7 +1472,12 @@ wpcd_status solve(wpcd_problem *pr, const wpcd_P *Pc, const double *E, int n_E,
       if (one.status < worst) worst = one.status;
     }
   } else {
-    const bool mixed = opt.precision == WPCD_SOLVE_MIXED;
+    const bool mixed = opt.precision != WPCD_SOLVE_FP64;
+    const bool dfres = opt.precision == WPCD_SOLVE_MIXED;  // float-float residual
+    if (dfres) {
+      wpcd_status st = df_prepare(pr, P, s);
+      if (st != WPCD_OK) return st;
+    }
     const int Bmax = opt.batch > 0 ? std::min(opt.batch, n_E) : n_E;
     const size_t dim = (size_t)pr->n_ch * pr->N * pr->M;
     if (mixed && tc_enabled() && tc_supported(pr)) {
@@ -1499,7 +1515,9 @@ wpcd_status solve(wpcd_problem *pr, const wpcd_P *Pc, const double *E, int n_E,
       if (st != WPCD_OK) return st;
       Workspace<double> ws64;
       WPCD_CUDA_TRY(ws64.alloc(dim, B));
-      st = born(pr, P, cx, ws64, s);
+      DfWork dfw;
+      if (dfres) WPCD_CUDA_TRY(dfw.alloc(dim, B));
+      st = dfres ? df_born(pr, P, cx.r0, B, cx.b, dfw, s) : born(pr, P, cx, ws64, s);
       if (st != WPCD_OK) return st;
       const bool warm = opt.u_init != nullptr;
       const int64_t n = (int64_t)dim * B;
@@ -1520,7 +1538,8 @@ wpcd_status solve(wpcd_problem *pr, const wpcd_P *Pc, const double *E, int n_E,
         WPCD_CUDA_TRY(k64.alloc(1, B, dim, false));  // norms only
         Workspace<float> ws32;
         WPCD_CUDA_TRY(ws32.alloc(dim, B));
-        st = solve_mixed(pr, P, opt, cx, kr, k64, ws64, ws32, status, relres, n64, n32, n_outer, warm, s);
+        st = solve_mixed(pr, P, opt, cx, kr, k64, ws64, ws32, dfres ? &dfw : nullptr, status, relres, n64, n32,
+                         n_outer, warm, s);
       } else {
         Krylov<double> kr;
         WPCD_CUDA_TRY(kr.alloc(opt.max_iter, B, dim));
@@ -1579,40 +1598,77 @@ wpcd_status solve(wpcd_problem *pr, const wpcd_P *Pc, const double *E, int n_E,
   return worst;
 }
 
+// z = P0 y for n_rhs vectors (the sparse step of the K application)
+wpcd_status spmm_apply(wpcd_problem *pr, wpcd_P *P, int mode, const void *y, void *z, int n_rhs, float *ms,
+                       cudaStream_t s) {
+  if (!y || !z || y == z || n_rhs < 1) return set_error(WPCD_EINVAL, "bad vectors or n_rhs");
+  if (mode < WPCD_SPMM_FP64 || mode > WPCD_SPMM_FF) return set_error(WPCD_EINVAL, "unknown SpMM mode");
+  WPCD_CUDA_TRY(cudaSetDevice(pr->device));
+  if (mode == WPCD_SPMM_FF) return df_spmm_op(pr, P, (const double *)y, (double *)z, n_rhs, ms, s);
+  const bool fp32 = mode == WPCD_SPMM_FP32;
+  if (fp32 && !P->val32 && !P->val32_copy) {
+    WPCD_CUDA_TRY(cudaMalloc(&P->val32_copy, sizeof(float) * (size_t)P->nnz * P->n_pairs + 4));
+    const int64_t nv = (int64_t)P->nnz * P->n_pairs;
+    d2f_kernel<<<grid_for(nv, 256), 256, 0, s>>>(nv, P->val64, P->val32_copy);
+    count_launches(1);
+  }
+  SpmmConfig cfg;  // tune (which synchronises) before any timed launch
+  wpcd_status st = tune_spmm(pr, P, n_rhs, fp32 ? 1 : 0, s, &cfg);
+  if (st != WPCD_OK) return st;
+  LaunchTimer t(ms, s);
+  t.start();
+  st = fp32 ? spmm<float>(pr, P, (const float *)y, (float *)z, n_rhs, s)
+            : spmm<double>(pr, P, (const double *)y, (double *)z, n_rhs, s);
+  t.stop();
+  return st;
+}
+
 // one channel-block product Y = A (G1 o X) of the K application
 wpcd_status channel_gemm(wpcd_problem *pr, int which, int mode, const void *g, const void *x, void *y, int n_rhs,
-                         cudaStream_t s) {
+                         float *ms, cudaStream_t s) {
   if (which != 0 && which != 1) return set_error(WPCD_EINVAL, "which must be 0 (Vt) or 1 (O)");
   if (!x || !y || x == y || n_rhs < 1) return set_error(WPCD_EINVAL, "bad vectors or n_rhs");
   WPCD_CUDA_TRY(cudaSetDevice(pr->device));
   const int N = pr->N;
   const int64_t ncol = 2LL * pr->M * n_rhs;
   dim3 grid((unsigned)((ncol + GB_N - 1) / GB_N), (N + GB_M - 1) / GB_M, pr->n_ch);
-  if (mode == WPCD_GEMM_FP64) {
-    const double *A = which ? pr->d.O : pr->d.Vt;
-    if (g)
-      gemm_kernel<double, true, false><<<grid, G_THREADS, 0, s>>>(N, ncol, A, (const double *)x, (const double *)g,
-                                                                  nullptr, (double *)y);
-    else
-      gemm_kernel<double, false, false><<<grid, G_THREADS, 0, s>>>(N, ncol, A, (const double *)x, nullptr, nullptr,
-                                                                   (double *)y);
-  } else if (mode == WPCD_GEMM_FP32) {
-    const float *A = which ? pr->d.O32 : pr->d.Vt32;
-    if (g)
-      gemm_kernel<float, true, false><<<grid, G_THREADS, 0, s>>>(N, ncol, A, (const float *)x, (const float *)g,
-                                                                 nullptr, (float *)y);
-    else
-      gemm_kernel<float, false, false><<<grid, G_THREADS, 0, s>>>(N, ncol, A, (const float *)x, nullptr, nullptr,
-                                                                  (float *)y);
-  } else if (mode == WPCD_GEMM_TF32X3) {
+  if (mode == WPCD_GEMM_FF)
+    return df_gemm_op(pr, which == 1, (const double *)g, (const double *)x, (double *)y, n_rhs, ms, s);
+  if (mode == WPCD_GEMM_TF32X3) {
     if (!tc_supported(pr)) return set_error(WPCD_EINVAL, "the tensor-core GEMM needs N <= 512");
     wpcd_status st = tc_prepare(pr, s);
     if (st != WPCD_OK) return st;
-    st = tc_gemm(pr, which == 1, (const float *)g, (const float *)x, nullptr, (float *)y, ncol, s);
+    {
+      LaunchTimer t(ms, s);
+      t.start();
+      st = tc_gemm(pr, which == 1, (const float *)g, (const float *)x, nullptr, (float *)y, ncol, s);
+      t.stop();
+    }
     if (st != WPCD_OK) return st;
     return tc_check(pr, s);
-  } else {
-    return set_error(WPCD_EINVAL, "unknown GEMM mode");
+  }
+  if (mode != WPCD_GEMM_FP64 && mode != WPCD_GEMM_FP32) return set_error(WPCD_EINVAL, "unknown GEMM mode");
+  {
+    LaunchTimer t(ms, s);
+    t.start();
+    if (mode == WPCD_GEMM_FP64) {
+      const double *A = which ? pr->d.O : pr->d.Vt;
+      if (g)
+        gemm_kernel<double, true, false><<<grid, G_THREADS, 0, s>>>(N, ncol, A, (const double *)x,
+                                                                    (const double *)g, nullptr, (double *)y);
+      else
+        gemm_kernel<double, false, false><<<grid, G_THREADS, 0, s>>>(N, ncol, A, (const double *)x, nullptr,
+                                                                     nullptr, (double *)y);
+    } else {
+      const float *A = which ? pr->d.O32 : pr->d.Vt32;
+      if (g)
+        gemm_kernel<float, true, false><<<grid, G_THREADS, 0, s>>>(N, ncol, A, (const float *)x, (const float *)g,
+                                                                   nullptr, (float *)y);
+      else
+        gemm_kernel<float, false, false><<<grid, G_THREADS, 0, s>>>(N, ncol, A, (const float *)x, nullptr,
+                                                                    nullptr, (float *)y);
+    }
+    t.stop();
   }
   count_launches(1);
   cudaError_t e = cudaGetLastError();

@@ -86,6 +86,8 @@ struct DeviceTables {
   double *O = nullptr, *Vt = nullptr;           // [n_ch][N][N]
   float *O32 = nullptr, *Vt32 = nullptr;        // FP32 copies for the inner solve
   float *O_tc = nullptr, *Vt_tc = nullptr;      // TF32 hi/lo operand blocks (tc_gemm.cu)
+  float *O_h = nullptr, *O_l = nullptr;         // float-float split of O (df.cu)
+  float *Vt_h = nullptr, *Vt_l = nullptr;       // float-float split of Vt
   int *tc_err = nullptr;                        // tensor-core wait-limit flag
 };
 
@@ -119,6 +121,7 @@ struct wpcd_P {
   float ms = 0.f;
   float ms_phase[3] = {0.f, 0.f, 0.f};  // count, scan, fill
   float *val32_copy = nullptr;          // FP32 values made from FP64 ones (mixed solve)
+  float *val_h = nullptr, *val_l = nullptr;  // float-float split of FP64 values (df.cu)
   std::map<int64_t, SpmmConfig> tuned;  // autotuner choices keyed by (B, precision)
 };
 
@@ -139,8 +142,10 @@ wpcd_status kapply_scratch(const wpcd_problem *pr, const wpcd_P *P, const double
                            double *y, double *scratch_y, double *scratch_z, cudaStream_t s);
 wpcd_status born_vectors(wpcd_problem *pr, const wpcd_P *P, const double *E, int n_E, double *b_major,
                          cudaStream_t s);
+wpcd_status spmm_apply(wpcd_problem *pr, wpcd_P *P, int mode, const void *y, void *z, int n_rhs, float *ms,
+                       cudaStream_t s);
 wpcd_status channel_gemm(wpcd_problem *pr, int which, int mode, const void *g, const void *x, void *y, int n_rhs,
-                         cudaStream_t s);
+                         float *ms, cudaStream_t s);
 // G1 of n_E energies in the batched layout (element (r, e) at r * n_E + e)
 wpcd_status resolvent_minor(const wpcd_problem *pr, const double *E, int n_E, double *g, cudaStream_t s);
 // tc_gemm.cu: tensor-core (TF32 x 3) channel-block products for FP32 vectors
@@ -150,6 +155,21 @@ wpcd_status tc_prepare(wpcd_problem *pr, cudaStream_t s);
 wpcd_status tc_gemm(const wpcd_problem *pr, bool use_O, const float *G, const float *X, const float *S, float *C,
                     int64_t ncol, cudaStream_t s);
 wpcd_status tc_check(const wpcd_problem *pr, cudaStream_t s);
+// df.cu: float-float ("FP64-class", about 48 significant bits) K application
+// on the FP32 pipe, for the refinement residual of the mixed solve
+struct DfWork {
+  float *xh = nullptr, *xl = nullptr, *yh = nullptr, *yl = nullptr;  // [2 dim B] each
+  ~DfWork();
+  cudaError_t alloc(size_t dim, int B);
+};
+wpcd_status df_prepare(wpcd_problem *pr, wpcd_P *P, cudaStream_t s);
+wpcd_status df_kapply(const wpcd_problem *pr, const wpcd_P *P, const double *g, const double *x, double *out, int B,
+                      DfWork &w, cudaStream_t s);
+wpcd_status df_gemm_op(wpcd_problem *pr, bool use_O, const double *g, const double *x, double *y, int B, float *ms,
+                       cudaStream_t s);
+wpcd_status df_spmm_op(wpcd_problem *pr, wpcd_P *P, const double *y, double *z, int B, float *ms, cudaStream_t s);
+wpcd_status df_born(const wpcd_problem *pr, const wpcd_P *P, const int *r0, int B, double *b, DfWork &w,
+                    cudaStream_t s);
 // group.cu
 wpcd_status solve_group(int n_prob, wpcd_problem *const *prs, const wpcd_P *const *Ps, const double *const *E,
                         const int *n_E, const wpcd_solve_opts *o, double *const *U00, wpcd_solve_stats *const *st,

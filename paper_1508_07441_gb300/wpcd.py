@@ -21,8 +21,9 @@ WPCD_OK, WPCD_EINVAL, WPCD_ENOMEM, WPCD_ECUDA = 0, -1, -2, -3
 WPCD_ENOCONV, WPCD_EBREAKDOWN, WPCD_ETIMEOUT, WPCD_ENOBOUND = -4, -5, -6, -7
 WPCD_FP64, WPCD_FP32C = 0, 1
 WPCD_SUM_KRYLOV, WPCD_SUM_WYNN = 0, 1
-WPCD_SOLVE_FP64, WPCD_SOLVE_MIXED = 0, 1
-WPCD_GEMM_FP64, WPCD_GEMM_FP32, WPCD_GEMM_TF32X3 = 0, 1, 2
+WPCD_SOLVE_FP64, WPCD_SOLVE_MIXED, WPCD_SOLVE_MIXED_FP64 = 0, 1, 2
+WPCD_GEMM_FP64, WPCD_GEMM_FP32, WPCD_GEMM_TF32X3, WPCD_GEMM_FF = 0, 1, 2, 3
+WPCD_SPMM_FP64, WPCD_SPMM_FP32, WPCD_SPMM_FF = 0, 1, 2
 
 _P = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
@@ -77,7 +78,8 @@ _SIGS = {
                                         ctypes.POINTER(_D), ctypes.POINTER(ctypes.POINTER(wpcd_solve_stats)),
                                         _P]),
     "wpcd_tune_spmm": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P, _I, _I, _I]),
-    "wpcd_channel_gemm": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P]),
+    "wpcd_channel_gemm": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, ctypes.c_int, _F, _P]),
+    "wpcd_spmm": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, ctypes.c_int, _F, _P]),
     "wpcd_born": (ctypes.c_int, [_P, _P, _D, ctypes.c_int, _P, _P]),
     "wpcd_kapply_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "wpcd_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
@@ -275,11 +277,22 @@ class Problem:
         check(st, allow=allow)
         return U.view(np.complex128), list(stats), st
 
-    def wpcd_channel_gemm(self, which, mode, g, x, y, n_rhs, stream=None):
+    def wpcd_spmm(self, P, y, z, n_rhs, mode=WPCD_SPMM_FP64, stream=None, timed=False):
+        """z = P0 y for n_rhs vectors (device tensors, batched layout).
+        With timed, returns the SpMM kernel's device milliseconds."""
+        ms = ctypes.c_float()
+        check(lib().wpcd_spmm(self._h, P.handle, mode, _tensor_ptr(y), _tensor_ptr(z), n_rhs,
+                              ctypes.byref(ms) if timed else None, _stream_ptr(stream)))
+        return ms.value if timed else None
+
+    def wpcd_channel_gemm(self, which, mode, g, x, y, n_rhs, stream=None, timed=False):
         """y = A (g o x) per channel block, A = Vt (which 0) or O (which 1);
-        g, x, y device tensors in the batched layout (g may be None)."""
+        g, x, y device tensors in the batched layout (g may be None).  With
+        timed, returns the product kernel's device milliseconds."""
+        ms = ctypes.c_float()
         check(lib().wpcd_channel_gemm(self._h, which, mode, _tensor_ptr(g), _tensor_ptr(x), _tensor_ptr(y),
-                                      n_rhs, _stream_ptr(stream)))
+                                      n_rhs, ctypes.byref(ms) if timed else None, _stream_ptr(stream)))
+        return ms.value if timed else None
 
     def wpcd_born(self, P, E, b, stream=None):
         """Born terms into device tensor b (float64, 2 * len(E) * dim)."""

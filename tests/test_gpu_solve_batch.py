@@ -53,12 +53,15 @@ def test_batched_fp64_matches_oracle(W, sys3):
     assert all(2 <= s.n_kapply <= 201 for s in stats)
 
 
+@pytest.mark.parametrize("residual", ["float-float", "fp64"])
 @pytest.mark.parametrize("pname", ["P64", "P32"])
-def test_mixed_matches_oracle(W, sys3, pname):
+def test_mixed_matches_oracle(W, sys3, pname, residual):
+    """Both refinement residuals (float-float on the FP32 pipe, native
+    FP64) reach the FP64 tolerance and the oracle's U00."""
     pr, P64, P32, opr = sys3
     P = P64 if pname == "P64" else P32
-    U, stats, st = pr.wpcd_solve(P, ENERGIES, tol=1e-12, precision=W.WPCD_SOLVE_MIXED,
-                                 batch=len(ENERGIES))
+    prec = W.WPCD_SOLVE_MIXED if residual == "float-float" else W.WPCD_SOLVE_MIXED_FP64
+    U, stats, st = pr.wpcd_solve(P, ENERGIES, tol=1e-12, precision=prec, batch=len(ENERGIES))
     assert st == W.WPCD_OK
     for s in stats:
         assert s.status == W.WPCD_OK and s.relres <= 1e-12

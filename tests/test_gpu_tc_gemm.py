@@ -68,21 +68,30 @@ def test_tensor_core_gemm_matches_fp64(W, N, M, B, which):
         assert err.max() < tol, (mode, err.max())
 
 
-def test_fp64_channel_gemm_matches_numpy(W):
+@pytest.mark.parametrize("mode,tol", [("FP64", 1e-14), ("FF", 1e-12)])
+@pytest.mark.parametrize("which", [0, 1])
+def test_fp64_class_channel_gemm_matches_numpy(W, mode, tol, which):
+    """FP64 SIMT and float-float (FP32 pipe) products against FP64 numpy on
+    the same blocks.  The float-float sum carries its low part in one float,
+    so its error grows like n 2^-48 of the magnitude sum (5e-13 for the
+    n = 140 blocks here; FP64: n 2^-53)."""
     import torch
     from paper_1508_07441_gb300 import inputs
 
-    N, M, B = 40, 30, 4
+    N, M, B = 140, 30, 4
     pr = _problem(W, N, M)
     n = pr.n_ch * N * M * B
     x = inputs.random_complex(n, 5)
-    g = inputs.random_complex(n, 6)
-    ref, scale = _reference(_blocks(pr, 0), x, g, N, M, B)
-    yd = torch.zeros(2 * n, dtype=torch.float64, device="cuda")
-    pr.wpcd_channel_gemm(0, W.WPCD_GEMM_FP64, torch.from_numpy(g.view(np.float64)).cuda(),
-                         torch.from_numpy(x.view(np.float64)).cuda(), yd, B)
+    g = inputs.random_complex(n, 6) if which == 0 else None
+    ref, scale = _reference(_blocks(pr, which), x, g, N, M, B)
+    yd = torch.full((2 * n,), float("nan"), dtype=torch.float64, device="cuda")
+    m = W.WPCD_GEMM_FP64 if mode == "FP64" else W.WPCD_GEMM_FF
+    ms = pr.wpcd_channel_gemm(which, m, None if g is None else torch.from_numpy(g.view(np.float64)).cuda(),
+                              torch.from_numpy(x.view(np.float64)).cuda(), yd, B, timed=True)
+    assert ms > 0.0
     got = yd.cpu().numpy().view(np.complex128).reshape(ref.shape)
-    assert np.max(np.abs(got - ref) / scale) < 1e-14
+    assert np.all(np.isfinite(got))
+    assert np.max(np.abs(got - ref) / scale) < tol
 
 
 def test_channel_gemm_rejects_bad_arguments(W):
@@ -114,3 +123,38 @@ def test_mixed_solve_with_either_fp32_product(W, orc, monkeypatch, gemm):
     opr = orc.Problem(dict(pe=pe, qe=qe, n_p=4, n_q=4, n_x=16, n_ch=3, V=[-6.0], a=[1.0], n_pair_nodes=8))
     ref = np.array([opr.solve_gmres(e, tol=1e-13, max_iter=300)["U00"] for e in E])
     assert np.max(np.abs(U - ref) / np.abs(ref)) < 1e-8
+
+
+@pytest.mark.parametrize("B", [1, 6, 40])
+def test_spmm_matches_oracle_P0(W, orc, B):
+    """wpcd_spmm (z = P0 y, FP64 and FP32 vectors, tuned shapes) against the
+    oracle's own P0 applied with scipy sparse products, per (l, l') block."""
+    import scipy.sparse as sp
+    import torch
+    from paper_1508_07441_gb300 import inputs
+
+    pe, qe = inputs.tangent_edges(26, 20.0), inputs.tangent_edges(22, 20.0)
+    n_ch = 3
+    pr = W.Problem(pe, qe, 4, 4, 16, n_ch, (-6.0,), (1.0,))
+    P = pr.wpcd_assemble_P(W.WPCD_FP64)
+    ref_P = orc.P0(pe, qe, 4, 4, 16, n_ch)
+    n_cells = 26 * 22
+    y = inputs.random_complex(n_ch * n_cells * B, 77 + B).reshape(n_ch, n_cells, B)
+    ref = np.zeros_like(y)
+    mag = np.zeros(y.shape)
+    for m, (l, lp) in enumerate(orc.pair_list(n_ch)):
+        A = sp.csr_matrix((ref_P["val"][:, m], ref_P["col"], ref_P["row_ptr"]), shape=(n_cells, n_cells))
+        ref[l] += A @ y[lp]
+        mag[l] += abs(A) @ np.abs(y[lp])
+    for mode, dt, tol in ((W.WPCD_SPMM_FP64, np.complex128, 1e-9), (W.WPCD_SPMM_FF, np.complex128, 1e-9),
+                          (W.WPCD_SPMM_FP32, np.complex64, 3e-6)):
+        fp32 = mode == W.WPCD_SPMM_FP32
+        yd = torch.from_numpy(y.astype(dt).reshape(-1).view(np.float32 if fp32 else np.float64)).cuda()
+        zd = torch.full_like(yd, float("nan"))
+        ms = pr.wpcd_spmm(P, yd, zd, B, mode=mode, timed=True)
+        assert ms > 0.0
+        got = zd.cpu().numpy().view(dt).astype(np.complex128).reshape(ref.shape)
+        assert np.all(np.isfinite(got))
+        # the P0 values themselves agree with the oracle's to 1e-10 (FP64
+        # assembly); FF carries them to ~2^-48
+        assert np.max(np.abs(got - ref) / np.maximum(mag, 1e-30)) < tol, mode
