@@ -146,6 +146,26 @@ NCU_TRAFFIC = {
 }
 
 
+def max_over_ranks(x, dist=None, device="cuda"):
+    """The largest of the ranks' values of x (every rank gets it); x itself
+    on one process.  The step time of a replicated run is the slowest
+    rank's."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, seconds, world):
+    """Whole-job throughput of a weak-scaling run: every rank processes the
+    same number of independent units (energies, lattices) in the slowest
+    rank's time; no data moves between ranks."""
+    return world * units_per_rank / seconds
+
+
 def _time_kernel(stream, flush, fn, reps=3):
     """Mean device time (ms) of the kernel fn() times (it returns the
     library's own event timing of that kernel alone), L2 flushed before each
@@ -480,18 +500,14 @@ def main():
     launches = W.wpcd_launch_count() - l0
 
     def maxr(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(x, dist, "cuda")
 
     step_ms = maxr(statistics.mean(r["step_ms"] for r in recs))
     asm_ms = maxr(statistics.mean(r["asm_ms"] for r in recs))
     solve_ms = maxr(statistics.mean(r["solve_ms"] for r in recs))
     phases = [statistics.mean(r["phases"][k] for r in recs) for k in range(3)]
-    value = world * n_nodes / (asm_ms * 1e-3) / 1e9
-    energies_per_s = world * len(energies) / (solve_ms * 1e-3)
+    value = job_throughput(n_nodes, asm_ms * 1e-3, world) / 1e9
+    energies_per_s = job_throughput(len(energies), solve_ms * 1e-3, world)
 
     # ---- FP32C assembly (FP64 binning, FP32 node values), same lattice ----
     f32 = []
