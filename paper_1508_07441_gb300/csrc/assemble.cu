@@ -61,6 +61,66 @@ struct BinConst {
   double A, Bp, C, D;
 };
 
+// Bitonic sort of n = E * blockDim.x keys (ascending) with the keys held in
+// registers: thread t owns s[t E .. t E + E - 1].  A compare-exchange at
+// distance j runs inside the thread for j < E, between lanes of a warp
+// (shuffles) for j < 32 E, and through shared memory only beyond that.
+template <int E>
+__device__ void bitonic_sort_reg(uint32_t *s, int n) {
+  const int t = threadIdx.x;
+  uint32_t v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) v[e] = s[t * E + e];
+  for (int k = 2; k <= n; k <<= 1) {
+    for (int j = k >> 1; j >= E; j >>= 1) {
+      if (j < 32 * E) {
+        const int d = j / E;  // partner lane distance
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const uint32_t p = __shfl_xor_sync(0xffffffffu, v[e], d);
+          const int i = t * E + e;
+          const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
+          v[e] = keep_min ? min(v[e], p) : max(v[e], p);
+        }
+      } else {
+        __syncthreads();  // the previous exchange has been read
+#pragma unroll
+        for (int e = 0; e < E; ++e) s[t * E + e] = v[e];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int i = t * E + e;
+          const uint32_t p = s[i ^ j];
+          const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
+          v[e] = keep_min ? min(v[e], p) : max(v[e], p);
+        }
+      }
+    }
+#pragma unroll
+    for (int jj = E / 2; jj >= 1; jj >>= 1) {
+      if (jj < k) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int f = e ^ jj;
+          if (f > e) {
+            const bool up = ((t * E + e) & k) == 0;
+            const uint32_t a = v[e], b = v[f];
+            if ((a > b) == up) {
+              v[e] = b;
+              v[f] = a;
+            }
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int e = 0; e < E; ++e) s[t * E + e] = v[e];
+  __syncthreads();
+}
+
+// shared-memory bitonic sort for any power-of-two n (used below 256 keys)
 template <int NT>
 __device__ void bitonic_sort(uint32_t *s, int n) {
   // n is a power of two; ascending
@@ -124,7 +184,14 @@ __global__ void __launch_bounds__(kThreads) count_kernel(AsmParams P, int64_t *c
     keys[n] = key;
   }
   __syncthreads();
-  bitonic_sort<kThreads>(keys, P.np2);
+  switch (P.np2 / kThreads) {  // keys per thread
+    case 1: bitonic_sort_reg<1>(keys, P.np2); break;
+    case 2: bitonic_sort_reg<2>(keys, P.np2); break;
+    case 4: bitonic_sort_reg<4>(keys, P.np2); break;
+    case 8: bitonic_sort_reg<8>(keys, P.np2); break;
+    case 16: bitonic_sort_reg<16>(keys, P.np2); break;
+    default: bitonic_sort<kThreads>(keys, P.np2); break;
+  }
   int local = 0;
   for (int n = threadIdx.x; n < P.np2; n += kThreads) {
     uint32_t k = keys[n];
