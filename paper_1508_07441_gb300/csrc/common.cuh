@@ -78,8 +78,10 @@ struct AccOf<float> {
 };
 
 // nonzeros a lane keeps in flight in the SpMM (fewer for wide channel sets,
-// whose value blocks take more registers)
-template <int NCH>
+// whose value blocks take more registers; measured: halving it for
+// several energies per lane buys occupancy but loses more in memory
+// parallelism)
+template <int NCH, int EPT>
 struct SpmmUnroll {
   static constexpr int value = NCH <= 3 ? 4 : 2;
 };
@@ -103,7 +105,7 @@ __device__ __forceinline__ void spmm_row(int64_t b, int64_t e, int nl, int nl_co
                                          int estride, typename AccOf<T>::t (&acc)[NCH][EPT][2]) {
   using C2 = typename Cx<T>::t;
   constexpr int NPAIR = pair_count(NCH);
-  constexpr int U = SpmmUnroll<NCH>::value;
+  constexpr int U = SpmmUnroll<NCH, EPT>::value;
   constexpr int TS = VEC ? 2 : 1;  // energies per load
   static_assert(!VEC || (sizeof(T) == 4 && EPT % 2 == 0), "vector loads need FP32 and an even EPT");
   for (int64_t o0 = b + nl; o0 < e; o0 += (int64_t)U * nl_count) {

@@ -51,30 +51,35 @@ __constant__ double kInvInt[17] = {0.0,       1.0,        1.0 / 2,  1.0 / 3,  1.
                                    1.0 / 6,   1.0 / 7,    1.0 / 8,  1.0 / 9,  1.0 / 10, 1.0 / 11,
                                    1.0 / 12,  1.0 / 13,   1.0 / 14, 1.0 / 15, 1.0 / 16};
 
+// reciprocal constants: an FP64 division costs a multi-instruction
+// sequence on the narrow FP64 pipe, a multiplication one instruction
+constexpr double kThird = 1.0 / 3.0, kSixth = 1.0 / 6.0, kNinth = 1.0 / 9.0;
+constexpr double kTwoThirds = 2.0 / 3.0, kFourThirds = 4.0 / 3.0;
+
 __device__ double f_lin(double q, double s, double sg) {
   // antiderivative of q^2 ln|q + sg s|; (q^3 + sg s^3) ln|.| -> 0 at q = -sg s
   double d = q + sg * s;
   double cube = d * (q * q - sg * q * s + s * s);  // q^3 + sg s^3
-  double lg = d == 0.0 ? 0.0 : cube * log(fabs(d)) / 3.0;
-  return lg - q * q * q / 9.0 + sg * s * q * q / 6.0 - s * s * q / 3.0;
+  double lg = d == 0.0 ? 0.0 : cube * log(fabs(d)) * kThird;
+  return lg - q * q * q * kNinth + sg * s * q * q * kSixth - s * s * q * kThird;
 }
 
 // int_{qa}^{qb} q^2 ln|a - 3q^2/4| dq without the ln(3/4) B term (it cancels
 // in the difference taken by the caller)
 __device__ double phi_noconst(double qa, double qb, double a) {
   if (a > 0.0) {
-    double s = sqrt(a / 0.75);
+    double s = sqrt(a * kFourThirds);
     return f_lin(qb, s, 1.0) + f_lin(qb, s, -1.0) - f_lin(qa, s, 1.0) - f_lin(qa, s, -1.0);
   }
   if (a < 0.0) {
-    double t = sqrt(-a / 0.75);
+    double t = sqrt(-a * kFourThirds), it = 1.0 / t;
     auto F = [&](double q) {
-      return q * q * q / 3.0 * log(q * q + t * t) -
-             (2.0 / 3.0) * (q * q * q / 3.0 - t * t * q + t * t * t * atan(q / t));
+      return q * q * q * kThird * log(q * q + t * t) -
+             kTwoThirds * (q * q * q * kThird - t * t * q + t * t * t * atan(q * it));
     };
     return F(qb) - F(qa);
   }
-  auto F0 = [&](double q) { return q > 0.0 ? (2.0 / 3.0) * q * q * q * (log(q) - 1.0 / 3.0) : 0.0; };
+  auto F0 = [&](double q) { return q > 0.0 ? kTwoThirds * q * q * q * (log(q) - kThird) : 0.0; };
   return F0(qb) - F0(qa);
 }
 
@@ -82,7 +87,6 @@ struct ResParams {
   int n_ch, N, M, n_E, minor;  // minor: energy index innermost
   const double *qe, *eps;
   const double *Elo, *Ehi;     // per energy
-  const double *gl_t, *gl_w;   // 32-point GL rule
   const double *gl8_t, *gl8_w; // 8-point GL rule
   const double *gl4_t, *gl4_w; // 4-point GL rule
 };
@@ -106,55 +110,69 @@ __global__ void resolvent_kernel(ResParams R, double *g) {
     double ek = R.eps[chk];
     double Elo = R.Elo[e], Ehi = R.Ehi[e], D = Ehi - Elo;
     double qa = R.qe[j], qb = R.qe[j + 1];
-    double Bq = (qb - qa) * (qb * qb + qb * qa + qa * qa) / 3.0;
+    double Bq = (qb - qa) * (qb * qb + qb * qa + qa * qa) * kThird;
     double lo_a = Elo - ek - 0.75 * qa * qa, lo_b = Elo - ek - 0.75 * qb * qb;
     double hi_a = Ehi - ek - 0.75 * qa * qa, hi_b = Ehi - ek - 0.75 * qb * qb;
     bool no_sign_change = (lo_a > 0.0 && lo_b > 0.0 && hi_a > 0.0 && hi_b > 0.0) ||
                           (lo_a < 0.0 && lo_b < 0.0 && hi_a < 0.0 && hi_b < 0.0);
-    double dist = fmin(fabs(lo_a), fabs(lo_b));
-    double re;
-    if (no_sign_change && fabs(D) < 0.05 * dist) {
-      // smooth integrand q^2 log(1 + D / (E_lo - eps - 3q^2/4)); its
-      // singularities sit at q^2 = (E_lo - eps)/(3/4) and (E_hi - eps)/(3/4),
-      // outside the bin.  At a distance rho, in half bin widths, from the bin
-      // centre the n-point GL error falls like r^-2n with r = rho +
-      // sqrt(rho^2 - 1) (Bernstein ellipse): rho > 32 gives r > 63 and a
-      // 4-point error below 1e-14, rho > 4 gives r > 7.8 and an 8-point error
-      // below 1e-14; otherwise 32 points.
-      double half = 0.5 * (qb - qa), mid = 0.5 * (qb + qa), s = 0.0;
-      double rho = 1e300;
-      for (double a2 : {(Elo - ek) / 0.75, (Ehi - ek) / 0.75}) {
+    // Where the energy shell does not cross the bin, the real part is the
+    // integral of the smooth q^2 log(1 + D / (E_lo - eps - 3q^2/4)); its
+    // singularities sit at q^2 = (E_lo - eps)/(3/4) and (E_hi - eps)/(3/4),
+    // outside the bin.  At a distance rho, in half bin widths, from the bin
+    // centre the n-point GL error falls like r^-2n with r = rho +
+    // sqrt(rho^2 - 1) (Bernstein ellipse): rho > 32 gives r > 63 and a
+    // 4-point error below 1e-14, rho > 4 gives r > 7.8 and an 8-point error
+    // below 1e-14.  Closer singularities, and bins the shell crosses, take
+    // the closed form.
+    double half = 0.5 * (qb - qa), mid = 0.5 * (qb + qa);
+    double rho = 0.0;
+    if (no_sign_change) {
+      rho = 1e300;
+      const double ih = 1.0 / half;
+      for (double a2 : {(Elo - ek) * kFourThirds, (Ehi - ek) * kFourThirds}) {
         double qs = sqrt(fabs(a2));
         // a real singular point at qs (a2 > 0), or a complex pair +-i qs
         double d = a2 > 0.0 ? fabs(qs - mid) : sqrt(mid * mid + qs * qs);
-        rho = fmin(rho, d / half);
+        rho = fmin(rho, d * ih);
       }
-      const int npts = rho > 32.0 ? 4 : (rho > 4.0 ? 8 : 32);
-      const double *t = npts == 4 ? R.gl4_t : (npts == 8 ? R.gl8_t : R.gl_t);
-      const double *wg = npts == 4 ? R.gl4_w : (npts == 8 ? R.gl8_w : R.gl_w);
-      // |x| = |D / (E_lo - eps - 3q^2/4)| <= |D| / dist < 0.05 at every node:
-      // log(1 + x) by its Mercator series, x (1 - x (1/2 - x (1/3 - ...))),
-      // with nt terms, nt the least with xmax^nt / (nt + 1) < 1e-17
-      const double xmax = fabs(D) / dist;
-      int nt = 1;
-      for (double pw = xmax; nt < 16 && pw > 1e-17 * (nt + 1); pw *= xmax) ++nt;
-      for (int m = 0; m < npts; ++m) {
-        double q = mid + half * t[m];
-        const double x = D / (Elo - ek - 0.75 * q * q);
-        double h = 1.0 / nt;
-        for (int i = nt - 1; i >= 1; --i) h = fma(-x, h, kInvInt[i]);
-        s += wg[m] * q * q * (x * h);
+    }
+    double re;
+    if (rho > 4.0) {
+      const int npts = rho > 32.0 ? 4 : 8;
+      const double *t = npts == 4 ? R.gl4_t : R.gl8_t;
+      const double *wg = npts == 4 ? R.gl4_w : R.gl8_w;
+      const double dist = fmin(fabs(lo_a), fabs(lo_b));
+      const double xmax = fabs(D) / dist;  // |x| at every node of the bin
+      double s = 0.0;
+      if (xmax < 0.05) {
+        // log(1 + x) by its Mercator series, x (1 - x (1/2 - x (1/3 - ...))),
+        // with nt terms, nt the least with xmax^nt / (nt + 1) < 1e-17
+        int nt = 1;
+        for (double pw = xmax; nt < 16 && pw > 1e-17 * (nt + 1); pw *= xmax) ++nt;
+        for (int m = 0; m < npts; ++m) {
+          double q = mid + half * t[m];
+          const double x = D / (Elo - ek - 0.75 * q * q);
+          double h = 1.0 / nt;
+          for (int i = nt - 1; i >= 1; --i) h = fma(-x, h, kInvInt[i]);
+          s += wg[m] * q * q * (x * h);
+        }
+      } else {
+        for (int m = 0; m < npts; ++m) {
+          double q = mid + half * t[m];
+          s += wg[m] * q * q * log1p(D / (Elo - ek - 0.75 * q * q));
+        }
       }
       re = half * s;
     } else {
       re = phi_noconst(qa, qb, Ehi - ek) - phi_noconst(qa, qb, Elo - ek);
     }
-    re /= D * Bq;
+    const double inv = 1.0 / (D * Bq);
+    re *= inv;
     double im = 0.0;
     if (Ehi - ek > 0.0) {
-      double lo = sqrt(fmax((Elo - ek) / 0.75, 0.0)), hi = sqrt((Ehi - ek) / 0.75);
+      double lo = sqrt(fmax((Elo - ek) * kFourThirds, 0.0)), hi = sqrt((Ehi - ek) * kFourThirds);
       double a = fmax(qa, lo), b = fmin(qb, hi);
-      if (b > a) im = -kPi * ((b - a) * (b * b + b * a + a * a) / 3.0) / (D * Bq);
+      if (b > a) im = -kPi * ((b - a) * (b * b + b * a + a * a) * kThird) * inv;
     }
     g[2 * out] = re;
     g[2 * out + 1] = im;
@@ -747,7 +765,7 @@ wpcd_status resolvent_impl(const wpcd_problem *pr, const double *E, int n_E, dou
                            int *j0, double *D, cudaStream_t s) {
   if (n_E < 0 || (n_E > 0 && (!E || !g))) return set_error(WPCD_EINVAL, "bad resolvent arguments");
   if (n_E == 0) return WPCD_OK;
-  std::vector<double> lohi(2 * (size_t)n_E + 88);
+  std::vector<double> lohi(2 * (size_t)n_E + 24);  // E_lo, E_hi, 8- and 4-point GL rules
   for (int e = 0; e < n_E; ++e) {
     int jj;
     double lo, hi;
@@ -758,9 +776,8 @@ wpcd_status resolvent_impl(const wpcd_problem *pr, const double *E, int n_E, dou
     if (j0) j0[e] = jj;
     if (D) D[e] = hi - lo;
   }
-  gauss_legendre(32, lohi.data() + 2 * n_E, lohi.data() + 2 * n_E + 32);
-  gauss_legendre(8, lohi.data() + 2 * n_E + 64, lohi.data() + 2 * n_E + 72);
-  gauss_legendre(4, lohi.data() + 2 * n_E + 80, lohi.data() + 2 * n_E + 84);
+  gauss_legendre(8, lohi.data() + 2 * n_E, lohi.data() + 2 * n_E + 8);
+  gauss_legendre(4, lohi.data() + 2 * n_E + 16, lohi.data() + 2 * n_E + 20);
   WPCD_CUDA_TRY(cudaSetDevice(pr->device));
   double *d_lohi = nullptr;
   WPCD_CUDA_TRY(cudaMallocAsync(&d_lohi, sizeof(double) * lohi.size(), s));
@@ -775,12 +792,10 @@ wpcd_status resolvent_impl(const wpcd_problem *pr, const double *E, int n_E, dou
   R.eps = pr->d.eps;
   R.Elo = d_lohi;
   R.Ehi = d_lohi + n_E;
-  R.gl_t = d_lohi + 2 * n_E;
-  R.gl_w = d_lohi + 2 * n_E + 32;
-  R.gl8_t = d_lohi + 2 * n_E + 64;
-  R.gl8_w = d_lohi + 2 * n_E + 72;
-  R.gl4_t = d_lohi + 2 * n_E + 80;
-  R.gl4_w = d_lohi + 2 * n_E + 84;
+  R.gl8_t = d_lohi + 2 * n_E;
+  R.gl8_w = d_lohi + 2 * n_E + 8;
+  R.gl4_t = d_lohi + 2 * n_E + 16;
+  R.gl4_w = d_lohi + 2 * n_E + 20;
   int64_t total = (int64_t)n_E * pr->n_ch * pr->N * pr->M;
   resolvent_kernel<<<grid_for(total, 256, 152 * 16), 256, 0, s>>>(R, g);
   count_launches(1);

@@ -8,7 +8,7 @@
 // significant bits in every product.
 //
 // One CTA computes RT row tiles of 128 rows (all of C's rows, N <= 512)
-// times BN output columns, so X' is read once.  Per K chunk of 16:
+// times 128 output columns, so X' is read once.  Per K chunk of 16:
 //   - A (constant per problem, packed once into the MMA operand layout as
 //     TF32 hi/lo blocks by tc_pack_kernel) arrives by one bulk async copy
 //     (cp.async.bulk, completion counted on an mbarrier);
@@ -163,7 +163,7 @@ __global__ void tc_pack_kernel(int n_ch, int n, int RT, int nK, const double *__
 }
 
 template <int BN, bool SCALE_G, bool SUB>
-__global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcParams p) {
+__global__ void __launch_bounds__(TC_THREADS, 2) tc_gemm_kernel(TcParams p) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar_a[TC_MAX_STAGES], bar_mma[TC_MAX_STAGES], bar_done;
   __shared__ uint32_t tmem_holder;
@@ -336,13 +336,16 @@ struct TcShape {
   uint32_t stage_bytes, tmem_cols;
 };
 
+// 128 output columns per CTA: up to two row tiles (N <= 256) then take 96 KB
+// of shared memory and 256 TMEM columns, so two CTAs share an SM and hide
+// each other's load latency
 TcShape tc_shape(int n) {
   TcShape sh{};
   sh.RT = (n + TC_M - 1) / TC_M;
-  sh.BN = sh.RT <= 2 ? 256 : 128;
+  sh.BN = 128;
   sh.nK = (n + TC_KC - 1) / TC_KC;
   sh.stage_bytes = (uint32_t)sh.RT * TC_A_BLOCK + 2u * (uint32_t)sh.BN * TC_KC * 4;
-  sh.stages = sh.stage_bytes <= 72u * 1024 ? 3 : 2;
+  sh.stages = 3 * sh.stage_bytes <= 96u * 1024 ? 3 : 2;
   const int cols = sh.RT * sh.BN;
   sh.tmem_cols = 32;
   while ((int)sh.tmem_cols < cols) sh.tmem_cols <<= 1;
@@ -378,15 +381,9 @@ wpcd_status tc_prepare(wpcd_problem *pr, cudaStream_t s) {
   static bool attr_set[64] = {};
   if (pr->device < 0 || pr->device >= 64) return set_error(WPCD_EINVAL, "device ordinal out of range");
   if (!attr_set[pr->device]) {
-    // the largest stage set of any shape (tc_shape): 3 x 64 KB; the static
-    // barriers and the TMEM address take the rest of the 227 KB opt-in limit
-    const int max_bytes = 3 * 64 * 1024;
-    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<256, true, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes));
-    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<256, false, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes));
-    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<256, false, true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes));
+    // the largest stage set of any shape (tc_shape: N <= 512 -> 2 x 80 KB);
+    // the static barriers and the TMEM address take part of the rest
+    const int max_bytes = 160 * 1024;
     WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<128, true, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes));
     WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<128, false, false>,
@@ -419,23 +416,14 @@ wpcd_status tc_gemm(const wpcd_problem *pr, bool use_O, const float *G, const fl
   p.S = S;
   p.C = C;
   p.err = pr->d.tc_err;
-  const size_t smem = (size_t)sh.stages * sh.stage_bytes;  // <= 192 KB for N <= 512
+  const size_t smem = (size_t)sh.stages * sh.stage_bytes;  // <= 160 KB for N <= 512
   dim3 grid((unsigned)((ncol + sh.BN - 1) / sh.BN), 1, pr->n_ch);
-  if (sh.BN == 256) {
-    if (G)
-      tc_gemm_kernel<256, true, false><<<grid, TC_THREADS, smem, s>>>(p);
-    else if (S)
-      tc_gemm_kernel<256, false, true><<<grid, TC_THREADS, smem, s>>>(p);
-    else
-      tc_gemm_kernel<256, false, false><<<grid, TC_THREADS, smem, s>>>(p);
-  } else {
-    if (G)
-      tc_gemm_kernel<128, true, false><<<grid, TC_THREADS, smem, s>>>(p);
-    else if (S)
-      tc_gemm_kernel<128, false, true><<<grid, TC_THREADS, smem, s>>>(p);
-    else
-      tc_gemm_kernel<128, false, false><<<grid, TC_THREADS, smem, s>>>(p);
-  }
+  if (G)
+    tc_gemm_kernel<128, true, false><<<grid, TC_THREADS, smem, s>>>(p);
+  else if (S)
+    tc_gemm_kernel<128, false, true><<<grid, TC_THREADS, smem, s>>>(p);
+  else
+    tc_gemm_kernel<128, false, false><<<grid, TC_THREADS, smem, s>>>(p);
   count_launches(1);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? WPCD_OK : cuda_error(e, "tensor-core gemm launch");
