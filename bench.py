@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--warm-train", type=int, default=2000)
     ap.add_argument("--warm-test", type=int, default=512)
     ap.add_argument("--no-batching", action="store_true")
+    ap.add_argument("--no-precision-stress", action="store_true")
     return ap.parse_args()
 
 
@@ -146,6 +147,58 @@ NCU_TRAFFIC = {
 }
 
 
+def bench_precision_stress(args, W, inputs, stream, flush, device):
+    """Precision stress: 5 channels, 300 x 300 lattice (dimension 450 000),
+    V = -6 exp(-r^2/0.5) + 2 exp(-r^2/0.1).  Assembly in FP64 and FP32C, and
+    the amplitude at E = 0.5 from the plain FP64 solve and from the mixed
+    solve on FP64 and on FP32C values, each against the FP64 oracle."""
+    import torch
+
+    w = inputs.workload("cfg4")
+    pr = W.Problem(w["p_edges"], w["q_edges"], *w["nodes"], w["n_ch"], w["V"], w["a"], device=device)
+    n_nodes = w["N"] * w["M"] * w["nodes"][0] * w["nodes"][1] * w["nodes"][2]
+    out = {"workload": "3 bosons, V=-6exp(-r^2/0.5)+2exp(-r^2/0.1), 5 channels, N=M=300, GL 8x8x32 "
+                       "nodes per cell (184M nodes), dim 450000"}
+    Ps = {}
+    for name, prec in (("fp64", W.WPCD_FP64), ("fp32c", W.WPCD_FP32C)):
+        ts = []
+        for it in range(3):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            P = pr.wpcd_assemble_P(prec, stream=stream)
+            if it > 0:
+                ts.append(P.ms)
+            if it < 2:
+                P.close()
+        Ps[name] = P
+        ms = statistics.mean(ts)
+        out[f"assembly_{name}"] = {"value": n_nodes / (ms * 1e-3) / 1e9, "unit": "Gnodes/s", "ms": ms,
+                                    "nnz_cells": P.nnz}
+    E = 0.5
+    U64, _, _ = pr.wpcd_solve(Ps["fp64"], [E], tol=1e-10, max_iter=300, batch=1, stream=stream)
+    Um64, _, _ = pr.wpcd_solve(Ps["fp64"], [E], tol=1e-10, precision=W.WPCD_SOLVE_MIXED, batch=1, stream=stream)
+    Um32, _, _ = pr.wpcd_solve(Ps["fp32c"], [E], tol=1e-10, precision=W.WPCD_SOLVE_MIXED, batch=1,
+                               stream=stream)
+    U = {"fp64": U64[0], "mixed_fp64_values": Um64[0], "mixed_fp32c_values": Um32[0]}
+    out["energy"] = E
+    out["U00"] = {k: [v.real, v.imag] for k, v in U.items()}
+    if not args.no_oracle_check:
+        import oracle
+
+        oracle.build()
+        t0 = time.perf_counter()
+        opr = oracle.Problem(dict(pe=w["p_edges"], qe=w["q_edges"], n_p=w["nodes"][0], n_q=w["nodes"][1],
+                                  n_x=w["nodes"][2], n_ch=w["n_ch"], V=list(w["V"]), a=list(w["a"]),
+                                  n_pair_nodes=8))
+        ref = opr.solve_gmres(E, tol=1e-12, max_iter=400)["U00"]
+        out["rel_err_vs_oracle"] = {k: abs(v - ref) / abs(ref) for k, v in U.items()}
+        out["oracle_s"] = time.perf_counter() - t0
+    for P in Ps.values():
+        P.close()
+    pr.close()
+    return out
+
+
 def max_over_ranks(x, dist=None, device="cuda"):
     """The largest of the ranks' values of x (every rank gets it); x itself
     on one process.  The step time of a replicated run is the slowest
@@ -186,10 +239,12 @@ def _time_kernel(stream, flush, fn, reps=3):
 FF_INSTR_PER_FMA = 12
 
 
-def kernel_rooflines(W, pr, w, phases, n_nodes, n_e, stream, flush, peaks, f_sm):
+def kernel_rooflines(W, pr, w, phases, n_nodes, n_e, stream, flush, peaks, f_sm, n32, n64):
     """Achieved vs peak for the kernels that make up the step, each timed on
     its own (the library's CUDA events around that kernel, on the bench
-    stream) in the launch configuration the step uses."""
+    stream) in the launch configuration the step uses.  n32, n64: the FP32
+    and float-float K applications of one step (the Born term takes one
+    SpMM and one O product, every residual one SpMM and two products)."""
     import torch
 
     N, M, n_ch = w["N"], w["M"], w["n_ch"]
@@ -226,29 +281,29 @@ def kernel_rooflines(W, pr, w, phases, n_nodes, n_e, stream, flush, peaks, f_sm)
     # FP32 inner cycles: P0 SpMM and the two tensor-core channel products
     ms = _time_kernel(stream, flush, lambda: pr.wpcd_spmm(P, x32, y32, n_e, mode=W.WPCD_SPMM_FP32, stream=stream,
                                                            timed=True))
-    entry("spmm_kernel<float>", "alu", spmm_flops / (ms * 1e-3) / 1e12, fp32, "TFLOP/s", ms, 32,
+    entry("spmm_kernel<float>", "alu", spmm_flops / (ms * 1e-3) / 1e12, fp32, "TFLOP/s", ms, n32,
           f"4 n_pairs nnz B = {spmm_flops:.3e} FP32 flops (one real-by-complex multiply-add per block entry and "
           "energy; the compensated sums add issued work that is not counted)", src32)
     tc_bytes = 3.0 * 8 * dim * n_e
     ms = _time_kernel(stream, flush, lambda: pr.wpcd_channel_gemm(0, W.WPCD_GEMM_TF32X3, g32, x32, y32, n_e,
                                                                    stream=stream, timed=True))
-    entry("tc_gemm_kernel<TF32x3> (Vt, G1)", "hbm", tc_bytes / (ms * 1e-3) / 1e9, hbm, "GB/s", ms, 32,
+    entry("tc_gemm_kernel<TF32x3> (Vt, G1)", "hbm", tc_bytes / (ms * 1e-3) / 1e9, hbm, "GB/s", ms, n32,
           f"X + G1 read, Y written (FP32 complex): {tc_bytes:.3e} B; {3 * gemm_flops:.3e} TF32 MMA flops",
           "measured HBM copy (hbm_gbs)")
     o_bytes = 2.0 * 8 * dim * n_e
     ms = _time_kernel(stream, flush, lambda: pr.wpcd_channel_gemm(1, W.WPCD_GEMM_TF32X3, None, x32, y32, n_e,
                                                                    stream=stream, timed=True))
-    entry("tc_gemm_kernel<TF32x3> (O)", "hbm", o_bytes / (ms * 1e-3) / 1e9, hbm, "GB/s", ms, 32,
+    entry("tc_gemm_kernel<TF32x3> (O)", "hbm", o_bytes / (ms * 1e-3) / 1e9, hbm, "GB/s", ms, n32,
           f"Z read, Y written (FP32 complex): {o_bytes:.3e} B (the solve's O step also reads S)",
           "measured HBM copy (hbm_gbs)")
     # refinement residual and Born term: float-float SpMM and channel products
     ms = _time_kernel(stream, flush, lambda: pr.wpcd_spmm(P, x64, y64, n_e, mode=W.WPCD_SPMM_FF, stream=stream,
                                                            timed=True))
-    entry("spmm_df_kernel", "alu", spmm_flops / (ms * 1e-3) / 1e12, ff, "TFLOP/s", ms, 3,
+    entry("spmm_df_kernel", "alu", spmm_flops / (ms * 1e-3) / 1e12, ff, "TFLOP/s", ms, n64,
           f"4 n_pairs nnz B = {spmm_flops:.3e} FP64-equivalent flops in float-float", srcff)
     ms = _time_kernel(stream, flush, lambda: pr.wpcd_channel_gemm(1, W.WPCD_GEMM_FF, None, x64, y64, n_e,
                                                                    stream=stream, timed=True))
-    entry("gemm_df_kernel", "alu", gemm_flops / (ms * 1e-3) / 1e12, ff, "TFLOP/s", ms, 5,
+    entry("gemm_df_kernel", "alu", gemm_flops / (ms * 1e-3) / 1e12, ff, "TFLOP/s", ms, 2 * n64 - 1,
           f"2 N^2 (2 M B) n_ch = {gemm_flops:.3e} FP64-equivalent flops in float-float", srcff)
     # the plain FP64 iteration's kernels (the comparison baseline), one energy
     x1 = torch.randn(2 * dim, dtype=torch.float64, device="cuda")
@@ -541,6 +596,11 @@ def main():
     if not args.no_batching:
         batching = bench_batching(args, W, inputs, stream, flush, local, maxr_fn=None)
 
+    # ---- precision stress: 5 channels, 300 x 300 (dimension 450 000) ------
+    stress = None
+    if not args.no_precision_stress and world == 1:
+        stress = bench_precision_stress(args, W, inputs, stream, flush, local)
+
     # ---- end to end through the public API with host buffers -------------
     barrier()
     t0 = time.perf_counter()
@@ -608,7 +668,8 @@ def main():
     peaks, peak_src = measured_peaks()
     clocks = clk.summary()
     f_sm = (clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    rl = kernel_rooflines(W, pr, w, phases, n_nodes, len(energies), stream, flush, peaks, f_sm)
+    rl = kernel_rooflines(W, pr, w, phases, n_nodes, len(energies), stream, flush, peaks, f_sm,
+                          recs[-1]["n32"], recs[-1]["n64"])
     dom = max(rl, key=lambda r: r["ms_per_step"])  # the kernel with the largest share of the step
     roofline = {k: dom[k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac", "traffic")}
     roofline["peak_source"] = dom["peak_source"]
@@ -660,7 +721,8 @@ def main():
                    "energies": f"{len(energies)} uniform in [-0.9|E_d|, 5] (E_d = {pr.eps_bound:.6f})",
                    "assembly": "FP64",
                    "solve": "batched (all energies in one iteration), FP32 inner Krylov cycles "
-                            "of 16 (CUDA graph) + FP64 refinement to rel residual 1e-10",
+                            "of 10 steps (tensor-core TF32x3 block products, CUDA graph) + float-float "
+                            "refinement residual to rel residual 1e-10",
                    "l2": "flushed (512 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "assembly": {"ms": asm_ms, "count_ms": phases[0], "scan_ms": phases[1], "fill_ms": phases[2],
@@ -679,6 +741,7 @@ def main():
                   "accuracy_vs_oracle": acc},
         "warm_start": warm,
         "batching": batching,
+        "precision_stress": stress,
         "roofline": roofline,
         "roofline_peak_source": peak_src,
         "kernel_rooflines": rl,

@@ -195,7 +195,7 @@ typedef struct {
                       mixed modes) */
   int batch;       /* energies solved together in one batched iteration
                       (block K applications, SpMM over the batch); 0: all */
-  int inner_iter;  /* mixed: Krylov steps per refinement cycle (0: 16) */
+  int inner_iter;  /* mixed: Krylov steps per refinement cycle (0: 10) */
   int max_outer;   /* mixed: cap on refinement cycles (0: 12) */
   int use_graph;   /* mixed: replay each inner cycle from a CUDA graph (1) or
                       launch its kernels one by one (0) */

@@ -1055,7 +1055,7 @@ wpcd_status solve_group(int n_prob, wpcd_problem *const *prs, const wpcd_P *cons
   if (mixed) {
     GKrylov<float> kr;
     GKrylov<double> k64;
-    WPCD_CUDA_TRY(kr.alloc(gr, opt.inner_iter > 0 ? opt.inner_iter : 16));
+    WPCD_CUDA_TRY(kr.alloc(gr, opt.inner_iter > 0 ? opt.inner_iter : kDefaultInner));
     WPCD_CUDA_TRY(k64.alloc(gr, 1, false));  // norms only
     st = gsolve_mixed(gr, opt, cx, kr, k64, status, relres, n64, n32, n_outer, s);
   } else {

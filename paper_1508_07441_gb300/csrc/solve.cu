@@ -1546,7 +1546,7 @@ wpcd_status solve(wpcd_problem *pr, const wpcd_P *Pc, const double *E, int n_E,
       std::vector<double> relres;
       int n64 = 0, n32 = 0, n_outer = 0;
       if (mixed) {
-        const int m_in = opt.inner_iter > 0 ? opt.inner_iter : 16;
+        const int m_in = opt.inner_iter > 0 ? opt.inner_iter : kDefaultInner;
         Krylov<float> kr;
         Krylov<double> k64;
         WPCD_CUDA_TRY(kr.alloc(m_in, B, dim));

@@ -44,12 +44,13 @@ constexpr uint32_t TC_A_BLOCK = 2 * TC_A_HALF;    // hi + lo: 16 KB
 constexpr uint32_t TC_KSTRIDE = 128;              // between core matrices along K
 constexpr uint32_t TC_RSTRIDE = 512;              // between 8-row groups
 constexpr int TC_MAX_STAGES = 3;
+constexpr int TC_MAX_RAW = 4;  // raw panel chunks in flight (bulk-copy path)
 constexpr long long TC_SPIN_LIMIT = 1LL << 22;
 
 struct TcParams {
-  int n, RT, nK, stages;
+  int n, RT, nK, stages, raw_stages;
   int64_t ncol;
-  uint32_t stage_bytes, tmem_cols;
+  uint32_t stage_bytes, raw_bytes, tmem_cols;
   const float *A;       // packed TF32 blocks [n_ch][nK][RT][hi | lo]
   const float2 *X, *G;  // [n_ch][n][ncol / 2] complex
   const float *S;       // epilogue S - C (SUB)
@@ -162,10 +163,14 @@ __global__ void tc_pack_kernel(int n_ch, int n, int RT, int nK, const double *__
   }
 }
 
-template <int BN, bool SCALE_G, bool SUB>
-__global__ void __launch_bounds__(TC_THREADS, 2) tc_gemm_kernel(TcParams p) {
+// RAW: the X (and G1) panel rows arrive by bulk async copies into a ring of
+// raw chunks in shared memory, issued TC_MAX_RAW chunks ahead by one
+// thread; otherwise each thread prefetches the next chunk into registers
+template <int BN, bool SCALE_G, bool SUB, bool RAW>
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcParams p) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar_a[TC_MAX_STAGES], bar_mma[TC_MAX_STAGES], bar_done;
+  __shared__ __align__(8) uint64_t bar_raw[TC_MAX_RAW];
   __shared__ uint32_t tmem_holder;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ch = blockIdx.z;
@@ -179,6 +184,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_gemm_kernel(TcParams p) {
       mbar_init(&bar_mma[s], 1);
     }
     mbar_init(&bar_done, 1);
+    if (RAW)
+      for (int r = 0; r < p.raw_stages; ++r) mbar_init(&bar_raw[r], 1);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 0) {
@@ -199,9 +206,10 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_gemm_kernel(TcParams p) {
   // X' chunk c: rows k = c*KC .. c*KC+15, output columns col0 .. col0+BN-1.
   // Item (kg, nn): operand row nn (output column col0 + nn), K group kg
   // (4 rows); consecutive lanes take consecutive nn, so each store
-  // instruction of a warp fills 512 contiguous bytes.  The raw values of
-  // chunk c + 1 are loaded into registers while chunk c is converted.
+  // instruction of a warp fills 512 contiguous bytes.
   constexpr int ITEMS = (TC_KC / 4) * BN / TC_THREADS;
+  // register path: the raw values of chunk c + 1 are loaded while chunk c
+  // is converted
   auto load_chunk = [&](int c, float2 (&xv)[ITEMS][4], float2 (&gv)[ITEMS][4]) {
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) {
@@ -218,8 +226,43 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_gemm_kernel(TcParams p) {
       }
     }
   };
+  // bulk-copy path: raw chunk c (rows of X, then of G1; BN floats each,
+  // the valid columns only) into ring slot c % raw_stages
+  unsigned char *raw0 = smem + (size_t)NS * p.stage_bytes;
+  const int valid_cols = (int)min((int64_t)BN, ncol - col0);  // a multiple of 4 on this path
+  auto issue_raw = [&](int c) {
+    const int r = c % p.raw_stages;
+    unsigned char *dst = raw0 + (size_t)r * p.raw_bytes;
+    const int rows = min(TC_KC, n - c * TC_KC);
+    const uint32_t row_bytes = (uint32_t)valid_cols * 4;
+    const uint32_t total = (uint32_t)rows * row_bytes * (SCALE_G ? 2u : 1u);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar_raw[r])),
+                 "r"(total)
+                 : "memory");
+    for (int k = 0; k < rows; ++k) {
+      const float *src = reinterpret_cast<const float *>(X) + (size_t)(c * TC_KC + k) * ncol + col0;
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       smem_u32(dst + (size_t)k * BN * 4)),
+                   "l"(src), "r"(row_bytes), "r"(smem_u32(&bar_raw[r]))
+                   : "memory");
+      if (SCALE_G) {
+        const float *gsrc = reinterpret_cast<const float *>(G) + (size_t)(c * TC_KC + k) * ncol + col0;
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(dst + (size_t)(TC_KC + k) * BN * 4)),
+            "l"(gsrc), "r"(row_bytes), "r"(smem_u32(&bar_raw[r]))
+            : "memory");
+      }
+    }
+  };
+  int a_last = -1, raw_last = -1;  // thread 0: last chunks whose copies it saw complete
   float2 xv[ITEMS][4], gv[ITEMS][4];
-  load_chunk(0, xv, gv);
+  if (RAW) {
+    if (tid == 0)
+      for (int c = 0; c < min(p.raw_stages, nK); ++c) issue_raw(c);
+  } else {
+    load_chunk(0, xv, gv);
+  }
   for (int c = 0; c < nK; ++c) {
     const int s = c % NS;
     const uint32_t use = (uint32_t)(c / NS);
@@ -237,7 +280,28 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_gemm_kernel(TcParams p) {
                    : "memory");
     }
     float2 xn[ITEMS][4], gn[ITEMS][4];
-    if (c + 1 < nK) load_chunk(c + 1, xn, gn);
+    if (RAW) {
+      const int r = c % p.raw_stages;
+      if (ok) ok = mbar_wait(&bar_raw[r], (uint32_t)(c / p.raw_stages) & 1);
+      if (ok) raw_last = c;
+      const float2 *rx = reinterpret_cast<const float2 *>(raw0 + (size_t)r * p.raw_bytes);
+      const float2 *rg = rx + TC_KC * BN / 2;
+#pragma unroll
+      for (int it = 0; it < ITEMS; ++it) {
+        const int item = tid + it * TC_THREADS;
+        const int nn = item % BN, kg = item / BN;
+        const bool col_in = nn < valid_cols;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int kl = kg * 4 + q;
+          const bool in = col_in && c * TC_KC + kl < n;
+          xv[it][q] = in ? rx[kl * (BN / 2) + (nn >> 1)] : make_float2(0.f, 0.f);
+          if (SCALE_G) gv[it][q] = in ? rg[kl * (BN / 2) + (nn >> 1)] : make_float2(0.f, 0.f);
+        }
+      }
+    } else if (c + 1 < nK) {
+      load_chunk(c + 1, xn, gn);
+    }
     unsigned char *bhi = st + (size_t)RT * TC_A_BLOCK, *blo = bhi + b_half;
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) {
@@ -268,7 +332,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_gemm_kernel(TcParams p) {
       *reinterpret_cast<uint4 *>(bhi + off) = h;
       *reinterpret_cast<uint4 *>(blo + off) = l;
     }
-    if (c + 1 < nK) {
+    if (!RAW && c + 1 < nK) {
 #pragma unroll
       for (int it = 0; it < ITEMS; ++it)
 #pragma unroll
@@ -283,7 +347,10 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_gemm_kernel(TcParams p) {
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
+      // every thread has read raw slot c % raw_stages: refill it
+      if (RAW && c + p.raw_stages < nK) issue_raw(c + p.raw_stages);
       if (ok) ok = mbar_wait(&bar_a[s], use & 1);
+      if (ok) a_last = c;
       const uint32_t a0 = smem_u32(st), b0 = smem_u32(bhi);
 #pragma unroll 1
       for (int rt = 0; rt < RT; ++rt) {
@@ -302,23 +369,48 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_gemm_kernel(TcParams p) {
       tc_commit(&bar_mma[s]);
     }
   }
-  if (tid == 0) tc_commit(&bar_done);
+  if (tid == 0) {
+    // after a wait ran out, still wait (bounded) for the copies this CTA
+    // issued, so that none lands in shared memory after the CTA has gone
+    for (int c = a_last + 1; c < nK; ++c) mbar_wait(&bar_a[c % NS], (uint32_t)(c / NS) & 1);
+    if (RAW)
+      for (int c = raw_last + 1; c < nK; ++c)
+        mbar_wait(&bar_raw[c % p.raw_stages], (uint32_t)(c / p.raw_stages) & 1);
+    tc_commit(&bar_done);
+  }
   // always wait (bounded) for the MMAs before TMEM is read or freed
   const bool done = mbar_wait(&bar_done, 0);
   ok = ok && done;
   tc_fence_after();
   // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, half w / 4 of the columns
   const int lg = warp & 3, half = warp >> 2;
+  // a thread's 16 columns of one row go out as four 16-byte stores when the
+  // row start is 16-byte aligned (ncol a multiple of 4) and all 16 exist
+  const bool vec_out = ncol % 4 == 0;
   for (int rt = 0; rt < RT; ++rt) {
     const int row = rt * TC_M + lg * 32 + lane;
     for (int cb = half * (BN / 2); cb < (half + 1) * (BN / 2); cb += 16) {
+      const size_t o = ((size_t)ch * n + min(row, n - 1)) * ncol + col0 + cb;
+      const bool full = vec_out && col0 + cb + 16 <= ncol;
+      float4 sv[4];
+      if (SUB && full && row < n)  // issue the S loads before the TMEM read
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sv[q] = *reinterpret_cast<const float4 *>(p.S + o + 4 * q);
       float v[16];
       tc_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(rt * BN + cb), v);
       if (row < n && done) {
-        const size_t o = ((size_t)ch * n + row) * ncol + col0 + cb;
+        if (full) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          if (col0 + cb + j < ncol) p.C[o + j] = SUB ? p.S[o + j] - v[j] : v[j];
+          for (int q = 0; q < 4; ++q) {
+            float4 w = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            if (SUB) w = make_float4(sv[q].x - w.x, sv[q].y - w.y, sv[q].z - w.z, sv[q].w - w.w);
+            *reinterpret_cast<float4 *>(p.C + o + 4 * q) = w;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (col0 + cb + j < ncol) p.C[o + j] = SUB ? p.S[o + j] - v[j] : v[j];
+        }
       }
     }
   }
@@ -332,13 +424,14 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_gemm_kernel(TcParams p) {
 }
 
 struct TcShape {
-  int RT, BN, nK, stages;
-  uint32_t stage_bytes, tmem_cols;
+  int RT, BN, nK, stages, raw_stages;
+  uint32_t stage_bytes, raw_bytes, tmem_cols;
 };
 
-// 128 output columns per CTA: up to two row tiles (N <= 256) then take 96 KB
-// of shared memory and 256 TMEM columns, so two CTAs share an SM and hide
-// each other's load latency
+// 128 output columns per CTA, all N rows (RT tiles of 128); operand stages
+// of one K chunk (A hi/lo for every row tile, the panel's hi/lo), two or
+// three of them, then a ring of raw panel chunks (rows of X and G1) for
+// the bulk-copy path: at most 192 KB, one CTA per SM
 TcShape tc_shape(int n) {
   TcShape sh{};
   sh.RT = (n + TC_M - 1) / TC_M;
@@ -346,6 +439,8 @@ TcShape tc_shape(int n) {
   sh.nK = (n + TC_KC - 1) / TC_KC;
   sh.stage_bytes = (uint32_t)sh.RT * TC_A_BLOCK + 2u * (uint32_t)sh.BN * TC_KC * 4;
   sh.stages = 3 * sh.stage_bytes <= 96u * 1024 ? 3 : 2;
+  sh.raw_bytes = 2u * TC_KC * sh.BN * 4;
+  sh.raw_stages = sh.stages * sh.stage_bytes + TC_MAX_RAW * sh.raw_bytes <= 192u * 1024 ? TC_MAX_RAW : 2;
   const int cols = sh.RT * sh.BN;
   sh.tmem_cols = 32;
   while ((int)sh.tmem_cols < cols) sh.tmem_cols <<= 1;
@@ -381,14 +476,20 @@ wpcd_status tc_prepare(wpcd_problem *pr, cudaStream_t s) {
   static bool attr_set[64] = {};
   if (pr->device < 0 || pr->device >= 64) return set_error(WPCD_EINVAL, "device ordinal out of range");
   if (!attr_set[pr->device]) {
-    // the largest stage set of any shape (tc_shape: N <= 512 -> 2 x 80 KB);
-    // the static barriers and the TMEM address take part of the rest
-    const int max_bytes = 160 * 1024;
-    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<128, true, false>,
+    // the largest stage set of any shape (tc_shape: at most 192 KB); the
+    // static barriers and the TMEM address take part of the rest
+    const int max_bytes = 192 * 1024;
+    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<128, true, false, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes));
-    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<128, false, false>,
+    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<128, false, false, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes));
-    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<128, false, true>,
+    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<128, false, true, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes));
+    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<128, true, false, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes));
+    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<128, false, false, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes));
+    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<128, false, true, true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes));
     attr_set[pr->device] = true;
   }
@@ -416,14 +517,28 @@ wpcd_status tc_gemm(const wpcd_problem *pr, bool use_O, const float *G, const fl
   p.S = S;
   p.C = C;
   p.err = pr->d.tc_err;
-  const size_t smem = (size_t)sh.stages * sh.stage_bytes;  // <= 160 KB for N <= 512
+  p.raw_stages = sh.raw_stages;
+  p.raw_bytes = sh.raw_bytes;
+  // bulk copies need 16-byte aligned panel rows: ncol a multiple of 4 and
+  // aligned bases (every row, and every column tile, then starts aligned)
+  const bool raw = ncol % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
+                   (!G || (reinterpret_cast<uintptr_t>(G) & 15) == 0);
+  const size_t smem = (size_t)sh.stages * sh.stage_bytes + (raw ? (size_t)sh.raw_stages * sh.raw_bytes : 0);
   dim3 grid((unsigned)((ncol + sh.BN - 1) / sh.BN), 1, pr->n_ch);
-  if (G)
-    tc_gemm_kernel<128, true, false><<<grid, TC_THREADS, smem, s>>>(p);
-  else if (S)
-    tc_gemm_kernel<128, false, true><<<grid, TC_THREADS, smem, s>>>(p);
+#define WPCD_TC_LAUNCH(RAW)                                                 \
+  do {                                                                      \
+    if (G)                                                                  \
+      tc_gemm_kernel<128, true, false, RAW><<<grid, TC_THREADS, smem, s>>>(p);  \
+    else if (S)                                                             \
+      tc_gemm_kernel<128, false, true, RAW><<<grid, TC_THREADS, smem, s>>>(p);  \
+    else                                                                    \
+      tc_gemm_kernel<128, false, false, RAW><<<grid, TC_THREADS, smem, s>>>(p); \
+  } while (0)
+  if (raw)
+    WPCD_TC_LAUNCH(true);
   else
-    tc_gemm_kernel<128, false, false><<<grid, TC_THREADS, smem, s>>>(p);
+    WPCD_TC_LAUNCH(false);
+#undef WPCD_TC_LAUNCH
   count_launches(1);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? WPCD_OK : cuda_error(e, "tensor-core gemm launch");

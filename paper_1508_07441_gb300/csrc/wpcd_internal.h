@@ -13,6 +13,13 @@
 namespace wpcd {
 
 constexpr int kMaxCh = 8;
+// Krylov steps per FP32 inner cycle of the mixed solve when the caller
+// leaves it open.  A cycle's gain is bounded by the FP32 arithmetic (about
+// 5e-6 in residual per cycle on the 200 x 200, 3-channel workload) and ten
+// steps already reach that bound: measured there at 128 energies, 8 steps
+// need 3 cycles, 10-32 steps 2 cycles, so 10 gives the fewest K
+// applications (20 against 32 at 16 steps).
+constexpr int kDefaultInner = 10;
 constexpr int kMaxPairs = kMaxCh * kMaxCh;
 
 // (l, l') channel pairs with l + l' even, ordered by l then l' (compile-time

@@ -65,7 +65,7 @@ def test_mixed_matches_oracle(W, sys3, pname, residual):
     assert st == W.WPCD_OK
     for s in stats:
         assert s.status == W.WPCD_OK and s.relres <= 1e-12
-        assert s.n_outer >= 1 and s.n_kapply32 >= 16
+        assert s.n_outer >= 1 and s.n_kapply32 >= 10
     ref = _ref(opr, ENERGIES)
     err = np.max(np.abs(U - ref) / np.abs(ref))
     # FP64 values: refined to the FP64 system at residual 1e-12; the U00

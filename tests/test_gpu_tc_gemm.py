@@ -44,7 +44,9 @@ def _reference(A, x, g, N, M, B):
     return np.einsum("cik,ckj->cij", A, xc), np.einsum("cik,ckj->cij", np.abs(A), np.abs(xc))
 
 
-@pytest.mark.parametrize("N,M,B", [(30, 28, 3), (130, 20, 5), (200, 16, 8), (300, 12, 2)])
+# panels with M B even take the bulk-copy path, (40, 15, 3) (M B odd: rows not
+# 16-byte aligned) the register path
+@pytest.mark.parametrize("N,M,B", [(30, 28, 3), (130, 20, 5), (200, 16, 8), (300, 12, 2), (40, 15, 3)])
 @pytest.mark.parametrize("which", [0, 1])
 def test_tensor_core_gemm_matches_fp64(W, N, M, B, which):
     import torch
