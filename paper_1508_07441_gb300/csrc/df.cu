@@ -79,9 +79,13 @@ __global__ void df_split_scaled_kernel(int64_t nc, const double2 *__restrict__ x
   }
 }
 
-// C[b] (n x ncol) = A[b] (n x n) B[b] (n x ncol) in float-float; the tiling
-// of the FP64 block product (32 x 64 outputs per CTA, 2 x 4 per thread).
+// C[b] (n x ncol) = A[b] (n x n) B[b] (n x ncol) in float-float: 32 x 128
+// outputs per CTA, 2 x 8 per thread (rows ty, ty + 16; columns 4 tx .. 4 tx
+// + 3 and 64 + 4 tx .. + 3), so that a k step reads the panel with two
+// 16-byte loads per part; 16-deep K tiles in shared memory.
 // OUT_DF: C as a float-float pair (Ch, Cl); otherwise FP64 C.
+constexpr int DF_N = 128;
+
 template <bool OUT_DF>
 __global__ void __launch_bounds__(G_THREADS) gemm_df_kernel(int n, int64_t ncol, const float *__restrict__ Ah,
                                                             const float *__restrict__ Al,
@@ -89,17 +93,18 @@ __global__ void __launch_bounds__(G_THREADS) gemm_df_kernel(int n, int64_t ncol,
                                                             const float *__restrict__ Bl, double *__restrict__ C,
                                                             float *__restrict__ Ch, float *__restrict__ Cl) {
   __shared__ float sAh[GB_K][GB_M + 1], sAl[GB_K][GB_M + 1];
-  __shared__ float sBh[GB_K][GB_N], sBl[GB_K][GB_N];
+  __shared__ __align__(16) float sBh[GB_K][DF_N], sBl[GB_K][DF_N];
   const int b = blockIdx.z;
   const size_t offA = (size_t)b * n * n, offB = (size_t)b * n * ncol;
   const int row0 = blockIdx.y * GB_M;
-  const int64_t col0 = (int64_t)blockIdx.x * GB_N;
+  const int64_t col0 = (int64_t)blockIdx.x * DF_N;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  float hi[2][4], lo[2][4];
+  const bool vec = ncol % 4 == 0;  // 16-byte aligned panel rows
+  float hi[2][8], lo[2][8];
 #pragma unroll
   for (int u = 0; u < 2; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) hi[u][v] = lo[u][v] = 0.f;
+    for (int v = 0; v < 8; ++v) hi[u][v] = lo[u][v] = 0.f;
   for (int k0 = 0; k0 < n; k0 += GB_K) {
     for (int t = threadIdx.x; t < GB_M * GB_K; t += G_THREADS) {
       const int r = t / GB_K, kk = t % GB_K;
@@ -109,33 +114,57 @@ __global__ void __launch_bounds__(G_THREADS) gemm_df_kernel(int n, int64_t ncol,
       sAh[kk][r] = in ? Ah[o] : 0.f;
       sAl[kk][r] = in ? Al[o] : 0.f;
     }
-    for (int t = threadIdx.x; t < GB_K * GB_N; t += G_THREADS) {
-      const int kk = t / GB_N, cc = t % GB_N;
-      const int gk = k0 + kk;
-      const int64_t gc = col0 + cc;
-      const bool in = gk < n && gc < ncol;
-      const size_t o = offB + (size_t)gk * ncol + gc;
-      sBh[kk][cc] = in ? Bh[o] : 0.f;
-      sBl[kk][cc] = in ? Bl[o] : 0.f;
+    if (vec) {
+      for (int t = threadIdx.x; t < GB_K * DF_N / 4; t += G_THREADS) {
+        const int kk = t / (DF_N / 4), c4 = (t % (DF_N / 4)) * 4;
+        const int gk = k0 + kk;
+        const int64_t gc = col0 + c4;
+        float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+        if (gk < n && gc < ncol) {  // ncol % 4 == 0: the four columns are all in or all out
+          const size_t o = offB + (size_t)gk * ncol + gc;
+          h = *reinterpret_cast<const float4 *>(Bh + o);
+          l = *reinterpret_cast<const float4 *>(Bl + o);
+        }
+        *reinterpret_cast<float4 *>(&sBh[kk][c4]) = h;
+        *reinterpret_cast<float4 *>(&sBl[kk][c4]) = l;
+      }
+    } else {
+      for (int t = threadIdx.x; t < GB_K * DF_N; t += G_THREADS) {
+        const int kk = t / DF_N, cc = t % DF_N;
+        const int gk = k0 + kk;
+        const int64_t gc = col0 + cc;
+        const bool in = gk < n && gc < ncol;
+        const size_t o = offB + (size_t)gk * ncol + gc;
+        sBh[kk][cc] = in ? Bh[o] : 0.f;
+        sBl[kk][cc] = in ? Bl[o] : 0.f;
+      }
     }
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < GB_K; ++kk) {
-      float ah[2], al[2], bh[4], bl[4];
+      float ah[2], al[2], bh[8], bl[8];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         ah[u] = sAh[kk][ty + 16 * u];
         al[u] = sAl[kk][ty + 16 * u];
       }
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        bh[v] = sBh[kk][tx + 16 * v];
-        bl[v] = sBl[kk][tx + 16 * v];
+      for (int h = 0; h < 2; ++h) {
+        const float4 qh = *reinterpret_cast<const float4 *>(&sBh[kk][64 * h + 4 * tx]);
+        const float4 ql = *reinterpret_cast<const float4 *>(&sBl[kk][64 * h + 4 * tx]);
+        bh[4 * h] = qh.x;
+        bh[4 * h + 1] = qh.y;
+        bh[4 * h + 2] = qh.z;
+        bh[4 * h + 3] = qh.w;
+        bl[4 * h] = ql.x;
+        bl[4 * h + 1] = ql.y;
+        bl[4 * h + 2] = ql.z;
+        bl[4 * h + 3] = ql.w;
       }
 #pragma unroll
       for (int u = 0; u < 2; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
+        for (int v = 0; v < 8; ++v) {
           float p, e;
           df_mul(ah[u], al[u], bh[v], bl[v], p, e);
           df_add(hi[u][v], lo[u][v], p, e);
@@ -146,9 +175,9 @@ __global__ void __launch_bounds__(G_THREADS) gemm_df_kernel(int n, int64_t ncol,
 #pragma unroll
   for (int u = 0; u < 2; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < 8; ++v) {
       const int gr = row0 + ty + 16 * u;
-      const int64_t gc = col0 + tx + 16 * v;
+      const int64_t gc = col0 + 64 * (v / 4) + 4 * tx + (v % 4);
       if (gr < n && gc < ncol) {
         const size_t o = offB + (size_t)gr * ncol + gc;
         float h = hi[u][v], l = lo[u][v];
@@ -276,7 +305,7 @@ template <bool OUT_DF>
 void gemm_df(const wpcd_problem *pr, bool use_O, const float *Bh, const float *Bl, double *C, float *Ch, float *Cl,
              int64_t ncol, cudaStream_t s) {
   const int N = pr->N;
-  dim3 grid((unsigned)((ncol + GB_N - 1) / GB_N), (N + GB_M - 1) / GB_M, pr->n_ch);
+  dim3 grid((unsigned)((ncol + DF_N - 1) / DF_N), (N + GB_M - 1) / GB_M, pr->n_ch);
   gemm_df_kernel<OUT_DF><<<grid, G_THREADS, 0, s>>>(N, ncol, use_O ? pr->d.O_h : pr->d.Vt_h,
                                                     use_O ? pr->d.O_l : pr->d.Vt_l, Bh, Bl, C, Ch, Cl);
   count_launches(1);

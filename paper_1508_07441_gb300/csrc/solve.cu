@@ -761,8 +761,10 @@ wpcd_status onshell(const wpcd_problem *pr, double E, int *j0, double *Elo, doub
 
 namespace {
 
+// max_blocks caps the grid (measured: the full grid is faster than one CTA
+// per SM even next to the Born term, which then finds fewer free slots)
 wpcd_status resolvent_impl(const wpcd_problem *pr, const double *E, int n_E, double *g, int minor,
-                           int *j0, double *D, cudaStream_t s) {
+                           int *j0, double *D, cudaStream_t s, int max_blocks = 152 * 16) {
   if (n_E < 0 || (n_E > 0 && (!E || !g))) return set_error(WPCD_EINVAL, "bad resolvent arguments");
   if (n_E == 0) return WPCD_OK;
   std::vector<double> lohi(2 * (size_t)n_E + 24);  // E_lo, E_hi, 8- and 4-point GL rules
@@ -797,7 +799,7 @@ wpcd_status resolvent_impl(const wpcd_problem *pr, const double *E, int n_E, dou
   R.gl4_t = d_lohi + 2 * n_E + 16;
   R.gl4_w = d_lohi + 2 * n_E + 20;
   int64_t total = (int64_t)n_E * pr->n_ch * pr->N * pr->M;
-  resolvent_kernel<<<grid_for(total, 256, 152 * 16), 256, 0, s>>>(R, g);
+  resolvent_kernel<<<grid_for(total, 256, max_blocks), 256, 0, s>>>(R, g);
   count_launches(1);
   cudaError_t e = cudaGetLastError();
   cudaFreeAsync(d_lohi, s);
@@ -970,9 +972,10 @@ struct BatchInfo {
   std::vector<double> D, pref;
 };
 
+// on-shell data of the batch (host) and its upload; the resolvent follows
+// separately (batch_resolvent) so that it can overlap the Born term
 wpcd_status batch_setup(const wpcd_problem *pr, const double *E, int B, SolveCtx &cx, BatchInfo &bi,
-                        bool need32, cudaStream_t s) {
-  const size_t dim = (size_t)pr->n_ch * pr->N * pr->M;
+                        cudaStream_t s) {
   bi.j0.assign(B, 0);
   bi.D.assign(B, 0.0);
   bi.pref.assign(B, 0.0);
@@ -983,16 +986,32 @@ wpcd_status batch_setup(const wpcd_problem *pr, const double *E, int B, SolveCtx
     bi.D[e] = hi - lo;
     bi.pref[e] = 2.0 / (3.0 * q0) / (pr->qe[bi.j0[e] + 1] - pr->qe[bi.j0[e]]);
   }
-  wpcd_status st = resolvent_impl(pr, E, B, cx.g, 1, nullptr, nullptr, s);
-  if (st != WPCD_OK) return st;
-  if (need32) {
-    d2f_kernel<<<grid_for(2 * (int64_t)dim * B, 256), 256, 0, s>>>(2 * (int64_t)dim * B, cx.g, cx.g32);
-    count_launches(1);
-  }
   // e0 = channel 0, k = 0 (the dimer), q-bin j0: vector index j0
   WPCD_CUDA_TRY(cudaMemcpyAsync(cx.r0, bi.j0.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
   WPCD_CUDA_TRY(cudaMemcpyAsync(cx.Dd, bi.D.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
   WPCD_CUDA_TRY(cudaMemcpyAsync(cx.pref, bi.pref.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
+  // the host vectors must outlive the copies: the caller synchronises s
+  // (through the resolvent's own synchronisation) before bi goes away
+  return WPCD_OK;
+}
+
+// G1 of the batch (and its FP32 copy) on stream s2, ordered after the
+// work already queued on s and before the work queued on s afterwards;
+// meanwhile s may run the Born term, which does not involve G1 (the
+// resolvent keeps the FP64 pipe busy, the float-float Born term the FP32
+// pipe)
+wpcd_status batch_resolvent(const wpcd_problem *pr, const double *E, int B, SolveCtx &cx, bool need32,
+                            cudaStream_t s, cudaStream_t s2, cudaEvent_t before, cudaEvent_t after) {
+  const size_t dim = (size_t)pr->n_ch * pr->N * pr->M;
+  WPCD_CUDA_TRY(cudaStreamWaitEvent(s2, before, 0));
+  wpcd_status st = resolvent_impl(pr, E, B, cx.g, 1, nullptr, nullptr, s2);
+  if (st != WPCD_OK) return st;
+  if (need32) {
+    d2f_kernel<<<grid_for(2 * (int64_t)dim * B, 256), 256, 0, s2>>>(2 * (int64_t)dim * B, cx.g, cx.g32);
+    count_launches(1);
+  }
+  WPCD_CUDA_TRY(cudaEventRecord(after, s2));
+  WPCD_CUDA_TRY(cudaStreamWaitEvent(s, after, 0));
   return WPCD_OK;
 }
 
@@ -1526,13 +1545,29 @@ wpcd_status solve(wpcd_problem *pr, const wpcd_P *Pc, const double *E, int n_E,
       WPCD_CUDA_TRY(cudaEventCreate(&ev0));
       WPCD_CUDA_TRY(cudaEventCreate(&ev1));
       cudaEventRecord(ev0, s);
-      wpcd_status st = batch_setup(pr, E + e0, B, cx, bi, mixed, s);
+      wpcd_status st = batch_setup(pr, E + e0, B, cx, bi, s);
       if (st != WPCD_OK) return st;
       Workspace<double> ws64;
       WPCD_CUDA_TRY(ws64.alloc(dim, B));
       DfWork dfw;
       if (dfres) WPCD_CUDA_TRY(dfw.alloc(dim, B));
+      // Born term on s, resolvent concurrently on a side stream
+      struct Side {
+        cudaStream_t s2 = nullptr;
+        cudaEvent_t before = nullptr, after = nullptr;
+        ~Side() {
+          if (before) cudaEventDestroy(before);
+          if (after) cudaEventDestroy(after);
+          if (s2) cudaStreamDestroy(s2);
+        }
+      } side;
+      WPCD_CUDA_TRY(cudaStreamCreateWithFlags(&side.s2, cudaStreamNonBlocking));
+      WPCD_CUDA_TRY(cudaEventCreateWithFlags(&side.before, cudaEventDisableTiming));
+      WPCD_CUDA_TRY(cudaEventCreateWithFlags(&side.after, cudaEventDisableTiming));
+      WPCD_CUDA_TRY(cudaEventRecord(side.before, s));
       st = dfres ? df_born(pr, P, cx.r0, B, cx.b, dfw, s) : born(pr, P, cx, ws64, s);
+      if (st != WPCD_OK) return st;
+      st = batch_resolvent(pr, E + e0, B, cx, mixed, s, side.s2, side.before, side.after);
       if (st != WPCD_OK) return st;
       const bool warm = opt.u_init != nullptr;
       const int64_t n = (int64_t)dim * B;
