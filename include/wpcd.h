@@ -310,12 +310,14 @@ wpcd_status wpcd_channel_gemm(wpcd_problem *pr, int which, int mode, const void 
 
 /* Autotuner (batching): time the candidate SpMM launch shapes (rows per
  * warp, energy lanes per row, energies per lane = RHS tile width) for a
- * batch of n_rhs energies in FP64 (fp32 = 0) or FP32 (fp32 = 1) and keep the
- * fastest in P for later solves; returns the choice.  Solves tune on first
- * use of a (batch, precision) pair.  With WPCD_TUNE_CACHE set to a file
- * path, choices are also read from / appended to that file (text lines
- * "key rows_per_warp energy_lanes energies_per_lane"). */
-wpcd_status wpcd_tune_spmm(wpcd_problem *pr, wpcd_P *P, int n_rhs, int fp32, void *stream,
+ * batch of n_rhs energies in the arithmetic of mode (WPCD_SPMM_FP64,
+ * WPCD_SPMM_FP32 or WPCD_SPMM_FF) and keep the fastest for later solves
+ * (for every P0 of the same shape in the process); returns the choice.
+ * Solves tune on first use of a (batch, arithmetic) pair.  With
+ * WPCD_TUNE_CACHE set to a file path, choices are also read from /
+ * appended to that file (text lines "key rows_per_warp energy_lanes
+ * energies_per_lane"). */
+wpcd_status wpcd_tune_spmm(wpcd_problem *pr, wpcd_P *P, int n_rhs, int mode, void *stream,
                            int *rows_per_warp, int *energy_lanes, int *energies_per_lane);
 
 /* Largest problem dimension n_ch*N*M that wpcd_kapply_noalloc accepts. */

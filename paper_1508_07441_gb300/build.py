@@ -37,6 +37,7 @@ def _stale(obj: str, src: str) -> bool:
         return True
     t = os.path.getmtime(obj)
     deps = [src, os.path.join(CSRC, "wpcd_internal.h"), os.path.join(CSRC, "common.cuh"),
+            os.path.join(CSRC, "df_common.cuh"),
             os.path.join(ROOT, "include", "wpcd.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 

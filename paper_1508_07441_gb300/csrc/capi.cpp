@@ -395,17 +395,23 @@ wpcd_status wpcd_born(wpcd_problem *pr, const wpcd_P *P, const double *E, int n_
   WPCD_GUARD_END
 }
 
-wpcd_status wpcd_tune_spmm(wpcd_problem *pr, wpcd_P *P, int n_rhs, int fp32, void *stream,
+wpcd_status wpcd_tune_spmm(wpcd_problem *pr, wpcd_P *P, int n_rhs, int mode, void *stream,
                            int *rows_per_warp, int *energy_lanes, int *energies_per_lane) {
   WPCD_GUARD_BEGIN
   clear_error();
   if (!pr || !P || P->pr != pr) return set_error(WPCD_EINVAL, "bad problem or P");
   if (n_rhs < 1 || n_rhs > 1024) return set_error(WPCD_EINVAL, "n_rhs must be in [1, 1024]");
-  if (fp32 && !P->val32 && !P->val32_copy)
+  if (mode < WPCD_SPMM_FP64 || mode > WPCD_SPMM_FF) return set_error(WPCD_EINVAL, "unknown SpMM mode");
+  if (mode == WPCD_SPMM_FP32 && !P->val32 && !P->val32_copy)
     return set_error(WPCD_EINVAL, "FP32 tuning needs an FP32C P (or a mixed solve first)");
   WPCD_CUDA_TRY(cudaSetDevice(pr->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (mode == WPCD_SPMM_FF) {
+    wpcd_status st = df_prepare(pr, P, s);
+    if (st != WPCD_OK) return st;
+  }
   SpmmConfig c;
-  wpcd_status st = tune_spmm(pr, P, n_rhs, fp32 ? 1 : 0, static_cast<cudaStream_t>(stream), &c);
+  wpcd_status st = tune_spmm(pr, P, n_rhs, mode, s, &c);
   if (st != WPCD_OK) return st;
   if (rows_per_warp) *rows_per_warp = c.rpw;
   if (energy_lanes) *energy_lanes = c.el;

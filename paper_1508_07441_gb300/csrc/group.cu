@@ -296,18 +296,26 @@ template <typename T>
 __global__ void greduce_kernel(const GMeta *__restrict__ gm, int nv, int NBT, const double2 *__restrict__ partial,
                                double2 *__restrict__ out, int accumulate, typename Cx<T>::t *coef, double sign,
                                T *inv) {
+  // one warp per output (j, s): the lanes stride over the problem's blocks
   const int S = gm->S;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nv * S) return;
+  const int idx = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (idx >= nv * S) return;  // warp-uniform
   const int j = idx / S, s = idx % S;
   const int g = seg_of(gm->sys, gm->n, s);
   const int e = s - gm->sys[g];
   double sx = 0.0, sy = 0.0;
-  for (int b = gm->blk_off[g]; b < gm->blk_off[g + 1]; ++b) {
+  for (int b = gm->blk_off[g] + lane; b < gm->blk_off[g + 1]; b += 32) {
     const double2 p = partial[((size_t)j * NBT + b) * kMaxGroupE + e];
     sx += p.x;
     sy += p.y;
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+  }
+  if (lane != 0) return;
   if (coef) {
     coef[idx].x = (T)(sign * sx);
     coef[idx].y = (T)(sign * sy);
@@ -639,7 +647,7 @@ struct GKrylov {
   void dots(int nv, const typename Cx<U>::t *base, size_t ld, const typename Cx<U>::t *x, double2 *out,
             int accumulate, cudaStream_t s, bool hcoef = false, bool scale = false) {
     gdot_kernel<U><<<gr->nbt(), gr->dot_block(), 0, s>>>(gr->d_meta, nv, base, ld, x, partial);
-    greduce_kernel<T><<<(nv * S + 255) / 256, 256, 0, s>>>(gr->d_meta, nv, gr->nbt(), partial, out, accumulate,
+    greduce_kernel<T><<<(nv * S * 32 + 255) / 256, 256, 0, s>>>(gr->d_meta, nv, gr->nbt(), partial, out, accumulate,
                                                            hcoef ? hc : nullptr, -1.0, scale ? inv : nullptr);
     count_launches(2);
   }
@@ -659,7 +667,7 @@ struct GKrylov {
       dots<T>(k + 1, vec(0), ld, wv(), h2, 0, s, true);
       gaxpy_kernel<T><<<vg, 256, 0, s>>>(gr->d_meta, L, k + 1, vec(0), ld, hc, wv());
       // h += h2: the second pass's coefficients, summed from its partials
-      greduce_kernel<T><<<((k + 1) * S + 255) / 256, 256, 0, s>>>(gr->d_meta, k + 1, gr->nbt(), partial, h, 1,
+      greduce_kernel<T><<<((k + 1) * S * 32 + 255) / 256, 256, 0, s>>>(gr->d_meta, k + 1, gr->nbt(), partial, h, 1,
                                                                    nullptr, 0.0, nullptr);
       count_launches(2);
     }

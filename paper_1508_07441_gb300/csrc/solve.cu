@@ -332,15 +332,23 @@ __global__ void __launch_bounds__(V_THREADS) bdot_kernel(int rows, int B, int nv
 template <typename T>
 __global__ void breduce_kernel(int nv, int nblk, int B, const double2 *partial, double2 *out, int accumulate,
                                typename Cx<T>::t *coef, double sign, T *inv) {
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nv * B) return;
-  int j = idx / B, e = idx % B;
+  // one warp per output (j, e): the lanes stride over the block partials
+  const int idx = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (idx >= nv * B) return;  // warp-uniform
+  const int j = idx / B, e = idx % B;
   double sx = 0.0, sy = 0.0;
-  for (int b = 0; b < nblk; ++b) {
-    double2 p = partial[((size_t)j * nblk + b) * B + e];
+  for (int b = lane; b < nblk; b += 32) {
+    const double2 p = partial[((size_t)j * nblk + b) * B + e];
     sx += p.x;
     sy += p.y;
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+  }
+  if (lane != 0) return;
   if (coef) {
     coef[idx].x = (T)(sign * sx);
     coef[idx].y = (T)(sign * sy);
@@ -353,6 +361,9 @@ __global__ void breduce_kernel(int nv, int nblk, int B, const double2 *partial, 
     out[idx] = make_double2(sx, sy);
   }
 }
+
+// launch shape of breduce_kernel: one warp per output
+inline int breduce_blocks(int outputs) { return (outputs * 32 + 255) / 256; }
 
 // w[f] += sum_j c[j * B + e] V_j[f]   (coefficients in the vector precision)
 template <typename T>
@@ -603,12 +614,15 @@ void store_cached(int64_t key, const SpmmConfig &c) {
 }  // namespace
 
 // Time every candidate launch shape on the real P0 (3 launches each, CUDA
-// events, the minimum kept) and remember the fastest.
-wpcd_status tune_spmm(const wpcd_problem *pr, wpcd_P *P, int B, int fp32, cudaStream_t s,
+// events, the minimum kept) and remember the fastest.  mode: 0 FP64
+// vectors, 1 FP32, 2 float-float (the refinement residual's SpMM).
+wpcd_status tune_spmm(const wpcd_problem *pr, wpcd_P *P, int B, int mode, cudaStream_t s,
                       SpmmConfig *out) {
   std::lock_guard<std::mutex> lock(g_tune_mutex);
+  if (mode < 0 || mode > 2) return set_error(WPCD_EINVAL, "unknown SpMM tuning mode");
+  const bool fp32 = mode == 1, ff = mode == 2;
   // the key carries the shape so that one cache file can serve several problems
-  const int64_t key = ((((int64_t)pr->n_ch * 4096 + pr->N) * 4096 + pr->M) * 4096 + B) * 2 + (fp32 ? 1 : 0);
+  const int64_t key = ((((int64_t)pr->n_ch * 4096 + pr->N) * 4096 + pr->M) * 4096 + B) * 4 + mode;
   auto it = P->tuned.find(key);
   if (it != P->tuned.end()) {
     *out = it->second;
@@ -628,8 +642,10 @@ wpcd_status tune_spmm(const wpcd_problem *pr, wpcd_P *P, int B, int fp32, cudaSt
     return WPCD_OK;
   }
   if (fp32 && !P->val32 && !P->val32_copy) return set_error(WPCD_EINVAL, "no FP32 values to tune on");
+  if (ff && P->prec == WPCD_FP64 && !P->val_h) return set_error(WPCD_EINVAL, "no float-float values to tune on");
   const size_t dim = (size_t)pr->n_ch * pr->N * pr->M;
   void *y = nullptr, *z = nullptr;
+  // float-float vectors: hi and lo float arrays, the size of one FP64 vector
   const size_t esz = fp32 ? sizeof(float) : sizeof(double);
   WPCD_CUDA_TRY(cudaMalloc(&y, 2 * esz * dim * B));
   cudaError_t ce = cudaMalloc(&z, 2 * esz * dim * B);
@@ -648,7 +664,11 @@ wpcd_status tune_spmm(const wpcd_problem *pr, wpcd_P *P, int B, int fp32, cudaSt
     float tmin = 1e30f;
     for (int rep = 0; rep < 3 && st == WPCD_OK; ++rep) {
       cudaEventRecord(a, s);
-      if (fp32) {
+      if (ff) {
+        const size_t half = 2 * dim * (size_t)B;  // floats per part
+        st = launch_spmm_df_cfg(pr, P, (const float *)y, (const float *)y + half, (float *)z, (float *)z + half, B,
+                                c, s);
+      } else if (fp32) {
         const float *v32 = P->val32 ? P->val32 : P->val32_copy;
         st = launch_spmm_cfg<float, float>(pr, P, v32, (const float *)y, (float *)z, B, c, s);
       } else if (P->prec == WPCD_FP64) {
@@ -921,7 +941,7 @@ struct Krylov {
   void dots(int nv, const typename Cx<U>::t *base, size_t ld, const typename Cx<U>::t *x, double2 *out,
             int accumulate, cudaStream_t s, bool hcoef = false, bool scale = false) {
     bdot_kernel<U><<<dot_grid(), dot_block(), 0, s>>>((int)dim, B, nv, base, ld, x, partial);
-    breduce_kernel<T><<<(nv * B + 255) / 256, 256, 0, s>>>(nv, nblk, B, partial, out, accumulate,
+    breduce_kernel<T><<<breduce_blocks(nv * B), 256, 0, s>>>(nv, nblk, B, partial, out, accumulate,
                                                            hcoef ? hc : nullptr, -1.0, scale ? inv : nullptr);
     count_launches(2);
   }
@@ -942,7 +962,7 @@ struct Krylov {
       dots<T>(k + 1, vec(0), ld, wv(), h2, 0, s, true);
       baxpy_kernel<T><<<vg, 256, 0, s>>>(n, B, k + 1, vec(0), ld, hc, wv());
       // h += h2 (the second pass's partials are still in place)
-      breduce_kernel<T><<<((k + 1) * B + 255) / 256, 256, 0, s>>>(k + 1, nblk, B, partial, h, 1, nullptr, 0.0,
+      breduce_kernel<T><<<breduce_blocks((k + 1) * B), 256, 0, s>>>(k + 1, nblk, B, partial, h, 1, nullptr, 0.0,
                                                                    nullptr);
       count_launches(2);
     }

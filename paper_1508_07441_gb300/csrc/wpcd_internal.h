@@ -143,7 +143,7 @@ wpcd_status kapply(const wpcd_problem *pr, const wpcd_P *P, const double *g, con
                    double *y, cudaStream_t s);
 wpcd_status solve(wpcd_problem *pr, const wpcd_P *P, const double *E, int n_E,
                   const wpcd_solve_opts *o, double *U00, wpcd_solve_stats *st, cudaStream_t s);
-wpcd_status tune_spmm(const wpcd_problem *pr, wpcd_P *P, int B, int fp32, cudaStream_t s,
+wpcd_status tune_spmm(const wpcd_problem *pr, wpcd_P *P, int B, int mode, cudaStream_t s,
                       SpmmConfig *out);
 wpcd_status kapply_scratch(const wpcd_problem *pr, const wpcd_P *P, const double *g, const double *x,
                            double *y, double *scratch_y, double *scratch_z, cudaStream_t s);
@@ -172,6 +172,8 @@ struct DfWork {
 wpcd_status df_prepare(wpcd_problem *pr, wpcd_P *P, cudaStream_t s);
 wpcd_status df_kapply(const wpcd_problem *pr, const wpcd_P *P, const double *g, const double *x, double *out, int B,
                       DfWork &w, cudaStream_t s);
+wpcd_status launch_spmm_df_cfg(const wpcd_problem *pr, const wpcd_P *P, const float *yh, const float *yl,
+                               float *zh, float *zl, int B, const SpmmConfig &cfg, cudaStream_t s);
 wpcd_status df_gemm_op(wpcd_problem *pr, bool use_O, const double *g, const double *x, double *y, int B, float *ms,
                        cudaStream_t s);
 wpcd_status df_spmm_op(wpcd_problem *pr, wpcd_P *P, const double *y, double *z, int B, float *ms, cudaStream_t s);

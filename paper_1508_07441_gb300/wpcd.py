@@ -299,10 +299,12 @@ class Problem:
         E = np.ascontiguousarray(np.atleast_1d(E), dtype=np.float64)
         check(lib().wpcd_born(self._h, P.handle, _dp(E), len(E), _tensor_ptr(b), _stream_ptr(stream)))
 
-    def wpcd_tune_spmm(self, P, n_rhs, fp32=False, stream=None):
-        """(rows_per_warp, energy_lanes, energies_per_lane) chosen by timing."""
+    def wpcd_tune_spmm(self, P, n_rhs, fp32=False, stream=None, mode=None):
+        """(rows_per_warp, energy_lanes, energies_per_lane) chosen by timing;
+        mode: WPCD_SPMM_* (default: FP32 if fp32 else FP64)."""
+        m = (WPCD_SPMM_FP32 if fp32 else WPCD_SPMM_FP64) if mode is None else mode
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        check(lib().wpcd_tune_spmm(self._h, P.handle, n_rhs, 1 if fp32 else 0, _stream_ptr(stream),
+        check(lib().wpcd_tune_spmm(self._h, P.handle, n_rhs, m, _stream_ptr(stream),
                                    ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return a.value, b.value, c.value
 

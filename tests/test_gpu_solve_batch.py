@@ -132,8 +132,8 @@ def test_autotuner(W, sys3, tmp_path, monkeypatch):
     cache = tmp_path / "tune.txt"
     monkeypatch.setenv("WPCD_TUNE_CACHE", str(cache))
     for B in (1, 3, 8, 64):
-        for fp32, P in ((0, P64), (1, P32)):
-            rpw, el, ept = pr.wpcd_tune_spmm(P, B, fp32=bool(fp32))
+        for mode, P in ((W.WPCD_SPMM_FP64, P64), (W.WPCD_SPMM_FP32, P32), (W.WPCD_SPMM_FF, P64)):
+            rpw, el, ept = pr.wpcd_tune_spmm(P, B, mode=mode)
             assert rpw * el <= 32 and 32 % (rpw * el) == 0
             assert ept in (1, 2, 4)
             if B == 1:
