@@ -190,9 +190,9 @@ typedef struct {
   double tol;      /* Krylov, mixed: relative residual; Wynn: relative change */
   int check_every; /* FP64 Krylov: read the residual estimates back every n
                       steps (1 gives exact per-energy step counts) */
-  int precision;   /* WPCD_SOLVE_FP64, WPCD_SOLVE_MIXED or WPCD_SOLVE_MIXED_FP64
-                      (the grouped solve forms its residual in FP64 in both
-                      mixed modes) */
+  int precision;   /* WPCD_SOLVE_FP64, WPCD_SOLVE_MIXED (float-float residual
+                      and Born term) or WPCD_SOLVE_MIXED_FP64 (native FP64
+                      residual), in wpcd_solve and wpcd_solve_batch alike */
   int batch;       /* energies solved together in one batched iteration
                       (block K applications, SpMM over the batch); 0: all */
   int inner_iter;  /* mixed: Krylov steps per refinement cycle (0: 10) */
@@ -251,7 +251,8 @@ wpcd_status wpcd_solve(wpcd_problem *pr, const wpcd_P *P, const double *E, int n
  * Krylov vector kernels work on the concatenated per-problem batches (the
  * wpcd_solve layout, energy index innermost, one segment per problem).
  * Each (problem, energy) system keeps its own G1 and Krylov basis; with
- * WPCD_SOLVE_MIXED the FP32 inner cycle of all problems is one CUDA graph.
+ * WPCD_SOLVE_MIXED the FP32 inner cycle of all problems is one CUDA graph
+ * and the refinement residual is one float-float launch per operation.
  * problems[g], P[g]: problem g and its assembled P0 (all on one device, the
  * same channel count and the same P0 precision); E[g]: host [n_E[g]]
  * energies, 1 <= n_E[g] <= WPCD_GROUP_MAX_E; U00[g]: host [n_E[g]] complex

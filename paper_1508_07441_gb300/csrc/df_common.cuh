@@ -92,7 +92,8 @@ __device__ __forceinline__ void gemm_df_tile(int n, int64_t ncol, const float *_
   auto &sBl = sm.sBl;
   const size_t offA = 0, offB = 0;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  const bool vec = ncol % 4 == 0;  // 16-byte aligned panel rows
+  // 16-byte aligned panel rows (the grouped solve's segments may start on 8 bytes)
+  const bool vec = ncol % 4 == 0 && ((reinterpret_cast<uintptr_t>(Bh) | reinterpret_cast<uintptr_t>(Bl)) & 15) == 0;
   float hi[2][8], lo[2][8];
 #pragma unroll
   for (int u = 0; u < 2; ++u)

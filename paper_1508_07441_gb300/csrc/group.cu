@@ -11,6 +11,8 @@
 //   gspmm_kernel  warps walk the concatenated row space of all P0 matrices;
 //                 each row finds its problem by binary search over the row
 //                 offsets (held in shared memory)
+//   ggemm_df_kernel / gspmm_df_kernel  the same two walks in float-float
+//                 (hi + lo floats) for the refinement residual
 //   gdot / gaxpy / gscale / gupdate ...  Krylov vector kernels over the
 //                 concatenated segments; an element finds its system
 //                 (problem, energy) by binary search over segment offsets
@@ -30,6 +32,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "df_common.cuh"
 #include "wpcd_internal.h"
 
 namespace wpcd {
@@ -47,6 +50,7 @@ struct GMeta {
   int B[kMaxGroup];                 // energies per problem
   int sys[kMaxGroup + 1];           // first system of each problem
   int tile_off[kMaxGroup + 1];      // first GEMM tile of each problem
+  int dtile_off[kMaxGroup + 1];     // first float-float GEMM tile (32 x 128) of each problem
   int cell_off[kMaxGroup + 1];      // first P0 row of each problem
   int blk_off[kMaxGroup + 1];       // first dot-product block of each problem
 };
@@ -54,6 +58,7 @@ struct GMeta {
 // one problem's operands (device pointers)
 struct alignas(16) GProb {
   int N, M, B, n_cells, rt, ct;     // grid, energies, cells, GEMM tiles per channel
+  int dct, pad_;                    // float-float GEMM column tiles per channel
   int64_t eoff, nnz;
   const int64_t *row_ptr;
   const int32_t *col;
@@ -61,6 +66,8 @@ struct alignas(16) GProb {
   const float *val32;               // FP32 P0 values (FP32C assembly, or the FP32 copy)
   const double *O, *Vt;
   const float *O32, *Vt32;
+  const float *O_h, *O_l, *Vt_h, *Vt_l;  // float-float splits of O and Vt
+  const float *val_h, *val_l;            // float-float P0 values (val_l NULL for FP32C values)
 };
 
 // largest g in [0, n) with off[g] <= x
@@ -226,6 +233,104 @@ __global__ void __launch_bounds__(256) gspmm_kernel(const GMeta *__restrict__ gm
           }
       }
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// grouped float-float operators for the refinement residual: the same tile
+// list and row walk, with hi + lo float operands (exact splits of the FP64
+// values) and float-float accumulation
+// ---------------------------------------------------------------------------
+template <bool OUT_DF>
+__global__ void __launch_bounds__(G_THREADS) ggemm_df_kernel(const GMeta *__restrict__ gm,
+                                                                const GProb *__restrict__ gp, int use_O,
+                                                                const float *__restrict__ Xh,
+                                                                const float *__restrict__ Xl, double *__restrict__ C,
+                                                                float *__restrict__ Ch, float *__restrict__ Cl) {
+  __shared__ DfGemmSmem sm;
+  __shared__ int toff[kMaxGroup + 1];
+  const int n = gm->n;
+  for (int i = threadIdx.x; i <= n; i += blockDim.x) toff[i] = gm->dtile_off[i];
+  __syncthreads();
+  const int total = toff[n];
+  for (int t = blockIdx.x; t < total; t += gridDim.x) {  // uniform per CTA
+    const int g = seg_of(toff, n, t);
+    const GProb &P = gp[g];
+    const int N = P.N, ct = P.dct;
+    const int lt = t - toff[g];
+    const int per_ch = P.rt * ct;
+    const int ch = lt / per_ch, rem = lt % per_ch;
+    const int64_t ncol = 2LL * P.M * P.B;
+    const size_t ao = (size_t)ch * N * N;
+    const float *Ah = (use_O ? P.O_h : P.Vt_h) + ao, *Al = (use_O ? P.O_l : P.Vt_l) + ao;
+    const size_t base = 2 * (size_t)P.eoff + (size_t)ch * N * ncol;
+    gemm_df_tile<OUT_DF>(N, ncol, Ah, Al, Xh + base, Xl + base, OUT_DF ? nullptr : C + base,
+                         OUT_DF ? Ch + base : nullptr, OUT_DF ? Cl + base : nullptr, (rem / ct) * GB_M,
+                         (int64_t)(rem % ct) * DF_N, sm);
+  }
+}
+
+template <int NCH, int EPT>
+__global__ void __launch_bounds__(256) gspmm_df_kernel(const GMeta *__restrict__ gm, const GProb *__restrict__ gp,
+                                                       int rpw, int el_n, const float2 *__restrict__ yh,
+                                                       const float2 *__restrict__ yl, float2 *__restrict__ zh,
+                                                       float2 *__restrict__ zl) {
+  __shared__ int coff[kMaxGroup + 1];
+  __shared__ GProb sp[kMaxGroup];
+  const int n = gm->n;
+  for (int i = threadIdx.x; i <= n; i += blockDim.x) {
+    coff[i] = gm->cell_off[i];
+    if (i < n) sp[i] = gp[i];
+  }
+  __syncthreads();
+  const int total = coff[n];
+  const int lane = threadIdx.x & 31;
+  const int lpr = 32 / rpw, nl_count = lpr / el_n;
+  const int r_in = lane / lpr, sub = lane % lpr;
+  const int el = sub % el_n, nl = sub / el_n;
+  const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int n_warps = gridDim.x * blockDim.x / 32;
+  const int e_base = blockIdx.y * el_n * EPT;
+  // warp-uniform loop bound: every lane reaches the full-mask shuffles
+  for (int base = warp_global * rpw; base < total; base += n_warps * rpw) {
+    const int R = base + r_in;
+    const bool active = R < total;
+    const int g = active ? seg_of(coff, n, R) : 0;
+    const GProb &P = sp[g];
+    const int c = R - coff[g];
+    float ah[NCH][EPT][2], al[NCH][EPT][2];
+#pragma unroll
+    for (int l = 0; l < NCH; ++l)
+#pragma unroll
+      for (int t = 0; t < EPT; ++t) ah[l][t][0] = ah[l][t][1] = al[l][t][0] = al[l][t][1] = 0.f;
+    const int64_t b = active ? P.row_ptr[c] : 0, e = active ? P.row_ptr[c + 1] : 0;
+    spmm_df_row<NCH, EPT>(b, e, nl, nl_count, P.col, P.val_h, P.val_l, P.nnz, yh + P.eoff, yl + P.eoff, P.n_cells,
+                          P.B, e_base + el, el_n, ah, al);
+    spmm_df_finish<NCH, EPT>(el_n, lpr, active && nl == 0, ah, al, zh + P.eoff, zl + P.eoff, P.n_cells, c, P.B,
+                             e_base + el, el_n);
+  }
+}
+
+// Vt e0 for every system in float-float (the splits of gborn_vt_kernel's values)
+__global__ void gborn_vt_df_kernel(const GMeta *__restrict__ gm, const GProb *__restrict__ gp, int64_t len,
+                                   const int *__restrict__ j0, float2 *__restrict__ yh, float2 *__restrict__ yl) {
+  __shared__ SegSmem sm;
+  load_segs(gm, sm);
+  const int n = gm->n;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < len; f += (int64_t)gridDim.x * blockDim.x) {
+    const int g = seg_of(sm.off, n, f);
+    const int B = sm.B[g];
+    const int64_t loc = f - sm.off[g];
+    const int e = (int)(loc % B);
+    const int64_t r = loc / B;
+    const int N = gp[g].N, M = gp[g].M;
+    float h = 0.f, l = 0.f;
+    if (r < (int64_t)N * M && (int)(r % M) == j0[sm.sys[g] + e]) {
+      h = gp[g].Vt_h[(r / M) * N];
+      l = gp[g].Vt_l[(r / M) * N];
+    }
+    yh[f] = make_float2(h, 0.f);
+    yl[f] = make_float2(l, 0.f);
   }
 }
 
@@ -466,7 +571,7 @@ struct Group {
   std::vector<GProb> probs;
   GMeta *d_meta = nullptr;
   GProb *d_probs = nullptr;
-  SpmmConfig cfg64, cfg32;
+  SpmmConfig cfg64, cfg32, cfgff;
   dim3 dot_block() const {
     int el = 1;
     while (el < Bmax) el *= 2;
@@ -474,9 +579,52 @@ struct Group {
   }
   int nbt() const { return meta.blk_off[n]; }
   int tiles() const { return meta.tile_off[n]; }
+  int dtiles() const { return meta.dtile_off[n]; }
 };
 
 int gemm_grid(const Group &gr) { return std::max(1, std::min(gr.tiles(), 152 * 4)); }
+
+// C = A X' per (problem, channel) in float-float; OUT_DF: C as (Ch, Cl)
+template <bool OUT_DF>
+void ggemm_df(const Group &gr, bool use_O, const float *Xh, const float *Xl, double *C, float *Ch, float *Cl,
+              cudaStream_t s) {
+  const int grid = std::max(1, std::min(gr.dtiles(), 152 * 2));
+  ggemm_df_kernel<OUT_DF><<<grid, G_THREADS, 0, s>>>(gr.d_meta, gr.d_probs, use_O, Xh, Xl, C, Ch, Cl);
+  count_launches(1);
+}
+
+wpcd_status gspmm_df_cfg(const Group &gr, const float *yh, const float *yl, float *zh, float *zl,
+                         const SpmmConfig &cfg, cudaStream_t s) {
+  const float2 *y2h = reinterpret_cast<const float2 *>(yh), *y2l = reinterpret_cast<const float2 *>(yl);
+  float2 *z2h = reinterpret_cast<float2 *>(zh), *z2l = reinterpret_cast<float2 *>(zl);
+  dim3 grid(grid_for((int64_t)gr.meta.cell_off[gr.n], 8 * cfg.rpw, 152 * 16),
+            (gr.Bmax + cfg.el * cfg.ept - 1) / (cfg.el * cfg.ept));
+#define WPCD_GDF_EPT(NCH, EPT) \
+  gspmm_df_kernel<NCH, EPT><<<grid, 256, 0, s>>>(gr.d_meta, gr.d_probs, cfg.rpw, cfg.el, y2h, y2l, z2h, z2l)
+#define WPCD_GDF_CASE(NCH)  \
+  case NCH:                 \
+    if (cfg.ept == 1)       \
+      WPCD_GDF_EPT(NCH, 1); \
+    else if (cfg.ept == 2)  \
+      WPCD_GDF_EPT(NCH, 2); \
+    else                    \
+      WPCD_GDF_EPT(NCH, 4); \
+    break;
+  switch (gr.n_ch) {
+    WPCD_GDF_CASE(1)
+    WPCD_GDF_CASE(2)
+    WPCD_GDF_CASE(3)
+    WPCD_GDF_CASE(4)
+    WPCD_GDF_CASE(5)
+    default:
+      return set_error(WPCD_EINVAL, "unsupported channel count for the SpMM");
+  }
+#undef WPCD_GDF_CASE
+#undef WPCD_GDF_EPT
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? WPCD_OK : cuda_error(e, "grouped float-float spmm launch");
+}
 
 template <typename T>
 void ggemm(const Group &gr, bool use_O, bool scale_g, bool sub, const T *X, const T *G, const T *S, T *C,
@@ -538,8 +686,8 @@ wpcd_status gspmm(const Group &gr, const T *y, T *z, const SpmmConfig &cfg, cuda
 std::mutex g_gtune_mutex;
 std::map<std::string, SpmmConfig> g_gtuned;
 
-std::string group_key(const Group &gr, int fp32) {
-  std::string k = std::to_string(gr.n_ch) + "/" + std::to_string(gr.prec) + "/" + std::to_string(fp32);
+std::string group_key(const Group &gr, int mode) {
+  std::string k = std::to_string(gr.n_ch) + "/" + std::to_string(gr.prec) + "/" + std::to_string(mode);
   for (int g = 0; g < gr.n; ++g)
     k += ":" + std::to_string(gr.probs[g].N) + "x" + std::to_string(gr.probs[g].M) + "b" +
          std::to_string(gr.probs[g].B) + "n" + std::to_string(gr.probs[g].nnz);
@@ -547,17 +695,17 @@ std::string group_key(const Group &gr, int fp32) {
 }
 
 // time every candidate shape on the whole group (3 launches each, CUDA
-// events, the minimum kept); must run outside stream capture
-template <typename T>
-wpcd_status gtune(const Group &gr, T *y, T *z, cudaStream_t s, SpmmConfig *out) {
+// events, the minimum kept) with run(cfg); mode 0 FP64, 1 FP32, 2
+// float-float; the caller zeroes the input vectors; outside stream capture
+template <typename Run>
+wpcd_status gtune(const Group &gr, int mode, Run run, cudaStream_t s, SpmmConfig *out) {
   std::lock_guard<std::mutex> lock(g_gtune_mutex);
-  const std::string key = group_key(gr, sizeof(T) == 4);
+  const std::string key = group_key(gr, mode);
   auto it = g_gtuned.find(key);
   if (it != g_gtuned.end()) {
     *out = it->second;
     return WPCD_OK;
   }
-  WPCD_CUDA_TRY(cudaMemsetAsync(y, 0, 2 * sizeof(T) * gr.L, s));
   cudaEvent_t a, b;
   WPCD_CUDA_TRY(cudaEventCreate(&a));
   WPCD_CUDA_TRY(cudaEventCreate(&b));
@@ -568,7 +716,7 @@ wpcd_status gtune(const Group &gr, T *y, T *z, cudaStream_t s, SpmmConfig *out) 
     float tmin = 1e30f;
     for (int rep = 0; rep < 3 && st == WPCD_OK; ++rep) {
       cudaEventRecord(a, s);
-      st = gspmm<T>(gr, y, z, c, s);
+      st = run(c);
       cudaEventRecord(b, s);
       cudaEventSynchronize(b);
       float ms = 0.f;
@@ -599,6 +747,25 @@ wpcd_status gkapply(const Group &gr, const T *g, const T *x, T *out, const T *su
   ggemm<T>(gr, true, false, sub != nullptr, wz, nullptr, sub, out, s);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? WPCD_OK : cuda_error(e, "grouped kapply launch");
+}
+
+// float-float work vectors of the grouped residual (2 L floats each)
+struct GDf {
+  float *xh = nullptr, *xl = nullptr, *yh = nullptr, *yl = nullptr;
+};
+
+// out = O P0 Vt (g o x) for every system in float-float, FP64 in and out
+wpcd_status gkapply_df(const Group &gr, const double *g, const double *x, double *out, const GDf &w,
+                       cudaStream_t s) {
+  df_split_scaled_kernel<<<grid_for(gr.L, 256), 256, 0, s>>>(gr.L, reinterpret_cast<const double2 *>(x),
+                                                            reinterpret_cast<const double2 *>(g), w.xh, w.xl);
+  count_launches(1);
+  ggemm_df<true>(gr, false, w.xh, w.xl, nullptr, w.yh, w.yl, s);
+  wpcd_status st = gspmm_df_cfg(gr, w.yh, w.yl, w.xh, w.xl, gr.cfgff, s);
+  if (st != WPCD_OK) return st;
+  ggemm_df<false>(gr, true, w.xh, w.xl, out, nullptr, nullptr, s);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? WPCD_OK : cuda_error(e, "grouped float-float kapply launch");
 }
 
 // Krylov bases and least-squares state of all systems
@@ -681,6 +848,7 @@ struct GKrylov {
 struct GCtx {
   double *g = nullptr, *b = nullptr, *u = nullptr, *r = nullptr, *t = nullptr, *wy = nullptr, *wz = nullptr;
   float *g32 = nullptr, *wy32 = nullptr, *wz32 = nullptr;
+  GDf df;               // float-float residual work (WPCD_SOLVE_MIXED)
   int *j0 = nullptr;
   int64_t *idx0 = nullptr;
   double *D = nullptr, *pref = nullptr, *amp = nullptr;
@@ -803,7 +971,8 @@ wpcd_status gsolve_mixed(const Group &gr, const wpcd_solve_opts &o, GCtx &cx, GK
   wpcd_status result = WPCD_OK;
   for (int outer = 0; outer <= max_outer; ++outer) {
     if (outer > 0) {  // r = b - (I - K) u in FP64
-      wpcd_status st = gkapply<double>(gr, cx.g, cx.u, cx.t, nullptr, cx.wy, cx.wz, s);
+      wpcd_status st = cx.df.xh ? gkapply_df(gr, cx.g, cx.u, cx.t, cx.df, s)
+                                : gkapply<double>(gr, cx.g, cx.u, cx.t, nullptr, cx.wy, cx.wz, s);
       if (st != WPCD_OK) {
         result = st;
         break;
@@ -930,10 +1099,16 @@ wpcd_status solve_group(int n_prob, wpcd_problem *const *prs, const wpcd_P *cons
     }
   }
   WPCD_CUDA_TRY(cudaSetDevice(prs[0]->device));
-  // both mixed modes run the refinement residual in native FP64 here
   const bool mixed = opt.precision != WPCD_SOLVE_FP64;
+  // WPCD_SOLVE_MIXED: float-float residual and Born term; WPCD_SOLVE_MIXED_FP64: native FP64
+  const bool ff = opt.precision == WPCD_SOLVE_MIXED;
   gr.n_ch = prs[0]->n_ch;
   gr.prec = Ps[0]->prec;
+  if (ff)
+    for (int g = 0; g < n_prob; ++g) {
+      wpcd_status st = df_prepare(const_cast<wpcd_problem *>(prs[g]), const_cast<wpcd_P *>(Ps[g]), s);
+      if (st != WPCD_OK) return st;
+    }
   // FP32 values of FP64-assembled matrices for the inner cycles
   for (int g = 0; g < n_prob; ++g) {
     wpcd_P *P = const_cast<wpcd_P *>(Ps[g]);
@@ -948,7 +1123,7 @@ wpcd_status solve_group(int n_prob, wpcd_problem *const *prs, const wpcd_P *cons
   GMeta &mt = gr.meta;
   mt.n = n_prob;
   mt.eoff[0] = 0;
-  mt.sys[0] = mt.tile_off[0] = mt.cell_off[0] = 0;
+  mt.sys[0] = mt.tile_off[0] = mt.dtile_off[0] = mt.cell_off[0] = 0;
   for (int g = 0; g < n_prob; ++g) {
     const wpcd_problem *pr = prs[g];
     const wpcd_P *P = Ps[g];
@@ -960,6 +1135,7 @@ wpcd_status solve_group(int n_prob, wpcd_problem *const *prs, const wpcd_P *cons
     q.n_cells = pr->N * pr->M;
     q.rt = (pr->N + GB_M - 1) / GB_M;
     q.ct = (int)((2LL * pr->M * B + GB_N - 1) / GB_N);
+    q.dct = (int)((2LL * pr->M * B + DF_N - 1) / DF_N);
     q.eoff = mt.eoff[g];
     q.nnz = P->nnz;
     q.row_ptr = P->row_ptr;
@@ -970,11 +1146,18 @@ wpcd_status solve_group(int n_prob, wpcd_problem *const *prs, const wpcd_P *cons
     q.Vt = pr->d.Vt;
     q.O32 = pr->d.O32;
     q.Vt32 = pr->d.Vt32;
+    q.O_h = pr->d.O_h;
+    q.O_l = pr->d.O_l;
+    q.Vt_h = pr->d.Vt_h;
+    q.Vt_l = pr->d.Vt_l;
+    q.val_h = P->prec == WPCD_FP64 ? P->val_h : P->val32;
+    q.val_l = P->prec == WPCD_FP64 ? P->val_l : nullptr;
     gr.probs.push_back(q);
     mt.B[g] = B;
     mt.eoff[g + 1] = mt.eoff[g] + (int64_t)pr->n_ch * pr->N * pr->M * B;
     mt.sys[g + 1] = mt.sys[g] + B;
     mt.tile_off[g + 1] = mt.tile_off[g] + pr->n_ch * q.rt * q.ct;
+    mt.dtile_off[g + 1] = mt.dtile_off[g] + pr->n_ch * q.rt * q.dct;
     mt.cell_off[g + 1] = mt.cell_off[g] + q.n_cells;
     gr.Bmax = std::max(gr.Bmax, B);
   }
@@ -1005,6 +1188,12 @@ wpcd_status solve_group(int n_prob, wpcd_problem *const *prs, const wpcd_P *cons
     WPCD_CUDA_TRY(cx.mem.alloc(&cx.wy32, nb / 2));
     WPCD_CUDA_TRY(cx.mem.alloc(&cx.wz32, nb / 2));
   }
+  if (ff) {
+    WPCD_CUDA_TRY(cx.mem.alloc(&cx.df.xh, nb / 2));
+    WPCD_CUDA_TRY(cx.mem.alloc(&cx.df.xl, nb / 2));
+    WPCD_CUDA_TRY(cx.mem.alloc(&cx.df.yh, nb / 2));
+    WPCD_CUDA_TRY(cx.mem.alloc(&cx.df.yl, nb / 2));
+  }
   const int S = gr.S;
   WPCD_CUDA_TRY(cx.mem.alloc(&cx.j0, sizeof(int) * S));
   WPCD_CUDA_TRY(cx.mem.alloc(&cx.idx0, sizeof(int64_t) * S));
@@ -1028,8 +1217,21 @@ wpcd_status solve_group(int n_prob, wpcd_problem *const *prs, const wpcd_P *cons
   WPCD_CUDA_TRY(cudaMemcpyAsync(cx.idx0, idx0.data(), sizeof(int64_t) * S, cudaMemcpyHostToDevice, s));
   WPCD_CUDA_TRY(cudaMemcpyAsync(cx.D, Dh.data(), sizeof(double) * S, cudaMemcpyHostToDevice, s));
   WPCD_CUDA_TRY(cudaMemcpyAsync(cx.pref, prefh.data(), sizeof(double) * S, cudaMemcpyHostToDevice, s));
-  wpcd_status st = gtune<double>(gr, cx.wy, cx.wz, s, &gr.cfg64);
-  if (st == WPCD_OK && mixed) st = gtune<float>(gr, cx.wy32, cx.wz32, s, &gr.cfg32);
+  WPCD_CUDA_TRY(cudaMemsetAsync(cx.wy, 0, nb, s));
+  wpcd_status st = gtune(
+      gr, 0, [&](const SpmmConfig &c) { return gspmm<double>(gr, cx.wy, cx.wz, c, s); }, s, &gr.cfg64);
+  if (st == WPCD_OK && mixed) {
+    WPCD_CUDA_TRY(cudaMemsetAsync(cx.wy32, 0, nb / 2, s));
+    st = gtune(
+        gr, 1, [&](const SpmmConfig &c) { return gspmm<float>(gr, cx.wy32, cx.wz32, c, s); }, s, &gr.cfg32);
+  }
+  if (st == WPCD_OK && ff) {
+    WPCD_CUDA_TRY(cudaMemsetAsync(cx.df.yh, 0, nb / 2, s));
+    WPCD_CUDA_TRY(cudaMemsetAsync(cx.df.yl, 0, nb / 2, s));
+    st = gtune(
+        gr, 2, [&](const SpmmConfig &c) { return gspmm_df_cfg(gr, cx.df.yh, cx.df.yl, cx.df.xh, cx.df.xl, c, s); },
+        s, &gr.cfgff);
+  }
   if (st != WPCD_OK) return st;
   WPCD_CUDA_TRY(cudaStreamSynchronize(s));  // host staging vectors
 
@@ -1052,11 +1254,20 @@ wpcd_status solve_group(int n_prob, wpcd_problem *const *prs, const wpcd_P *cons
     gd2f_kernel<<<grid_for(2 * gr.L, 256), 256, 0, s>>>(2 * gr.L, cx.g, cx.g32);
     count_launches(1);
   }
-  gborn_vt_kernel<<<grid_for(gr.L, 256), 256, 0, s>>>(gr.d_meta, gr.d_probs, gr.L, cx.j0, (double2 *)cx.wy);
-  count_launches(1);
-  st = gspmm<double>(gr, cx.wy, cx.wz, gr.cfg64, s);
-  if (st != WPCD_OK) return st;
-  ggemm<double>(gr, true, false, false, cx.wz, nullptr, nullptr, cx.b, s);
+  if (ff) {
+    gborn_vt_df_kernel<<<grid_for(gr.L, 256), 256, 0, s>>>(gr.d_meta, gr.d_probs, gr.L, cx.j0, (float2 *)cx.df.yh,
+                                                           (float2 *)cx.df.yl);
+    count_launches(1);
+    st = gspmm_df_cfg(gr, cx.df.yh, cx.df.yl, cx.df.xh, cx.df.xl, gr.cfgff, s);
+    if (st != WPCD_OK) return st;
+    ggemm_df<false>(gr, true, cx.df.xh, cx.df.xl, cx.b, nullptr, nullptr, s);
+  } else {
+    gborn_vt_kernel<<<grid_for(gr.L, 256), 256, 0, s>>>(gr.d_meta, gr.d_probs, gr.L, cx.j0, (double2 *)cx.wy);
+    count_launches(1);
+    st = gspmm<double>(gr, cx.wy, cx.wz, gr.cfg64, s);
+    if (st != WPCD_OK) return st;
+    ggemm<double>(gr, true, false, false, cx.wz, nullptr, nullptr, cx.b, s);
+  }
   std::vector<int> status, conv;
   std::vector<double> relres;
   int n64 = 0, n32 = 0, n_outer = 0;

@@ -65,13 +65,16 @@ def test_group_fp64_matches_oracle(W, group):
                 assert abs(abs(complex(*s.S)) - 1.0) < 1e-8
 
 
+@pytest.mark.parametrize("resid", ["MIXED", "MIXED_FP64"])
 @pytest.mark.parametrize("prec", ["FP64", "FP32C"])
-def test_group_mixed_matches_oracle(W, orc, group, prec):
+def test_group_mixed_matches_oracle(W, orc, group, prec, resid):
+    """Both refinement residuals: float-float (WPCD_SOLVE_MIXED) and native
+    FP64 (WPCD_SOLVE_MIXED_FP64)."""
     items, energies = group
     if prec == "FP32C":
         items = [(pr, pr.wpcd_assemble_P(W.WPCD_FP32C), opr) for pr, _, opr in items]
     U, stats, st = W.wpcd_solve_batch([i[0] for i in items], [i[1] for i in items], energies,
-                                      tol=1e-12, precision=W.WPCD_SOLVE_MIXED)
+                                      tol=1e-12, precision=getattr(W, "WPCD_SOLVE_" + resid))
     assert st == W.WPCD_OK
     worst = 0.0
     for (pr, P, opr), E, u, sl in zip(items, energies, U, stats):
@@ -83,6 +86,22 @@ def test_group_mixed_matches_oracle(W, orc, group, prec):
     # FP32-valued P0 shifts U00 by its node-evaluation error (the same bar as
     # the single-problem mixed solve)
     assert worst < (1e-8 if prec == "FP64" else 2e-5), worst
+
+
+def test_group_float_float_odd_segment_offsets(W, orc):
+    """Segments that start on an odd complex element (n_ch N M B odd), so
+    the float-float block products of the later problems read panels that
+    are only 8-byte aligned; float-float residual against the oracle."""
+    shapes = [(13, 11), (15, 9), (20, 16)]
+    energies = [[0.3, 1.7, 2.9], [0.9], [-0.4, 2.2]]
+    items = [_make(W, orc, N, M) for N, M in shapes]
+    U, stats, st = W.wpcd_solve_batch([i[0] for i in items], [i[1] for i in items], energies,
+                                      tol=1e-12, precision=W.WPCD_SOLVE_MIXED)
+    assert st == W.WPCD_OK
+    for (pr, P, opr), E, u, sl in zip(items, energies, U, stats):
+        assert all(s.status == W.WPCD_OK and s.relres <= 1e-12 for s in sl)
+        ref = _oracle(opr, E)
+        assert np.max(np.abs(u - ref) / np.abs(ref)) < 1e-8
 
 
 def test_group_equals_per_problem_solves(W, group):
