@@ -340,6 +340,46 @@ __global__ void gborn_vt_df_kernel(const GMeta *__restrict__ gm, const GProb *__
 // partial[((j * NBT) + blk) * 32 + e] = sum over blk's rows of conj(V_j) w,
 // blocks blk_off[g] .. blk_off[g+1]-1 serve problem g; block (EL, RB) with
 // EL >= the problem's energies
+// partial[blk * kMaxGroupE + e] = (sum over blk's rows of |x|^2, 0): the norm
+// pass of gdot_kernel, one vector read once, four rows in flight per thread
+template <typename T>
+__global__ void __launch_bounds__(GV_THREADS) gnorm_kernel(const GMeta *__restrict__ gm,
+                                                           const typename Cx<T>::t *__restrict__ x,
+                                                           double2 *__restrict__ partial) {
+  __shared__ double red[GV_THREADS];
+  const int EL = blockDim.x, RB = blockDim.y;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * EL + tx;
+  const int n = gm->n;
+  const int g = seg_of(gm->blk_off, n, (int)blockIdx.x);
+  const int nb = gm->blk_off[g + 1] - gm->blk_off[g], lb = blockIdx.x - gm->blk_off[g];
+  const int B = gm->B[g];
+  const int64_t off = gm->eoff[g];
+  const int rows = (int)((gm->eoff[g + 1] - off) / B);
+  const int stride = nb * RB;
+  T acc = T(0);
+  if (tx < B) {
+    int r = lb * RB + ty;
+    for (; r + 3 * stride < rows; r += 4 * stride) {
+      typename Cx<T>::t a[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = x[(size_t)off + (size_t)(r + u * stride) * B + tx];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc = fma(a[u].x, a[u].x, fma(a[u].y, a[u].y, acc));
+    }
+    for (; r < rows; r += stride) {
+      const auto a = x[(size_t)off + (size_t)r * B + tx];
+      acc = fma(a.x, a.x, fma(a.y, a.y, acc));
+    }
+  }
+  red[tid] = (double)acc;
+  __syncthreads();
+  for (int h = RB / 2; h > 0; h >>= 1) {
+    if (ty < h) red[tid] += red[(ty + h) * EL + tx];
+    __syncthreads();
+  }
+  if (ty == 0 && tx < B) partial[(size_t)blockIdx.x * kMaxGroupE + tx] = make_double2(red[tx], 0.0);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(GV_THREADS) gdot_kernel(const GMeta *__restrict__ gm, int nv,
                                                           const typename Cx<T>::t *__restrict__ V, size_t ld,
@@ -821,7 +861,10 @@ struct GKrylov {
   // nrm[s] = |x_s|^2 (and inv = 1 / |x_s| in T with scale)
   template <typename U>
   void norms(const typename Cx<U>::t *x, cudaStream_t s, bool scale = false) {
-    dots<U>(1, x, 0, x, nrm, 0, s, false, scale);
+    gnorm_kernel<U><<<gr->nbt(), gr->dot_block(), 0, s>>>(gr->d_meta, x, partial);
+    greduce_kernel<T><<<(S * 32 + 255) / 256, 256, 0, s>>>(gr->d_meta, 1, gr->nbt(), partial, nrm, 0, nullptr, -1.0,
+                                                          scale ? inv : nullptr);
+    count_launches(2);
   }
   // one Arnoldi step from column k (w = (I - K) v_k on entry); classical
   // Gram-Schmidt with a second pass (reorth) or a single pass

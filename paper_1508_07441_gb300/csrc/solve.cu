@@ -325,6 +325,41 @@ __global__ void __launch_bounds__(V_THREADS) bdot_kernel(int rows, int B, int nv
   }
 }
 
+// partial[blk * B + e] = (sum over blk's rows of |x[row, e]|^2, 0): the norm
+// pass, one vector read once, four rows in flight per thread, squares summed
+// in the vector type per thread and in FP64 across the block
+template <typename T>
+__global__ void __launch_bounds__(V_THREADS) bnorm_kernel(int rows, int B, const typename Cx<T>::t *__restrict__ x,
+                                                          double2 *__restrict__ partial) {
+  __shared__ double red[V_THREADS];
+  const int EL = blockDim.x, RB = blockDim.y;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * EL + tx;
+  const int e = blockIdx.y * EL + tx;
+  const int stride = gridDim.x * RB;
+  T acc = T(0);
+  if (e < B) {
+    int r = blockIdx.x * RB + ty;
+    for (; r + 3 * stride < rows; r += 4 * stride) {
+      typename Cx<T>::t a[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = x[(size_t)(r + u * stride) * B + e];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc = fma(a[u].x, a[u].x, fma(a[u].y, a[u].y, acc));
+    }
+    for (; r < rows; r += stride) {
+      const auto a = x[(size_t)r * B + e];
+      acc = fma(a.x, a.x, fma(a.y, a.y, acc));
+    }
+  }
+  red[tid] = (double)acc;
+  __syncthreads();
+  for (int h = RB / 2; h > 0; h >>= 1) {
+    if (ty < h) red[tid] += red[(ty + h) * EL + tx];
+    __syncthreads();
+  }
+  if (ty == 0 && e < B) partial[(size_t)blockIdx.x * B + e] = make_double2(red[tx], 0.0);
+}
+
 // out[j * B + e] (+)= sum_blk partial[(j * nblk + blk) * B + e]; also, in
 // the vector precision T, coef = sign * (this pass's sum) for an axpy, and
 // for a norm pass (nv = 1) inv = 1 / sqrt(sum.x) (0 for a zero norm), so
@@ -948,7 +983,10 @@ struct Krylov {
   // nrm[e] = |x_e|^2 (and inv = 1 / |x_e| in T with scale)
   template <typename U>
   void norms(const typename Cx<U>::t *x, cudaStream_t s, bool scale = false) {
-    dots<U>(1, x, 0, x, nrm, 0, s, false, scale);
+    bnorm_kernel<U><<<dot_grid(), dot_block(), 0, s>>>((int)dim, B, x, partial);
+    breduce_kernel<T><<<breduce_blocks(B), 256, 0, s>>>(1, nblk, B, partial, nrm, 0, nullptr, -1.0,
+                                                      scale ? inv : nullptr);
+    count_launches(2);
   }
   // one Arnoldi step from column k (w holds (I - K) v_k on entry); classical
   // Gram-Schmidt with a second pass (reorth = true) or a single pass

@@ -7,18 +7,20 @@
 // K step; the lo*lo term is below FP32 resolution), which keeps about 21
 // significant bits in every product.
 //
-// One CTA computes RT row tiles of 128 rows (all of C's rows, N <= 512)
+// An output tile is RT row tiles of 128 rows (all of C's rows, N <= 512)
 // times 128 output columns, so X' is read once.  Per K chunk of 16:
 //   - A (constant per problem, packed once into the MMA operand layout as
 //     TF32 hi/lo blocks by tc_pack_kernel) arrives by one bulk async copy
 //     (cp.async.bulk, completion counted on an mbarrier);
-//   - the threads form X' (the G1 complex scaling fused in), split it into
-//     TF32 hi/lo and store it in the operand layout;
-//   - one thread issues the MMAs into TMEM accumulators (one 128 x BN
+//   - X' (the G1 complex scaling fused in) is formed, split into TF32 hi/lo
+//     and stored in the operand layout;
+//   - one thread issues the MMAs into TMEM accumulators (one 128 x 128
 //     accumulator per row tile) and commits them to the stage's mbarrier,
-//     which frees the stage for chunk + STAGES.
+//     which frees the stage.
 // The epilogue reads the accumulators with tcgen05.ld and writes C (or
-// S - C).  Shared-memory operands use the no-swizzle K-major layout: 8-row
+// S - C).  Aligned panels run in a persistent warp-specialised kernel (one
+// CTA per SM, rings of A, raw-panel and operand stages, double-buffered
+// accumulators); other panels in a one-tile-per-CTA kernel.  Shared-memory operands use the no-swizzle K-major layout: 8-row
 // groups of 512 B, each four 8 x 16 B core matrices along K (K-core stride
 // 128 B, row-group stride 512 B).  Every mbarrier wait has an iteration
 // limit; a wait that runs out sets the error word and the kernel still
@@ -44,18 +46,18 @@ constexpr uint32_t TC_A_BLOCK = 2 * TC_A_HALF;    // hi + lo: 16 KB
 constexpr uint32_t TC_KSTRIDE = 128;              // between core matrices along K
 constexpr uint32_t TC_RSTRIDE = 512;              // between 8-row groups
 constexpr int TC_MAX_STAGES = 3;
-constexpr int TC_MAX_RAW = 4;  // raw panel chunks in flight (bulk-copy path)
 constexpr long long TC_SPIN_LIMIT = 1LL << 22;
 
 struct TcParams {
-  int n, RT, nK, stages, raw_stages;
+  int n, RT, nK, stages;
   int64_t ncol;
-  uint32_t stage_bytes, raw_bytes, tmem_cols;
+  uint32_t stage_bytes, tmem_cols;
   const float *A;       // packed TF32 blocks [n_ch][nK][RT][hi | lo]
   const float2 *X, *G;  // [n_ch][n][ncol / 2] complex
   const float *S;       // epilogue S - C (SUB)
   float *C;
   int *err;
+  int vec_out;          // C (and S) rows 16-byte aligned: float4 epilogue
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -163,14 +165,13 @@ __global__ void tc_pack_kernel(int n_ch, int n, int RT, int nK, const double *__
   }
 }
 
-// RAW: the X (and G1) panel rows arrive by bulk async copies into a ring of
-// raw chunks in shared memory, issued TC_MAX_RAW chunks ahead by one
-// thread; otherwise each thread prefetches the next chunk into registers
-template <int BN, bool SCALE_G, bool SUB, bool RAW>
+// Panels that are not 16-byte aligned (the persistent kernel below takes
+// the aligned ones): one CTA per 128-column tile, every thread converts
+// chunk c while it holds the raw values of chunk c + 1 in registers
+template <int BN, bool SCALE_G, bool SUB>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcParams p) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar_a[TC_MAX_STAGES], bar_mma[TC_MAX_STAGES], bar_done;
-  __shared__ __align__(8) uint64_t bar_raw[TC_MAX_RAW];
   __shared__ uint32_t tmem_holder;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ch = blockIdx.z;
@@ -184,8 +185,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcParams p) {
       mbar_init(&bar_mma[s], 1);
     }
     mbar_init(&bar_done, 1);
-    if (RAW)
-      for (int r = 0; r < p.raw_stages; ++r) mbar_init(&bar_raw[r], 1);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 0) {
@@ -208,8 +207,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcParams p) {
   // (4 rows); consecutive lanes take consecutive nn, so each store
   // instruction of a warp fills 512 contiguous bytes.
   constexpr int ITEMS = (TC_KC / 4) * BN / TC_THREADS;
-  // register path: the raw values of chunk c + 1 are loaded while chunk c
-  // is converted
+  // the raw values of chunk c + 1 are loaded while chunk c is converted
   auto load_chunk = [&](int c, float2 (&xv)[ITEMS][4], float2 (&gv)[ITEMS][4]) {
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) {
@@ -226,43 +224,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcParams p) {
       }
     }
   };
-  // bulk-copy path: raw chunk c (rows of X, then of G1; BN floats each,
-  // the valid columns only) into ring slot c % raw_stages
-  unsigned char *raw0 = smem + (size_t)NS * p.stage_bytes;
-  const int valid_cols = (int)min((int64_t)BN, ncol - col0);  // a multiple of 4 on this path
-  auto issue_raw = [&](int c) {
-    const int r = c % p.raw_stages;
-    unsigned char *dst = raw0 + (size_t)r * p.raw_bytes;
-    const int rows = min(TC_KC, n - c * TC_KC);
-    const uint32_t row_bytes = (uint32_t)valid_cols * 4;
-    const uint32_t total = (uint32_t)rows * row_bytes * (SCALE_G ? 2u : 1u);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar_raw[r])),
-                 "r"(total)
-                 : "memory");
-    for (int k = 0; k < rows; ++k) {
-      const float *src = reinterpret_cast<const float *>(X) + (size_t)(c * TC_KC + k) * ncol + col0;
-      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                       smem_u32(dst + (size_t)k * BN * 4)),
-                   "l"(src), "r"(row_bytes), "r"(smem_u32(&bar_raw[r]))
-                   : "memory");
-      if (SCALE_G) {
-        const float *gsrc = reinterpret_cast<const float *>(G) + (size_t)(c * TC_KC + k) * ncol + col0;
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                smem_u32(dst + (size_t)(TC_KC + k) * BN * 4)),
-            "l"(gsrc), "r"(row_bytes), "r"(smem_u32(&bar_raw[r]))
-            : "memory");
-      }
-    }
-  };
-  int a_last = -1, raw_last = -1;  // thread 0: last chunks whose copies it saw complete
+  int a_last = -1;  // thread 0: last chunk whose A copy it saw complete
   float2 xv[ITEMS][4], gv[ITEMS][4];
-  if (RAW) {
-    if (tid == 0)
-      for (int c = 0; c < min(p.raw_stages, nK); ++c) issue_raw(c);
-  } else {
-    load_chunk(0, xv, gv);
-  }
+  load_chunk(0, xv, gv);
   for (int c = 0; c < nK; ++c) {
     const int s = c % NS;
     const uint32_t use = (uint32_t)(c / NS);
@@ -280,26 +244,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcParams p) {
                    : "memory");
     }
     float2 xn[ITEMS][4], gn[ITEMS][4];
-    if (RAW) {
-      const int r = c % p.raw_stages;
-      if (ok) ok = mbar_wait(&bar_raw[r], (uint32_t)(c / p.raw_stages) & 1);
-      if (ok) raw_last = c;
-      const float2 *rx = reinterpret_cast<const float2 *>(raw0 + (size_t)r * p.raw_bytes);
-      const float2 *rg = rx + TC_KC * BN / 2;
-#pragma unroll
-      for (int it = 0; it < ITEMS; ++it) {
-        const int item = tid + it * TC_THREADS;
-        const int nn = item % BN, kg = item / BN;
-        const bool col_in = nn < valid_cols;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int kl = kg * 4 + q;
-          const bool in = col_in && c * TC_KC + kl < n;
-          xv[it][q] = in ? rx[kl * (BN / 2) + (nn >> 1)] : make_float2(0.f, 0.f);
-          if (SCALE_G) gv[it][q] = in ? rg[kl * (BN / 2) + (nn >> 1)] : make_float2(0.f, 0.f);
-        }
-      }
-    } else if (c + 1 < nK) {
+    if (c + 1 < nK) {
       load_chunk(c + 1, xn, gn);
     }
     unsigned char *bhi = st + (size_t)RT * TC_A_BLOCK, *blo = bhi + b_half;
@@ -332,7 +277,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcParams p) {
       *reinterpret_cast<uint4 *>(bhi + off) = h;
       *reinterpret_cast<uint4 *>(blo + off) = l;
     }
-    if (!RAW && c + 1 < nK) {
+    if (c + 1 < nK) {
 #pragma unroll
       for (int it = 0; it < ITEMS; ++it)
 #pragma unroll
@@ -347,8 +292,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcParams p) {
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
-      // every thread has read raw slot c % raw_stages: refill it
-      if (RAW && c + p.raw_stages < nK) issue_raw(c + p.raw_stages);
       if (ok) ok = mbar_wait(&bar_a[s], use & 1);
       if (ok) a_last = c;
       const uint32_t a0 = smem_u32(st), b0 = smem_u32(bhi);
@@ -373,9 +316,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcParams p) {
     // after a wait ran out, still wait (bounded) for the copies this CTA
     // issued, so that none lands in shared memory after the CTA has gone
     for (int c = a_last + 1; c < nK; ++c) mbar_wait(&bar_a[c % NS], (uint32_t)(c / NS) & 1);
-    if (RAW)
-      for (int c = raw_last + 1; c < nK; ++c)
-        mbar_wait(&bar_raw[c % p.raw_stages], (uint32_t)(c / p.raw_stages) & 1);
     tc_commit(&bar_done);
   }
   // always wait (bounded) for the MMAs before TMEM is read or freed
@@ -386,7 +326,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcParams p) {
   const int lg = warp & 3, half = warp >> 2;
   // a thread's 16 columns of one row go out as four 16-byte stores when the
   // row start is 16-byte aligned (ncol a multiple of 4) and all 16 exist
-  const bool vec_out = ncol % 4 == 0;
+  const bool vec_out = p.vec_out != 0;
   for (int rt = 0; rt < RT; ++rt) {
     const int row = rt * TC_M + lg * 32 + lane;
     for (int cb = half * (BN / 2); cb < (half + 1) * (BN / 2); cb += 16) {
@@ -423,15 +363,362 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcParams p) {
   if (!ok && lane == 0) atomicOr(p.err, 1);
 }
 
+// ---------------------------------------------------------------------------
+// Persistent warp-specialised version for 16-byte aligned panels: one CTA
+// per SM walks the (channel, 128-column) output tiles; its warps take fixed
+// roles and hand work over through mbarrier rings, so that copies, format
+// conversion, MMAs and the epilogue of different chunks and tiles overlap:
+//   warp 0      producer: bulk async copies of the packed A chunks (ring of
+//               nsa stages) and of the raw X / G1 panel rows (ring of nr)
+//   warp 1      MMA issuer (one thread) and TMEM owner: 3 TF32 MMAs per
+//               K step and row tile; commits free the A and B stages and,
+//               after a tile's last chunk, hand the accumulator to the
+//               epilogue
+//   warps 2-5   converters: raw chunk -> G1 o X -> TF32 hi/lo in the
+//               operand layout (ring of nsb B stages)
+//   warps 6-9   epilogue: TMEM -> registers -> C (or S - C); warp w reads
+//               TMEM lanes 32 (w % 4) .. +31
+// The accumulators are double-buffered in TMEM when 2 RT 128 columns fit
+// (N <= 256), so the epilogue of tile i overlaps the MMAs of tile i + 1.
+// Every wait is bounded and also gives up once another role has set the
+// CTA's abort flag; before the CTA exits, the producer waits (bounded) for
+// every copy it issued and the MMA thread for every MMA it issued.
+// ---------------------------------------------------------------------------
+constexpr int WS_THREADS = 320;
+constexpr int WS_MAX_A = 3, WS_MAX_B = 3, WS_MAX_R = 8;
+constexpr int WS_BN = 128;
+constexpr uint32_t WS_B_HALF = WS_BN * TC_KC * 4;  // one TF32 part of a B stage: 8 KB
+constexpr uint32_t WS_B_STAGE = 2 * WS_B_HALF;
+constexpr int WS_CONV = 128;                       // converter threads
+
+struct TcWsParams {
+  int n, RT, nK, n_cb, n_tiles, nsa, nsb, nr, n_acc;
+  int64_t ncol;
+  uint32_t raw_bytes, tmem_cols;
+  const float *A;
+  const float2 *X, *G;
+  const float *S;
+  float *C;
+  int *err;
+};
+
+struct WsBars {
+  uint64_t a_full[WS_MAX_A], a_empty[WS_MAX_A], b_full[WS_MAX_B], b_empty[WS_MAX_B];
+  uint64_t r_full[WS_MAX_R], r_empty[WS_MAX_R], t_full[2], t_empty[2], fin;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// bounded wait that also ends when another role has aborted; running out
+// of the limit aborts the CTA and sets the error word
+__device__ __forceinline__ bool ws_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *err) {
+  for (long long i = 0; i < TC_SPIN_LIMIT; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort_flag) return false;
+  }
+  *abort_flag = 1;
+  atomicOr(err, 1);
+  return false;
+}
+
+template <bool SCALE_G, bool SUB>
+__global__ void __launch_bounds__(WS_THREADS, 1) tc_gemm_ws_kernel(TcWsParams p) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) WsBars bars;
+  __shared__ uint32_t tmem_holder;
+  __shared__ volatile int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n = p.n, RT = p.RT, nK = p.nK;
+  const int64_t ncol = p.ncol;
+  unsigned char *a_ring = smem;
+  unsigned char *b_ring = smem + (size_t)p.nsa * RT * TC_A_BLOCK;
+  unsigned char *r_ring = b_ring + (size_t)p.nsb * WS_B_STAGE;
+  const int my_tiles = (p.n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+
+  if (tid == 0) {
+    for (int i = 0; i < p.nsa; ++i) {
+      mbar_init(&bars.a_full[i], 1);
+      mbar_init(&bars.a_empty[i], 1);
+    }
+    for (int i = 0; i < p.nsb; ++i) {
+      mbar_init(&bars.b_full[i], WS_CONV);
+      mbar_init(&bars.b_empty[i], 1);
+    }
+    for (int i = 0; i < p.nr; ++i) {
+      mbar_init(&bars.r_full[i], 1);
+      mbar_init(&bars.r_empty[i], WS_CONV);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bars.t_full[i], 1);
+      mbar_init(&bars.t_empty[i], WS_CONV);
+    }
+    mbar_init(&bars.fin, 1);
+    abort_flag = 0;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
+                 "r"(p.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_holder;
+
+  if (warp == 0) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      int last_a[WS_MAX_A], last_r[WS_MAX_R];
+      for (int i = 0; i < WS_MAX_A; ++i) last_a[i] = -1;
+      for (int i = 0; i < WS_MAX_R; ++i) last_r[i] = -1;
+      bool ok = true;
+      int q = 0;
+      for (int lt = 0; lt < my_tiles && ok; ++lt) {
+        const int t = (int)blockIdx.x + lt * (int)gridDim.x;
+        const int ch = t / p.n_cb;
+        const int64_t col0 = (int64_t)(t % p.n_cb) * WS_BN;
+        const uint32_t row_bytes = (uint32_t)min((int64_t)WS_BN, ncol - col0) * 4;  // a multiple of 16
+        const float *Xc = reinterpret_cast<const float *>(p.X) + (size_t)ch * n * ncol + col0;
+        const float *Gc = SCALE_G ? reinterpret_cast<const float *>(p.G) + (size_t)ch * n * ncol + col0 : nullptr;
+        for (int c = 0; c < nK; ++c, ++q) {
+          const int sr = q % p.nr;
+          if (q >= p.nr && !(ok = ws_wait(&bars.r_empty[sr], (uint32_t)(q / p.nr - 1) & 1, &abort_flag, p.err)))
+            break;
+          const int rows = min(TC_KC, n - c * TC_KC);
+          unsigned char *dst = r_ring + (size_t)sr * p.raw_bytes;
+          expect_tx(&bars.r_full[sr], (uint32_t)rows * row_bytes * (SCALE_G ? 2u : 1u));
+          for (int k = 0; k < rows; ++k) {
+            const size_t ro = (size_t)(c * TC_KC + k) * ncol;
+            bulk_g2s(dst + (size_t)k * WS_BN * 4, Xc + ro, row_bytes, &bars.r_full[sr]);
+            if (SCALE_G) bulk_g2s(dst + (size_t)(TC_KC + k) * WS_BN * 4, Gc + ro, row_bytes, &bars.r_full[sr]);
+          }
+          last_r[sr] = q;
+          const int sa = q % p.nsa;
+          if (q >= p.nsa && !(ok = ws_wait(&bars.a_empty[sa], (uint32_t)(q / p.nsa - 1) & 1, &abort_flag, p.err)))
+            break;
+          const uint32_t abytes = (uint32_t)RT * TC_A_BLOCK;
+          expect_tx(&bars.a_full[sa], abytes);
+          bulk_g2s(a_ring + (size_t)sa * abytes, p.A + ((size_t)ch * nK + c) * RT * (TC_A_BLOCK / 4), abytes,
+                   &bars.a_full[sa]);
+          last_a[sa] = q;
+        }
+      }
+      // every issued copy lands before the CTA exits
+      for (int i = 0; i < p.nsa; ++i)
+        if (last_a[i] >= 0) mbar_wait(&bars.a_full[i], (uint32_t)(last_a[i] / p.nsa) & 1);
+      for (int i = 0; i < p.nr; ++i)
+        if (last_r[i] >= 0) mbar_wait(&bars.r_full[i], (uint32_t)(last_r[i] / p.nr) & 1);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = tc_idesc(WS_BN);
+      bool ok = true;
+      int q = 0;
+      for (int lt = 0; lt < my_tiles && ok; ++lt) {
+        const int buf = lt % p.n_acc;
+        if (lt >= p.n_acc && !(ok = ws_wait(&bars.t_empty[buf], (uint32_t)(lt / p.n_acc - 1) & 1, &abort_flag, p.err)))
+          break;
+        tc_fence_after();
+        const uint32_t d0 = tmem + (uint32_t)(buf * RT * WS_BN);
+        for (int c = 0; c < nK; ++c, ++q) {
+          const int sa = q % p.nsa, sb = q % p.nsb;
+          if (!(ok = ws_wait(&bars.a_full[sa], (uint32_t)(q / p.nsa) & 1, &abort_flag, p.err))) break;
+          if (!(ok = ws_wait(&bars.b_full[sb], (uint32_t)(q / p.nsb) & 1, &abort_flag, p.err))) break;
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(a_ring + (size_t)sa * RT * TC_A_BLOCK);
+          const uint32_t b0 = smem_u32(b_ring + (size_t)sb * WS_B_STAGE);
+#pragma unroll 1
+          for (int rt = 0; rt < RT; ++rt) {
+            const uint32_t d = d0 + (uint32_t)(rt * WS_BN);
+#pragma unroll
+            for (int ks = 0; ks < TC_KC / 8; ++ks) {
+              const uint32_t ko = (uint32_t)ks * 2 * TC_KSTRIDE;
+              const uint64_t ahi = umma_desc(a0 + rt * TC_A_BLOCK + ko);
+              const uint64_t alo = umma_desc(a0 + rt * TC_A_BLOCK + TC_A_HALF + ko);
+              const uint64_t bh = umma_desc(b0 + ko), bl = umma_desc(b0 + WS_B_HALF + ko);
+              tc_mma(d, ahi, bh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+              tc_mma(d, ahi, bl, idesc, 1u);
+              tc_mma(d, alo, bh, idesc, 1u);
+            }
+          }
+          tc_commit(&bars.a_empty[sa]);
+          tc_commit(&bars.b_empty[sb]);
+        }
+        if (ok) tc_commit(&bars.t_full[buf]);
+      }
+      // every issued MMA completes before TMEM is freed
+      tc_commit(&bars.fin);
+      mbar_wait(&bars.fin, 0);
+    }
+  } else if (warp < 6) {
+    // ---------------- converters ----------------
+    const int ct = tid - 64;
+    constexpr int ITEMS = (TC_KC / 4) * WS_BN / WS_CONV;
+    bool ok = true;
+    int q = 0;
+    for (int lt = 0; lt < my_tiles && ok; ++lt) {
+      const int t = (int)blockIdx.x + lt * (int)gridDim.x;
+      const int64_t col0 = (int64_t)(t % p.n_cb) * WS_BN;
+      const int valid_cols = (int)min((int64_t)WS_BN, ncol - col0);
+      for (int c = 0; c < nK; ++c, ++q) {
+        const int sr = q % p.nr, sb = q % p.nsb;
+        if (!(ok = ws_wait(&bars.r_full[sr], (uint32_t)(q / p.nr) & 1, &abort_flag, p.err))) break;
+        const float2 *rx = reinterpret_cast<const float2 *>(r_ring + (size_t)sr * p.raw_bytes);
+        const float2 *rg = rx + TC_KC * WS_BN / 2;
+        float2 xv[ITEMS][4], gv[ITEMS][4];
+#pragma unroll
+        for (int it = 0; it < ITEMS; ++it) {
+          const int item = ct + it * WS_CONV;
+          const int nn = item % WS_BN, kg = item / WS_BN;
+          const bool col_in = nn < valid_cols;
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) {
+            const int kl = kg * 4 + qq;
+            const bool in = col_in && c * TC_KC + kl < n;
+            xv[it][qq] = in ? rx[kl * (WS_BN / 2) + (nn >> 1)] : make_float2(0.f, 0.f);
+            if (SCALE_G) gv[it][qq] = in ? rg[kl * (WS_BN / 2) + (nn >> 1)] : make_float2(0.f, 0.f);
+          }
+        }
+        mbar_arrive(&bars.r_empty[sr]);
+        if (q >= p.nsb && !(ok = ws_wait(&bars.b_empty[sb], (uint32_t)(q / p.nsb - 1) & 1, &abort_flag, p.err)))
+          break;
+        unsigned char *bhi = b_ring + (size_t)sb * WS_B_STAGE, *blo = bhi + WS_B_HALF;
+#pragma unroll
+        for (int it = 0; it < ITEMS; ++it) {
+          const int item = ct + it * WS_CONV;
+          const int nn = item % WS_BN, kg = item / WS_BN;
+          const bool odd = ((col0 + nn) & 1) != 0;
+          float v[4];
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) {
+            const float2 x = xv[it][qq];
+            if (SCALE_G) {
+              const float2 g = gv[it][qq];
+              v[qq] = odd ? (g.x * x.y + g.y * x.x) : (g.x * x.x - g.y * x.y);
+            } else {
+              v[qq] = odd ? x.y : x.x;
+            }
+          }
+          uint4 h, l;
+          h.x = to_tf32(v[0]);
+          h.y = to_tf32(v[1]);
+          h.z = to_tf32(v[2]);
+          h.w = to_tf32(v[3]);
+          l.x = to_tf32(v[0] - __uint_as_float(h.x));
+          l.y = to_tf32(v[1] - __uint_as_float(h.y));
+          l.z = to_tf32(v[2] - __uint_as_float(h.z));
+          l.w = to_tf32(v[3] - __uint_as_float(h.w));
+          const uint32_t off = tc_off(nn, kg * 4);
+          *reinterpret_cast<uint4 *>(bhi + off) = h;
+          *reinterpret_cast<uint4 *>(blo + off) = l;
+        }
+        // generic-proxy stores -> visible to the tensor core (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&bars.b_full[sb]);
+      }
+    }
+  } else {
+    // ---------------- epilogue ----------------
+    const int lg = warp & 3;
+    bool ok = true;
+    for (int lt = 0; lt < my_tiles && ok; ++lt) {
+      const int t = (int)blockIdx.x + lt * (int)gridDim.x;
+      const int ch = t / p.n_cb;
+      const int64_t col0 = (int64_t)(t % p.n_cb) * WS_BN;
+      const int buf = lt % p.n_acc;
+      ok = ws_wait(&bars.t_full[buf], (uint32_t)(lt / p.n_acc) & 1, &abort_flag, p.err);
+      // the TMEM loads below are warp-collective: the warp decides together
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      tc_fence_after();
+      for (int rt = 0; rt < RT; ++rt) {
+        const int row = rt * TC_M + lg * 32 + lane;
+        for (int cb = 0; cb < WS_BN; cb += 16) {
+          const size_t o = ((size_t)ch * n + min(row, n - 1)) * ncol + col0 + cb;
+          // ncol % 4 == 0 and 16-byte aligned C and S on this path
+          const bool full = col0 + cb + 16 <= ncol;
+          float4 sv[4];
+          if (SUB && full && row < n)  // the S loads go out before the TMEM read
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) sv[qq] = *reinterpret_cast<const float4 *>(p.S + o + 4 * qq);
+          float v[16];
+          __syncwarp();  // the TMEM load is warp-collective
+          tc_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(buf * RT * WS_BN + rt * WS_BN + cb), v);
+          if (row < n) {
+            if (full) {
+#pragma unroll
+              for (int qq = 0; qq < 4; ++qq) {
+                float4 w = make_float4(v[4 * qq], v[4 * qq + 1], v[4 * qq + 2], v[4 * qq + 3]);
+                if (SUB) w = make_float4(sv[qq].x - w.x, sv[qq].y - w.y, sv[qq].z - w.z, sv[qq].w - w.w);
+                *reinterpret_cast<float4 *>(p.C + o + 4 * qq) = w;
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                if (col0 + cb + j < ncol) p.C[o + j] = SUB ? p.S[o + j] - v[j] : v[j];
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&bars.t_empty[buf]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols) : "memory");
+  }
+}
+
+struct TcWsShape {
+  int nsa, nsb, nr, n_acc;
+  uint32_t raw_bytes, smem, tmem_cols;
+};
+
+// rings for the persistent kernel: A stages (RT 16 KB blocks each), three
+// B stages of 16 KB, as many raw panel chunks as fit in 216 KB (at most 8);
+// two accumulator buffers when they fit in the 512 TMEM columns
+TcWsShape tc_ws_shape(int RT, bool scale_g) {
+  TcWsShape w{};
+  w.raw_bytes = (uint32_t)TC_KC * WS_BN * 4 * (scale_g ? 2u : 1u);
+  w.nsa = RT <= 2 ? 3 : 2;
+  w.nsb = WS_MAX_B;
+  const uint32_t used = (uint32_t)w.nsa * RT * TC_A_BLOCK + (uint32_t)w.nsb * WS_B_STAGE;
+  w.nr = (int)std::min<uint32_t>(WS_MAX_R, (216u * 1024 - used) / w.raw_bytes);
+  w.smem = used + (uint32_t)w.nr * w.raw_bytes;
+  w.n_acc = 2 * RT * WS_BN <= 512 ? 2 : 1;
+  const int cols = w.n_acc * RT * WS_BN;
+  w.tmem_cols = 32;
+  while ((int)w.tmem_cols < cols) w.tmem_cols <<= 1;
+  return w;
+}
+
 struct TcShape {
-  int RT, BN, nK, stages, raw_stages;
-  uint32_t stage_bytes, raw_bytes, tmem_cols;
+  int RT, BN, nK, stages;
+  uint32_t stage_bytes, tmem_cols;
 };
 
 // 128 output columns per CTA, all N rows (RT tiles of 128); operand stages
 // of one K chunk (A hi/lo for every row tile, the panel's hi/lo), two or
-// three of them, then a ring of raw panel chunks (rows of X and G1) for
-// the bulk-copy path: at most 192 KB, one CTA per SM
+// three of them: at most 192 KB, one CTA per SM
 TcShape tc_shape(int n) {
   TcShape sh{};
   sh.RT = (n + TC_M - 1) / TC_M;
@@ -439,8 +726,6 @@ TcShape tc_shape(int n) {
   sh.nK = (n + TC_KC - 1) / TC_KC;
   sh.stage_bytes = (uint32_t)sh.RT * TC_A_BLOCK + 2u * (uint32_t)sh.BN * TC_KC * 4;
   sh.stages = 3 * sh.stage_bytes <= 96u * 1024 ? 3 : 2;
-  sh.raw_bytes = 2u * TC_KC * sh.BN * 4;
-  sh.raw_stages = sh.stages * sh.stage_bytes + TC_MAX_RAW * sh.raw_bytes <= 192u * 1024 ? TC_MAX_RAW : 2;
   const int cols = sh.RT * sh.BN;
   sh.tmem_cols = 32;
   while ((int)sh.tmem_cols < cols) sh.tmem_cols <<= 1;
@@ -448,6 +733,10 @@ TcShape tc_shape(int n) {
 }
 
 }  // namespace
+
+// per device: kernel attributes set, SM count (the persistent grid)
+bool attr_set[64] = {};
+int sm_count[64] = {};
 
 bool tc_supported(const wpcd_problem *pr) { return pr->N >= 1 && pr->N <= 4 * TC_M; }
 
@@ -473,24 +762,25 @@ wpcd_status tc_prepare(wpcd_problem *pr, cudaStream_t s) {
   tc_pack_kernel<<<grid_for(total, 256), 256, 0, s>>>(pr->n_ch, pr->N, sh.RT, sh.nK, pr->d.Vt, pr->d.Vt_tc);
   count_launches(2);
   // the shared-memory limit is an attribute of the kernel on each device
-  static bool attr_set[64] = {};
   if (pr->device < 0 || pr->device >= 64) return set_error(WPCD_EINVAL, "device ordinal out of range");
   if (!attr_set[pr->device]) {
     // the largest stage set of any shape (tc_shape: at most 192 KB); the
     // static barriers and the TMEM address take part of the rest
     const int max_bytes = 192 * 1024;
-    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<128, true, false, false>,
+    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<128, true, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes));
-    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<128, false, false, false>,
+    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<128, false, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes));
-    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<128, false, true, false>,
+    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<128, false, true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes));
-    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<128, true, false, true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes));
-    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<128, false, false, true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes));
-    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<128, false, true, true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes));
+    const int ws_bytes = 216 * 1024;  // tc_ws_shape: at most 216 KB
+    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_ws_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       ws_bytes));
+    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_ws_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       ws_bytes));
+    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_ws_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       ws_bytes));
+    WPCD_CUDA_TRY(cudaDeviceGetAttribute(&sm_count[pr->device], cudaDevAttrMultiProcessorCount, pr->device));
     attr_set[pr->device] = true;
   }
   cudaError_t e = cudaGetLastError();
@@ -517,28 +807,51 @@ wpcd_status tc_gemm(const wpcd_problem *pr, bool use_O, const float *G, const fl
   p.S = S;
   p.C = C;
   p.err = pr->d.tc_err;
-  p.raw_stages = sh.raw_stages;
-  p.raw_bytes = sh.raw_bytes;
+  auto aligned16 = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+  // 16-byte aligned C and S rows: float4 epilogue stores and loads
+  const bool vec_out = ncol % 4 == 0 && aligned16(C) && (!S || aligned16(S));
   // bulk copies need 16-byte aligned panel rows: ncol a multiple of 4 and
   // aligned bases (every row, and every column tile, then starts aligned)
-  const bool raw = ncol % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
-                   (!G || (reinterpret_cast<uintptr_t>(G) & 15) == 0);
-  const size_t smem = (size_t)sh.stages * sh.stage_bytes + (raw ? (size_t)sh.raw_stages * sh.raw_bytes : 0);
-  dim3 grid((unsigned)((ncol + sh.BN - 1) / sh.BN), 1, pr->n_ch);
-#define WPCD_TC_LAUNCH(RAW)                                                 \
-  do {                                                                      \
-    if (G)                                                                  \
-      tc_gemm_kernel<128, true, false, RAW><<<grid, TC_THREADS, smem, s>>>(p);  \
-    else if (S)                                                             \
-      tc_gemm_kernel<128, false, true, RAW><<<grid, TC_THREADS, smem, s>>>(p);  \
-    else                                                                    \
-      tc_gemm_kernel<128, false, false, RAW><<<grid, TC_THREADS, smem, s>>>(p); \
-  } while (0)
-  if (raw)
-    WPCD_TC_LAUNCH(true);
-  else
-    WPCD_TC_LAUNCH(false);
-#undef WPCD_TC_LAUNCH
+  const bool raw = vec_out && aligned16(X) && (!G || aligned16(G));
+  if (raw) {
+    const TcWsShape w = tc_ws_shape(sh.RT, G != nullptr);
+    TcWsParams q{};
+    q.n = pr->N;
+    q.RT = sh.RT;
+    q.nK = sh.nK;
+    q.n_cb = (int)((ncol + WS_BN - 1) / WS_BN);
+    q.n_tiles = pr->n_ch * q.n_cb;
+    q.nsa = w.nsa;
+    q.nsb = w.nsb;
+    q.nr = w.nr;
+    q.n_acc = w.n_acc;
+    q.ncol = ncol;
+    q.raw_bytes = w.raw_bytes;
+    q.tmem_cols = w.tmem_cols;
+    q.A = p.A;
+    q.X = p.X;
+    q.G = p.G;
+    q.S = S;
+    q.C = C;
+    q.err = p.err;
+    const int grid = std::max(1, std::min(q.n_tiles, sm_count[pr->device] > 0 ? sm_count[pr->device] : 152));
+    if (G)
+      tc_gemm_ws_kernel<true, false><<<grid, WS_THREADS, w.smem, s>>>(q);
+    else if (S)
+      tc_gemm_ws_kernel<false, true><<<grid, WS_THREADS, w.smem, s>>>(q);
+    else
+      tc_gemm_ws_kernel<false, false><<<grid, WS_THREADS, w.smem, s>>>(q);
+  } else {
+    p.vec_out = vec_out;
+    const size_t smem = (size_t)sh.stages * sh.stage_bytes;
+    dim3 grid((unsigned)((ncol + sh.BN - 1) / sh.BN), 1, pr->n_ch);
+    if (G)
+      tc_gemm_kernel<128, true, false><<<grid, TC_THREADS, smem, s>>>(p);
+    else if (S)
+      tc_gemm_kernel<128, false, true><<<grid, TC_THREADS, smem, s>>>(p);
+    else
+      tc_gemm_kernel<128, false, false><<<grid, TC_THREADS, smem, s>>>(p);
+  }
   count_launches(1);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? WPCD_OK : cuda_error(e, "tensor-core gemm launch");
