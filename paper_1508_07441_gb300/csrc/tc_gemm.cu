@@ -25,12 +25,15 @@
 // 128 B, row-group stride 512 B).  Every mbarrier wait has an iteration
 // limit; a wait that runs out sets the error word and the kernel still
 // waits (bounded) for its MMAs before it frees TMEM and returns.
+#include <cuda.h>  // CUtensorMap (encoded through the runtime's driver entry point)
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 #include "wpcd_internal.h"
@@ -369,7 +372,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcParams p) {
 // roles and hand work over through mbarrier rings, so that copies, format
 // conversion, MMAs and the epilogue of different chunks and tiles overlap:
 //   warp 0      producer: bulk async copies of the packed A chunks (ring of
-//               nsa stages) and of the raw X / G1 panel rows (ring of nr)
+//               nsa stages) and tensor (TMA) copies of the raw X / G1 panel
+//               chunks, one 16-row x 128-column box each (ring of nr)
 //   warp 1      MMA issuer (one thread) and TMEM owner: 3 TF32 MMAs per
 //               K step and row tile; commits free the A and B stages and,
 //               after a tile's last chunk, hand the accumulator to the
@@ -390,13 +394,13 @@ constexpr int WS_BN = 128;
 constexpr uint32_t WS_B_HALF = WS_BN * TC_KC * 4;  // one TF32 part of a B stage: 8 KB
 constexpr uint32_t WS_B_STAGE = 2 * WS_B_HALF;
 constexpr int WS_CONV = 128;                       // converter threads
+constexpr int WS_EPI = 128;                        // epilogue threads
 
 struct TcWsParams {
   int n, RT, nK, n_cb, n_tiles, nsa, nsb, nr, n_acc;
   int64_t ncol;
   uint32_t raw_bytes, tmem_cols;
   const float *A;
-  const float2 *X, *G;
   const float *S;
   float *C;
   int *err;
@@ -418,6 +422,16 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                : "memory");
 }
 
+// one 2-D box of a tensor map at (x = column, y = row) into shared memory;
+// x is a multiple of 128 floats (512 bytes), rows past the end read zeros
+__device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ void expect_tx(uint64_t *bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
@@ -434,8 +448,10 @@ __device__ __forceinline__ bool ws_wait(uint64_t *bar, uint32_t parity, volatile
   return false;
 }
 
+// tmx, tmg: tensor maps of X and G1 as [n_ch n rows][ncol floats], box 16 x 128
 template <bool SCALE_G, bool SUB>
-__global__ void __launch_bounds__(WS_THREADS, 1) tc_gemm_ws_kernel(TcWsParams p) {
+__global__ void __launch_bounds__(WS_THREADS, 1)
+    tc_gemm_ws_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmg, TcWsParams p) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) WsBars bars;
   __shared__ uint32_t tmem_holder;
@@ -463,7 +479,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_gemm_ws_kernel(TcWsParams p)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&bars.t_full[i], 1);
-      mbar_init(&bars.t_empty[i], WS_CONV);
+      mbar_init(&bars.t_empty[i], WS_EPI);
     }
     mbar_init(&bars.fin, 1);
     abort_flag = 0;
@@ -491,22 +507,17 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_gemm_ws_kernel(TcWsParams p)
       for (int lt = 0; lt < my_tiles && ok; ++lt) {
         const int t = (int)blockIdx.x + lt * (int)gridDim.x;
         const int ch = t / p.n_cb;
-        const int64_t col0 = (int64_t)(t % p.n_cb) * WS_BN;
-        const uint32_t row_bytes = (uint32_t)min((int64_t)WS_BN, ncol - col0) * 4;  // a multiple of 16
-        const float *Xc = reinterpret_cast<const float *>(p.X) + (size_t)ch * n * ncol + col0;
-        const float *Gc = SCALE_G ? reinterpret_cast<const float *>(p.G) + (size_t)ch * n * ncol + col0 : nullptr;
+        const int col0 = (t % p.n_cb) * WS_BN;
         for (int c = 0; c < nK; ++c, ++q) {
           const int sr = q % p.nr;
           if (q >= p.nr && !(ok = ws_wait(&bars.r_empty[sr], (uint32_t)(q / p.nr - 1) & 1, &abort_flag, p.err)))
             break;
-          const int rows = min(TC_KC, n - c * TC_KC);
+          // the whole box counts, zero-filled parts included; rows of the
+          // next channel that a last chunk reaches are masked by the converters
           unsigned char *dst = r_ring + (size_t)sr * p.raw_bytes;
-          expect_tx(&bars.r_full[sr], (uint32_t)rows * row_bytes * (SCALE_G ? 2u : 1u));
-          for (int k = 0; k < rows; ++k) {
-            const size_t ro = (size_t)(c * TC_KC + k) * ncol;
-            bulk_g2s(dst + (size_t)k * WS_BN * 4, Xc + ro, row_bytes, &bars.r_full[sr]);
-            if (SCALE_G) bulk_g2s(dst + (size_t)(TC_KC + k) * WS_BN * 4, Gc + ro, row_bytes, &bars.r_full[sr]);
-          }
+          expect_tx(&bars.r_full[sr], TC_KC * WS_BN * 4 * (SCALE_G ? 2u : 1u));
+          tma_2d(dst, &tmx, col0, ch * n + c * TC_KC, &bars.r_full[sr]);
+          if (SCALE_G) tma_2d(dst + TC_KC * WS_BN * 4, &tmg, col0, ch * n + c * TC_KC, &bars.r_full[sr]);
           last_r[sr] = q;
           const int sa = q % p.nsa;
           if (q >= p.nsa && !(ok = ws_wait(&bars.a_empty[sa], (uint32_t)(q / p.nsa - 1) & 1, &abort_flag, p.err)))
@@ -734,6 +745,35 @@ TcShape tc_shape(int n) {
 
 }  // namespace
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  return fn;
+}
+
+// [rows][ncol] FP32 panel, 16 x 128 boxes, zero fill outside
+bool panel_map(CUtensorMap *m, const float *base, int64_t rows, int64_t ncol) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)ncol, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ncol * 4};
+  const cuuint32_t box[2] = {WS_BN, TC_KC};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // per device: kernel attributes set, SM count (the persistent grid)
 bool attr_set[64] = {};
 int sm_count[64] = {};
@@ -829,18 +869,20 @@ wpcd_status tc_gemm(const wpcd_problem *pr, bool use_O, const float *G, const fl
     q.raw_bytes = w.raw_bytes;
     q.tmem_cols = w.tmem_cols;
     q.A = p.A;
-    q.X = p.X;
-    q.G = p.G;
     q.S = S;
     q.C = C;
     q.err = p.err;
+    CUtensorMap tmx{}, tmg{};
+    const int64_t rows = (int64_t)pr->n_ch * pr->N;
+    if (!panel_map(&tmx, X, rows, ncol) || (G && !panel_map(&tmg, G, rows, ncol)))
+      return set_error(WPCD_ECUDA, "tensor map encoding failed");
     const int grid = std::max(1, std::min(q.n_tiles, sm_count[pr->device] > 0 ? sm_count[pr->device] : 152));
     if (G)
-      tc_gemm_ws_kernel<true, false><<<grid, WS_THREADS, w.smem, s>>>(q);
+      tc_gemm_ws_kernel<true, false><<<grid, WS_THREADS, w.smem, s>>>(tmx, tmg, q);
     else if (S)
-      tc_gemm_ws_kernel<false, true><<<grid, WS_THREADS, w.smem, s>>>(q);
+      tc_gemm_ws_kernel<false, true><<<grid, WS_THREADS, w.smem, s>>>(tmx, tmg, q);
     else
-      tc_gemm_ws_kernel<false, false><<<grid, WS_THREADS, w.smem, s>>>(q);
+      tc_gemm_ws_kernel<false, false><<<grid, WS_THREADS, w.smem, s>>>(tmx, tmg, q);
   } else {
     p.vec_out = vec_out;
     const size_t smem = (size_t)sh.stages * sh.stage_bytes;
