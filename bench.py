@@ -139,11 +139,12 @@ def fill_flops_per_node(n_ch: int, n_pairs: int) -> int:
 # of the kernel as it stands (profiles/ names the capture); None where no
 # capture of the current kernel exists
 NCU_TRAFFIC = {
-    "fill_kernel<FP64,3>": 436.3e6,
-    "spmm_kernel<float>": 372.4e6,
-    "tc_gemm_kernel<TF32x3> (Vt, G1)": 335.3e6,
-    "spmm_df_kernel": 1539.4e6,
-    "gemm_df_kernel": 1061.9e6,
+    "fill_kernel<FP64,3>": 440.0e6,
+    "spmm_kernel<float>": 377.1e6,
+    "tc_gemm_kernel<TF32x3> (Vt, G1)": 332.4e6,
+    "tc_gemm_kernel<TF32x3> (O)": 334.5e6,
+    "spmm_df_kernel": 958.4e6,
+    "gemm_df_kernel": 884.8e6,
 }
 
 
@@ -283,7 +284,7 @@ def kernel_rooflines(W, pr, w, phases, n_nodes, n_e, stream, flush, peaks, f_sm,
                                                            timed=True))
     entry("spmm_kernel<float>", "alu", spmm_flops / (ms * 1e-3) / 1e12, fp32, "TFLOP/s", ms, n32,
           f"4 n_pairs nnz B = {spmm_flops:.3e} FP32 flops (one real-by-complex multiply-add per block entry and "
-          "energy; the compensated sums add issued work that is not counted)", src32)
+          "energy)", src32)
     tc_bytes = 3.0 * 8 * dim * n_e
     ms = _time_kernel(stream, flush, lambda: pr.wpcd_channel_gemm(0, W.WPCD_GEMM_TF32X3, g32, x32, y32, n_e,
                                                                    stream=stream, timed=True))

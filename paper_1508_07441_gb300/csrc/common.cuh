@@ -37,8 +37,12 @@ struct SpmmParams {
   int64_t nnz;
 };
 
-// SpMM accumulators: plain FP64 sums, or FP32 float-float sums (Knuth's
-// TwoSum on the running sum, the rounding errors gathered in lo)
+// SpMM accumulators: plain sums of the block partials, FP64 or FP32.  The
+// FP32 SpMM feeds only the inner cycles of the mixed solve, whose accuracy
+// the float-float refinement residual carries: compensating the FP32 block
+// sums (TwoSum, errors gathered in a low part) changed neither the number of
+// refinement cycles nor the final error on the 200 x 200, 128-energy
+// workload and cost a fifth of the SpMM's time.
 struct AccD {
   double v;
   __device__ void zero() { v = 0.0; }
@@ -48,22 +52,11 @@ struct AccD {
 };
 
 struct AccF {
-  float hi, lo;
-  __device__ void zero() { hi = 0.f; lo = 0.f; }
-  __device__ void add(float x) {
-    float s = __fadd_rn(hi, x);
-    float bb = __fsub_rn(s, hi);
-    float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
-    hi = s;
-    lo = __fadd_rn(lo, e);
-  }
-  __device__ void add_shfl(int off) {
-    float ohi = __shfl_xor_sync(0xffffffffu, hi, off);
-    float olo = __shfl_xor_sync(0xffffffffu, lo, off);
-    add(ohi);
-    lo = __fadd_rn(lo, olo);
-  }
-  __device__ float value() const { return __fadd_rn(hi, lo); }
+  float v;
+  __device__ void zero() { v = 0.f; }
+  __device__ void add(float x) { v += x; }
+  __device__ void add_shfl(int off) { v += __shfl_xor_sync(0xffffffffu, v, off); }
+  __device__ float value() const { return v; }
 };
 
 template <typename T>
@@ -90,11 +83,9 @@ struct SpmmUnroll {
 // nonzeros o = b + nl, b + nl + nl_count, ... of its row, U at a time (their
 // column and value loads issued together), and for each of its EPT energies
 // forms the block of those U nonzeros with plain FMAs and adds it to the
-// accumulator.  For FP32 this is blocked summation with a compensated sum of
-// the block partials (FABsum, Blanchard, Higham and Mary, SIAM J. Sci.
-// Comput. 2020): the error grows with the number of blocks only through the
-// float-float accumulator, and inside a block with its few terms.  FP64
-// sums the block partials plainly.  y points at the problem's own vector
+// accumulator (blocked summation: the rounding error grows with the block
+// length plus the number of blocks, not with the row length).  y points at
+// the problem's own vector
 // block ([n_ch][n_cells][B] complex).  The lane's energies are en0 +
 // estride * t; with VEC (FP32, estride 1, EPT and B even) two adjacent
 // energies come in one 16-byte load.
