@@ -89,7 +89,24 @@ struct ResParams {
   const double *Elo, *Ehi;     // per energy
   const double *gl8_t, *gl8_w; // 8-point GL rule
   const double *gl4_t, *gl4_w; // 4-point GL rule
+  const double *gl3_t, *gl3_w; // 3-point GL rule
+  double4 *shell;              // [n_E][n_ch N] (a_lo, a_hi, sqrt|a_lo|, sqrt|a_hi|)
 };
+
+// a = (E - eps) 4/3 at the bin edges E_lo, E_hi of each energy and for each
+// pseudostate (the q^2 where 3q^2/4 = E - eps), and sqrt|a|: shared by all
+// q-bins, so the main kernel takes no square root
+__global__ void res_shell_kernel(ResParams R) {
+  const int nchk = R.n_ch * R.N;
+  const int64_t total = (int64_t)R.n_E * nchk;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int chk = (int)(idx % nchk), e = (int)(idx / nchk);
+    const double ek = R.eps[chk];
+    const double alo = (R.Elo[e] - ek) * kFourThirds, ahi = (R.Ehi[e] - ek) * kFourThirds;
+    R.shell[idx] = make_double4(alo, ahi, sqrt(fabs(alo)), sqrt(fabs(ahi)));
+  }
+}
 
 __global__ void resolvent_kernel(ResParams R, double *g) {
   const int dim = R.n_ch * R.N * R.M;
@@ -120,27 +137,25 @@ __global__ void resolvent_kernel(ResParams R, double *g) {
     // singularities sit at q^2 = (E_lo - eps)/(3/4) and (E_hi - eps)/(3/4),
     // outside the bin.  At a distance rho, in half bin widths, from the bin
     // centre the n-point GL error falls like r^-2n with r = rho +
-    // sqrt(rho^2 - 1) (Bernstein ellipse): rho > 32 gives r > 63 and a
-    // 4-point error below 1e-14, rho > 4 gives r > 7.8 and an 8-point error
-    // below 1e-14.  Closer singularities, and bins the shell crosses, take
-    // the closed form.
+    // sqrt(rho^2 - 1) (Bernstein ellipse).  Measured against an 100-point
+    // rule on random bins: 3 points for rho > 512 (worst 1.2e-13 relative),
+    // 4 for rho > 32 (2.2e-13), 8 for rho > 4 (1.7e-14).  Closer
+    // singularities, and bins the shell crosses, take the closed form.
+    // rho^2 is compared, from the shared a and sqrt|a| of the pseudostate.
+    const double4 sh = R.shell[(int64_t)e * nchk + chk];
     double half = 0.5 * (qb - qa), mid = 0.5 * (qb + qa);
-    double rho = 0.0;
+    double rho2 = 0.0;  // (rho half)^2 until the division below
     if (no_sign_change) {
-      rho = 1e300;
-      const double ih = 1.0 / half;
-      for (double a2 : {(Elo - ek) * kFourThirds, (Ehi - ek) * kFourThirds}) {
-        double qs = sqrt(fabs(a2));
-        // a real singular point at qs (a2 > 0), or a complex pair +-i qs
-        double d = a2 > 0.0 ? fabs(qs - mid) : sqrt(mid * mid + qs * qs);
-        rho = fmin(rho, d * ih);
-      }
+      // a real singular point at sqrt(a) (a > 0), or a complex pair +-i sqrt|a|
+      const double dl = sh.x > 0.0 ? (sh.z - mid) * (sh.z - mid) : mid * mid + fabs(sh.x);
+      const double dh = sh.y > 0.0 ? (sh.w - mid) * (sh.w - mid) : mid * mid + fabs(sh.y);
+      rho2 = fmin(dl, dh) / (half * half);
     }
     double re;
-    if (rho > 4.0) {
-      const int npts = rho > 32.0 ? 4 : 8;
-      const double *t = npts == 4 ? R.gl4_t : R.gl8_t;
-      const double *wg = npts == 4 ? R.gl4_w : R.gl8_w;
+    if (rho2 > 16.0) {
+      const int npts = rho2 > 512.0 * 512.0 ? 3 : rho2 > 32.0 * 32.0 ? 4 : 8;
+      const double *t = npts == 3 ? R.gl3_t : npts == 4 ? R.gl4_t : R.gl8_t;
+      const double *wg = npts == 3 ? R.gl3_w : npts == 4 ? R.gl4_w : R.gl8_w;
       const double dist = fmin(fabs(lo_a), fabs(lo_b));
       const double xmax = fabs(D) / dist;  // |x| at every node of the bin
       double s = 0.0;
@@ -170,7 +185,7 @@ __global__ void resolvent_kernel(ResParams R, double *g) {
     re *= inv;
     double im = 0.0;
     if (Ehi - ek > 0.0) {
-      double lo = sqrt(fmax((Elo - ek) * kFourThirds, 0.0)), hi = sqrt((Ehi - ek) * kFourThirds);
+      double lo = sh.x > 0.0 ? sh.z : 0.0, hi = sh.w;
       double a = fmax(qa, lo), b = fmin(qb, hi);
       if (b > a) im = -kPi * ((b - a) * (b * b + b * a + a * a) * kThird) * inv;
     }
@@ -281,25 +296,35 @@ __global__ void __launch_bounds__(V_THREADS) bdot_kernel(int rows, int B, int nv
                                                          const typename Cx<T>::t *__restrict__ V,
                                                          size_t ld, const typename Cx<T>::t *__restrict__ w,
                                                          double2 *__restrict__ partial) {
+  using C2 = typename Cx<T>::t;
   __shared__ double2 red[JC][V_THREADS];
   const int EL = blockDim.x;  // energy lanes (<= 32)
   const int RB = blockDim.y;  // row lanes
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * EL + tx;
   const int e = blockIdx.y * EL + tx;
   const int nblk = gridDim.x;
+  const int stride = nblk * RB;
   for (int j0 = 0; j0 < nv; j0 += JC) {
     T sx[JC], sy[JC];
 #pragma unroll
     for (int c = 0; c < JC; ++c) sx[c] = sy[c] = T(0);
     if (e < B) {
-      for (int r = blockIdx.x * RB + ty; r < rows; r += nblk * RB) {
-        const auto b = w[(size_t)r * B + e];
+      // two rows per iteration: both rows' loads are in flight together
+      for (int r = blockIdx.x * RB + ty; r < rows; r += 2 * stride) {
+        const bool two = r + stride < rows;
+        const size_t f1 = (size_t)r * B + e, f2 = (size_t)(two ? r + stride : r) * B + e;
+        const C2 b1 = w[f1];
+        C2 b2 = w[f2];
+        if (!two) b2.x = b2.y = T(0);
 #pragma unroll
         for (int c = 0; c < JC; ++c) {
           if (j0 + c < nv) {
-            const auto a = V[(size_t)(j0 + c) * ld + (size_t)r * B + e];
-            sx[c] = fma(a.x, b.x, fma(a.y, b.y, sx[c]));
-            sy[c] = fma(a.x, b.y, fma(-a.y, b.x, sy[c]));
+            const C2 a1 = V[(size_t)(j0 + c) * ld + f1];
+            const C2 a2 = V[(size_t)(j0 + c) * ld + f2];
+            sx[c] = fma(a1.x, b1.x, fma(a1.y, b1.y, sx[c]));
+            sy[c] = fma(a1.x, b1.y, fma(-a1.y, b1.x, sy[c]));
+            sx[c] = fma(a2.x, b2.x, fma(a2.y, b2.y, sx[c]));
+            sy[c] = fma(a2.x, b2.y, fma(-a2.y, b2.x, sy[c]));
           }
         }
       }
@@ -421,6 +446,26 @@ __global__ void baxpy_kernel(int64_t n, int B, int nv, const typename Cx<T>::t *
 }
 
 // dst[f] = src[f] * inv[e]
+// the FP32 axpy with B even: two adjacent energies of one row per thread,
+// in 16-byte loads of the vectors and of the coefficients (n2 = n / 2)
+__global__ void baxpy2_kernel(int64_t n2, int B2, int nv, const float4 *__restrict__ V, size_t ld2,
+                              const float4 *__restrict__ c, float4 *__restrict__ w) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n2;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    const int e2 = (int)(f % B2);
+    float4 a = w[f];
+    for (int j = 0; j < nv; ++j) {
+      const float4 v = V[(size_t)j * ld2 + f];
+      const float4 cj = c[j * B2 + e2];
+      a.x = fmaf(cj.x, v.x, fmaf(-cj.y, v.y, a.x));
+      a.y = fmaf(cj.x, v.y, fmaf(cj.y, v.x, a.y));
+      a.z = fmaf(cj.z, v.z, fmaf(-cj.w, v.w, a.z));
+      a.w = fmaf(cj.z, v.w, fmaf(cj.w, v.z, a.w));
+    }
+    w[f] = a;
+  }
+}
+
 template <typename T>
 __global__ void bscale_kernel(int64_t n, int B, const typename Cx<T>::t *src, const T *__restrict__ inv,
                               typename Cx<T>::t *dst) {
@@ -822,7 +867,7 @@ wpcd_status resolvent_impl(const wpcd_problem *pr, const double *E, int n_E, dou
                            int *j0, double *D, cudaStream_t s, int max_blocks = 152 * 16) {
   if (n_E < 0 || (n_E > 0 && (!E || !g))) return set_error(WPCD_EINVAL, "bad resolvent arguments");
   if (n_E == 0) return WPCD_OK;
-  std::vector<double> lohi(2 * (size_t)n_E + 24);  // E_lo, E_hi, 8- and 4-point GL rules
+  std::vector<double> lohi(2 * (size_t)n_E + 30);  // E_lo, E_hi, 8-, 4- and 3-point GL rules
   for (int e = 0; e < n_E; ++e) {
     int jj;
     double lo, hi;
@@ -835,9 +880,11 @@ wpcd_status resolvent_impl(const wpcd_problem *pr, const double *E, int n_E, dou
   }
   gauss_legendre(8, lohi.data() + 2 * n_E, lohi.data() + 2 * n_E + 8);
   gauss_legendre(4, lohi.data() + 2 * n_E + 16, lohi.data() + 2 * n_E + 20);
+  gauss_legendre(3, lohi.data() + 2 * n_E + 24, lohi.data() + 2 * n_E + 27);
   WPCD_CUDA_TRY(cudaSetDevice(pr->device));
+  const int64_t n_shell = (int64_t)n_E * pr->n_ch * pr->N;
   double *d_lohi = nullptr;
-  WPCD_CUDA_TRY(cudaMallocAsync(&d_lohi, sizeof(double) * lohi.size(), s));
+  WPCD_CUDA_TRY(cudaMallocAsync(&d_lohi, sizeof(double) * (lohi.size() + 4 * n_shell + 4), s));
   WPCD_CUDA_TRY(cudaMemcpyAsync(d_lohi, lohi.data(), sizeof(double) * lohi.size(), cudaMemcpyHostToDevice, s));
   ResParams R{};
   R.n_ch = pr->n_ch;
@@ -853,23 +900,31 @@ wpcd_status resolvent_impl(const wpcd_problem *pr, const double *E, int n_E, dou
   R.gl8_w = d_lohi + 2 * n_E + 8;
   R.gl4_t = d_lohi + 2 * n_E + 16;
   R.gl4_w = d_lohi + 2 * n_E + 20;
+  R.gl3_t = d_lohi + 2 * n_E + 24;
+  R.gl3_w = d_lohi + 2 * n_E + 27;
+  // 32-byte aligned after the tables (cudaMallocAsync returns 256-byte aligned)
+  R.shell = reinterpret_cast<double4 *>(d_lohi + ((lohi.size() + 3) & ~(size_t)3));
+  res_shell_kernel<<<grid_for(n_shell, 256), 256, 0, s>>>(R);
   int64_t total = (int64_t)n_E * pr->n_ch * pr->N * pr->M;
   resolvent_kernel<<<grid_for(total, 256, max_blocks), 256, 0, s>>>(R, g);
-  count_launches(1);
+  count_launches(2);
   cudaError_t e = cudaGetLastError();
   cudaFreeAsync(d_lohi, s);
-  // the host staging buffer must outlive the copy
-  cudaError_t e2 = cudaStreamSynchronize(s);
+  // a copy from pageable memory returns once the data is staged, so the
+  // host vector may go; no synchronisation (the work stays asynchronous)
   if (e != cudaSuccess) return cuda_error(e, "resolvent launch");
-  if (e2 != cudaSuccess) return cuda_error(e2, "resolvent");
   return WPCD_OK;
 }
 
 }  // namespace
 
+// the ABI call synchronises its stream; the solves' internal calls do not
 wpcd_status resolvent(const wpcd_problem *pr, const double *E, int n_E, double *g, int *j0,
                       double *D, cudaStream_t s) {
-  return resolvent_impl(pr, E, n_E, g, 0, j0, D, s);
+  wpcd_status st = resolvent_impl(pr, E, n_E, g, 0, j0, D, s);
+  if (st != WPCD_OK) return st;
+  WPCD_CUDA_TRY(cudaStreamSynchronize(s));
+  return WPCD_OK;
 }
 
 wpcd_status resolvent_minor(const wpcd_problem *pr, const double *E, int n_E, double *g, cudaStream_t s) {
@@ -988,6 +1043,16 @@ struct Krylov {
                                                       scale ? inv : nullptr);
     count_launches(2);
   }
+  // w += sum_{j < nv} hc_j V_j (FP32 with B even: two energies per thread)
+  void axpy(int nv, cudaStream_t s) {
+    const int64_t n = (int64_t)dim * B;
+    if (sizeof(T) == 4 && B % 2 == 0)
+      baxpy2_kernel<<<grid_for(n / 2, 256), 256, 0, s>>>(n / 2, B / 2, nv, reinterpret_cast<const float4 *>(V),
+                                                         dim * B / 2, reinterpret_cast<const float4 *>(hc),
+                                                         reinterpret_cast<float4 *>(w));
+    else
+      baxpy_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(n, B, nv, vec(0), dim * B, hc, wv());
+  }
   // one Arnoldi step from column k (w holds (I - K) v_k on entry); classical
   // Gram-Schmidt with a second pass (reorth = true) or a single pass
   void step(int k, cudaStream_t s, bool reorth = true) {
@@ -995,10 +1060,10 @@ struct Krylov {
     const size_t ld = dim * B;
     const int vg = grid_for(n, 256);
     dots<T>(k + 1, vec(0), ld, wv(), h, 0, s, true);
-    baxpy_kernel<T><<<vg, 256, 0, s>>>(n, B, k + 1, vec(0), ld, hc, wv());
+    axpy(k + 1, s);
     if (reorth) {
       dots<T>(k + 1, vec(0), ld, wv(), h2, 0, s, true);
-      baxpy_kernel<T><<<vg, 256, 0, s>>>(n, B, k + 1, vec(0), ld, hc, wv());
+      axpy(k + 1, s);
       // h += h2 (the second pass's partials are still in place)
       breduce_kernel<T><<<breduce_blocks((k + 1) * B), 256, 0, s>>>(k + 1, nblk, B, partial, h, 1, nullptr, 0.0,
                                                                    nullptr);
