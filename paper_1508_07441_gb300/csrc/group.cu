@@ -166,7 +166,7 @@ __device__ __forceinline__ const float *vals_of<float>(const GProb &P) {
   return P.val32;
 }
 
-template <typename VT, typename T, int NCH, int EPT>
+template <typename VT, typename T, int NCH, int EPT, bool VEC>
 __global__ void __launch_bounds__(256) gspmm_kernel(const GMeta *__restrict__ gm, const GProb *__restrict__ gp,
                                                     int rpw, int el_n, const typename Cx<T>::t *__restrict__ y,
                                                     typename Cx<T>::t *__restrict__ z) {
@@ -209,7 +209,9 @@ __global__ void __launch_bounds__(256) gspmm_kernel(const GMeta *__restrict__ gm
         acc[l][t][1].zero();
       }
     const int64_t b = active ? P.row_ptr[c] : 0, e = active ? P.row_ptr[c + 1] : 0;
-    spmm_row<VT, T, NCH, EPT, false>(b, e, nl, nl_count, P.col, val, P.nnz, yg, n_cells, B, e_base + el, el_n, acc);
+    // lane energies: VEC adjacent (en0 + t), otherwise strided (el + el_n t)
+    const int en0 = VEC ? e_base + el * EPT : e_base + el, estride = VEC ? 1 : el_n;
+    spmm_row<VT, T, NCH, EPT, VEC>(b, e, nl, nl_count, P.col, val, P.nnz, yg, n_cells, B, en0, estride, acc);
     for (int off = el_n; off < lpr; off <<= 1)
 #pragma unroll
       for (int l = 0; l < NCH; ++l)
@@ -222,7 +224,7 @@ __global__ void __launch_bounds__(256) gspmm_kernel(const GMeta *__restrict__ gm
       C2 *zg = z + P.eoff;
 #pragma unroll
       for (int t = 0; t < EPT; ++t) {
-        const int en = e_base + el + el_n * t;
+        const int en = VEC ? e_base + el * EPT + t : e_base + el + el_n * t;
         if (en < B)
 #pragma unroll
           for (int l = 0; l < NCH; ++l) {
@@ -400,15 +402,24 @@ __global__ void __launch_bounds__(GV_THREADS) gdot_kernel(const GMeta *__restric
 #pragma unroll
     for (int c = 0; c < GJC; ++c) sx[c] = sy[c] = T(0);
     if (tx < B) {
-      for (int r = lb * RB + ty; r < rows; r += nb * RB) {
-        const size_t f = (size_t)off + (size_t)r * B + tx;
-        const auto b = w[f];
+      // two rows per iteration: both rows' loads are in flight together
+      const int stride = nb * RB;
+      for (int r = lb * RB + ty; r < rows; r += 2 * stride) {
+        const bool two = r + stride < rows;
+        const size_t f1 = (size_t)off + (size_t)r * B + tx;
+        const size_t f2 = (size_t)off + (size_t)(two ? r + stride : r) * B + tx;
+        const auto b1 = w[f1];
+        auto b2 = w[f2];
+        if (!two) b2.x = b2.y = T(0);
 #pragma unroll
         for (int c = 0; c < GJC; ++c) {
           if (j0 + c < nv) {
-            const auto a = V[(size_t)(j0 + c) * ld + f];
-            sx[c] = fma(a.x, b.x, fma(a.y, b.y, sx[c]));
-            sy[c] = fma(a.x, b.y, fma(-a.y, b.x, sy[c]));
+            const auto a1 = V[(size_t)(j0 + c) * ld + f1];
+            const auto a2 = V[(size_t)(j0 + c) * ld + f2];
+            sx[c] = fma(a1.x, b1.x, fma(a1.y, b1.y, sx[c]));
+            sy[c] = fma(a1.x, b1.y, fma(-a1.y, b1.x, sy[c]));
+            sx[c] = fma(a2.x, b2.x, fma(a2.y, b2.y, sx[c]));
+            sy[c] = fma(a2.x, b2.y, fma(-a2.y, b2.x, sy[c]));
           }
         }
       }
@@ -493,6 +504,29 @@ __global__ void gaxpy_kernel(const GMeta *__restrict__ gm, int64_t len, int nv,
     }
     w[f].x = ax;
     w[f].y = ay;
+  }
+}
+
+// the FP32 axpy of an even group (every B_g and segment offset even): two
+// adjacent energies of one row per thread in 16-byte loads; len2 = len / 2
+__global__ void gaxpy2_kernel(const GMeta *__restrict__ gm, int64_t len2, int nv, const float4 *__restrict__ V,
+                              size_t ld2, const float4 *__restrict__ c, float4 *__restrict__ w) {
+  __shared__ SegSmem sm;
+  load_segs(gm, sm);
+  const int n = gm->n, S2 = gm->S / 2;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < len2;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    const int s2 = system_of(sm, n, 2 * f) / 2;  // even system of the pair
+    float4 a = w[f];
+    for (int j = 0; j < nv; ++j) {
+      const float4 v = V[(size_t)j * ld2 + f];
+      const float4 cj = c[(size_t)j * S2 + s2];
+      a.x = fmaf(cj.x, v.x, fmaf(-cj.y, v.y, a.x));
+      a.y = fmaf(cj.x, v.y, fmaf(cj.y, v.x, a.y));
+      a.z = fmaf(cj.z, v.z, fmaf(-cj.w, v.w, a.z));
+      a.w = fmaf(cj.z, v.w, fmaf(cj.w, v.z, a.w));
+    }
+    w[f] = a;
   }
 }
 
@@ -606,6 +640,7 @@ struct DevFree {
 
 struct Group {
   int n = 0, n_ch = 0, S = 0, prec = WPCD_FP64, Bmax = 1;
+  bool even = true;        // every B_g and every segment offset even
   int64_t L = 0;           // complex elements of one concatenated vector
   GMeta meta;              // host copy
   std::vector<GProb> probs;
@@ -687,16 +722,19 @@ wpcd_status gspmm_cfg(const Group &gr, const T *y, T *z, const SpmmConfig &cfg, 
   const int rows_per_block = 8 * cfg.rpw;
   dim3 grid(grid_for((int64_t)gr.meta.cell_off[gr.n], rows_per_block, 152 * 16),
             (gr.Bmax + cfg.el * cfg.ept - 1) / (cfg.el * cfg.ept));
-#define WPCD_GSPMM_EPT(NCH, EPT) \
-  gspmm_kernel<VT, T, NCH, EPT><<<grid, 256, 0, s>>>(gr.d_meta, gr.d_probs, cfg.rpw, cfg.el, yy, zz)
-#define WPCD_GSPMM_CASE(NCH)  \
-  case NCH:                   \
-    if (cfg.ept == 1)         \
-      WPCD_GSPMM_EPT(NCH, 1); \
-    else if (cfg.ept == 2)    \
-      WPCD_GSPMM_EPT(NCH, 2); \
-    else                      \
-      WPCD_GSPMM_EPT(NCH, 4); \
+  // FP32 vectors, every batch even and every segment 16-byte aligned: two
+  // adjacent energies per load
+  const bool vec = sizeof(T) == 4 && gr.even;
+#define WPCD_GSPMM_EPT(NCH, EPT, VEC) \
+  gspmm_kernel<VT, T, NCH, EPT, VEC><<<grid, 256, 0, s>>>(gr.d_meta, gr.d_probs, cfg.rpw, cfg.el, yy, zz)
+#define WPCD_GSPMM_CASE(NCH)                                                         \
+  case NCH:                                                                          \
+    if (cfg.ept == 1)                                                                \
+      WPCD_GSPMM_EPT(NCH, 1, false);                                                 \
+    else if (cfg.ept == 2)                                                           \
+      vec ? WPCD_GSPMM_EPT(NCH, 2, sizeof(T) == 4) : WPCD_GSPMM_EPT(NCH, 2, false);  \
+    else                                                                             \
+      vec ? WPCD_GSPMM_EPT(NCH, 4, sizeof(T) == 4) : WPCD_GSPMM_EPT(NCH, 4, false);  \
     break;
   switch (gr.n_ch) {
     WPCD_GSPMM_CASE(1)
@@ -866,16 +904,25 @@ struct GKrylov {
                                                           scale ? inv : nullptr);
     count_launches(2);
   }
+  // w += sum_{j < nv} hc_j V_j (FP32 in an even group: two energies per thread)
+  void axpy(int nv, cudaStream_t s) {
+    if (sizeof(T) == 4 && gr->even)
+      gaxpy2_kernel<<<grid_for(L / 2, 256), 256, 0, s>>>(gr->d_meta, L / 2, nv, reinterpret_cast<const float4 *>(V),
+                                                         (size_t)L / 2, reinterpret_cast<const float4 *>(hc),
+                                                         reinterpret_cast<float4 *>(w));
+    else
+      gaxpy_kernel<T><<<grid_for(L, 256), 256, 0, s>>>(gr->d_meta, L, nv, vec(0), (size_t)L, hc, wv());
+  }
   // one Arnoldi step from column k (w = (I - K) v_k on entry); classical
   // Gram-Schmidt with a second pass (reorth) or a single pass
   void step(int k, cudaStream_t s, bool reorth) {
     const int vg = grid_for(L, 256);
     const size_t ld = (size_t)L;
     dots<T>(k + 1, vec(0), ld, wv(), h, 0, s, true);
-    gaxpy_kernel<T><<<vg, 256, 0, s>>>(gr->d_meta, L, k + 1, vec(0), ld, hc, wv());
+    axpy(k + 1, s);
     if (reorth) {
       dots<T>(k + 1, vec(0), ld, wv(), h2, 0, s, true);
-      gaxpy_kernel<T><<<vg, 256, 0, s>>>(gr->d_meta, L, k + 1, vec(0), ld, hc, wv());
+      axpy(k + 1, s);
       // h += h2: the second pass's coefficients, summed from its partials
       greduce_kernel<T><<<((k + 1) * S * 32 + 255) / 256, 256, 0, s>>>(gr->d_meta, k + 1, gr->nbt(), partial, h, 1,
                                                                    nullptr, 0.0, nullptr);
@@ -1203,6 +1250,7 @@ wpcd_status solve_group(int n_prob, wpcd_problem *const *prs, const wpcd_P *cons
     mt.dtile_off[g + 1] = mt.dtile_off[g] + pr->n_ch * q.rt * q.dct;
     mt.cell_off[g + 1] = mt.cell_off[g] + q.n_cells;
     gr.Bmax = std::max(gr.Bmax, B);
+    gr.even = gr.even && B % 2 == 0 && mt.eoff[g] % 2 == 0;
   }
   gr.S = mt.S = mt.sys[n_prob];
   gr.L = mt.eoff[n_prob];
