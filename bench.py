@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="cfg2")
+    ap.add_argument("--workload", default="bosons3_200")
     ap.add_argument("--n-energies", type=int, default=128)
     ap.add_argument("--plain-energy", type=float, default=0.5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -155,7 +155,7 @@ def bench_precision_stress(args, W, inputs, stream, flush, device):
     solve on FP64 and on FP32C values, each against the FP64 oracle."""
     import torch
 
-    w = inputs.workload("cfg4")
+    w = inputs.workload("stress5_300")
     pr = W.Problem(w["p_edges"], w["q_edges"], *w["nodes"], w["n_ch"], w["V"], w["a"], device=device)
     n_nodes = w["N"] * w["M"] * w["nodes"][0] * w["nodes"][1] * w["nodes"][2]
     out = {"workload": "3 bosons, V=-6exp(-r^2/0.5)+2exp(-r^2/0.1), 5 channels, N=M=300, GL 8x8x32 "
@@ -386,7 +386,7 @@ def bench_batching(args, W, inputs, stream, flush, device, maxr_fn=None):
     import numpy as np
     import torch
 
-    w = inputs.workload("cfg3")
+    w = inputs.workload("bosons3_150")
     pr = W.Problem(w["p_edges"], w["q_edges"], *w["nodes"], w["n_ch"], w["V"], w["a"], device=device)
     P = pr.wpcd_assemble_P(W.WPCD_FP64, stream=stream)
     Eb = [float(x) for x in inputs.batch_energies(pr.eps_bound, 128)]

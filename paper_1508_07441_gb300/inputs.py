@@ -38,16 +38,16 @@ def jittered_edges(n_bins: int, k_max: float, seed: int, frac: float = 0.1) -> n
 # Workloads: (N = M, nodes (n_p, n_q, n_x), channels, potential terms)
 WORKLOADS = {
     # s-wave, V = -3 exp(-r^2), 50 x 50 lattice, 4x4x16 nodes; one energy E = 0.5
-    "cfg1": dict(N=50, M=50, k_max=20.0, nodes=(4, 4, 16), n_ch=1, V=(-3.0,), a=(1.0,),
+    "swave_50": dict(N=50, M=50, k_max=20.0, nodes=(4, 4, 16), n_ch=1, V=(-3.0,), a=(1.0,),
                  energies=(0.5,)),
     # l = lambda <= 2 (3 channels), 200 x 200 lattice, 8x8x32 nodes (dimension 120 000)
-    "cfg2": dict(N=200, M=200, k_max=20.0, nodes=(8, 8, 32), n_ch=3, V=(-3.0,), a=(1.0,),
+    "bosons3_200": dict(N=200, M=200, k_max=20.0, nodes=(8, 8, 32), n_ch=3, V=(-3.0,), a=(1.0,),
                  energies=(0.5,)),
     # batching: 150 x 150, 3 channels, 128 energies in [-0.9 |E_d|, 5]
-    "cfg3": dict(N=150, M=150, k_max=20.0, nodes=(8, 8, 32), n_ch=3, V=(-3.0,), a=(1.0,),
+    "bosons3_150": dict(N=150, M=150, k_max=20.0, nodes=(8, 8, 32), n_ch=3, V=(-3.0,), a=(1.0,),
                  energies=None),
     # precision stress: short-range repulsion, 5 channels, 300 x 300 (dimension 450 000)
-    "cfg4": dict(N=300, M=300, k_max=20.0, nodes=(8, 8, 32), n_ch=5, V=(-6.0, 2.0), a=(0.5, 0.1),
+    "stress5_300": dict(N=300, M=300, k_max=20.0, nodes=(8, 8, 32), n_ch=5, V=(-6.0, 2.0), a=(0.5, 0.1),
                  energies=(0.5,)),
 }
 

@@ -83,7 +83,7 @@ def test_assemble_full_size_3_channels(W, orc):
     compared element by element with the oracle (FP64 and FP32C)."""
     from paper_1508_07441_gb300 import inputs
 
-    w = inputs.workload("cfg2")
+    w = inputs.workload("bosons3_200")
     pr = W.Problem(w["p_edges"], w["q_edges"], *w["nodes"], w["n_ch"], w["V"], w["a"])
     ref = orc.P0(w["p_edges"], w["q_edges"], *w["nodes"], w["n_ch"], with_abs=True)
     for prec, name in [(W.WPCD_FP64, "fp64"), (W.WPCD_FP32C, "fp32c")]:
@@ -171,7 +171,7 @@ def test_solve_s_wave_benchmark_lattice(W, orc):
     """The s-wave 50 x 50 lattice, V = -3 exp(-r^2), E = 0.5: both summations."""
     from paper_1508_07441_gb300 import inputs
 
-    w = inputs.workload("cfg1")
+    w = inputs.workload("swave_50")
     pr = W.Problem(w["p_edges"], w["q_edges"], *w["nodes"], 1, w["V"], w["a"])
     P = pr.wpcd_assemble_P(W.WPCD_FP64)
     opr = orc.Problem(dict(pe=w["p_edges"], qe=w["q_edges"], n_p=4, n_q=4, n_x=16, n_ch=1,

@@ -26,7 +26,7 @@ def W():
 def test_precision_stress_amplitudes(W, orc, capsys):
     from paper_1508_07441_gb300 import inputs
 
-    w = inputs.workload("cfg4")
+    w = inputs.workload("stress5_300")
     pr = W.Problem(w["p_edges"], w["q_edges"], *w["nodes"], w["n_ch"], w["V"], w["a"])
     P64 = pr.wpcd_assemble_P(W.WPCD_FP64)
     P32 = pr.wpcd_assemble_P(W.WPCD_FP32C)
@@ -40,7 +40,7 @@ def test_precision_stress_amplitudes(W, orc, capsys):
     err = {name: abs(u[0] - ref) / abs(ref) for name, u in (("fp64", U64), ("mixed_fp64_values", Um64),
                                                              ("mixed_fp32c_values", Um32))}
     with capsys.disabled():
-        print(f"\ncfg4 U00 = {ref:.12e}; rel. errors vs the FP64 oracle: {err}")
+        print(f"\nstress5_300 U00 = {ref:.12e}; rel. errors vs the FP64 oracle: {err}")
     assert err["fp64"] < 1e-8
     assert err["mixed_fp64_values"] < 1e-8
     # FP32C: P0 values carry FP32 node-evaluation errors (1e-5 parity bar per
