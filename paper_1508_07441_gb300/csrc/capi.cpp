@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -35,6 +36,35 @@ wpcd_status cuda_error(cudaError_t e, const char *what) {
 void clear_error() {
   g_last_error.clear();
   (void)cudaGetLastError();
+}
+
+cudaError_t pool_malloc(void **p, size_t bytes, cudaStream_t s) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+      cudaMemPoolProps props{};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      if ((e = cudaMemPoolCreate(&pools[dev], &props)) != cudaSuccess) return e;
+      // keep freed blocks for reuse rather than returning them at each sync
+      uint64_t keep = UINT64_MAX;
+      if ((e = cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) return e;
+    }
+    pool = pools[dev];
+  }
+  return cudaMallocFromPoolAsync(p, bytes ? bytes : 16, pool, s);
+}
+
+void pool_free(void *p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
 }
 
 static void free_tables(DeviceTables &d) {

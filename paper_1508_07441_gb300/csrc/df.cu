@@ -160,19 +160,20 @@ wpcd_status spmm_df(const wpcd_problem *pr, const wpcd_P *P, const float *yh, co
 }  // namespace
 
 DfWork::~DfWork() {
-  cudaFree(xh);
-  cudaFree(xl);
-  cudaFree(yh);
-  cudaFree(yl);
+  pool_free(xh, st);
+  pool_free(xl, st);
+  pool_free(yh, st);
+  pool_free(yl, st);
 }
 
-cudaError_t DfWork::alloc(size_t dim, int B) {
+cudaError_t DfWork::alloc(size_t dim, int B, cudaStream_t s) {
   const size_t bytes = 2 * sizeof(float) * dim * (size_t)B;
+  st = s;
   cudaError_t e;
-  if ((e = cudaMalloc(&xh, bytes)) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&xl, bytes)) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&yh, bytes)) != cudaSuccess) return e;
-  return cudaMalloc(&yl, bytes);
+  if ((e = pool_malloc(&xh, bytes, s)) != cudaSuccess) return e;
+  if ((e = pool_malloc(&xl, bytes, s)) != cudaSuccess) return e;
+  if ((e = pool_malloc(&yh, bytes, s)) != cudaSuccess) return e;
+  return pool_malloc(&yl, bytes, s);
 }
 
 // split O, Vt (once per problem) and FP64 P0 values (once per matrix)
@@ -222,7 +223,7 @@ wpcd_status df_gemm_op(wpcd_problem *pr, bool use_O, const double *g, const doub
   if (st != WPCD_OK) return st;
   const size_t dim = (size_t)pr->n_ch * pr->N * pr->M;
   DfWork w;
-  WPCD_CUDA_TRY(w.alloc(dim, B));
+  WPCD_CUDA_TRY(w.alloc(dim, B, s));
   const int64_t nc = (int64_t)dim * B;
   df_split_scaled_kernel<<<grid_for(nc, 256), 256, 0, s>>>(nc, reinterpret_cast<const double2 *>(x),
                                                           reinterpret_cast<const double2 *>(g), w.xh, w.xl);
@@ -246,7 +247,7 @@ wpcd_status df_spmm_op(wpcd_problem *pr, wpcd_P *P, const double *y, double *z, 
   const size_t dim = (size_t)pr->n_ch * pr->N * pr->M;
   const int64_t nr = 2LL * (int64_t)dim * B;  // reals
   DfWork w;
-  WPCD_CUDA_TRY(w.alloc(dim, B));
+  WPCD_CUDA_TRY(w.alloc(dim, B, s));
   df_split_kernel<<<grid_for(nr, 256), 256, 0, s>>>(nr, y, w.yh, w.yl);
   count_launches(1);
   {

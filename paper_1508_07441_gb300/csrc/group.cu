@@ -621,12 +621,15 @@ __global__ void gamplitude_kernel(int S, const double2 *__restrict__ u, const in
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+// device memory from the library's stream-ordered pool, allocated and freed
+// on the solve's stream
 struct DevFree {
   std::vector<void *> p;
+  cudaStream_t st = nullptr;
   template <typename T>
   cudaError_t alloc(T **out, size_t bytes) {
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+    cudaError_t e = pool_malloc(&q, bytes, st);
     if (e == cudaSuccess) {
       p.push_back(q);
       *out = static_cast<T *>(q);
@@ -634,7 +637,7 @@ struct DevFree {
     return e;
   }
   ~DevFree() {
-    for (void *q : p) cudaFree(q);
+    for (void *q : p) pool_free(q, st);
   }
 };
 
@@ -860,8 +863,9 @@ struct GKrylov {
   C2 *hc = nullptr;  // axpy / update coefficients in T [(m+1)][S]
   T *inv = nullptr;  // 1 / norm per system in T [S]
   DevFree mem;
-  cudaError_t alloc(const Group &g, int m_, bool vectors = true) {
+  cudaError_t alloc(const Group &g, int m_, cudaStream_t s, bool vectors = true) {
     gr = &g;
+    mem.st = s;
     m = m_;
     S = g.S;
     L = g.L;
@@ -1031,6 +1035,7 @@ wpcd_status gsolve_mixed(const Group &gr, const wpcd_solve_opts &o, GCtx &cx, GK
   std::vector<double2> bet0((size_t)S * (m + 1), make_double2(0.0, 0.0));
   for (int e = 0; e < S; ++e) bet0[(size_t)e * (m + 1)] = make_double2(1.0, 0.0);
   DevFree tmp;
+  tmp.st = s;
   double2 *d_bet0 = nullptr;
   WPCD_CUDA_TRY(tmp.alloc(&d_bet0, sizeof(double2) * bet0.size()));
   WPCD_CUDA_TRY(cudaMemcpyAsync(kr.bnorm, ones.data(), sizeof(double) * S, cudaMemcpyHostToDevice, s));
@@ -1262,6 +1267,7 @@ wpcd_status solve_group(int n_prob, wpcd_problem *const *prs, const wpcd_P *cons
     mt.blk_off[g + 1] = mt.blk_off[g] + std::max(1, (int)std::lround(share * target));
   }
   GCtx cx;
+  cx.mem.st = s;
   WPCD_CUDA_TRY(cx.mem.alloc(&gr.d_meta, sizeof(GMeta)));
   WPCD_CUDA_TRY(cx.mem.alloc(&gr.d_probs, sizeof(GProb) * n_prob));
   WPCD_CUDA_TRY(cudaMemcpyAsync(gr.d_meta, &mt, sizeof(GMeta), cudaMemcpyHostToDevice, s));
@@ -1365,12 +1371,12 @@ wpcd_status solve_group(int n_prob, wpcd_problem *const *prs, const wpcd_P *cons
   if (mixed) {
     GKrylov<float> kr;
     GKrylov<double> k64;
-    WPCD_CUDA_TRY(kr.alloc(gr, opt.inner_iter > 0 ? opt.inner_iter : kDefaultInner));
-    WPCD_CUDA_TRY(k64.alloc(gr, 1, false));  // norms only
+    WPCD_CUDA_TRY(kr.alloc(gr, opt.inner_iter > 0 ? opt.inner_iter : kDefaultInner, s));
+    WPCD_CUDA_TRY(k64.alloc(gr, 1, s, false));  // norms only
     st = gsolve_mixed(gr, opt, cx, kr, k64, status, relres, n64, n32, n_outer, s);
   } else {
     GKrylov<double> kr;
-    WPCD_CUDA_TRY(kr.alloc(gr, opt.max_iter));
+    WPCD_CUDA_TRY(kr.alloc(gr, opt.max_iter, s));
     st = gsolve_fp64(gr, opt, cx, kr, status, relres, conv, n64, s);
   }
   if (st != WPCD_OK) return st;

@@ -602,14 +602,16 @@ __global__ void extract_kernel(const double2 *x, int r0, double2 *c_out) { *c_ou
 template <typename T>
 struct Workspace {
   T *y = nullptr, *z = nullptr;  // [dim * B] complex
+  cudaStream_t st = nullptr;     // stream of the pool frees
   ~Workspace() {
-    cudaFree(y);
-    cudaFree(z);
+    pool_free(y, st);
+    pool_free(z, st);
   }
-  cudaError_t alloc(size_t dim, int B) {
-    cudaError_t e = cudaMalloc(&y, 2 * sizeof(T) * dim * B);
+  cudaError_t alloc(size_t dim, int B, cudaStream_t s) {
+    st = s;
+    cudaError_t e = pool_malloc(&y, 2 * sizeof(T) * dim * B, s);
     if (e != cudaSuccess) return e;
-    return cudaMalloc(&z, 2 * sizeof(T) * dim * B);
+    return pool_malloc(&z, 2 * sizeof(T) * dim * B, s);
   }
 };
 
@@ -963,7 +965,7 @@ wpcd_status kapply(const wpcd_problem *pr, const wpcd_P *P, const double *g, con
   WPCD_CUDA_TRY(cudaSetDevice(pr->device));
   const size_t dim = (size_t)pr->n_ch * pr->N * pr->M;
   Workspace<double> ws;
-  WPCD_CUDA_TRY(ws.alloc(dim, 1));
+  WPCD_CUDA_TRY(ws.alloc(dim, 1, s));
   wpcd_status st = kapply_ws<double>(pr, P, g, x, y, nullptr, 1, ws, s);
   if (st != WPCD_OK) return st;
   WPCD_CUDA_TRY(cudaStreamSynchronize(s));
@@ -985,34 +987,36 @@ struct Krylov {
   typename Cx<T>::t *hc = nullptr;  // axpy coefficients in T [(m+1)][B]
   T *inv = nullptr;                  // 1 / |w| per energy in T [B]
   int nblk = 0;
+  cudaStream_t st = nullptr;  // stream of the pool frees
   ~Krylov() {
-    cudaFree(V); cudaFree(w); cudaFree(H); cudaFree(cs); cudaFree(sn); cudaFree(bet); cudaFree(h);
-    cudaFree(h2); cudaFree(nrm); cudaFree(y); cudaFree(partial); cudaFree(resid); cudaFree(bnorm);
-    cudaFree(hc); cudaFree(inv);
+    for (void *q : {(void *)V, (void *)w, (void *)H, (void *)cs, (void *)sn, (void *)bet, (void *)h, (void *)h2,
+                    (void *)nrm, (void *)y, (void *)partial, (void *)resid, (void *)bnorm, (void *)hc, (void *)inv})
+      pool_free(q, st);
   }
-  cudaError_t alloc(int m_, int B_, size_t dim_, bool vectors = true) {
+  cudaError_t alloc(int m_, int B_, size_t dim_, cudaStream_t s, bool vectors = true) {
     m = m_;
     B = B_;
     dim = dim_;
     nblk = 152 * 2;
+    st = s;
     cudaError_t e;
     if (vectors) {
-      if ((e = cudaMalloc(&V, 2 * sizeof(T) * dim * B * (m + 1))) != cudaSuccess) return e;
-      if ((e = cudaMalloc(&w, 2 * sizeof(T) * dim * B)) != cudaSuccess) return e;
+      if ((e = pool_malloc(&V, 2 * sizeof(T) * dim * B * (m + 1), s)) != cudaSuccess) return e;
+      if ((e = pool_malloc(&w, 2 * sizeof(T) * dim * B, s)) != cudaSuccess) return e;
     }
-    if ((e = cudaMalloc(&H, sizeof(double2) * (size_t)B * (m + 1) * m)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&cs, sizeof(double2) * (size_t)B * m)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&sn, sizeof(double2) * (size_t)B * m)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&bet, sizeof(double2) * (size_t)B * (m + 1))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&h, sizeof(double2) * (size_t)B * (m + 1))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&h2, sizeof(double2) * (size_t)B * (m + 1))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&nrm, sizeof(double2) * (size_t)B)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&y, sizeof(double2) * (size_t)B * m)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&partial, sizeof(double2) * (size_t)B * (m + 1) * nblk)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&resid, sizeof(double) * B)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&hc, 2 * sizeof(T) * (size_t)B * (m + 1))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&inv, sizeof(T) * (size_t)B)) != cudaSuccess) return e;
-    return cudaMalloc(&bnorm, sizeof(double) * B);
+    if ((e = pool_malloc(&H, sizeof(double2) * (size_t)B * (m + 1) * m, s)) != cudaSuccess) return e;
+    if ((e = pool_malloc(&cs, sizeof(double2) * (size_t)B * m, s)) != cudaSuccess) return e;
+    if ((e = pool_malloc(&sn, sizeof(double2) * (size_t)B * m, s)) != cudaSuccess) return e;
+    if ((e = pool_malloc(&bet, sizeof(double2) * (size_t)B * (m + 1), s)) != cudaSuccess) return e;
+    if ((e = pool_malloc(&h, sizeof(double2) * (size_t)B * (m + 1), s)) != cudaSuccess) return e;
+    if ((e = pool_malloc(&h2, sizeof(double2) * (size_t)B * (m + 1), s)) != cudaSuccess) return e;
+    if ((e = pool_malloc(&nrm, sizeof(double2) * (size_t)B, s)) != cudaSuccess) return e;
+    if ((e = pool_malloc(&y, sizeof(double2) * (size_t)B * m, s)) != cudaSuccess) return e;
+    if ((e = pool_malloc(&partial, sizeof(double2) * (size_t)B * (m + 1) * nblk, s)) != cudaSuccess) return e;
+    if ((e = pool_malloc(&resid, sizeof(double) * B, s)) != cudaSuccess) return e;
+    if ((e = pool_malloc(&hc, 2 * sizeof(T) * (size_t)B * (m + 1), s)) != cudaSuccess) return e;
+    if ((e = pool_malloc(&inv, sizeof(T) * (size_t)B, s)) != cudaSuccess) return e;
+    return pool_malloc(&bnorm, sizeof(double) * B, s);
   }
   using C2 = typename Cx<T>::t;
   C2 *vec(int j) { return reinterpret_cast<C2 *>(V) + (size_t)j * dim * B; }
@@ -1084,9 +1088,11 @@ struct SolveCtx {
   double *b = nullptr, *u = nullptr, *r = nullptr, *t = nullptr;  // FP64 [dim][B] complex
   int *r0 = nullptr;    // [B]
   double *Dd = nullptr, *pref = nullptr, *amp = nullptr;
+  cudaStream_t st = nullptr;  // stream of the pool allocations and frees
   ~SolveCtx() {
-    cudaFree(g); cudaFree(g32); cudaFree(b); cudaFree(u); cudaFree(r); cudaFree(t); cudaFree(r0);
-    cudaFree(Dd); cudaFree(pref); cudaFree(amp);
+    for (void *q : {(void *)g, (void *)g32, (void *)b, (void *)u, (void *)r, (void *)t, (void *)r0, (void *)Dd,
+                    (void *)pref, (void *)amp})
+      pool_free(q, st);
   }
 };
 
@@ -1207,14 +1213,14 @@ wpcd_status solve_fp64(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solve
       }
     if (any) {
       int *d_flag = nullptr;
-      WPCD_CUDA_TRY(cudaMalloc(&d_flag, sizeof(int) * B));
-      WPCD_CUDA_TRY(cudaMemcpy(d_flag, fallback.data(), sizeof(int) * B, cudaMemcpyHostToDevice));
+      WPCD_CUDA_TRY(pool_malloc(&d_flag, sizeof(int) * B, s));
+      WPCD_CUDA_TRY(cudaMemcpyAsync(d_flag, fallback.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
       bfallback_kernel<<<vg, 256, 0, s>>>(n, B, d_flag, (const double2 *)cx.b, (double2 *)cx.u, (double2 *)cx.r);
       count_launches(1);
       kr.norms<double>((const double2 *)cx.r, s);
       WPCD_CUDA_TRY(cudaMemcpyAsync(nr.data(), kr.nrm, sizeof(double2) * B, cudaMemcpyDeviceToHost, s));
       WPCD_CUDA_TRY(cudaStreamSynchronize(s));
-      cudaFree(d_flag);
+      pool_free(d_flag, s);
     }
   }
   std::vector<double> bn(B);
@@ -1306,7 +1312,7 @@ wpcd_status solve_mixed(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solv
   std::vector<double2> bet0((size_t)B * (m + 1), make_double2(0.0, 0.0));
   for (int e = 0; e < B; ++e) bet0[(size_t)e * (m + 1)] = make_double2(1.0, 0.0);
   double2 *d_bet0 = nullptr;
-  WPCD_CUDA_TRY(cudaMalloc(&d_bet0, sizeof(double2) * bet0.size()));
+  WPCD_CUDA_TRY(pool_malloc(&d_bet0, sizeof(double2) * bet0.size(), s));
   WPCD_CUDA_TRY(cudaMemcpyAsync(kr.bnorm, ones.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
   WPCD_CUDA_TRY(cudaMemcpyAsync(d_bet0, bet0.data(), sizeof(double2) * bet0.size(), cudaMemcpyHostToDevice, s));
   WPCD_CUDA_TRY(cudaStreamSynchronize(s));  // host staging vectors
@@ -1336,7 +1342,7 @@ wpcd_status solve_mixed(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solv
     wpcd_status st = tune_spmm(pr, const_cast<wpcd_P *>(P), B, 1, s, &c);
     if (st == WPCD_OK) st = tune_spmm(pr, const_cast<wpcd_P *>(P), B, 0, s, &c);
     if (st != WPCD_OK) {
-      cudaFree(d_bet0);
+      pool_free(d_bet0, s);
       return st;
     }
   }
@@ -1432,7 +1438,7 @@ wpcd_status solve_mixed(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solv
     n32 += m;
   }
   if (exec) cudaGraphExecDestroy(exec);
-  cudaFree(d_bet0);
+  pool_free(d_bet0, s);
   return result;
 }
 
@@ -1448,7 +1454,7 @@ wpcd_status solve_wynn(const wpcd_problem *pr, const wpcd_P *P, double E, const 
   if (st != WPCD_OK) return st;
   double D = Ehi - Elo;
   Workspace<double> ws;
-  WPCD_CUDA_TRY(ws.alloc(dim, 1));
+  WPCD_CUDA_TRY(ws.alloc(dim, 1, s));
   struct Free {
     std::vector<void *> p;
     ~Free() {
@@ -1569,12 +1575,13 @@ wpcd_status born_vectors(wpcd_problem *pr, const wpcd_P *P, const double *E, int
   SolveCtx cx;
   cx.B = n_E;
   cx.dim = dim;
-  WPCD_CUDA_TRY(cudaMalloc(&cx.b, 16 * dim * n_E));
-  WPCD_CUDA_TRY(cudaMalloc(&cx.t, 16 * dim * n_E));
-  WPCD_CUDA_TRY(cudaMalloc(&cx.r0, sizeof(int) * n_E));
+  cx.st = s;
+  WPCD_CUDA_TRY(pool_malloc(&cx.b, 16 * dim * n_E, s));
+  WPCD_CUDA_TRY(pool_malloc(&cx.t, 16 * dim * n_E, s));
+  WPCD_CUDA_TRY(pool_malloc(&cx.r0, sizeof(int) * n_E, s));
   WPCD_CUDA_TRY(cudaMemcpyAsync(cx.r0, j0.data(), sizeof(int) * n_E, cudaMemcpyHostToDevice, s));
   Workspace<double> ws;
-  WPCD_CUDA_TRY(ws.alloc(dim, n_E));
+  WPCD_CUDA_TRY(ws.alloc(dim, n_E, s));
   wpcd_status st = born(pr, P, cx, ws, s);
   if (st != WPCD_OK) return st;
   const int64_t n = (int64_t)dim * n_E;
@@ -1652,17 +1659,18 @@ wpcd_status solve(wpcd_problem *pr, const wpcd_P *Pc, const double *E, int n_E,
       SolveCtx cx;
       cx.B = B;
       cx.dim = dim;
+      cx.st = s;
       const size_t nb = 16 * dim * B;
-      WPCD_CUDA_TRY(cudaMalloc(&cx.g, nb));
-      if (mixed) WPCD_CUDA_TRY(cudaMalloc(&cx.g32, nb / 2));
-      WPCD_CUDA_TRY(cudaMalloc(&cx.b, nb));
-      WPCD_CUDA_TRY(cudaMalloc(&cx.u, nb));
-      WPCD_CUDA_TRY(cudaMalloc(&cx.r, nb));
-      WPCD_CUDA_TRY(cudaMalloc(&cx.t, nb));
-      WPCD_CUDA_TRY(cudaMalloc(&cx.r0, sizeof(int) * B));
-      WPCD_CUDA_TRY(cudaMalloc(&cx.Dd, sizeof(double) * B));
-      WPCD_CUDA_TRY(cudaMalloc(&cx.pref, sizeof(double) * B));
-      WPCD_CUDA_TRY(cudaMalloc(&cx.amp, sizeof(double) * 6 * B));
+      WPCD_CUDA_TRY(pool_malloc(&cx.g, nb, s));
+      if (mixed) WPCD_CUDA_TRY(pool_malloc(&cx.g32, nb / 2, s));
+      WPCD_CUDA_TRY(pool_malloc(&cx.b, nb, s));
+      WPCD_CUDA_TRY(pool_malloc(&cx.u, nb, s));
+      WPCD_CUDA_TRY(pool_malloc(&cx.r, nb, s));
+      WPCD_CUDA_TRY(pool_malloc(&cx.t, nb, s));
+      WPCD_CUDA_TRY(pool_malloc(&cx.r0, sizeof(int) * B, s));
+      WPCD_CUDA_TRY(pool_malloc(&cx.Dd, sizeof(double) * B, s));
+      WPCD_CUDA_TRY(pool_malloc(&cx.pref, sizeof(double) * B, s));
+      WPCD_CUDA_TRY(pool_malloc(&cx.amp, sizeof(double) * 6 * B, s));
       BatchInfo bi;
       cudaEvent_t ev0, ev1;
       WPCD_CUDA_TRY(cudaEventCreate(&ev0));
@@ -1671,9 +1679,9 @@ wpcd_status solve(wpcd_problem *pr, const wpcd_P *Pc, const double *E, int n_E,
       wpcd_status st = batch_setup(pr, E + e0, B, cx, bi, s);
       if (st != WPCD_OK) return st;
       Workspace<double> ws64;
-      WPCD_CUDA_TRY(ws64.alloc(dim, B));
+      WPCD_CUDA_TRY(ws64.alloc(dim, B, s));
       DfWork dfw;
-      if (dfres) WPCD_CUDA_TRY(dfw.alloc(dim, B));
+      if (dfres) WPCD_CUDA_TRY(dfw.alloc(dim, B, s));
       // Born term on s, resolvent concurrently on a side stream
       struct Side {
         cudaStream_t s2 = nullptr;
@@ -1707,15 +1715,15 @@ wpcd_status solve(wpcd_problem *pr, const wpcd_P *Pc, const double *E, int n_E,
         const int m_in = opt.inner_iter > 0 ? opt.inner_iter : kDefaultInner;
         Krylov<float> kr;
         Krylov<double> k64;
-        WPCD_CUDA_TRY(kr.alloc(m_in, B, dim));
-        WPCD_CUDA_TRY(k64.alloc(1, B, dim, false));  // norms only
+        WPCD_CUDA_TRY(kr.alloc(m_in, B, dim, s));
+        WPCD_CUDA_TRY(k64.alloc(1, B, dim, s, false));  // norms only
         Workspace<float> ws32;
-        WPCD_CUDA_TRY(ws32.alloc(dim, B));
+        WPCD_CUDA_TRY(ws32.alloc(dim, B, s));
         st = solve_mixed(pr, P, opt, cx, kr, k64, ws64, ws32, dfres ? &dfw : nullptr, status, relres, n64, n32,
                          n_outer, warm, s);
       } else {
         Krylov<double> kr;
-        WPCD_CUDA_TRY(kr.alloc(opt.max_iter, B, dim));
+        WPCD_CUDA_TRY(kr.alloc(opt.max_iter, B, dim, s));
         st = solve_fp64(pr, P, opt, cx, kr, ws64, status, relres, conv, fallback, n64, warm, s);
       }
       if (st != WPCD_OK) return st;

@@ -164,10 +164,22 @@ wpcd_status tc_gemm(const wpcd_problem *pr, bool use_O, const float *G, const fl
 wpcd_status tc_check(const wpcd_problem *pr, cudaStream_t s);
 // df.cu: float-float ("FP64-class", about 48 significant bits) K application
 // on the FP32 pipe, for the refinement residual of the mixed solve
+// Work space of the solves: a stream-ordered pool per device that keeps
+// freed memory for the next solve (allocation from it takes microseconds
+// instead of a cudaMalloc's page mapping, and a free does not synchronise
+// the device).  The pool lives as long as the process.
+cudaError_t pool_malloc(void **p, size_t bytes, cudaStream_t s);
+void pool_free(void *p, cudaStream_t s);
+template <typename T>
+cudaError_t pool_malloc(T **p, size_t bytes, cudaStream_t s) {
+  return pool_malloc(reinterpret_cast<void **>(p), bytes, s);
+}
+
 struct DfWork {
   float *xh = nullptr, *xl = nullptr, *yh = nullptr, *yl = nullptr;  // [2 dim B] each
+  cudaStream_t st = nullptr;                                         // stream of the pool frees
   ~DfWork();
-  cudaError_t alloc(size_t dim, int B);
+  cudaError_t alloc(size_t dim, int B, cudaStream_t s);
 };
 wpcd_status df_prepare(wpcd_problem *pr, wpcd_P *P, cudaStream_t s);
 wpcd_status df_kapply(const wpcd_problem *pr, const wpcd_P *P, const double *g, const double *x, double *out, int B,
