@@ -28,7 +28,10 @@
  *
  * Ownership: the library allocates and owns everything behind a handle
  * (device memory via cudaMalloc on the problem's device) until the matching
- * *_destroy.  Caller arrays are never retained.  Pointers documented as
+ * *_destroy.  The solves take their work space from a stream-ordered memory
+ * pool per device, owned by the library: freed blocks stay in the pool for
+ * the next solve (no cudaFree, no device synchronisation) until the process
+ * exits.  Caller arrays are never retained.  Pointers documented as
  * "device" must be device (or managed) memory on the problem's device;
  * "host" pointers are ordinary host memory.  `stream` is a cudaStream_t
  * (NULL: the legacy default stream); calls that return results to host
@@ -259,8 +262,8 @@ wpcd_status wpcd_solve(wpcd_problem *pr, const wpcd_P *P, const double *E, int n
  * (interleaved) results; stats: NULL, or host array of n_prob pointers each
  * NULL or to [n_E[g]] stats.  opts as for wpcd_solve, with method
  * WPCD_SUM_KRYLOV, batch 0 and no vectors (EINVAL otherwise); 1 <= n_prob
- * <= WPCD_GROUP_MAX.  Allocates its work space with cudaMalloc and frees it
- * before returning.  Returns the worst per-energy status (ENOCONV and
+ * <= WPCD_GROUP_MAX.  Work space from the library's pool (returned to it
+ * before this call returns).  Returns the worst per-energy status (ENOCONV and
  * EBREAKDOWN still deliver the best estimate). */
 wpcd_status wpcd_solve_batch(int n_prob, wpcd_problem *const *problems, const wpcd_P *const *P,
                              const double *const *E, const int *n_E, const wpcd_solve_opts *opts,
