@@ -4,6 +4,7 @@
 
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -38,7 +39,19 @@ void clear_error() {
   (void)cudaGetLastError();
 }
 
+// WPCD_POOL=0 takes the work space with cudaMalloc / cudaFree instead (for
+// tools that save and restore device allocations around a kernel, which
+// know plain allocations)
+static bool pool_enabled() {
+  static const bool on = [] {
+    const char *v = std::getenv("WPCD_POOL");
+    return !(v && std::strcmp(v, "0") == 0);
+  }();
+  return on;
+}
+
 cudaError_t pool_malloc(void **p, size_t bytes, cudaStream_t s) {
+  if (!pool_enabled()) return cudaMalloc(p, bytes ? bytes : 16);
   static std::mutex mu;
   static cudaMemPool_t pools[64] = {};
   int dev = 0;
@@ -64,7 +77,11 @@ cudaError_t pool_malloc(void **p, size_t bytes, cudaStream_t s) {
 }
 
 void pool_free(void *p, cudaStream_t s) {
-  if (p) cudaFreeAsync(p, s);
+  if (!p) return;
+  if (pool_enabled())
+    cudaFreeAsync(p, s);
+  else
+    cudaFree(p);
 }
 
 static void free_tables(DeviceTables &d) {

@@ -402,24 +402,15 @@ __global__ void __launch_bounds__(GV_THREADS) gdot_kernel(const GMeta *__restric
 #pragma unroll
     for (int c = 0; c < GJC; ++c) sx[c] = sy[c] = T(0);
     if (tx < B) {
-      // two rows per iteration: both rows' loads are in flight together
-      const int stride = nb * RB;
-      for (int r = lb * RB + ty; r < rows; r += 2 * stride) {
-        const bool two = r + stride < rows;
-        const size_t f1 = (size_t)off + (size_t)r * B + tx;
-        const size_t f2 = (size_t)off + (size_t)(two ? r + stride : r) * B + tx;
-        const auto b1 = w[f1];
-        auto b2 = w[f2];
-        if (!two) b2.x = b2.y = T(0);
+      for (int r = lb * RB + ty; r < rows; r += nb * RB) {
+        const size_t f = (size_t)off + (size_t)r * B + tx;
+        const auto b = w[f];
 #pragma unroll
         for (int c = 0; c < GJC; ++c) {
           if (j0 + c < nv) {
-            const auto a1 = V[(size_t)(j0 + c) * ld + f1];
-            const auto a2 = V[(size_t)(j0 + c) * ld + f2];
-            sx[c] = fma(a1.x, b1.x, fma(a1.y, b1.y, sx[c]));
-            sy[c] = fma(a1.x, b1.y, fma(-a1.y, b1.x, sy[c]));
-            sx[c] = fma(a2.x, b2.x, fma(a2.y, b2.y, sx[c]));
-            sy[c] = fma(a2.x, b2.y, fma(-a2.y, b2.x, sy[c]));
+            const auto a = V[(size_t)(j0 + c) * ld + f];
+            sx[c] = fma(a.x, b.x, fma(a.y, b.y, sx[c]));
+            sy[c] = fma(a.x, b.y, fma(-a.y, b.x, sy[c]));
           }
         }
       }
@@ -644,6 +635,8 @@ struct DevFree {
 struct Group {
   int n = 0, n_ch = 0, S = 0, prec = WPCD_FP64, Bmax = 1;
   bool even = true;        // every B_g and every segment offset even
+  bool tc = false;         // FP32 block products on the tensor cores (tc_gemm_group)
+  std::vector<TcGroupProb> tcp;
   int64_t L = 0;           // complex elements of one concatenated vector
   GMeta meta;              // host copy
   std::vector<GProb> probs;
@@ -822,6 +815,15 @@ wpcd_status gtune(const Group &gr, int mode, Run run, cudaStream_t s, SpmmConfig
 template <typename T>
 wpcd_status gkapply(const Group &gr, const T *g, const T *x, T *out, const T *sub, T *wy, T *wz,
                     cudaStream_t s) {
+  if (sizeof(T) == 4 && gr.tc) {  // FP32: both block products on the tensor cores, one launch each
+    const float *gf = reinterpret_cast<const float *>(g), *xf = reinterpret_cast<const float *>(x);
+    wpcd_status st = tc_gemm_group(gr.tcp.data(), gr.n, false, gf, xf, nullptr, reinterpret_cast<float *>(wy), s);
+    if (st == WPCD_OK) st = gspmm<T>(gr, wy, wz, gr.cfg32, s);
+    if (st == WPCD_OK)
+      st = tc_gemm_group(gr.tcp.data(), gr.n, true, nullptr, reinterpret_cast<const float *>(wz),
+                         reinterpret_cast<const float *>(sub), reinterpret_cast<float *>(out), s);
+    return st;
+  }
   ggemm<T>(gr, false, g != nullptr, false, x, g, nullptr, wy, s);
   wpcd_status st = gspmm<T>(gr, wy, wz, sizeof(T) == 4 ? gr.cfg32 : gr.cfg64, s);
   if (st != WPCD_OK) return st;
@@ -1257,6 +1259,20 @@ wpcd_status solve_group(int n_prob, wpcd_problem *const *prs, const wpcd_P *cons
     gr.Bmax = std::max(gr.Bmax, B);
     gr.even = gr.even && B % 2 == 0 && mt.eoff[g] % 2 == 0;
   }
+  // FP32 block products of the inner cycles on the tensor cores when every
+  // problem fits (N <= 512) and every segment is 16-byte aligned
+  if (mixed && tc_enabled() && gr.even) {
+    bool ok = true;
+    for (int g = 0; g < n_prob; ++g) ok = ok && tc_supported(prs[g]);
+    if (ok) {
+      for (int g = 0; g < n_prob; ++g) {
+        wpcd_status st = tc_prepare(const_cast<wpcd_problem *>(prs[g]), s);
+        if (st != WPCD_OK) return st;
+        gr.tcp.push_back(TcGroupProb{prs[g], 2 * mt.eoff[g], 2LL * prs[g]->M * n_E[g]});
+      }
+      gr.tc = true;
+    }
+  }
   gr.S = mt.S = mt.sys[n_prob];
   gr.L = mt.eoff[n_prob];
   // dot-product blocks: about two per SM, split in proportion to segment size
@@ -1380,6 +1396,7 @@ wpcd_status solve_group(int n_prob, wpcd_problem *const *prs, const wpcd_P *cons
     st = gsolve_fp64(gr, opt, cx, kr, status, relres, conv, n64, s);
   }
   if (st != WPCD_OK) return st;
+  if (gr.tc && (st = tc_check(prs[0], s)) != WPCD_OK) return st;
   n64 += 1;  // the Born term
   gamplitude_kernel<<<(S + 127) / 128, 128, 0, s>>>(S, (const double2 *)cx.u, cx.idx0, cx.D, cx.pref, cx.amp);
   count_launches(1);

@@ -309,22 +309,15 @@ __global__ void __launch_bounds__(V_THREADS) bdot_kernel(int rows, int B, int nv
 #pragma unroll
     for (int c = 0; c < JC; ++c) sx[c] = sy[c] = T(0);
     if (e < B) {
-      // two rows per iteration: both rows' loads are in flight together
-      for (int r = blockIdx.x * RB + ty; r < rows; r += 2 * stride) {
-        const bool two = r + stride < rows;
-        const size_t f1 = (size_t)r * B + e, f2 = (size_t)(two ? r + stride : r) * B + e;
-        const C2 b1 = w[f1];
-        C2 b2 = w[f2];
-        if (!two) b2.x = b2.y = T(0);
+      for (int r = blockIdx.x * RB + ty; r < rows; r += stride) {
+        const size_t f = (size_t)r * B + e;
+        const C2 b = w[f];
 #pragma unroll
         for (int c = 0; c < JC; ++c) {
           if (j0 + c < nv) {
-            const C2 a1 = V[(size_t)(j0 + c) * ld + f1];
-            const C2 a2 = V[(size_t)(j0 + c) * ld + f2];
-            sx[c] = fma(a1.x, b1.x, fma(a1.y, b1.y, sx[c]));
-            sy[c] = fma(a1.x, b1.y, fma(-a1.y, b1.x, sy[c]));
-            sx[c] = fma(a2.x, b2.x, fma(a2.y, b2.y, sx[c]));
-            sy[c] = fma(a2.x, b2.y, fma(-a2.y, b2.x, sy[c]));
+            const C2 a = V[(size_t)(j0 + c) * ld + f];
+            sx[c] = fma(a.x, b.x, fma(a.y, b.y, sx[c]));
+            sy[c] = fma(a.x, b.y, fma(-a.y, b.x, sy[c]));
           }
         }
       }

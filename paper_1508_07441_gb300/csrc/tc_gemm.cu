@@ -33,6 +33,7 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <mutex>
 
 #include "common.cuh"
@@ -397,13 +398,90 @@ constexpr int WS_CONV = 128;                       // converter threads
 constexpr int WS_EPI = 128;                        // epilogue threads
 
 struct TcWsParams {
-  int n, RT, nK, n_cb, n_tiles, nsa, nsb, nr, n_acc;
-  int64_t ncol;
+  int RT, n_tiles, nsa, nsb, nr, n_acc;  // RT: the largest row-tile count of any tile
   uint32_t raw_bytes, tmem_cols;
-  const float *A;
+  int *err;
+};
+
+// one output tile: 128 columns (col0 ..) of one channel block C = A X'
+// ([n][ncol] floats at C), A packed as [nK][RT][hi | lo] TF32 blocks; the
+// panel chunks come from rows y0 + 16 c of the tensor maps
+struct WsTile {
+  int n, RT, nK, y0;
+  int64_t ncol, col0;
+  const float *A, *S;
+  float *C;
+  const CUtensorMap *tmx, *tmg;
+};
+
+// the tiles of one problem: t -> (channel, column block)
+struct WsTilesOne {
+  CUtensorMap tmx, tmg;  // X and G1 as [n_ch n rows][ncol floats], box 16 x 128
+  int n, RT, nK, n_cb;
+  int64_t ncol;
+  const float *A, *S;
+  float *C;
+  __device__ __forceinline__ WsTile get(int t) const {
+    WsTile T;
+    const int ch = t / n_cb;
+    T.n = n;
+    T.RT = RT;
+    T.nK = nK;
+    T.y0 = ch * n;
+    T.ncol = ncol;
+    T.col0 = (int64_t)(t % n_cb) * WS_BN;
+    T.A = A + (size_t)ch * nK * RT * (TC_A_BLOCK / 4);
+    const size_t blk = (size_t)ch * n * ncol;
+    T.S = S ? S + blk : nullptr;
+    T.C = C + blk;
+    T.tmx = &tmx;
+    T.tmg = &tmg;
+    return T;
+  }
+};
+
+// the tiles of a group of problems (the grouped solve): problem g owns
+// tiles toff[g] .. toff[g+1]-1 over (channel, column block) of its segment
+constexpr int WS_GROUP_MAX = WPCD_GROUP_MAX;
+struct alignas(64) WsProb {
+  CUtensorMap tmx, tmg;  // the segment's X and G1 as [n_ch n rows][ncol floats]
+  const float *A;        // packed A of the problem (all channels)
+  int64_t off;           // float offset of the segment in the group vectors
+  int64_t ncol;
+  int n, RT, nK, n_cb;
+};
+struct WsTilesGroup {
+  WsProb p[WS_GROUP_MAX];
+  int toff[WS_GROUP_MAX + 1];
+  int n_prob;
   const float *S;
   float *C;
-  int *err;
+  __device__ __forceinline__ WsTile get(int t) const {
+    int lo = 0, hi = n_prob - 1;  // largest g with toff[g] <= t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (toff[mid] <= t)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const WsProb &q = p[lo];
+    const int lt = t - toff[lo], ch = lt / q.n_cb;
+    WsTile T;
+    T.n = q.n;
+    T.RT = q.RT;
+    T.nK = q.nK;
+    T.y0 = ch * q.n;
+    T.ncol = q.ncol;
+    T.col0 = (int64_t)(lt % q.n_cb) * WS_BN;
+    T.A = q.A + (size_t)ch * q.nK * q.RT * (TC_A_BLOCK / 4);
+    const size_t blk = (size_t)q.off + (size_t)ch * q.n * q.ncol;
+    T.S = S ? S + blk : nullptr;
+    T.C = C + blk;
+    T.tmx = &q.tmx;
+    T.tmg = &q.tmg;
+    return T;
+  }
 };
 
 struct WsBars {
@@ -448,19 +526,19 @@ __device__ __forceinline__ bool ws_wait(uint64_t *bar, uint32_t parity, volatile
   return false;
 }
 
-// tmx, tmg: tensor maps of X and G1 as [n_ch n rows][ncol floats], box 16 x 128
-template <bool SCALE_G, bool SUB>
+// Tiles: WsTilesOne or WsTilesGroup (a parameter in the constant bank, so
+// that the tensor maps it holds have the address the TMA copies need)
+template <bool SCALE_G, bool SUB, class Tiles>
 __global__ void __launch_bounds__(WS_THREADS, 1)
-    tc_gemm_ws_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmg, TcWsParams p) {
+    tc_gemm_ws_kernel(const __grid_constant__ Tiles tiles, TcWsParams p) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) WsBars bars;
   __shared__ uint32_t tmem_holder;
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int n = p.n, RT = p.RT, nK = p.nK;
-  const int64_t ncol = p.ncol;
+  const int RTM = p.RT;  // A stage and accumulator stride (largest RT)
   unsigned char *a_ring = smem;
-  unsigned char *b_ring = smem + (size_t)p.nsa * RT * TC_A_BLOCK;
+  unsigned char *b_ring = smem + (size_t)p.nsa * RTM * TC_A_BLOCK;
   unsigned char *r_ring = b_ring + (size_t)p.nsb * WS_B_STAGE;
   const int my_tiles = (p.n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
 
@@ -505,10 +583,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
       bool ok = true;
       int q = 0;
       for (int lt = 0; lt < my_tiles && ok; ++lt) {
-        const int t = (int)blockIdx.x + lt * (int)gridDim.x;
-        const int ch = t / p.n_cb;
-        const int col0 = (t % p.n_cb) * WS_BN;
-        for (int c = 0; c < nK; ++c, ++q) {
+        const WsTile T = tiles.get((int)blockIdx.x + lt * (int)gridDim.x);
+        for (int c = 0; c < T.nK; ++c, ++q) {
           const int sr = q % p.nr;
           if (q >= p.nr && !(ok = ws_wait(&bars.r_empty[sr], (uint32_t)(q / p.nr - 1) & 1, &abort_flag, p.err)))
             break;
@@ -516,15 +592,15 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
           // next channel that a last chunk reaches are masked by the converters
           unsigned char *dst = r_ring + (size_t)sr * p.raw_bytes;
           expect_tx(&bars.r_full[sr], TC_KC * WS_BN * 4 * (SCALE_G ? 2u : 1u));
-          tma_2d(dst, &tmx, col0, ch * n + c * TC_KC, &bars.r_full[sr]);
-          if (SCALE_G) tma_2d(dst + TC_KC * WS_BN * 4, &tmg, col0, ch * n + c * TC_KC, &bars.r_full[sr]);
+          tma_2d(dst, T.tmx, (int)T.col0, T.y0 + c * TC_KC, &bars.r_full[sr]);
+          if (SCALE_G) tma_2d(dst + TC_KC * WS_BN * 4, T.tmg, (int)T.col0, T.y0 + c * TC_KC, &bars.r_full[sr]);
           last_r[sr] = q;
           const int sa = q % p.nsa;
           if (q >= p.nsa && !(ok = ws_wait(&bars.a_empty[sa], (uint32_t)(q / p.nsa - 1) & 1, &abort_flag, p.err)))
             break;
-          const uint32_t abytes = (uint32_t)RT * TC_A_BLOCK;
+          const uint32_t abytes = (uint32_t)T.RT * TC_A_BLOCK;
           expect_tx(&bars.a_full[sa], abytes);
-          bulk_g2s(a_ring + (size_t)sa * abytes, p.A + ((size_t)ch * nK + c) * RT * (TC_A_BLOCK / 4), abytes,
+          bulk_g2s(a_ring + (size_t)sa * RTM * TC_A_BLOCK, T.A + (size_t)c * T.RT * (TC_A_BLOCK / 4), abytes,
                    &bars.a_full[sa]);
           last_a[sa] = q;
         }
@@ -546,16 +622,17 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
         if (lt >= p.n_acc && !(ok = ws_wait(&bars.t_empty[buf], (uint32_t)(lt / p.n_acc - 1) & 1, &abort_flag, p.err)))
           break;
         tc_fence_after();
-        const uint32_t d0 = tmem + (uint32_t)(buf * RT * WS_BN);
-        for (int c = 0; c < nK; ++c, ++q) {
+        const WsTile T = tiles.get((int)blockIdx.x + lt * (int)gridDim.x);
+        const uint32_t d0 = tmem + (uint32_t)(buf * RTM * WS_BN);
+        for (int c = 0; c < T.nK; ++c, ++q) {
           const int sa = q % p.nsa, sb = q % p.nsb;
           if (!(ok = ws_wait(&bars.a_full[sa], (uint32_t)(q / p.nsa) & 1, &abort_flag, p.err))) break;
           if (!(ok = ws_wait(&bars.b_full[sb], (uint32_t)(q / p.nsb) & 1, &abort_flag, p.err))) break;
           tc_fence_after();
-          const uint32_t a0 = smem_u32(a_ring + (size_t)sa * RT * TC_A_BLOCK);
+          const uint32_t a0 = smem_u32(a_ring + (size_t)sa * RTM * TC_A_BLOCK);
           const uint32_t b0 = smem_u32(b_ring + (size_t)sb * WS_B_STAGE);
 #pragma unroll 1
-          for (int rt = 0; rt < RT; ++rt) {
+          for (int rt = 0; rt < T.RT; ++rt) {
             const uint32_t d = d0 + (uint32_t)(rt * WS_BN);
 #pragma unroll
             for (int ks = 0; ks < TC_KC / 8; ++ks) {
@@ -584,10 +661,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
     bool ok = true;
     int q = 0;
     for (int lt = 0; lt < my_tiles && ok; ++lt) {
-      const int t = (int)blockIdx.x + lt * (int)gridDim.x;
-      const int64_t col0 = (int64_t)(t % p.n_cb) * WS_BN;
-      const int valid_cols = (int)min((int64_t)WS_BN, ncol - col0);
-      for (int c = 0; c < nK; ++c, ++q) {
+      const WsTile T = tiles.get((int)blockIdx.x + lt * (int)gridDim.x);
+      const int64_t col0 = T.col0;
+      const int valid_cols = (int)min((int64_t)WS_BN, T.ncol - col0);
+      for (int c = 0; c < T.nK; ++c, ++q) {
         const int sr = q % p.nr, sb = q % p.nsb;
         if (!(ok = ws_wait(&bars.r_full[sr], (uint32_t)(q / p.nr) & 1, &abort_flag, p.err))) break;
         const float2 *rx = reinterpret_cast<const float2 *>(r_ring + (size_t)sr * p.raw_bytes);
@@ -601,7 +678,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
 #pragma unroll
           for (int qq = 0; qq < 4; ++qq) {
             const int kl = kg * 4 + qq;
-            const bool in = col_in && c * TC_KC + kl < n;
+            const bool in = col_in && c * TC_KC + kl < T.n;
             xv[it][qq] = in ? rx[kl * (WS_BN / 2) + (nn >> 1)] : make_float2(0.f, 0.f);
             if (SCALE_G) gv[it][qq] = in ? rg[kl * (WS_BN / 2) + (nn >> 1)] : make_float2(0.f, 0.f);
           }
@@ -649,40 +726,40 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
     const int lg = warp & 3;
     bool ok = true;
     for (int lt = 0; lt < my_tiles && ok; ++lt) {
-      const int t = (int)blockIdx.x + lt * (int)gridDim.x;
-      const int ch = t / p.n_cb;
-      const int64_t col0 = (int64_t)(t % p.n_cb) * WS_BN;
+      const WsTile T = tiles.get((int)blockIdx.x + lt * (int)gridDim.x);
+      const int n = T.n;
+      const int64_t col0 = T.col0, ncol = T.ncol;
       const int buf = lt % p.n_acc;
       ok = ws_wait(&bars.t_full[buf], (uint32_t)(lt / p.n_acc) & 1, &abort_flag, p.err);
       // the TMEM loads below are warp-collective: the warp decides together
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) break;
       tc_fence_after();
-      for (int rt = 0; rt < RT; ++rt) {
+      for (int rt = 0; rt < T.RT; ++rt) {
         const int row = rt * TC_M + lg * 32 + lane;
         for (int cb = 0; cb < WS_BN; cb += 16) {
-          const size_t o = ((size_t)ch * n + min(row, n - 1)) * ncol + col0 + cb;
+          const size_t o = (size_t)min(row, n - 1) * ncol + col0 + cb;
           // ncol % 4 == 0 and 16-byte aligned C and S on this path
           const bool full = col0 + cb + 16 <= ncol;
           float4 sv[4];
           if (SUB && full && row < n)  // the S loads go out before the TMEM read
 #pragma unroll
-            for (int qq = 0; qq < 4; ++qq) sv[qq] = *reinterpret_cast<const float4 *>(p.S + o + 4 * qq);
+            for (int qq = 0; qq < 4; ++qq) sv[qq] = *reinterpret_cast<const float4 *>(T.S + o + 4 * qq);
           float v[16];
           __syncwarp();  // the TMEM load is warp-collective
-          tc_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(buf * RT * WS_BN + rt * WS_BN + cb), v);
+          tc_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(buf * RTM * WS_BN + rt * WS_BN + cb), v);
           if (row < n) {
             if (full) {
 #pragma unroll
               for (int qq = 0; qq < 4; ++qq) {
                 float4 w = make_float4(v[4 * qq], v[4 * qq + 1], v[4 * qq + 2], v[4 * qq + 3]);
                 if (SUB) w = make_float4(sv[qq].x - w.x, sv[qq].y - w.y, sv[qq].z - w.z, sv[qq].w - w.w);
-                *reinterpret_cast<float4 *>(p.C + o + 4 * qq) = w;
+                *reinterpret_cast<float4 *>(T.C + o + 4 * qq) = w;
               }
             } else {
 #pragma unroll
               for (int j = 0; j < 16; ++j)
-                if (col0 + cb + j < ncol) p.C[o + j] = SUB ? p.S[o + j] - v[j] : v[j];
+                if (col0 + cb + j < ncol) T.C[o + j] = SUB ? T.S[o + j] - v[j] : v[j];
             }
           }
         }
@@ -778,6 +855,49 @@ bool panel_map(CUtensorMap *m, const float *base, int64_t rows, int64_t ncol) {
 bool attr_set[64] = {};
 int sm_count[64] = {};
 
+// the persistent kernel over a tile source: rings sized for the largest
+// row-tile count RT, one CTA per SM (at most one per tile)
+template <class Tiles>
+wpcd_status launch_ws(const Tiles &tiles, int n_tiles, int RT, bool scale_g, bool sub, int *err, int device,
+                      cudaStream_t s) {
+  const TcWsShape w = tc_ws_shape(RT, scale_g);
+  TcWsParams q{};
+  q.RT = RT;
+  q.n_tiles = n_tiles;
+  q.nsa = w.nsa;
+  q.nsb = w.nsb;
+  q.nr = w.nr;
+  q.n_acc = w.n_acc;
+  q.raw_bytes = w.raw_bytes;
+  q.tmem_cols = w.tmem_cols;
+  q.err = err;
+  const int grid = std::max(1, std::min(n_tiles, sm_count[device] > 0 ? sm_count[device] : 152));
+  if (scale_g)
+    tc_gemm_ws_kernel<true, false, Tiles><<<grid, WS_THREADS, w.smem, s>>>(tiles, q);
+  else if (sub)
+    tc_gemm_ws_kernel<false, true, Tiles><<<grid, WS_THREADS, w.smem, s>>>(tiles, q);
+  else
+    tc_gemm_ws_kernel<false, false, Tiles><<<grid, WS_THREADS, w.smem, s>>>(tiles, q);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? WPCD_OK : cuda_error(e, "tensor-core gemm launch");
+}
+
+// the shared-memory limit of the persistent kernels (tc_ws_shape: at most 216 KB)
+template <class Tiles>
+cudaError_t set_ws_attributes() {
+  const int ws_bytes = 216 * 1024;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(tc_gemm_ws_kernel<true, false, Tiles>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                ws_bytes)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(tc_gemm_ws_kernel<false, true, Tiles>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                ws_bytes)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(tc_gemm_ws_kernel<false, false, Tiles>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              ws_bytes);
+}
+
+
 bool tc_supported(const wpcd_problem *pr) { return pr->N >= 1 && pr->N <= 4 * TC_M; }
 
 // the FP32 channel-block products run on the tensor cores unless
@@ -813,13 +933,8 @@ wpcd_status tc_prepare(wpcd_problem *pr, cudaStream_t s) {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes));
     WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<128, false, true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes));
-    const int ws_bytes = 216 * 1024;  // tc_ws_shape: at most 216 KB
-    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_ws_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       ws_bytes));
-    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_ws_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       ws_bytes));
-    WPCD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_ws_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       ws_bytes));
+    WPCD_CUDA_TRY(set_ws_attributes<WsTilesOne>());
+    WPCD_CUDA_TRY(set_ws_attributes<WsTilesGroup>());
     WPCD_CUDA_TRY(cudaDeviceGetAttribute(&sm_count[pr->device], cudaDevAttrMultiProcessorCount, pr->device));
     attr_set[pr->device] = true;
   }
@@ -854,35 +969,20 @@ wpcd_status tc_gemm(const wpcd_problem *pr, bool use_O, const float *G, const fl
   // aligned bases (every row, and every column tile, then starts aligned)
   const bool raw = vec_out && aligned16(X) && (!G || aligned16(G));
   if (raw) {
-    const TcWsShape w = tc_ws_shape(sh.RT, G != nullptr);
-    TcWsParams q{};
-    q.n = pr->N;
-    q.RT = sh.RT;
-    q.nK = sh.nK;
-    q.n_cb = (int)((ncol + WS_BN - 1) / WS_BN);
-    q.n_tiles = pr->n_ch * q.n_cb;
-    q.nsa = w.nsa;
-    q.nsb = w.nsb;
-    q.nr = w.nr;
-    q.n_acc = w.n_acc;
-    q.ncol = ncol;
-    q.raw_bytes = w.raw_bytes;
-    q.tmem_cols = w.tmem_cols;
-    q.A = p.A;
-    q.S = S;
-    q.C = C;
-    q.err = p.err;
-    CUtensorMap tmx{}, tmg{};
+    WsTilesOne tiles{};
+    tiles.n = pr->N;
+    tiles.RT = sh.RT;
+    tiles.nK = sh.nK;
+    tiles.n_cb = (int)((ncol + WS_BN - 1) / WS_BN);
+    tiles.ncol = ncol;
+    tiles.A = p.A;
+    tiles.S = S;
+    tiles.C = C;
     const int64_t rows = (int64_t)pr->n_ch * pr->N;
-    if (!panel_map(&tmx, X, rows, ncol) || (G && !panel_map(&tmg, G, rows, ncol)))
+    if (!panel_map(&tiles.tmx, X, rows, ncol) || (G && !panel_map(&tiles.tmg, G, rows, ncol)))
       return set_error(WPCD_ECUDA, "tensor map encoding failed");
-    const int grid = std::max(1, std::min(q.n_tiles, sm_count[pr->device] > 0 ? sm_count[pr->device] : 152));
-    if (G)
-      tc_gemm_ws_kernel<true, false><<<grid, WS_THREADS, w.smem, s>>>(tmx, tmg, q);
-    else if (S)
-      tc_gemm_ws_kernel<false, true><<<grid, WS_THREADS, w.smem, s>>>(tmx, tmg, q);
-    else
-      tc_gemm_ws_kernel<false, false><<<grid, WS_THREADS, w.smem, s>>>(tmx, tmg, q);
+    wpcd_status st = launch_ws(tiles, pr->n_ch * tiles.n_cb, sh.RT, G != nullptr, S != nullptr, p.err, pr->device, s);
+    if (st != WPCD_OK) return st;
   } else {
     p.vec_out = vec_out;
     const size_t smem = (size_t)sh.stages * sh.stage_bytes;
@@ -897,6 +997,52 @@ wpcd_status tc_gemm(const wpcd_problem *pr, bool use_O, const float *G, const fl
   count_launches(1);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? WPCD_OK : cuda_error(e, "tensor-core gemm launch");
+}
+
+// C = A X' (or S - A X') for every (problem, channel) block of a group in
+// one persistent launch; problem g's vectors are the segment at float
+// offset off[g] of X, G, S and C ([n_ch][N][ncol] floats), 16-byte aligned
+// with ncol % 4 == 0; every problem prepared (tc_prepare), N <= 512
+wpcd_status tc_gemm_group(const TcGroupProb *gp, int n_prob, bool use_O, const float *G, const float *X,
+                          const float *S, float *C, cudaStream_t s) {
+  if (n_prob < 1 || n_prob > WS_GROUP_MAX) return set_error(WPCD_EINVAL, "bad tensor-core group size");
+  auto aligned16 = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+  // about 21 KB: held on the heap, passed by value as the kernel parameter
+  std::unique_ptr<WsTilesGroup> tiles(new WsTilesGroup());
+  tiles->n_prob = n_prob;
+  tiles->S = S;
+  tiles->C = C;
+  tiles->toff[0] = 0;
+  int RTmax = 1;
+  for (int g = 0; g < n_prob; ++g) {
+    const wpcd_problem *pr = gp[g].pr;
+    const int64_t off = gp[g].off, ncol = gp[g].ncol;
+    if (!pr->d.O_tc || !tc_supported(pr)) return set_error(WPCD_EINVAL, "tensor-core operands not prepared");
+    if (ncol % 4 != 0 || !aligned16(X + off) || !aligned16(C + off) || (G && !aligned16(G + off)) ||
+        (S && !aligned16(S + off)))
+      return set_error(WPCD_EINVAL, "tensor-core group segments must be 16-byte aligned");
+    const TcShape sh = tc_shape(pr->N);
+    WsProb &q = tiles->p[g];
+    q.A = use_O ? pr->d.O_tc : pr->d.Vt_tc;
+    q.off = off;
+    q.ncol = ncol;
+    q.n = pr->N;
+    q.RT = sh.RT;
+    q.nK = sh.nK;
+    q.n_cb = (int)((ncol + WS_BN - 1) / WS_BN);
+    const int64_t rows = (int64_t)pr->n_ch * pr->N;
+    if (!panel_map(&q.tmx, X + off, rows, ncol) || (G && !panel_map(&q.tmg, G + off, rows, ncol)))
+      return set_error(WPCD_ECUDA, "tensor map encoding failed");
+    tiles->toff[g + 1] = tiles->toff[g] + pr->n_ch * q.n_cb;
+    RTmax = std::max(RTmax, sh.RT);
+  }
+  const wpcd_problem *pr0 = gp[0].pr;
+  wpcd_status st = launch_ws(*tiles, tiles->toff[n_prob], RTmax, G != nullptr, S != nullptr, pr0->d.tc_err,
+                             pr0->device, s);
+  if (st != WPCD_OK) return st;
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? WPCD_OK : cuda_error(e, "tensor-core group gemm launch");
 }
 
 // nonzero if a tensor-core GEMM of this problem ran out of a wait limit

@@ -159,6 +159,14 @@ wpcd_status resolvent_minor(const wpcd_problem *pr, const double *E, int n_E, do
 bool tc_supported(const wpcd_problem *pr);
 bool tc_enabled();
 wpcd_status tc_prepare(wpcd_problem *pr, cudaStream_t s);
+// one problem of a grouped tensor-core product: its vectors are the segment
+// at float offset off of the group vectors, [n_ch][N][ncol] floats
+struct TcGroupProb {
+  const wpcd_problem *pr;
+  int64_t off, ncol;
+};
+wpcd_status tc_gemm_group(const TcGroupProb *gp, int n_prob, bool use_O, const float *G, const float *X,
+                          const float *S, float *C, cudaStream_t s);
 wpcd_status tc_gemm(const wpcd_problem *pr, bool use_O, const float *G, const float *X, const float *S, float *C,
                     int64_t ncol, cudaStream_t s);
 wpcd_status tc_check(const wpcd_problem *pr, cudaStream_t s);

@@ -104,6 +104,27 @@ def test_group_float_float_odd_segment_offsets(W, orc):
         assert np.max(np.abs(u - ref) / np.abs(ref)) < 1e-8
 
 
+def test_group_tensor_core_products(W, orc, monkeypatch):
+    """An even group (every batch even, so every segment is 16-byte aligned)
+    runs its FP32 block products as one grouped tensor-core launch each, over
+    problems of one and two 128-row tiles; the amplitudes match the oracle
+    and the same group with the SIMT products (WPCD_GEMM=simt)."""
+    shapes = [(130, 20), (40, 36), (90, 70)]
+    energies = [[0.4, 2.6], [-0.2, 0.8, 1.5, 3.9], [0.3, 1.1, 2.0, 2.7, 3.3, 4.6]]
+    items = [_make(W, orc, N, M) for N, M in shapes]
+    args = ([i[0] for i in items], [i[1] for i in items], energies)
+    U, stats, st = W.wpcd_solve_batch(*args, tol=1e-12, precision=W.WPCD_SOLVE_MIXED)
+    assert st == W.WPCD_OK
+    monkeypatch.setenv("WPCD_GEMM", "simt")
+    Us, _, st2 = W.wpcd_solve_batch(*args, tol=1e-12, precision=W.WPCD_SOLVE_MIXED)
+    assert st2 == W.WPCD_OK
+    for (pr, P, opr), E, u, us, sl in zip(items, energies, U, Us, stats):
+        assert all(s.status == W.WPCD_OK and s.relres <= 1e-12 for s in sl)
+        ref = _oracle(opr, E)
+        assert np.max(np.abs(u - ref) / np.abs(ref)) < 1e-8
+        assert np.max(np.abs(u - us) / np.abs(us)) < 1e-9
+
+
 def test_group_equals_per_problem_solves(W, group):
     items, energies = group
     U, _, _ = W.wpcd_solve_batch([i[0] for i in items], [i[1] for i in items], energies,
