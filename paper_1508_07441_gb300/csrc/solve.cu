@@ -84,7 +84,9 @@ __device__ double phi_noconst(double qa, double qb, double a) {
 }
 
 struct ResParams {
-  int n_ch, N, M, n_E, minor;  // minor: energy index innermost
+  int n_ch, N, M, n_E, minor;  // n_E: distinct on-shell bins; minor: energy index innermost
+  int n_out;                   // energies of the output (the bins' energies, uoff / elist)
+  const int *uoff, *elist;     // bin u serves energies elist[uoff[u] .. uoff[u+1]-1]
   const double *qe, *eps;
   const double *Elo, *Ehi;     // per energy
   const double *gl8_t, *gl8_w; // 8-point GL rule
@@ -112,10 +114,13 @@ __global__ void resolvent_kernel(ResParams R, double *g) {
   const int dim = R.n_ch * R.N * R.M;
   const int64_t total = (int64_t)R.n_E * dim;
   const int nchk = R.n_ch * R.N;
-  // threads run over (energy, q-bin j, pseudostate ch*N + k) with the
-  // pseudostate fastest: a warp shares the energy and the bin, so its lanes
-  // mostly take the same branch below (the writes are scattered; their
-  // traffic is small next to the arithmetic)
+  // threads run over (on-shell bin, q-bin j, pseudostate ch*N + k) with the
+  // pseudostate fastest: a warp shares the energy bin and the q-bin, so its
+  // lanes mostly take the same branch below.  G1 depends on an energy only
+  // through its on-shell bin (E_lo, E_hi: the average over that energy bin,
+  // Sec. 2.3), so each distinct bin is computed once and written for every
+  // energy in it (the writes are scattered; their traffic is small next to
+  // the arithmetic)
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int chk = (int)(idx % nchk);
@@ -123,7 +128,6 @@ __global__ void resolvent_kernel(ResParams R, double *g) {
     const int j = (int)(rest % R.M);
     const int e = (int)(rest / R.M);
     const int r = chk * R.M + j;
-    const int64_t out = R.minor ? (int64_t)r * R.n_E + e : (int64_t)e * dim + r;
     double ek = R.eps[chk];
     double Elo = R.Elo[e], Ehi = R.Ehi[e], D = Ehi - Elo;
     double qa = R.qe[j], qb = R.qe[j + 1];
@@ -189,8 +193,12 @@ __global__ void resolvent_kernel(ResParams R, double *g) {
       double a = fmax(qa, lo), b = fmin(qb, hi);
       if (b > a) im = -kPi * ((b - a) * (b * b + b * a + a * a) * kThird) * inv;
     }
-    g[2 * out] = re;
-    g[2 * out + 1] = im;
+    for (int k = R.uoff[e]; k < R.uoff[e + 1]; ++k) {
+      const int eo = R.elist[k];
+      const int64_t out = R.minor ? (int64_t)r * R.n_out + eo : (int64_t)eo * dim + r;
+      g[2 * out] = re;
+      g[2 * out + 1] = im;
+    }
   }
 }
 
@@ -862,51 +870,76 @@ wpcd_status resolvent_impl(const wpcd_problem *pr, const double *E, int n_E, dou
                            int *j0, double *D, cudaStream_t s, int max_blocks = 152 * 16) {
   if (n_E < 0 || (n_E > 0 && (!E || !g))) return set_error(WPCD_EINVAL, "bad resolvent arguments");
   if (n_E == 0) return WPCD_OK;
-  std::vector<double> lohi(2 * (size_t)n_E + 30);  // E_lo, E_hi, 8-, 4- and 3-point GL rules
+  // distinct on-shell bins (in order of first appearance) and their energies
+  std::vector<int> jj(n_E), bin_of(pr->M, -1), uoff, elist(n_E);
+  std::vector<double> ulo, uhi;
   for (int e = 0; e < n_E; ++e) {
-    int jj;
     double lo, hi;
-    wpcd_status st = onshell(pr, E[e], &jj, &lo, &hi, nullptr);
+    wpcd_status st = onshell(pr, E[e], &jj[e], &lo, &hi, nullptr);
     if (st != WPCD_OK) return st;
-    lohi[e] = lo;
-    lohi[n_E + e] = hi;
-    if (j0) j0[e] = jj;
+    if (bin_of[jj[e]] < 0) {
+      bin_of[jj[e]] = (int)ulo.size();
+      ulo.push_back(lo);
+      uhi.push_back(hi);
+    }
+    if (j0) j0[e] = jj[e];
     if (D) D[e] = hi - lo;
   }
-  gauss_legendre(8, lohi.data() + 2 * n_E, lohi.data() + 2 * n_E + 8);
-  gauss_legendre(4, lohi.data() + 2 * n_E + 16, lohi.data() + 2 * n_E + 20);
-  gauss_legendre(3, lohi.data() + 2 * n_E + 24, lohi.data() + 2 * n_E + 27);
+  const int n_U = (int)ulo.size();
+  uoff.assign(n_U + 1, 0);
+  for (int e = 0; e < n_E; ++e) ++uoff[bin_of[jj[e]] + 1];
+  for (int u = 0; u < n_U; ++u) uoff[u + 1] += uoff[u];
+  {
+    std::vector<int> fill(uoff.begin(), uoff.end() - 1);
+    for (int e = 0; e < n_E; ++e) elist[fill[bin_of[jj[e]]]++] = e;
+  }
+  // staging: E_lo, E_hi per bin, 8-, 4- and 3-point GL rules; the shell
+  // table; the bin -> energies lists
+  const int64_t n_shell = (int64_t)n_U * pr->n_ch * pr->N;
+  std::vector<double> lohi(2 * (size_t)n_U + 30);
+  std::copy(ulo.begin(), ulo.end(), lohi.begin());
+  std::copy(uhi.begin(), uhi.end(), lohi.begin() + n_U);
+  gauss_legendre(8, lohi.data() + 2 * n_U, lohi.data() + 2 * n_U + 8);
+  gauss_legendre(4, lohi.data() + 2 * n_U + 16, lohi.data() + 2 * n_U + 20);
+  gauss_legendre(3, lohi.data() + 2 * n_U + 24, lohi.data() + 2 * n_U + 27);
+  const size_t shell_at = (lohi.size() + 3) & ~(size_t)3;  // in doubles, 32-byte aligned
+  const size_t ints_at = shell_at + 4 * (size_t)n_shell;    // in doubles
+  std::vector<int> ints(uoff);
+  ints.insert(ints.end(), elist.begin(), elist.end());
   WPCD_CUDA_TRY(cudaSetDevice(pr->device));
-  const int64_t n_shell = (int64_t)n_E * pr->n_ch * pr->N;
   double *d_lohi = nullptr;
-  WPCD_CUDA_TRY(cudaMallocAsync(&d_lohi, sizeof(double) * (lohi.size() + 4 * n_shell + 4), s));
+  WPCD_CUDA_TRY(cudaMallocAsync(&d_lohi, sizeof(double) * ints_at + sizeof(int) * ints.size(), s));
   WPCD_CUDA_TRY(cudaMemcpyAsync(d_lohi, lohi.data(), sizeof(double) * lohi.size(), cudaMemcpyHostToDevice, s));
+  int *d_ints = reinterpret_cast<int *>(d_lohi + ints_at);
+  WPCD_CUDA_TRY(cudaMemcpyAsync(d_ints, ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice, s));
   ResParams R{};
   R.n_ch = pr->n_ch;
   R.N = pr->N;
   R.M = pr->M;
-  R.n_E = n_E;
+  R.n_E = n_U;
+  R.n_out = n_E;
   R.minor = minor;
   R.qe = pr->d.qe;
   R.eps = pr->d.eps;
   R.Elo = d_lohi;
-  R.Ehi = d_lohi + n_E;
-  R.gl8_t = d_lohi + 2 * n_E;
-  R.gl8_w = d_lohi + 2 * n_E + 8;
-  R.gl4_t = d_lohi + 2 * n_E + 16;
-  R.gl4_w = d_lohi + 2 * n_E + 20;
-  R.gl3_t = d_lohi + 2 * n_E + 24;
-  R.gl3_w = d_lohi + 2 * n_E + 27;
-  // 32-byte aligned after the tables (cudaMallocAsync returns 256-byte aligned)
-  R.shell = reinterpret_cast<double4 *>(d_lohi + ((lohi.size() + 3) & ~(size_t)3));
+  R.Ehi = d_lohi + n_U;
+  R.gl8_t = d_lohi + 2 * n_U;
+  R.gl8_w = d_lohi + 2 * n_U + 8;
+  R.gl4_t = d_lohi + 2 * n_U + 16;
+  R.gl4_w = d_lohi + 2 * n_U + 20;
+  R.gl3_t = d_lohi + 2 * n_U + 24;
+  R.gl3_w = d_lohi + 2 * n_U + 27;
+  R.shell = reinterpret_cast<double4 *>(d_lohi + shell_at);
+  R.uoff = d_ints;
+  R.elist = d_ints + n_U + 1;
   res_shell_kernel<<<grid_for(n_shell, 256), 256, 0, s>>>(R);
-  int64_t total = (int64_t)n_E * pr->n_ch * pr->N * pr->M;
+  int64_t total = (int64_t)n_U * pr->n_ch * pr->N * pr->M;
   resolvent_kernel<<<grid_for(total, 256, max_blocks), 256, 0, s>>>(R, g);
   count_launches(2);
   cudaError_t e = cudaGetLastError();
   cudaFreeAsync(d_lohi, s);
   // a copy from pageable memory returns once the data is staged, so the
-  // host vector may go; no synchronisation (the work stays asynchronous)
+  // host vectors may go; no synchronisation (the work stays asynchronous)
   if (e != cudaSuccess) return cuda_error(e, "resolvent launch");
   return WPCD_OK;
 }

@@ -120,6 +120,26 @@ def test_resolvent_matches_oracle(W, orc, E):
     assert np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)) < 1e-9
 
 
+def test_resolvent_many_energies_shared_bins(W, orc):
+    """Several energies, some in the same on-shell bin and out of order: G1
+    is computed once per bin and written for each of its energies; every
+    energy's block matches the oracle's G1 at that energy."""
+    import torch
+
+    pe, qe = _inputs(30, 40)
+    pr = W.Problem(pe, qe, 4, 4, 16, 3, (-6.0,), (1.0,))
+    E = [0.5, 3.0, 0.5001, -0.3, 2.9999, 0.52, 0.5]
+    g = torch.zeros(2 * pr.dim * len(E), dtype=torch.float64, device="cuda")
+    j0, D = pr.wpcd_resolvent(E, g)
+    assert len(set(j0)) < len(E)  # some bins are shared
+    eps = np.stack([pr.wpcd_problem_pair(l)[0] for l in range(3)])
+    got = g.cpu().numpy().view(np.complex128).reshape(len(E), 3, 30, 40)
+    for k, e in enumerate(E):
+        ref, j0r, Dr = orc.G1(eps, qe, e, pr.eps_bound)
+        assert j0[k] == j0r
+        assert np.max(np.abs(got[k] - ref) / np.maximum(np.abs(ref), 1e-300)) < 1e-9
+
+
 def test_kapply_matches_oracle(W, orc):
     import torch
     from paper_1508_07441_gb300 import inputs
