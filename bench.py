@@ -300,11 +300,13 @@ def kernel_rooflines(W, pr, w, phases, n_nodes, n_e, stream, flush, peaks, f_sm,
     # refinement residual and Born term: float-float SpMM and channel products
     ms = _time_kernel(stream, flush, lambda: pr.wpcd_spmm(P, x64, y64, n_e, mode=W.WPCD_SPMM_FF, stream=stream,
                                                            timed=True))
-    entry("spmm_df_kernel", "alu", spmm_flops / (ms * 1e-3) / 1e12, ff, "TFLOP/s", ms, n64,
+    # per step at the full batch: the refinement residuals (n64 - 1 of them);
+    # the Born term runs once per distinct on-shell bin, in smaller launches
+    entry("spmm_df_kernel", "alu", spmm_flops / (ms * 1e-3) / 1e12, ff, "TFLOP/s", ms, n64 - 1,
           f"4 n_pairs nnz B = {spmm_flops:.3e} FP64-equivalent flops in float-float", srcff)
     ms = _time_kernel(stream, flush, lambda: pr.wpcd_channel_gemm(1, W.WPCD_GEMM_FF, None, x64, y64, n_e,
                                                                    stream=stream, timed=True))
-    entry("gemm_df_kernel", "alu", gemm_flops / (ms * 1e-3) / 1e12, ff, "TFLOP/s", ms, 2 * n64 - 1,
+    entry("gemm_df_kernel", "alu", gemm_flops / (ms * 1e-3) / 1e12, ff, "TFLOP/s", ms, 2 * (n64 - 1),
           f"2 N^2 (2 M B) n_ch = {gemm_flops:.3e} FP64-equivalent flops in float-float", srcff)
     # the plain FP64 iteration's kernels (the comparison baseline), one energy
     x1 = torch.randn(2 * dim, dtype=torch.float64, device="cuda")

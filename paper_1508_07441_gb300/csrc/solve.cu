@@ -1145,8 +1145,7 @@ wpcd_status batch_setup(const wpcd_problem *pr, const double *E, int B, SolveCtx
   WPCD_CUDA_TRY(cudaMemcpyAsync(cx.r0, bi.j0.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
   WPCD_CUDA_TRY(cudaMemcpyAsync(cx.Dd, bi.D.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
   WPCD_CUDA_TRY(cudaMemcpyAsync(cx.pref, bi.pref.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
-  // the host vectors must outlive the copies: the caller synchronises s
-  // (through the resolvent's own synchronisation) before bi goes away
+  // copies from pageable host memory are staged before the calls return
   return WPCD_OK;
 }
 
@@ -1197,6 +1196,47 @@ wpcd_status born(const wpcd_problem *pr, const wpcd_P *P, SolveCtx &cx, Workspac
   count_launches(1);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? WPCD_OK : cuda_error(e, "born launch");
+}
+
+// b[r][e] = bu[r][map[e]] (complex FP64, energy index innermost)
+__global__ void expand_kernel(int64_t n, int B, int BU, const int *__restrict__ map, const double2 *__restrict__ bu,
+                              double2 *__restrict__ b) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n; f += (int64_t)gridDim.x * blockDim.x) {
+    const int e = (int)(f % B);
+    b[f] = bu[(f / B) * BU + map[e]];
+  }
+}
+
+// Born terms of a batch.  The Born term O P0 Vt e0 depends on an energy only
+// through its on-shell bin (e0 is the unit vector of bin j0), so it is formed
+// once per distinct bin and copied to each energy of the bin
+wpcd_status batch_born(const wpcd_problem *pr, const wpcd_P *P, SolveCtx &cx, const std::vector<int> &j0,
+                       bool dfres, Workspace<double> &ws64, DfWork &dfw, cudaStream_t s) {
+  const int B = cx.B;
+  std::vector<int> bin_of(pr->M, -1), ints;
+  for (int e = 0; e < B; ++e)
+    if (bin_of[j0[e]] < 0) {
+      bin_of[j0[e]] = (int)ints.size();
+      ints.push_back(j0[e]);
+    }
+  const int BU = (int)ints.size();
+  if (BU == B) return dfres ? df_born(pr, P, cx.r0, B, cx.b, dfw, s) : born(pr, P, cx, ws64, s);
+  for (int e = 0; e < B; ++e) ints.push_back(bin_of[j0[e]]);  // [BU] bins, then [B] energy -> bin
+  SolveCtx cu;
+  cu.B = BU;
+  cu.dim = cx.dim;
+  cu.st = s;
+  WPCD_CUDA_TRY(pool_malloc(&cu.b, 16 * cx.dim * BU, s));
+  WPCD_CUDA_TRY(pool_malloc(&cu.r0, sizeof(int) * ints.size(), s));
+  WPCD_CUDA_TRY(cudaMemcpyAsync(cu.r0, ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice, s));
+  wpcd_status st = dfres ? df_born(pr, P, cu.r0, BU, cu.b, dfw, s) : born(pr, P, cu, ws64, s);
+  if (st != WPCD_OK) return st;
+  const int64_t n = (int64_t)cx.dim * B;
+  expand_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, B, BU, cu.r0 + BU, reinterpret_cast<const double2 *>(cu.b),
+                                                 reinterpret_cast<double2 *>(cx.b));
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? WPCD_OK : cuda_error(e, "born expand launch");
 }
 
 // Plain FP64 Krylov on (I - K) u = b, started from u (0 or a warm start).
@@ -1722,7 +1762,7 @@ wpcd_status solve(wpcd_problem *pr, const wpcd_P *Pc, const double *E, int n_E,
       WPCD_CUDA_TRY(cudaEventCreateWithFlags(&side.before, cudaEventDisableTiming));
       WPCD_CUDA_TRY(cudaEventCreateWithFlags(&side.after, cudaEventDisableTiming));
       WPCD_CUDA_TRY(cudaEventRecord(side.before, s));
-      st = dfres ? df_born(pr, P, cx.r0, B, cx.b, dfw, s) : born(pr, P, cx, ws64, s);
+      st = batch_born(pr, P, cx, bi.j0, dfres, ws64, dfw, s);
       if (st != WPCD_OK) return st;
       st = batch_resolvent(pr, E + e0, B, cx, mixed, s, side.s2, side.before, side.after);
       if (st != WPCD_OK) return st;
