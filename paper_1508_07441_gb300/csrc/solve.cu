@@ -351,6 +351,68 @@ __global__ void __launch_bounds__(V_THREADS) bdot_kernel(int rows, int B, int nv
   }
 }
 
+// The FP32 dots with B even: as bdot_kernel, two adjacent energies per
+// thread in 16-byte loads (a warp reads 512 contiguous bytes of each
+// vector per row); the block sums in FP32, the cross-block sums (breduce)
+// in FP64
+__global__ void __launch_bounds__(V_THREADS) bdot2_kernel(int rows, int B, int nv, const float4 *__restrict__ V,
+                                                          size_t ld2, const float4 *__restrict__ w,
+                                                          double2 *__restrict__ partial) {
+  __shared__ float4 red[JC][V_THREADS];
+  const int EL = blockDim.x;  // energy-pair lanes (<= 32)
+  const int RB = blockDim.y;  // row lanes
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * EL + tx;
+  const int B2 = B / 2;
+  const int e2 = blockIdx.y * EL + tx;
+  const int nblk = gridDim.x;
+  for (int j0 = 0; j0 < nv; j0 += JC) {
+    float4 acc[JC];
+#pragma unroll
+    for (int c = 0; c < JC; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (e2 < B2) {
+      for (int r = blockIdx.x * RB + ty; r < rows; r += nblk * RB) {
+        const size_t f = (size_t)r * B2 + e2;
+        const float4 b = w[f];
+#pragma unroll
+        for (int c = 0; c < JC; ++c) {
+          if (j0 + c < nv) {
+            const float4 a = V[(size_t)(j0 + c) * ld2 + f];
+            acc[c].x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc[c].x));
+            acc[c].y = fmaf(a.x, b.y, fmaf(-a.y, b.x, acc[c].y));
+            acc[c].z = fmaf(a.z, b.z, fmaf(a.w, b.w, acc[c].z));
+            acc[c].w = fmaf(a.z, b.w, fmaf(-a.w, b.z, acc[c].w));
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < JC; ++c) red[c][tid] = acc[c];
+    __syncthreads();
+    for (int h = RB / 2; h > 0; h >>= 1) {
+      if (ty < h)
+#pragma unroll
+        for (int c = 0; c < JC; ++c) {
+          const float4 o = red[c][(ty + h) * EL + tx];
+          red[c][tid].x += o.x;
+          red[c][tid].y += o.y;
+          red[c][tid].z += o.z;
+          red[c][tid].w += o.w;
+        }
+      __syncthreads();
+    }
+    if (ty == 0 && e2 < B2)
+#pragma unroll
+      for (int c = 0; c < JC; ++c)
+        if (j0 + c < nv) {
+          const float4 v = red[c][tx];
+          double2 *o = partial + ((size_t)(j0 + c) * nblk + blockIdx.x) * B + 2 * e2;
+          o[0] = make_double2(v.x, v.y);
+          o[1] = make_double2(v.z, v.w);
+        }
+    __syncthreads();
+  }
+}
+
 // partial[blk * B + e] = (sum over blk's rows of |x[row, e]|^2, 0): the norm
 // pass, one vector read once, four rows in flight per thread, squares summed
 // in the vector type per thread and in FP64 across the block
@@ -1060,7 +1122,15 @@ struct Krylov {
   template <typename U>
   void dots(int nv, const typename Cx<U>::t *base, size_t ld, const typename Cx<U>::t *x, double2 *out,
             int accumulate, cudaStream_t s, bool hcoef = false, bool scale = false) {
-    bdot_kernel<U><<<dot_grid(), dot_block(), 0, s>>>((int)dim, B, nv, base, ld, x, partial);
+    if (sizeof(U) == 4 && B % 2 == 0) {  // FP32, B even: two energies per thread
+      int el = 1;
+      while (el < B / 2 && el < 32) el *= 2;
+      const dim3 blk(el, V_THREADS / el), grd(nblk, (B / 2 + el - 1) / el);
+      bdot2_kernel<<<grd, blk, 0, s>>>((int)dim, B, nv, reinterpret_cast<const float4 *>(base), ld / 2,
+                                       reinterpret_cast<const float4 *>(x), partial);
+    } else {
+      bdot_kernel<U><<<dot_grid(), dot_block(), 0, s>>>((int)dim, B, nv, base, ld, x, partial);
+    }
     breduce_kernel<T><<<breduce_blocks(nv * B), 256, 0, s>>>(nv, nblk, B, partial, out, accumulate,
                                                            hcoef ? hc : nullptr, -1.0, scale ? inv : nullptr);
     count_launches(2);
