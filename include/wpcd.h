@@ -177,7 +177,7 @@ wpcd_status wpcd_kapply(const wpcd_problem *pr, const wpcd_P *P, const double *g
 /* precision of the solve */
 #define WPCD_SOLVE_FP64 0  /* plain FP64 iteration (the comparison baseline) */
 #define WPCD_SOLVE_MIXED 1 /* FP32 inner Krylov cycles (FP32 P0 values,
-                              tensor-core TF32x3 block products, blocked
+                              tensor-core TF32x3 block products, compensated
                               FP32 SpMM sums) inside an iterative-refinement
                               loop whose Born term and residual
                               b - (I - K) u are formed in float-float
@@ -272,7 +272,7 @@ wpcd_status wpcd_solve_batch(int n_prob, wpcd_problem *const *problems, const wp
 /* arithmetic of wpcd_spmm */
 #define WPCD_SPMM_FP64 0 /* FP64 vectors, the P's own value precision */
 #define WPCD_SPMM_FP32 1 /* FP32 vectors and values (FP32 values made from FP64
-                            ones on first use), blocked FP32 sums */
+                            ones on first use), blocked compensated sums */
 #define WPCD_SPMM_FF 2   /* FP64 vectors in and out, float-float arithmetic on
                             the FP32 pipe (about 48 significant bits), as in
                             the refinement residual of WPCD_SOLVE_MIXED */

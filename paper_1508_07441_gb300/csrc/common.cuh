@@ -37,12 +37,8 @@ struct SpmmParams {
   int64_t nnz;
 };
 
-// SpMM accumulators: plain sums of the block partials, FP64 or FP32.  The
-// FP32 SpMM feeds only the inner cycles of the mixed solve, whose accuracy
-// the float-float refinement residual carries: compensating the FP32 block
-// sums (TwoSum, errors gathered in a low part) changed neither the number of
-// refinement cycles nor the final error on the 200 x 200, 128-energy
-// workload and cost a fifth of the SpMM's time.
+// SpMM accumulators: plain FP64 sums, or FP32 compensated sums (Knuth's
+// TwoSum on the running sum, the rounding errors gathered in lo)
 struct AccD {
   double v;
   __device__ void zero() { v = 0.0; }
@@ -52,11 +48,22 @@ struct AccD {
 };
 
 struct AccF {
-  float v;
-  __device__ void zero() { v = 0.f; }
-  __device__ void add(float x) { v += x; }
-  __device__ void add_shfl(int off) { v += __shfl_xor_sync(0xffffffffu, v, off); }
-  __device__ float value() const { return v; }
+  float hi, lo;
+  __device__ void zero() { hi = 0.f; lo = 0.f; }
+  __device__ void add(float x) {
+    float s = __fadd_rn(hi, x);
+    float bb = __fsub_rn(s, hi);
+    float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ void add_shfl(int off) {
+    float ohi = __shfl_xor_sync(0xffffffffu, hi, off);
+    float olo = __shfl_xor_sync(0xffffffffu, lo, off);
+    add(ohi);
+    lo = __fadd_rn(lo, olo);
+  }
+  __device__ float value() const { return __fadd_rn(hi, lo); }
 };
 
 template <typename T>
@@ -79,13 +86,22 @@ struct SpmmUnroll {
   static constexpr int value = NCH <= 3 ? 4 : 2;
 };
 
+// groups of U nonzeros per block partial: FP32 blocks of 4 U nonzeros (one
+// compensated add per 16 nonzeros for U = 4), FP64 blocks of U
+template <typename T>
+struct SpmmGroups {
+  static constexpr int value = sizeof(T) == 4 ? 4 : 1;
+};
+
 // The sums of one block-CSR row for the SpMM kernels.  A lane takes the
 // nonzeros o = b + nl, b + nl + nl_count, ... of its row, U at a time (their
 // column and value loads issued together), and for each of its EPT energies
-// forms the block of those U nonzeros with plain FMAs and adds it to the
-// accumulator (blocked summation: the rounding error grows with the block
-// length plus the number of blocks, not with the row length).  y points at
-// the problem's own vector
+// forms the block partial of G such groups (G U nonzeros) with plain FMAs
+// and adds it to the accumulator.  For FP32 this is blocked summation with a
+// compensated sum of the block partials (FABsum, Blanchard, Higham and Mary,
+// SIAM J. Sci. Comput. 2020, block size b = 16): the error grows with the
+// number of blocks only through the float-float accumulator, and inside a
+// block with its b terms.  FP64 sums the block partials plainly.  y points at the problem's own vector
 // block ([n_ch][n_cells][B] complex).  The lane's energies are en0 +
 // estride * t; with VEC (FP32, estride 1, EPT and B even) two adjacent
 // energies come in one 16-byte load.
@@ -99,65 +115,71 @@ __device__ __forceinline__ void spmm_row(int64_t b, int64_t e, int nl, int nl_co
   constexpr int U = SpmmUnroll<NCH, EPT>::value;
   constexpr int TS = VEC ? 2 : 1;  // energies per load
   static_assert(!VEC || (sizeof(T) == 4 && EPT % 2 == 0), "vector loads need FP32 and an even EPT");
-  for (int64_t o0 = b + nl; o0 < e; o0 += (int64_t)U * nl_count) {
-    int tc[U];
-    T v[U][NPAIR];
+  constexpr int G = SpmmGroups<T>::value;
+  for (int64_t ob = b + nl; ob < e; ob += (int64_t)G * U * nl_count) {
+    T part[NCH][EPT][2];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t o = o0 + (int64_t)u * nl_count;
-      const bool ok = o < e;
-      tc[u] = ok ? __ldg(col + o) : -1;
+    for (int l = 0; l < NCH; ++l)
 #pragma unroll
-      for (int m = 0; m < NPAIR; ++m) v[u][m] = ok ? (T)__ldg(val + (size_t)m * nnz + o) : T(0);
-    }
+      for (int t = 0; t < EPT; ++t) part[l][t][0] = part[l][t][1] = T(0);
+#pragma unroll 1
+    for (int gi = 0; gi < G; ++gi) {
+      const int64_t o0 = ob + (int64_t)gi * U * nl_count;
+      if (o0 >= e) break;
+      int tc[U];
+      T v[U][NPAIR];
 #pragma unroll
-    for (int t0 = 0; t0 < EPT; t0 += TS) {
-      const int en = en0 + estride * t0;
-      if (en < B) {
-        T part[NCH][TS][2];
+      for (int u = 0; u < U; ++u) {
+        const int64_t o = o0 + (int64_t)u * nl_count;
+        const bool ok = o < e;
+        tc[u] = ok ? __ldg(col + o) : -1;
 #pragma unroll
-        for (int l = 0; l < NCH; ++l)
+        for (int m = 0; m < NPAIR; ++m) v[u][m] = ok ? (T)__ldg(val + (size_t)m * nnz + o) : T(0);
+      }
 #pragma unroll
-          for (int q = 0; q < TS; ++q) part[l][q][0] = part[l][q][1] = T(0);
+      for (int t0 = 0; t0 < EPT; t0 += TS) {
+        const int en = en0 + estride * t0;
+        if (en < B) {
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if (tc[u] >= 0) {
-            T yr[NCH][TS], yi[NCH][TS];
+          for (int u = 0; u < U; ++u) {
+            if (tc[u] >= 0) {
+              T yr[NCH][TS], yi[NCH][TS];
 #pragma unroll
-            for (int l = 0; l < NCH; ++l) {
-              const C2 *p = y + ((size_t)l * n_cells + tc[u]) * B + en;
-              if constexpr (VEC) {
-                const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
-                yr[l][0] = q.x;
-                yi[l][0] = q.y;
-                yr[l][TS - 1] = q.z;
-                yi[l][TS - 1] = q.w;
-              } else {
-                const C2 q = __ldg(p);
-                yr[l][0] = q.x;
-                yi[l][0] = q.y;
+              for (int l = 0; l < NCH; ++l) {
+                const C2 *p = y + ((size_t)l * n_cells + tc[u]) * B + en;
+                if constexpr (VEC) {
+                  const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+                  yr[l][0] = q.x;
+                  yi[l][0] = q.y;
+                  yr[l][TS - 1] = q.z;
+                  yi[l][TS - 1] = q.w;
+                } else {
+                  const C2 q = __ldg(p);
+                  yr[l][0] = q.x;
+                  yi[l][0] = q.y;
+                }
               }
-            }
 #pragma unroll
-            for (int m = 0; m < NPAIR; ++m) {
-              const int l = pair_first(NCH, m), lp = pair_second(NCH, m);
+              for (int m = 0; m < NPAIR; ++m) {
+                const int l = pair_first(NCH, m), lp = pair_second(NCH, m);
 #pragma unroll
-              for (int q = 0; q < TS; ++q) {
-                part[l][q][0] = fma(v[u][m], yr[lp][q], part[l][q][0]);
-                part[l][q][1] = fma(v[u][m], yi[lp][q], part[l][q][1]);
+                for (int q = 0; q < TS; ++q) {
+                  part[l][t0 + q][0] = fma(v[u][m], yr[lp][q], part[l][t0 + q][0]);
+                  part[l][t0 + q][1] = fma(v[u][m], yi[lp][q], part[l][t0 + q][1]);
+                }
               }
             }
           }
         }
-#pragma unroll
-        for (int l = 0; l < NCH; ++l)
-#pragma unroll
-          for (int q = 0; q < TS; ++q) {
-            acc[l][t0 + q][0].add(part[l][q][0]);
-            acc[l][t0 + q][1].add(part[l][q][1]);
-          }
       }
     }
+#pragma unroll
+    for (int l = 0; l < NCH; ++l)
+#pragma unroll
+      for (int t = 0; t < EPT; ++t) {
+        acc[l][t][0].add(part[l][t][0]);
+        acc[l][t][1].add(part[l][t][1]);
+      }
   }
 }
 

@@ -17,7 +17,7 @@
 //          iterates of (I - K), one basis per energy, Givens updates on the
 //          device: the minimal-residual (reduced-rank) extrapolation of the
 //          iterates.  FP64, or MIXED: FP32 inner cycles (FP32 values,
-//          blocked FP32 SpMM sums, CUDA-graph replay) inside an FP64
+//          compensated SpMM sums, CUDA-graph replay) inside an FP64
 //          iterative-refinement loop r = b - (I - K) u.
 //   WYNN (the paper's scalar route)  c_n = e0^T K^n u0 summed by Wynn's
 //          epsilon algorithm on the device (FP64, one energy at a time).
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(G_THREADS) gemm_kernel(int n, int64_t ncol, co
 // A warp holds `rpw` rows; each row's 32/rpw lanes split into `el` energy
 // lanes times 32/(rpw el) nonzero lanes; every lane keeps EPT energies
 // (RHS tile = el * EPT, grid.y walks the tiles).  Values pair-major.
-// FP64 sums in double, FP32 sums in float, both blocked (spmm_row).
+// FP64 sums in double; FP32 sums blocked and compensated (spmm_row).
 // ---------------------------------------------------------------------------
 
 template <typename VT, typename T, int NCH, int EPT, bool VEC>
