@@ -139,12 +139,12 @@ def fill_flops_per_node(n_ch: int, n_pairs: int) -> int:
 # of the kernel as it stands (profiles/ names the capture); None where no
 # capture of the current kernel exists
 NCU_TRAFFIC = {
-    "fill_kernel<FP64,3>": 440.0e6,
-    "spmm_kernel<float>": 377.1e6,
-    "tc_gemm_kernel<TF32x3> (Vt, G1)": 332.4e6,
-    "tc_gemm_kernel<TF32x3> (O)": 334.5e6,
-    "spmm_df_kernel": 958.4e6,
-    "gemm_df_kernel": 884.8e6,
+    "fill_kernel<FP64,3>": 435.7e6,
+    "spmm_kernel<float>": 368.9e6,
+    "tc_gemm_kernel<TF32x3> (Vt, G1)": 329.1e6,
+    "tc_gemm_kernel<TF32x3> (O)": 331.6e6,
+    "spmm_df_kernel": 1045.6e6,
+    "gemm_df_kernel": 907.3e6,
 }
 
 

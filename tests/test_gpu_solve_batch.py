@@ -87,6 +87,26 @@ def test_mixed_graph_and_eager_identical(W, sys3):
     assert [s.n_outer for s in sg] == [s.n_outer for s in se]
 
 
+@pytest.mark.parametrize("precision", ["FP64", "MIXED"])
+def test_energies_sharing_on_shell_bins(W, sys3, precision):
+    """Energies that share on-shell bins (out of order): G1 and the Born term
+    are formed once per bin; every energy matches the oracle, and energies of
+    one bin, whose discretised equation is the same, give the same U00."""
+    pr, P64, _, opr = sys3
+    E = [0.9, 0.9001, 2.0, 0.8995, 2.0002, -0.3]
+    U, stats, st = pr.wpcd_solve(P64, E, tol=1e-12, max_iter=300, batch=len(E),
+                                 precision=getattr(W, "WPCD_SOLVE_" + precision))
+    assert st == W.WPCD_OK
+    j0 = [s.j0 for s in stats]
+    assert len(set(j0)) < len(E)
+    ref = np.array([opr.solve_gmres(e, tol=1e-13, max_iter=400)["U00"] for e in E])
+    assert np.max(np.abs(U - ref) / np.abs(ref)) < 1e-9
+    for a in range(len(E)):
+        for b in range(len(E)):
+            if j0[a] == j0[b]:
+                assert abs(U[a] - U[b]) <= 1e-11 * abs(U[a])
+
+
 def test_batch_of_128_energies(W, orc):
     """The batching workload's energy grid (128 energies uniform in
     [-0.9 |E_d|, 5]) solved in one batch, mixed precision, on a 3-channel
