@@ -80,6 +80,24 @@ const char *wpcd_last_error(void);
 /* ABI version (major * 10000 + minor * 100 + patch). */
 int wpcd_version(void);
 
+/* Caller-supplied device allocator.  alloc returns `bytes` of device memory
+ * on device `device`, to be used on `stream` (a cudaStream_t; NULL: the
+ * legacy default stream), or NULL on failure (the call then returns
+ * WPCD_ECUDA); free releases such a block, ordered after the work already
+ * queued on `stream` (persistent tables are freed with stream NULL after a
+ * device synchronisation).  `user` is passed through.  The callbacks may be
+ * called from any library call that allocates (problem creation, assembly,
+ * the solves' work space, the MLP). */
+typedef void *(*wpcd_alloc_fn)(size_t bytes, int device, void *stream, void *user);
+typedef void (*wpcd_free_fn)(void *ptr, void *stream, void *user);
+
+/* Route every device allocation of the library through (alloc, free), or
+ * back to the library's own (cudaMalloc for tables, a stream-ordered pool
+ * for work space) with both NULL.  Process-wide; EINVAL if only one is NULL
+ * or while allocations of the other allocator are live (set it before
+ * creating handles, or after destroying them all). */
+wpcd_status wpcd_set_allocator(wpcd_alloc_fn alloc, wpcd_free_fn free_fn, void *user);
+
 /* Number of CUDA kernel launches this library has issued in this process
  * (all devices, all threads); lets a caller count the device work of a
  * region by differencing. */

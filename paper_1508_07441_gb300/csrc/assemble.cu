@@ -577,12 +577,12 @@ wpcd_status assemble(wpcd_problem *pr, int prec, cudaStream_t s, wpcd_P **out) {
   Pm->prec = prec;
   Pm->n_pairs = pr->n_pairs;
   auto fail = [&](wpcd_status st) {
-    cudaFree(counts);
-    cudaFree(sorted);
-    cudaFree(Pm->row_ptr);
-    cudaFree(Pm->col);
-    cudaFree(Pm->val64);
-    cudaFree(Pm->val32);
+    dev_free(counts);
+    dev_free(sorted);
+    dev_free(Pm->row_ptr);
+    dev_free(Pm->col);
+    dev_free(Pm->val64);
+    dev_free(Pm->val32);
     delete Pm;
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
@@ -591,9 +591,9 @@ wpcd_status assemble(wpcd_problem *pr, int prec, cudaStream_t s, wpcd_P **out) {
     return st;
   };
   cudaError_t e;
-  if ((e = cudaMalloc(&counts, sizeof(int64_t) * n_cells)) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc counts"));
-  if ((e = cudaMalloc(&sorted, sizeof(uint32_t) * (size_t)n_cells * np2)) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc sorted keys"));
-  if ((e = cudaMalloc(&Pm->row_ptr, sizeof(int64_t) * (n_cells + 1))) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc row_ptr"));
+  if ((e = dev_malloc(&counts, sizeof(int64_t) * n_cells)) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc counts"));
+  if ((e = dev_malloc(&sorted, sizeof(uint32_t) * (size_t)n_cells * np2)) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc sorted keys"));
+  if ((e = dev_malloc(&Pm->row_ptr, sizeof(int64_t) * (n_cells + 1))) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc row_ptr"));
 
   cudaEventRecord(ev0, s);
   size_t smem_count = sizeof(long long) * (P.N + P.M + 2) + sizeof(BinConst) * P.n_p * P.n_q +
@@ -611,13 +611,13 @@ wpcd_status assemble(wpcd_problem *pr, int prec, cudaStream_t s, wpcd_P **out) {
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(cuda_error(e, "count pass"));
   Pm->nnz = nnz;
   size_t nz = nnz > 0 ? (size_t)nnz : 1;
-  if ((e = cudaMalloc(&Pm->col, sizeof(int32_t) * nz)) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc col"));
+  if ((e = dev_malloc(&Pm->col, sizeof(int32_t) * nz)) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc col"));
   void *val = nullptr;
   if (prec == WPCD_FP64) {
-    if ((e = cudaMalloc(&Pm->val64, sizeof(double) * nz * P.n_pairs)) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc val"));
+    if ((e = dev_malloc(&Pm->val64, sizeof(double) * nz * P.n_pairs)) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc val"));
     val = Pm->val64;
   } else {
-    if ((e = cudaMalloc(&Pm->val32, sizeof(float) * nz * P.n_pairs)) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc val"));
+    if ((e = dev_malloc(&Pm->val32, sizeof(float) * nz * P.n_pairs)) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc val"));
     val = Pm->val32;
   }
   size_t rsz = prec == WPCD_FP64 ? sizeof(double) : sizeof(float);
@@ -636,8 +636,8 @@ wpcd_status assemble(wpcd_problem *pr, int prec, cudaStream_t s, wpcd_P **out) {
   cudaEventElapsedTime(&Pm->ms_phase[0], ev0, evc);
   cudaEventElapsedTime(&Pm->ms_phase[1], evc, evs);
   cudaEventElapsedTime(&Pm->ms_phase[2], evs, ev1);
-  cudaFree(counts);
-  cudaFree(sorted);
+  dev_free(counts);
+  dev_free(sorted);
   cudaEventDestroy(ev0);
   cudaEventDestroy(ev1);
   cudaEventDestroy(evc);

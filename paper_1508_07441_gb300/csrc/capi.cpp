@@ -50,13 +50,66 @@ static bool pool_enabled() {
   return on;
 }
 
-cudaError_t pool_malloc(void **p, size_t bytes, cudaStream_t s) {
-  if (!pool_enabled()) return cudaMalloc(p, bytes ? bytes : 16);
-  static std::mutex mu;
-  static cudaMemPool_t pools[64] = {};
+// the caller's allocator (wpcd_set_allocator), and the number of live
+// blocks of whichever allocator is current
+struct AllocHook {
+  wpcd_alloc_fn alloc = nullptr;
+  wpcd_free_fn free = nullptr;
+  void *user = nullptr;
+};
+static std::mutex g_hook_mu;
+static AllocHook g_hook;
+static std::atomic<long long> g_live{0};
+
+static AllocHook current_hook() {
+  std::lock_guard<std::mutex> lock(g_hook_mu);
+  return g_hook;
+}
+
+static cudaError_t hook_alloc(const AllocHook &h, void **p, size_t bytes, cudaStream_t s) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  void *q = h.alloc(bytes ? bytes : 16, dev, static_cast<void *>(s), h.user);
+  if (!q) return cudaErrorMemoryAllocation;
+  *p = q;
+  ++g_live;
+  return cudaSuccess;
+}
+
+cudaError_t dev_malloc(void **p, size_t bytes) {
+  const AllocHook h = current_hook();
+  if (h.alloc) return hook_alloc(h, p, bytes, nullptr);
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e == cudaSuccess) ++g_live;
+  return e;
+}
+
+void dev_free(void *p) {
+  if (!p) return;
+  --g_live;
+  const AllocHook h = current_hook();
+  if (h.free) {
+    cudaDeviceSynchronize();  // as cudaFree: no queued work still uses the block
+    h.free(p, nullptr, h.user);
+  } else {
+    cudaFree(p);
+  }
+}
+
+cudaError_t pool_malloc(void **p, size_t bytes, cudaStream_t s) {
+  const AllocHook h = current_hook();
+  if (h.alloc) return hook_alloc(h, p, bytes, s);
+  cudaError_t e;
+  if (!pool_enabled()) {
+    e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e == cudaSuccess) ++g_live;
+    return e;
+  }
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   cudaMemPool_t pool;
   {
@@ -73,12 +126,18 @@ cudaError_t pool_malloc(void **p, size_t bytes, cudaStream_t s) {
     }
     pool = pools[dev];
   }
-  return cudaMallocFromPoolAsync(p, bytes ? bytes : 16, pool, s);
+  e = cudaMallocFromPoolAsync(p, bytes ? bytes : 16, pool, s);
+  if (e == cudaSuccess) ++g_live;
+  return e;
 }
 
 void pool_free(void *p, cudaStream_t s) {
   if (!p) return;
-  if (pool_enabled())
+  --g_live;
+  const AllocHook h = current_hook();
+  if (h.free)
+    h.free(p, static_cast<void *>(s), h.user);
+  else if (pool_enabled())
     cudaFreeAsync(p, s);
   else
     cudaFree(p);
@@ -87,27 +146,27 @@ void pool_free(void *p, cudaStream_t s) {
 static void free_tables(DeviceTables &d) {
   double **all[] = {&d.pe2, &d.qe2, &d.pn, &d.wp, &d.qn, &d.wq, &d.yn, &d.wy, &d.rsb, &d.qe, &d.eps, &d.O, &d.Vt};
   for (double **p : all) {
-    cudaFree(*p);
+    dev_free(*p);
     *p = nullptr;
   }
-  cudaFree(d.O32);
-  cudaFree(d.Vt32);
+  dev_free(d.O32);
+  dev_free(d.Vt32);
   d.O32 = d.Vt32 = nullptr;
-  cudaFree(d.O_tc);
-  cudaFree(d.Vt_tc);
-  cudaFree(d.O_h);
-  cudaFree(d.O_l);
-  cudaFree(d.Vt_h);
-  cudaFree(d.Vt_l);
+  dev_free(d.O_tc);
+  dev_free(d.Vt_tc);
+  dev_free(d.O_h);
+  dev_free(d.O_l);
+  dev_free(d.Vt_h);
+  dev_free(d.Vt_l);
   d.O_h = d.O_l = d.Vt_h = d.Vt_l = nullptr;
-  cudaFree(d.tc_err);
+  dev_free(d.tc_err);
   d.O_tc = d.Vt_tc = nullptr;
   d.tc_err = nullptr;
 }
 
 static wpcd_status upload32(float **dst, const std::vector<double> &src) {
   std::vector<float> f(src.begin(), src.end());
-  cudaError_t e = cudaMalloc(dst, sizeof(float) * (f.empty() ? 1 : f.size()));
+  cudaError_t e = dev_malloc(dst, sizeof(float) * (f.empty() ? 1 : f.size()));
   if (e != cudaSuccess) return cuda_error(e, "cudaMalloc (problem tables)");
   if (!f.empty()) {
     e = cudaMemcpy(*dst, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice);
@@ -117,7 +176,7 @@ static wpcd_status upload32(float **dst, const std::vector<double> &src) {
 }
 
 static wpcd_status upload(double **dst, const std::vector<double> &src) {
-  cudaError_t e = cudaMalloc(dst, sizeof(double) * (src.empty() ? 1 : src.size()));
+  cudaError_t e = dev_malloc(dst, sizeof(double) * (src.empty() ? 1 : src.size()));
   if (e != cudaSuccess) return cuda_error(e, "cudaMalloc (problem tables)");
   if (!src.empty()) {
     e = cudaMemcpy(*dst, src.data(), sizeof(double) * src.size(), cudaMemcpyHostToDevice);
@@ -271,6 +330,20 @@ int wpcd_version(void) { return 100; }
 
 int64_t wpcd_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
+wpcd_status wpcd_set_allocator(wpcd_alloc_fn alloc, wpcd_free_fn free_fn, void *user) {
+  clear_error();
+  if ((alloc == nullptr) != (free_fn == nullptr)) return set_error(WPCD_EINVAL, "give both allocator callbacks or neither");
+  std::lock_guard<std::mutex> lock(g_hook_mu);
+  const long long live = g_live.load();
+  if (live != 0)
+    return set_error(WPCD_EINVAL, "device blocks of the current allocator are live (" + std::to_string(live) +
+                                      "); set the allocator before creating handles or after destroying them");
+  g_hook.alloc = alloc;
+  g_hook.free = free_fn;
+  g_hook.user = user;
+  return WPCD_OK;
+}
+
 wpcd_status wpcd_tangent_edges(int n_bins, double k_max, double *edges) {
   if (n_bins < 1 || !(k_max > 0.0) || !std::isfinite(k_max) || !edges)
     return set_error(WPCD_EINVAL, "tangent edges need n_bins >= 1, finite k_max > 0");
@@ -326,13 +399,13 @@ wpcd_status wpcd_assemble_P(wpcd_problem *pr, int prec, void *stream, wpcd_P **o
 void wpcd_P_destroy(wpcd_P *P) {
   if (!P) return;
   cudaSetDevice(P->pr->device);
-  cudaFree(P->row_ptr);
-  cudaFree(P->col);
-  cudaFree(P->val64);
-  cudaFree(P->val32);
-  cudaFree(P->val32_copy);
-  cudaFree(P->val_h);
-  cudaFree(P->val_l);
+  dev_free(P->row_ptr);
+  dev_free(P->col);
+  dev_free(P->val64);
+  dev_free(P->val32);
+  dev_free(P->val32_copy);
+  dev_free(P->val_h);
+  dev_free(P->val_l);
   delete P;
 }
 

@@ -180,18 +180,18 @@ cudaError_t DfWork::alloc(size_t dim, int B, cudaStream_t s) {
 wpcd_status df_prepare(wpcd_problem *pr, wpcd_P *P, cudaStream_t s) {
   const int64_t nmat = (int64_t)pr->n_ch * pr->N * pr->N;
   if (!pr->d.O_h) {
-    WPCD_CUDA_TRY(cudaMalloc(&pr->d.O_h, sizeof(float) * nmat));
-    WPCD_CUDA_TRY(cudaMalloc(&pr->d.O_l, sizeof(float) * nmat));
-    WPCD_CUDA_TRY(cudaMalloc(&pr->d.Vt_h, sizeof(float) * nmat));
-    WPCD_CUDA_TRY(cudaMalloc(&pr->d.Vt_l, sizeof(float) * nmat));
+    WPCD_CUDA_TRY(dev_malloc(&pr->d.O_h, sizeof(float) * nmat));
+    WPCD_CUDA_TRY(dev_malloc(&pr->d.O_l, sizeof(float) * nmat));
+    WPCD_CUDA_TRY(dev_malloc(&pr->d.Vt_h, sizeof(float) * nmat));
+    WPCD_CUDA_TRY(dev_malloc(&pr->d.Vt_l, sizeof(float) * nmat));
     df_split_kernel<<<grid_for(nmat, 256), 256, 0, s>>>(nmat, pr->d.O, pr->d.O_h, pr->d.O_l);
     df_split_kernel<<<grid_for(nmat, 256), 256, 0, s>>>(nmat, pr->d.Vt, pr->d.Vt_h, pr->d.Vt_l);
     count_launches(2);
   }
   if (P && P->prec == WPCD_FP64 && !P->val_h) {
     const int64_t nv = (int64_t)P->nnz * P->n_pairs;
-    WPCD_CUDA_TRY(cudaMalloc(&P->val_h, sizeof(float) * nv + 4));
-    WPCD_CUDA_TRY(cudaMalloc(&P->val_l, sizeof(float) * nv + 4));
+    WPCD_CUDA_TRY(dev_malloc(&P->val_h, sizeof(float) * nv + 4));
+    WPCD_CUDA_TRY(dev_malloc(&P->val_l, sizeof(float) * nv + 4));
     df_split_kernel<<<grid_for(nv, 256), 256, 0, s>>>(nv, P->val64, P->val_h, P->val_l);
     count_launches(1);
   }

@@ -193,21 +193,21 @@ wpcd_status ensure_cap(wpcd_mlp *m, int n) {
   if (n <= m->cap) return WPCD_OK;
   float **bufs[] = {&m->xn, &m->h1, &m->h2, &m->z, &m->dz, &m->d1, &m->d2, &m->tn};
   for (float **b : bufs) {
-    cudaFree(*b);
+    dev_free(*b);
     *b = nullptr;
   }
-  cudaFree(m->idx);
+  dev_free(m->idx);
   m->idx = nullptr;
   const int W = m->width;
-  WPCD_CUDA_TRY(cudaMalloc(&m->xn, sizeof(float) * (size_t)n * m->n_in));
-  WPCD_CUDA_TRY(cudaMalloc(&m->h1, sizeof(float) * (size_t)n * W));
-  WPCD_CUDA_TRY(cudaMalloc(&m->h2, sizeof(float) * (size_t)n * W));
-  WPCD_CUDA_TRY(cudaMalloc(&m->z, sizeof(float) * (size_t)n * m->n_out));
-  WPCD_CUDA_TRY(cudaMalloc(&m->dz, sizeof(float) * (size_t)n * m->n_out));
-  WPCD_CUDA_TRY(cudaMalloc(&m->d1, sizeof(float) * (size_t)n * W));
-  WPCD_CUDA_TRY(cudaMalloc(&m->d2, sizeof(float) * (size_t)n * W));
-  WPCD_CUDA_TRY(cudaMalloc(&m->tn, sizeof(float) * (size_t)n * m->n_out));
-  WPCD_CUDA_TRY(cudaMalloc(&m->idx, sizeof(int) * (size_t)n));
+  WPCD_CUDA_TRY(dev_malloc(&m->xn, sizeof(float) * (size_t)n * m->n_in));
+  WPCD_CUDA_TRY(dev_malloc(&m->h1, sizeof(float) * (size_t)n * W));
+  WPCD_CUDA_TRY(dev_malloc(&m->h2, sizeof(float) * (size_t)n * W));
+  WPCD_CUDA_TRY(dev_malloc(&m->z, sizeof(float) * (size_t)n * m->n_out));
+  WPCD_CUDA_TRY(dev_malloc(&m->dz, sizeof(float) * (size_t)n * m->n_out));
+  WPCD_CUDA_TRY(dev_malloc(&m->d1, sizeof(float) * (size_t)n * W));
+  WPCD_CUDA_TRY(dev_malloc(&m->d2, sizeof(float) * (size_t)n * W));
+  WPCD_CUDA_TRY(dev_malloc(&m->tn, sizeof(float) * (size_t)n * m->n_out));
+  WPCD_CUDA_TRY(dev_malloc(&m->idx, sizeof(int) * (size_t)n));
   m->cap = n;
   return WPCD_OK;
 }
@@ -374,14 +374,14 @@ wpcd_status wpcd_mlp_create(int n_in, int width, int n_out, uint64_t seed, int d
   fill(m->oW3, n_out, width, 3);
   const size_t nb = sizeof(float) * m->n_params;
   cudaError_t e;
-  if ((e = cudaMalloc(&m->params, nb)) != cudaSuccess || (e = cudaMalloc(&m->grads, nb)) != cudaSuccess ||
-      (e = cudaMalloc(&m->adam_m, nb)) != cudaSuccess || (e = cudaMalloc(&m->adam_v, nb)) != cudaSuccess ||
-      (e = cudaMalloc(&m->params_bf16, sizeof(__nv_bfloat16) * m->n_params)) != cudaSuccess ||
-      (e = cudaMalloc(&m->in_scale, sizeof(float) * n_in)) != cudaSuccess ||
-      (e = cudaMalloc(&m->in_shift, sizeof(float) * n_in)) != cudaSuccess ||
-      (e = cudaMalloc(&m->out_scale, sizeof(float) * n_out)) != cudaSuccess ||
-      (e = cudaMalloc(&m->out_shift, sizeof(float) * n_out)) != cudaSuccess ||
-      (e = cudaMalloc(&m->loss, sizeof(float))) != cudaSuccess) {
+  if ((e = dev_malloc(&m->params, nb)) != cudaSuccess || (e = dev_malloc(&m->grads, nb)) != cudaSuccess ||
+      (e = dev_malloc(&m->adam_m, nb)) != cudaSuccess || (e = dev_malloc(&m->adam_v, nb)) != cudaSuccess ||
+      (e = dev_malloc(&m->params_bf16, sizeof(__nv_bfloat16) * m->n_params)) != cudaSuccess ||
+      (e = dev_malloc(&m->in_scale, sizeof(float) * n_in)) != cudaSuccess ||
+      (e = dev_malloc(&m->in_shift, sizeof(float) * n_in)) != cudaSuccess ||
+      (e = dev_malloc(&m->out_scale, sizeof(float) * n_out)) != cudaSuccess ||
+      (e = dev_malloc(&m->out_shift, sizeof(float) * n_out)) != cudaSuccess ||
+      (e = dev_malloc(&m->loss, sizeof(float))) != cudaSuccess) {
     wpcd_mlp_destroy(m);
     return cuda_error(e, "cudaMalloc (MLP)");
   }
@@ -403,7 +403,7 @@ void wpcd_mlp_destroy(wpcd_mlp *m) {
   void *bufs[] = {m->params, m->grads, m->adam_m, m->adam_v, m->params_bf16, m->in_scale, m->in_shift,
                   m->out_scale, m->out_shift, m->xn, m->h1, m->h2, m->z, m->dz, m->d1, m->d2,
                   m->loss, m->tn, m->idx};
-  for (void *b : bufs) cudaFree(b);
+  for (void *b : bufs) dev_free(b);
   delete m;
 }
 
@@ -488,7 +488,7 @@ wpcd_status wpcd_mlp_loss_grad(wpcd_mlp *m, const float *X, const float *T, int 
     ish[c] = -sh[c] / sc[c];
   }
   float *d_isc = nullptr;
-  WPCD_CUDA_TRY(cudaMalloc(&d_isc, sizeof(float) * 2 * m->n_out));
+  WPCD_CUDA_TRY(dev_malloc(&d_isc, sizeof(float) * 2 * m->n_out));
   cudaMemcpy(d_isc, isc.data(), sizeof(float) * m->n_out, cudaMemcpyHostToDevice);
   cudaMemcpy(d_isc + m->n_out, ish.data(), sizeof(float) * m->n_out, cudaMemcpyHostToDevice);
   affine_kernel<<<gridn((int64_t)n * m->n_out), 256, 0, s>>>(n, m->n_out, T, d_isc, d_isc + m->n_out, m->tn);
@@ -500,7 +500,7 @@ wpcd_status wpcd_mlp_loss_grad(wpcd_mlp *m, const float *X, const float *T, int 
   cudaMemcpyAsync(&l, m->loss, sizeof(float), cudaMemcpyDeviceToHost, s);
   if (grad) cudaMemcpyAsync(grad, m->grads, sizeof(float) * m->n_params, cudaMemcpyDefault, s);
   cudaError_t e = cudaStreamSynchronize(s);
-  cudaFree(d_isc);
+  dev_free(d_isc);
   if (e != cudaSuccess) return cuda_error(e, "MLP loss/grad");
   if (loss) *loss = l;
   return WPCD_OK;
@@ -522,10 +522,10 @@ wpcd_status wpcd_mlp_train(wpcd_mlp *m, const float *X, const float *T, int n, i
   if (st != WPCD_OK) return st;
   float *Xb = nullptr, *Tb = nullptr, *d_isc = nullptr;
   int *d_order = nullptr;
-  WPCD_CUDA_TRY(cudaMalloc(&d_order, sizeof(int) * (size_t)n));
-  WPCD_CUDA_TRY(cudaMalloc(&Xb, sizeof(float) * (size_t)batch * m->n_in));
-  WPCD_CUDA_TRY(cudaMalloc(&Tb, sizeof(float) * (size_t)batch * m->n_out));
-  WPCD_CUDA_TRY(cudaMalloc(&d_isc, sizeof(float) * 2 * m->n_out));
+  WPCD_CUDA_TRY(dev_malloc(&d_order, sizeof(int) * (size_t)n));
+  WPCD_CUDA_TRY(dev_malloc(&Xb, sizeof(float) * (size_t)batch * m->n_in));
+  WPCD_CUDA_TRY(dev_malloc(&Tb, sizeof(float) * (size_t)batch * m->n_out));
+  WPCD_CUDA_TRY(dev_malloc(&d_isc, sizeof(float) * 2 * m->n_out));
   std::vector<float> sc(m->n_out), sh(m->n_out), isc(2 * m->n_out);
   cudaMemcpy(sc.data(), m->out_scale, sizeof(float) * m->n_out, cudaMemcpyDeviceToHost);
   cudaMemcpy(sh.data(), m->out_shift, sizeof(float) * m->n_out, cudaMemcpyDeviceToHost);
@@ -569,10 +569,10 @@ wpcd_status wpcd_mlp_train(wpcd_mlp *m, const float *X, const float *T, int n, i
   }
   m->bf16_stale = true;
   cudaError_t e = cudaStreamSynchronize(s);
-  cudaFree(Xb);
-  cudaFree(Tb);
-  cudaFree(d_isc);
-  cudaFree(d_order);
+  dev_free(Xb);
+  dev_free(Tb);
+  dev_free(d_isc);
+  dev_free(d_order);
   return e == cudaSuccess ? WPCD_OK : cuda_error(e, "MLP training");
 }
 
@@ -604,7 +604,7 @@ wpcd_status wpcd_basis_orthonormalize(double *Phi, int k, int dim, void *stream)
   if (!Phi || k < 1 || dim < 1) return set_error(WPCD_EINVAL, "bad basis arguments");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double2 *c = nullptr;
-  WPCD_CUDA_TRY(cudaMalloc(&c, sizeof(double2)));
+  WPCD_CUDA_TRY(dev_malloc(&c, sizeof(double2)));
   double2 *V = (double2 *)Phi;
   for (int j = 0; j < k; ++j) {
     for (int pass = 0; pass < 2; ++pass)
@@ -618,7 +618,7 @@ wpcd_status wpcd_basis_orthonormalize(double *Phi, int k, int dim, void *stream)
     count_launches(2);
   }
   cudaError_t e = cudaStreamSynchronize(s);
-  cudaFree(c);
+  dev_free(c);
   return e == cudaSuccess ? WPCD_OK : cuda_error(e, "orthonormalisation");
 }
 
@@ -640,12 +640,12 @@ wpcd_status wpcd_warm_features(const wpcd_problem *pr, const double *E, int n, d
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double *d_eb = nullptr;
-  WPCD_CUDA_TRY(cudaMalloc(&d_eb, sizeof(double) * n));
+  WPCD_CUDA_TRY(dev_malloc(&d_eb, sizeof(double) * n));
   WPCD_CUDA_TRY(cudaMemcpy(d_eb, eb.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
   features_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, k, kf, d_eb, e_lo, e_hi, (const double2 *)Cb, X);
   count_launches(1);
   cudaError_t e = cudaStreamSynchronize(s);
-  cudaFree(d_eb);
+  dev_free(d_eb);
   return e == cudaSuccess ? WPCD_OK : cuda_error(e, "features");
 }
 

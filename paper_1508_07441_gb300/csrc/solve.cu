@@ -792,10 +792,10 @@ wpcd_status tune_spmm(const wpcd_problem *pr, wpcd_P *P, int B, int mode, cudaSt
   void *y = nullptr, *z = nullptr;
   // float-float vectors: hi and lo float arrays, the size of one FP64 vector
   const size_t esz = fp32 ? sizeof(float) : sizeof(double);
-  WPCD_CUDA_TRY(cudaMalloc(&y, 2 * esz * dim * B));
-  cudaError_t ce = cudaMalloc(&z, 2 * esz * dim * B);
+  WPCD_CUDA_TRY(dev_malloc(&y, 2 * esz * dim * B));
+  cudaError_t ce = dev_malloc(&z, 2 * esz * dim * B);
   if (ce != cudaSuccess) {
-    cudaFree(y);
+    dev_free(y);
     return cuda_error(ce, "cudaMalloc (tuning)");
   }
   cudaMemsetAsync(y, 0, 2 * esz * dim * B, s);
@@ -835,8 +835,8 @@ wpcd_status tune_spmm(const wpcd_problem *pr, wpcd_P *P, int B, int mode, cudaSt
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  cudaFree(y);
-  cudaFree(z);
+  dev_free(y);
+  dev_free(z);
   if (st != WPCD_OK) return st;
   P->tuned[key] = pick;
   g_tuned_shapes[shape] = pick;
@@ -970,7 +970,7 @@ wpcd_status resolvent_impl(const wpcd_problem *pr, const double *E, int n_E, dou
   ints.insert(ints.end(), elist.begin(), elist.end());
   WPCD_CUDA_TRY(cudaSetDevice(pr->device));
   double *d_lohi = nullptr;
-  WPCD_CUDA_TRY(cudaMallocAsync(&d_lohi, sizeof(double) * ints_at + sizeof(int) * ints.size(), s));
+  WPCD_CUDA_TRY(pool_malloc(&d_lohi, sizeof(double) * ints_at + sizeof(int) * ints.size(), s));
   WPCD_CUDA_TRY(cudaMemcpyAsync(d_lohi, lohi.data(), sizeof(double) * lohi.size(), cudaMemcpyHostToDevice, s));
   int *d_ints = reinterpret_cast<int *>(d_lohi + ints_at);
   WPCD_CUDA_TRY(cudaMemcpyAsync(d_ints, ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice, s));
@@ -999,7 +999,7 @@ wpcd_status resolvent_impl(const wpcd_problem *pr, const double *E, int n_E, dou
   resolvent_kernel<<<grid_for(total, 256, max_blocks), 256, 0, s>>>(R, g);
   count_launches(2);
   cudaError_t e = cudaGetLastError();
-  cudaFreeAsync(d_lohi, s);
+  pool_free(d_lohi, s);
   // a copy from pageable memory returns once the data is staged, so the
   // host vectors may go; no synchronisation (the work stays asynchronous)
   if (e != cudaSuccess) return cuda_error(e, "resolvent launch");
@@ -1594,21 +1594,21 @@ wpcd_status solve_wynn(const wpcd_problem *pr, const wpcd_P *P, double E, const 
   struct Free {
     std::vector<void *> p;
     ~Free() {
-      for (void *q : p) cudaFree(q);
+      for (void *q : p) dev_free(q);
     }
   } fr;
   double *g = nullptr, *x0d = nullptr, *x1d = nullptr;
   double2 *small = nullptr;
   int *flag = nullptr;
-  WPCD_CUDA_TRY(cudaMalloc(&g, 16 * dim));
+  WPCD_CUDA_TRY(dev_malloc(&g, 16 * dim));
   fr.p.push_back(g);
-  WPCD_CUDA_TRY(cudaMalloc(&x0d, 16 * dim));
+  WPCD_CUDA_TRY(dev_malloc(&x0d, 16 * dim));
   fr.p.push_back(x0d);
-  WPCD_CUDA_TRY(cudaMalloc(&x1d, 16 * dim));
+  WPCD_CUDA_TRY(dev_malloc(&x1d, 16 * dim));
   fr.p.push_back(x1d);
-  WPCD_CUDA_TRY(cudaMalloc(&small, sizeof(double2) * (5 * (size_t)m + 8)));
+  WPCD_CUDA_TRY(dev_malloc(&small, sizeof(double2) * (5 * (size_t)m + 8)));
   fr.p.push_back(small);
-  WPCD_CUDA_TRY(cudaMalloc(&flag, 2 * sizeof(int)));
+  WPCD_CUDA_TRY(dev_malloc(&flag, 2 * sizeof(int)));
   fr.p.push_back(flag);
   st = resolvent_impl(pr, &E, 1, g, 1, nullptr, nullptr, s);
   if (st != WPCD_OK) return st;
@@ -1785,7 +1785,7 @@ wpcd_status solve(wpcd_problem *pr, const wpcd_P *Pc, const double *E, int n_E,
       if (st != WPCD_OK) return st;
     }
     if (mixed && !P->val32 && !P->val32_copy) {
-      WPCD_CUDA_TRY(cudaMalloc(&P->val32_copy, sizeof(float) * (size_t)P->nnz * P->n_pairs + 4));
+      WPCD_CUDA_TRY(dev_malloc(&P->val32_copy, sizeof(float) * (size_t)P->nnz * P->n_pairs + 4));
       int64_t nv = (int64_t)P->nnz * P->n_pairs;
       d2f_kernel<<<grid_for(nv, 256), 256, 0, s>>>(nv, P->val64, P->val32_copy);
       count_launches(1);
@@ -1924,7 +1924,7 @@ wpcd_status spmm_apply(wpcd_problem *pr, wpcd_P *P, int mode, const void *y, voi
   if (mode == WPCD_SPMM_FF) return df_spmm_op(pr, P, (const double *)y, (double *)z, n_rhs, ms, s);
   const bool fp32 = mode == WPCD_SPMM_FP32;
   if (fp32 && !P->val32 && !P->val32_copy) {
-    WPCD_CUDA_TRY(cudaMalloc(&P->val32_copy, sizeof(float) * (size_t)P->nnz * P->n_pairs + 4));
+    WPCD_CUDA_TRY(dev_malloc(&P->val32_copy, sizeof(float) * (size_t)P->nnz * P->n_pairs + 4));
     const int64_t nv = (int64_t)P->nnz * P->n_pairs;
     d2f_kernel<<<grid_for(nv, 256), 256, 0, s>>>(nv, P->val64, P->val32_copy);
     count_launches(1);

@@ -182,6 +182,14 @@ template <typename T>
 cudaError_t pool_malloc(T **p, size_t bytes, cudaStream_t s) {
   return pool_malloc(reinterpret_cast<void **>(p), bytes, s);
 }
+// Persistent device memory (problem tables, P0, packed operands, the MLP):
+// cudaMalloc / cudaFree, or the caller's allocator (wpcd_set_allocator)
+cudaError_t dev_malloc(void **p, size_t bytes);
+void dev_free(void *p);
+template <typename T>
+cudaError_t dev_malloc(T **p, size_t bytes) {
+  return dev_malloc(reinterpret_cast<void **>(p), bytes);
+}
 
 struct DfWork {
   float *xh = nullptr, *xl = nullptr, *yh = nullptr, *yl = nullptr;  // [2 dim B] each

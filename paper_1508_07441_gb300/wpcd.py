@@ -59,6 +59,7 @@ _SIGS = {
     "wpcd_last_error": (ctypes.c_char_p, []),
     "wpcd_version": (ctypes.c_int, []),
     "wpcd_launch_count": (ctypes.c_int64, []),
+    "wpcd_set_allocator": (ctypes.c_int, [_P, _P, _P]),
     "wpcd_P_timing": (ctypes.c_int, [_P, _F]),
     "wpcd_tangent_edges": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, _D]),
     "wpcd_problem_create": (ctypes.c_int, [ctypes.POINTER(wpcd_problem_desc), ctypes.POINTER(_P)]),
@@ -162,6 +163,47 @@ def _tensor_ptr(t):
 # ---------------------------------------------------------------------------
 def wpcd_launch_count() -> int:
     return int(lib().wpcd_launch_count())
+
+
+# device allocator callbacks: alloc(bytes, device, stream, user) -> pointer,
+# free(pointer, stream, user)
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+_hooks = None  # the installed callbacks, kept alive while installed
+
+
+def wpcd_set_allocator(alloc=None, free=None):
+    """Route every device allocation of the library through Python callables
+    alloc(nbytes, device, stream) -> int pointer and free(pointer, stream)
+    (stream: a cudaStream_t as int, 0 for the legacy default stream), or back
+    to the library's own allocator with both None.  Set it before creating
+    handles or after destroying them (the library refuses otherwise)."""
+    global _hooks
+    if alloc is None and free is None:
+        check(lib().wpcd_set_allocator(None, None, None))
+        _hooks = None
+        return
+    a = _ALLOC_FN(lambda n, dev, s, u: int(alloc(int(n), int(dev), int(s or 0))) or None)
+    f = _FREE_FN(lambda p, s, u: free(int(p), int(s or 0)))
+    check(lib().wpcd_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p), None))
+    _hooks = (a, f)
+
+
+def use_torch_allocator(enable=True):
+    """Take the library's device memory from PyTorch's caching allocator on
+    the stream of each request (enable=False: back to the library's own)."""
+    if not enable:
+        wpcd_set_allocator(None, None)
+        return
+    import torch
+
+    def alloc(nbytes, device, stream):
+        return torch.cuda.caching_allocator_alloc(nbytes, device=device, stream=stream)
+
+    def free(ptr, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    wpcd_set_allocator(alloc, free)
 
 
 def wpcd_solve_batch(problems, Ps, energies, max_iter=100, tol=1e-10, check_every=4,

@@ -95,6 +95,16 @@ def test_null_handles_are_rejected(W):
     L.wpcd_P_destroy(None)
 
 
+def test_set_allocator_argument_checks(W):
+    """wpcd_set_allocator takes both callbacks or neither (host-only check);
+    restoring the library's own allocator with nothing live succeeds."""
+    L = W.lib()
+    cb = W._ALLOC_FN(lambda n, dev, s, u: None)
+    assert L.wpcd_set_allocator(ctypes.cast(cb, ctypes.c_void_p), None, None) == W.WPCD_EINVAL
+    assert "both" in W.last_error()
+    assert L.wpcd_set_allocator(None, None, None) == W.WPCD_OK
+
+
 def test_no_cpu_fallback_when_library_missing(W, monkeypatch, tmp_path):
     monkeypatch.setattr(W, "LIB_PATH", str(tmp_path / "missing.so"))
     monkeypatch.setattr(W, "_lib", None)
