@@ -371,8 +371,8 @@ wpcd_status wpcd_born(wpcd_problem *pr, const wpcd_P *P, const double *E, int n_
 
 /* ---------------------------------------------------------------------------
  * Learned warm start.  The paper has no learned component: this is a growth
- * line around its iteration, which stays the fallback and the judge.  A
- * 3-layer MLP (n_in -> width -> width -> n_out, tanh hidden layers) is
+ * line around its iteration, which stays the fallback and decides
+ * convergence.  A 3-layer MLP (n_in -> width -> width -> n_out, tanh hidden layers) is
  * trained on the GPU by the library's own FP32 forward, backward and Adam
  * kernels and inferred with BF16 weights (FP32 arithmetic); its outputs are
  * coefficients of the solution in a projected basis Phi built from the

@@ -4,7 +4,7 @@
 // projected-basis helpers (Born terms, orthonormalisation, projection and
 // expansion) that turn its outputs into a starting vector for the solve.
 // The paper has no learned component; this is a growth line around its
-// iteration, which stays the fallback and the judge of convergence.
+// iteration, which stays the fallback and decides convergence.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 

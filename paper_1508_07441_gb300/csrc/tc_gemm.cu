@@ -823,7 +823,7 @@ TcShape tc_shape(int n) {
 }  // namespace
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
-// against the driver library)
+// against libcuda)
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
