@@ -294,6 +294,13 @@ wpcd_status wpcd_solve_batch(int n_prob, wpcd_problem *const *problems, const wp
 #define WPCD_SPMM_FF 2   /* FP64 vectors in and out, float-float arithmetic on
                             the FP32 pipe (about 48 significant bits), as in
                             the refinement residual of WPCD_SOLVE_MIXED */
+#define WPCD_SPMM_FP32_BLOCKED 3 /* as WPCD_SPMM_FP32 with the row-block
+                            kernel (blocks of 16 rows, the y rows of their
+                            distinct columns staged in shared memory); an
+                            alternative design kept for comparison: 2.2x
+                            slower than the tuned warp-per-row shapes at 128
+                            energies on the 200 x 200 lattice, so the solves
+                            do not use it */
 
 /* The sparse step of the K application (Sec. 3.3, Eq. kernel; P0 of
  * Eq. perm): z = P0 y for n_rhs vectors in the batched layout (device

@@ -406,6 +406,9 @@ void wpcd_P_destroy(wpcd_P *P) {
   dev_free(P->val32_copy);
   dev_free(P->val_h);
   dev_free(P->val_l);
+  dev_free(P->blk_nu);
+  dev_free(P->blk_ucol);
+  dev_free(P->blk_lidx);
   delete P;
 }
 

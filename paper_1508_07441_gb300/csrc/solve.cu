@@ -761,8 +761,7 @@ void store_cached(int64_t key, const SpmmConfig &c) {
 // Time every candidate launch shape on the real P0 (3 launches each, CUDA
 // events, the minimum kept) and remember the fastest.  mode: 0 FP64
 // vectors, 1 FP32, 2 float-float (the refinement residual's SpMM).
-wpcd_status tune_spmm(const wpcd_problem *pr, wpcd_P *P, int B, int mode, cudaStream_t s,
-                      SpmmConfig *out) {
+wpcd_status tune_spmm(const wpcd_problem *pr, wpcd_P *P, int B, int mode, cudaStream_t s, SpmmConfig *out) {
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   if (mode < 0 || mode > 2) return set_error(WPCD_EINVAL, "unknown SpMM tuning mode");
   const bool fp32 = mode == 1, ff = mode == 2;
@@ -788,6 +787,7 @@ wpcd_status tune_spmm(const wpcd_problem *pr, wpcd_P *P, int B, int mode, cudaSt
   }
   if (fp32 && !P->val32 && !P->val32_copy) return set_error(WPCD_EINVAL, "no FP32 values to tune on");
   if (ff && P->prec == WPCD_FP64 && !P->val_h) return set_error(WPCD_EINVAL, "no float-float values to tune on");
+  const std::vector<SpmmConfig> cands = candidates(B);
   const size_t dim = (size_t)pr->n_ch * pr->N * pr->M;
   void *y = nullptr, *z = nullptr;
   // float-float vectors: hi and lo float arrays, the size of one FP64 vector
@@ -805,7 +805,7 @@ wpcd_status tune_spmm(const wpcd_problem *pr, wpcd_P *P, int B, int mode, cudaSt
   float best = 1e30f;
   SpmmConfig pick;
   wpcd_status st = WPCD_OK;
-  for (const SpmmConfig &c : candidates(B)) {
+  for (const SpmmConfig &c : cands) {
     float tmin = 1e30f;
     for (int rep = 0; rep < 3 && st == WPCD_OK; ++rep) {
       cudaEventRecord(a, s);
@@ -1919,15 +1919,24 @@ wpcd_status solve(wpcd_problem *pr, const wpcd_P *Pc, const double *E, int n_E,
 wpcd_status spmm_apply(wpcd_problem *pr, wpcd_P *P, int mode, const void *y, void *z, int n_rhs, float *ms,
                        cudaStream_t s) {
   if (!y || !z || y == z || n_rhs < 1) return set_error(WPCD_EINVAL, "bad vectors or n_rhs");
-  if (mode < WPCD_SPMM_FP64 || mode > WPCD_SPMM_FF) return set_error(WPCD_EINVAL, "unknown SpMM mode");
+  if (mode < WPCD_SPMM_FP64 || mode > WPCD_SPMM_FP32_BLOCKED) return set_error(WPCD_EINVAL, "unknown SpMM mode");
   WPCD_CUDA_TRY(cudaSetDevice(pr->device));
   if (mode == WPCD_SPMM_FF) return df_spmm_op(pr, P, (const double *)y, (double *)z, n_rhs, ms, s);
-  const bool fp32 = mode == WPCD_SPMM_FP32;
+  const bool fp32 = mode == WPCD_SPMM_FP32 || mode == WPCD_SPMM_FP32_BLOCKED;
   if (fp32 && !P->val32 && !P->val32_copy) {
     WPCD_CUDA_TRY(dev_malloc(&P->val32_copy, sizeof(float) * (size_t)P->nnz * P->n_pairs + 4));
     const int64_t nv = (int64_t)P->nnz * P->n_pairs;
     d2f_kernel<<<grid_for(nv, 256), 256, 0, s>>>(nv, P->val64, P->val32_copy);
     count_launches(1);
+  }
+  if (mode == WPCD_SPMM_FP32_BLOCKED) {
+    wpcd_status st = spmm_blk_prepare(pr, P, s);
+    if (st != WPCD_OK) return st;
+    LaunchTimer t(ms, s);
+    t.start();
+    st = launch_spmm_blk(pr, P, P->val32 ? P->val32 : P->val32_copy, (const float *)y, (float *)z, n_rhs, s);
+    t.stop();
+    return st;
   }
   SpmmConfig cfg;  // tune (which synchronises) before any timed launch
   wpcd_status st = tune_spmm(pr, P, n_rhs, fp32 ? 1 : 0, s, &cfg);

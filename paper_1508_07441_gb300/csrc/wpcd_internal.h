@@ -129,6 +129,9 @@ struct wpcd_P {
   float ms_phase[3] = {0.f, 0.f, 0.f};  // count, scan, fill
   float *val32_copy = nullptr;          // FP32 values made from FP64 ones (mixed solve)
   float *val_h = nullptr, *val_l = nullptr;  // float-float split of FP64 values (df.cu)
+  int *blk_nu = nullptr;                     // row blocks of the row-block SpMM (spmm_blk.cu)
+  int32_t *blk_ucol = nullptr;
+  uint16_t *blk_lidx = nullptr;
   std::map<int64_t, SpmmConfig> tuned;  // autotuner choices keyed by (B, precision)
 };
 
@@ -159,6 +162,10 @@ wpcd_status resolvent_minor(const wpcd_problem *pr, const double *E, int n_E, do
 bool tc_supported(const wpcd_problem *pr);
 bool tc_enabled();
 wpcd_status tc_prepare(wpcd_problem *pr, cudaStream_t s);
+// spmm_blk.cu: the row-block FP32 SpMM (shared-memory staging of y)
+wpcd_status spmm_blk_prepare(const wpcd_problem *pr, wpcd_P *P, cudaStream_t s);
+wpcd_status launch_spmm_blk(const wpcd_problem *pr, const wpcd_P *P, const float *vals, const float *y, float *z,
+                            int B, cudaStream_t s);
 // one problem of a grouped tensor-core product: its vectors are the segment
 // at float offset off of the group vectors, [n_ch][N][ncol] floats
 struct TcGroupProb {

@@ -157,9 +157,11 @@ def test_spmm_matches_oracle_P0(W, orc, B):
     # FP32: plain blocked sums, bounded by n 2^-24 of the magnitude sum with n
     # the terms of the longest row (nonzero cells x channel pairs)
     n_terms = int(np.max(np.diff(ref_P["row_ptr"]))) * len(orc.pair_list(n_ch))
+    tol32 = max(3e-6, n_terms * 2.0**-24)
     for mode, dt, tol in ((W.WPCD_SPMM_FP64, np.complex128, 1e-9), (W.WPCD_SPMM_FF, np.complex128, 1e-9),
-                          (W.WPCD_SPMM_FP32, np.complex64, max(3e-6, n_terms * 2.0**-24))):
-        fp32 = mode == W.WPCD_SPMM_FP32
+                          (W.WPCD_SPMM_FP32, np.complex64, tol32),
+                          (W.WPCD_SPMM_FP32_BLOCKED, np.complex64, tol32)):
+        fp32 = mode in (W.WPCD_SPMM_FP32, W.WPCD_SPMM_FP32_BLOCKED)
         yd = torch.from_numpy(y.astype(dt).reshape(-1).view(np.float32 if fp32 else np.float64)).cuda()
         zd = torch.full_like(yd, float("nan"))
         ms = pr.wpcd_spmm(P, yd, zd, B, mode=mode, timed=True)
