@@ -59,10 +59,8 @@ __global__ void df_split_scaled_kernel(int64_t nc, const double2 *__restrict__ x
       v = make_double2(b.x * a.x - b.y * a.y, b.x * a.y + b.y * a.x);
     }
     const float hr = (float)v.x, hm = (float)v.y;
-    hi[2 * f] = hr;
-    hi[2 * f + 1] = hm;
-    lo[2 * f] = (float)(v.x - (double)hr);
-    lo[2 * f + 1] = (float)(v.y - (double)hm);
+    reinterpret_cast<float2 *>(hi)[f] = make_float2(hr, hm);
+    reinterpret_cast<float2 *>(lo)[f] = make_float2((float)(v.x - (double)hr), (float)(v.y - (double)hm));
   }
 }
 

@@ -561,13 +561,41 @@ __global__ void bupdate_kernel(int64_t n, int B, int k, const typename Cx<T>::t 
 }
 
 
-// dst32[f] = (float)(src[f] * inv[e])
+// the FP32 update with B even: two adjacent energies per thread, 16-byte
+// loads of the basis and the coefficients; u += sum_j c_j V_j in FP64
+__global__ void bupdate2_kernel(int64_t n2, int B2, int k, const float4 *__restrict__ V, size_t ld2,
+                                const float4 *__restrict__ c, double2 *__restrict__ u) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n2;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    const int e2 = (int)(f % B2);
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int j = 0; j < k; ++j) {
+      const float4 v = V[(size_t)j * ld2 + f];
+      const float4 cj = c[(size_t)j * B2 + e2];
+      a.x = fmaf(cj.x, v.x, fmaf(-cj.y, v.y, a.x));
+      a.y = fmaf(cj.x, v.y, fmaf(cj.y, v.x, a.y));
+      a.z = fmaf(cj.z, v.z, fmaf(-cj.w, v.w, a.z));
+      a.w = fmaf(cj.z, v.w, fmaf(cj.w, v.z, a.w));
+    }
+    double2 u0 = u[2 * f], u1 = u[2 * f + 1];
+    u0.x += (double)a.x;
+    u0.y += (double)a.y;
+    u1.x += (double)a.z;
+    u1.y += (double)a.w;
+    u[2 * f] = u0;
+    u[2 * f + 1] = u1;
+  }
+}
+
+// dst32[f] = (float)(src[f] * inv[e]) (the inner cycle's start vector,
+// scaled in FP64 and rounded once)
 __global__ void bnormalize_f32_kernel(int64_t n, int B, const double2 *src, const double *__restrict__ inv,
                                       float2 *dst) {
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n;
        f += (int64_t)gridDim.x * blockDim.x) {
     const double sc = inv[(int)(f % B)];
-    dst[f] = make_float2((float)(src[f].x * sc), (float)(src[f].y * sc));
+    const double2 v = src[f];
+    dst[f] = make_float2((float)(v.x * sc), (float)(v.y * sc));
   }
 }
 
@@ -1468,7 +1496,12 @@ wpcd_status solve_mixed(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solv
     bbacksub_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, m, m, kr.H, kr.bet, kr.y);
     // u += |r| (V y)   (FP64 accumulation of the FP32 correction)
     bupdate_coef_kernel<float><<<(m * B + 255) / 256, 256, 0, s>>>(m, B, kr.y, k64.nrm, kr.hc);
-    bupdate_kernel<float><<<vg, 256, 0, s>>>(n, B, m, kr.vec(0), cx.dim * B, kr.hc, (double2 *)cx.u);
+    if (B % 2 == 0)
+      bupdate2_kernel<<<grid_for(n / 2, 256), 256, 0, s>>>(n / 2, B / 2, m, reinterpret_cast<const float4 *>(kr.vec(0)),
+                                                           cx.dim * B / 2, reinterpret_cast<const float4 *>(kr.hc),
+                                                           (double2 *)cx.u);
+    else
+      bupdate_kernel<float><<<vg, 256, 0, s>>>(n, B, m, kr.vec(0), cx.dim * B, kr.hc, (double2 *)cx.u);
     count_launches(3);
     return WPCD_OK;
   };
