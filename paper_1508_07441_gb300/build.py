@@ -54,6 +54,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
             cmd = [cc] + _flags() + ["-c", src, "-o", obj]
             if s.endswith(".cu"):
                 cmd += ["-Xptxas", "-warn-spills"]
+            else:  # host setup: OpenMP over the pair-matrix rows
+                cmd += ["-Xcompiler", "-fopenmp"]
             jobs.append((s, cmd))
     with cf.ThreadPoolExecutor(max_workers=max(1, len(jobs))) as ex:
         futs = {ex.submit(subprocess.run, cmd, capture_output=True, text=True): s for s, cmd in jobs}
@@ -66,7 +68,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     objs = [os.path.join(OUT_DIR, s + ".o") for s in SOURCES]
     if force or jobs or not os.path.exists(LIB):
         tmp = LIB + f".{os.getpid()}.tmp"
-        cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
+        cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-Xcompiler", "-fopenmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             print(r.stdout + r.stderr)

@@ -240,9 +240,15 @@ static wpcd_status create(const wpcd_problem_desc *d, wpcd_problem **out) {
   pr->O.assign((size_t)d->n_ch * N * N, 0.0);
   pr->v.assign((size_t)d->n_ch * N * N, 0.0);
   pr->Vt.assign((size_t)d->n_ch * N * N, 0.0);
+  // the potential matrices of every channel (rows in parallel inside), then
+  // the channels' eigenproblems side by side on the host cores
+  std::vector<std::vector<double>> vs(d->n_ch), hs(d->n_ch), epss(d->n_ch), Os(d->n_ch);
+  for (int l = 0; l < d->n_ch; ++l)
+    pair_matrices(N, d->p_edges, d->n_pair_nodes, l, d->n_terms, d->V, d->a, vs[l], hs[l]);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int l = 0; l < d->n_ch; ++l) pair_eig(N, hs[l], epss[l], Os[l]);
   for (int l = 0; l < d->n_ch; ++l) {
-    std::vector<double> v, eps, O;
-    pair_setup(N, d->p_edges, d->n_pair_nodes, l, d->n_terms, d->V, d->a, v, eps, O);
+    const std::vector<double> &v = vs[l], &eps = epss[l], &O = Os[l];
     if ((int)eps.size() != N) {
       delete pr;
       return set_error(WPCD_EINVAL, "pair Hamiltonian eigensolver did not converge");
@@ -252,6 +258,7 @@ static wpcd_status create(const wpcd_problem_desc *d, wpcd_problem **out) {
     std::copy(v.begin(), v.end(), pr->v.begin() + (size_t)l * N * N);
     // Vt = O^T V1 in the channel basis = v O^T:  Vt[i][k] = sum_m v[i][m] O[k][m]
     double *Vt = pr->Vt.data() + (size_t)l * N * N;
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < N; ++i)
       for (int k = 0; k < N; ++k) {
         double s = 0.0;

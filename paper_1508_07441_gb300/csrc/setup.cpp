@@ -205,12 +205,12 @@ bool sym_eig(int n, std::vector<double> A, std::vector<double> &evals, std::vect
   return true;
 }
 
-// Pair quantities of channel l: free-packet potential matrix v (Eq. vpot
+// Pair matrices of channel l: the free-packet potential matrix v (Eq. vpot
 // with unit weight functions in the p^2 dp measure, n_nodes GL points per
-// bin), h1 = diag(<p^2>) + v and its eigen-decomposition (Eq. exp_z).
-void pair_setup(int N, const double *edges, int n_nodes, int l, int n_terms, const double *V,
-                const double *a, std::vector<double> &v, std::vector<double> &eps,
-                std::vector<double> &O) {
+// bin) and h1 = diag(<p^2>) + v, whose eigen-decomposition (Eq. exp_z) is
+// pair_eig's
+void pair_matrices(int N, const double *edges, int n_nodes, int l, int n_terms, const double *V,
+                   const double *a, std::vector<double> &v, std::vector<double> &h) {
   std::vector<double> t(n_nodes), w(n_nodes);
   gauss_legendre(n_nodes, t.data(), w.data());
   std::vector<double> pn((size_t)N * n_nodes), pw((size_t)N * n_nodes), rsB(N);
@@ -225,6 +225,10 @@ void pair_setup(int N, const double *edges, int n_nodes, int l, int n_terms, con
     rsB[i] = 1.0 / std::sqrt(shell_volume(lo, hi));
   }
   v.assign((size_t)N * N, 0.0);
+  // rows in parallel on the host cores (each element is computed once, by
+  // one thread, in the same order as serially: the result does not depend
+  // on the thread count)
+#pragma omp parallel for schedule(dynamic, 2)
   for (int i = 0; i < N; ++i)
     for (int k = i; k < N; ++k) {
       double s = 0.0;
@@ -240,7 +244,7 @@ void pair_setup(int N, const double *edges, int n_nodes, int l, int n_terms, con
       v[(size_t)i * N + k] = s;
       v[(size_t)k * N + i] = s;
     }
-  std::vector<double> h(v);
+  h = v;
   for (int i = 0; i < N; ++i) {
     double lo = edges[i], hi = edges[i + 1];
     // <p^2>_i = int p^4 dp / B_i
@@ -248,6 +252,10 @@ void pair_setup(int N, const double *edges, int n_nodes, int l, int n_terms, con
     double p5 = (hi - lo) * (hi2 * hi2 + hi2 * hi * lo + hi2 * lo2 + hi * lo * lo2 + lo2 * lo2) / 5.0;
     h[(size_t)i * N + i] += p5 / shell_volume(lo, hi);
   }
+}
+
+// eps, O (eigenvectors as rows) of h1; empty on failure
+void pair_eig(int N, const std::vector<double> &h, std::vector<double> &eps, std::vector<double> &O) {
   if (!sym_eig(N, h, eps, O)) {
     eps.clear();
     O.clear();

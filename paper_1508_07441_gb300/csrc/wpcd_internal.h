@@ -73,9 +73,9 @@ double v_partial_wave(int l, double p, double pp, int n_terms, const double *V, 
 // symmetric eigensolver: A (n x n, row-major) -> eigenvalues ascending,
 // vectors as rows with the largest-magnitude component positive.
 bool sym_eig(int n, std::vector<double> A, std::vector<double> &evals, std::vector<double> &rows);
-void pair_setup(int N, const double *edges, int n_nodes, int l, int n_terms, const double *V,
-                const double *a, std::vector<double> &v, std::vector<double> &eps,
-                std::vector<double> &O);
+void pair_matrices(int N, const double *edges, int n_nodes, int l, int n_terms, const double *V,
+                   const double *a, std::vector<double> &v, std::vector<double> &h);
+void pair_eig(int N, const std::vector<double> &h, std::vector<double> &eps, std::vector<double> &O);
 inline double shell_volume(double lo, double hi) {
   // int_lo^hi p^2 dp, written to avoid cancellation for narrow bins
   return (hi - lo) * (hi * hi + hi * lo + lo * lo) / 3.0;
