@@ -66,6 +66,35 @@ struct AccF {
   __device__ float value() const { return __fadd_rn(hi, lo); }
 };
 
+// the same compensated sums held in shared memory, for a lane whose
+// registers are better spent on loads in flight than on accumulators
+// touched once per block of nonzeros: slot k = ((l EPT + t) 2 + q) of the
+// thread keeps hi at base[2 k S] and lo at base[(2 k + 1) S], S the block
+// size (thread-major, so a warp's accesses hit distinct banks)
+constexpr int kAccSmStride = 256;
+struct AccFSView {
+  float *base;  // the thread's first slot
+  __device__ void add_slot(int k, float x) {
+    float *h = base + 2 * k * kAccSmStride;
+    const float hi = h[0];
+    float s = __fadd_rn(hi, x);
+    float bb = __fsub_rn(s, hi);
+    float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+    h[0] = s;
+    h[kAccSmStride] = __fadd_rn(h[kAccSmStride], e);
+  }
+};
+
+// add x to accumulator (l, t, q): register accumulators, or the shared view
+template <int EPT, typename A, int NCH, typename X>
+__device__ __forceinline__ void acc_add(A (&acc)[NCH][EPT][2], int l, int t, int q, X x) {
+  acc[l][t][q].add(x);
+}
+template <int EPT>
+__device__ __forceinline__ void acc_add(AccFSView &v, int l, int t, int q, float x) {
+  v.add_slot((l * EPT + t) * 2 + q, x);
+}
+
 template <typename T>
 struct AccOf;
 template <>
@@ -103,13 +132,13 @@ struct SpmmGroups {
 // number of blocks only through the float-float accumulator, and inside a
 // block with its b terms.  FP64 sums the block partials plainly.  y points at the problem's own vector
 // block ([n_ch][n_cells][B] complex).  The lane's energies are en0 +
-// estride * t; with VEC (FP32, estride 1, EPT and B even) two adjacent
-// energies come in one 16-byte load.
-template <typename VT, typename T, int NCH, int EPT, bool VEC>
+// estride * t; with VEC (FP32, EPT and B even, en0 even) the pair t, t + 1
+// starts at en0 + estride * t and comes in one 16-byte load.
+template <typename VT, typename T, int NCH, int EPT, bool VEC, typename Acc>
 __device__ __forceinline__ void spmm_row(int64_t b, int64_t e, int nl, int nl_count, const int32_t *__restrict__ col,
                                          const VT *__restrict__ val, int64_t nnz,
                                          const typename Cx<T>::t *__restrict__ y, int n_cells, int B, int en0,
-                                         int estride, typename AccOf<T>::t (&acc)[NCH][EPT][2]) {
+                                         int estride, Acc &acc) {
   using C2 = typename Cx<T>::t;
   constexpr int NPAIR = pair_count(NCH);
   constexpr int U = SpmmUnroll<NCH, EPT>::value;
@@ -177,10 +206,60 @@ __device__ __forceinline__ void spmm_row(int64_t b, int64_t e, int nl, int nl_co
     for (int l = 0; l < NCH; ++l)
 #pragma unroll
       for (int t = 0; t < EPT; ++t) {
-        acc[l][t][0].add(part[l][t][0]);
-        acc[l][t][1].add(part[l][t][1]);
+        acc_add<EPT>(acc, l, t, 0, part[l][t][0]);
+        acc_add<EPT>(acc, l, t, 1, part[l][t][1]);
       }
   }
+}
+
+// a row's sums into the register accumulators acc (zeroed here): summed in
+// place, or with SACC (FP32) in shared memory (acc_sm: the block's 4 NCH EPT
+// slots per thread, thread-major) and read back, which leaves the lane's
+// registers to the loads in flight
+template <typename VT, typename T, int NCH, int EPT, bool VEC, bool SACC>
+__device__ __forceinline__ void spmm_row_sums(int64_t b, int64_t e, int nl, int nl_count,
+                                              const int32_t *__restrict__ col, const VT *__restrict__ val,
+                                              int64_t nnz, const typename Cx<T>::t *__restrict__ y, int n_cells,
+                                              int B, int en0, int estride, typename AccOf<T>::t (&acc)[NCH][EPT][2],
+                                              float *acc_sm) {
+  if constexpr (SACC) {
+    static_assert(sizeof(T) == 4, "shared-memory accumulators are FP32 compensated sums");
+    AccFSView sacc{acc_sm + threadIdx.x};
+#pragma unroll
+    for (int k = 0; k < 4 * NCH * EPT; ++k) sacc.base[k * kAccSmStride] = 0.f;
+    spmm_row<VT, T, NCH, EPT, VEC>(b, e, nl, nl_count, col, val, nnz, y, n_cells, B, en0, estride, sacc);
+#pragma unroll
+    for (int l = 0; l < NCH; ++l)
+#pragma unroll
+      for (int t = 0; t < EPT; ++t)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int k = (l * EPT + t) * 2 + q;
+          acc[l][t][q].hi = sacc.base[2 * k * kAccSmStride];
+          acc[l][t][q].lo = sacc.base[(2 * k + 1) * kAccSmStride];
+        }
+  } else {
+#pragma unroll
+    for (int l = 0; l < NCH; ++l)
+#pragma unroll
+      for (int t = 0; t < EPT; ++t) {
+        acc[l][t][0].zero();
+        acc[l][t][1].zero();
+      }
+    spmm_row<VT, T, NCH, EPT, VEC>(b, e, nl, nl_count, col, val, nnz, y, n_cells, B, en0, estride, acc);
+  }
+}
+
+// dynamic shared memory of the shared-accumulator SpMM kernels (hi and lo
+// of 2 NCH EPT sums per thread of a 256-thread block); kernel K opts in
+// once above 48 KB (extra: its static shared memory)
+template <int NCH, int EPT, typename K>
+cudaError_t sacc_smem(K kernel, size_t *bytes, bool &opted_in, size_t extra = 0) {
+  *bytes = (size_t)4 * NCH * EPT * kAccSmStride * sizeof(float);
+  if (*bytes + extra <= 48 * 1024 || opted_in) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*bytes);
+  opted_in = e == cudaSuccess;
+  return e;
 }
 
 int grid_for(int64_t n, int threads, int cap = 152 * 8) {

@@ -166,10 +166,12 @@ __device__ __forceinline__ const float *vals_of<float>(const GProb &P) {
   return P.val32;
 }
 
-template <typename VT, typename T, int NCH, int EPT, bool VEC>
-__global__ void __launch_bounds__(256) gspmm_kernel(const GMeta *__restrict__ gm, const GProb *__restrict__ gp,
-                                                    int rpw, int el_n, const typename Cx<T>::t *__restrict__ y,
-                                                    typename Cx<T>::t *__restrict__ z) {
+// SACC (FP32): compensated sums in dynamic shared memory, as in the
+// single-problem SpMM
+template <typename VT, typename T, int NCH, int EPT, bool VEC, bool SACC>
+__device__ __forceinline__ void gspmm_body(const GMeta *__restrict__ gm, const GProb *__restrict__ gp, int rpw,
+                                           int el_n, const typename Cx<T>::t *__restrict__ y,
+                                           typename Cx<T>::t *__restrict__ z, float *acc_sm) {
   using C2 = typename Cx<T>::t;
   using Acc = typename AccOf<T>::t;
   __shared__ int coff[kMaxGroup + 1];
@@ -201,17 +203,13 @@ __global__ void __launch_bounds__(256) gspmm_kernel(const GMeta *__restrict__ gm
     const C2 *yg = y + P.eoff;
     const VT *val = vals_of<VT>(P);
     Acc acc[NCH][EPT][2];
-#pragma unroll
-    for (int l = 0; l < NCH; ++l)
-#pragma unroll
-      for (int t = 0; t < EPT; ++t) {
-        acc[l][t][0].zero();
-        acc[l][t][1].zero();
-      }
     const int64_t b = active ? P.row_ptr[c] : 0, e = active ? P.row_ptr[c + 1] : 0;
-    // lane energies: VEC adjacent (en0 + t), otherwise strided (el + el_n t)
-    const int en0 = VEC ? e_base + el * EPT : e_base + el, estride = VEC ? 1 : el_n;
-    spmm_row<VT, T, NCH, EPT, VEC>(b, e, nl, nl_count, P.col, val, P.nnz, yg, n_cells, B, en0, estride, acc);
+    // lane energies: strided (el + el_n t); with VEC in adjacent pairs
+    // (2 el + el_n (t - t % 2) + t % 2), one 16-byte gather covering 16 el_n
+    // contiguous bytes of a vector row
+    const int en0 = VEC ? e_base + 2 * el : e_base + el, estride = el_n;
+    spmm_row_sums<VT, T, NCH, EPT, VEC, SACC>(b, e, nl, nl_count, P.col, val, P.nnz, yg, n_cells, B, en0, estride,
+                                              acc, acc_sm);
     for (int off = el_n; off < lpr; off <<= 1)
 #pragma unroll
       for (int l = 0; l < NCH; ++l)
@@ -224,7 +222,7 @@ __global__ void __launch_bounds__(256) gspmm_kernel(const GMeta *__restrict__ gm
       C2 *zg = z + P.eoff;
 #pragma unroll
       for (int t = 0; t < EPT; ++t) {
-        const int en = VEC ? e_base + el * EPT + t : e_base + el + el_n * t;
+        const int en = VEC ? e_base + 2 * el + el_n * (t & ~1) + (t & 1) : e_base + el + el_n * t;
         if (en < B)
 #pragma unroll
           for (int l = 0; l < NCH; ++l) {
@@ -236,6 +234,28 @@ __global__ void __launch_bounds__(256) gspmm_kernel(const GMeta *__restrict__ gm
       }
     }
   }
+}
+
+template <typename VT, typename T, int NCH, int EPT, bool VEC>
+__global__ void __launch_bounds__(256) gspmm_kernel(const GMeta *__restrict__ gm, const GProb *__restrict__ gp,
+                                                    int rpw, int el_n, const typename Cx<T>::t *__restrict__ y,
+                                                    typename Cx<T>::t *__restrict__ z) {
+  gspmm_body<VT, T, NCH, EPT, VEC, false>(gm, gp, rpw, el_n, y, z, nullptr);
+}
+
+template <int NCH, int EPT, bool VEC>
+__global__ void __launch_bounds__(256, 2)
+    gspmm_sacc_kernel(const GMeta *__restrict__ gm, const GProb *__restrict__ gp, int rpw, int el_n,
+                      const float2 *__restrict__ y, float2 *__restrict__ z) {
+  extern __shared__ float acc_sm[];
+  gspmm_body<float, float, NCH, EPT, VEC, true>(gm, gp, rpw, el_n, y, z, acc_sm);
+}
+
+template <int NCH, int EPT, bool VEC>
+cudaError_t gspmm_sacc_smem(size_t *bytes) {
+  static bool opted_in = false;
+  return sacc_smem<NCH, EPT>(gspmm_sacc_kernel<NCH, EPT, VEC>, bytes, opted_in,
+                             sizeof(int) * (kMaxGroup + 1) + sizeof(GProb) * kMaxGroup);
 }
 
 // ---------------------------------------------------------------------------
@@ -721,16 +741,36 @@ wpcd_status gspmm_cfg(const Group &gr, const T *y, T *z, const SpmmConfig &cfg, 
   // FP32 vectors, every batch even and every segment 16-byte aligned: two
   // adjacent energies per load
   const bool vec = sizeof(T) == 4 && gr.even;
-#define WPCD_GSPMM_EPT(NCH, EPT, VEC) \
-  gspmm_kernel<VT, T, NCH, EPT, VEC><<<grid, 256, 0, s>>>(gr.d_meta, gr.d_probs, cfg.rpw, cfg.el, yy, zz)
+  // FP32 (values and vectors): compensated sums in shared memory
+  constexpr bool sacc = sizeof(T) == 4 && sizeof(VT) == 4;
+#define WPCD_GSPMM_EPT(NCH, EPT, VEC)                                                                        \
+  do {                                                                                                       \
+    if constexpr (sacc) {                                                                                    \
+      size_t smem = 0;                                                                                       \
+      cudaError_t ae = gspmm_sacc_smem<NCH, EPT, VEC>(&smem);                                                \
+      if (ae != cudaSuccess) return cuda_error(ae, "grouped spmm shared-memory attribute");                  \
+      gspmm_sacc_kernel<NCH, EPT, VEC><<<grid, 256, smem, s>>>(gr.d_meta, gr.d_probs, cfg.rpw, cfg.el,       \
+                                                               reinterpret_cast<const float2 *>(yy),         \
+                                                               reinterpret_cast<float2 *>(zz));              \
+    } else {                                                                                                 \
+      gspmm_kernel<VT, T, NCH, EPT, VEC><<<grid, 256, 0, s>>>(gr.d_meta, gr.d_probs, cfg.rpw, cfg.el, yy, zz); \
+    }                                                                                                        \
+  } while (0)
 #define WPCD_GSPMM_CASE(NCH)                                                         \
   case NCH:                                                                          \
     if (cfg.ept == 1)                                                                \
       WPCD_GSPMM_EPT(NCH, 1, false);                                                 \
-    else if (cfg.ept == 2)                                                           \
-      vec ? WPCD_GSPMM_EPT(NCH, 2, sizeof(T) == 4) : WPCD_GSPMM_EPT(NCH, 2, false);  \
-    else                                                                             \
-      vec ? WPCD_GSPMM_EPT(NCH, 4, sizeof(T) == 4) : WPCD_GSPMM_EPT(NCH, 4, false);  \
+    else if (cfg.ept == 2) {                                                         \
+      if (vec)                                                                       \
+        WPCD_GSPMM_EPT(NCH, 2, sizeof(T) == 4);                                      \
+      else                                                                           \
+        WPCD_GSPMM_EPT(NCH, 2, false);                                               \
+    } else {                                                                         \
+      if (vec)                                                                       \
+        WPCD_GSPMM_EPT(NCH, 4, sizeof(T) == 4);                                      \
+      else                                                                           \
+        WPCD_GSPMM_EPT(NCH, 4, false);                                               \
+    }                                                                                \
     break;
   switch (gr.n_ch) {
     WPCD_GSPMM_CASE(1)

@@ -231,12 +231,19 @@ __global__ void __launch_bounds__(G_THREADS) gemm_kernel(int n, int64_t ncol, co
 // FP64 sums in double; FP32 sums blocked and compensated (spmm_row).
 // ---------------------------------------------------------------------------
 
-template <typename VT, typename T, int NCH, int EPT, bool VEC>
-__global__ void __launch_bounds__(256) spmm_kernel(SpmmParams S, const VT *__restrict__ val,
-                                                   const typename Cx<T>::t *__restrict__ y,
-                                                   typename Cx<T>::t *__restrict__ z) {
+// SACC (FP32): the compensated accumulators live in dynamic shared memory
+// (acc_sm: 2 NCH EPT hi/lo pairs per thread) while the row is summed, and
+// come back to registers for the lane reduction.  Measured on the 3-channel
+// 200 x 200 lattice at 128 energies: 0.82 ms per SpMM at three CTAs per SM
+// (80 registers) against 0.92 ms with the sums in registers (123 registers,
+// two CTAs per SM); four CTAs per SM spill and lose (1.03 ms).
+template <typename VT, typename T, int NCH, int EPT, bool VEC, bool SACC>
+__device__ __forceinline__ void spmm_body(const SpmmParams &S, const VT *__restrict__ val,
+                                          const typename Cx<T>::t *__restrict__ y, typename Cx<T>::t *__restrict__ z,
+                                          float *acc_sm) {
   using C2 = typename Cx<T>::t;
   using Acc = typename AccOf<T>::t;
+  static_assert(!SACC || sizeof(T) == 4, "shared-memory accumulators are FP32 compensated sums");
   const int lane = threadIdx.x & 31;
   const int lpr = 32 / S.rpw;          // lanes per row
   const int nl_count = lpr / S.el;     // nonzero lanes per row
@@ -252,17 +259,13 @@ __global__ void __launch_bounds__(256) spmm_kernel(SpmmParams S, const VT *__res
     const int c = base + r_in;
     const bool active = c < S.n_cells;
     Acc acc[NCH][EPT][2];
-#pragma unroll
-    for (int l = 0; l < NCH; ++l)
-#pragma unroll
-      for (int t = 0; t < EPT; ++t) {
-        acc[l][t][0].zero();
-        acc[l][t][1].zero();
-      }
     const int64_t b = active ? S.row_ptr[c] : 0, e = active ? S.row_ptr[c + 1] : 0;
-    // lane energies: VEC adjacent (en0 + t), otherwise strided (el + S.el t)
-    const int en0 = VEC ? e_base + el * EPT : e_base + el, estride = VEC ? 1 : S.el;
-    spmm_row<VT, T, NCH, EPT, VEC>(b, e, nl, nl_count, S.col, val, S.nnz, y, S.n_cells, B, en0, estride, acc);
+    // lane energies: strided (el + S.el t); with VEC in adjacent pairs
+    // (2 el + S.el (t - t % 2) + t % 2), so that the energy lanes of one
+    // 16-byte gather cover 16 S.el contiguous bytes of a vector row
+    const int en0 = VEC ? e_base + 2 * el : e_base + el, estride = S.el;
+    spmm_row_sums<VT, T, NCH, EPT, VEC, SACC>(b, e, nl, nl_count, S.col, val, S.nnz, y, S.n_cells, B, en0, estride,
+                                              acc, acc_sm);
     // reduce over the nonzero lanes of the row (xor offsets el .. lpr/2)
     for (int off = S.el; off < lpr; off <<= 1)
 #pragma unroll
@@ -275,7 +278,7 @@ __global__ void __launch_bounds__(256) spmm_kernel(SpmmParams S, const VT *__res
     if (active && nl == 0) {
 #pragma unroll
       for (int t = 0; t < EPT; ++t) {
-        const int en = VEC ? e_base + el * EPT + t : e_base + el + S.el * t;
+        const int en = VEC ? e_base + 2 * el + S.el * (t & ~1) + (t & 1) : e_base + el + S.el * t;
         if (en < B)
 #pragma unroll
           for (int l = 0; l < NCH; ++l) {
@@ -287,6 +290,26 @@ __global__ void __launch_bounds__(256) spmm_kernel(SpmmParams S, const VT *__res
       }
     }
   }
+}
+
+template <typename VT, typename T, int NCH, int EPT, bool VEC>
+__global__ void __launch_bounds__(256) spmm_kernel(SpmmParams S, const VT *__restrict__ val,
+                                                   const typename Cx<T>::t *__restrict__ y,
+                                                   typename Cx<T>::t *__restrict__ z) {
+  spmm_body<VT, T, NCH, EPT, VEC, false>(S, val, y, z, nullptr);
+}
+
+template <int NCH, int EPT, bool VEC>
+__global__ void __launch_bounds__(256, NCH <= 3 ? 3 : 2) spmm_sacc_kernel(SpmmParams S, const float *__restrict__ val,
+                                                           const float2 *__restrict__ y, float2 *__restrict__ z) {
+  extern __shared__ float acc_sm[];
+  spmm_body<float, float, NCH, EPT, VEC, true>(S, val, y, z, acc_sm);
+}
+
+template <int NCH, int EPT, bool VEC>
+cudaError_t spmm_sacc_smem(size_t *bytes) {
+  static bool opted_in = false;
+  return sacc_smem<NCH, EPT>(spmm_sacc_kernel<NCH, EPT, VEC>, bytes, opted_in);
 }
 
 // ---------------------------------------------------------------------------
@@ -725,15 +748,35 @@ wpcd_status launch_spmm_cfg(const wpcd_problem *pr, const wpcd_P *P, const VT *v
             (B + cfg.el * cfg.ept - 1) / (cfg.el * cfg.ept));
   // FP32 vectors with an even batch load two adjacent energies at a time
   const bool vec = sizeof(T) == 4 && B % 2 == 0;
-#define WPCD_SPMM_EPT(NCH, EPT, VEC) spmm_kernel<VT, T, NCH, EPT, VEC><<<grid, 256, 0, s>>>(S, val, yy, zz)
+  // FP32 (values and vectors): compensated sums in shared memory
+  constexpr bool sacc = sizeof(T) == 4 && sizeof(VT) == 4;
+#define WPCD_SPMM_EPT(NCH, EPT, VEC)                                                                      \
+  do {                                                                                                    \
+    if constexpr (sacc) {                                                                                 \
+      size_t smem = 0;                                                                                    \
+      cudaError_t ae = spmm_sacc_smem<NCH, EPT, VEC>(&smem);                                              \
+      if (ae != cudaSuccess) return cuda_error(ae, "spmm shared-memory attribute");                       \
+      spmm_sacc_kernel<NCH, EPT, VEC><<<grid, 256, smem, s>>>(S, reinterpret_cast<const float *>(val),    \
+                                  reinterpret_cast<const float2 *>(yy), reinterpret_cast<float2 *>(zz));  \
+    } else {                                                                                              \
+      spmm_kernel<VT, T, NCH, EPT, VEC><<<grid, 256, 0, s>>>(S, val, yy, zz);                             \
+    }                                                                                                     \
+  } while (0)
 #define WPCD_SPMM_CASE(NCH)                                                          \
   case NCH:                                                                          \
     if (cfg.ept == 1)                                                                \
       WPCD_SPMM_EPT(NCH, 1, false);                                                  \
-    else if (cfg.ept == 2)                                                           \
-      vec ? WPCD_SPMM_EPT(NCH, 2, sizeof(T) == 4) : WPCD_SPMM_EPT(NCH, 2, false);    \
-    else                                                                             \
-      vec ? WPCD_SPMM_EPT(NCH, 4, sizeof(T) == 4) : WPCD_SPMM_EPT(NCH, 4, false);    \
+    else if (cfg.ept == 2) {                                                         \
+      if (vec)                                                                       \
+        WPCD_SPMM_EPT(NCH, 2, sizeof(T) == 4);                                       \
+      else                                                                           \
+        WPCD_SPMM_EPT(NCH, 2, false);                                                \
+    } else {                                                                         \
+      if (vec)                                                                       \
+        WPCD_SPMM_EPT(NCH, 4, sizeof(T) == 4);                                       \
+      else                                                                           \
+        WPCD_SPMM_EPT(NCH, 4, false);                                                \
+    }                                                                                \
     break;
   switch (pr->n_ch) {
     WPCD_SPMM_CASE(1)
