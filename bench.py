@@ -139,12 +139,12 @@ def fill_flops_per_node(n_ch: int, n_pairs: int) -> int:
 # of the kernel as it stands (profiles/ names the capture); None where no
 # capture of the current kernel exists
 NCU_TRAFFIC = {
-    "fill_kernel<FP64,3>": 435.7e6,
-    "spmm_kernel<float>": 368.9e6,
+    "fill_kernel<FP64,3>": 436.8e6,
+    "spmm_sacc_kernel<FP32>": 375.9e6,
     "tc_gemm_kernel<TF32x3> (Vt, G1)": 329.1e6,
-    "tc_gemm_kernel<TF32x3> (O)": 331.6e6,
-    "spmm_df_kernel": 1045.6e6,
-    "gemm_df_kernel": 907.3e6,
+    "tc_gemm_kernel<TF32x3> (O)": 331.5e6,
+    "spmm_df_kernel": 956.8e6,
+    "gemm_df_kernel": 903.6e6,
 }
 
 
@@ -282,7 +282,7 @@ def kernel_rooflines(W, pr, w, phases, n_nodes, n_e, stream, flush, peaks, f_sm,
     # FP32 inner cycles: P0 SpMM and the two tensor-core channel products
     ms = _time_kernel(stream, flush, lambda: pr.wpcd_spmm(P, x32, y32, n_e, mode=W.WPCD_SPMM_FP32, stream=stream,
                                                            timed=True))
-    entry("spmm_kernel<float>", "alu", spmm_flops / (ms * 1e-3) / 1e12, fp32, "TFLOP/s", ms, n32,
+    entry("spmm_sacc_kernel<FP32>", "alu", spmm_flops / (ms * 1e-3) / 1e12, fp32, "TFLOP/s", ms, n32,
           f"4 n_pairs nnz B = {spmm_flops:.3e} FP32 flops (one real-by-complex multiply-add per block entry and "
           "energy)", src32)
     tc_bytes = 3.0 * 8 * dim * n_e
