@@ -320,6 +320,13 @@ wpcd_status wpcd_spmm(wpcd_problem *pr, wpcd_P *P, int mode, const void *y, void
                               hi*hi + hi*lo + lo*hi accumulated in FP32 */
 #define WPCD_GEMM_FF 3     /* FP64 vectors in and out, float-float arithmetic on
                               the FP32 pipe (about 48 significant bits) */
+#define WPCD_GEMM_DIGITS 4 /* FP64 vectors in and out: the FP64 A and the
+                              float-float split of (G1 o X) cut into eight
+                              7-bit bf16 digit planes over per-row / per-column
+                              power-of-two scales; the 36 digit-plane products
+                              of weight above 2^-56 on the tensor cores
+                              (tcgen05 kind::f16), each diagonal summed exactly
+                              in FP32, combined in FP64; N <= 256 */
 
 /* One dense step of the K application (Sec. 3.3, Eq. kernel): for every
  * channel block ch, Y_ch = A_ch (G1 o X)_ch with A = Vt (which = 0) or O
@@ -330,9 +337,11 @@ wpcd_status wpcd_spmm(wpcd_problem *pr, wpcd_P *P, int mode, const void *y, void
  * WPCD_GEMM_TF32X3, FP64 otherwise, distinct.  The mixed solve runs its FP32
  * inner cycles with WPCD_GEMM_TF32X3 when N <= 512 (the environment
  * variable WPCD_GEMM=simt selects WPCD_GEMM_FP32 instead) and its residual
- * with WPCD_GEMM_FF.  kernel_ms: NULL, or receives the device time of the
+ * and Born-term products with WPCD_GEMM_DIGITS when N <= 256, else
+ * WPCD_GEMM_FF (WPCD_RESIDUAL_GEMM=ff selects WPCD_GEMM_FF always).  kernel_ms: NULL, or receives the device time of the
  * product kernel alone (the call then synchronises).  EINVAL for a bad
- * mode, bad vectors, or WPCD_GEMM_TF32X3 with N > 512; ETIMEOUT if a
+ * mode, bad vectors, WPCD_GEMM_TF32X3 with N > 512 or WPCD_GEMM_DIGITS with
+ * N > 256; ETIMEOUT if a
  * tensor-core wait ran out. */
 wpcd_status wpcd_channel_gemm(wpcd_problem *pr, int which, int mode, const void *g, const void *x, void *y,
                               int n_rhs, float *kernel_ms, void *stream);

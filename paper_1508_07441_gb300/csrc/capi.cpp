@@ -159,6 +159,12 @@ static void free_tables(DeviceTables &d) {
   dev_free(d.Vt_h);
   dev_free(d.Vt_l);
   d.O_h = d.O_l = d.Vt_h = d.Vt_l = nullptr;
+  dev_free(d.O_oz);
+  dev_free(d.Vt_oz);
+  dev_free(d.O_ozE);
+  dev_free(d.Vt_ozE);
+  d.O_oz = d.Vt_oz = nullptr;
+  d.O_ozE = d.Vt_ozE = nullptr;
   dev_free(d.tc_err);
   d.O_tc = d.Vt_tc = nullptr;
   d.tc_err = nullptr;

@@ -93,13 +93,25 @@ __global__ void df_join_kernel(int64_t n, const float *__restrict__ hi, const fl
 }
 
 template <bool OUT_DF>
-void gemm_df(const wpcd_problem *pr, bool use_O, const float *Bh, const float *Bl, double *C, float *Ch, float *Cl,
-             int64_t ncol, cudaStream_t s) {
+wpcd_status gemm_df_simt(const wpcd_problem *pr, bool use_O, const float *Bh, const float *Bl, double *C, float *Ch,
+                         float *Cl, int64_t ncol, cudaStream_t s) {
   const int N = pr->N;
   dim3 grid((unsigned)((ncol + DF_N - 1) / DF_N), (N + GB_M - 1) / GB_M, pr->n_ch);
   gemm_df_kernel<OUT_DF><<<grid, G_THREADS, 0, s>>>(N, ncol, use_O ? pr->d.O_h : pr->d.Vt_h,
                                                     use_O ? pr->d.O_l : pr->d.Vt_l, Bh, Bl, C, Ch, Cl);
   count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? WPCD_OK : cuda_error(e, "float-float gemm launch");
+}
+
+// the channel-block products of the float-float K application: from bf16
+// digit planes on the tensor cores where prepared (oz_gemm.cu, N <= 256),
+// else float-float on the FP32 pipe
+template <bool OUT_DF>
+wpcd_status gemm_df(const wpcd_problem *pr, bool use_O, const float *Bh, const float *Bl, double *C, float *Ch,
+                    float *Cl, int64_t ncol, cudaStream_t s) {
+  if (pr->d.O_oz && oz_enabled()) return oz_gemm(pr, use_O, Bh, Bl, C, Ch, Cl, ncol, s);
+  return gemm_df_simt<OUT_DF>(pr, use_O, Bh, Bl, C, Ch, Cl, ncol, s);
 }
 
 }  // namespace
@@ -188,6 +200,11 @@ wpcd_status df_prepare(wpcd_problem *pr, wpcd_P *P, cudaStream_t s) {
     df_split_kernel<<<grid_for(nmat, 256), 256, 0, s>>>(nmat, pr->d.Vt, pr->d.Vt_h, pr->d.Vt_l);
     count_launches(2);
   }
+  // digit planes of O and Vt for the tensor-core products
+  if (oz_supported(pr) && oz_enabled()) {
+    wpcd_status st = oz_prepare(pr, s);
+    if (st != WPCD_OK) return st;
+  }
   if (P && P->prec == WPCD_FP64 && !P->val_h) {
     const int64_t nv = (int64_t)P->nnz * P->n_pairs;
     WPCD_CUDA_TRY(dev_malloc(&P->val_h, sizeof(float) * nv + 4));
@@ -208,19 +225,26 @@ wpcd_status df_kapply(const wpcd_problem *pr, const wpcd_P *P, const double *g, 
   df_split_scaled_kernel<<<grid_for(nc, 256), 256, 0, s>>>(nc, reinterpret_cast<const double2 *>(x),
                                                           reinterpret_cast<const double2 *>(g), w.xh, w.xl);
   count_launches(1);
-  gemm_df<true>(pr, false, w.xh, w.xl, nullptr, w.yh, w.yl, ncol, s);
-  wpcd_status st = spmm_df(pr, P, w.yh, w.yl, w.xh, w.xl, B, s);
+  wpcd_status st = gemm_df<true>(pr, false, w.xh, w.xl, nullptr, w.yh, w.yl, ncol, s);
   if (st != WPCD_OK) return st;
-  gemm_df<false>(pr, true, w.xh, w.xl, out, nullptr, nullptr, ncol, s);
+  st = spmm_df(pr, P, w.yh, w.yl, w.xh, w.xl, B, s);
+  if (st != WPCD_OK) return st;
+  st = gemm_df<false>(pr, true, w.xh, w.xl, out, nullptr, nullptr, ncol, s);
+  if (st != WPCD_OK) return st;
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? WPCD_OK : cuda_error(e, "float-float kapply launch");
 }
 
 // y = A (g o x) per channel block in float-float, FP64 in and out
-wpcd_status df_gemm_op(wpcd_problem *pr, bool use_O, const double *g, const double *x, double *y, int B, float *ms,
-                       cudaStream_t s) {
+wpcd_status df_gemm_op(wpcd_problem *pr, bool use_O, bool digits, const double *g, const double *x, double *y, int B,
+                       float *ms, cudaStream_t s) {
   wpcd_status st = df_prepare(pr, nullptr, s);
   if (st != WPCD_OK) return st;
+  if (digits) {
+    if (!oz_supported(pr)) return set_error(WPCD_EINVAL, "the digit-plane tensor-core GEMM needs N <= 256");
+    st = oz_prepare(pr, s);
+    if (st != WPCD_OK) return st;
+  }
   const size_t dim = (size_t)pr->n_ch * pr->N * pr->M;
   DfWork w;
   WPCD_CUDA_TRY(w.alloc(dim, B, s));
@@ -231,11 +255,15 @@ wpcd_status df_gemm_op(wpcd_problem *pr, bool use_O, const double *g, const doub
   {
     LaunchTimer t(ms, s);
     t.start();
-    gemm_df<false>(pr, use_O, w.xh, w.xl, y, nullptr, nullptr, 2LL * pr->M * B, s);
+    st = digits ? oz_gemm(pr, use_O, w.xh, w.xl, y, nullptr, nullptr, 2LL * pr->M * B, s)
+                : gemm_df_simt<false>(pr, use_O, w.xh, w.xl, y, nullptr, nullptr, 2LL * pr->M * B, s);
     t.stop();
   }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_error(e, "float-float gemm launch");
+  if (st != WPCD_OK) return st;
+  if (digits) {
+    st = tc_check(pr, s);
+    if (st != WPCD_OK) return st;
+  }
   WPCD_CUDA_TRY(cudaStreamSynchronize(s));  // the work space is freed on return
   return WPCD_OK;
 }
@@ -278,7 +306,8 @@ wpcd_status df_born(const wpcd_problem *pr, const wpcd_P *P, const int *r0, int 
   count_launches(1);
   wpcd_status st = spmm_df(pr, P, w.yh, w.yl, w.xh, w.xl, B, s);
   if (st != WPCD_OK) return st;
-  gemm_df<false>(pr, true, w.xh, w.xl, b, nullptr, nullptr, 2LL * pr->M * B, s);
+  st = gemm_df<false>(pr, true, w.xh, w.xl, b, nullptr, nullptr, 2LL * pr->M * B, s);
+  if (st != WPCD_OK) return st;
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? WPCD_OK : cuda_error(e, "float-float born launch");
 }

@@ -2034,8 +2034,9 @@ wpcd_status channel_gemm(wpcd_problem *pr, int which, int mode, const void *g, c
   const int N = pr->N;
   const int64_t ncol = 2LL * pr->M * n_rhs;
   dim3 grid((unsigned)((ncol + GB_N - 1) / GB_N), (N + GB_M - 1) / GB_M, pr->n_ch);
-  if (mode == WPCD_GEMM_FF)
-    return df_gemm_op(pr, which == 1, (const double *)g, (const double *)x, (double *)y, n_rhs, ms, s);
+  if (mode == WPCD_GEMM_FF || mode == WPCD_GEMM_DIGITS)
+    return df_gemm_op(pr, which == 1, mode == WPCD_GEMM_DIGITS, (const double *)g, (const double *)x, (double *)y,
+                      n_rhs, ms, s);
   if (mode == WPCD_GEMM_TF32X3) {
     if (!tc_supported(pr)) return set_error(WPCD_EINVAL, "the tensor-core GEMM needs N <= 512");
     wpcd_status st = tc_prepare(pr, s);

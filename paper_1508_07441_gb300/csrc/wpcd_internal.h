@@ -95,6 +95,8 @@ struct DeviceTables {
   float *O_tc = nullptr, *Vt_tc = nullptr;      // TF32 hi/lo operand blocks (tc_gemm.cu)
   float *O_h = nullptr, *O_l = nullptr;         // float-float split of O (df.cu)
   float *Vt_h = nullptr, *Vt_l = nullptr;       // float-float split of Vt
+  uint16_t *O_oz = nullptr, *Vt_oz = nullptr;   // bf16 digit planes (oz_gemm.cu)
+  int *O_ozE = nullptr, *Vt_ozE = nullptr;      // their row exponents
   int *tc_err = nullptr;                        // tensor-core wait-limit flag
 };
 
@@ -177,6 +179,13 @@ wpcd_status tc_gemm_group(const TcGroupProb *gp, int n_prob, bool use_O, const f
 wpcd_status tc_gemm(const wpcd_problem *pr, bool use_O, const float *G, const float *X, const float *S, float *C,
                     int64_t ncol, cudaStream_t s);
 wpcd_status tc_check(const wpcd_problem *pr, cudaStream_t s);
+// oz_gemm.cu: FP64-class channel-block products from bf16 digit planes on
+// the tensor cores (float-float panel in, FP64 or float-float out), N <= 256
+bool oz_supported(const wpcd_problem *pr);
+bool oz_enabled();
+wpcd_status oz_prepare(wpcd_problem *pr, cudaStream_t s);
+wpcd_status oz_gemm(const wpcd_problem *pr, bool use_O, const float *Bh, const float *Bl, double *C, float *Ch,
+                    float *Cl, int64_t ncol, cudaStream_t s);
 // df.cu: float-float ("FP64-class", about 48 significant bits) K application
 // on the FP32 pipe, for the refinement residual of the mixed solve
 // Work space of the solves: a stream-ordered pool per device that keeps
@@ -209,8 +218,10 @@ wpcd_status df_kapply(const wpcd_problem *pr, const wpcd_P *P, const double *g, 
                       DfWork &w, cudaStream_t s);
 wpcd_status launch_spmm_df_cfg(const wpcd_problem *pr, const wpcd_P *P, const float *yh, const float *yl,
                                float *zh, float *zl, int B, const SpmmConfig &cfg, cudaStream_t s);
-wpcd_status df_gemm_op(wpcd_problem *pr, bool use_O, const double *g, const double *x, double *y, int B, float *ms,
-                       cudaStream_t s);
+// digits: the digit-plane tensor-core product (oz_gemm.cu) instead of the
+// float-float SIMT kernel
+wpcd_status df_gemm_op(wpcd_problem *pr, bool use_O, bool digits, const double *g, const double *x, double *y, int B,
+                       float *ms, cudaStream_t s);
 wpcd_status df_spmm_op(wpcd_problem *pr, wpcd_P *P, const double *y, double *z, int B, float *ms, cudaStream_t s);
 wpcd_status df_born(const wpcd_problem *pr, const wpcd_P *P, const int *r0, int B, double *b, DfWork &w,
                     cudaStream_t s);

@@ -22,7 +22,7 @@ WPCD_ENOCONV, WPCD_EBREAKDOWN, WPCD_ETIMEOUT, WPCD_ENOBOUND = -4, -5, -6, -7
 WPCD_FP64, WPCD_FP32C = 0, 1
 WPCD_SUM_KRYLOV, WPCD_SUM_WYNN = 0, 1
 WPCD_SOLVE_FP64, WPCD_SOLVE_MIXED, WPCD_SOLVE_MIXED_FP64 = 0, 1, 2
-WPCD_GEMM_FP64, WPCD_GEMM_FP32, WPCD_GEMM_TF32X3, WPCD_GEMM_FF = 0, 1, 2, 3
+WPCD_GEMM_FP64, WPCD_GEMM_FP32, WPCD_GEMM_TF32X3, WPCD_GEMM_FF, WPCD_GEMM_DIGITS = 0, 1, 2, 3, 4
 WPCD_SPMM_FP64, WPCD_SPMM_FP32, WPCD_SPMM_FF, WPCD_SPMM_FP32_BLOCKED = 0, 1, 2, 3
 
 _P = ctypes.c_void_p

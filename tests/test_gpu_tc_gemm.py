@@ -76,7 +76,7 @@ def test_tensor_core_gemm_matches_fp64(W, N, M, B, which):
         assert err.max() < tol, (mode, err.max())
 
 
-@pytest.mark.parametrize("mode,tol", [("FP64", 1e-14), ("FF", 1e-12)])
+@pytest.mark.parametrize("mode,tol", [("FP64", 1e-14), ("FF", 1e-12), ("DIGITS", 1e-13)])
 @pytest.mark.parametrize("which", [0, 1])
 def test_fp64_class_channel_gemm_matches_numpy(W, mode, tol, which):
     """FP64 SIMT and float-float (FP32 pipe) products against FP64 numpy on
@@ -93,7 +93,7 @@ def test_fp64_class_channel_gemm_matches_numpy(W, mode, tol, which):
     g = inputs.random_complex(n, 6) if which == 0 else None
     ref, scale = _reference(_blocks(pr, which), x, g, N, M, B)
     yd = torch.full((2 * n,), float("nan"), dtype=torch.float64, device="cuda")
-    m = W.WPCD_GEMM_FP64 if mode == "FP64" else W.WPCD_GEMM_FF
+    m = {"FP64": W.WPCD_GEMM_FP64, "FF": W.WPCD_GEMM_FF, "DIGITS": W.WPCD_GEMM_DIGITS}[mode]
     ms = pr.wpcd_channel_gemm(which, m, None if g is None else torch.from_numpy(g.view(np.float64)).cuda(),
                               torch.from_numpy(x.view(np.float64)).cuda(), yd, B, timed=True)
     assert ms > 0.0
