@@ -16,8 +16,10 @@
 // over K stay integers below 2^24 for K <= 409 (diagonal d holds at most
 // two products of bound 2^13 and d - 1 of bound 2^12), so the FP32 tensor
 // accumulation of a diagonal is exact.  The 36 pairs with s + t < OZ_L run
-// as kind::f16 (bf16) MMAs into OZ_L diagonal accumulators in TMEM; the
-// epilogue forms C = 2^(E_i + F_j - 14) sum_d 2^(-7 d) acc_d in FP64.  The
+// as kind::f16 (bf16) MMAs into OZ_L diagonal accumulators in TMEM (one
+// MMA per A plane s, its N spanning the B planes 0 .. OZ_L - 1 - s); the
+// epilogue forms C = 2^(E_i + F_j - 14) sum_d 2^(-7 d) acc_d in float-float
+// on the FP32 pipe (GB300 runs FP64 at 1/64 of that rate).  The
 // pairs left out (s + t >= OZ_L) and the digits beyond plane 7 weigh below
 // 2^-56 of 2^(E_i + F_j) per term.
 //
@@ -25,7 +27,7 @@
 // of 16: the packed A digits of all row tiles (RT x OZ_L blocks of 128 x 16
 // bf16, packed once per problem) arrive by a bulk async copy; the threads
 // turn the chunk's B values into OZ_L digit blocks of 32 x 16 bf16; one
-// thread issues the 36 RT MMAs and commits them to the stage's mbarrier.
+// thread issues the 8 RT MMAs and commits them to the stage's mbarrier.
 // Shared-memory operands use the no-swizzle K-major layout: 8-row groups of
 // 256 B, each two 8 x 16 B core matrices along K (K-core stride 128 B,
 // row-group stride 256 B).  Every wait is bounded; a wait that runs out sets
@@ -86,9 +88,9 @@ __device__ __forceinline__ uint64_t oz_desc(uint32_t addr) {
 }
 
 // instruction descriptor of kind::f16: D F32, A and B bf16, both K-major,
-// N = OZ_BN, M = 128
-__host__ __device__ constexpr uint32_t oz_idesc() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) | ((uint32_t)(OZ_M >> 4) << 24);
+// N columns (a multiple of 16, at most 256), M = 128
+__host__ __device__ constexpr uint32_t oz_idesc(int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(OZ_M >> 4) << 24);
 }
 
 __device__ __forceinline__ void oz_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -178,7 +180,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzParams p) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_holder;
-  constexpr uint32_t idesc = oz_idesc();
   const uint32_t a_bytes = (uint32_t)RT * OZ_L * OZ_A_PLANE;
   bool ok = true, bail = false;
   uint32_t g = 0;                      // chunks begun by this CTA (stage ring position)
@@ -186,6 +187,24 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzParams p) {
   uint32_t tl = 0;                     // tiles finished (bar_done phase)
   // chunk c of a tile: thread (j, kp) converts rows 2 kp, 2 kp + 1 of column j
   const int j = tid & 31, kp = tid >> 5;
+  // the CTA's chunks in order: chunk q is K chunk q % nK of its tile q / nK;
+  // thread 0 copies the A digits two chunks ahead of the MMAs
+  const int my_tiles = blockIdx.x < p.n_tiles ? (p.n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const uint32_t G = (uint32_t)my_tiles * nK;
+  auto issue_a = [&](uint32_t q) {
+    const int tq = blockIdx.x + (int)(q / nK) * gridDim.x;
+    const int sq = (int)(q % OZ_STAGES);
+    const uint16_t *src = p.A + ((size_t)(tq / p.n_cb) * nK + q % nK) * (a_bytes / 2);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar_a[sq])), "r"(a_bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(smem + (size_t)sq * p.stage_bytes)),
+                 "l"(src), "r"(a_bytes), "r"(smem_u32(&bar_a[sq]))
+                 : "memory");
+    ++g_issued;
+  };
+  if (tid == 0)
+    for (uint32_t q = 0; q < 2 && q < G; ++q) issue_a(q);
   for (int t = blockIdx.x; t < p.n_tiles; t += gridDim.x, ++tl) {
     const int ch = t / p.n_cb;
     const int64_t col0 = (int64_t)(t % p.n_cb) * OZ_BN;
@@ -214,18 +233,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzParams p) {
       unsigned char *st = smem + (size_t)s * p.stage_bytes;
       // the MMAs of chunk g - OZ_STAGES read this stage
       if (g >= OZ_STAGES && ok) ok = mbar_wait(&bar_mma[s], (use - 1) & 1);
-      if (tid == 0 && ok) {
-        const uint16_t *src = p.A + ((size_t)ch * nK + c) * (a_bytes / 2);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar_a[s])),
-                     "r"(a_bytes)
-                     : "memory");
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                smem_u32(st)),
-            "l"(src), "r"(a_bytes), "r"(smem_u32(&bar_a[s]))
-            : "memory");
-        ++g_issued;
-      }
       float hn[2], ln[2];
       if (c + 1 < nK) load(c + 1, hn, ln);
       // B digits: plane t of (j, 2 kp .. 2 kp + 1) as one 32-bit store
@@ -243,6 +250,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzParams p) {
           hv[q] = hn[q];
           lv[q] = ln[q];
         }
+      // the A copy of chunk g + 2 into the stage that chunk g - 1 frees
+      if (tid == 0 && ok && g + 2 < G) {
+        if (g >= 1) ok = mbar_wait(&bar_mma[(g - 1) % OZ_STAGES], ((g - 1) / OZ_STAGES) & 1);
+        if (ok) issue_a(g + 2);
+      }
       // generic-proxy stores -> visible to the tensor core (async proxy)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tc_fence_before();
@@ -253,16 +265,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzParams p) {
         ok = mbar_wait(&bar_a[s], use & 1);
         if (ok) {
           g_seen = g + 1;
-          const uint32_t a0 = smem_u32(st), b0 = smem_u32(bst);
+          // descriptors of the plane blocks: the start address field is
+          // addr / 16, so a block offset adds offset / 16 (smem < 256 KB)
+          const uint64_t da = oz_desc(smem_u32(st)), db = oz_desc(smem_u32(bst));
+          // A plane sa against B planes 0 .. OZ_L - 1 - sa in one MMA: the B
+          // planes are consecutive 32-row groups of one K-major operand and
+          // the diagonal accumulators sa .. OZ_L - 1 consecutive 32-column
+          // groups of TMEM, so N = 32 (OZ_L - sa) and the A block is read
+          // once per plane
 #pragma unroll 1
           for (int rt = 0; rt < RT; ++rt)
 #pragma unroll
             for (int sa = 0; sa < OZ_L; ++sa)
-#pragma unroll
-              for (int tb = 0; tb < OZ_L - sa; ++tb)
-                oz_mma(tmem + (uint32_t)((rt * OZ_L + sa + tb) * OZ_BN),
-                       oz_desc(a0 + (uint32_t)(rt * OZ_L + sa) * OZ_A_PLANE), oz_desc(b0 + (uint32_t)tb * OZ_B_PLANE),
-                       idesc, (c > 0 || sa > 0) ? 1u : 0u);
+              oz_mma(tmem + (uint32_t)((rt * OZ_L + sa) * OZ_BN), da + (uint64_t)((rt * OZ_L + sa) * (OZ_A_PLANE >> 4)),
+                     db, oz_idesc(OZ_BN * (OZ_L - sa)), (c > 0 || sa > 0) ? 1u : 0u);
         }
         tc_commit(&bar_mma[s]);
       }
@@ -278,16 +294,29 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzParams p) {
     const int lg = warp & 3, half = warp >> 2;
     for (int rt = 0; rt < RT; ++rt) {
       const int row = rt * OZ_M + lg * 32 + lane;
-      double acc[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) acc[i] = 0.0;
+      // sum_d 2^(-7 d) acc_d in float-float (TwoSum; the acc_d are exact
+      // integers below 2^24 and their power-of-two scaling is exact), on the
+      // FP32 pipe: GB300's FP64 rate is 1/64 of it
+      float xh[16], xl[16];
 #pragma unroll
       for (int d = 0; d < OZ_L; ++d) {
         float v[16];
         tc_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)((rt * OZ_L + d) * OZ_BN + half * 16), v);
-        const double w = ldexp(1.0, -7 * d);
+        const float w = __int_as_float((127 - 7 * d) << 23);  // 2^(-7 d)
 #pragma unroll
-        for (int i = 0; i < 16; ++i) acc[i] += (double)v[i] * w;
+        for (int i = 0; i < 16; ++i) {
+          if (d == 0) {
+            xh[i] = v[i];
+            xl[i] = 0.f;
+          } else {
+            const float x = v[i] * w;
+            const float sum = __fadd_rn(xh[i], x);
+            const float bb = __fsub_rn(sum, xh[i]);
+            const float e = __fadd_rn(__fsub_rn(xh[i], __fsub_rn(sum, bb)), __fsub_rn(x, bb));
+            xh[i] = sum;
+            xl[i] = __fadd_rn(xl[i], e);
+          }
+        }
       }
       if (row < n) {
         const int E = p.EA[((size_t)ch * RT) * OZ_M + row];
@@ -295,13 +324,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzParams p) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           if (col0 + half * 16 + i >= ncol) break;
-          const double c = ldexp(acc[i], E + s_F[half * 16 + i] - 14);
+          const int k = E + s_F[half * 16 + i] - 14;  // scale 2^k
+          const float h = xh[i] + xl[i], l = xl[i] - (h - xh[i]);  // renormalised (Fast2Sum)
           if (OUT_DF) {
-            const float h = (float)c;
-            p.Ch[o + i] = h;
-            p.Cl[o + i] = (float)(c - (double)h);
+            // two float powers of two (a float-float result lies in the
+            // float range, so each half exponent stays within it)
+            const int k1 = min(max(k / 2, -126), 127), k2 = min(max(k - k / 2, -126), 127);
+            const float s1 = __int_as_float((127 + k1) << 23), s2 = __int_as_float((127 + k2) << 23);
+            p.Ch[o + i] = h * s1 * s2;
+            p.Cl[o + i] = l * s1 * s2;
           } else {
-            p.C[o + i] = c;
+            p.C[o + i] = ((double)h + (double)l) * __longlong_as_double((long long)(1023 + k) << 52);
           }
         }
       }
