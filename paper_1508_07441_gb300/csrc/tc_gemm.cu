@@ -867,8 +867,10 @@ wpcd_status tc_prepare(wpcd_problem *pr, cudaStream_t s) {
   const size_t bytes = (size_t)pr->n_ch * sh.nK * sh.RT * TC_A_BLOCK;
   WPCD_CUDA_TRY(dev_malloc(&pr->d.O_tc, bytes));
   WPCD_CUDA_TRY(dev_malloc(&pr->d.Vt_tc, bytes));
-  WPCD_CUDA_TRY(dev_malloc(&pr->d.tc_err, sizeof(int)));
-  WPCD_CUDA_TRY(cudaMemsetAsync(pr->d.tc_err, 0, sizeof(int), s));
+  if (!pr->d.tc_err) {  // shared with the digit-plane products (oz_gemm.cu)
+    WPCD_CUDA_TRY(dev_malloc(&pr->d.tc_err, sizeof(int)));
+    WPCD_CUDA_TRY(cudaMemsetAsync(pr->d.tc_err, 0, sizeof(int), s));
+  }
   const int64_t total = (int64_t)pr->n_ch * sh.nK * sh.RT * TC_M * TC_KC;
   tc_pack_kernel<<<grid_for(total, 256), 256, 0, s>>>(pr->n_ch, pr->N, sh.RT, sh.nK, pr->d.O, pr->d.O_tc);
   tc_pack_kernel<<<grid_for(total, 256), 256, 0, s>>>(pr->n_ch, pr->N, sh.RT, sh.nK, pr->d.Vt, pr->d.Vt_tc);
