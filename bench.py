@@ -304,9 +304,22 @@ def kernel_rooflines(W, pr, w, phases, n_nodes, n_e, stream, flush, peaks, f_sm,
     # the Born term runs once per distinct on-shell bin, in smaller launches
     entry("spmm_df_kernel", "alu", spmm_flops / (ms * 1e-3) / 1e12, ff, "TFLOP/s", ms, n64 - 1,
           f"4 n_pairs nnz B = {spmm_flops:.3e} FP64-equivalent flops in float-float", srcff)
+    # channel products of the residual: bf16 digit planes on the tensor cores
+    # when N <= 256 (the solve's path), else float-float SIMT
+    digits = N <= 256
+    if digits:
+        ms = _time_kernel(stream, flush, lambda: pr.wpcd_channel_gemm(1, W.WPCD_GEMM_DIGITS, None, x64, y64, n_e,
+                                                                       stream=stream, timed=True))
+        dflops = 36 * gemm_flops
+        entry("oz_gemm_kernel (digit planes)", "tensor", dflops / (ms * 1e-3) / 1e12, peaks.get("bf16_tflops", 1900.0),
+              "TFLOP/s", ms, 2 * (n64 - 1),
+              f"36 bf16 digit-plane products x 2 N^2 (2 M B) n_ch = {dflops:.3e} bf16 MMA flops "
+              f"(FP64-class result: {gemm_flops / (ms * 1e-3) / 1e12:.2f} FP64-equivalent TFLOP/s)",
+              "measured cuBLAS bf16 burst (bf16_tflops)")
     ms = _time_kernel(stream, flush, lambda: pr.wpcd_channel_gemm(1, W.WPCD_GEMM_FF, None, x64, y64, n_e,
                                                                    stream=stream, timed=True))
-    entry("gemm_df_kernel", "alu", gemm_flops / (ms * 1e-3) / 1e12, ff, "TFLOP/s", ms, 2 * (n64 - 1),
+    entry("gemm_df_kernel", "alu", gemm_flops / (ms * 1e-3) / 1e12, ff, "TFLOP/s", ms,
+          0 if digits else 2 * (n64 - 1),
           f"2 N^2 (2 M B) n_ch = {gemm_flops:.3e} FP64-equivalent flops in float-float", srcff)
     # the plain FP64 iteration's kernels (the comparison baseline), one energy
     x1 = torch.randn(2 * dim, dtype=torch.float64, device="cuda")
