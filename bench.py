@@ -139,11 +139,12 @@ def fill_flops_per_node(n_ch: int, n_pairs: int) -> int:
 # of the kernel as it stands (profiles/ names the capture); None where no
 # capture of the current kernel exists
 NCU_TRAFFIC = {
-    "fill_kernel<FP64,3>": 436.8e6,
-    "spmm_sacc_kernel<FP32>": 375.9e6,
-    "tc_gemm_kernel<TF32x3> (Vt, G1)": 329.1e6,
+    "fill_kernel<FP64,3>": 435.6e6,
+    "spmm_sacc_kernel<FP32>": 377.8e6,
+    "tc_gemm_kernel<TF32x3> (Vt, G1)": 329.2e6,
     "tc_gemm_kernel<TF32x3> (O)": 331.5e6,
-    "spmm_df_kernel": 956.8e6,
+    "spmm_df_kernel": 961.9e6,
+    "oz_gemm_kernel (digit planes)": 450.4e6,
     "gemm_df_kernel": 903.6e6,
 }
 
