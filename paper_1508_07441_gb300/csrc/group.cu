@@ -1083,19 +1083,20 @@ wpcd_status gsolve_mixed(const Group &gr, const wpcd_solve_opts &o, GCtx &cx, GK
   WPCD_CUDA_TRY(cudaMemcpyAsync(kr.bnorm, ones.data(), sizeof(double) * S, cudaMemcpyHostToDevice, s));
   WPCD_CUDA_TRY(cudaMemcpyAsync(d_bet0, bet0.data(), sizeof(double2) * bet0.size(), cudaMemcpyHostToDevice, s));
   WPCD_CUDA_TRY(cudaStreamSynchronize(s));
-  auto inner_cycle = [&]() -> wpcd_status {
+  // the inner cycle of mm <= m steps (the full one captured as a graph)
+  auto inner_cycle = [&](int mm) -> wpcd_status {
     cudaMemsetAsync(kr.H, 0, sizeof(double2) * (size_t)S * (m + 1) * m, s);
     cudaMemcpyAsync(kr.bet, d_bet0, sizeof(double2) * bet0.size(), cudaMemcpyDeviceToDevice, s);
-    for (int k = 0; k < m; ++k) {
+    for (int k = 0; k < mm; ++k) {
       wpcd_status st =
           gkapply<float>(gr, cx.g32, (float *)kr.vec(k), kr.w, (float *)kr.vec(k), cx.wy32, cx.wz32, s);
       if (st != WPCD_OK) return st;
       // single-pass Gram-Schmidt: the FP64 refinement residual judges the cycle
       kr.step(k, s, false);
     }
-    bbacksub_kernel<<<(S + 127) / 128, 128, 0, s>>>(S, m, m, kr.H, kr.bet, kr.y);
-    bupdate_coef_kernel<float><<<(m * S + 255) / 256, 256, 0, s>>>(m, S, kr.y, k64.nrm, kr.hc);
-    gupdate_kernel<float><<<vg, 256, 0, s>>>(gr.d_meta, L, m, kr.vec(0), (size_t)L, kr.hc, (double2 *)cx.u);
+    bbacksub_kernel<<<(S + 127) / 128, 128, 0, s>>>(S, m, mm, kr.H, kr.bet, kr.y);
+    bupdate_coef_kernel<float><<<(mm * S + 255) / 256, 256, 0, s>>>(mm, S, kr.y, k64.nrm, kr.hc);
+    gupdate_kernel<float><<<vg, 256, 0, s>>>(gr.d_meta, L, mm, kr.vec(0), (size_t)L, kr.hc, (double2 *)cx.u);
     count_launches(3);
     return WPCD_OK;
   };
@@ -1106,6 +1107,10 @@ wpcd_status gsolve_mixed(const Group &gr, const wpcd_solve_opts &o, GCtx &cx, GK
   std::vector<double2> nr(S);
   const int max_outer = o.max_outer > 0 ? o.max_outer : 12;
   wpcd_status result = WPCD_OK;
+  // cycle lengths after the first from the previous cycle's per-step
+  // reduction of the worst residual, as in the single-problem solve
+  double worst_prev = 0.0;
+  int mm_prev = 0;
   for (int outer = 0; outer <= max_outer; ++outer) {
     if (outer > 0) {  // r = b - (I - K) u in FP64
       wpcd_status st = cx.df.xh ? gkapply_df(gr, cx.g, cx.u, cx.t, cx.df, s)
@@ -1128,6 +1133,7 @@ wpcd_status gsolve_mixed(const Group &gr, const wpcd_solve_opts &o, GCtx &cx, GK
       break;
     }
     bool done = true;
+    double worst = 0.0;
     for (int e = 0; e < S; ++e) {
       relres[e] = std::sqrt(nr[e].x) / bn[e];
       if (!std::isfinite(relres[e])) {
@@ -1137,13 +1143,22 @@ wpcd_status gsolve_mixed(const Group &gr, const wpcd_solve_opts &o, GCtx &cx, GK
       } else {
         status[e] = WPCD_ENOCONV;
         done = false;
+        worst = std::max(worst, relres[e]);
       }
     }
     if (done || outer == max_outer) break;
     ++n_outer;
+    int mm = m;
+    if (mm_prev > 0 && worst_prev > 0.0 && worst > 0.0 && worst < worst_prev) {
+      const double rate = std::pow(worst / worst_prev, 1.0 / mm_prev);
+      const double need = std::log(0.1 * o.tol / worst) / std::log(rate);
+      if (need < m) mm = std::max(2, (int)std::ceil(need));
+    }
+    worst_prev = worst;
+    mm_prev = mm;
     gnormalize_f32_kernel<<<vg, 256, 0, s>>>(gr.d_meta, L, (const double2 *)cx.r, k64.inv, kr.vec(0));
     count_launches(1);
-    if (o.use_graph && s != nullptr) {  // the legacy default stream cannot be captured
+    if (o.use_graph && s != nullptr && mm == m) {  // the legacy default stream cannot be captured
       if (!exec) {
         cudaGraph_t graph;
         const int64_t launches0 = wpcd_launch_count();
@@ -1152,7 +1167,7 @@ wpcd_status gsolve_mixed(const Group &gr, const wpcd_solve_opts &o, GCtx &cx, GK
           result = cuda_error(ce, "begin capture");
           break;
         }
-        wpcd_status st = inner_cycle();
+        wpcd_status st = inner_cycle(m);
         ce = cudaStreamEndCapture(s, &graph);
         if (st != WPCD_OK) {
           result = st;
@@ -1179,13 +1194,13 @@ wpcd_status gsolve_mixed(const Group &gr, const wpcd_solve_opts &o, GCtx &cx, GK
       }
       count_launches(graph_kernels);
     } else {
-      wpcd_status st = inner_cycle();
+      wpcd_status st = inner_cycle(mm);
       if (st != WPCD_OK) {
         result = st;
         break;
       }
     }
-    n32 += m;
+    n32 += mm;
   }
   if (exec) cudaGraphExecDestroy(exec);
   return result;

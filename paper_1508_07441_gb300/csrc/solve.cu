@@ -1524,27 +1524,27 @@ wpcd_status solve_mixed(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solv
   WPCD_CUDA_TRY(cudaMemcpyAsync(d_bet0, bet0.data(), sizeof(double2) * bet0.size(), cudaMemcpyHostToDevice, s));
   WPCD_CUDA_TRY(cudaStreamSynchronize(s));  // host staging vectors
 
-  // the inner cycle: fixed sizes and pointers, so it can be captured once
-  // and replayed as a CUDA graph
-  auto inner_cycle = [&]() -> wpcd_status {
+  // the inner cycle of mm <= m steps: fixed sizes and pointers, so the full
+  // m-step cycle can be captured once and replayed as a CUDA graph
+  auto inner_cycle = [&](int mm) -> wpcd_status {
     cudaMemsetAsync(kr.H, 0, sizeof(double2) * (size_t)B * (m + 1) * m, s);
     cudaMemcpyAsync(kr.bet, d_bet0, sizeof(double2) * bet0.size(), cudaMemcpyDeviceToDevice, s);
-    for (int k = 0; k < m; ++k) {
+    for (int k = 0; k < mm; ++k) {
       wpcd_status st = kapply_ws<float>(pr, P, cx.g32, (float *)kr.vec(k), kr.w, (float *)kr.vec(k), B, ws32, s);
       if (st != WPCD_OK) return st;
       // single-pass Gram-Schmidt: the short FP32 cycle only has to cut the
       // residual, whose FP64 value the refinement loop recomputes and judges
       kr.step(k, s, false);
     }
-    bbacksub_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, m, m, kr.H, kr.bet, kr.y);
+    bbacksub_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, m, mm, kr.H, kr.bet, kr.y);
     // u += |r| (V y)   (FP64 accumulation of the FP32 correction)
-    bupdate_coef_kernel<float><<<(m * B + 255) / 256, 256, 0, s>>>(m, B, kr.y, k64.nrm, kr.hc);
+    bupdate_coef_kernel<float><<<(mm * B + 255) / 256, 256, 0, s>>>(mm, B, kr.y, k64.nrm, kr.hc);
     if (B % 2 == 0)
-      bupdate2_kernel<<<grid_for(n / 2, 256), 256, 0, s>>>(n / 2, B / 2, m, reinterpret_cast<const float4 *>(kr.vec(0)),
+      bupdate2_kernel<<<grid_for(n / 2, 256), 256, 0, s>>>(n / 2, B / 2, mm, reinterpret_cast<const float4 *>(kr.vec(0)),
                                                            cx.dim * B / 2, reinterpret_cast<const float4 *>(kr.hc),
                                                            (double2 *)cx.u);
     else
-      bupdate_kernel<float><<<vg, 256, 0, s>>>(n, B, m, kr.vec(0), cx.dim * B, kr.hc, (double2 *)cx.u);
+      bupdate_kernel<float><<<vg, 256, 0, s>>>(n, B, mm, kr.vec(0), cx.dim * B, kr.hc, (double2 *)cx.u);
     count_launches(3);
     return WPCD_OK;
   };
@@ -1566,6 +1566,12 @@ wpcd_status solve_mixed(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solv
   std::vector<double2> nr(B);
   const int max_outer = o.max_outer > 0 ? o.max_outer : 12;
   wpcd_status result = WPCD_OK;
+  // cycle lengths after the first: from the per-step reduction of the worst
+  // relative residual that the previous cycle achieved, the steps to reach a
+  // tenth of the tolerance (at least 2, at most m); a cycle that falls just
+  // short then costs a few steps, not another m
+  double worst_prev = 0.0;
+  int mm_prev = 0;
   for (int outer = 0; outer <= max_outer; ++outer) {
     // r = b - (I - K) u in FP64
     if (outer > 0 || warm) {
@@ -1589,6 +1595,7 @@ wpcd_status solve_mixed(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solv
       break;
     }
     bool done = true;
+    double worst = 0.0;
     for (int e = 0; e < B; ++e) {
       relres[e] = std::sqrt(nr[e].x) / bn[e];
       if (!std::isfinite(relres[e])) {
@@ -1598,14 +1605,23 @@ wpcd_status solve_mixed(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solv
       } else {
         status[e] = WPCD_ENOCONV;
         done = false;
+        worst = std::max(worst, relres[e]);
       }
     }
     if (done || outer == max_outer) break;
     ++n_outer;
+    int mm = m;
+    if (mm_prev > 0 && worst_prev > 0.0 && worst > 0.0 && worst < worst_prev) {
+      const double rate = std::pow(worst / worst_prev, 1.0 / mm_prev);
+      const double need = std::log(0.1 * o.tol / worst) / std::log(rate);
+      if (need < m) mm = std::max(2, (int)std::ceil(need));
+    }
+    worst_prev = worst;
+    mm_prev = mm;
     // v0 = (float)(r / |r|)
     bnormalize_f32_kernel<<<vg, 256, 0, s>>>(n, B, (const double2 *)cx.r, k64.inv, kr.vec(0));
     count_launches(1);
-    if (o.use_graph && s != nullptr) {  // the legacy default stream cannot be captured
+    if (o.use_graph && s != nullptr && mm == m) {  // the legacy default stream cannot be captured
       if (!exec) {
         cudaGraph_t graph;
         launches0 = wpcd_launch_count();
@@ -1614,7 +1630,7 @@ wpcd_status solve_mixed(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solv
           result = cuda_error(ce, "begin capture");
           break;
         }
-        wpcd_status st = inner_cycle();
+        wpcd_status st = inner_cycle(m);
         ce = cudaStreamEndCapture(s, &graph);
         if (st != WPCD_OK) {
           result = st;
@@ -1641,13 +1657,13 @@ wpcd_status solve_mixed(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solv
       }
       count_launches(graph_kernels);
     } else {
-      wpcd_status st = inner_cycle();
+      wpcd_status st = inner_cycle(mm);
       if (st != WPCD_OK) {
         result = st;
         break;
       }
     }
-    n32 += m;
+    n32 += mm;
   }
   if (exec) cudaGraphExecDestroy(exec);
   pool_free(d_bet0, s);
