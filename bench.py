@@ -312,8 +312,8 @@ def kernel_rooflines(W, pr, w, phases, n_nodes, n_e, stream, flush, peaks, f_sm,
         ms = _time_kernel(stream, flush, lambda: pr.wpcd_channel_gemm(1, W.WPCD_GEMM_DIGITS, None, x64, y64, n_e,
                                                                        stream=stream, timed=True))
         dflops = 36 * gemm_flops
-        entry("oz_gemm_kernel (digit planes)", "tensor", dflops / (ms * 1e-3) / 1e12, peaks.get("bf16_tflops", 1900.0),
-              "TFLOP/s", ms, 2 * (n64 - 1),
+        entry("oz_gemm_kernel (digit planes)", "tensor", dflops / (ms * 1e-3) / 1e12,
+              peaks.get("bf16_tflops", 1900.0), "TFLOP/s", ms, 2 * (n64 - 1),
               f"36 bf16 digit-plane products x 2 N^2 (2 M B) n_ch = {dflops:.3e} bf16 MMA flops "
               f"(FP64-class result: {gemm_flops / (ms * 1e-3) / 1e12:.2f} FP64-equivalent TFLOP/s)",
               "measured cuBLAS bf16 burst (bf16_tflops)")
