@@ -216,7 +216,10 @@ typedef struct {
                       residual), in wpcd_solve and wpcd_solve_batch alike */
   int batch;       /* energies solved together in one batched iteration
                       (block K applications, SpMM over the batch); 0: all */
-  int inner_iter;  /* mixed: Krylov steps per refinement cycle (0: 10) */
+  int inner_iter;  /* mixed: Krylov steps of the first refinement cycle and the
+                      most of any later one (0: 10); a later cycle takes the
+                      steps that the previous cycle's per-step reduction of the
+                      worst residual says reach a tenth of tol, at least 2 */
   int max_outer;   /* mixed: cap on refinement cycles (0: 12) */
   int use_graph;   /* mixed: replay each inner cycle from a CUDA graph (1) or
                       launch its kernels one by one (0) */
