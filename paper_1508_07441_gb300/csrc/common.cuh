@@ -8,6 +8,8 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <vector>
 
@@ -463,6 +465,17 @@ __global__ void bfallback_kernel(int64_t n, int B, const int *flag, const double
 }
 
 // launch shapes tried by the autotuner for a batch of B energies
+// Steps of a mixed-solve refinement cycle after the first: the previous
+// cycle (mm_prev steps) took the worst relative residual from worst_prev to
+// worst; at that per-step reduction, the steps to a tenth of tol, at least 2
+// and at most m (m when there is no reduction to go by)
+inline int next_cycle_steps(double worst, double worst_prev, int mm_prev, int m, double tol) {
+  if (mm_prev <= 0 || !(worst_prev > 0.0) || !(worst > 0.0) || !(worst < worst_prev)) return m;
+  const double rate = std::pow(worst / worst_prev, 1.0 / mm_prev);
+  const double need = std::log(0.1 * tol / worst) / std::log(rate);
+  return need < m ? std::max(2, (int)std::ceil(need)) : m;
+}
+
 std::vector<SpmmConfig> candidates(int B) {
   std::vector<SpmmConfig> c;
   if (B == 1) {

@@ -1148,12 +1148,7 @@ wpcd_status gsolve_mixed(const Group &gr, const wpcd_solve_opts &o, GCtx &cx, GK
     }
     if (done || outer == max_outer) break;
     ++n_outer;
-    int mm = m;
-    if (mm_prev > 0 && worst_prev > 0.0 && worst > 0.0 && worst < worst_prev) {
-      const double rate = std::pow(worst / worst_prev, 1.0 / mm_prev);
-      const double need = std::log(0.1 * o.tol / worst) / std::log(rate);
-      if (need < m) mm = std::max(2, (int)std::ceil(need));
-    }
+    const int mm = next_cycle_steps(worst, worst_prev, mm_prev, m, o.tol);
     worst_prev = worst;
     mm_prev = mm;
     gnormalize_f32_kernel<<<vg, 256, 0, s>>>(gr.d_meta, L, (const double2 *)cx.r, k64.inv, kr.vec(0));

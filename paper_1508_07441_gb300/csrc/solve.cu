@@ -1566,10 +1566,9 @@ wpcd_status solve_mixed(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solv
   std::vector<double2> nr(B);
   const int max_outer = o.max_outer > 0 ? o.max_outer : 12;
   wpcd_status result = WPCD_OK;
-  // cycle lengths after the first: from the per-step reduction of the worst
-  // relative residual that the previous cycle achieved, the steps to reach a
-  // tenth of the tolerance (at least 2, at most m); a cycle that falls just
-  // short then costs a few steps, not another m
+  // cycle lengths after the first from the previous cycle's reduction of the
+  // worst residual (next_cycle_steps): a cycle that falls just short then
+  // costs a few steps, not another m
   double worst_prev = 0.0;
   int mm_prev = 0;
   for (int outer = 0; outer <= max_outer; ++outer) {
@@ -1610,12 +1609,7 @@ wpcd_status solve_mixed(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solv
     }
     if (done || outer == max_outer) break;
     ++n_outer;
-    int mm = m;
-    if (mm_prev > 0 && worst_prev > 0.0 && worst > 0.0 && worst < worst_prev) {
-      const double rate = std::pow(worst / worst_prev, 1.0 / mm_prev);
-      const double need = std::log(0.1 * o.tol / worst) / std::log(rate);
-      if (need < m) mm = std::max(2, (int)std::ceil(need));
-    }
+    const int mm = next_cycle_steps(worst, worst_prev, mm_prev, m, o.tol);
     worst_prev = worst;
     mm_prev = mm;
     // v0 = (float)(r / |r|)
