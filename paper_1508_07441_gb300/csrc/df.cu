@@ -189,7 +189,7 @@ cudaError_t DfWork::alloc(size_t dim, int B, cudaStream_t s) {
 }
 
 // split O, Vt (once per problem) and FP64 P0 values (once per matrix)
-wpcd_status df_prepare(wpcd_problem *pr, wpcd_P *P, cudaStream_t s) {
+wpcd_status df_prepare(wpcd_problem *pr, wpcd_P *P, cudaStream_t s, bool digits) {
   const int64_t nmat = (int64_t)pr->n_ch * pr->N * pr->N;
   if (!pr->d.O_h) {
     WPCD_CUDA_TRY(dev_malloc(&pr->d.O_h, sizeof(float) * nmat));
@@ -201,7 +201,7 @@ wpcd_status df_prepare(wpcd_problem *pr, wpcd_P *P, cudaStream_t s) {
     count_launches(2);
   }
   // digit planes of O and Vt for the tensor-core products
-  if (oz_supported(pr) && oz_enabled()) {
+  if (digits && oz_supported(pr) && oz_enabled()) {
     wpcd_status st = oz_prepare(pr, s);
     if (st != WPCD_OK) return st;
   }

@@ -1253,7 +1253,8 @@ wpcd_status solve_group(int n_prob, wpcd_problem *const *prs, const wpcd_P *cons
   gr.prec = Ps[0]->prec;
   if (ff)
     for (int g = 0; g < n_prob; ++g) {
-      wpcd_status st = df_prepare(const_cast<wpcd_problem *>(prs[g]), const_cast<wpcd_P *>(Ps[g]), s);
+      // the grouped residual runs its own float-float products: no digit planes
+      wpcd_status st = df_prepare(const_cast<wpcd_problem *>(prs[g]), const_cast<wpcd_P *>(Ps[g]), s, false);
       if (st != WPCD_OK) return st;
     }
   // FP32 values of FP64-assembled matrices for the inner cycles

@@ -213,7 +213,9 @@ struct DfWork {
   ~DfWork();
   cudaError_t alloc(size_t dim, int B, cudaStream_t s);
 };
-wpcd_status df_prepare(wpcd_problem *pr, wpcd_P *P, cudaStream_t s);
+// the float-float splits of O, Vt (and P's values), and with digits the bf16
+// digit planes of O and Vt for the tensor-core products (N <= 256)
+wpcd_status df_prepare(wpcd_problem *pr, wpcd_P *P, cudaStream_t s, bool digits = true);
 wpcd_status df_kapply(const wpcd_problem *pr, const wpcd_P *P, const double *g, const double *x, double *out, int B,
                       DfWork &w, cudaStream_t s);
 wpcd_status launch_spmm_df_cfg(const wpcd_problem *pr, const wpcd_P *P, const float *yh, const float *yl,
