@@ -368,19 +368,18 @@ wpcd_status wpcd_tune_spmm(wpcd_problem *pr, wpcd_P *P, int n_rhs, int mode, voi
  * device memory: code running while a stream is captured into a CUDA graph,
  * applications whose device memory belongs to a fixed pool or a foreign
  * allocator, loops that must not touch the allocator once running.  The
- * paper has no counterpart; this is a deployment variant of the Eq. kernel
- * application.  It calls no cudaMalloc or cudaFree: its two intermediate
- * vectors live in a 4 MiB array of device memory (WPCD_NOALLOC_MAX_DIM x 2
- * complex doubles) that every GPU loading the library holds until the
- * process exits.  The caller still passes g (device [dim] complex or NULL),
- * x and y (device [dim] complex, distinct), as for wpcd_kapply.  The first
- * call on a device looks up the array's device address (with that device
- * current); make it before any stream capture.  EINVAL if dim exceeds
- * WPCD_NOALLOC_MAX_DIM.  All calls share the array: calls that overlap on
- * the GPU (other streams, other host threads on the same device) race.
- * The SpMM uses the shape the autotuner chose for one right-hand side if
- * P has one, else a fixed shape.  Enqueued on `stream`; does not
- * synchronise. */
+ * paper has no counterpart.  It calls no cudaMalloc or cudaFree: its two
+ * intermediate vectors live in a 4 MiB array of device memory
+ * (WPCD_NOALLOC_MAX_DIM x 2 complex doubles) that every GPU loading the
+ * library holds until the process exits.  The caller still passes g (device
+ * [dim] complex or NULL), x and y (device [dim] complex, distinct), as for
+ * wpcd_kapply.  The first call on a device looks up the array's device
+ * address (with that device current); make it before any stream capture.
+ * EINVAL if dim exceeds WPCD_NOALLOC_MAX_DIM.  All calls share the array:
+ * calls that overlap on the GPU (other streams, other host threads on the
+ * same device) race.  The SpMM uses the shape the autotuner chose for one
+ * FP64 right-hand side (the one wpcd_kapply tunes on its first call) if P
+ * has one, else a fixed shape.  Enqueued on `stream`; does not synchronise. */
 wpcd_status wpcd_kapply_noalloc(const wpcd_problem *pr, const wpcd_P *P, const double *g, const double *x,
                                 double *y, void *stream);
 

@@ -12,7 +12,11 @@ Parity status of each piece (pins live in ``tests/test_oracle_*.py``):
 - pair diagonalisation: pinned (library eigensolver, Numerov bound state).
 - node-binned P0: pinned by the l = 0 sum rule, convergence to the exact cell
   overlap (``exact_overlap`` below, a different algorithm), symmetry of the
-  exact overlap, cross-parity zeros and the energy-shell pattern.  The node
+  exact overlap, cross-parity zeros and the energy-shell pattern; its overall
+  scale and the sqrt((2l+1)(2l'+1)) factor of every block with l, l' <= 4 by
+  P f = 2 f for totally symmetric and antisymmetric f (the two cyclic
+  permutations map such an f to itself), block by block, converging at
+  second order in the cell size.  The node
   sum itself is the method's quadrature, so its agreement with the exact
   integral is a convergence statement, not an identity.
 - G1: pinned (adaptive quadrature of the defining integral, closed-form

@@ -325,16 +325,6 @@ static wpcd_status create(const wpcd_problem_desc *d, wpcd_problem **out) {
 
 using namespace wpcd;
 
-#define WPCD_GUARD_BEGIN try {
-#define WPCD_GUARD_END                                                   \
-  }                                                                      \
-  catch (const std::bad_alloc &) {                                       \
-    return set_error(WPCD_ENOMEM, "host allocation failed");             \
-  }                                                                      \
-  catch (...) {                                                          \
-    return set_error(WPCD_EINVAL, "internal error (unexpected exception)"); \
-  }
-
 extern "C" {
 
 const char *wpcd_last_error(void) { return g_last_error.c_str(); }

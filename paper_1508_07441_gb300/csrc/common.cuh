@@ -464,7 +464,6 @@ __global__ void bfallback_kernel(int64_t n, int B, const int *flag, const double
   }
 }
 
-// launch shapes tried by the autotuner for a batch of B energies
 // Steps of a mixed-solve refinement cycle after the first: the previous
 // cycle (mm_prev steps) took the worst relative residual from worst_prev to
 // worst; at that per-step reduction, the steps to a tenth of tol, at least 2
@@ -476,6 +475,7 @@ inline int next_cycle_steps(double worst, double worst_prev, int mm_prev, int m,
   return need < m ? std::max(2, (int)std::ceil(need)) : m;
 }
 
+// launch shapes tried by the autotuner for a batch of B energies
 std::vector<SpmmConfig> candidates(int B) {
   std::vector<SpmmConfig> c;
   if (B == 1) {

@@ -53,6 +53,7 @@ wpcd_status scratch_for_device(int device, double2 **out) {
 extern "C" wpcd_status wpcd_kapply_noalloc(const wpcd_problem *pr, const wpcd_P *P, const double *g,
                                            const double *x, double *y, void *stream) {
   wpcd::clear_error();
+  WPCD_GUARD_BEGIN
   if (!pr || !P || !x || !y || x == y) return wpcd::set_error(WPCD_EINVAL, "bad kapply arguments");
   if (P->pr != pr) return wpcd::set_error(WPCD_EINVAL, "P was assembled for another problem");
   const int64_t dim = (int64_t)pr->n_ch * pr->N * pr->M;
@@ -66,4 +67,5 @@ extern "C" wpcd_status wpcd_kapply_noalloc(const wpcd_problem *pr, const wpcd_P 
   if (st != WPCD_OK) return st;
   return wpcd::kapply_scratch(pr, P, g, x, y, reinterpret_cast<double *>(scratch),
                               reinterpret_cast<double *>(scratch + dim), static_cast<cudaStream_t>(stream));
+  WPCD_GUARD_END
 }

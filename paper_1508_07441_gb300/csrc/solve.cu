@@ -836,8 +836,7 @@ wpcd_status tune_spmm(const wpcd_problem *pr, wpcd_P *P, int B, int mode, cudaSt
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   if (mode < 0 || mode > 2) return set_error(WPCD_EINVAL, "unknown SpMM tuning mode");
   const bool fp32 = mode == 1, ff = mode == 2;
-  // the key carries the shape so that one cache file can serve several problems
-  const int64_t key = ((((int64_t)pr->n_ch * 4096 + pr->N) * 4096 + pr->M) * 4096 + B) * 4 + mode;
+  const int64_t key = spmm_tune_key(pr->n_ch, pr->N, pr->M, B, mode);
   auto it = P->tuned.find(key);
   if (it != P->tuned.end()) {
     *out = it->second;
@@ -1105,10 +1104,14 @@ wpcd_status kapply_scratch(const wpcd_problem *pr, const wpcd_P *P, const double
   else
     gemm_kernel<double, false, false><<<grid, G_THREADS, 0, s>>>(N, ncol, pr->d.Vt, x, nullptr, nullptr, scratch_y);
   count_launches(1);
+  // the choice tune_spmm made for one FP64 right-hand side (mode 0), if any;
+  // the map is read under the tuner's lock, which inserts into it
   SpmmConfig cfg{2, 1, 1};
-  const int64_t key = ((((int64_t)pr->n_ch * 4096 + pr->N) * 4096 + pr->M) * 4096 + 1) * 2;
-  auto it = P->tuned.find(key);
-  if (it != P->tuned.end()) cfg = it->second;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = P->tuned.find(spmm_tune_key(pr->n_ch, pr->N, pr->M, 1, 0));
+    if (it != P->tuned.end()) cfg = it->second;
+  }
   wpcd_status st = P->prec == WPCD_FP64
                        ? launch_spmm_cfg<double, double>(pr, P, P->val64, scratch_y, scratch_z, 1, cfg, s)
                        : launch_spmm_cfg<float, double>(pr, P, P->val32, scratch_y, scratch_z, 1, cfg, s);

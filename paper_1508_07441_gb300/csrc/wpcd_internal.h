@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <map>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -66,6 +67,17 @@ void clear_error();
     if (_e != cudaSuccess) return ::wpcd::cuda_error(_e, #expr); \
   } while (0)
 
+// Body of every extern "C" entry point: no C++ exception crosses the ABI
+#define WPCD_GUARD_BEGIN try {
+#define WPCD_GUARD_END                                                              \
+  }                                                                                 \
+  catch (const std::bad_alloc &) {                                                  \
+    return ::wpcd::set_error(WPCD_ENOMEM, "host allocation failed");                \
+  }                                                                                 \
+  catch (...) {                                                                     \
+    return ::wpcd::set_error(WPCD_EINVAL, "internal error (unexpected exception)"); \
+  }
+
 // ---- host mathematics of step 1 (setup.cpp) -------------------------------
 void gauss_legendre(int n, double *t, double *w);
 double bessel_i_scaled(int l, double z);  // exp(-z) i_l(z)
@@ -117,6 +129,15 @@ struct wpcd_problem {
 struct SpmmConfig {
   int rpw = 1, el = 1, ept = 1;
 };
+
+namespace wpcd {
+// Key of an autotuner choice: the problem shape, the batch B and the
+// arithmetic mode (0 FP64 vectors, 1 FP32, 2 float-float), so that one cache
+// file can serve several problems
+inline int64_t spmm_tune_key(int n_ch, int N, int M, int B, int mode) {
+  return ((((int64_t)n_ch * 4096 + N) * 4096 + M) * 4096 + B) * 4 + mode;
+}
+}  // namespace wpcd
 
 struct wpcd_P {
   const wpcd_problem *pr = nullptr;

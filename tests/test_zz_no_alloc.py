@@ -24,6 +24,10 @@ def W():
 
 
 def test_noalloc_matches_kapply_on_two_calls(W):
+    """After wpcd_kapply has tuned the one-right-hand-side SpMM shape, the
+    no-alloc call runs the same kernels with the same shape, so its result is
+    the same bit for bit; and the calls leave the device's free memory as it
+    was (nothing allocated)."""
     import torch
     from paper_1508_07441_gb300 import inputs
 
@@ -32,22 +36,26 @@ def test_noalloc_matches_kapply_on_two_calls(W):
     P = pr.wpcd_assemble_P(W.WPCD_FP64)
     g = torch.zeros(2 * pr.dim, dtype=torch.float64, device="cuda")
     pr.wpcd_resolvent([0.7], g)
-    for call, seed in enumerate((7, 8)):  # two calls in a row, different inputs
-        x = inputs.random_complex(pr.dim, seed)
-        xd = torch.from_numpy(x.view(np.float64).copy()).cuda()
-        ref = torch.zeros_like(xd)
-        got = torch.full_like(xd, float("nan"))
-        pr.wpcd_kapply(P, g, xd, ref)
-        pr.wpcd_kapply_noalloc(P, g, xd, got)
-        torch.cuda.synchronize()
-        r, o = ref.cpu().numpy(), got.cpu().numpy()
-        assert np.all(np.isfinite(o)), call
-        assert np.linalg.norm(o - r) / np.linalg.norm(r) < 1e-11, call
-    # and with G1 = 1
-    pr.wpcd_kapply(P, None, xd, ref)
-    pr.wpcd_kapply_noalloc(P, None, xd, got)
+    xs = [torch.from_numpy(inputs.random_complex(pr.dim, seed).view(np.float64).copy()).cuda()
+          for seed in (7, 8)]
+    refs = [torch.zeros_like(xs[0]) for _ in range(3)]
+    gots = [torch.full_like(xs[0], float("nan")) for _ in range(3)]
+    warm = torch.zeros_like(xs[0])
+    for k, (gg, x) in enumerate(((g, xs[0]), (g, xs[1]), (None, xs[1]))):
+        pr.wpcd_kapply(P, gg, x, refs[k])
+    pr.wpcd_kapply_noalloc(P, g, xs[0], warm)  # first call on the device: address look-up
     torch.cuda.synchronize()
-    assert np.linalg.norm(got.cpu().numpy() - ref.cpu().numpy()) / np.linalg.norm(ref.cpu().numpy()) < 1e-11
+    free0 = torch.cuda.mem_get_info()[0]
+    # two calls in a row with different inputs (the array keeps the previous
+    # call's contents), then one with G1 = 1
+    for k, (gg, x) in enumerate(((g, xs[0]), (g, xs[1]), (None, xs[1]))):
+        pr.wpcd_kapply_noalloc(P, gg, x, gots[k])
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    for k in range(3):
+        r, o = refs[k].cpu().numpy(), gots[k].cpu().numpy()
+        assert np.all(np.isfinite(o)), k
+        assert np.array_equal(o, r), (k, np.abs(o - r).max())
 
 
 def test_noalloc_rejects_dimension_above_limit(W):
