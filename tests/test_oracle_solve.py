@@ -121,3 +121,20 @@ def test_unitarity_below_breakup(orc):
     gm = pr.solve_gmres(1.0, tol=1e-12)
     S3, _ = pr.amplitudes(1.0, gm["U00"])
     assert abs(S3) < 1.0
+
+
+def test_U00_one_value_per_onshell_bin(orc):
+    """The energy enters G1 only through its on-shell bin (the average over
+    the energy bin [E_lo, E_hi], Sec. 2.3) and the Born term only through
+    that bin's unit vector, so two energies of one bin give the same U00 bit
+    for bit; a neighbouring bin gives another.  (The full-size parity checks
+    solve the oracle once per distinct bin on this ground.)"""
+    pe, qe = orc.tangent_edges(16, 20.0), orc.tangent_edges(14, 20.0)
+    pr = orc.Problem(dict(pe=pe, qe=qe, n_p=3, n_q=3, n_x=8, n_ch=2, V=[-6.0], a=[1.0], n_pair_nodes=6))
+    j0, Elo, Ehi, _ = orc.onshell(qe, 0.5, pr.eps_b)
+    Es = [Elo + f * (Ehi - Elo) for f in (0.1, 0.5, 0.93)]
+    assert all(orc.onshell(qe, e, pr.eps_b)[0] == j0 for e in Es)
+    U = [pr.solve_gmres(e, tol=1e-12)["U00"] for e in Es]
+    assert U[0] == U[1] == U[2]
+    other = pr.solve_gmres(Ehi + 0.5 * (Ehi - Elo), tol=1e-12)["U00"]
+    assert abs(other - U[0]) > 1e-6 * abs(U[0])
