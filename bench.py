@@ -382,6 +382,16 @@ def kernel_rooflines(W, pr, w, phases, n_nodes, n_e, stream, flush, peaks, f_sm,
           f"{spmv_flops:.3e} FP64 flops, {spmv_bytes:.3e} B (HBM fraction "
           f"{spmv_bytes / (ms * 1e-3) / 1e9 / hbm:.3f}): at 0.45 flop/B it sits above GB300's FP64 ridge "
           f"({fp64 * 1e3 / hbm:.2f} flop/B), so the FP64 pipe, not HBM, bounds it", src64)
+    # the FP32-valued one-right-hand-side SpMV (the mixed single-energy inner
+    # loop): HBM-bound, 4 B column + 4 n_pairs B values per nonzero
+    x1f = torch.randn(2 * dim, dtype=torch.float32, device="cuda")
+    y1f = torch.empty_like(x1f)
+    ms = _time_kernel(stream, flush, lambda: pr.wpcd_spmm(P, x1f, y1f, 1, mode=W.WPCD_SPMM_FP32, stream=stream,
+                                                           timed=True), reps=5)
+    spmv32_bytes = P.nnz * (4 + 4 * pr.n_pairs) + 8 * (N * M + 1) + 2 * 8 * dim
+    entry("spmm_sacc_kernel<FP32> (1 RHS)", "hbm", spmv32_bytes / (ms * 1e-3) / 1e9, hbm, "GB/s", ms, 0,
+          f"{spmv32_bytes:.3e} B: columns and FP32 values read once, row pointers, y read and z written "
+          "once (FP32 complex)", "measured HBM copy (hbm_gbs)")
     ms = _time_kernel(stream, flush, lambda: pr.wpcd_channel_gemm(1, W.WPCD_GEMM_FP64, None, x1, y1, 1,
                                                                    stream=stream, timed=True))
     g1 = 2.0 * N * N * (2 * M) * n_ch

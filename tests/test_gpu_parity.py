@@ -88,7 +88,7 @@ def test_assemble_matches_oracle(W, orc, N, M, nodes, n_ch, jit, prec):
     print(f"P0-measure {prec} {N}x{M} n_ch={n_ch}: {st}")
     # elements that pass only through the absolute term: vanishing sums and
     # FP32 terms at roots of P_l'; a bounded minority
-    assert st["n_abs_only"] <= (0.02 if prec == "fp32c" else 0.005) * st["n"], st
+    assert st["n_abs_only"] <= (0.01 if prec == "fp32c" else 0.005) * st["n"], st
 
 
 def test_assemble_deterministic(W):
@@ -116,7 +116,8 @@ def test_assemble_full_size_3_channels(W, orc):
         assert _excess(val.T, ref["val"], ref["absval"], name) <= 1.0
         st = _measure_stats(val.T, ref["val"], ref["absval"], ref["row_ptr"], w["n_ch"], name)
         print(f"P0-measure {name} 200x200 n_ch=3: {st}")
-        assert st["n_abs_only"] <= (0.02 if name == "fp32c" else 0.005) * st["n"], st
+        # measured: 11 881 (FP32C) and 1 306 (FP64) of 14 974 110
+        assert st["n_abs_only"] <= (0.002 if name == "fp32c" else 0.0005) * st["n"], st
 
 
 def test_pair_setup_matches_oracle(W, orc):
@@ -180,10 +181,14 @@ def _kapply_bound(opr, x, g):
 
 
 def test_kapply_matches_oracle(W, orc):
-    """Element by element: |y - y_ref| <= gamma S per output, S the sum of
-    its terms' magnitudes and gamma = 4 (N + n_terms + N) 2^-53 (three
-    summations, of N, of at most n_pairs times the longest row, and of N
-    terms), so a wrong small block cannot hide under the norm."""
+    """Element by element on the same inputs: the oracle applies the library's
+    own O, Vt = v O^T and P0 (exported), so the two sides differ by rounding
+    only, and |y - y_ref| <= gamma S per output, S the sum of its terms'
+    magnitudes and gamma = 4 (N + n_terms + N) 2^-53 (three summations, of
+    N, of at most n_pairs times the longest row, and of N terms): a wrong
+    small block cannot hide under a norm.  End to end (the oracle's own pair
+    setup and P0, whose eigenvectors agree with the library's to about 1e-8)
+    the results agree in norm."""
     import torch
     from paper_1508_07441_gb300 import inputs
 
@@ -193,7 +198,14 @@ def test_kapply_matches_oracle(W, orc):
     P = pr.wpcd_assemble_P(W.WPCD_FP64)
     opr = orc.Problem(dict(pe=pe, qe=qe, n_p=4, n_q=4, n_x=16, n_ch=n_ch, V=[-6.0], a=[1.0],
                            n_pair_nodes=8))
-    rowlen = int(np.diff(opr.P["row_ptr"]).max()) * orc.n_pairs(n_ch)
+    same = orc.Problem(dict(pe=pe, qe=qe, n_p=4, n_q=4, n_x=16, n_ch=n_ch, V=[-6.0], a=[1.0],
+                            n_pair_nodes=8), P=opr.P)
+    rp, col, val = P.wpcd_P_export()
+    same.P = dict(row_ptr=rp, col=col, val=np.ascontiguousarray(val.T))
+    pairs = [pr.wpcd_problem_pair(l) for l in range(n_ch)]
+    same.O = np.ascontiguousarray(np.stack([O for _, O, _ in pairs]))
+    same.Vt = np.ascontiguousarray(np.einsum("lij,lkj->lik", np.stack([v for _, _, v in pairs]), same.O))
+    rowlen = int(np.diff(rp).max()) * orc.n_pairs(n_ch)
     gamma = 4 * (28 + rowlen + 28) * 2.0 ** -53
     x = inputs.random_complex(pr.dim, 7)
     g = torch.zeros(2 * pr.dim, dtype=torch.float64, device="cuda")
@@ -204,11 +216,13 @@ def test_kapply_matches_oracle(W, orc):
     for gg, gh in ((g, gx), (None, None)):  # with G1, and G1 = 1
         pr.wpcd_kapply(P, gg, xd, yd)
         y = yd.cpu().numpy().view(np.complex128)
-        ref = opr.kapply(x, gh)
-        S = _kapply_bound(opr, x, gh)
+        ref = same.kapply(x, gh)
+        S = _kapply_bound(same, x, gh)
         assert np.all(np.abs(y - ref) <= gamma * S), np.max(np.abs(y - ref) / S)
         # the bar has power: the outputs are far above it
         assert np.median(np.abs(ref) / S) > 1e3 * gamma
+        end = opr.kapply(x, gh)
+        assert np.linalg.norm(y - end) / np.linalg.norm(end) < 1e-11
 
 
 def _problems(W, orc, N, M, nodes, n_ch, V=(-6.0,), a=(1.0,), prec=None):
