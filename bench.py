@@ -10,8 +10,9 @@ equation for all of them in one batched iteration (FP32 inner Krylov cycles
 replayed from a CUDA graph inside an FP64 refinement loop, relative residual
 1e-10).  The plain FP64 single-energy solve, the comparison baseline, is
 timed separately on the same P0.  Inputs are resident in HBM before the timed
-region; L2 is flushed (512 MB write) before every timed step, outside its
-events.
+region; L2 is flushed before every timed step, outside its events: a 512 MB
+write, then a 256 MB read of another buffer, so that L2 holds clean lines and
+the timed work pays no write-back of the flush's dirty lines.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
 on the host cores on the same workload instead.
@@ -51,6 +52,9 @@ def parse():
     ap.add_argument("--warm-test", type=int, default=512)
     ap.add_argument("--no-batching", action="store_true")
     ap.add_argument("--no-precision-stress", action="store_true")
+    ap.add_argument("--kernel", choices=["spmv32", "spmv64", "spmm32", "spmm64"], default=None,
+                    help="time one kernel of the path alone on the workload's lattice (for profiling)")
+    ap.add_argument("--kernel-reps", type=int, default=5)
     return ap.parse_args()
 
 
@@ -147,6 +151,24 @@ NCU_TRAFFIC = {
     "oz_gemm_kernel (digit planes)": 450.4e6,
     "gemm_df_kernel": 903.6e6,
 }
+
+
+class L2Flush:
+    """Clears L2 (129 MB on GB300) between timed runs: fill_() writes a
+    512 MB buffer and then reads a 256 MB one, leaving L2 full of clean lines
+    (a write alone would leave ~129 MB of dirty lines for the timed kernel's
+    misses to write back)."""
+
+    def __init__(self):
+        import torch
+
+        self.w = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+        self.r = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+        self.sink = None
+
+    def fill_(self, v):
+        self.w.fill_(v)
+        self.sink = self.r.sum()
 
 
 def bench_precision_stress(args, W, inputs, stream, flush, device):
@@ -563,10 +585,48 @@ def bench_batching(args, W, inputs, stream, flush, device, maxr_fn=None):
     return res
 
 
+def run_kernel(args):
+    """One kernel of the path on the workload's lattice (FP64 assembly, then
+    the kernel's tuning, then --kernel-reps timed launches, each after an L2
+    flush): spmv32 / spmv64 the one-right-hand-side SpMV with FP32 / FP64
+    values and vectors, spmm32 / spmm64 the SpMM over --n-energies energies."""
+    import numpy as np
+    import torch
+
+    from paper_1508_07441_gb300 import inputs
+    from paper_1508_07441_gb300 import wpcd as W
+
+    torch.cuda.set_device(0)
+    w = inputs.workload(args.workload)
+    pr = W.Problem(w["p_edges"], w["q_edges"], *w["nodes"], w["n_ch"], w["V"], w["a"], n_pair_nodes=8)
+    P = pr.wpcd_assemble_P(W.WPCD_FP64)
+    B = 1 if args.kernel.startswith("spmv") else args.n_energies
+    fp32 = args.kernel.endswith("32")
+    dt = torch.float32 if fp32 else torch.float64
+    y = torch.randn(2 * pr.dim * B, dtype=dt, device="cuda")
+    z = torch.empty_like(y)
+    flush = L2Flush()
+    mode = W.WPCD_SPMM_FP32 if fp32 else W.WPCD_SPMM_FP64
+    pr.wpcd_spmm(P, y, z, B, mode=mode)  # tuning (and the FP32 value copy)
+    ms = []
+    for _ in range(args.kernel_reps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        ms.append(pr.wpcd_spmm(P, y, z, B, mode=mode, timed=True))
+    s_val = 4 if fp32 else 8
+    nbytes = P.nnz * (4 + s_val * pr.n_pairs) + 8 * (pr.N * pr.M + 1) + 2 * 2 * s_val * pr.dim * B
+    print(json.dumps({"kernel": args.kernel, "n_rhs": B, "ms": ms, "ms_mean": float(np.mean(ms[1:] or ms)),
+                      "bytes": nbytes, "GB_per_s": nbytes / (float(np.mean(ms[1:] or ms)) * 1e-3) / 1e9,
+                      "flops": 4.0 * pr.n_pairs * P.nnz * B, "shape": pr.wpcd_tune_spmm(P, B, fp32=fp32)}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.kernel:
+        return run_kernel(args)
 
     import numpy as np
     import torch
@@ -592,7 +652,7 @@ def main():
     pr = W.Problem(w["p_edges"], w["q_edges"], *w["nodes"], w["n_ch"], w["V"], w["a"],
                    n_pair_nodes=8, device=local)
     energies = [float(x) for x in inputs.batch_energies(pr.eps_bound, args.n_energies)]
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    flush = L2Flush()
 
     def barrier():
         torch.cuda.synchronize()
@@ -810,7 +870,8 @@ def main():
                    "solve": "batched (all energies in one iteration), FP32 inner Krylov cycles "
                             "of 10 steps (tensor-core TF32x3 block products, CUDA graph) + float-float "
                             "refinement residual to rel residual 1e-10",
-                   "l2": "flushed (512 MB write) before every timed step",
+                   "l2": "flushed (512 MB write, then a 256 MB read) before every timed step and every "
+                         "timed kernel launch",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "assembly": {"ms": asm_ms, "count_ms": phases[0], "scan_ms": phases[1], "fill_ms": phases[2],
                      "nnz_cells": recs[-1]["nnz"]},

@@ -732,6 +732,14 @@ struct Workspace {
 template <typename VT, typename T>
 wpcd_status launch_spmm_cfg(const wpcd_problem *pr, const wpcd_P *P, const VT *val, const T *y, T *z,
                             int B, const SpmmConfig &cfg, cudaStream_t s) {
+  // one right-hand side with values in the vectors' precision: the SpMV
+  // (spmv.cu), cfg.rpw rows per warp; cfg.el = 2 the streaming form, else
+  // cfg.ept chunks per step
+  if (B == 1 && sizeof(VT) == sizeof(T)) {
+    if (cfg.el == 2)
+      return launch_spmv_stream(pr, const_cast<wpcd_P *>(P), sizeof(T) == 8, val, y, z, cfg.rpw, s);
+    return launch_spmv(pr, P, sizeof(T) == 8, val, y, z, cfg.rpw, cfg.ept, s);
+  }
   SpmmParams S{};
   S.n_cells = pr->N * pr->M;
   S.B = B;
@@ -812,7 +820,11 @@ bool load_cached(int64_t key, SpmmConfig *out) {
     std::istringstream is(line);
     long long k;
     SpmmConfig c;
-    if (is >> k >> c.rpw >> c.el >> c.ept && k == key) {
+    // a shape the kernels can run: rows per warp and energy lanes powers of
+    // two sharing the 32 lanes, 1, 2 or 4 energies per lane; others ignored
+    const auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
+    if (is >> k >> c.rpw >> c.el >> c.ept && k == key && pow2(c.rpw) && pow2(c.el) && c.rpw * c.el <= 32 &&
+        (c.ept == 1 || c.ept == 2 || c.ept == 4)) {
       *out = c;
       found = true;
     }
@@ -898,6 +910,9 @@ wpcd_status tune_spmm(const wpcd_problem *pr, wpcd_P *P, int B, int mode, cudaSt
       tmin = std::min(tmin, ms);
     }
     if (st != WPCD_OK) break;
+    if (std::getenv("WPCD_TUNE_LOG"))
+      std::fprintf(stderr, "wpcd tune B=%d mode=%d rpw=%d el=%d ept=%d: %.4f ms\n", B, mode, c.rpw, c.el, c.ept,
+                   tmin);
     if (tmin < best) {
       best = tmin;
       pick = c;
@@ -1112,6 +1127,9 @@ wpcd_status kapply_scratch(const wpcd_problem *pr, const wpcd_P *P, const double
     auto it = P->tuned.find(spmm_tune_key(pr->n_ch, pr->N, pr->M, 1, 0));
     if (it != P->tuned.end()) cfg = it->second;
   }
+  // the streaming form needs its row-block plan, made (with an allocation)
+  // on first use: without it, the plain form
+  if (cfg.el == 2 && !spmv_stream_ready(P, P->prec == WPCD_FP64)) cfg = SpmmConfig{2, 1, 1};
   wpcd_status st = P->prec == WPCD_FP64
                        ? launch_spmm_cfg<double, double>(pr, P, P->val64, scratch_y, scratch_z, 1, cfg, s)
                        : launch_spmm_cfg<float, double>(pr, P, P->val32, scratch_y, scratch_z, 1, cfg, s);
@@ -1874,7 +1892,7 @@ wpcd_status solve(wpcd_problem *pr, const wpcd_P *Pc, const double *E, int n_E,
       if (st != WPCD_OK) return st;
     }
     if (mixed && !P->val32 && !P->val32_copy) {
-      WPCD_CUDA_TRY(dev_malloc(&P->val32_copy, sizeof(float) * (size_t)P->nnz * P->n_pairs + 4));
+      WPCD_CUDA_TRY(dev_malloc(&P->val32_copy, sizeof(float) * (size_t)P->nnz * P->n_pairs + kPad));
       int64_t nv = (int64_t)P->nnz * P->n_pairs;
       d2f_kernel<<<grid_for(nv, 256), 256, 0, s>>>(nv, P->val64, P->val32_copy);
       count_launches(1);
@@ -2013,7 +2031,7 @@ wpcd_status spmm_apply(wpcd_problem *pr, wpcd_P *P, int mode, const void *y, voi
   if (mode == WPCD_SPMM_FF) return df_spmm_op(pr, P, (const double *)y, (double *)z, n_rhs, ms, s);
   const bool fp32 = mode == WPCD_SPMM_FP32 || mode == WPCD_SPMM_FP32_BLOCKED;
   if (fp32 && !P->val32 && !P->val32_copy) {
-    WPCD_CUDA_TRY(dev_malloc(&P->val32_copy, sizeof(float) * (size_t)P->nnz * P->n_pairs + 4));
+    WPCD_CUDA_TRY(dev_malloc(&P->val32_copy, sizeof(float) * (size_t)P->nnz * P->n_pairs + kPad));
     const int64_t nv = (int64_t)P->nnz * P->n_pairs;
     d2f_kernel<<<grid_for(nv, 256), 256, 0, s>>>(nv, P->val64, P->val32_copy);
     count_launches(1);
