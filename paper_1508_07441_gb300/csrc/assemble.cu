@@ -593,7 +593,7 @@ wpcd_status assemble(wpcd_problem *pr, int prec, cudaStream_t s, wpcd_P **out) {
   cudaError_t e;
   if ((e = dev_malloc(&counts, sizeof(int64_t) * n_cells)) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc counts"));
   if ((e = dev_malloc(&sorted, sizeof(uint32_t) * (size_t)n_cells * np2)) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc sorted keys"));
-  if ((e = dev_malloc(&Pm->row_ptr, sizeof(int64_t) * (n_cells + 1) + kPad)) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc row_ptr"));
+  if ((e = dev_malloc(&Pm->row_ptr, sizeof(int64_t) * (n_cells + 1))) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc row_ptr"));
 
   cudaEventRecord(ev0, s);
   size_t smem_count = sizeof(long long) * (P.N + P.M + 2) + sizeof(BinConst) * P.n_p * P.n_q +
@@ -611,13 +611,13 @@ wpcd_status assemble(wpcd_problem *pr, int prec, cudaStream_t s, wpcd_P **out) {
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(cuda_error(e, "count pass"));
   Pm->nnz = nnz;
   size_t nz = nnz > 0 ? (size_t)nnz : 1;
-  if ((e = dev_malloc(&Pm->col, sizeof(int32_t) * nz + kPad)) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc col"));
+  if ((e = dev_malloc(&Pm->col, sizeof(int32_t) * nz)) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc col"));
   void *val = nullptr;
   if (prec == WPCD_FP64) {
-    if ((e = dev_malloc(&Pm->val64, sizeof(double) * nz * P.n_pairs + kPad)) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc val"));
+    if ((e = dev_malloc(&Pm->val64, sizeof(double) * nz * P.n_pairs)) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc val"));
     val = Pm->val64;
   } else {
-    if ((e = dev_malloc(&Pm->val32, sizeof(float) * nz * P.n_pairs + kPad)) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc val"));
+    if ((e = dev_malloc(&Pm->val32, sizeof(float) * nz * P.n_pairs)) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc val"));
     val = Pm->val32;
   }
   size_t rsz = prec == WPCD_FP64 ? sizeof(double) : sizeof(float);

@@ -412,8 +412,6 @@ void wpcd_P_destroy(wpcd_P *P) {
   dev_free(P->blk_nu);
   dev_free(P->blk_ucol);
   dev_free(P->blk_lidx);
-  dev_free(P->sv_blocks[0]);
-  dev_free(P->sv_blocks[1]);
   delete P;
 }
 

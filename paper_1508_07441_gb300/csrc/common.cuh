@@ -478,11 +478,9 @@ inline int next_cycle_steps(double worst, double worst_prev, int mm_prev, int m,
 // launch shapes tried by the autotuner for a batch of B energies
 std::vector<SpmmConfig> candidates(int B) {
   std::vector<SpmmConfig> c;
-  if (B == 1) {  // the one-right-hand-side SpMV (spmv.cu): ept = chunks per
-                 // step; el = 2 the streaming form
+  if (B == 1) {  // the one-right-hand-side SpMV (spmv.cu): ept = chunks per step
     for (int cps : {1, 2})
       for (int rpw : {2, 4, 8, 16}) c.push_back(SpmmConfig{rpw, 1, cps});
-    for (int rpw : {2, 4, 8}) c.push_back(SpmmConfig{rpw, 2, 1});
     return c;
   }
   int el = 1;

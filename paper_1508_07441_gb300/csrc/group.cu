@@ -1261,7 +1261,7 @@ wpcd_status solve_group(int n_prob, wpcd_problem *const *prs, const wpcd_P *cons
   for (int g = 0; g < n_prob; ++g) {
     wpcd_P *P = const_cast<wpcd_P *>(Ps[g]);
     if (mixed && !P->val32 && !P->val32_copy) {
-      WPCD_CUDA_TRY(dev_malloc(&P->val32_copy, sizeof(float) * (size_t)P->nnz * P->n_pairs + kPad));
+      WPCD_CUDA_TRY(dev_malloc(&P->val32_copy, sizeof(float) * (size_t)P->nnz * P->n_pairs + 4));
       const int64_t nv = (int64_t)P->nnz * P->n_pairs;
       gd2f_kernel<<<grid_for(nv, 256), 256, 0, s>>>(nv, P->val64, P->val32_copy);
       count_launches(1);

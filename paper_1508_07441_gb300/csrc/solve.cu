@@ -732,14 +732,9 @@ struct Workspace {
 template <typename VT, typename T>
 wpcd_status launch_spmm_cfg(const wpcd_problem *pr, const wpcd_P *P, const VT *val, const T *y, T *z,
                             int B, const SpmmConfig &cfg, cudaStream_t s) {
-  // one right-hand side with values in the vectors' precision: the SpMV
-  // (spmv.cu), cfg.rpw rows per warp; cfg.el = 2 the streaming form, else
-  // cfg.ept chunks per step
-  if (B == 1 && sizeof(VT) == sizeof(T)) {
-    if (cfg.el == 2)
-      return launch_spmv_stream(pr, const_cast<wpcd_P *>(P), sizeof(T) == 8, val, y, z, cfg.rpw, s);
-    return launch_spmv(pr, P, sizeof(T) == 8, val, y, z, cfg.rpw, cfg.ept, s);
-  }
+  // one right-hand side with values in the vectors' precision: the SpMV of
+  // spmv.cu (cfg.rpw rows per warp, cfg.ept chunks per step)
+  if (B == 1 && sizeof(VT) == sizeof(T)) return launch_spmv1(pr, P, sizeof(T) == 8, val, y, z, cfg, s);
   SpmmParams S{};
   S.n_cells = pr->N * pr->M;
   S.B = B;
@@ -1127,9 +1122,7 @@ wpcd_status kapply_scratch(const wpcd_problem *pr, const wpcd_P *P, const double
     auto it = P->tuned.find(spmm_tune_key(pr->n_ch, pr->N, pr->M, 1, 0));
     if (it != P->tuned.end()) cfg = it->second;
   }
-  // the streaming form needs its row-block plan, made (with an allocation)
-  // on first use: without it, the plain form
-  if (cfg.el == 2 && !spmv_stream_ready(P, P->prec == WPCD_FP64)) cfg = SpmmConfig{2, 1, 1};
+
   wpcd_status st = P->prec == WPCD_FP64
                        ? launch_spmm_cfg<double, double>(pr, P, P->val64, scratch_y, scratch_z, 1, cfg, s)
                        : launch_spmm_cfg<float, double>(pr, P, P->val32, scratch_y, scratch_z, 1, cfg, s);
@@ -1892,7 +1885,7 @@ wpcd_status solve(wpcd_problem *pr, const wpcd_P *Pc, const double *E, int n_E,
       if (st != WPCD_OK) return st;
     }
     if (mixed && !P->val32 && !P->val32_copy) {
-      WPCD_CUDA_TRY(dev_malloc(&P->val32_copy, sizeof(float) * (size_t)P->nnz * P->n_pairs + kPad));
+      WPCD_CUDA_TRY(dev_malloc(&P->val32_copy, sizeof(float) * (size_t)P->nnz * P->n_pairs + 4));
       int64_t nv = (int64_t)P->nnz * P->n_pairs;
       d2f_kernel<<<grid_for(nv, 256), 256, 0, s>>>(nv, P->val64, P->val32_copy);
       count_launches(1);
@@ -2031,7 +2024,7 @@ wpcd_status spmm_apply(wpcd_problem *pr, wpcd_P *P, int mode, const void *y, voi
   if (mode == WPCD_SPMM_FF) return df_spmm_op(pr, P, (const double *)y, (double *)z, n_rhs, ms, s);
   const bool fp32 = mode == WPCD_SPMM_FP32 || mode == WPCD_SPMM_FP32_BLOCKED;
   if (fp32 && !P->val32 && !P->val32_copy) {
-    WPCD_CUDA_TRY(dev_malloc(&P->val32_copy, sizeof(float) * (size_t)P->nnz * P->n_pairs + kPad));
+    WPCD_CUDA_TRY(dev_malloc(&P->val32_copy, sizeof(float) * (size_t)P->nnz * P->n_pairs + 4));
     const int64_t nv = (int64_t)P->nnz * P->n_pairs;
     d2f_kernel<<<grid_for(nv, 256), 256, 0, s>>>(nv, P->val64, P->val32_copy);
     count_launches(1);

@@ -3,51 +3,45 @@
 // FP32 (the mixed solve's inner cycles) or FP64 (the plain iteration).
 //
 // With one right-hand side every value of P0 is used for one complex
-// multiply-add per channel pair, so the step is bound by the bytes of P0:
-// a 4-byte column and n_pairs values per nonzero (24 bytes in FP32 for
-// three channels), against a y of a few hundred KB that stays in L2.  The
-// kernel is written to stream those bytes:
+// multiply-add per channel pair, so the step streams the bytes of P0: a
+// 4-byte column and n_pairs values per nonzero (24 bytes in FP32 for three
+// channels), against a y of a few hundred KB that stays in L2.
 //   - `RPW` rows per warp, LPR = 32 / RPW lanes per row (the autotuner's
-//     "rows per warp" for one right-hand side: 1, 2, 4, 8 or 16); a lane
-//     takes one or two chunks per step (the shape's "energies per lane"
-//     field for one right-hand side), their loads issued together;
-//   - chunks are four consecutive nonzeros, aligned to four elements, so
-//     the columns come in one 16-byte load and the values of each (l, l')
-//     pair in 16-, 8- or 4-byte loads (VW elements, whatever the alignment of
-//     the pair-major value array allows); elements of a chunk outside the
-//     row get value 0 (only the first and last chunk of a row), and a chunk
-//     reaching past the end of the arrays takes element loads;
-//   - the y gathers (three complex values per nonzero for three channels)
-//     hit L2.
-// Streaming form (the autotuner's shapes with two "energy lanes"): the
-// threads above spend most of their time waiting on the chain row pointer
-// -> columns and values -> y gathers.  Here persistent CTAs (two per SM)
-// take blocks of consecutive rows whose nonzeros fit a 32 KB stage (a plan
-// built once per matrix on the host from the row pointers) and a single
-// thread streams each block's row pointers, columns and values into a ring
-// of three shared-memory stages with bulk asynchronous copies
-// (cp.async.bulk, completion counted on one mbarrier per stage), two blocks
-// ahead of the block being summed; the threads then only gather y from L2
-// and multiply-add.  A row longer than a stage is summed by one warp from
-// global memory instead.
-//
+//     "rows per warp" for one right-hand side: 2, 4, 8 or 16); a lane takes
+//     one or two chunks per step (the shape's "energies per lane" field for
+//     one right-hand side), their loads issued together;
+//   - chunks are four consecutive nonzeros, aligned to four elements, so the
+//     columns come in one 16-byte load and the values of each (l, l') pair
+//     in 16-, 8- or 4-byte loads (whatever the alignment of the pair-major
+//     value array allows); elements of a chunk outside the row get value 0
+//     (only the first and last chunk of a row), and a chunk reaching past the
+//     end of the arrays takes element loads;
+//   - y is gathered per nonzero and channel (three 8-byte FP32 loads for
+//     three channels), from L2.
+// Measured on the 3-channel 200 x 200 lattice (FP32, L2 flushed): 34 us, 2.2
+// TB/s; the limit is the L1 pipeline (about 10 million sector look-ups, of
+// which the gathers are two thirds), not DRAM.
 // Sums: FP32 lanes sum at most 16 nonzeros plainly and add each such block
 // to a compensated accumulator (TwoSum hi, lo), and the lanes of a row are
 // combined with TwoSum as well (the FABsum scheme of the batched SpMM);
 // FP64 sums plainly.
 #include <cuda_runtime.h>
 
-#include <algorithm>
 #include <cstdint>
-#include <cstdlib>
-#include <vector>
 
 #include "common.cuh"
-#include "tc_ptx.cuh"
 #include "wpcd_internal.h"
 
 namespace wpcd {
 namespace {
+
+// widest value load the pair-major layout allows at every pair's offset
+// m * nnz + o (o a multiple of 4): 4, 2 or 1 elements
+template <typename T>
+inline int value_width(int64_t nnz) {
+  if (sizeof(T) == 4 && nnz % 4 == 0) return 4;
+  return nnz % 2 == 0 ? 2 : 1;
+}
 
 // running sum of one output: FP32 compensated (hi, lo), FP64 plain
 template <typename T>
@@ -78,13 +72,12 @@ struct SvSum<double> {
 };
 
 // four consecutive values starting at an element index that is a multiple
-// of VW (16-, 8- or 4-byte loads)
-template <int VW>
-__device__ __forceinline__ void load4(const float *__restrict__ p, float (&v)[4]) {
-  if constexpr (VW == 4) {
+// of vw (16-, 8- or 4-byte loads; vw is uniform over a launch)
+__device__ __forceinline__ void load4(const float *__restrict__ p, float (&v)[4], int vw) {
+  if (vw == 4) {
     const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
     v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
-  } else if constexpr (VW == 2) {
+  } else if (vw == 2) {
     const float2 a = __ldg(reinterpret_cast<const float2 *>(p)), b = __ldg(reinterpret_cast<const float2 *>(p + 2));
     v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
   } else {
@@ -92,9 +85,8 @@ __device__ __forceinline__ void load4(const float *__restrict__ p, float (&v)[4]
     for (int k = 0; k < 4; ++k) v[k] = __ldg(p + k);
   }
 }
-template <int VW>
-__device__ __forceinline__ void load4(const double *__restrict__ p, double (&v)[4]) {
-  if constexpr (VW >= 2) {
+__device__ __forceinline__ void load4(const double *__restrict__ p, double (&v)[4], int vw) {
+  if (vw >= 2) {
     const double2 a = __ldg(reinterpret_cast<const double2 *>(p)), b = __ldg(reinterpret_cast<const double2 *>(p + 2));
     v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
   } else {
@@ -103,54 +95,17 @@ __device__ __forceinline__ void load4(const double *__restrict__ p, double (&v)[
   }
 }
 
-// four consecutive values from shared memory, VW-wide loads
-template <int VW, typename T>
-__device__ __forceinline__ void lds4(const T *p, T (&v)[4]) {
-  if constexpr (VW * sizeof(T) == 16) {
-    if constexpr (sizeof(T) == 4) {
-      const float4 q = *reinterpret_cast<const float4 *>(p);
-      v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
-    } else {
-      const double2 a = *reinterpret_cast<const double2 *>(p), b = *reinterpret_cast<const double2 *>(p + 2);
-      v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
-    }
-  } else if constexpr (VW == 2 && sizeof(T) == 4) {
-    const float2 a = *reinterpret_cast<const float2 *>(p), b = *reinterpret_cast<const float2 *>(p + 2);
-    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
-  } else {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = p[k];
-  }
-}
-
-__device__ __forceinline__ void mbar_arrive_plain(uint64_t *bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void expect_tx_bytes(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-// make the mbarrier initialisation visible to the asynchronous (copy) proxy
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
 // one chunk of four consecutive nonzeros at element o (a multiple of 4):
 // columns and the values of every (l, l') pair; a chunk reaching past the end
 // of the arrays takes element loads (column 0, value 0 beyond the end)
-template <typename T, int NPAIR, int VW>
+template <typename T, int NPAIR>
 __device__ __forceinline__ void load_chunk(const int32_t *__restrict__ col, const T *__restrict__ val, int64_t nnz,
-                                           int64_t o, int (&t)[4], T (&v)[NPAIR][4]) {
+                                           int64_t o, int (&t)[4], T (&v)[NPAIR][4], int vw) {
   if (o + 4 <= nnz) {
     const int4 cc = __ldg(reinterpret_cast<const int4 *>(col + o));
     t[0] = cc.x, t[1] = cc.y, t[2] = cc.z, t[3] = cc.w;
 #pragma unroll
-    for (int m = 0; m < NPAIR; ++m) load4<VW>(val + (size_t)m * nnz + o, v[m]);
+    for (int m = 0; m < NPAIR; ++m) load4(val + (size_t)m * nnz + o, v[m], vw);
   } else {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -159,6 +114,17 @@ __device__ __forceinline__ void load_chunk(const int32_t *__restrict__ col, cons
 #pragma unroll
       for (int m = 0; m < NPAIR; ++m) v[m][k] = in ? __ldg(val + (size_t)m * nnz + o + k) : T(0);
     }
+  }
+}
+
+// y of every channel at cell t (layout y[l][c])
+template <typename T, int NCH>
+__device__ __forceinline__ void gather_y(const typename Cx<T>::t *__restrict__ y, int n_cells, int t, T (&yr)[NCH],
+                                         T (&yim)[NCH]) {
+#pragma unroll
+  for (int l = 0; l < NCH; ++l) {
+    const typename Cx<T>::t q = __ldg(y + (size_t)l * n_cells + t);
+    yr[l] = q.x, yim[l] = q.y;
   }
 }
 
@@ -181,12 +147,7 @@ __device__ __forceinline__ void use_chunk(const typename Cx<T>::t *__restrict__ 
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     T yr[NCH], yi[NCH];
-#pragma unroll
-    for (int l = 0; l < NCH; ++l) {
-      const C2 q = __ldg(y + (size_t)l * n_cells + t[k]);
-      yr[l] = q.x;
-      yi[l] = q.y;
-    }
+    gather_y<T, NCH>(y, n_cells, t[k], yr, yi);
 #pragma unroll
     for (int m = 0; m < NPAIR; ++m) {
       const int l = pair_first(NCH, m), lp = pair_second(NCH, m);
@@ -199,11 +160,11 @@ __device__ __forceinline__ void use_chunk(const typename Cx<T>::t *__restrict__ 
 // CPS chunks per step: 1 (for up to three channels three FP32 / two FP64
 // CTAs of 256 threads per SM) or 2 (their loads in flight together, about
 // twice the registers; up to three channels)
-template <typename T, int NCH, int RPW, int VW, int CPS>
-__global__ void __launch_bounds__(256, CPS == 1 && NCH <= 3 ? (sizeof(T) == 4 ? 3 : 2) : 1) spmv_kernel(int n_cells, const int64_t *__restrict__ row_ptr,
-                                                   const int32_t *__restrict__ col, const T *__restrict__ val,
-                                                   int64_t nnz, const typename Cx<T>::t *__restrict__ y,
-                                                   typename Cx<T>::t *__restrict__ z) {
+template <typename T, int NCH, int RPW, int CPS>
+__global__ void __launch_bounds__(256, CPS == 1 && NCH <= 3 ? (sizeof(T) == 4 ? 3 : 2) : 1)
+    spmv_kernel(int n_cells, const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                const T *__restrict__ val, int64_t nnz, const typename Cx<T>::t *__restrict__ y,
+                typename Cx<T>::t *__restrict__ z, int vw) {
   using C2 = typename Cx<T>::t;
   constexpr int NPAIR = pair_count(NCH);
   constexpr int LPR = 32 / RPW;
@@ -226,8 +187,8 @@ __global__ void __launch_bounds__(256, CPS == 1 && NCH <= 3 ? (sizeof(T) == 4 ? 
     T v0[NPAIR][4], v1[NPAIR][4];
     const int64_t o1 = o + 4 * LPR;
     const bool second = CPS == 2 && o1 < e;
-    load_chunk<T, NPAIR, VW>(col, val, nnz, o, t0, v0);
-    if (second) load_chunk<T, NPAIR, VW>(col, val, nnz, o1, t1, v1);
+    load_chunk<T, NPAIR>(col, val, nnz, o, t0, v0, vw);
+    if (second) load_chunk<T, NPAIR>(col, val, nnz, o1, t1, v1, vw);
     use_chunk<T, NCH, NPAIR>(y, n_cells, o, b, e, t0, v0, part);
     if (second) use_chunk<T, NCH, NPAIR>(y, n_cells, o1, b, e, t1, v1, part);
     if (++nblk == BLK) {
@@ -263,235 +224,20 @@ __global__ void __launch_bounds__(256, CPS == 1 && NCH <= 3 ? (sizeof(T) == 4 ? 
     }
 }
 
-// ---------------------------------------------------------------------------
-// streaming form
-// ---------------------------------------------------------------------------
-constexpr int SV_NS = 3;                // stages in the ring
-constexpr int SV_STAGE = 32 * 1024;     // bytes of one stage
-constexpr int SV_RMAX = 128;            // rows per block
-constexpr int SV_THREADS = 256;
-
-// stage layout: row pointers [SV_RMAX + 4] int64, columns [cap + 8] int32,
-// values [n_pairs][cap + 8] T, every region 16-byte aligned; cap = the
-// nonzeros a block may hold
-template <typename T, int NCH>
-struct SvLayout {
-  static constexpr int NPAIR = pair_count(NCH);
-  static constexpr int RP_BYTES = (SV_RMAX + 4) * 8;
-  static constexpr int CAP = ((SV_STAGE - RP_BYTES - 16 * (NPAIR + 1)) / (4 + NPAIR * (int)sizeof(T)) - 8) & ~3;
-  static constexpr int COL_BYTES = ((CAP + 8) * 4 + 15) & ~15;
-  static constexpr int VAL_BYTES = ((CAP + 8) * (int)sizeof(T) + 15) & ~15;
-  static_assert(RP_BYTES + COL_BYTES + NPAIR * VAL_BYTES <= SV_STAGE, "stage overflow");
-};
-
-struct SvArgs {
-  const int4 *blocks;  // {r0, r1, big, 0} per block of rows [r0, r1)
-  int n_blocks, n_cells;
-  const int64_t *row_ptr;
-  const int32_t *col;
-  int64_t nnz;
-  int *err;            // wait-limit flag
-};
-
-// issue the copies of block k into stage st (one thread)
-template <typename T, int NCH>
-__device__ __forceinline__ void sv_issue(const SvArgs &a, const T *__restrict__ val, int k, unsigned char *st,
-                                         uint64_t *bar) {
-  using L = SvLayout<T, NCH>;
-  const int4 bk = a.blocks[k];
-  if (bk.z) {  // a long row, summed from global memory: nothing to stage
-    mbar_arrive_plain(bar);
-    return;
-  }
-  const int64_t gs = a.row_ptr[bk.x], ge = a.row_ptr[bk.y];
-  // row pointers r0 .. r1 (inclusive), from the even index at or below r0
-  const int64_t ra = bk.x & ~1;
-  const uint32_t rp_bytes = (uint32_t)(((bk.y + 1 - ra) * 8 + 15) & ~15);
-  const int64_t ca = gs & ~(int64_t)3, ce = (ge + 3) & ~(int64_t)3;
-  const uint32_t c_bytes = (uint32_t)((ce - ca) * 4);
-  constexpr int VE = 16 / sizeof(T);
-  uint32_t v_bytes[L::NPAIR];
-  int64_t va[L::NPAIR];
-  uint32_t total = rp_bytes + c_bytes;
-#pragma unroll
-  for (int m = 0; m < L::NPAIR; ++m) {
-    va[m] = ((int64_t)m * a.nnz + gs) & ~(int64_t)(VE - 1);
-    const int64_t ve = ((int64_t)m * a.nnz + ge + VE - 1) & ~(int64_t)(VE - 1);
-    v_bytes[m] = (uint32_t)((ve - va[m]) * sizeof(T));
-    total += v_bytes[m];
-  }
-  expect_tx_bytes(bar, total);
-  bulk_copy(st, a.row_ptr + ra, rp_bytes, bar);
-  if (c_bytes) bulk_copy(st + L::RP_BYTES, a.col + ca, c_bytes, bar);
-#pragma unroll
-  for (int m = 0; m < L::NPAIR; ++m)
-    if (v_bytes[m]) bulk_copy(st + L::RP_BYTES + L::COL_BYTES + m * L::VAL_BYTES, val + va[m], v_bytes[m], bar);
-}
-
-template <typename T, int NCH, int RPW, int VW>
-__global__ void __launch_bounds__(SV_THREADS, 2) spmv_stream_kernel(SvArgs a, const T *__restrict__ val,
-                                                                   const typename Cx<T>::t *__restrict__ y,
-                                                                   typename Cx<T>::t *__restrict__ z) {
-  using L = SvLayout<T, NCH>;
-  using C2 = typename Cx<T>::t;
-  constexpr int NPAIR = L::NPAIR;
-  constexpr int LPR = 32 / RPW;
-  constexpr int BLK = sizeof(T) == 4 ? 4 : 1 << 30;
-  constexpr int VE = 16 / sizeof(T);
-  extern __shared__ __align__(128) unsigned char sv_sm[];
-  uint64_t *full = reinterpret_cast<uint64_t *>(sv_sm);
-  unsigned char *stages = sv_sm + 128;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nmine = blockIdx.x < a.n_blocks ? (a.n_blocks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  if (tid == 0) {
-    for (int s = 0; s < SV_NS; ++s) mbar_init(&full[s], 1);
-    fence_mbar_init();
-    for (int i = 0; i < SV_NS && i < nmine; ++i)
-      sv_issue<T, NCH>(a, val, blockIdx.x + i * gridDim.x, stages + i * SV_STAGE, &full[i]);
-  }
-  __syncthreads();
-  int consumed = 0;  // blocks whose stage has been waited for
-  for (int i = 0; i < nmine; ++i) {
-    const int s = i % SV_NS;
-    const bool ok = mbar_wait(&full[s], (uint32_t)(i / SV_NS) & 1);
-    if (__syncthreads_or(!ok)) {  // a copy did not arrive: stop here (all threads)
-      if (tid == 0) atomicOr(a.err, 1);
-      break;
-    }
-    consumed = i + 1;
-    const int4 bk = a.blocks[blockIdx.x + i * gridDim.x];
-    const unsigned char *st = stages + s * SV_STAGE;
-    const int64_t *rp = reinterpret_cast<const int64_t *>(st);
-    const int32_t *cb = reinterpret_cast<const int32_t *>(st + L::RP_BYTES);
-    const T *vb = reinterpret_cast<const T *>(st + L::RP_BYTES + L::COL_BYTES);
-    const int64_t ra = bk.x & ~1;
-    const int64_t gs = bk.z ? 0 : rp[bk.x - ra];
-    const int64_t ca = gs & ~(int64_t)3;
-    int64_t vsh[NPAIR];  // stage index of value element o of pair m: o + vsh[m]
-#pragma unroll
-    for (int m = 0; m < NPAIR; ++m)
-      vsh[m] = (int64_t)m * L::VAL_BYTES / (int64_t)sizeof(T) + (int64_t)m * a.nnz -
-               (((int64_t)m * a.nnz + gs) & ~(int64_t)(VE - 1));
-    const int nrows = bk.y - bk.x;
-    const int lpr = bk.z ? 32 : LPR, rpw = 32 / lpr;
-    for (int g = warp; g * rpw < nrows && !(bk.z && warp > 0); g += SV_THREADS / 32) {
-      const int ri = g * rpw + lane / lpr, sub = lane % lpr;
-      const bool active = ri < nrows;
-      const int c = bk.x + ri;
-      int64_t b = 0, e = 0;
-      if (active) {
-        if (bk.z) {
-          b = a.row_ptr[c];
-          e = a.row_ptr[c + 1];
-        } else {
-          b = rp[c - ra];
-          e = rp[c + 1 - ra];
-        }
-      }
-      SvSum<T> acc[NCH][2];
-      T part[NCH][2];
-#pragma unroll
-      for (int l = 0; l < NCH; ++l) part[l][0] = part[l][1] = T(0);
-      int nblk = 0;
-      for (int64_t o = (b & ~(int64_t)3) + 4 * sub; o < e; o += 4 * lpr) {
-        int t[4];
-        T v[NPAIR][4];
-        if (bk.z) {
-          load_chunk<T, NPAIR, VW>(a.col, val, a.nnz, o, t, v);
-        } else {
-          const int4 cc = *reinterpret_cast<const int4 *>(cb + (o - ca));
-          t[0] = cc.x, t[1] = cc.y, t[2] = cc.z, t[3] = cc.w;
-#pragma unroll
-          for (int m = 0; m < NPAIR; ++m) lds4<VW>(vb + o + vsh[m], v[m]);
-        }
-        if (o < b || o + 4 > e) {  // elements outside the row: value 0, column 0
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const bool in = o + k >= b && o + k < e;
-            t[k] = in ? t[k] : 0;
-#pragma unroll
-            for (int m = 0; m < NPAIR; ++m) v[m][k] = in ? v[m][k] : T(0);
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          T yr[NCH], yi[NCH];
-#pragma unroll
-          for (int l = 0; l < NCH; ++l) {
-            const C2 q = __ldg(y + (size_t)l * a.n_cells + t[k]);
-            yr[l] = q.x;
-            yi[l] = q.y;
-          }
-#pragma unroll
-          for (int m = 0; m < NPAIR; ++m) {
-            const int l = pair_first(NCH, m), lp = pair_second(NCH, m);
-            part[l][0] = fma(v[m][k], yr[lp], part[l][0]);
-            part[l][1] = fma(v[m][k], yi[lp], part[l][1]);
-          }
-        }
-        if (++nblk == BLK) {
-          nblk = 0;
-#pragma unroll
-          for (int l = 0; l < NCH; ++l) {
-            acc[l][0].add(part[l][0]);
-            acc[l][1].add(part[l][1]);
-            part[l][0] = part[l][1] = T(0);
-          }
-        }
-      }
-#pragma unroll
-      for (int l = 0; l < NCH; ++l) {
-        acc[l][0].add(part[l][0]);
-        acc[l][1].add(part[l][1]);
-      }
-      for (int off = 1; off < lpr; off <<= 1)
-#pragma unroll
-        for (int l = 0; l < NCH; ++l) {
-          acc[l][0].add_lane(off);
-          acc[l][1].add_lane(off);
-        }
-      if (active && sub == 0)
-#pragma unroll
-        for (int l = 0; l < NCH; ++l) {
-          C2 out;
-          out.x = acc[l][0].value();
-          out.y = acc[l][1].value();
-          z[(size_t)l * a.n_cells + c] = out;
-        }
-    }
-    __syncthreads();  // stage s is free again
-    if (tid == 0 && i + SV_NS < nmine)
-      sv_issue<T, NCH>(a, val, blockIdx.x + (i + SV_NS) * gridDim.x, stages + s * SV_STAGE, &full[s]);
-  }
-  // after an expired wait: let every copy already issued land (bounded)
-  // before the CTA's shared memory goes away
-  if (tid == 0)
-    for (int i = consumed; i < nmine && i < consumed + SV_NS; ++i)
-      (void)mbar_wait(&full[i % SV_NS], (uint32_t)(i / SV_NS) & 1);
-}
-
 template <typename T, int NCH, int RPW, int CPS>
 void launch_vw(int n_cells, const int64_t *row_ptr, const int32_t *col, const T *val, int64_t nnz, const void *y,
                void *z, cudaStream_t s) {
   using C2 = typename Cx<T>::t;
   const int rows_per_cta = 8 * RPW;
   const unsigned grid = (unsigned)((n_cells + rows_per_cta - 1) / rows_per_cta);
-  const C2 *yy = static_cast<const C2 *>(y);
-  C2 *zz = static_cast<C2 *>(z);
-  // widest value load the pair-major layout allows at every pair's offset
-  if (sizeof(T) == 4 && nnz % 4 == 0)
-    spmv_kernel<T, NCH, RPW, 4, CPS><<<grid, 256, 0, s>>>(n_cells, row_ptr, col, val, nnz, yy, zz);
-  else if (nnz % 2 == 0)
-    spmv_kernel<T, NCH, RPW, 2, CPS><<<grid, 256, 0, s>>>(n_cells, row_ptr, col, val, nnz, yy, zz);
-  else
-    spmv_kernel<T, NCH, RPW, 1, CPS><<<grid, 256, 0, s>>>(n_cells, row_ptr, col, val, nnz, yy, zz);
+  spmv_kernel<T, NCH, RPW, CPS><<<grid, 256, 0, s>>>(n_cells, row_ptr, col, val, nnz, static_cast<const C2 *>(y),
+                                                    static_cast<C2 *>(z), value_width<T>(nnz));
 }
 
 template <typename T, int NCH, int CPS>
 void launch_rpw(int rpw, int n_cells, const int64_t *row_ptr, const int32_t *col, const T *val, int64_t nnz,
                 const void *y, void *z, cudaStream_t s) {
   switch (rpw) {
-    case 1: launch_vw<T, NCH, 1, CPS>(n_cells, row_ptr, col, val, nnz, y, z, s); break;
     case 2: launch_vw<T, NCH, 2, CPS>(n_cells, row_ptr, col, val, nnz, y, z, s); break;
     case 4: launch_vw<T, NCH, 4, CPS>(n_cells, row_ptr, col, val, nnz, y, z, s); break;
     case 8: launch_vw<T, NCH, 8, CPS>(n_cells, row_ptr, col, val, nnz, y, z, s); break;
@@ -502,10 +248,13 @@ void launch_rpw(int rpw, int n_cells, const int64_t *row_ptr, const int32_t *col
 template <typename T, int NCH>
 void launch_cps(int cps, int rpw, int n_cells, const int64_t *row_ptr, const int32_t *col, const T *val,
                 int64_t nnz, const void *y, void *z, cudaStream_t s) {
-  if (cps == 2 && NCH <= 3)
-    launch_rpw<T, NCH, 2>(rpw, n_cells, row_ptr, col, val, nnz, y, z, s);
-  else
-    launch_rpw<T, NCH, 1>(rpw, n_cells, row_ptr, col, val, nnz, y, z, s);
+  if constexpr (NCH <= 3) {
+    if (cps == 2) {
+      launch_rpw<T, NCH, 2>(rpw, n_cells, row_ptr, col, val, nnz, y, z, s);
+      return;
+    }
+  }
+  launch_rpw<T, NCH, 1>(rpw, n_cells, row_ptr, col, val, nnz, y, z, s);
 }
 
 template <typename T>
@@ -524,137 +273,15 @@ wpcd_status launch_spmv_t(int n_ch, int rpw, int cps, int n_cells, const int64_t
   return e == cudaSuccess ? WPCD_OK : cuda_error(e, "spmv launch");
 }
 
-template <typename T, int NCH, int RPW>
-cudaError_t sv_launch_vw(const SvArgs &a, const T *val, const void *y, void *z, int grid, cudaStream_t s) {
-  using C2 = typename Cx<T>::t;
-  const size_t smem = 128 + (size_t)SV_NS * SV_STAGE;
-  const C2 *yy = static_cast<const C2 *>(y);
-  C2 *zz = static_cast<C2 *>(z);
-  auto go = [&](auto kern) {
-    // the shared-memory opt-in once per kernel (before any graph capture:
-    // the first launch comes from the autotuner)
-    static bool opted_in = false;
-    if (!opted_in) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      opted_in = true;
-    }
-    kern<<<grid, SV_THREADS, smem, s>>>(a, val, yy, zz);
-    return cudaGetLastError();
-  };
-  if (sizeof(T) == 4 && a.nnz % 4 == 0) return go(spmv_stream_kernel<T, NCH, RPW, 4>);
-  if (a.nnz % 2 == 0) return go(spmv_stream_kernel<T, NCH, RPW, 2>);
-  return go(spmv_stream_kernel<T, NCH, RPW, 1>);
-}
-
-template <typename T, int NCH>
-cudaError_t sv_launch_rpw(int rpw, const SvArgs &a, const T *val, const void *y, void *z, int grid, cudaStream_t s) {
-  switch (rpw) {
-    case 2: return sv_launch_vw<T, NCH, 2>(a, val, y, z, grid, s);
-    case 4: return sv_launch_vw<T, NCH, 4>(a, val, y, z, grid, s);
-    default: return sv_launch_vw<T, NCH, 8>(a, val, y, z, grid, s);
-  }
-}
-
-template <typename T>
-int sv_cap(int n_ch) {
-  switch (n_ch) {
-    case 1: return SvLayout<T, 1>::CAP;
-    case 2: return SvLayout<T, 2>::CAP;
-    case 3: return SvLayout<T, 3>::CAP;
-    case 4: return SvLayout<T, 4>::CAP;
-    default: return SvLayout<T, 5>::CAP;
-  }
-}
-
-// The row blocks of the streaming form for values of type T: consecutive
-// rows, at most SV_RMAX of them and at most the stage's capacity of
-// nonzeros; a row longer than that forms a block of its own, summed from
-// global memory.  Built once per matrix and precision on the host from the
-// row pointers (synchronises the stream on that first call).
-template <typename T>
-wpcd_status sv_plan(const wpcd_problem *pr, wpcd_P *P, cudaStream_t s) {
-  const int idx = sizeof(T) == 8;
-  if (P->sv_blocks[idx]) return WPCD_OK;
-  const int n = pr->N * pr->M;
-  int64_t cap = sv_cap<T>(pr->n_ch);
-  // WPCD_SPMV_CAP lowers the nonzeros per block (tests of the long-row path)
-  if (const char *env = std::getenv("WPCD_SPMV_CAP")) {
-    const long long v = std::atoll(env);
-    if (v >= 4 && v < cap) cap = v;
-  }
-  std::vector<int64_t> rp(n + 1);
-  WPCD_CUDA_TRY(cudaMemcpyAsync(rp.data(), P->row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s));
-  WPCD_CUDA_TRY(cudaStreamSynchronize(s));
-  std::vector<int4> blocks;
-  for (int r = 0; r < n;) {
-    if (rp[r + 1] - rp[r] > cap) {
-      blocks.push_back(make_int4(r, r + 1, 1, 0));
-      ++r;
-      continue;
-    }
-    const int r0 = r;
-    while (r < n && r - r0 < SV_RMAX && rp[r + 1] - rp[r0] <= cap) ++r;
-    blocks.push_back(make_int4(r0, r, 0, 0));
-  }
-  int4 *d = nullptr;
-  WPCD_CUDA_TRY(dev_malloc(&d, sizeof(int4) * blocks.size()));
-  cudaError_t e = cudaMemcpyAsync(d, blocks.data(), sizeof(int4) * blocks.size(), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) {
-    dev_free(d);
-    return cuda_error(e, "SpMV plan upload");
-  }
-  P->sv_blocks[idx] = d;
-  P->sv_nblocks[idx] = (int)blocks.size();
-  return WPCD_OK;
-}
-
-template <typename T>
-wpcd_status launch_stream_t(const wpcd_problem *pr, wpcd_P *P, const T *val, const void *y, void *z, int rpw,
-                            cudaStream_t s) {
-  wpcd_status st = sv_plan<T>(pr, P, s);
-  if (st != WPCD_OK) return st;
-  if (!pr->d.tc_err) return set_error(WPCD_EINVAL, "SpMV: no wait-limit flag");
-  const int idx = sizeof(T) == 8;
-  SvArgs a{P->sv_blocks[idx], P->sv_nblocks[idx], pr->N * pr->M, P->row_ptr, P->col, P->nnz, pr->d.tc_err};
-  int sms = 0;
-  WPCD_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pr->device));
-  const int grid = std::max(1, std::min(a.n_blocks, 2 * sms));  // persistent: two CTAs per SM
-  cudaError_t e;
-  switch (pr->n_ch) {
-    case 1: e = sv_launch_rpw<T, 1>(rpw, a, val, y, z, grid, s); break;
-    case 2: e = sv_launch_rpw<T, 2>(rpw, a, val, y, z, grid, s); break;
-    case 3: e = sv_launch_rpw<T, 3>(rpw, a, val, y, z, grid, s); break;
-    case 4: e = sv_launch_rpw<T, 4>(rpw, a, val, y, z, grid, s); break;
-    case 5: e = sv_launch_rpw<T, 5>(rpw, a, val, y, z, grid, s); break;
-    default: return set_error(WPCD_EINVAL, "SpMV: unsupported channel count");
-  }
-  count_launches(1);
-  return e == cudaSuccess ? WPCD_OK : cuda_error(e, "streaming spmv launch");
-}
-
 }  // namespace
 
-bool spmv_stream_ready(const wpcd_P *P, bool fp64) { return P->sv_blocks[fp64 ? 1 : 0] != nullptr; }
-
-wpcd_status launch_spmv_stream(const wpcd_problem *pr, wpcd_P *P, bool fp64, const void *val, const void *y,
-                               void *z, int rpw, cudaStream_t s) {
-  if (!pr->d.tc_err) {  // the wait-limit flag, shared with the tensor-core kernels
-    WPCD_CUDA_TRY(dev_malloc(const_cast<int **>(&pr->d.tc_err), sizeof(int)));
-    WPCD_CUDA_TRY(cudaMemsetAsync(pr->d.tc_err, 0, sizeof(int), s));
-  }
-  if (fp64) return launch_stream_t<double>(pr, P, static_cast<const double *>(val), y, z, rpw, s);
-  return launch_stream_t<float>(pr, P, static_cast<const float *>(val), y, z, rpw, s);
-}
-
-wpcd_status launch_spmv(const wpcd_problem *pr, const wpcd_P *P, bool fp64, const void *val, const void *y, void *z,
-                        int rpw, int cps, cudaStream_t s) {
+wpcd_status launch_spmv1(const wpcd_problem *pr, const wpcd_P *P, bool fp64, const void *val, const void *y, void *z,
+                         const SpmmConfig &cfg, cudaStream_t s) {
   const int n_cells = pr->N * pr->M;
   if (fp64)
-    return launch_spmv_t<double>(pr->n_ch, rpw, cps, n_cells, P->row_ptr, P->col, static_cast<const double *>(val),
-                                 P->nnz, y, z, s);
-  return launch_spmv_t<float>(pr->n_ch, rpw, cps, n_cells, P->row_ptr, P->col, static_cast<const float *>(val),
+    return launch_spmv_t<double>(pr->n_ch, cfg.rpw, cfg.ept, n_cells, P->row_ptr, P->col,
+                                 static_cast<const double *>(val), P->nnz, y, z, s);
+  return launch_spmv_t<float>(pr->n_ch, cfg.rpw, cfg.ept, n_cells, P->row_ptr, P->col, static_cast<const float *>(val),
                               P->nnz, y, z, s);
 }
 

@@ -155,8 +155,6 @@ struct wpcd_P {
   int *blk_nu = nullptr;                     // row blocks of the row-block SpMM (spmm_blk.cu)
   int32_t *blk_ucol = nullptr;
   uint16_t *blk_lidx = nullptr;
-  int4 *sv_blocks[2] = {nullptr, nullptr};  // row blocks of the streaming SpMV (FP32, FP64 values)
-  int sv_nblocks[2] = {0, 0};
   std::map<int64_t, SpmmConfig> tuned;  // autotuner choices keyed by (B, precision)
 };
 
@@ -188,18 +186,10 @@ bool tc_supported(const wpcd_problem *pr);
 bool tc_enabled();
 wpcd_status tc_prepare(wpcd_problem *pr, cudaStream_t s);
 // spmv.cu: one-right-hand-side SpMV in the vectors' precision (FP32 values
-// and vectors, or FP64 both), rpw rows per warp, cps chunks of four
+// and vectors, or FP64 both): cfg.rpw rows per warp, cfg.ept chunks of four
 // nonzeros per lane and step
-wpcd_status launch_spmv(const wpcd_problem *pr, const wpcd_P *P, bool fp64, const void *val, const void *y, void *z,
-                        int rpw, int cps, cudaStream_t s);
-// the streaming form (row blocks staged by bulk copies); builds the row-block
-// plan on first use (host round trip, allocation); ready: the plan exists
-wpcd_status launch_spmv_stream(const wpcd_problem *pr, wpcd_P *P, bool fp64, const void *val, const void *y,
-                               void *z, int rpw, cudaStream_t s);
-bool spmv_stream_ready(const wpcd_P *P, bool fp64);
-// bytes of padding after every P0 array (row pointers, columns, values):
-// the streaming SpMV's bulk copies round their ends up to 16 bytes
-constexpr size_t kPad = 16;
+wpcd_status launch_spmv1(const wpcd_problem *pr, const wpcd_P *P, bool fp64, const void *val, const void *y, void *z,
+                         const SpmmConfig &cfg, cudaStream_t s);
 // spmm_blk.cu: the row-block FP32 SpMM (shared-memory staging of y)
 wpcd_status spmm_blk_prepare(const wpcd_problem *pr, wpcd_P *P, cudaStream_t s);
 wpcd_status launch_spmm_blk(const wpcd_problem *pr, const wpcd_P *P, const float *vals, const float *y, float *z,

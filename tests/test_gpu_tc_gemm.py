@@ -173,17 +173,15 @@ def test_spmm_matches_oracle_P0(W, orc, B):
         assert np.max(np.abs(got - ref) / np.maximum(mag, 1e-30)) < tol, mode
 
 
-@pytest.mark.parametrize("N,M,rpw,el,cap", [(23, 19, 2, 1, None), (25, 21, 4, 1, None), (21, 17, 8, 1, None),
-                                            (24, 20, 16, 1, None), (27, 23, 2, 2, None), (22, 18, 4, 2, None),
-                                            (28, 24, 8, 2, None), (30, 26, 4, 2, 40)])
-def test_spmv_one_rhs_every_shape(W, orc, tmp_path, monkeypatch, N, M, rpw, el, cap):
+@pytest.mark.parametrize("N,M,rpw,cps", [(23, 19, 2, 1), (25, 21, 4, 2), (21, 17, 8, 1), (24, 20, 16, 2),
+                                          (28, 24, 4, 1), (27, 23, 8, 2)])
+def test_spmv_one_rhs_every_shape(W, orc, tmp_path, monkeypatch, N, M, rpw, cps):
     """The one-right-hand-side SpMV (FP64 and FP32) in every rows-per-warp
-    shape, direct (el = 1) and streaming (el = 2: row blocks staged by bulk
-    copies; with cap, rows longer than cap nonzeros are summed from global
-    memory), forced through the autotuner's cache file, element by element
-    against the oracle's P0 applied with scipy; the lattices give nnz odd
-    (element loads of the values and a chunk at the end of the arrays),
-    nnz = 2 mod 4 (8-byte value loads) and nnz = 0 mod 4."""
+    shape with one and two chunks per step, forced through the autotuner's
+    cache file, element by element against the oracle's P0 applied with
+    scipy; the lattices give nnz odd (element loads of the values and a chunk
+    at the end of the arrays), nnz = 2 mod 4 (8-byte value loads) and
+    nnz = 0 mod 4 (16-byte value loads)."""
     import scipy.sparse as sp
     import torch
     from paper_1508_07441_gb300 import inputs
@@ -193,10 +191,8 @@ def test_spmv_one_rhs_every_shape(W, orc, tmp_path, monkeypatch, N, M, rpw, el, 
     with open(cache, "w") as f:
         for mode in (0, 1):  # FP64 and FP32 vectors, B = 1
             key = ((((n_ch * 4096 + N) * 4096 + M) * 4096 + 1) * 4 + mode)
-            f.write(f"{key} {rpw} {el} 1\n")
+            f.write(f"{key} {rpw} 1 {cps}\n")
     monkeypatch.setenv("WPCD_TUNE_CACHE", str(cache))
-    if cap:
-        monkeypatch.setenv("WPCD_SPMV_CAP", str(cap))
     pe, qe = inputs.tangent_edges(N, 20.0), inputs.tangent_edges(M, 20.0)
     pr = W.Problem(pe, qe, 4, 4, 16, n_ch, (-6.0,), (1.0,))
     P = pr.wpcd_assemble_P(W.WPCD_FP64)
@@ -213,7 +209,7 @@ def test_spmv_one_rhs_every_shape(W, orc, tmp_path, monkeypatch, N, M, rpw, el, 
         yd = torch.from_numpy(y.astype(dt).reshape(-1).view(np.float32 if fp32 else np.float64)).cuda()
         zd = torch.full_like(yd, float("nan"))
         pr.wpcd_spmm(P, yd, zd, 1, mode=W.WPCD_SPMM_FP32 if fp32 else W.WPCD_SPMM_FP64)
-        assert pr.wpcd_tune_spmm(P, 1, fp32=fp32) == (rpw, el, 1)  # the forced shape ran
+        assert pr.wpcd_tune_spmm(P, 1, fp32=fp32) == (rpw, 1, cps)  # the forced shape ran
         got = zd.cpu().numpy().view(dt).astype(np.complex128).reshape(ref.shape)
         assert np.all(np.isfinite(got))
         assert np.max(np.abs(got - ref) / np.maximum(mag, 1e-30)) < tol, (fp32, rpw)
