@@ -297,13 +297,11 @@ wpcd_status wpcd_solve_batch(int n_prob, wpcd_problem *const *problems, const wp
 #define WPCD_SPMM_FF 2   /* FP64 vectors in and out, float-float arithmetic on
                             the FP32 pipe (about 48 significant bits), as in
                             the refinement residual of WPCD_SOLVE_MIXED */
-#define WPCD_SPMM_FP32_BLOCKED 3 /* as WPCD_SPMM_FP32 with the row-block
-                            kernel (blocks of 16 rows, the y rows of their
-                            distinct columns staged in shared memory); an
-                            alternative design kept for comparison: 2.2x
-                            slower than the tuned warp-per-row shapes at 128
-                            energies on the 200 x 200 lattice, so the solves
-                            do not use it */
+#define WPCD_SPMM_FP32_BLOCKED 3 /* as WPCD_SPMM_FP32 with the row-tiled kernel
+                            on tiles of 2 x 2 cells (every column of a tile
+                            gathered once for its four rows; n_rhs even, at
+                            most three channels); the autotuner also weighs
+                            the row-tiled shapes for WPCD_SPMM_FP32 */
 
 /* The sparse step of the K application (Sec. 3.3, Eq. kernel; P0 of
  * Eq. perm): z = P0 y for n_rhs vectors in the batched layout (device
@@ -354,10 +352,16 @@ wpcd_status wpcd_channel_gemm(wpcd_problem *pr, int which, int mode, const void 
  * batch of n_rhs energies in the arithmetic of mode (WPCD_SPMM_FP64,
  * WPCD_SPMM_FP32 or WPCD_SPMM_FF) and keep the fastest for later solves
  * (for every P0 of the same shape in the process); returns the choice.
+ * For WPCD_SPMM_FP32 with an even batch of at least 16 the candidates
+ * include the row-tiled kernel (WPCD_SPMM_FP32_BLOCKED's), reported as
+ * rows_per_warp = 2 or 4 (the cells of a tile) with 32 energy lanes, a pair
+ * the warp-per-row shapes never use.  For one right-hand side the shapes are
+ * those of the one-vector SpMV: rows per warp 2-16, energy lanes 1 and
+ * energies per lane = nonzero chunks per step (1 or 2).
  * Solves tune on first use of a (batch, arithmetic) pair.  With
  * WPCD_TUNE_CACHE set to a file path, choices are also read from /
  * appended to that file (text lines "key rows_per_warp energy_lanes
- * energies_per_lane"). */
+ * energies_per_lane [cells_per_tile]"). */
 wpcd_status wpcd_tune_spmm(wpcd_problem *pr, wpcd_P *P, int n_rhs, int mode, void *stream,
                            int *rows_per_warp, int *energy_lanes, int *energies_per_lane);
 

@@ -409,9 +409,11 @@ void wpcd_P_destroy(wpcd_P *P) {
   dev_free(P->val32_copy);
   dev_free(P->val_h);
   dev_free(P->val_l);
-  dev_free(P->blk_nu);
-  dev_free(P->blk_ucol);
-  dev_free(P->blk_lidx);
+  for (int i = 0; i < 2; ++i) {
+    dev_free(P->tile_ptr[i]);
+    dev_free(P->tile_col[i]);
+    dev_free(P->tile_val[i]);
+  }
   delete P;
 }
 
@@ -539,7 +541,7 @@ wpcd_status wpcd_tune_spmm(wpcd_problem *pr, wpcd_P *P, int n_rhs, int mode, voi
   SpmmConfig c;
   wpcd_status st = tune_spmm(pr, P, n_rhs, mode, s, &c);
   if (st != WPCD_OK) return st;
-  if (rows_per_warp) *rows_per_warp = c.rpw;
+  if (rows_per_warp) *rows_per_warp = c.tile ? c.tile : c.rpw;  // a tile's rows per warp
   if (energy_lanes) *energy_lanes = c.el;
   if (energies_per_lane) *energies_per_lane = c.ept;
   return WPCD_OK;

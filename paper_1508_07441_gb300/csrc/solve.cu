@@ -735,6 +735,13 @@ wpcd_status launch_spmm_cfg(const wpcd_problem *pr, const wpcd_P *P, const VT *v
   // one right-hand side with values in the vectors' precision: the SpMV of
   // spmv.cu (cfg.rpw rows per warp, cfg.ept chunks per step)
   if (B == 1 && sizeof(VT) == sizeof(T)) return launch_spmv1(pr, P, sizeof(T) == 8, val, y, z, cfg, s);
+  // the row-tiled FP32 SpMM (spmm_tile.cu)
+  if (cfg.tile) {
+    if constexpr (sizeof(T) == 4 && sizeof(VT) == 4)
+      return launch_spmm_tile(pr, const_cast<wpcd_P *>(P), reinterpret_cast<const float *>(val),
+                              reinterpret_cast<const float *>(y), reinterpret_cast<float *>(z), B, cfg, s);
+    return set_error(WPCD_EINVAL, "tile SpMM: FP32 values and vectors only");
+  }
   SpmmParams S{};
   S.n_cells = pr->N * pr->M;
   S.B = B;
@@ -818,8 +825,13 @@ bool load_cached(int64_t key, SpmmConfig *out) {
     // a shape the kernels can run: rows per warp and energy lanes powers of
     // two sharing the 32 lanes, 1, 2 or 4 energies per lane; others ignored
     const auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
-    if (is >> k >> c.rpw >> c.el >> c.ept && k == key && pow2(c.rpw) && pow2(c.el) && c.rpw * c.el <= 32 &&
+    // an optional fifth field: cells per tile of the row-tiled SpMM (2 or 4)
+    if (is >> k >> c.rpw >> c.el >> c.ept && k == key && pow2(c.rpw) && pow2(c.el) && c.rpw * c.el <= 64 &&
         (c.ept == 1 || c.ept == 2 || c.ept == 4)) {
+      if (!(is >> c.tile)) c.tile = 0;
+      if (c.tile == 0 ? c.rpw * c.el > 32
+                      : !((c.tile == 2 && (c.ept == 2 || c.ept == 4)) || (c.tile == 4 && c.ept == 2)) || c.rpw > 2)
+        continue;
       *out = c;
       found = true;
     }
@@ -831,7 +843,7 @@ void store_cached(int64_t key, const SpmmConfig &c) {
   const char *path = std::getenv("WPCD_TUNE_CACHE");
   if (!path || !*path) return;
   std::ofstream f(path, std::ios::app);
-  f << (long long)key << " " << c.rpw << " " << c.el << " " << c.ept << "\n";
+  f << (long long)key << " " << c.rpw << " " << c.el << " " << c.ept << " " << c.tile << "\n";
 }
 
 }  // namespace
@@ -864,7 +876,11 @@ wpcd_status tune_spmm(const wpcd_problem *pr, wpcd_P *P, int B, int mode, cudaSt
   }
   if (fp32 && !P->val32 && !P->val32_copy) return set_error(WPCD_EINVAL, "no FP32 values to tune on");
   if (ff && P->prec == WPCD_FP64 && !P->val_h) return set_error(WPCD_EINVAL, "no float-float values to tune on");
-  const std::vector<SpmmConfig> cands = candidates(B);
+  std::vector<SpmmConfig> cands = candidates(B);
+  if (fp32 && B >= 16 && tile_supported(pr, B))  // the row-tiled SpMM: 2-cell tiles (4 or 2 energies per lane), 2 x 2
+    for (int fab : {1, 2})  // rpw: plain blocks of 32 (1) or 64 (2) columns
+      for (const SpmmConfig &c : {SpmmConfig{fab, 32, 4, 2}, SpmmConfig{fab, 32, 2, 2}, SpmmConfig{fab, 32, 2, 4}})
+        cands.push_back(c);
   const size_t dim = (size_t)pr->n_ch * pr->N * pr->M;
   void *y = nullptr, *z = nullptr;
   // float-float vectors: hi and lo float arrays, the size of one FP64 vector
@@ -906,8 +922,8 @@ wpcd_status tune_spmm(const wpcd_problem *pr, wpcd_P *P, int B, int mode, cudaSt
     }
     if (st != WPCD_OK) break;
     if (std::getenv("WPCD_TUNE_LOG"))
-      std::fprintf(stderr, "wpcd tune B=%d mode=%d rpw=%d el=%d ept=%d: %.4f ms\n", B, mode, c.rpw, c.el, c.ept,
-                   tmin);
+      std::fprintf(stderr, "wpcd tune B=%d mode=%d rpw=%d el=%d ept=%d tile=%d: %.4f ms\n", B, mode, c.rpw, c.el,
+                   c.ept, c.tile, tmin);
     if (tmin < best) {
       best = tmin;
       pick = c;
@@ -1566,6 +1582,10 @@ wpcd_status solve_mixed(const wpcd_problem *pr, const wpcd_P *P, const wpcd_solv
   {
     SpmmConfig c;
     wpcd_status st = tune_spmm(pr, const_cast<wpcd_P *>(P), B, 1, s, &c);
+    // a row-tiled choice (possibly from the tuning cache) builds its tile
+    // structure here, outside the capture
+    if (st == WPCD_OK && c.tile)
+      st = tile_prepare(pr, const_cast<wpcd_P *>(P), P->val32 ? P->val32 : P->val32_copy, c.tile, s);
     if (st == WPCD_OK) st = tune_spmm(pr, const_cast<wpcd_P *>(P), B, 0, s, &c);
     if (st != WPCD_OK) {
       pool_free(d_bet0, s);
@@ -2029,17 +2049,21 @@ wpcd_status spmm_apply(wpcd_problem *pr, wpcd_P *P, int mode, const void *y, voi
     d2f_kernel<<<grid_for(nv, 256), 256, 0, s>>>(nv, P->val64, P->val32_copy);
     count_launches(1);
   }
-  if (mode == WPCD_SPMM_FP32_BLOCKED) {
-    wpcd_status st = spmm_blk_prepare(pr, P, s);
+  if (mode == WPCD_SPMM_FP32_BLOCKED) {  // the row-tiled kernel, 2 x 2 tiles (built before the timed launch)
+    if (!tile_supported(pr, n_rhs)) return set_error(WPCD_EINVAL, "tiled SpMM: even n_rhs and up to three channels");
+    const float *v32 = P->val32 ? P->val32 : P->val32_copy;
+    const SpmmConfig cfg{1, 32, 2, 4};
+    wpcd_status st = launch_spmm_tile(pr, P, v32, (const float *)y, (float *)z, n_rhs, cfg, s);
     if (st != WPCD_OK) return st;
     LaunchTimer t(ms, s);
     t.start();
-    st = launch_spmm_blk(pr, P, P->val32 ? P->val32 : P->val32_copy, (const float *)y, (float *)z, n_rhs, s);
+    st = launch_spmm_tile(pr, P, v32, (const float *)y, (float *)z, n_rhs, cfg, s);
     t.stop();
     return st;
   }
   SpmmConfig cfg;  // tune (which synchronises) before any timed launch
   wpcd_status st = tune_spmm(pr, P, n_rhs, fp32 ? 1 : 0, s, &cfg);
+  if (st == WPCD_OK && cfg.tile) st = tile_prepare(pr, P, P->val32 ? P->val32 : P->val32_copy, cfg.tile, s);
   if (st != WPCD_OK) return st;
   LaunchTimer t(ms, s);
   t.start();

@@ -125,9 +125,10 @@ struct wpcd_problem {
 };
 
 // SpMM launch shape chosen by the autotuner: rows per warp, energy lanes per
-// row, energies per lane (RHS tile = el * ept)
+// row, energies per lane (RHS tile = el * ept); tile > 0: the row-tiled FP32
+// SpMM (spmm_tile.cu) with tiles of `tile` cells and ept energies per lane
 struct SpmmConfig {
-  int rpw = 1, el = 1, ept = 1;
+  int rpw = 1, el = 1, ept = 1, tile = 0;
 };
 
 namespace wpcd {
@@ -152,9 +153,10 @@ struct wpcd_P {
   float ms_phase[3] = {0.f, 0.f, 0.f};  // count, scan, fill
   float *val32_copy = nullptr;          // FP32 values made from FP64 ones (mixed solve)
   float *val_h = nullptr, *val_l = nullptr;  // float-float split of FP64 values (df.cu)
-  int *blk_nu = nullptr;                     // row blocks of the row-block SpMM (spmm_blk.cu)
-  int32_t *blk_ucol = nullptr;
-  uint16_t *blk_lidx = nullptr;
+  int64_t *tile_ptr[2] = {nullptr, nullptr};  // row tiles of 2 / 4 cells (spmm_tile.cu): offsets,
+  int32_t *tile_col[2] = {nullptr, nullptr};  // merged columns,
+  float *tile_val[2] = {nullptr, nullptr};    // per-column value blocks (FP32)
+  int64_t tile_n[2] = {0, 0};
   std::map<int64_t, SpmmConfig> tuned;  // autotuner choices keyed by (B, precision)
 };
 
@@ -190,10 +192,12 @@ wpcd_status tc_prepare(wpcd_problem *pr, cudaStream_t s);
 // nonzeros per lane and step
 wpcd_status launch_spmv1(const wpcd_problem *pr, const wpcd_P *P, bool fp64, const void *val, const void *y, void *z,
                          const SpmmConfig &cfg, cudaStream_t s);
-// spmm_blk.cu: the row-block FP32 SpMM (shared-memory staging of y)
-wpcd_status spmm_blk_prepare(const wpcd_problem *pr, wpcd_P *P, cudaStream_t s);
-wpcd_status launch_spmm_blk(const wpcd_problem *pr, const wpcd_P *P, const float *vals, const float *y, float *z,
-                            int B, cudaStream_t s);
+// spmm_tile.cu: the row-tiled FP32 SpMM (tiles of 2 or 4 cells; the tile
+// structure built on first use, which synchronises the stream)
+bool tile_supported(const wpcd_problem *pr, int B);
+wpcd_status tile_prepare(const wpcd_problem *pr, wpcd_P *P, const float *v32, int tile, cudaStream_t s);
+wpcd_status launch_spmm_tile(const wpcd_problem *pr, wpcd_P *P, const float *v32, const float *y, float *z, int B,
+                             const SpmmConfig &cfg, cudaStream_t s);
 // one problem of a grouped tensor-core product: its vectors are the segment
 // at float offset off of the group vectors, [n_ch][N][ncol] floats
 struct TcGroupProb {

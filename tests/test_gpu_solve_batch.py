@@ -154,7 +154,8 @@ def test_autotuner(W, sys3, tmp_path, monkeypatch):
     for B in (1, 3, 8, 64):
         for mode, P in ((W.WPCD_SPMM_FP64, P64), (W.WPCD_SPMM_FP32, P32), (W.WPCD_SPMM_FF, P64)):
             rpw, el, ept = pr.wpcd_tune_spmm(P, B, mode=mode)
-            assert rpw * el <= 32 and 32 % (rpw * el) == 0
+            tiled = mode == W.WPCD_SPMM_FP32 and el == 32 and rpw in (2, 4)  # the row-tiled kernel
+            assert tiled or (rpw * el <= 32 and 32 % (rpw * el) == 0)
             assert ept in (1, 2, 4)
             if B == 1:
                 assert el == 1

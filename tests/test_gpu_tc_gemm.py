@@ -158,9 +158,11 @@ def test_spmm_matches_oracle_P0(W, orc, B):
     # the terms of the longest row (nonzero cells x channel pairs)
     n_terms = int(np.max(np.diff(ref_P["row_ptr"]))) * len(orc.pair_list(n_ch))
     tol32 = max(3e-6, n_terms * 2.0**-24)
-    for mode, dt, tol in ((W.WPCD_SPMM_FP64, np.complex128, 1e-9), (W.WPCD_SPMM_FF, np.complex128, 1e-9),
-                          (W.WPCD_SPMM_FP32, np.complex64, tol32),
-                          (W.WPCD_SPMM_FP32_BLOCKED, np.complex64, tol32)):
+    modes = [(W.WPCD_SPMM_FP64, np.complex128, 1e-9), (W.WPCD_SPMM_FF, np.complex128, 1e-9),
+             (W.WPCD_SPMM_FP32, np.complex64, tol32)]
+    if B % 2 == 0:  # the row-tiled kernel takes even batches
+        modes.append((W.WPCD_SPMM_FP32_BLOCKED, np.complex64, tol32))
+    for mode, dt, tol in modes:
         fp32 = mode in (W.WPCD_SPMM_FP32, W.WPCD_SPMM_FP32_BLOCKED)
         yd = torch.from_numpy(y.astype(dt).reshape(-1).view(np.float32 if fp32 else np.float64)).cuda()
         zd = torch.full_like(yd, float("nan"))
@@ -213,3 +215,42 @@ def test_spmv_one_rhs_every_shape(W, orc, tmp_path, monkeypatch, N, M, rpw, cps)
         got = zd.cpu().numpy().view(dt).astype(np.complex128).reshape(ref.shape)
         assert np.all(np.isfinite(got))
         assert np.max(np.abs(got - ref) / np.maximum(mag, 1e-30)) < tol, (fp32, rpw)
+
+
+@pytest.mark.parametrize("N,M,B,tile,ept,fab", [(19, 23, 6, 2, 4, 1), (20, 17, 40, 2, 2, 2), (17, 21, 130, 4, 2, 1),
+                                               (22, 19, 128, 2, 4, 2), (18, 25, 64, 4, 2, 2), (21, 20, 2, 2, 2, 1)])
+def test_spmm_tiled_every_shape(W, orc, tmp_path, monkeypatch, N, M, B, tile, ept, fab):
+    """The row-tiled FP32 SpMM (tiles of 2 cells with 4 or 2 energies per
+    lane, of 2 x 2 cells with 2; plain blocks of 32 (fab 1) or 64 (fab 2)
+    columns), forced through the autotuner's cache file,
+    element by element against the oracle's P0 applied with scipy; odd
+    lattice sizes give tiles cut by the lattice edge, and batches of 6, 40,
+    130 leave lanes without energies."""
+    import scipy.sparse as sp
+    import torch
+    from paper_1508_07441_gb300 import inputs
+
+    n_ch = 3
+    cache = tmp_path / "tune.txt"
+    key = ((((n_ch * 4096 + N) * 4096 + M) * 4096 + B) * 4 + 1)
+    cache.write_text(f"{key} {fab} 32 {ept} {tile}\n")
+    monkeypatch.setenv("WPCD_TUNE_CACHE", str(cache))
+    pe, qe = inputs.tangent_edges(N, 20.0), inputs.tangent_edges(M, 20.0)
+    pr = W.Problem(pe, qe, 4, 4, 16, n_ch, (-6.0,), (1.0,))
+    P = pr.wpcd_assemble_P(W.WPCD_FP64)
+    ref_P = orc.P0(pe, qe, 4, 4, 16, n_ch)
+    n_cells = N * M
+    y = inputs.random_complex(n_ch * n_cells * B, 900 + B).reshape(n_ch, n_cells, B)
+    ref, mag = np.zeros_like(y), np.zeros(y.shape)
+    for m, (l, lp) in enumerate(orc.pair_list(n_ch)):
+        A = sp.csr_matrix((ref_P["val"][:, m], ref_P["col"], ref_P["row_ptr"]), shape=(n_cells, n_cells))
+        ref[l] += A @ y[lp]
+        mag[l] += abs(A) @ np.abs(y[lp])
+    n_terms = int(np.max(np.diff(ref_P["row_ptr"]))) * len(orc.pair_list(n_ch))
+    yd = torch.from_numpy(y.astype(np.complex64).reshape(-1).view(np.float32)).cuda()
+    zd = torch.full_like(yd, float("nan"))
+    pr.wpcd_spmm(P, yd, zd, B, mode=W.WPCD_SPMM_FP32)
+    assert pr.wpcd_tune_spmm(P, B, fp32=True) == (tile, 32, ept)  # the forced shape ran
+    got = zd.cpu().numpy().view(np.complex64).astype(np.complex128).reshape(ref.shape)
+    assert np.all(np.isfinite(got))
+    assert np.max(np.abs(got - ref) / np.maximum(mag, 1e-30)) < max(3e-6, n_terms * 2.0**-24)
