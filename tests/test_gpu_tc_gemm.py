@@ -176,7 +176,7 @@ def test_spmm_matches_oracle_P0(W, orc, B):
 
 
 @pytest.mark.parametrize("N,M,rpw,cps", [(23, 19, 2, 1), (25, 21, 4, 2), (21, 17, 8, 1), (24, 20, 16, 2),
-                                          (28, 24, 4, 1), (27, 23, 8, 2)])
+                                          (31, 27, 4, 1), (27, 23, 8, 2)])
 def test_spmv_one_rhs_every_shape(W, orc, tmp_path, monkeypatch, N, M, rpw, cps):
     """The one-right-hand-side SpMV (FP64 and FP32) in every rows-per-warp
     shape with one and two chunks per step, forced through the autotuner's
