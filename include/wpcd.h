@@ -126,13 +126,56 @@ typedef struct {
 
 typedef struct wpcd_problem wpcd_problem;
 typedef struct wpcd_P wpcd_P;
+typedef struct wpcd_grid wpcd_grid;
+
+/* The packet lattice alone (all pointers host, read during
+ * wpcd_grid_create only). */
+typedef struct {
+  int N, M;               /* number of p-bins and q-bins */
+  const double *p_edges;  /* N + 1 strictly increasing, p_edges[0] = 0 */
+  const double *q_edges;  /* M + 1 strictly increasing, q_edges[0] = 0 */
+  int n_p, n_q, n_x;      /* GL nodes per p-bin, per q-bin, and in y on [-1, 1] */
+  int device;             /* CUDA device ordinal */
+} wpcd_grid_desc;
+
+/* The pair interaction on a grid (pointers host, read during
+ * wpcd_pair_create only). */
+typedef struct {
+  int n_ch;               /* channels l = 0 .. n_ch - 1 (1 <= n_ch <= 5) */
+  int n_terms;            /* Gaussian terms of V(r) */
+  const double *V;        /* strengths V_k */
+  const double *a;        /* ranges a_k > 0 (V_k exp(-r^2 / a_k)) */
+  int n_pair_nodes;       /* GL nodes per bin for the pair double integrals */
+} wpcd_pair_desc;
+
+/* Step 1, the lattice (Sec. 2.2 Eq. ip, Sec. 2.4 Eq. xij): the p and q
+ * packet bins with their GL node and weight tables, squared edges and cell
+ * norms, uploaded to the device.  This is all that P0 depends on: P0 is
+ * computed once per lattice and serves every potential and every energy
+ * (Sec. 3.3).  EINVAL for sizes or edges as in wpcd_problem_create. */
+wpcd_status wpcd_grid_create(const wpcd_grid_desc *desc, wpcd_grid **out);
+/* Releases the caller's reference: problems and P0 matrices made on the grid
+ * keep it alive until they are destroyed. */
+void wpcd_grid_destroy(wpcd_grid *g);
+
+/* Step 1, the pair part (Sec. 3.3 "processing of the input data"; Sec. 2.2
+ * Eq. vpot and Eq. exp_z) on a grid: potential matrices v_l on the grid's p
+ * bins, diagonalisation of h1 in every channel (O, eps), Vt = v O^T.  The
+ * result is a problem (grid + pair) usable with every call that takes one;
+ * it holds a reference to the grid.  ENOBOUND if channel 0 has no bound pair
+ * state. */
+wpcd_status wpcd_pair_create(wpcd_grid *g, const wpcd_pair_desc *desc, wpcd_problem **out);
+
+/* The grid of a problem (a new reference: release it with wpcd_grid_destroy). */
+wpcd_status wpcd_problem_grid(const wpcd_problem *pr, wpcd_grid **out);
 
 /* Step 1 (Sec. 3.3, "processing of the input data"; Sec. 2.2 Eq. vpot and
- * Eq. exp_z): free-packet potential matrices v_l, diagonalisation of
- * h1 = h0 + v in every channel (rotation matrices O, energies eps),
- * Vt = O^T V1 = v O^T, node and edge tables, all uploaded to the device.
- * Runs on the host in FP64 (the paper calls this step negligible).
- * ENOBOUND if channel 0 has no bound pair state. */
+ * Eq. exp_z) in one call: a grid of its own (wpcd_grid_create) and the pair
+ * setup on it (wpcd_pair_create): free-packet potential matrices v_l,
+ * diagonalisation of h1 = h0 + v in every channel (rotation matrices O,
+ * energies eps), Vt = O^T V1 = v O^T, node and edge tables, all uploaded to
+ * the device.  Runs on the host in FP64 (the paper calls this step
+ * negligible).  ENOBOUND if channel 0 has no bound pair state. */
 wpcd_status wpcd_problem_create(const wpcd_problem_desc *desc, wpcd_problem **out);
 void wpcd_problem_destroy(wpcd_problem *pr);
 
@@ -155,8 +198,18 @@ wpcd_status wpcd_problem_pair(const wpcd_problem *pr, int l, double *eps, double
  * prec = WPCD_FP64 or WPCD_FP32C.  Two passes (count, then fill) with no
  * atomics: the result is bit-reproducible for a given device.
  * Runs on `stream` and returns when the assembly has completed (the stream
- * is synchronised twice: for the nonzero count, and at the end). */
+ * is synchronised twice: for the nonzero count, and at the end).  The P0
+ * belongs to the problem's grid and channel count (see wpcd_assemble_P_grid):
+ * every problem on that grid with that many channels can use it. */
 wpcd_status wpcd_assemble_P(wpcd_problem *pr, int prec, void *stream, wpcd_P **out);
+
+/* Step 2 on a grid alone: P0 for channels l = 0 .. n_ch - 1 (1 <= n_ch <= 5)
+ * as in wpcd_assemble_P.  P0 depends on the lattice only, not on the
+ * potential or the energy (Sec. 3.3: computed once, then used for many
+ * energies); the calls that take (problem, P) accept it for every problem
+ * made on this grid (wpcd_pair_create) with n_ch channels, EINVAL for
+ * another grid or channel count.  The P0 holds a reference to the grid. */
+wpcd_status wpcd_assemble_P_grid(wpcd_grid *g, int n_ch, int prec, void *stream, wpcd_P **out);
 void wpcd_P_destroy(wpcd_P *P);
 
 /* nnz (cell pairs), n_pairs, prec, and the timing of the last assembly in

@@ -528,38 +528,39 @@ wpcd_status dispatch_fill(const AsmParams &P, int n_cells, size_t smem, cudaStre
 
 }  // namespace
 
-wpcd_status assemble(wpcd_problem *pr, int prec, cudaStream_t s, wpcd_P **out) {
+wpcd_status assemble(wpcd_grid *g, int n_ch, int prec, cudaStream_t s, wpcd_P **out) {
   if (prec != WPCD_FP64 && prec != WPCD_FP32C) return set_error(WPCD_EINVAL, "prec must be WPCD_FP64 or WPCD_FP32C");
-  WPCD_CUDA_TRY(cudaSetDevice(pr->device));
+  if (n_ch < 1 || n_ch > 5) return set_error(WPCD_EINVAL, "n_ch must be in [1, 5]");
+  WPCD_CUDA_TRY(cudaSetDevice(g->device));
   AsmParams P{};
-  P.N = pr->N;
-  P.M = pr->M;
-  P.n_p = pr->n_p;
-  P.n_q = pr->n_q;
-  P.n_x = pr->n_x;
-  P.n_nodes = pr->n_p * pr->n_q * pr->n_x;
+  P.N = g->N;
+  P.M = g->M;
+  P.n_p = g->n_p;
+  P.n_q = g->n_q;
+  P.n_x = g->n_x;
+  P.n_nodes = g->n_p * g->n_q * g->n_x;
   int np2 = kThreads;
   while (np2 < P.n_nodes) np2 *= 2;
   P.np2 = np2;
   int nbits = 0;
   while ((1 << nbits) < np2) ++nbits;
   P.nbits = nbits;
-  P.n_ch = pr->n_ch;
-  P.n_pairs = pr->n_pairs;
-  for (int m = 0; m < pr->n_pairs; ++m) {
-    P.pl[m] = pr->pair_l[m];
-    P.plp[m] = pr->pair_lp[m];
+  P.n_ch = n_ch;
+  P.n_pairs = pair_count(n_ch);
+  for (int m = 0; m < P.n_pairs; ++m) {
+    P.pl[m] = pair_first(n_ch, m);
+    P.plp[m] = pair_second(n_ch, m);
     P.cnorm[m] = sqrt((2.0 * P.pl[m] + 1.0) * (2.0 * P.plp[m] + 1.0));
   }
-  P.pe2 = pr->d.pe2;
-  P.qe2 = pr->d.qe2;
-  P.pn = pr->d.pn;
-  P.wp = pr->d.wp;
-  P.qn = pr->d.qn;
-  P.wq = pr->d.wq;
-  P.yn = pr->d.yn;
-  P.wy = pr->d.wy;
-  P.rsb = pr->d.rsb;
+  P.pe2 = g->pe2;
+  P.qe2 = g->qe2;
+  P.pn = g->pn;
+  P.wp = g->wp;
+  P.qn = g->qn;
+  P.wq = g->wq;
+  P.yn = g->yn;
+  P.wy = g->wy;
+  P.rsb = g->rsb;
   const int n_cells = P.N * P.M;
   if (np2 > 8192) return set_error(WPCD_EINVAL, "too many quadrature nodes per cell (max 8192)");
   if ((int64_t)n_cells << nbits >= (int64_t)1 << 32)
@@ -573,9 +574,11 @@ wpcd_status assemble(wpcd_problem *pr, int prec, cudaStream_t s, wpcd_P **out) {
   int64_t *counts = nullptr;
   uint32_t *sorted = nullptr;
   wpcd_P *Pm = new wpcd_P();
-  Pm->pr = pr;
+  Pm->grid = g;
+  Pm->device = g->device;
+  Pm->n_ch = n_ch;
   Pm->prec = prec;
-  Pm->n_pairs = pr->n_pairs;
+  Pm->n_pairs = P.n_pairs;
   auto fail = [&](wpcd_status st) {
     dev_free(counts);
     dev_free(sorted);
@@ -642,6 +645,7 @@ wpcd_status assemble(wpcd_problem *pr, int prec, cudaStream_t s, wpcd_P **out) {
   cudaEventDestroy(ev1);
   cudaEventDestroy(evc);
   cudaEventDestroy(evs);
+  grid_retain(g);  // P0 keeps its lattice alive
   *out = Pm;
   return WPCD_OK;
 }

@@ -144,7 +144,8 @@ void pool_free(void *p, cudaStream_t s) {
 }
 
 static void free_tables(DeviceTables &d) {
-  double **all[] = {&d.pe2, &d.qe2, &d.pn, &d.wp, &d.qn, &d.wq, &d.yn, &d.wy, &d.rsb, &d.qe, &d.eps, &d.O, &d.Vt};
+  // the lattice tables (pe2 ... qe) belong to the grid: not freed here
+  double **all[] = {&d.eps, &d.O, &d.Vt};
   for (double **p : all) {
     dev_free(*p);
     *p = nullptr;
@@ -198,19 +199,33 @@ static bool valid_edges(const double *e, int n) {
   return true;
 }
 
-static wpcd_status create(const wpcd_problem_desc *d, wpcd_problem **out) {
+static void free_grid_tables(wpcd_grid &g) {
+  double **all[] = {&g.pe2, &g.qe2, &g.pn, &g.wp, &g.qn, &g.wq, &g.yn, &g.wy, &g.rsb, &g.qe_d};
+  for (double **p : all) {
+    dev_free(*p);
+    *p = nullptr;
+  }
+}
+
+void grid_retain(wpcd_grid *g) { g->refs.fetch_add(1, std::memory_order_relaxed); }
+
+void grid_release(wpcd_grid *g) {
+  if (!g || g->refs.fetch_sub(1, std::memory_order_acq_rel) != 1) return;
+  cudaSetDevice(g->device);
+  free_grid_tables(*g);
+  delete g;
+}
+
+// Step 1, the lattice part (Sec. 2.2 Eq. ip, Sec. 2.4 Eq. xij): edges, the
+// GL node and weight tables of every bin, squared edges and the cell norms
+// 1/sqrt(B_i Bq_j), uploaded once; everything P0 needs
+static wpcd_status grid_create(const wpcd_grid_desc *d, wpcd_grid **out) {
   if (!d || !out) return set_error(WPCD_EINVAL, "null argument");
   *out = nullptr;
   if (d->N < 1 || d->M < 1) return set_error(WPCD_EINVAL, "N and M must be >= 1");
   if ((int64_t)d->N * d->M > (1 << 24)) return set_error(WPCD_EINVAL, "lattice too large (N*M > 2^24)");
   if (d->n_p < 1 || d->n_q < 1 || d->n_x < 1 || d->n_p > 64 || d->n_q > 64 || d->n_x > 256)
     return set_error(WPCD_EINVAL, "node counts must be in [1, 64] (p, q) and [1, 256] (x)");
-  if (d->n_ch < 1 || d->n_ch > 5) return set_error(WPCD_EINVAL, "n_ch must be in [1, 5]");
-  if (d->n_terms < 1 || !d->V || !d->a) return set_error(WPCD_EINVAL, "potential needs >= 1 term");
-  for (int k = 0; k < d->n_terms; ++k)
-    if (!std::isfinite(d->V[k]) || !(d->a[k] > 0.0) || !std::isfinite(d->a[k]))
-      return set_error(WPCD_EINVAL, "potential terms must be finite with a_k > 0");
-  if (d->n_pair_nodes < 1 || d->n_pair_nodes > 64) return set_error(WPCD_EINVAL, "n_pair_nodes in [1, 64]");
   if (!valid_edges(d->p_edges, d->N) || !valid_edges(d->q_edges, d->M))
     return set_error(WPCD_EINVAL, "edges must start at 0 and increase strictly");
   int ndev = 0;
@@ -219,15 +234,88 @@ static wpcd_status create(const wpcd_problem_desc *d, wpcd_problem **out) {
   if (d->device < 0 || d->device >= ndev) return set_error(WPCD_EINVAL, "no such CUDA device");
   ce = cudaSetDevice(d->device);
   if (ce != cudaSuccess) return cuda_error(ce, "cudaSetDevice");
+  wpcd_grid *g = new (std::nothrow) wpcd_grid();
+  if (!g) return set_error(WPCD_ENOMEM, "host allocation");
+  g->device = d->device;
+  g->N = d->N;
+  g->M = d->M;
+  g->n_p = d->n_p;
+  g->n_q = d->n_q;
+  g->n_x = d->n_x;
+  g->pe.assign(d->p_edges, d->p_edges + d->N + 1);
+  g->qe.assign(d->q_edges, d->q_edges + d->M + 1);
+  const int N = d->N, M = d->M;
+  // node and edge tables (canonical node placement: mid + half * t)
+  std::vector<double> tp(d->n_p), wp(d->n_p), tq(d->n_q), wq(d->n_q), ty(d->n_x), wy(d->n_x);
+  gauss_legendre(d->n_p, tp.data(), wp.data());
+  gauss_legendre(d->n_q, tq.data(), wq.data());
+  gauss_legendre(d->n_x, ty.data(), wy.data());
+  std::vector<double> pn((size_t)N * d->n_p), pw((size_t)N * d->n_p), qn((size_t)M * d->n_q),
+      qw((size_t)M * d->n_q), pe2(N + 1), qe2(M + 1), rsb((size_t)N * M);
+  for (int i = 0; i < N; ++i) {
+    double lo = g->pe[i], hi = g->pe[i + 1], half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
+    for (int a = 0; a < d->n_p; ++a) {
+      double p = mid + half * tp[a];
+      pn[(size_t)i * d->n_p + a] = p;
+      pw[(size_t)i * d->n_p + a] = half * wp[a] * p * p;
+    }
+  }
+  for (int j = 0; j < M; ++j) {
+    double lo = g->qe[j], hi = g->qe[j + 1], half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
+    for (int b = 0; b < d->n_q; ++b) {
+      double q = mid + half * tq[b];
+      qn[(size_t)j * d->n_q + b] = q;
+      qw[(size_t)j * d->n_q + b] = half * wq[b] * q * q;
+    }
+  }
+  for (int k = 0; k <= N; ++k) pe2[k] = g->pe[k] * g->pe[k];
+  for (int k = 0; k <= M; ++k) qe2[k] = g->qe[k] * g->qe[k];
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < M; ++j)
+      rsb[(size_t)i * M + j] = 1.0 / std::sqrt(shell_volume(g->pe[i], g->pe[i + 1]) *
+                                               shell_volume(g->qe[j], g->qe[j + 1]));
+  wpcd_status st = WPCD_OK;
+  if ((st = upload(&g->pe2, pe2)) || (st = upload(&g->qe2, qe2)) || (st = upload(&g->pn, pn)) ||
+      (st = upload(&g->wp, pw)) || (st = upload(&g->qn, qn)) || (st = upload(&g->wq, qw)) ||
+      (st = upload(&g->yn, ty)) || (st = upload(&g->wy, wy)) || (st = upload(&g->rsb, rsb)) ||
+      (st = upload(&g->qe_d, g->qe))) {
+    free_grid_tables(*g);
+    delete g;
+    return st;
+  }
+  *out = g;
+  return WPCD_OK;
+}
 
+// Step 1, the pair part (Sec. 3.3 "processing of the input data"; Sec. 2.2
+// Eq. vpot, Eq. exp_z): free-packet potential matrices v_l on the grid's p
+// bins, diagonalisation of h1 = h0 + v in every channel (O, eps), Vt = v O^T,
+// uploaded; the lattice tables are the grid's (the problem holds a reference)
+static wpcd_status check_pair_desc(const wpcd_pair_desc *d) {
+  if (d->n_ch < 1 || d->n_ch > 5) return set_error(WPCD_EINVAL, "n_ch must be in [1, 5]");
+  if (d->n_terms < 1 || !d->V || !d->a) return set_error(WPCD_EINVAL, "potential needs >= 1 term");
+  for (int k = 0; k < d->n_terms; ++k)
+    if (!std::isfinite(d->V[k]) || !(d->a[k] > 0.0) || !std::isfinite(d->a[k]))
+      return set_error(WPCD_EINVAL, "potential terms must be finite with a_k > 0");
+  if (d->n_pair_nodes < 1 || d->n_pair_nodes > 64) return set_error(WPCD_EINVAL, "n_pair_nodes in [1, 64]");
+  return WPCD_OK;
+}
+
+static wpcd_status pair_create(wpcd_grid *g, const wpcd_pair_desc *d, wpcd_problem **out) {
+  if (!g || !d || !out) return set_error(WPCD_EINVAL, "null argument");
+  *out = nullptr;
+  wpcd_status vst = check_pair_desc(d);
+  if (vst != WPCD_OK) return vst;
+  cudaError_t ce = cudaSetDevice(g->device);
+  if (ce != cudaSuccess) return cuda_error(ce, "cudaSetDevice");
   wpcd_problem *pr = new (std::nothrow) wpcd_problem();
   if (!pr) return set_error(WPCD_ENOMEM, "host allocation");
-  pr->device = d->device;
-  pr->N = d->N;
-  pr->M = d->M;
-  pr->n_p = d->n_p;
-  pr->n_q = d->n_q;
-  pr->n_x = d->n_x;
+  pr->device = g->device;
+  pr->N = g->N;
+  pr->M = g->M;
+  pr->n_p = g->n_p;
+  pr->n_q = g->n_q;
+  pr->n_x = g->n_x;
   pr->n_ch = d->n_ch;
   int np = 0;
   for (int l = 0; l < d->n_ch; ++l)
@@ -238,9 +326,9 @@ static wpcd_status create(const wpcd_problem_desc *d, wpcd_problem **out) {
         ++np;
       }
   pr->n_pairs = np;
-  pr->pe.assign(d->p_edges, d->p_edges + d->N + 1);
-  pr->qe.assign(d->q_edges, d->q_edges + d->M + 1);
-  const int N = d->N, M = d->M;
+  pr->pe = g->pe;
+  pr->qe = g->qe;
+  const int N = g->N;
   // pair quantities per channel
   pr->eps.assign((size_t)d->n_ch * N, 0.0);
   pr->O.assign((size_t)d->n_ch * N * N, 0.0);
@@ -250,7 +338,7 @@ static wpcd_status create(const wpcd_problem_desc *d, wpcd_problem **out) {
   // the channels' eigenproblems side by side on the host cores
   std::vector<std::vector<double>> vs(d->n_ch), hs(d->n_ch), epss(d->n_ch), Os(d->n_ch);
   for (int l = 0; l < d->n_ch; ++l)
-    pair_matrices(N, d->p_edges, d->n_pair_nodes, l, d->n_terms, d->V, d->a, vs[l], hs[l]);
+    pair_matrices(N, g->pe.data(), d->n_pair_nodes, l, d->n_terms, d->V, d->a, vs[l], hs[l]);
 #pragma omp parallel for schedule(dynamic, 1)
   for (int l = 0; l < d->n_ch; ++l) pair_eig(N, hs[l], epss[l], Os[l]);
   for (int l = 0; l < d->n_ch; ++l) {
@@ -277,50 +365,46 @@ static wpcd_status create(const wpcd_problem_desc *d, wpcd_problem **out) {
     delete pr;
     return set_error(WPCD_ENOBOUND, "channel 0 has no bound pair state on this grid");
   }
-  // node and edge tables (canonical node placement: mid + half * t)
-  std::vector<double> tp(d->n_p), wp(d->n_p), tq(d->n_q), wq(d->n_q), ty(d->n_x), wy(d->n_x);
-  gauss_legendre(d->n_p, tp.data(), wp.data());
-  gauss_legendre(d->n_q, tq.data(), wq.data());
-  gauss_legendre(d->n_x, ty.data(), wy.data());
-  std::vector<double> pn((size_t)N * d->n_p), pw((size_t)N * d->n_p), qn((size_t)M * d->n_q),
-      qw((size_t)M * d->n_q), pe2(N + 1), qe2(M + 1), rsb((size_t)N * M);
-  for (int i = 0; i < N; ++i) {
-    double lo = pr->pe[i], hi = pr->pe[i + 1], half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
-    for (int a = 0; a < d->n_p; ++a) {
-      double p = mid + half * tp[a];
-      pn[(size_t)i * d->n_p + a] = p;
-      pw[(size_t)i * d->n_p + a] = half * wp[a] * p * p;
-    }
-  }
-  for (int j = 0; j < M; ++j) {
-    double lo = pr->qe[j], hi = pr->qe[j + 1], half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
-    for (int b = 0; b < d->n_q; ++b) {
-      double q = mid + half * tq[b];
-      qn[(size_t)j * d->n_q + b] = q;
-      qw[(size_t)j * d->n_q + b] = half * wq[b] * q * q;
-    }
-  }
-  for (int k = 0; k <= N; ++k) pe2[k] = pr->pe[k] * pr->pe[k];
-  for (int k = 0; k <= M; ++k) qe2[k] = pr->qe[k] * pr->qe[k];
-  for (int i = 0; i < N; ++i)
-    for (int j = 0; j < M; ++j)
-      rsb[(size_t)i * M + j] = 1.0 / std::sqrt(shell_volume(pr->pe[i], pr->pe[i + 1]) *
-                                               shell_volume(pr->qe[j], pr->qe[j + 1]));
   wpcd_status st = WPCD_OK;
   DeviceTables &t = pr->d;
-  if ((st = upload(&t.pe2, pe2)) || (st = upload(&t.qe2, qe2)) || (st = upload(&t.pn, pn)) ||
-      (st = upload(&t.wp, pw)) || (st = upload(&t.qn, qn)) || (st = upload(&t.wq, qw)) ||
-      (st = upload(&t.yn, ty)) || (st = upload(&t.wy, wy)) || (st = upload(&t.rsb, rsb)) ||
-      (st = upload(&t.qe, pr->qe)) || (st = upload(&t.eps, pr->eps)) || (st = upload(&t.O, pr->O)) ||
-      (st = upload(&t.Vt, pr->Vt)) || (st = upload32(&t.O32, pr->O)) || (st = upload32(&t.Vt32, pr->Vt))) {
+  if ((st = upload(&t.eps, pr->eps)) || (st = upload(&t.O, pr->O)) || (st = upload(&t.Vt, pr->Vt)) ||
+      (st = upload32(&t.O32, pr->O)) || (st = upload32(&t.Vt32, pr->Vt))) {
     free_tables(t);
     delete pr;
     return st;
   }
+  // the lattice tables: the grid's
+  t.pe2 = g->pe2;
+  t.qe2 = g->qe2;
+  t.pn = g->pn;
+  t.wp = g->wp;
+  t.qn = g->qn;
+  t.wq = g->wq;
+  t.yn = g->yn;
+  t.wy = g->wy;
+  t.rsb = g->rsb;
+  t.qe = g->qe_d;
+  pr->grid = g;
+  grid_retain(g);
   *out = pr;
   return WPCD_OK;
 }
 
+// wpcd_problem_create: a grid of its own and the pair setup on it
+static wpcd_status create(const wpcd_problem_desc *d, wpcd_problem **out) {
+  if (!d || !out) return set_error(WPCD_EINVAL, "null argument");
+  *out = nullptr;
+  const wpcd_pair_desc pd{d->n_ch, d->n_terms, d->V, d->a, d->n_pair_nodes};
+  wpcd_status st = check_pair_desc(&pd);  // every input checked before any device call
+  if (st != WPCD_OK) return st;
+  const wpcd_grid_desc gd{d->N, d->M, d->p_edges, d->q_edges, d->n_p, d->n_q, d->n_x, d->device};
+  wpcd_grid *g = nullptr;
+  st = grid_create(&gd, &g);
+  if (st != WPCD_OK) return st;
+  st = pair_create(g, &pd, out);
+  grid_release(g);  // the problem holds the remaining reference
+  return st;
+}
 }  // namespace wpcd
 
 using namespace wpcd;
@@ -370,6 +454,7 @@ void wpcd_problem_destroy(wpcd_problem *pr) {
   if (!pr) return;
   cudaSetDevice(pr->device);
   free_tables(pr->d);
+  grid_release(pr->grid);
   delete pr;
 }
 
@@ -395,13 +480,45 @@ wpcd_status wpcd_assemble_P(wpcd_problem *pr, int prec, void *stream, wpcd_P **o
   clear_error();
   if (!pr || !out) return set_error(WPCD_EINVAL, "null argument");
   *out = nullptr;
-  return assemble(pr, prec, static_cast<cudaStream_t>(stream), out);
+  return assemble(pr->grid, pr->n_ch, prec, static_cast<cudaStream_t>(stream), out);
   WPCD_GUARD_END
+}
+
+wpcd_status wpcd_grid_create(const wpcd_grid_desc *desc, wpcd_grid **out) {
+  WPCD_GUARD_BEGIN
+  clear_error();
+  return grid_create(desc, out);
+  WPCD_GUARD_END
+}
+
+void wpcd_grid_destroy(wpcd_grid *g) { grid_release(g); }
+
+wpcd_status wpcd_pair_create(wpcd_grid *g, const wpcd_pair_desc *desc, wpcd_problem **out) {
+  WPCD_GUARD_BEGIN
+  clear_error();
+  return pair_create(g, desc, out);
+  WPCD_GUARD_END
+}
+
+wpcd_status wpcd_assemble_P_grid(wpcd_grid *g, int n_ch, int prec, void *stream, wpcd_P **out) {
+  WPCD_GUARD_BEGIN
+  clear_error();
+  if (!g || !out) return set_error(WPCD_EINVAL, "null argument");
+  *out = nullptr;
+  return assemble(g, n_ch, prec, static_cast<cudaStream_t>(stream), out);
+  WPCD_GUARD_END
+}
+
+wpcd_status wpcd_problem_grid(const wpcd_problem *pr, wpcd_grid **out) {
+  if (!pr || !out) return set_error(WPCD_EINVAL, "null argument");
+  grid_retain(pr->grid);
+  *out = pr->grid;
+  return WPCD_OK;
 }
 
 void wpcd_P_destroy(wpcd_P *P) {
   if (!P) return;
-  cudaSetDevice(P->pr->device);
+  cudaSetDevice(P->device);
   dev_free(P->row_ptr);
   dev_free(P->col);
   dev_free(P->val64);
@@ -414,6 +531,7 @@ void wpcd_P_destroy(wpcd_P *P) {
     dev_free(P->tile_col[i]);
     dev_free(P->tile_val[i]);
   }
+  grid_release(P->grid);
   delete P;
 }
 
@@ -437,8 +555,8 @@ wpcd_status wpcd_P_export(const wpcd_P *P, int64_t *row_ptr, int32_t *col, doubl
   clear_error();
   if (!P) return set_error(WPCD_EINVAL, "null P");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  WPCD_CUDA_TRY(cudaSetDevice(P->pr->device));
-  const size_t ncell = (size_t)P->pr->N * P->pr->M;
+  WPCD_CUDA_TRY(cudaSetDevice(P->device));
+  const size_t ncell = (size_t)P->grid->N * P->grid->M;
   if (row_ptr) WPCD_CUDA_TRY(cudaMemcpyAsync(row_ptr, P->row_ptr, sizeof(int64_t) * (ncell + 1), cudaMemcpyDefault, s));
   if (col && P->nnz) WPCD_CUDA_TRY(cudaMemcpyAsync(col, P->col, sizeof(int32_t) * P->nnz, cudaMemcpyDefault, s));
   if (val && P->nnz) {
@@ -472,7 +590,7 @@ wpcd_status wpcd_kapply(const wpcd_problem *pr, const wpcd_P *P, const double *g
   WPCD_GUARD_BEGIN
   clear_error();
   if (!pr || !P || !x || !y || x == y) return set_error(WPCD_EINVAL, "bad kapply arguments");
-  if (P->pr != pr) return set_error(WPCD_EINVAL, "P was assembled for another problem");
+  if (!P_fits(P, pr)) return set_error(WPCD_EINVAL, "P was assembled on another lattice or for another channel count");
   return kapply(pr, P, g, x, y, static_cast<cudaStream_t>(stream));
   WPCD_GUARD_END
 }
@@ -482,7 +600,7 @@ wpcd_status wpcd_solve(wpcd_problem *pr, const wpcd_P *P, const double *E, int n
   WPCD_GUARD_BEGIN
   clear_error();
   if (!pr || !P) return set_error(WPCD_EINVAL, "null problem or P");
-  if (P->pr != pr) return set_error(WPCD_EINVAL, "P was assembled for another problem");
+  if (!P_fits(P, pr)) return set_error(WPCD_EINVAL, "P was assembled on another lattice or for another channel count");
   return solve(pr, P, E, n_E, opts, U00, stats, static_cast<cudaStream_t>(stream));
   WPCD_GUARD_END
 }
@@ -501,7 +619,7 @@ wpcd_status wpcd_spmm(wpcd_problem *pr, wpcd_P *P, int mode, const void *y, void
   WPCD_GUARD_BEGIN
   clear_error();
   if (!pr || !P) return set_error(WPCD_EINVAL, "null problem or P");
-  if (P->pr != pr) return set_error(WPCD_EINVAL, "P was assembled for another problem");
+  if (!P_fits(P, pr)) return set_error(WPCD_EINVAL, "P was assembled on another lattice or for another channel count");
   return spmm_apply(pr, P, mode, y, z, n_rhs, kernel_ms, static_cast<cudaStream_t>(stream));
   WPCD_GUARD_END
 }
@@ -518,7 +636,7 @@ wpcd_status wpcd_channel_gemm(wpcd_problem *pr, int which, int mode, const void 
 wpcd_status wpcd_born(wpcd_problem *pr, const wpcd_P *P, const double *E, int n_E, double *b, void *stream) {
   WPCD_GUARD_BEGIN
   clear_error();
-  if (!pr || !P || P->pr != pr) return set_error(WPCD_EINVAL, "bad problem or P");
+  if (!pr || !P || !P_fits(P, pr)) return set_error(WPCD_EINVAL, "bad problem or P");
   return born_vectors(pr, P, E, n_E, b, static_cast<cudaStream_t>(stream));
   WPCD_GUARD_END
 }
@@ -527,7 +645,7 @@ wpcd_status wpcd_tune_spmm(wpcd_problem *pr, wpcd_P *P, int n_rhs, int mode, voi
                            int *rows_per_warp, int *energy_lanes, int *energies_per_lane) {
   WPCD_GUARD_BEGIN
   clear_error();
-  if (!pr || !P || P->pr != pr) return set_error(WPCD_EINVAL, "bad problem or P");
+  if (!pr || !P || !P_fits(P, pr)) return set_error(WPCD_EINVAL, "bad problem or P");
   if (n_rhs < 1 || n_rhs > 1024) return set_error(WPCD_EINVAL, "n_rhs must be in [1, 1024]");
   if (mode < WPCD_SPMM_FP64 || mode > WPCD_SPMM_FF) return set_error(WPCD_EINVAL, "unknown SpMM mode");
   if (mode == WPCD_SPMM_FP32 && !P->val32 && !P->val32_copy)

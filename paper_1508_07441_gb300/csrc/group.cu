@@ -1232,7 +1232,7 @@ wpcd_status solve_group(int n_prob, wpcd_problem *const *prs, const wpcd_P *cons
     const wpcd_problem *pr = prs[g];
     const wpcd_P *P = Ps[g];
     if (!pr || !P || !E[g] || !U00[g]) return set_error(WPCD_EINVAL, "NULL problem, P, energies or output");
-    if (P->pr != pr) return set_error(WPCD_EINVAL, "P was assembled for another problem");
+    if (!P_fits(P, pr)) return set_error(WPCD_EINVAL, "P was assembled on another lattice or for another channel count");
     if (n_E[g] < 1 || n_E[g] > kMaxGroupE) return set_error(WPCD_EINVAL, "n_E must be in [1, WPCD_GROUP_MAX_E]");
     if (g > 0 && (pr->device != prs[0]->device || pr->n_ch != prs[0]->n_ch || P->prec != Ps[0]->prec))
       return set_error(WPCD_EINVAL, "grouped problems must share device, channel count and P precision");

@@ -55,7 +55,7 @@ extern "C" wpcd_status wpcd_kapply_noalloc(const wpcd_problem *pr, const wpcd_P 
   wpcd::clear_error();
   WPCD_GUARD_BEGIN
   if (!pr || !P || !x || !y || x == y) return wpcd::set_error(WPCD_EINVAL, "bad kapply arguments");
-  if (P->pr != pr) return wpcd::set_error(WPCD_EINVAL, "P was assembled for another problem");
+  if (!wpcd::P_fits(P, pr)) return wpcd::set_error(WPCD_EINVAL, "P was assembled on another lattice or for another channel count");
   const int64_t dim = (int64_t)pr->n_ch * pr->N * pr->M;
   if (dim > WPCD_NOALLOC_MAX_DIM)
     return wpcd::set_error(WPCD_EINVAL,

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <map>
 #include <new>
@@ -114,7 +115,24 @@ struct DeviceTables {
 
 }  // namespace wpcd
 
+// The packet lattice (Sec. 2.4 Eq. xij) and its quadrature tables: what P0
+// depends on.  Reference-counted: problems built on it and P0 matrices
+// assembled on it keep it alive after wpcd_grid_destroy.
+struct wpcd_grid {
+  int device = 0;
+  int N = 0, M = 0, n_p = 0, n_q = 0, n_x = 0;
+  std::vector<double> pe, qe;                   // host edges
+  double *pe2 = nullptr, *qe2 = nullptr;        // squared edges [N+1], [M+1]
+  double *pn = nullptr, *wp = nullptr;          // p nodes / weights*p^2 [N*n_p]
+  double *qn = nullptr, *wq = nullptr;          // q nodes / weights*q^2 [M*n_q]
+  double *yn = nullptr, *wy = nullptr;          // y nodes / weights [n_x]
+  double *rsb = nullptr;                        // 1/sqrt(B_i Bq_j) per cell [N*M]
+  double *qe_d = nullptr;                       // q edges [M+1]
+  std::atomic<int> refs{1};
+};
+
 struct wpcd_problem {
+  wpcd_grid *grid = nullptr;  // the lattice (one reference held)
   int device = 0;
   int N = 0, M = 0, n_p = 0, n_q = 0, n_x = 0, n_ch = 0, n_pairs = 0;
   int pair_l[wpcd::kMaxPairs], pair_lp[wpcd::kMaxPairs];
@@ -141,7 +159,8 @@ inline int64_t spmm_tune_key(int n_ch, int N, int M, int B, int mode) {
 }  // namespace wpcd
 
 struct wpcd_P {
-  const wpcd_problem *pr = nullptr;
+  wpcd_grid *grid = nullptr;  // the lattice P0 was assembled on (one reference held)
+  int device = 0, n_ch = 0;
   int prec = WPCD_FP64;
   int n_pairs = 0;
   int64_t nnz = 0;
@@ -161,8 +180,14 @@ struct wpcd_P {
 };
 
 namespace wpcd {
+// a P0 serves every problem on its lattice with its channel count (P0
+// depends on neither the potential nor the energy, Sec. 3.3)
+inline bool P_fits(const wpcd_P *P, const wpcd_problem *pr) { return P->grid == pr->grid && P->n_ch == pr->n_ch; }
+// capi.cpp: grid references
+void grid_retain(wpcd_grid *g);
+void grid_release(wpcd_grid *g);
 // assemble.cu
-wpcd_status assemble(wpcd_problem *pr, int prec, cudaStream_t s, wpcd_P **out);
+wpcd_status assemble(wpcd_grid *g, int n_ch, int prec, cudaStream_t s, wpcd_P **out);
 // solve.cu
 wpcd_status resolvent(const wpcd_problem *pr, const double *E, int n_E, double *g, int *j0,
                       double *D, cudaStream_t s);

@@ -40,6 +40,16 @@ class wpcd_problem_desc(ctypes.Structure):
                 ("n_pair_nodes", ctypes.c_int), ("device", ctypes.c_int)]
 
 
+class wpcd_grid_desc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("M", ctypes.c_int), ("p_edges", _D), ("q_edges", _D),
+                ("n_p", ctypes.c_int), ("n_q", ctypes.c_int), ("n_x", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+class wpcd_pair_desc(ctypes.Structure):
+    _fields_ = [("n_ch", ctypes.c_int), ("n_terms", ctypes.c_int), ("V", _D), ("a", _D),
+                ("n_pair_nodes", ctypes.c_int)]
+
+
 class wpcd_solve_opts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("max_iter", ctypes.c_int), ("min_iter", ctypes.c_int),
                 ("tol", ctypes.c_double), ("check_every", ctypes.c_int), ("precision", ctypes.c_int),
@@ -67,6 +77,11 @@ _SIGS = {
     "wpcd_problem_info": (ctypes.c_int, [_P, _I, _I, _D]),
     "wpcd_problem_pair": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, _D]),
     "wpcd_assemble_P": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.POINTER(_P)]),
+    "wpcd_grid_create": (ctypes.c_int, [ctypes.POINTER(wpcd_grid_desc), ctypes.POINTER(_P)]),
+    "wpcd_grid_destroy": (None, [_P]),
+    "wpcd_pair_create": (ctypes.c_int, [_P, ctypes.POINTER(wpcd_pair_desc), ctypes.POINTER(_P)]),
+    "wpcd_assemble_P_grid": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(_P)]),
+    "wpcd_problem_grid": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
     "wpcd_P_destroy": (None, [_P]),
     "wpcd_P_info": (ctypes.c_int, [_P, _I64, _I, _I, _F]),
     "wpcd_P_export": (ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -238,6 +253,47 @@ def wpcd_tangent_edges(n_bins: int, k_max: float) -> np.ndarray:
     return e
 
 
+class Grid:
+    """Handle of wpcd_grid: the packet lattice and its quadrature tables,
+    all that P0 depends on."""
+
+    def __init__(self, p_edges, q_edges, n_p, n_q, n_x, device=0):
+        self.pe = np.ascontiguousarray(p_edges, dtype=np.float64)
+        self.qe = np.ascontiguousarray(q_edges, dtype=np.float64)
+        self.N, self.M = len(self.pe) - 1, len(self.qe) - 1
+        d = wpcd_grid_desc(self.N, self.M, _dp(self.pe), _dp(self.qe), n_p, n_q, n_x, device)
+        h = _P()
+        self._h = None
+        check(lib().wpcd_grid_create(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None:
+            lib().wpcd_grid_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def wpcd_assemble_P(self, n_ch, prec=WPCD_FP64, stream=None) -> "PMatrix":
+        """P0 of this lattice for n_ch channels, usable with every Problem made
+        on the grid with n_ch channels."""
+        h = _P()
+        check(lib().wpcd_assemble_P_grid(self._h, n_ch, prec, _stream_ptr(stream), ctypes.byref(h)))
+        return PMatrix(h, self)
+
+    def wpcd_pair_create(self, V, a, n_ch, n_pair_nodes=8) -> "Problem":
+        """A Problem (this grid + the pair setup of V(r) = sum V_k exp(-r^2/a_k))."""
+        return Problem.on_grid(self, V, a, n_ch, n_pair_nodes)
+
+
 class Problem:
     """Handle of wpcd_problem (step 1 of the scheme, done by the library)."""
 
@@ -249,6 +305,22 @@ class Problem:
         h = _P()
         self._h = None
         check(lib().wpcd_problem_create(ctypes.byref(d), ctypes.byref(h)))
+        self._init(h, pe, qe, n_ch)
+
+    @classmethod
+    def on_grid(cls, grid, V, a, n_ch, n_pair_nodes=8):
+        """The pair setup on an existing grid (wpcd_pair_create)."""
+        self = cls.__new__(cls)
+        self._keep = [np.ascontiguousarray(x, dtype=np.float64) for x in (V, a)]
+        Vv, av = self._keep
+        d = wpcd_pair_desc(n_ch, len(Vv), _dp(Vv), _dp(av), n_pair_nodes)
+        h = _P()
+        self._h = None
+        check(lib().wpcd_pair_create(grid.handle, ctypes.byref(d), ctypes.byref(h)))
+        self._init(h, grid.pe, grid.qe, n_ch)
+        return self
+
+    def _init(self, h, pe, qe, n_ch):
         self._h = h
         self.N, self.M, self.n_ch = len(pe) - 1, len(qe) - 1, n_ch
         self.pe, self.qe = pe, qe
@@ -352,7 +424,8 @@ class Problem:
 
 
 class PMatrix:
-    """Handle of wpcd_P (block-CSR P0 on the device)."""
+    """Handle of wpcd_P (block-CSR P0 on the device); `problem` is the Problem
+    or Grid it was assembled from (for the lattice sizes)."""
 
     def __init__(self, h, problem):
         self._h = h

@@ -33,14 +33,16 @@ def test_struct_layouts_match_header(W, tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     src = tmp_path / "sz.c"
-    src.write_text('#include <stdio.h>\n#include "wpcd.h"\nint main(void){printf("%zu %zu %zu",'
-                   'sizeof(wpcd_problem_desc), sizeof(wpcd_solve_opts), sizeof(wpcd_solve_stats));}\n')
+    src.write_text('#include <stdio.h>\n#include "wpcd.h"\nint main(void){printf("%zu %zu %zu %zu %zu",'
+                   'sizeof(wpcd_problem_desc), sizeof(wpcd_solve_opts), sizeof(wpcd_solve_stats),'
+                   'sizeof(wpcd_grid_desc), sizeof(wpcd_pair_desc));}\n')
     exe = tmp_path / "sz"
     inc = W.HEADER.rsplit("/", 1)[0]
     subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
     sizes = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     assert sizes == [ctypes.sizeof(W.wpcd_problem_desc), ctypes.sizeof(W.wpcd_solve_opts),
-                     ctypes.sizeof(W.wpcd_solve_stats)]
+                     ctypes.sizeof(W.wpcd_solve_stats), ctypes.sizeof(W.wpcd_grid_desc),
+                     ctypes.sizeof(W.wpcd_pair_desc)]
 
 
 def _desc(W, N=4, M=4, **kw):
@@ -110,3 +112,21 @@ def test_no_cpu_fallback_when_library_missing(W, monkeypatch, tmp_path):
     monkeypatch.setattr(W, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU path"):
         W.lib()
+
+
+def test_grid_and_pair_reject_invalid_input(W):
+    """wpcd_grid_create, wpcd_pair_create and wpcd_assemble_P_grid validate
+    their arguments on the host (EINVAL) before any device call."""
+    L = W.lib()
+    h = ctypes.c_void_p()
+    pe = np.array([0.0, 1.0, 0.5])  # not increasing
+    qe = np.linspace(0, 3, 5)
+    d = W.wpcd_grid_desc(2, 4, pe.ctypes.data_as(W._D), qe.ctypes.data_as(W._D), 2, 2, 4, 0)
+    assert L.wpcd_grid_create(ctypes.byref(d), ctypes.byref(h)) == W.WPCD_EINVAL
+    assert "edges" in W.last_error()
+    d = W.wpcd_grid_desc(4, 4, qe.ctypes.data_as(W._D), qe.ctypes.data_as(W._D), 0, 2, 4, 0)
+    assert L.wpcd_grid_create(ctypes.byref(d), ctypes.byref(h)) == W.WPCD_EINVAL
+    V, a = np.array([-3.0]), np.array([1.0])
+    pd = W.wpcd_pair_desc(3, 1, V.ctypes.data_as(W._D), a.ctypes.data_as(W._D), 8)
+    assert L.wpcd_pair_create(None, ctypes.byref(pd), ctypes.byref(h)) == W.WPCD_EINVAL
+    assert L.wpcd_assemble_P_grid(None, 3, W.WPCD_FP64, None, ctypes.byref(h)) == W.WPCD_EINVAL

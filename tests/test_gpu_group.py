@@ -173,7 +173,7 @@ def test_group_rejects_bad_arguments(W, orc, group):
         W.wpcd_solve_batch(prs[:1] + [one_ch[0]], Ps[:1] + [one_ch[1]], energies[:2])
     with pytest.raises(W.WpcdError, match="WPCD_GROUP_MAX_E"):
         W.wpcd_solve_batch(prs[:1], Ps[:1], [np.linspace(0.1, 2.0, 33)])
-    with pytest.raises(W.WpcdError, match="another problem"):
+    with pytest.raises(W.WpcdError, match="another lattice"):
         W.wpcd_solve_batch(prs[:2], [Ps[1], Ps[0]], energies[:2])
     with pytest.raises(W.WpcdError, match="dimer threshold"):
         W.wpcd_solve_batch(prs[:1], Ps[:1], [[-50.0]])
