@@ -83,6 +83,9 @@ def lib():
                                         _I32, _D, _D, _D]),
                 "orc_P0_node_totals": (c_int, [c_int, _D, c_int, _D, c_int, c_int, c_int, c_int, _D]),
                 "orc_P0_normalize": (None, [c_int, _D, c_int, _D, c_int, _I64, _I32, _D]),
+                "orc_P0_vl_count": (c_i64, [c_int, _D, c_int, _D, c_int, c_int, c_int, _I64]),
+                "orc_P0_vl_fill": (c_int, [c_int, _D, c_int, _D, c_int, c_int, c_int, c_int, _I64,
+                                           _I32, _D, _D]),
                 "orc_onshell": (c_int, [c_int, _D, c_double, c_double, _INT, _D, _D, _D]),
                 "orc_G1": (c_int, [c_int, c_int, _D, c_int, _D, c_double, c_double, _D, _INT, _D]),
                 "orc_kapply": (None, [c_int, c_int, c_int, _D, _D, _I64, _I32, _D, _D, _D, _D]),
@@ -205,6 +208,30 @@ def P0(pe, qe, n_p, n_q, n_x, n_ch, normalize=True, with_outgrid=False, with_abs
     out = dict(row_ptr=rp, col=col[:nnz], val=val[:nnz], N=N, M=M, n_ch=n_ch)
     if with_abs:
         out["absval"] = av[:nnz]
+    if with_outgrid:
+        out["outgrid"] = og
+    return out
+
+
+def P0_vl(pe, qe, n_p, n_q, n_x, n_ch, normalize=True, with_outgrid=False):
+    """P0 with variable limits (the y-interval of every (p, q) node cut where
+    p'^2 or q'^2 crosses a squared bin edge, each piece integrated by the
+    n_x-point GL rule): block-CSR like P0()."""
+    pe, qe = _f64(pe), _f64(qe)
+    N, M = len(pe) - 1, len(qe) - 1
+    rp = np.zeros(N * M + 1, dtype=np.int64)
+    nnz = lib().orc_P0_vl_count(N, _p(pe), M, _p(qe), n_p, n_q, n_x, _p(rp, _I64))
+    assert nnz >= 0, nnz
+    npair = n_pairs(n_ch)
+    col = np.zeros(max(nnz, 1), dtype=np.int32)
+    val = np.zeros((max(nnz, 1), npair))
+    og = np.zeros((N * M, npair)) if with_outgrid else None
+    st = lib().orc_P0_vl_fill(N, _p(pe), M, _p(qe), n_p, n_q, n_x, n_ch, _p(rp, _I64), _p(col, _I32),
+                              _p(val), _p(og))
+    assert st == OK, st
+    if normalize:
+        lib().orc_P0_normalize(N, _p(pe), M, _p(qe), n_ch, _p(rp, _I64), _p(col, _I32), _p(val))
+    out = dict(row_ptr=rp, col=col[:nnz], val=val[:nnz], N=N, M=M, n_ch=n_ch)
     if with_outgrid:
         out["outgrid"] = og
     return out

@@ -610,6 +610,191 @@ int orc_P0_node_totals(int N, const double *pe, int M, const double *qe, int np_
   return ORC_OK;
 }
 
+/* ------------------------------------------------------------------------ */
+/* P0 with variable limits (Sec. 3.2, after Eq. gal: the cell overlap as an */
+/* integral with variable limits).  For a GL node (p, q) of the source cell */
+/* the recoupled squares are linear in y = p.q/(|p||q|):                    */
+/*   p'^2 = A y + Bp,  A = 3 p q / 4 > 0,   q'^2 = C y + Dq,  C = -p q < 0,  */
+/* so the theta functions of Eq. perm switch where p'^2 or q'^2 equals a    */
+/* squared bin edge.  Those y cut [-1, 1] into pieces that each lie in one  */
+/* target cell (or outside the grid); P_l(y) P_l'(y') is integrated over    */
+/* each piece with the n_x-point GL rule mapped onto it, and the p and q    */
+/* integrals keep the cell's GL rule.                                       */
+/* ------------------------------------------------------------------------ */
+
+static int cmp_double(const void *a, const void *b) {
+  double x = *(const double *)a, y = *(const double *)b;
+  return (x > y) - (x < y);
+}
+
+/* ys[0] = -1 < ys[1] < ... < ys[n] = 1: the cut points of node (p, q);
+   returns n, the number of pieces (ys holds N + M + 4 entries) */
+static int vl_cuts(const lattice *L, double p, double q, double *ys) {
+  double A = (0.75 * p) * q, Bp = (p * p) * 0.25 + (q * q) * 0.5625;
+  double C = -(p * q), Dq = (p * p) + (q * q) * 0.25;
+  int n = 0;
+  ys[n++] = -1.0;
+  for (int k = 0; k <= L->N; ++k) {
+    double y = (L->pe2[k] - Bp) / A;
+    if (y > -1.0 && y < 1.0) ys[n++] = y;
+  }
+  for (int k = 0; k <= L->M; ++k) {
+    double y = (L->qe2[k] - Dq) / C;
+    if (y > -1.0 && y < 1.0) ys[n++] = y;
+  }
+  ys[n++] = 1.0;
+  qsort(ys, n, sizeof(double), cmp_double);
+  int m = 1; /* drop repeated cut points */
+  for (int k = 1; k < n; ++k)
+    if (ys[k] > ys[m - 1]) ys[m++] = ys[k];
+  return m - 1;
+}
+
+/* target cell of the piece [a, b] of node (p, q): binned at its midpoint
+   (in the canonical rounding order of the node-binned P0), -1 outside */
+static int vl_target(const lattice *L, double p, double q, double a, double b) {
+  double A = (0.75 * p) * q, Bp = (p * p) * 0.25 + (q * q) * 0.5625;
+  double C = -(p * q), Dq = (p * p) + (q * q) * 0.25;
+  double mid = 0.5 * (a + b);
+  int ip = bin_of(fma(A, mid, Bp), L->pe2, L->N);
+  int jq = bin_of(fma(C, mid, Dq), L->qe2, L->M);
+  if (ip < 0 || jq < 0) return -1;
+  return ip * L->M + jq;
+}
+
+/* y' of the node (p, q) at y, as in the node-binned P0 */
+static double vl_yprime(double p, double q, double y) {
+  double A = (0.75 * p) * q, Bp = (p * p) * 0.25 + (q * q) * 0.5625;
+  double C = -(p * q), Dq = (p * p) + (q * q) * 0.25;
+  double p2 = fma(A, y, Bp), q2 = fma(C, y, Dq);
+  double num = -0.5 * p * p - 0.5 * p * q * y + 0.375 * q * q;
+  double den = sqrt(fmax(p2, 0.0) * fmax(q2, 0.0));
+  double c = den > 0.0 ? num / den : 0.0;
+  return c > 1.0 ? 1.0 : (c < -1.0 ? -1.0 : c);
+}
+
+/* row lengths of the variable-limit P0 (distinct target cells per source
+   cell); returns nnz or < 0 */
+int64_t orc_P0_vl_count(int N, const double *pe, int M, const double *qe, int np_, int nq, int nx,
+                        int64_t *row_ptr) {
+  lattice L;
+  if (lattice_init(&L, N, pe, M, qe, np_, nq, nx) != ORC_OK) return ORC_ENOMEM;
+  int ncell = N * M, err = 0;
+#pragma omp parallel
+  {
+    unsigned char *seen = calloc((size_t)ncell, 1);
+    int *touched = malloc(sizeof(int) * (size_t)ncell);
+    double *ys = malloc(sizeof(double) * (size_t)(N + M + 4));
+    if (!seen || !touched || !ys) {
+#pragma omp atomic write
+      err = 1;
+    }
+#pragma omp for schedule(dynamic, 8)
+    for (int c = 0; c < ncell; ++c) {
+      if (!seen || !touched || !ys) continue;
+      int i = c / M, j = c % M, nt = 0;
+      for (int a = 0; a < np_; ++a)
+        for (int b = 0; b < nq; ++b) {
+          double p = L.pn[(size_t)i * np_ + a], q = L.qn[(size_t)j * nq + b];
+          int npc = vl_cuts(&L, p, q, ys);
+          for (int s = 0; s < npc; ++s) {
+            int t = vl_target(&L, p, q, ys[s], ys[s + 1]);
+            if (t >= 0 && !seen[t]) { seen[t] = 1; touched[nt++] = t; }
+          }
+        }
+      row_ptr[c + 1] = nt;
+      for (int k = 0; k < nt; ++k) seen[touched[k]] = 0;
+    }
+    free(seen);
+    free(touched);
+    free(ys);
+  }
+  lattice_free(&L);
+  if (err) return ORC_ENOMEM;
+  row_ptr[0] = 0;
+  for (int c = 0; c < ncell; ++c) row_ptr[c + 1] += row_ptr[c];
+  return row_ptr[ncell];
+}
+
+/* values of the variable-limit P0, unnormalised, in the layout of
+   orc_P0_fill (val [nnz][n_pairs], columns ascending); outgrid (optional,
+   [N*M][n_pairs]) receives the weight of the pieces outside the grid */
+int orc_P0_vl_fill(int N, const double *pe, int M, const double *qe, int np_, int nq, int nx, int n_ch,
+                   const int64_t *row_ptr, int32_t *col, double *val, double *outgrid) {
+  lattice L;
+  if (n_ch < 1) return ORC_EINVAL;
+  if (lattice_init(&L, N, pe, M, qe, np_, nq, nx) != ORC_OK) return ORC_ENOMEM;
+  int npair = orc_n_pairs(n_ch);
+  int pl[64], plp[64];
+  pair_list(n_ch, pl, plp);
+  int ncell = N * M, err = 0;
+#pragma omp parallel
+  {
+    double *acc = calloc((size_t)ncell * npair, sizeof(double));
+    unsigned char *seen = calloc((size_t)ncell, 1);
+    int *touched = malloc(sizeof(int) * (size_t)ncell);
+    double *ys = malloc(sizeof(double) * (size_t)(N + M + 4));
+    double Py[32], Pyp[32], og[64];
+    if (!acc || !seen || !touched || !ys) {
+#pragma omp atomic write
+      err = 1;
+    }
+#pragma omp for schedule(dynamic, 8)
+    for (int c = 0; c < ncell; ++c) {
+      if (!acc || !seen || !touched || !ys) continue;
+      int i = c / M, j = c % M, nt = 0;
+      for (int k = 0; k < npair; ++k) og[k] = 0.0;
+      for (int a = 0; a < np_; ++a)
+        for (int b = 0; b < nq; ++b) {
+          double p = L.pn[(size_t)i * np_ + a], q = L.qn[(size_t)j * nq + b];
+          double Wpq = L.wpn[(size_t)i * np_ + a] * L.wqn[(size_t)j * nq + b];
+          int npc = vl_cuts(&L, p, q, ys);
+          for (int s = 0; s < npc; ++s) {
+            double ya = ys[s], yb = ys[s + 1], half = 0.5 * (yb - ya), mid = 0.5 * (ya + yb);
+            int t = vl_target(&L, p, q, ya, yb);
+            if (t >= 0 && !seen[t]) { seen[t] = 1; touched[nt++] = t; }
+            for (int x = 0; x < nx; ++x) {
+              double y = mid + half * L.yn[x];
+              double W = Wpq * (half * L.wyn[x]);
+              legendre(n_ch - 1, y, Py);
+              legendre(n_ch - 1, vl_yprime(p, q, y), Pyp);
+              for (int k = 0; k < npair; ++k) {
+                double term = W * Py[pl[k]] * Pyp[plp[k]];
+                if (t < 0)
+                  og[k] += term;
+                else
+                  acc[(size_t)t * npair + k] += term;
+              }
+            }
+          }
+        }
+      if (row_ptr[c + 1] - row_ptr[c] != nt) {
+#pragma omp atomic write
+        err = 2;
+      }
+      qsort(touched, nt, sizeof(int), cmp_int);
+      int64_t o = row_ptr[c];
+      for (int k = 0; k < nt && o + k < row_ptr[c + 1]; ++k) {
+        int t = touched[k];
+        col[o + k] = t;
+        for (int m = 0; m < npair; ++m) {
+          val[(o + k) * npair + m] = acc[(size_t)t * npair + m];
+          acc[(size_t)t * npair + m] = 0.0;
+        }
+        seen[t] = 0;
+      }
+      if (outgrid)
+        for (int k = 0; k < npair; ++k) outgrid[(size_t)c * npair + k] = og[k];
+    }
+    free(acc);
+    free(seen);
+    free(touched);
+    free(ys);
+  }
+  lattice_free(&L);
+  return err == 1 ? ORC_ENOMEM : (err == 2 ? ORC_EINVAL : ORC_OK);
+}
+
 /* Normalisation of Eq. perm: sqrt((2l+1)(2l'+1)) / sqrt(B_i Bq_j B_i' Bq_j'). */
 void orc_P0_normalize(int N, const double *pe, int M, const double *qe, int n_ch,
                       const int64_t *row_ptr, const int32_t *col, double *val) {

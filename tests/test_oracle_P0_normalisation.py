@@ -105,9 +105,9 @@ def block_errors(G, F, ls):
     return {l: np.linalg.norm(G[l] - 2 * F[l]) / np.linalg.norm(2 * F[l]) for l in ls}
 
 
-def _run(orc, f, n_ch, a, N, nodes, ls, mistake=None):
+def _run(orc, f, n_ch, a, N, nodes, ls, mistake=None, builder=None):
     e = np.linspace(0.0, KMAX, N + 1)
-    P = orc.P0(e, e, *nodes, n_ch)
+    P = (builder or orc.P0)(e, e, *nodes, n_ch)
     F = cell_projection(f, e, e, n_ch, a)
     for l in range(n_ch):
         if l not in ls:  # no content of this parity: the block product vanishes too
@@ -143,3 +143,14 @@ def test_symmetric_l4_block(orc):
     got = _run(orc, f_sym8, 5, 0.5, 64, (8, 8, 64), (0, 2, 4))
     assert got[0] < 5e-3 and got[2] < 1e-2 and got[4] < 0.15, got
     assert _run(orc, f_sym8, 5, 0.5, 64, (8, 8, 64), (0, 2, 4), "no_2l+1")[4] > 0.5
+
+
+def test_variable_limit_P0_converges_to_2f(orc):
+    """The same pin for the variable-limit P0 (y-interval cut at the squared
+    bin edges, each piece integrated by GL): symmetric f with l = 0, 2 and
+    antisymmetric f with l = 1, 3, second order in the cell size."""
+    for f, n_ch, ls in ((f_sym4, 3, (0, 2)), (f_anti, 4, (1, 3))):
+        coarse = _run(orc, f, n_ch, 1.0, 24, (4, 4, 8), ls, builder=orc.P0_vl)
+        fine = _run(orc, f, n_ch, 1.0, 48, (4, 4, 8), ls, builder=orc.P0_vl)
+        for l in ls:
+            assert fine[l] < 4e-2 and coarse[l] > 2.5 * fine[l], (l, coarse, fine)
