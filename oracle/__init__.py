@@ -214,9 +214,10 @@ def P0(pe, qe, n_p, n_q, n_x, n_ch, normalize=True, with_outgrid=False, with_abs
 
 
 def P0_vl(pe, qe, n_p, n_q, n_x, n_ch, normalize=True, with_outgrid=False):
-    """P0 with variable limits (the y-interval of every (p, q) node cut where
-    p'^2 or q'^2 crosses a squared bin edge, each piece integrated by the
-    n_x-point GL rule): block-CSR like P0()."""
+    """P0 with variable limits: for every (p, q) node of a source cell and
+    every target cell, the y-interval on which p' and q' lie in the target's
+    bins (limits where p'^2, q'^2, linear in y, equal squared bin edges),
+    integrated by the n_x-point GL rule mapped onto it; block-CSR like P0()."""
     pe, qe = _f64(pe), _f64(qe)
     N, M = len(pe) - 1, len(qe) - 1
     rp = np.zeros(N * M + 1, dtype=np.int64)

@@ -615,51 +615,32 @@ int orc_P0_node_totals(int N, const double *pe, int M, const double *qe, int np_
 /* integral with variable limits).  For a GL node (p, q) of the source cell */
 /* the recoupled squares are linear in y = p.q/(|p||q|):                    */
 /*   p'^2 = A y + Bp,  A = 3 p q / 4 > 0,   q'^2 = C y + Dq,  C = -p q < 0,  */
-/* so the theta functions of Eq. perm switch where p'^2 or q'^2 equals a    */
-/* squared bin edge.  Those y cut [-1, 1] into pieces that each lie in one  */
-/* target cell (or outside the grid); P_l(y) P_l'(y') is integrated over    */
-/* each piece with the n_x-point GL rule mapped onto it, and the p and q    */
-/* integrals keep the cell's GL rule.                                       */
+/* so theta(p' in bin i') theta(q' in bin j') of Eq. perm holds on one      */
+/* y-interval, its limits where p'^2 or q'^2 equals the bins' squared edges:*/
+/*   p-bin i': y in [(e_i'^2 - Bp)/A, (e_i'+1^2 - Bp)/A]                     */
+/*   q-bin j': y in [(f_j'+1^2 - Dq)/C, (f_j'^2 - Dq)/C]                     */
+/* intersected with [-1, 1].  P_l(y) P_l'(y') is integrated over it with    */
+/* the n_x-point GL rule mapped onto it; the p and q integrals keep the     */
+/* cell's GL rule.  Neighbouring targets share the same computed limit, so  */
+/* the intervals of one node tile [-1, 1] (those beyond the last edges      */
+/* leave the grid).                                                         */
 /* ------------------------------------------------------------------------ */
 
-static int cmp_double(const void *a, const void *b) {
-  double x = *(const double *)a, y = *(const double *)b;
-  return (x > y) - (x < y);
-}
-
-/* ys[0] = -1 < ys[1] < ... < ys[n] = 1: the cut points of node (p, q);
-   returns n, the number of pieces (ys holds N + M + 4 entries) */
-static int vl_cuts(const lattice *L, double p, double q, double *ys) {
+/* the y-interval [ya, yb] of node (p, q) for target (it, jt); returns 1 if
+   it is not empty */
+static int vl_interval(const lattice *L, double p, double q, int it, int jt, double *ya, double *yb) {
   double A = (0.75 * p) * q, Bp = (p * p) * 0.25 + (q * q) * 0.5625;
   double C = -(p * q), Dq = (p * p) + (q * q) * 0.25;
-  int n = 0;
-  ys[n++] = -1.0;
-  for (int k = 0; k <= L->N; ++k) {
-    double y = (L->pe2[k] - Bp) / A;
-    if (y > -1.0 && y < 1.0) ys[n++] = y;
-  }
-  for (int k = 0; k <= L->M; ++k) {
-    double y = (L->qe2[k] - Dq) / C;
-    if (y > -1.0 && y < 1.0) ys[n++] = y;
-  }
-  ys[n++] = 1.0;
-  qsort(ys, n, sizeof(double), cmp_double);
-  int m = 1; /* drop repeated cut points */
-  for (int k = 1; k < n; ++k)
-    if (ys[k] > ys[m - 1]) ys[m++] = ys[k];
-  return m - 1;
-}
-
-/* target cell of the piece [a, b] of node (p, q): binned at its midpoint
-   (in the canonical rounding order of the node-binned P0), -1 outside */
-static int vl_target(const lattice *L, double p, double q, double a, double b) {
-  double A = (0.75 * p) * q, Bp = (p * p) * 0.25 + (q * q) * 0.5625;
-  double C = -(p * q), Dq = (p * p) + (q * q) * 0.25;
-  double mid = 0.5 * (a + b);
-  int ip = bin_of(fma(A, mid, Bp), L->pe2, L->N);
-  int jq = bin_of(fma(C, mid, Dq), L->qe2, L->M);
-  if (ip < 0 || jq < 0) return -1;
-  return ip * L->M + jq;
+  double lo = -1.0, hi = 1.0;
+  double plo = (L->pe2[it] - Bp) / A, phi = (L->pe2[it + 1] - Bp) / A;
+  double qlo = (L->qe2[jt + 1] - Dq) / C, qhi = (L->qe2[jt] - Dq) / C;
+  if (plo > lo) lo = plo;
+  if (qlo > lo) lo = qlo;
+  if (phi < hi) hi = phi;
+  if (qhi < hi) hi = qhi;
+  *ya = lo;
+  *yb = hi;
+  return hi > lo;
 }
 
 /* y' of the node (p, q) at y, as in the node-binned P0 */
@@ -673,6 +654,21 @@ static double vl_yprime(double p, double q, double y) {
   return c > 1.0 ? 1.0 : (c < -1.0 ? -1.0 : c);
 }
 
+/* the p-bins and q-bins a node can reach (a superset: the bins whose
+   squared-momentum range meets [min, max] of p'^2 and q'^2 over y) */
+static void vl_range(const lattice *L, double p, double q, int *i0, int *i1, int *j0, int *j1) {
+  double pmin = fabs(0.5 * p - 0.75 * q), pmax = 0.5 * p + 0.75 * q;
+  double qmin = fabs(p - 0.5 * q), qmax = p + 0.5 * q;
+  *i0 = 0;
+  while (*i0 + 1 < L->N && L->pe2[*i0 + 1] <= pmin * pmin * (1.0 - 1e-12)) ++*i0;
+  *i1 = *i0;
+  while (*i1 + 1 < L->N && L->pe2[*i1 + 1] < pmax * pmax * (1.0 + 1e-12)) ++*i1;
+  *j0 = 0;
+  while (*j0 + 1 < L->M && L->qe2[*j0 + 1] <= qmin * qmin * (1.0 - 1e-12)) ++*j0;
+  *j1 = *j0;
+  while (*j1 + 1 < L->M && L->qe2[*j1 + 1] < qmax * qmax * (1.0 + 1e-12)) ++*j1;
+}
+
 /* row lengths of the variable-limit P0 (distinct target cells per source
    cell); returns nnz or < 0 */
 int64_t orc_P0_vl_count(int N, const double *pe, int M, const double *qe, int np_, int nq, int nx,
@@ -684,30 +680,30 @@ int64_t orc_P0_vl_count(int N, const double *pe, int M, const double *qe, int np
   {
     unsigned char *seen = calloc((size_t)ncell, 1);
     int *touched = malloc(sizeof(int) * (size_t)ncell);
-    double *ys = malloc(sizeof(double) * (size_t)(N + M + 4));
-    if (!seen || !touched || !ys) {
+    if (!seen || !touched) {
 #pragma omp atomic write
       err = 1;
     }
 #pragma omp for schedule(dynamic, 8)
     for (int c = 0; c < ncell; ++c) {
-      if (!seen || !touched || !ys) continue;
+      if (!seen || !touched) continue;
       int i = c / M, j = c % M, nt = 0;
       for (int a = 0; a < np_; ++a)
         for (int b = 0; b < nq; ++b) {
-          double p = L.pn[(size_t)i * np_ + a], q = L.qn[(size_t)j * nq + b];
-          int npc = vl_cuts(&L, p, q, ys);
-          for (int s = 0; s < npc; ++s) {
-            int t = vl_target(&L, p, q, ys[s], ys[s + 1]);
-            if (t >= 0 && !seen[t]) { seen[t] = 1; touched[nt++] = t; }
-          }
+          double p = L.pn[(size_t)i * np_ + a], q = L.qn[(size_t)j * nq + b], ya, yb;
+          int i0, i1, j0, j1;
+          vl_range(&L, p, q, &i0, &i1, &j0, &j1);
+          for (int it = i0; it <= i1; ++it)
+            for (int jt = j0; jt <= j1; ++jt) {
+              int t = it * M + jt;
+              if (!seen[t] && vl_interval(&L, p, q, it, jt, &ya, &yb)) { seen[t] = 1; touched[nt++] = t; }
+            }
         }
       row_ptr[c + 1] = nt;
       for (int k = 0; k < nt; ++k) seen[touched[k]] = 0;
     }
     free(seen);
     free(touched);
-    free(ys);
   }
   lattice_free(&L);
   if (err) return ORC_ENOMEM;
@@ -718,7 +714,7 @@ int64_t orc_P0_vl_count(int N, const double *pe, int M, const double *qe, int np
 
 /* values of the variable-limit P0, unnormalised, in the layout of
    orc_P0_fill (val [nnz][n_pairs], columns ascending); outgrid (optional,
-   [N*M][n_pairs]) receives the weight of the pieces outside the grid */
+   [N*M][n_pairs]) receives the integral over the y that leave the grid */
 int orc_P0_vl_fill(int N, const double *pe, int M, const double *qe, int np_, int nq, int nx, int n_ch,
                    const int64_t *row_ptr, int32_t *col, double *val, double *outgrid) {
   lattice L;
@@ -733,37 +729,59 @@ int orc_P0_vl_fill(int N, const double *pe, int M, const double *qe, int np_, in
     double *acc = calloc((size_t)ncell * npair, sizeof(double));
     unsigned char *seen = calloc((size_t)ncell, 1);
     int *touched = malloc(sizeof(int) * (size_t)ncell);
-    double *ys = malloc(sizeof(double) * (size_t)(N + M + 4));
     double Py[32], Pyp[32], og[64];
-    if (!acc || !seen || !touched || !ys) {
+    if (!acc || !seen || !touched) {
 #pragma omp atomic write
       err = 1;
     }
 #pragma omp for schedule(dynamic, 8)
     for (int c = 0; c < ncell; ++c) {
-      if (!acc || !seen || !touched || !ys) continue;
+      if (!acc || !seen || !touched) continue;
       int i = c / M, j = c % M, nt = 0;
       for (int k = 0; k < npair; ++k) og[k] = 0.0;
       for (int a = 0; a < np_; ++a)
         for (int b = 0; b < nq; ++b) {
-          double p = L.pn[(size_t)i * np_ + a], q = L.qn[(size_t)j * nq + b];
+          double p = L.pn[(size_t)i * np_ + a], q = L.qn[(size_t)j * nq + b], ya, yb;
           double Wpq = L.wpn[(size_t)i * np_ + a] * L.wqn[(size_t)j * nq + b];
-          int npc = vl_cuts(&L, p, q, ys);
-          for (int s = 0; s < npc; ++s) {
-            double ya = ys[s], yb = ys[s + 1], half = 0.5 * (yb - ya), mid = 0.5 * (ya + yb);
-            int t = vl_target(&L, p, q, ya, yb);
-            if (t >= 0 && !seen[t]) { seen[t] = 1; touched[nt++] = t; }
-            for (int x = 0; x < nx; ++x) {
-              double y = mid + half * L.yn[x];
-              double W = Wpq * (half * L.wyn[x]);
-              legendre(n_ch - 1, y, Py);
-              legendre(n_ch - 1, vl_yprime(p, q, y), Pyp);
-              for (int k = 0; k < npair; ++k) {
-                double term = W * Py[pl[k]] * Pyp[plp[k]];
-                if (t < 0)
-                  og[k] += term;
-                else
+          int i0, i1, j0, j1;
+          vl_range(&L, p, q, &i0, &i1, &j0, &j1);
+          for (int it = i0; it <= i1; ++it)
+            for (int jt = j0; jt <= j1; ++jt) {
+              if (!vl_interval(&L, p, q, it, jt, &ya, &yb)) continue;
+              int t = it * M + jt;
+              if (!seen[t]) { seen[t] = 1; touched[nt++] = t; }
+              double half = 0.5 * (yb - ya), mid = 0.5 * (ya + yb);
+              for (int x = 0; x < nx; ++x) {
+                double y = mid + half * L.yn[x];
+                double W = Wpq * (half * L.wyn[x]);
+                legendre(n_ch - 1, y, Py);
+                legendre(n_ch - 1, vl_yprime(p, q, y), Pyp);
+                for (int k = 0; k < npair; ++k) {
+                  double term = W * Py[pl[k]] * Pyp[plp[k]];
                   acc[(size_t)t * npair + k] += term;
+                }
+              }
+            }
+          /* outside the grid: p'^2 above the last p edge (y > yp) or q'^2
+             above the last q edge (y < yq); both pieces by the GL rule */
+          {
+            double A = (0.75 * p) * q, Bp = (p * p) * 0.25 + (q * q) * 0.5625;
+            double C = -(p * q), Dq = (p * p) + (q * q) * 0.25;
+            double yp = (L.pe2[N] - Bp) / A, yq = (L.qe2[M] - Dq) / C;
+            double lo[2], hi[2];
+            int npc = 0;
+            if (yq >= yp) { lo[0] = -1.0; hi[0] = 1.0; npc = 1; } /* no y inside the grid */
+            else {
+              if (yq > -1.0) { lo[npc] = -1.0; hi[npc] = yq < 1.0 ? yq : 1.0; ++npc; }
+              if (yp < 1.0) { lo[npc] = yp > -1.0 ? yp : -1.0; hi[npc] = 1.0; ++npc; }
+            }
+            for (int s2 = 0; s2 < npc; ++s2) {
+              double half = 0.5 * (hi[s2] - lo[s2]), mid = 0.5 * (hi[s2] + lo[s2]);
+              for (int x = 0; x < nx; ++x) {
+                double y = mid + half * L.yn[x];
+                legendre(n_ch - 1, y, Py);
+                legendre(n_ch - 1, vl_yprime(p, q, y), Pyp);
+                for (int k = 0; k < npair; ++k) og[k] += Wpq * (half * L.wyn[x]) * Py[pl[k]] * Pyp[plp[k]];
               }
             }
           }
@@ -789,7 +807,6 @@ int orc_P0_vl_fill(int N, const double *pe, int M, const double *qe, int np_, in
     free(acc);
     free(seen);
     free(touched);
-    free(ys);
   }
   lattice_free(&L);
   return err == 1 ? ORC_ENOMEM : (err == 2 ? ORC_EINVAL : ORC_OK);
