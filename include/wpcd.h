@@ -67,6 +67,10 @@ typedef int wpcd_status;
 /* arithmetic of the assembled values and of the solve */
 #define WPCD_FP64 0   /* all node values and sums in FP64 */
 #define WPCD_FP32C 1  /* FP64 binning, FP32 node values, compensated sums */
+#define WPCD_FP64_VL 2 /* assembly only: FP64 with variable limits instead of
+                          node binning (the y-interval of every (p, q) node and
+                          target cell from the theta limits of Eq. perm,
+                          integrated by the n_x-point GL rule; Sec. 3.2) */
 
 /* summation of the iterates */
 #define WPCD_SUM_KRYLOV 0 /* vector form: minimal-residual extrapolation of
@@ -197,6 +201,15 @@ wpcd_status wpcd_problem_pair(const wpcd_problem *pr, int l, double *eps, double
  *                       * sum_nodes w p^2 q^2 P_l(y) P_l'(y') [node -> c'].
  * prec = WPCD_FP64 or WPCD_FP32C.  Two passes (count, then fill) with no
  * atomics: the result is bit-reproducible for a given device.
+ * prec = WPCD_FP64_VL assembles the same elements with variable limits (the
+ * paper's "double integral with variable limits", Sec. 3.2): for every GL
+ * node (p, q) of the source cell and every target cell, the y-interval on
+ * which p' and q' lie in the target's bins (p'^2, q'^2 are linear in y, so
+ * the limits are (e^2 - Bp) / A for the edges e) is integrated with the
+ * n_x-point GL rule mapped onto it; the theta functions are then exact in y.
+ * FP64 values (the P0 reports WPCD_FP64), one thread per nonzero element,
+ * bit-reproducible; EINVAL if a source cell has more than 8192 (node,
+ * target) pieces.
  * Runs on `stream` and returns when the assembly has completed (the stream
  * is synchronised twice: for the nonzero count, and at the end).  The P0
  * belongs to the problem's grid and channel count (see wpcd_assemble_P_grid):

@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwpcd.so")
 SOURCES = ["capi.cpp", "setup.cpp", "assemble.cu", "solve.cu", "group.cu", "tc_gemm.cu", "df.cu", "mlp.cu",
-           "kapply_noalloc.cu", "spmm_tile.cu", "oz_gemm.cu", "spmv.cu"]
+           "kapply_noalloc.cu", "spmm_tile.cu", "oz_gemm.cu", "spmv.cu",
+           "assemble_vl.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

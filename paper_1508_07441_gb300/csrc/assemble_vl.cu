@@ -1,0 +1,297 @@
+// P0 with variable limits (Sec. 3.2, after Eq. gal: the element of Eq. perm
+// reduced to an integral with variable limits, "calculated numerically").
+//
+// For a GL node (p, q) of the source cell the recoupled squares are linear
+// in y = p.q / (|p| |q|):
+//   p'^2 = A y + Bp,  A = 3 p q / 4 > 0;   q'^2 = C y + Dq,  C = -p q < 0,
+// so the theta functions of Eq. perm hold on one y-interval per target cell
+// (i', j'): [yp(i'), yp(i'+1)] from the p edges, yp(k) = (e_k^2 - Bp) / A,
+// intersected with [yq(j'+1), yq(j')] from the q edges, yq(k) =
+// (f_k^2 - Dq) / C, and with [-1, 1].  P_l(y) P_l'(y') is integrated over the
+// interval with the n_x-point GL rule mapped onto it; the p and q integrals
+// keep the cell's GL rule.  Against node binning the theta functions are
+// exact in y, so the element converges faster to the exact cell overlap.
+//
+// Kernels (FP64 throughout; the limits are IEEE divisions of values rounded
+// in the canonical order, so identical inputs give identical limits):
+//   vl_rows_kernel   one CTA per source cell: every (p, q) node walks its
+//                    targets in increasing y (the next limit is the smaller
+//                    of the next p limit and the next q limit) and appends
+//                    the non-empty ones to a shared-memory list, which is
+//                    sorted and deduplicated: the row length, or (second
+//                    launch) the row's ascending columns;
+//   vl_value_kernel  one thread per nonzero element (the paper's own
+//                    decomposition, Sec. 4.2): the sum over the source
+//                    cell's nodes, in a fixed order, of the GL integral over
+//                    the element's interval, normalised as in Eq. perm.
+// The row lengths are summed into row pointers on the host (one copy each
+// way); no atomics on values, so the result is bit-reproducible.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdint>
+#include <vector>
+
+#include "common.cuh"
+#include "wpcd_internal.h"
+
+namespace wpcd {
+namespace {
+
+constexpr int VL_THREADS = 128;
+constexpr int VL_KEYS = 8192;  // node-target pieces of one source cell
+
+struct VlParams {
+  int N, M, n_p, n_q, n_x, n_ch, n_pairs;
+  int pl[kMaxPairs], plp[kMaxPairs];
+  double cnorm[kMaxPairs];  // sqrt((2l+1)(2l'+1))
+  const double *pe2, *qe2, *pn, *wp, *qn, *wq, *yn, *wy, *rsb;
+};
+
+// the linear coefficients of node (p, q), each product and sum rounded
+// separately (no contraction), in the canonical order of the node-binned P0
+struct VlNode {
+  double A, Bp, C, Dq;
+  __device__ VlNode(double p, double q) {
+    A = __dmul_rn(__dmul_rn(0.75, p), q);
+    Bp = __dadd_rn(__dmul_rn(__dmul_rn(p, p), 0.25), __dmul_rn(__dmul_rn(q, q), 0.5625));
+    C = -__dmul_rn(p, q);
+    Dq = __dadd_rn(__dmul_rn(p, p), __dmul_rn(__dmul_rn(q, q), 0.25));
+  }
+  // y limits of p edge k and q edge k (k beyond the grid: +-infinity)
+  __device__ double yp(const VlParams &P, int k) const {
+    return k > P.N ? INFINITY : __ddiv_rn(__dsub_rn(P.pe2[k], Bp), A);
+  }
+  __device__ double yq(const VlParams &P, int k) const {
+    return k > P.M ? -INFINITY : __ddiv_rn(__dsub_rn(P.qe2[k], Dq), C);
+  }
+};
+
+// the y-interval of target (it, jt) for the node; true if not empty
+__device__ __forceinline__ bool vl_interval(const VlParams &P, const VlNode &nd, int it, int jt, double &lo,
+                                            double &hi) {
+  lo = fmax(-1.0, fmax(nd.yp(P, it), nd.yq(P, jt + 1)));
+  hi = fmin(1.0, fmin(nd.yp(P, it + 1), nd.yq(P, jt)));
+  return hi > lo;
+}
+
+// row lengths (cols == nullptr: counts[c]) or the row's ascending columns
+__global__ void __launch_bounds__(VL_THREADS) vl_rows_kernel(VlParams P, int64_t *counts, const int64_t *row_ptr,
+                                                            int32_t *cols, int *err) {
+  __shared__ int keys[VL_KEYS];
+  __shared__ int n_keys, n_unique;
+  const int c = blockIdx.x, i = c / P.M, j = c % P.M;
+  if (threadIdx.x == 0) n_keys = 0;
+  __syncthreads();
+  for (int node = threadIdx.x; node < P.n_p * P.n_q; node += blockDim.x) {
+    const int a = node / P.n_q, b = node % P.n_q;
+    const VlNode nd(P.pn[i * P.n_p + a], P.qn[j * P.n_q + b]);
+    // the p bin and the q bin at y just above -1 (bin N, M: beyond the grid)
+    int it = 0;
+    while (it < P.N && !(nd.yp(P, it + 1) > -1.0)) ++it;
+    int jt = P.M;
+    while (jt > 0 && !(nd.yq(P, jt) > -1.0)) --jt;
+    // walk up in y: from one target to the next across the nearer limit
+    for (int guard = 0; guard < 2 * (P.N + P.M) + 4; ++guard) {
+      double lo, hi;
+      const bool in = it < P.N && jt < P.M;
+      if (vl_interval(P, nd, it, jt, lo, hi) && in) {
+        const int k = atomicAdd(&n_keys, 1);
+        if (k < VL_KEYS) keys[k] = it * P.M + jt;
+      }
+      const double up = nd.yp(P, it + 1), uq = nd.yq(P, jt);
+      const double top = fmin(up, uq);
+      if (!(top < 1.0) || it >= P.N || jt < 0) break;
+      if (up <= uq) ++it;
+      if (uq <= up) --jt;
+      if (jt < 0) break;
+    }
+  }
+  __syncthreads();
+  const int n = n_keys;
+  if (n > VL_KEYS) {
+    if (threadIdx.x == 0) atomicOr(err, 1);
+    return;  // uniform over the CTA
+  }
+  int np2 = 1;
+  while (np2 < n) np2 <<= 1;
+  for (int k = n + threadIdx.x; k < np2; k += blockDim.x) keys[k] = INT_MAX;
+  __syncthreads();
+  // bitonic sort, ascending
+  for (int k = 2; k <= np2; k <<= 1)
+    for (int d = k >> 1; d > 0; d >>= 1) {
+      for (int x = threadIdx.x; x < np2; x += blockDim.x) {
+        const int y = x ^ d;
+        if (y > x) {
+          const int u = keys[x], v = keys[y];
+          if ((u > v) == ((x & k) == 0)) {
+            keys[x] = v;
+            keys[y] = u;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  // distinct keys: thread 0 compacts (rows are a few hundred long)
+  if (threadIdx.x == 0) {
+    int m = 0;
+    for (int k = 0; k < n; ++k)
+      if (k == 0 || keys[k] != keys[k - 1]) keys[m++] = keys[k];
+    n_unique = m;
+  }
+  __syncthreads();
+  if (!cols) {
+    if (threadIdx.x == 0) counts[c] = n_unique;
+  } else {
+    const int64_t o = row_ptr[c];
+    for (int k = threadIdx.x; k < n_unique; k += blockDim.x) cols[o + k] = keys[k];
+  }
+}
+
+// P_l(x) for l = 0 .. lmax by the three-term recurrence
+__device__ __forceinline__ void legendre_all(int lmax, double x, double *Pl) {
+  Pl[0] = 1.0;
+  if (lmax >= 1) Pl[1] = x;
+  for (int n = 1; n < lmax; ++n) Pl[n + 1] = ((2.0 * n + 1.0) * x * Pl[n] - n * Pl[n - 1]) / (n + 1.0);
+}
+
+// one thread per nonzero of row c (CTA c): sum over the cell's nodes
+__global__ void __launch_bounds__(VL_THREADS) vl_value_kernel(VlParams P, const int64_t *row_ptr,
+                                                             const int32_t *cols, int64_t nnz, double *val) {
+  const int c = blockIdx.x, i = c / P.M, j = c % P.M;
+  const int64_t b0 = row_ptr[c], b1 = row_ptr[c + 1];
+  for (int64_t o = b0 + threadIdx.x; o < b1; o += blockDim.x) {
+    const int t = cols[o], it = t / P.M, jt = t % P.M;
+    double sum[kMaxPairs];
+    for (int m = 0; m < P.n_pairs; ++m) sum[m] = 0.0;
+    for (int a = 0; a < P.n_p; ++a)
+      for (int b = 0; b < P.n_q; ++b) {
+        const double p = P.pn[i * P.n_p + a], q = P.qn[j * P.n_q + b];
+        const VlNode nd(p, q);
+        double lo, hi;
+        if (!vl_interval(P, nd, it, jt, lo, hi)) continue;
+        const double Wpq = P.wp[i * P.n_p + a] * P.wq[j * P.n_q + b];
+        const double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
+        for (int x = 0; x < P.n_x; ++x) {
+          const double y = mid + half * P.yn[x];
+          const double W = Wpq * (half * P.wy[x]);
+          // y' = p'.q' / (|p'| |q'|), p'.q' = -p^2/2 - p q y / 2 + 3 q^2 / 8
+          const double p2 = fma(nd.A, y, nd.Bp), q2 = fma(nd.C, y, nd.Dq);
+          const double num = -0.5 * p * p - 0.5 * p * q * y + 0.375 * q * q;
+          const double den = sqrt(fmax(p2, 0.0) * fmax(q2, 0.0));
+          const double yp = den > 0.0 ? fmin(1.0, fmax(-1.0, num / den)) : 0.0;
+          double Py[kMaxCh], Pyp[kMaxCh];
+          legendre_all(P.n_ch - 1, y, Py);
+          legendre_all(P.n_ch - 1, yp, Pyp);
+          for (int m = 0; m < P.n_pairs; ++m) sum[m] += W * Py[P.pl[m]] * Pyp[P.plp[m]];
+        }
+      }
+    const double nrm = P.rsb[c] * P.rsb[t];
+    for (int m = 0; m < P.n_pairs; ++m) val[(size_t)m * nnz + o] = sum[m] * nrm * P.cnorm[m];
+  }
+}
+
+}  // namespace
+
+wpcd_status assemble_vl(wpcd_grid *g, int n_ch, cudaStream_t s, wpcd_P **out) {
+  if (n_ch < 1 || n_ch > 5) return set_error(WPCD_EINVAL, "n_ch must be in [1, 5]");
+  WPCD_CUDA_TRY(cudaSetDevice(g->device));
+  VlParams P{};
+  P.N = g->N;
+  P.M = g->M;
+  P.n_p = g->n_p;
+  P.n_q = g->n_q;
+  P.n_x = g->n_x;
+  P.n_ch = n_ch;
+  P.n_pairs = pair_count(n_ch);
+  for (int m = 0; m < P.n_pairs; ++m) {
+    P.pl[m] = pair_first(n_ch, m);
+    P.plp[m] = pair_second(n_ch, m);
+    P.cnorm[m] = sqrt((2.0 * P.pl[m] + 1.0) * (2.0 * P.plp[m] + 1.0));
+  }
+  P.pe2 = g->pe2;
+  P.qe2 = g->qe2;
+  P.pn = g->pn;
+  P.wp = g->wp;
+  P.qn = g->qn;
+  P.wq = g->wq;
+  P.yn = g->yn;
+  P.wy = g->wy;
+  P.rsb = g->rsb;
+  const int n_cells = P.N * P.M;
+  cudaEvent_t ev0, ev1, evc, evs;
+  WPCD_CUDA_TRY(cudaEventCreate(&ev0));
+  WPCD_CUDA_TRY(cudaEventCreate(&ev1));
+  WPCD_CUDA_TRY(cudaEventCreate(&evc));
+  WPCD_CUDA_TRY(cudaEventCreate(&evs));
+  int64_t *counts = nullptr;
+  int *err = nullptr;
+  wpcd_P *Pm = new wpcd_P();
+  Pm->grid = g;
+  Pm->device = g->device;
+  Pm->n_ch = n_ch;
+  Pm->prec = WPCD_FP64;
+  Pm->n_pairs = P.n_pairs;
+  auto fail = [&](wpcd_status st) {
+    dev_free(counts);
+    dev_free(err);
+    dev_free(Pm->row_ptr);
+    dev_free(Pm->col);
+    dev_free(Pm->val64);
+    delete Pm;
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    cudaEventDestroy(evc);
+    cudaEventDestroy(evs);
+    return st;
+  };
+  cudaError_t e;
+  if ((e = dev_malloc(&counts, sizeof(int64_t) * n_cells)) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc counts"));
+  if ((e = dev_malloc(&err, sizeof(int))) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc flag"));
+  if ((e = dev_malloc(&Pm->row_ptr, sizeof(int64_t) * (n_cells + 1))) != cudaSuccess)
+    return fail(cuda_error(e, "cudaMalloc row_ptr"));
+  cudaMemsetAsync(err, 0, sizeof(int), s);
+  cudaEventRecord(ev0, s);
+  vl_rows_kernel<<<n_cells, VL_THREADS, 0, s>>>(P, counts, nullptr, nullptr, err);
+  count_launches(1);
+  cudaEventRecord(evc, s);
+  // row pointers: prefix sum of the row lengths on the host
+  std::vector<int64_t> rp(n_cells + 1, 0);
+  int herr = 0;
+  if ((e = cudaMemcpyAsync(rp.data() + 1, counts, sizeof(int64_t) * n_cells, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return fail(cuda_error(e, "variable-limit row lengths"));
+  if (herr) return fail(set_error(WPCD_EINVAL, "variable-limit assembly: more than 8192 node-target pieces in a cell"));
+  for (int c = 0; c < n_cells; ++c) rp[c + 1] += rp[c];
+  const int64_t nz = rp[n_cells];
+  Pm->nnz = nz;
+  if ((e = cudaMemcpyAsync(Pm->row_ptr, rp.data(), sizeof(int64_t) * (n_cells + 1), cudaMemcpyHostToDevice, s)) !=
+      cudaSuccess)
+    return fail(cuda_error(e, "row_ptr upload"));
+  cudaEventRecord(evs, s);
+  if ((e = dev_malloc(&Pm->col, sizeof(int32_t) * (nz > 0 ? nz : 1))) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc col"));
+  if ((e = dev_malloc(&Pm->val64, sizeof(double) * (nz > 0 ? nz : 1) * P.n_pairs)) != cudaSuccess)
+    return fail(cuda_error(e, "cudaMalloc val"));
+  vl_rows_kernel<<<n_cells, VL_THREADS, 0, s>>>(P, nullptr, Pm->row_ptr, Pm->col, err);
+  vl_value_kernel<<<n_cells, VL_THREADS, 0, s>>>(P, Pm->row_ptr, Pm->col, nz, Pm->val64);
+  count_launches(2);
+  cudaEventRecord(ev1, s);
+  if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaEventSynchronize(ev1)) != cudaSuccess)
+    return fail(cuda_error(e, "variable-limit assembly"));
+  cudaEventElapsedTime(&Pm->ms, ev0, ev1);
+  cudaEventElapsedTime(&Pm->ms_phase[0], ev0, evc);
+  cudaEventElapsedTime(&Pm->ms_phase[1], evc, evs);
+  cudaEventElapsedTime(&Pm->ms_phase[2], evs, ev1);
+  dev_free(counts);
+  dev_free(err);
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  cudaEventDestroy(evc);
+  cudaEventDestroy(evs);
+  grid_retain(g);  // P0 keeps its lattice alive
+  *out = Pm;
+  return WPCD_OK;
+}
+
+}  // namespace wpcd

@@ -480,6 +480,7 @@ wpcd_status wpcd_assemble_P(wpcd_problem *pr, int prec, void *stream, wpcd_P **o
   clear_error();
   if (!pr || !out) return set_error(WPCD_EINVAL, "null argument");
   *out = nullptr;
+  if (prec == WPCD_FP64_VL) return assemble_vl(pr->grid, pr->n_ch, static_cast<cudaStream_t>(stream), out);
   return assemble(pr->grid, pr->n_ch, prec, static_cast<cudaStream_t>(stream), out);
   WPCD_GUARD_END
 }
@@ -505,6 +506,7 @@ wpcd_status wpcd_assemble_P_grid(wpcd_grid *g, int n_ch, int prec, void *stream,
   clear_error();
   if (!g || !out) return set_error(WPCD_EINVAL, "null argument");
   *out = nullptr;
+  if (prec == WPCD_FP64_VL) return assemble_vl(g, n_ch, static_cast<cudaStream_t>(stream), out);
   return assemble(g, n_ch, prec, static_cast<cudaStream_t>(stream), out);
   WPCD_GUARD_END
 }

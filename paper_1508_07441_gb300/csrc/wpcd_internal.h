@@ -188,6 +188,8 @@ void grid_retain(wpcd_grid *g);
 void grid_release(wpcd_grid *g);
 // assemble.cu
 wpcd_status assemble(wpcd_grid *g, int n_ch, int prec, cudaStream_t s, wpcd_P **out);
+// assemble_vl.cu: P0 with variable limits (FP64 values)
+wpcd_status assemble_vl(wpcd_grid *g, int n_ch, cudaStream_t s, wpcd_P **out);
 // solve.cu
 wpcd_status resolvent(const wpcd_problem *pr, const double *E, int n_E, double *g, int *j0,
                       double *D, cudaStream_t s);

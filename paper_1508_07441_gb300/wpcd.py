@@ -19,7 +19,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "wpcd.h")
 
 WPCD_OK, WPCD_EINVAL, WPCD_ENOMEM, WPCD_ECUDA = 0, -1, -2, -3
 WPCD_ENOCONV, WPCD_EBREAKDOWN, WPCD_ETIMEOUT, WPCD_ENOBOUND = -4, -5, -6, -7
-WPCD_FP64, WPCD_FP32C = 0, 1
+WPCD_FP64, WPCD_FP32C, WPCD_FP64_VL = 0, 1, 2
 WPCD_SUM_KRYLOV, WPCD_SUM_WYNN = 0, 1
 WPCD_SOLVE_FP64, WPCD_SOLVE_MIXED, WPCD_SOLVE_MIXED_FP64 = 0, 1, 2
 WPCD_GEMM_FP64, WPCD_GEMM_FP32, WPCD_GEMM_TF32X3, WPCD_GEMM_FF, WPCD_GEMM_DIGITS = 0, 1, 2, 3, 4
