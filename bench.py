@@ -342,6 +342,22 @@ def kernel_rooflines(W, pr, w, phases, n_nodes, n_e, stream, flush, peaks, f_sm,
     fpn = fill_flops_per_node(n_ch, pr.n_pairs)
     entry("fill_kernel<FP64,3>", "alu", n_nodes * fpn / (phases[2] * 1e-3) / 1e12, fp64, "TFLOP/s", phases[2], 1,
           f"{fpn} FP64 flops per node x {n_nodes} nodes", src64)
+    # variable-limit assembly (WPCD_FP64_VL) of the same lattice: its value
+    # kernel evaluates n_x GL points on every (node, target) y-interval
+    grid = W.Grid(w["p_edges"], w["q_edges"], *w["nodes"], device=torch.cuda.current_device())
+    vl_ms = []
+    for _ in range(2):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        Pvl = grid.wpcd_assemble_P(n_ch, W.WPCD_FP64_VL, stream=stream)
+        vl_ms.append(Pvl.wpcd_P_timing())
+        vl_points, vl_nnz = Pvl.wpcd_P_work(), Pvl.nnz
+        Pvl.close()
+    grid.close()
+    ph = vl_ms[-1]
+    entry("vl_value_kernel<FP64> (variable limits)", "alu", vl_points * fpn / (ph[2] * 1e-3) / 1e12, fp64, "TFLOP/s",
+          ph[2], 0, f"{fpn} FP64 flops per y point x {vl_points} points (n_x per (node, target) interval; "
+          f"{vl_nnz} nonzeros; rows pass {ph[0]:.2f} ms, columns and values {ph[2]:.2f} ms)", src64)
     P = pr.wpcd_assemble_P(W.WPCD_FP64, stream=stream)
     x64 = torch.randn(2 * dim * n_e, dtype=torch.float64, device="cuda")
     g64 = torch.randn_like(x64)

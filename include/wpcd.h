@@ -234,6 +234,11 @@ wpcd_status wpcd_P_info(const wpcd_P *P, int64_t *nnz, int *n_pairs, int *prec, 
  * ms[1] scan, ms[2] fill pass (values and segmented reduction). */
 wpcd_status wpcd_P_timing(const wpcd_P *P, float ms[3]);
 
+/* Quadrature points the assembly of P evaluated: N M n_p n_q n_x for node
+ * binning (every node mapped once), the (node, target) y-intervals times n_x
+ * for WPCD_FP64_VL. */
+wpcd_status wpcd_P_work(const wpcd_P *P, int64_t *points);
+
 /* Copy P0 out: row_ptr[N*M + 1], col[nnz], val[n_pairs][nnz] as FP64 (FP32C
  * values are widened).  Destinations may be host or device memory; any may
  * be NULL.  Synchronises `stream`. */

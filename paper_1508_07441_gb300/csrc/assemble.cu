@@ -579,6 +579,7 @@ wpcd_status assemble(wpcd_grid *g, int n_ch, int prec, cudaStream_t s, wpcd_P **
   Pm->n_ch = n_ch;
   Pm->prec = prec;
   Pm->n_pairs = P.n_pairs;
+  Pm->work = (int64_t)n_cells * P.n_nodes;  // every node of every cell mapped once
   auto fail = [&](wpcd_status st) {
     dev_free(counts);
     dev_free(sorted);

@@ -30,6 +30,7 @@
 
 #include <climits>
 #include <cstdint>
+#include <cstring>
 #include <vector>
 
 #include "common.cuh"
@@ -77,7 +78,8 @@ __device__ __forceinline__ bool vl_interval(const VlParams &P, const VlNode &nd,
 
 // row lengths (cols == nullptr: counts[c]) or the row's ascending columns
 __global__ void __launch_bounds__(VL_THREADS) vl_rows_kernel(VlParams P, int64_t *counts, const int64_t *row_ptr,
-                                                            int32_t *cols, int *err) {
+                                                            int32_t *cols, int *err,
+                                                            unsigned long long *pieces) {
   __shared__ int keys[VL_KEYS];
   __shared__ int n_keys, n_unique;
   const int c = blockIdx.x, i = c / P.M, j = c % P.M;
@@ -109,6 +111,7 @@ __global__ void __launch_bounds__(VL_THREADS) vl_rows_kernel(VlParams P, int64_t
   }
   __syncthreads();
   const int n = n_keys;
+  if (pieces && threadIdx.x == 0) atomicAdd(pieces, (unsigned long long)n);
   if (n > VL_KEYS) {
     if (threadIdx.x == 0) atomicOr(err, 1);
     return;  // uniform over the CTA
@@ -225,7 +228,7 @@ wpcd_status assemble_vl(wpcd_grid *g, int n_ch, cudaStream_t s, wpcd_P **out) {
   WPCD_CUDA_TRY(cudaEventCreate(&evc));
   WPCD_CUDA_TRY(cudaEventCreate(&evs));
   int64_t *counts = nullptr;
-  int *err = nullptr;
+  int *err = nullptr;  // err[0] overflow flag, err[2..3] piece count (8-byte aligned)
   wpcd_P *Pm = new wpcd_P();
   Pm->grid = g;
   Pm->device = g->device;
@@ -247,22 +250,26 @@ wpcd_status assemble_vl(wpcd_grid *g, int n_ch, cudaStream_t s, wpcd_P **out) {
   };
   cudaError_t e;
   if ((e = dev_malloc(&counts, sizeof(int64_t) * n_cells)) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc counts"));
-  if ((e = dev_malloc(&err, sizeof(int))) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc flag"));
+  if ((e = dev_malloc(&err, 4 * sizeof(int))) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc flag"));
   if ((e = dev_malloc(&Pm->row_ptr, sizeof(int64_t) * (n_cells + 1))) != cudaSuccess)
     return fail(cuda_error(e, "cudaMalloc row_ptr"));
-  cudaMemsetAsync(err, 0, sizeof(int), s);
+  cudaMemsetAsync(err, 0, 4 * sizeof(int), s);
+  unsigned long long *d_pieces = reinterpret_cast<unsigned long long *>(err + 2);
   cudaEventRecord(ev0, s);
-  vl_rows_kernel<<<n_cells, VL_THREADS, 0, s>>>(P, counts, nullptr, nullptr, err);
+  vl_rows_kernel<<<n_cells, VL_THREADS, 0, s>>>(P, counts, nullptr, nullptr, err, d_pieces);
   count_launches(1);
   cudaEventRecord(evc, s);
   // row pointers: prefix sum of the row lengths on the host
   std::vector<int64_t> rp(n_cells + 1, 0);
-  int herr = 0;
+  int herr[4] = {0, 0, 0, 0};
   if ((e = cudaMemcpyAsync(rp.data() + 1, counts, sizeof(int64_t) * n_cells, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(herr, err, 4 * sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess)
     return fail(cuda_error(e, "variable-limit row lengths"));
-  if (herr) return fail(set_error(WPCD_EINVAL, "variable-limit assembly: more than 8192 node-target pieces in a cell"));
+  if (herr[0]) return fail(set_error(WPCD_EINVAL, "variable-limit assembly: more than 8192 node-target pieces in a cell"));
+  unsigned long long n_pieces = 0;
+  std::memcpy(&n_pieces, herr + 2, sizeof(n_pieces));
+  Pm->work = (int64_t)n_pieces * P.n_x;  // y points integrated
   for (int c = 0; c < n_cells; ++c) rp[c + 1] += rp[c];
   const int64_t nz = rp[n_cells];
   Pm->nnz = nz;
@@ -273,7 +280,7 @@ wpcd_status assemble_vl(wpcd_grid *g, int n_ch, cudaStream_t s, wpcd_P **out) {
   if ((e = dev_malloc(&Pm->col, sizeof(int32_t) * (nz > 0 ? nz : 1))) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc col"));
   if ((e = dev_malloc(&Pm->val64, sizeof(double) * (nz > 0 ? nz : 1) * P.n_pairs)) != cudaSuccess)
     return fail(cuda_error(e, "cudaMalloc val"));
-  vl_rows_kernel<<<n_cells, VL_THREADS, 0, s>>>(P, nullptr, Pm->row_ptr, Pm->col, err);
+  vl_rows_kernel<<<n_cells, VL_THREADS, 0, s>>>(P, nullptr, Pm->row_ptr, Pm->col, err, nullptr);
   vl_value_kernel<<<n_cells, VL_THREADS, 0, s>>>(P, Pm->row_ptr, Pm->col, nz, Pm->val64);
   count_launches(2);
   cudaEventRecord(ev1, s);

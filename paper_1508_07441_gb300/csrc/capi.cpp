@@ -546,6 +546,12 @@ wpcd_status wpcd_P_info(const wpcd_P *P, int64_t *nnz, int *n_pairs, int *prec, 
   return WPCD_OK;
 }
 
+wpcd_status wpcd_P_work(const wpcd_P *P, int64_t *points) {
+  if (!P || !points) return set_error(WPCD_EINVAL, "null argument");
+  *points = P->work;
+  return WPCD_OK;
+}
+
 wpcd_status wpcd_P_timing(const wpcd_P *P, float ms[3]) {
   if (!P || !ms) return set_error(WPCD_EINVAL, "null argument");
   for (int i = 0; i < 3; ++i) ms[i] = P->ms_phase[i];

@@ -170,6 +170,7 @@ struct wpcd_P {
   float *val32 = nullptr;       // device [n_pairs][nnz] (FP32C assembly)
   float ms = 0.f;
   float ms_phase[3] = {0.f, 0.f, 0.f};  // count, scan, fill
+  int64_t work = 0;                     // quadrature points evaluated by the assembly
   float *val32_copy = nullptr;          // FP32 values made from FP64 ones (mixed solve)
   float *val_h = nullptr, *val_l = nullptr;  // float-float split of FP64 values (df.cu)
   int64_t *tile_ptr[2] = {nullptr, nullptr};  // row tiles of 2 / 4 cells (spmm_tile.cu): offsets,

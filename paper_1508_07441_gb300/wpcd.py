@@ -71,6 +71,7 @@ _SIGS = {
     "wpcd_launch_count": (ctypes.c_int64, []),
     "wpcd_set_allocator": (ctypes.c_int, [_P, _P, _P]),
     "wpcd_P_timing": (ctypes.c_int, [_P, _F]),
+    "wpcd_P_work": (ctypes.c_int, [_P, _I64]),
     "wpcd_tangent_edges": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, _D]),
     "wpcd_problem_create": (ctypes.c_int, [ctypes.POINTER(wpcd_problem_desc), ctypes.POINTER(_P)]),
     "wpcd_problem_destroy": (None, [_P]),
@@ -449,6 +450,12 @@ class PMatrix:
             self.close()
         except Exception:
             pass
+
+    def wpcd_P_work(self):
+        """Quadrature points the assembly evaluated."""
+        n = ctypes.c_int64()
+        check(lib().wpcd_P_work(self._h, ctypes.byref(n)))
+        return n.value
 
     def wpcd_P_timing(self):
         """(count, scan, fill) device milliseconds of this assembly."""
