@@ -107,6 +107,18 @@ wpcd_status wpcd_set_allocator(wpcd_alloc_fn alloc, wpcd_free_fn free_fn, void *
  * region by differencing. */
 int64_t wpcd_launch_count(void);
 
+/* Test knob of the wait-limit path of the tensor-core GEMMs, on valid input
+ * and without a fault.  kernel 1: the warp-specialised TF32x3 GEMM of the
+ * FP32 inner cycles, role 0 producer, 1 MMA issuer, 2 converters, 3
+ * epilogue; kernel 2: the digit-plane GEMM of the refinement residual, role
+ * 0 (the first operand-copy wait).  Until the knob is cleared (kernel 0),
+ * every launch of that kernel gives the first wait of that role a limit of
+ * zero spins: the wait runs out, the CTA aborts, every copy and MMA already
+ * issued is still waited for (with the full limit) before the tensor memory
+ * is freed, and the operation returns WPCD_ETIMEOUT.  Process-wide, for tests
+ * only; EINVAL for another kernel or role. */
+wpcd_status wpcd_debug_expire_first_wait(int kernel, int role);
+
 /* Step 1, packet grid (Sec. 2.2 Eq. ip, Sec. 2.4 Eq. xij): n_bins + 1 edges
  * of the tangent map k_n = s tan(pi n / (2 (n_bins + 1))), s chosen so that
  * the last edge is k_max; edges[0] = 0.  edges: host, n_bins + 1 doubles.
@@ -208,8 +220,9 @@ wpcd_status wpcd_problem_pair(const wpcd_problem *pr, int l, double *eps, double
  * the limits are (e^2 - Bp) / A for the edges e) is integrated with the
  * n_x-point GL rule mapped onto it; the theta functions are then exact in y.
  * FP64 values (the P0 reports WPCD_FP64), one thread per nonzero element,
- * bit-reproducible; EINVAL if a source cell has more than 8192 (node,
- * target) pieces.
+ * bit-reproducible; EINVAL if a row (source cell) has more than
+ * 3 (N + M) target cells (rounded up to 3/4 of a power of two, 6144 at
+ * most).
  * Runs on `stream` and returns when the assembly has completed (the stream
  * is synchronised twice: for the nonzero count, and at the end).  The P0
  * belongs to the problem's grid and channel count (see wpcd_assemble_P_grid):

@@ -16,10 +16,11 @@
 // in the canonical order, so identical inputs give identical limits):
 //   vl_rows_kernel   one CTA per source cell: every (p, q) node walks its
 //                    targets in increasing y (the next limit is the smaller
-//                    of the next p limit and the next q limit) and appends
-//                    the non-empty ones to a shared-memory list, which is
-//                    sorted and deduplicated: the row length, or (second
-//                    launch) the row's ascending columns;
+//                    of the next p limit and the next q limit) and inserts
+//                    the non-empty ones into a shared-memory hash set of
+//                    the row's targets, which is compacted and sorted: the
+//                    row length, or (second launch) the row's ascending
+//                    columns;
 //   vl_value_kernel  one thread per nonzero element (the paper's own
 //                    decomposition, Sec. 4.2): the sum over the source
 //                    cell's nodes, in a fixed order, of the GL integral over
@@ -30,6 +31,7 @@
 
 #include <climits>
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -40,10 +42,12 @@ namespace wpcd {
 namespace {
 
 constexpr int VL_THREADS = 128;
-constexpr int VL_KEYS = 8192;  // node-target pieces of one source cell
+constexpr int VL_MAX_SLOTS = 8192;  // hash slots for one row's distinct targets, at most
+constexpr int VL_EMPTY = INT_MAX;
 
 struct VlParams {
   int N, M, n_p, n_q, n_x, n_ch, n_pairs;
+  int slot_bits, max_row;  // the row hash set: 2^slot_bits slots, filled to 3/4 at most
   int pl[kMaxPairs], plp[kMaxPairs];
   double cnorm[kMaxPairs];  // sqrt((2l+1)(2l'+1))
   const double *pe2, *qe2, *pn, *wp, *qn, *wq, *yn, *wy, *rsb;
@@ -76,15 +80,40 @@ __device__ __forceinline__ bool vl_interval(const VlParams &P, const VlNode &nd,
   return hi > lo;
 }
 
-// row lengths (cols == nullptr: counts[c]) or the row's ascending columns
+// insert a target into the shared hash set of the row (multiplicative
+// hash, linear probing): 1 new, 0 already present, -1 table full
+__device__ __forceinline__ int vl_insert(int *table, int bits, int key) {
+  const uint32_t mask = (1u << bits) - 1;
+  uint32_t h = ((uint32_t)key * 2654435761u) >> (32 - bits);
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    const int old = atomicCAS(&table[h], VL_EMPTY, key);
+    if (old == VL_EMPTY) return 1;
+    if (old == key) return 0;
+    h = (h + 1) & mask;
+  }
+  return -1;
+}
+
+// row lengths (cols == nullptr: counts[c]) or the row's ascending columns.
+// The nodes' pieces overlap heavily (neighbouring nodes cross nearly the
+// same targets), so each piece goes into a hash set of the row's distinct
+// targets at once; the set is then compacted and sorted.
 __global__ void __launch_bounds__(VL_THREADS) vl_rows_kernel(VlParams P, int64_t *counts, const int64_t *row_ptr,
                                                             int32_t *cols, int *err,
                                                             unsigned long long *pieces) {
-  __shared__ int keys[VL_KEYS];
-  __shared__ int n_keys, n_unique;
+  extern __shared__ int vl_smem[];
+  const int slots = 1 << P.slot_bits;
+  int *table = vl_smem, *keys = vl_smem + slots;
+  __shared__ int n_distinct, n_fill, overflow;
+  __shared__ unsigned long long n_pieces;
   const int c = blockIdx.x, i = c / P.M, j = c % P.M;
-  if (threadIdx.x == 0) n_keys = 0;
+  for (int k = threadIdx.x; k < slots; k += blockDim.x) table[k] = VL_EMPTY;
+  if (threadIdx.x == 0) {
+    n_distinct = n_fill = overflow = 0;
+    n_pieces = 0;
+  }
   __syncthreads();
+  unsigned long long my_pieces = 0;
   for (int node = threadIdx.x; node < P.n_p * P.n_q; node += blockDim.x) {
     const int a = node / P.n_q, b = node % P.n_q;
     const VlNode nd(P.pn[i * P.n_p + a], P.qn[j * P.n_q + b]);
@@ -98,8 +127,12 @@ __global__ void __launch_bounds__(VL_THREADS) vl_rows_kernel(VlParams P, int64_t
       double lo, hi;
       const bool in = it < P.N && jt < P.M;
       if (vl_interval(P, nd, it, jt, lo, hi) && in) {
-        const int k = atomicAdd(&n_keys, 1);
-        if (k < VL_KEYS) keys[k] = it * P.M + jt;
+        ++my_pieces;
+        const int r = vl_insert(table, P.slot_bits, it * P.M + jt);
+        if (r > 0)
+          atomicAdd(&n_distinct, 1);
+        else if (r < 0)
+          overflow = 1;
       }
       const double up = nd.yp(P, it + 1), uq = nd.yq(P, jt);
       const double top = fmin(up, uq);
@@ -109,18 +142,24 @@ __global__ void __launch_bounds__(VL_THREADS) vl_rows_kernel(VlParams P, int64_t
       if (jt < 0) break;
     }
   }
+  if (my_pieces) atomicAdd(&n_pieces, my_pieces);
   __syncthreads();
-  const int n = n_keys;
-  if (pieces && threadIdx.x == 0) atomicAdd(pieces, (unsigned long long)n);
-  if (n > VL_KEYS) {
+  const int n = n_distinct;
+  if (pieces && threadIdx.x == 0) atomicAdd(pieces, n_pieces);
+  if (overflow || n > P.max_row) {
     if (threadIdx.x == 0) atomicOr(err, 1);
     return;  // uniform over the CTA
   }
+  // compact the set (any order), pad to a power of two, sort ascending
+  for (int k = threadIdx.x; k < slots; k += blockDim.x) {
+    const int v = table[k];
+    if (v != VL_EMPTY) keys[atomicAdd(&n_fill, 1)] = v;
+  }
   int np2 = 1;
   while (np2 < n) np2 <<= 1;
+  __syncthreads();
   for (int k = n + threadIdx.x; k < np2; k += blockDim.x) keys[k] = INT_MAX;
   __syncthreads();
-  // bitonic sort, ascending
   for (int k = 2; k <= np2; k <<= 1)
     for (int d = k >> 1; d > 0; d >>= 1) {
       for (int x = threadIdx.x; x < np2; x += blockDim.x) {
@@ -135,19 +174,11 @@ __global__ void __launch_bounds__(VL_THREADS) vl_rows_kernel(VlParams P, int64_t
       }
       __syncthreads();
     }
-  // distinct keys: thread 0 compacts (rows are a few hundred long)
-  if (threadIdx.x == 0) {
-    int m = 0;
-    for (int k = 0; k < n; ++k)
-      if (k == 0 || keys[k] != keys[k - 1]) keys[m++] = keys[k];
-    n_unique = m;
-  }
-  __syncthreads();
   if (!cols) {
-    if (threadIdx.x == 0) counts[c] = n_unique;
+    if (threadIdx.x == 0) counts[c] = n;
   } else {
     const int64_t o = row_ptr[c];
-    for (int k = threadIdx.x; k < n_unique; k += blockDim.x) cols[o + k] = keys[k];
+    for (int k = threadIdx.x; k < n; k += blockDim.x) cols[o + k] = keys[k];
   }
 }
 
@@ -221,6 +252,11 @@ wpcd_status assemble_vl(wpcd_grid *g, int n_ch, cudaStream_t s, wpcd_P **out) {
   P.yn = g->yn;
   P.wy = g->wy;
   P.rsb = g->rsb;
+  // a row's targets lie near the paths of its nodes, each a monotone walk of
+  // at most N + M + 1 cells: the hash set starts with 4 (N + M) slots (a
+  // power of two) and doubles, up to VL_MAX_SLOTS, while a row overflows it
+  P.slot_bits = 6;
+  while ((1 << P.slot_bits) < 4 * (P.N + P.M) && (1 << P.slot_bits) < VL_MAX_SLOTS) ++P.slot_bits;
   const int n_cells = P.N * P.M;
   cudaEvent_t ev0, ev1, evc, evs;
   WPCD_CUDA_TRY(cudaEventCreate(&ev0));
@@ -253,20 +289,35 @@ wpcd_status assemble_vl(wpcd_grid *g, int n_ch, cudaStream_t s, wpcd_P **out) {
   if ((e = dev_malloc(&err, 4 * sizeof(int))) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc flag"));
   if ((e = dev_malloc(&Pm->row_ptr, sizeof(int64_t) * (n_cells + 1))) != cudaSuccess)
     return fail(cuda_error(e, "cudaMalloc row_ptr"));
-  cudaMemsetAsync(err, 0, 4 * sizeof(int), s);
   unsigned long long *d_pieces = reinterpret_cast<unsigned long long *>(err + 2);
-  cudaEventRecord(ev0, s);
-  vl_rows_kernel<<<n_cells, VL_THREADS, 0, s>>>(P, counts, nullptr, nullptr, err, d_pieces);
-  count_launches(1);
-  cudaEventRecord(evc, s);
-  // row pointers: prefix sum of the row lengths on the host
   std::vector<int64_t> rp(n_cells + 1, 0);
   int herr[4] = {0, 0, 0, 0};
-  if ((e = cudaMemcpyAsync(rp.data() + 1, counts, sizeof(int64_t) * n_cells, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(herr, err, 4 * sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-      (e = cudaStreamSynchronize(s)) != cudaSuccess)
-    return fail(cuda_error(e, "variable-limit row lengths"));
-  if (herr[0]) return fail(set_error(WPCD_EINVAL, "variable-limit assembly: more than 8192 node-target pieces in a cell"));
+  size_t vl_smem = 0;
+  cudaEventRecord(ev0, s);
+  for (;;) {
+    P.max_row = 3 * (1 << P.slot_bits) / 4;
+    vl_smem = 2 * sizeof(int) * ((size_t)1 << P.slot_bits);  // hash set + sort buffer
+    if ((e = cudaFuncSetAttribute(vl_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vl_smem)) !=
+        cudaSuccess)
+      return fail(cuda_error(e, "variable-limit rows kernel attribute"));
+    cudaMemsetAsync(err, 0, 4 * sizeof(int), s);
+    vl_rows_kernel<<<n_cells, VL_THREADS, vl_smem, s>>>(P, counts, nullptr, nullptr, err, d_pieces);
+    count_launches(1);
+    cudaEventRecord(evc, s);
+    // row pointers: prefix sum of the row lengths on the host
+    if ((e = cudaMemcpyAsync(rp.data() + 1, counts, sizeof(int64_t) * n_cells, cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(herr, err, 4 * sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+      return fail(cuda_error(e, "variable-limit row lengths"));
+    if (!herr[0]) break;
+    if ((1 << P.slot_bits) >= VL_MAX_SLOTS) {
+      char msg[96];
+      std::snprintf(msg, sizeof msg, "variable-limit assembly: a row has more than %d targets", P.max_row);
+      return fail(set_error(WPCD_EINVAL, msg));
+    }
+    ++P.slot_bits;
+  }
   unsigned long long n_pieces = 0;
   std::memcpy(&n_pieces, herr + 2, sizeof(n_pieces));
   Pm->work = (int64_t)n_pieces * P.n_x;  // y points integrated
@@ -280,7 +331,7 @@ wpcd_status assemble_vl(wpcd_grid *g, int n_ch, cudaStream_t s, wpcd_P **out) {
   if ((e = dev_malloc(&Pm->col, sizeof(int32_t) * (nz > 0 ? nz : 1))) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc col"));
   if ((e = dev_malloc(&Pm->val64, sizeof(double) * (nz > 0 ? nz : 1) * P.n_pairs)) != cudaSuccess)
     return fail(cuda_error(e, "cudaMalloc val"));
-  vl_rows_kernel<<<n_cells, VL_THREADS, 0, s>>>(P, nullptr, Pm->row_ptr, Pm->col, err, nullptr);
+  vl_rows_kernel<<<n_cells, VL_THREADS, vl_smem, s>>>(P, nullptr, Pm->row_ptr, Pm->col, err, nullptr);
   vl_value_kernel<<<n_cells, VL_THREADS, 0, s>>>(P, Pm->row_ptr, Pm->col, nz, Pm->val64);
   count_launches(2);
   cudaEventRecord(ev1, s);

@@ -417,6 +417,21 @@ int wpcd_version(void) { return 100; }
 
 int64_t wpcd_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
+wpcd_status wpcd_debug_expire_first_wait(int kernel, int role) {
+  clear_error();
+  if (kernel == 0) {
+    g_ws_expire_role.store(-1);
+    g_oz_expire_first.store(0);
+  } else if (kernel == 1 && role >= 0 && role <= 3) {
+    g_ws_expire_role.store(role);
+  } else if (kernel == 2 && role == 0) {
+    g_oz_expire_first.store(1);
+  } else {
+    return set_error(WPCD_EINVAL, "kernel 1 takes roles 0-3, kernel 2 role 0, kernel 0 clears");
+  }
+  return WPCD_OK;
+}
+
 wpcd_status wpcd_set_allocator(wpcd_alloc_fn alloc, wpcd_free_fn free_fn, void *user) {
   clear_error();
   if ((alloc == nullptr) != (free_fn == nullptr)) return set_error(WPCD_EINVAL, "give both allocator callbacks or neither");

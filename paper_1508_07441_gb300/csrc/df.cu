@@ -243,6 +243,7 @@ wpcd_status df_gemm_op(wpcd_problem *pr, bool use_O, bool digits, const double *
   if (digits) {
     if (!oz_supported(pr)) return set_error(WPCD_EINVAL, "the digit-plane tensor-core GEMM needs N <= 256");
     st = oz_prepare(pr, s);
+    if (st == WPCD_OK) st = tc_clear(pr, s);
     if (st != WPCD_OK) return st;
   }
   const size_t dim = (size_t)pr->n_ch * pr->N * pr->M;

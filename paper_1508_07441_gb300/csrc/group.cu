@@ -1321,6 +1321,7 @@ wpcd_status solve_group(int n_prob, wpcd_problem *const *prs, const wpcd_P *cons
         if (st != WPCD_OK) return st;
         gr.tcp.push_back(TcGroupProb{prs[g], 2 * mt.eoff[g], 2LL * prs[g]->M * n_E[g]});
       }
+      if (wpcd_status st = tc_clear(prs[0], s); st != WPCD_OK) return st;
       gr.tc = true;
     }
   }

@@ -72,6 +72,7 @@ struct OzParams {
   double *C;              // FP64 output, or
   float *Ch, *Cl;         // float-float output
   int *err;
+  int expire_first;       // nonzero: thread 0's first copy wait runs out at once
 };
 
 // byte offset of element (row r, k) in a [rows / 8][2][8][8] bf16 block
@@ -185,6 +186,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzParams p) {
   uint32_t g = 0;                      // chunks begun by this CTA (stage ring position)
   uint32_t g_issued = 0, g_seen = 0;   // thread 0: A copies issued / seen complete
   uint32_t tl = 0;                     // tiles finished (bar_done phase)
+  WaitLimit lim(tid == 0 && p.expire_first != 0);
   // chunk c of a tile: thread (j, kp) converts rows 2 kp, 2 kp + 1 of column j
   const int j = tid & 31, kp = tid >> 5;
   // the CTA's chunks in order: chunk q is K chunk q % nK of its tile q / nK;
@@ -262,7 +264,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzParams p) {
       if (bail) break;
       if (tid == 0) {
         tc_fence_after();
-        ok = mbar_wait(&bar_a[s], use & 1);
+        ok = mbar_wait(&bar_a[s], use & 1, lim.next());
         if (ok) {
           g_seen = g + 1;
           // descriptors of the plane blocks: the start address field is
@@ -365,6 +367,8 @@ bool g_oz_attr[64];
 
 }  // namespace
 
+std::atomic<int> g_oz_expire_first{0};
+
 bool oz_supported(const wpcd_problem *pr) { return pr->N >= 1 && pr->N <= OZ_MAX_RT * OZ_M; }
 
 // the refinement products run on the tensor cores (digit planes) when N <=
@@ -460,6 +464,7 @@ wpcd_status oz_gemm(const wpcd_problem *pr, bool use_O, const float *Bh, const f
   p.Ch = Ch;
   p.Cl = Cl;
   p.err = pr->d.tc_err;
+  p.expire_first = g_oz_expire_first.load(std::memory_order_relaxed);
   int *F = nullptr;
   WPCD_CUDA_TRY(pool_malloc(&F, sizeof(int) * (size_t)n_ch * ncol, s));
   p.FB = F;

@@ -1880,6 +1880,7 @@ wpcd_status solve(wpcd_problem *pr, const wpcd_P *Pc, const double *E, int n_E,
   }
   WPCD_CUDA_TRY(cudaSetDevice(pr->device));
   if (n_E == 0) return WPCD_OK;
+  if (wpcd_status st = tc_clear(pr, s); st != WPCD_OK) return st;
   wpcd_status worst = WPCD_OK;
   if (opt.method == WPCD_SUM_WYNN) {
     for (int e = 0; e < n_E; ++e) {
@@ -2088,6 +2089,7 @@ wpcd_status channel_gemm(wpcd_problem *pr, int which, int mode, const void *g, c
   if (mode == WPCD_GEMM_TF32X3) {
     if (!tc_supported(pr)) return set_error(WPCD_EINVAL, "the tensor-core GEMM needs N <= 512");
     wpcd_status st = tc_prepare(pr, s);
+    if (st == WPCD_OK) st = tc_clear(pr, s);
     if (st != WPCD_OK) return st;
     {
       LaunchTimer t(ms, s);

@@ -353,7 +353,10 @@ struct TcWsParams {
   int RT, n_tiles, nsa, nsb, nr, n_acc;  // RT: the largest row-tile count of any tile
   uint32_t raw_bytes, tmem_cols;
   int *err;
+  int expire_role;  // -1, or the role (WsRole) whose first wait runs out at once
 };
+
+enum WsRole { WS_PRODUCER = 0, WS_MMA = 1, WS_CONVERTER = 2, WS_EPILOGUE = 3 };
 
 // one output tile: 128 columns (col0 ..) of one channel block C = A X'
 // ([n][ncol] floats at C), A packed as [nK][RT][hi | lo] TF32 blocks; the
@@ -468,8 +471,9 @@ __device__ __forceinline__ void expect_tx(uint64_t *bar, uint32_t bytes) {
 
 // bounded wait that also ends when another role has aborted; running out
 // of the limit aborts the CTA and sets the error word
-__device__ __forceinline__ bool ws_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *err) {
-  for (long long i = 0; i < TC_SPIN_LIMIT; ++i) {
+__device__ __forceinline__ bool ws_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *err,
+                                        long long limit) {
+  for (long long i = 0; i < limit; ++i) {
     if (mbar_try(bar, parity)) return true;
     if (*abort_flag) return false;
   }
@@ -529,6 +533,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
   if (warp == 0) {
     // ---------------- producer ----------------
     if (lane == 0) {
+      WaitLimit lim(p.expire_role == WS_PRODUCER);
       int last_a[WS_MAX_A], last_r[WS_MAX_R];
       for (int i = 0; i < WS_MAX_A; ++i) last_a[i] = -1;
       for (int i = 0; i < WS_MAX_R; ++i) last_r[i] = -1;
@@ -538,7 +543,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
         const WsTile T = tiles.get((int)blockIdx.x + lt * (int)gridDim.x);
         for (int c = 0; c < T.nK; ++c, ++q) {
           const int sr = q % p.nr;
-          if (q >= p.nr && !(ok = ws_wait(&bars.r_empty[sr], (uint32_t)(q / p.nr - 1) & 1, &abort_flag, p.err)))
+          if (q >= p.nr && !(ok = ws_wait(&bars.r_empty[sr], (uint32_t)(q / p.nr - 1) & 1, &abort_flag, p.err, lim.next())))
             break;
           // the whole box counts, zero-filled parts included; rows of the
           // next channel that a last chunk reaches are masked by the converters
@@ -548,7 +553,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
           if (SCALE_G) tma_2d(dst + TC_KC * WS_BN * 4, T.tmg, (int)T.col0, T.y0 + c * TC_KC, &bars.r_full[sr]);
           last_r[sr] = q;
           const int sa = q % p.nsa;
-          if (q >= p.nsa && !(ok = ws_wait(&bars.a_empty[sa], (uint32_t)(q / p.nsa - 1) & 1, &abort_flag, p.err)))
+          if (q >= p.nsa && !(ok = ws_wait(&bars.a_empty[sa], (uint32_t)(q / p.nsa - 1) & 1, &abort_flag, p.err, lim.next())))
             break;
           const uint32_t abytes = (uint32_t)T.RT * TC_A_BLOCK;
           expect_tx(&bars.a_full[sa], abytes);
@@ -567,19 +572,21 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       const uint32_t idesc = tc_idesc(WS_BN);
+      WaitLimit lim(p.expire_role == WS_MMA);
       bool ok = true;
       int q = 0;
       for (int lt = 0; lt < my_tiles && ok; ++lt) {
         const int buf = lt % p.n_acc;
-        if (lt >= p.n_acc && !(ok = ws_wait(&bars.t_empty[buf], (uint32_t)(lt / p.n_acc - 1) & 1, &abort_flag, p.err)))
+        if (lt >= p.n_acc && !(ok = ws_wait(&bars.t_empty[buf], (uint32_t)(lt / p.n_acc - 1) & 1, &abort_flag, p.err,
+                                          lim.next())))
           break;
         tc_fence_after();
         const WsTile T = tiles.get((int)blockIdx.x + lt * (int)gridDim.x);
         const uint32_t d0 = tmem + (uint32_t)(buf * RTM * WS_BN);
         for (int c = 0; c < T.nK; ++c, ++q) {
           const int sa = q % p.nsa, sb = q % p.nsb;
-          if (!(ok = ws_wait(&bars.a_full[sa], (uint32_t)(q / p.nsa) & 1, &abort_flag, p.err))) break;
-          if (!(ok = ws_wait(&bars.b_full[sb], (uint32_t)(q / p.nsb) & 1, &abort_flag, p.err))) break;
+          if (!(ok = ws_wait(&bars.a_full[sa], (uint32_t)(q / p.nsa) & 1, &abort_flag, p.err, lim.next()))) break;
+          if (!(ok = ws_wait(&bars.b_full[sb], (uint32_t)(q / p.nsb) & 1, &abort_flag, p.err, lim.next()))) break;
           tc_fence_after();
           const uint32_t a0 = smem_u32(a_ring + (size_t)sa * RTM * TC_A_BLOCK);
           const uint32_t b0 = smem_u32(b_ring + (size_t)sb * WS_B_STAGE);
@@ -610,6 +617,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
     // ---------------- converters ----------------
     const int ct = tid - 64;
     constexpr int ITEMS = (TC_KC / 4) * WS_BN / WS_CONV;
+    WaitLimit lim(p.expire_role == WS_CONVERTER);
     bool ok = true;
     int q = 0;
     for (int lt = 0; lt < my_tiles && ok; ++lt) {
@@ -618,7 +626,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
       const int valid_cols = (int)min((int64_t)WS_BN, T.ncol - col0);
       for (int c = 0; c < T.nK; ++c, ++q) {
         const int sr = q % p.nr, sb = q % p.nsb;
-        if (!(ok = ws_wait(&bars.r_full[sr], (uint32_t)(q / p.nr) & 1, &abort_flag, p.err))) break;
+        if (!(ok = ws_wait(&bars.r_full[sr], (uint32_t)(q / p.nr) & 1, &abort_flag, p.err, lim.next()))) break;
         const float2 *rx = reinterpret_cast<const float2 *>(r_ring + (size_t)sr * p.raw_bytes);
         const float2 *rg = rx + TC_KC * WS_BN / 2;
         float2 xv[ITEMS][4], gv[ITEMS][4];
@@ -636,7 +644,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
           }
         }
         mbar_arrive(&bars.r_empty[sr]);
-        if (q >= p.nsb && !(ok = ws_wait(&bars.b_empty[sb], (uint32_t)(q / p.nsb - 1) & 1, &abort_flag, p.err)))
+        if (q >= p.nsb && !(ok = ws_wait(&bars.b_empty[sb], (uint32_t)(q / p.nsb - 1) & 1, &abort_flag, p.err, lim.next())))
           break;
         unsigned char *bhi = b_ring + (size_t)sb * WS_B_STAGE, *blo = bhi + WS_B_HALF;
 #pragma unroll
@@ -676,13 +684,14 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
   } else {
     // ---------------- epilogue ----------------
     const int lg = warp & 3;
+    WaitLimit lim(p.expire_role == WS_EPILOGUE);
     bool ok = true;
     for (int lt = 0; lt < my_tiles && ok; ++lt) {
       const WsTile T = tiles.get((int)blockIdx.x + lt * (int)gridDim.x);
       const int n = T.n;
       const int64_t col0 = T.col0, ncol = T.ncol;
       const int buf = lt % p.n_acc;
-      ok = ws_wait(&bars.t_full[buf], (uint32_t)(lt / p.n_acc) & 1, &abort_flag, p.err);
+      ok = ws_wait(&bars.t_full[buf], (uint32_t)(lt / p.n_acc) & 1, &abort_flag, p.err, lim.next());
       // the TMEM loads below are warp-collective: the warp decides together
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) break;
@@ -774,6 +783,8 @@ TcShape tc_shape(int n) {
 
 }  // namespace
 
+std::atomic<int> g_ws_expire_role{-1};
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
 // against libcuda)
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -823,6 +834,7 @@ wpcd_status launch_ws(const Tiles &tiles, int n_tiles, int RT, bool scale_g, boo
   q.raw_bytes = w.raw_bytes;
   q.tmem_cols = w.tmem_cols;
   q.err = err;
+  q.expire_role = g_ws_expire_role.load(std::memory_order_relaxed);
   const int grid = std::max(1, std::min(n_tiles, sm_count[device] > 0 ? sm_count[device] : 152));
   if (scale_g)
     tc_gemm_ws_kernel<true, false, Tiles><<<grid, WS_THREADS, w.smem, s>>>(tiles, q);
@@ -1000,12 +1012,22 @@ wpcd_status tc_gemm_group(const TcGroupProb *gp, int n_prob, bool use_O, const f
 }
 
 // nonzero if a tensor-core GEMM of this problem ran out of a wait limit
+// since the last check or clear; the word is cleared for the next operation
 wpcd_status tc_check(const wpcd_problem *pr, cudaStream_t s) {
   if (!pr->d.tc_err) return WPCD_OK;
   int h = 0;
   WPCD_CUDA_TRY(cudaMemcpyAsync(&h, pr->d.tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   WPCD_CUDA_TRY(cudaStreamSynchronize(s));
-  if (h) return set_error(WPCD_ETIMEOUT, "tensor-core GEMM wait limit reached");
+  if (!h) return WPCD_OK;
+  WPCD_CUDA_TRY(cudaMemsetAsync(pr->d.tc_err, 0, sizeof(int), s));
+  return set_error(WPCD_ETIMEOUT, "tensor-core GEMM wait limit reached");
+}
+
+// a clean error word at the start of an operation that ends in tc_check, so
+// that a word left set by an operation that returned early is not reported
+// against the next one
+wpcd_status tc_clear(const wpcd_problem *pr, cudaStream_t s) {
+  if (pr->d.tc_err) WPCD_CUDA_TRY(cudaMemsetAsync(pr->d.tc_err, 0, sizeof(int), s));
   return WPCD_OK;
 }
 

@@ -34,11 +34,25 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
 }
 
 // bounded wait for the completion of the phase with the given parity
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-  for (long long i = 0; i < TC_SPIN_LIMIT; ++i)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit = TC_SPIN_LIMIT) {
+  for (long long i = 0; i < limit; ++i)
     if (mbar_try(bar, parity)) return true;
   return false;
 }
+
+// The spin limit of one thread's successive waits.  The host can give the
+// first wait of one role a limit of zero, so that it runs out on valid input
+// and the abort path is exercised without a fault; every later wait, and
+// every wait that drains copies or MMAs in flight, keeps the full limit.
+struct WaitLimit {
+  long long first;
+  __device__ __forceinline__ explicit WaitLimit(bool expire_first) : first(expire_first ? 0 : TC_SPIN_LIMIT) {}
+  __device__ __forceinline__ long long next() {
+    const long long l = first;
+    first = TC_SPIN_LIMIT;
+    return l;
+  }
+};
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }

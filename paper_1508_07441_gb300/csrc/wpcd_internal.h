@@ -237,6 +237,13 @@ wpcd_status tc_gemm_group(const TcGroupProb *gp, int n_prob, bool use_O, const f
 wpcd_status tc_gemm(const wpcd_problem *pr, bool use_O, const float *G, const float *X, const float *S, float *C,
                     int64_t ncol, cudaStream_t s);
 wpcd_status tc_check(const wpcd_problem *pr, cudaStream_t s);
+wpcd_status tc_clear(const wpcd_problem *pr, cudaStream_t s);
+// test knobs of the abort path: the role of the warp-specialised GEMM (0
+// producer, 1 MMA issuer, 2 converters, 3 epilogue; -1 none) whose first
+// wait runs out at once, and whether the digit-plane GEMM's first copy wait
+// does
+extern std::atomic<int> g_ws_expire_role;
+extern std::atomic<int> g_oz_expire_first;
 // oz_gemm.cu: FP64-class channel-block products from bf16 digit planes on
 // the tensor cores (float-float panel in, FP64 or float-float out), N <= 256
 bool oz_supported(const wpcd_problem *pr);

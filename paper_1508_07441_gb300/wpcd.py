@@ -69,6 +69,7 @@ _SIGS = {
     "wpcd_last_error": (ctypes.c_char_p, []),
     "wpcd_version": (ctypes.c_int, []),
     "wpcd_launch_count": (ctypes.c_int64, []),
+    "wpcd_debug_expire_first_wait": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
     "wpcd_set_allocator": (ctypes.c_int, [_P, _P, _P]),
     "wpcd_P_timing": (ctypes.c_int, [_P, _F]),
     "wpcd_P_work": (ctypes.c_int, [_P, _I64]),
@@ -179,6 +180,13 @@ def _tensor_ptr(t):
 # ---------------------------------------------------------------------------
 def wpcd_launch_count() -> int:
     return int(lib().wpcd_launch_count())
+
+
+def wpcd_debug_expire_first_wait(kernel: int, role: int = 0):
+    """Test knob: the first wait of `role` in every launch of tensor-core GEMM
+    `kernel` (1 warp-specialised TF32x3, 2 digit-plane) runs out at once, so
+    the operation returns WPCD_ETIMEOUT on valid input; kernel 0 clears it."""
+    check(lib().wpcd_debug_expire_first_wait(kernel, role))
 
 
 # device allocator callbacks: alloc(bytes, device, stream, user) -> pointer,

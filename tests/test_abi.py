@@ -107,6 +107,16 @@ def test_set_allocator_argument_checks(W):
     assert L.wpcd_set_allocator(None, None, None) == W.WPCD_OK
 
 
+def test_wait_limit_knob_argument_checks(W):
+    """the test knob of the tensor-core wait-limit path takes kernel 1 with
+    roles 0-3, kernel 2 with role 0, and kernel 0 (clear); nothing else"""
+    L = W.lib()
+    for kernel, role in ((1, 4), (1, -1), (2, 1), (3, 0), (-1, 0)):
+        assert L.wpcd_debug_expire_first_wait(kernel, role) == W.WPCD_EINVAL, (kernel, role)
+    for kernel, role in ((1, 0), (1, 3), (2, 0), (0, 0)):
+        assert L.wpcd_debug_expire_first_wait(kernel, role) == W.WPCD_OK, (kernel, role)
+
+
 def test_no_cpu_fallback_when_library_missing(W, monkeypatch, tmp_path):
     monkeypatch.setattr(W, "LIB_PATH", str(tmp_path / "missing.so"))
     monkeypatch.setattr(W, "_lib", None)

@@ -30,10 +30,8 @@ def _edges(N, M, jitter):
     return inputs.jittered_edges(N, 20.0, jitter), inputs.jittered_edges(M, 20.0, jitter + 1)
 
 
-@pytest.mark.parametrize("N,M,nodes,n_ch,jit", [(20, 16, (4, 4, 8), 1, None), (12, 14, (3, 5, 6), 3, None),
-                                               (17, 23, (4, 6, 5), 2, 11), (26, 22, (8, 8, 8), 5, 21)])
-def test_vl_assembly_matches_oracle(W, orc, N, M, nodes, n_ch, jit):
-    pe, qe = _edges(N, M, jit)
+def _check_vl(W, orc, pe, qe, nodes, n_ch):
+    N, M = len(pe) - 1, len(qe) - 1
     grid = W.Grid(pe, qe, *nodes)
     P = grid.wpcd_assemble_P(n_ch, W.WPCD_FP64_VL)
     rp, col, val = P.wpcd_P_export()
@@ -47,6 +45,33 @@ def test_vl_assembly_matches_oracle(W, orc, N, M, nodes, n_ch, jit):
     assert np.all(np.abs(val.T - ref["val"]) <= bar), np.max(np.abs(val.T - ref["val"]) / bar)
     again = grid.wpcd_assemble_P(n_ch, W.WPCD_FP64_VL).wpcd_P_export()
     assert all(np.array_equal(x, y) for x, y in zip((rp, col, val), again))
+    return np.diff(rp).max()
+
+
+@pytest.mark.parametrize("N,M,nodes,n_ch,jit", [(20, 16, (4, 4, 8), 1, None), (12, 14, (3, 5, 6), 3, None),
+                                               (17, 23, (4, 6, 5), 2, 11), (26, 22, (8, 8, 8), 5, 21)])
+def test_vl_assembly_matches_oracle(W, orc, N, M, nodes, n_ch, jit):
+    pe, qe = _edges(N, M, jit)
+    _check_vl(W, orc, pe, qe, nodes, n_ch)
+
+
+def test_vl_assembly_fine_lattice(W, orc):
+    """150 x 150 bins, 8 x 8 nodes: up to about 9000 (node, target) pieces
+    per source cell, which the row's hash set of distinct targets (about
+    300) absorbs"""
+    from paper_1508_07441_gb300 import inputs
+
+    pe = inputs.tangent_edges(150, 20.0)
+    assert _check_vl(W, orc, pe, pe, (8, 8, 2), 1) > 250
+
+
+def test_vl_assembly_row_beyond_first_hash_size(W, orc):
+    """60 fine bins and one coarse outer bin, 16 x 16 nodes: the coarse cells'
+    rows hold about 530 targets, more than the first hash set of 4 (N + M)
+    slots takes (384 = 3/4 of 512), so the row pass runs again with twice
+    the slots"""
+    pe = np.concatenate([np.linspace(0.0, 4.0, 61), [8.0]])
+    assert _check_vl(W, orc, pe, pe, (16, 16, 2), 1) > 384
 
 
 def test_vl_solve_matches_oracle(W, orc):
