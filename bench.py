@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--warm-test", type=int, default=512)
     ap.add_argument("--no-batching", action="store_true")
     ap.add_argument("--no-precision-stress", action="store_true")
-    ap.add_argument("--kernel", choices=["spmv32", "spmv64", "spmm32", "spmm64"], default=None,
+    ap.add_argument("--kernel", choices=["spmv32", "spmv64", "spmm32", "spmm64", "asm64", "asm32c", "asmvl"],
+                    default=None,
                     help="time one kernel of the path alone on the workload's lattice (for profiling)")
     ap.add_argument("--kernel-reps", type=int, default=5)
     return ap.parse_args()
@@ -605,7 +606,10 @@ def run_kernel(args):
     """One kernel of the path on the workload's lattice (FP64 assembly, then
     the kernel's tuning, then --kernel-reps timed launches, each after an L2
     flush): spmv32 / spmv64 the one-right-hand-side SpMV with FP32 / FP64
-    values and vectors, spmm32 / spmm64 the SpMM over --n-energies energies."""
+    values and vectors, spmm32 / spmm64 the SpMM over --n-energies energies;
+    asm64 / asm32c / asmvl --kernel-reps assemblies of P0 (node-binned FP64
+    and FP32C, variable-limit FP64), each after an L2 flush, with the device
+    time of each phase."""
     import numpy as np
     import torch
 
@@ -615,6 +619,18 @@ def run_kernel(args):
     torch.cuda.set_device(0)
     w = inputs.workload(args.workload)
     pr = W.Problem(w["p_edges"], w["q_edges"], *w["nodes"], w["n_ch"], w["V"], w["a"], n_pair_nodes=8)
+    if args.kernel.startswith("asm"):
+        prec = {"asm64": W.WPCD_FP64, "asm32c": W.WPCD_FP32C, "asmvl": W.WPCD_FP64_VL}[args.kernel]
+        flush = L2Flush()
+        phases = []
+        for _ in range(args.kernel_reps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            Pk = pr.wpcd_assemble_P(prec)
+            phases.append(Pk.wpcd_P_timing())
+            Pk.close()
+        print(json.dumps({"kernel": args.kernel, "phases_ms": phases, "nnz": pr.wpcd_assemble_P(prec).nnz}))
+        return 0
     P = pr.wpcd_assemble_P(W.WPCD_FP64)
     B = 1 if args.kernel.startswith("spmv") else args.n_energies
     fp32 = args.kernel.endswith("32")

@@ -34,15 +34,22 @@
 namespace wpcd {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;  // count pass: threads per source cell
+constexpr int kFill = 128;     // fill pass: threads per source cell (np2 / 128 sorted elements each)
 constexpr uint32_t kInvalid = 0xFFFFFFFFu;
 
 struct AsmParams {
   int N, M, n_p, n_q, n_x, n_nodes, np2, nbits, n_ch, n_pairs;
+  uint64_t nx_magic;  // ceil(2^32 / n_x): node / n_x by a multiply and a shift
   int pl[kMaxPairs], plp[kMaxPairs];
   double cnorm[kMaxPairs];  // sqrt((2l+1)(2l'+1))
   const double *pe2, *qe2, *pn, *wp, *qn, *wq, *yn, *wy, *rsb;
 };
+
+// n / d for 0 <= n < 2^13 and d <= 2^13 from magic = ceil(2^32 / d): with
+// magic d = 2^32 + r, 0 <= r < d, the product n magic / 2^32 exceeds n / d by
+// n r / (d 2^32) < 1 / d, too little to reach the next integer
+__device__ __forceinline__ int div_magic(int n, uint64_t magic) { return (int)(((uint64_t)n * magic) >> 32); }
 
 __device__ __forceinline__ int bin_search(const long long *e2, int n, long long x) {
   // number of interior squared edges e2[1..n-1] that are <= x
@@ -61,66 +68,7 @@ struct BinConst {
   double A, Bp, C, D;
 };
 
-// Bitonic sort of n = E * blockDim.x keys (ascending) with the keys held in
-// registers: thread t owns s[t E .. t E + E - 1].  A compare-exchange at
-// distance j runs inside the thread for j < E, between lanes of a warp
-// (shuffles) for j < 32 E, and through shared memory only beyond that.
-template <int E>
-__device__ void bitonic_sort_reg(uint32_t *s, int n) {
-  const int t = threadIdx.x;
-  uint32_t v[E];
-#pragma unroll
-  for (int e = 0; e < E; ++e) v[e] = s[t * E + e];
-  for (int k = 2; k <= n; k <<= 1) {
-    for (int j = k >> 1; j >= E; j >>= 1) {
-      if (j < 32 * E) {
-        const int d = j / E;  // partner lane distance
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const uint32_t p = __shfl_xor_sync(0xffffffffu, v[e], d);
-          const int i = t * E + e;
-          const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
-          v[e] = keep_min ? min(v[e], p) : max(v[e], p);
-        }
-      } else {
-        __syncthreads();  // the previous exchange has been read
-#pragma unroll
-        for (int e = 0; e < E; ++e) s[t * E + e] = v[e];
-        __syncthreads();
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int i = t * E + e;
-          const uint32_t p = s[i ^ j];
-          const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
-          v[e] = keep_min ? min(v[e], p) : max(v[e], p);
-        }
-      }
-    }
-#pragma unroll
-    for (int jj = E / 2; jj >= 1; jj >>= 1) {
-      if (jj < k) {
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int f = e ^ jj;
-          if (f > e) {
-            const bool up = ((t * E + e) & k) == 0;
-            const uint32_t a = v[e], b = v[f];
-            if ((a > b) == up) {
-              v[e] = b;
-              v[f] = a;
-            }
-          }
-        }
-      }
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int e = 0; e < E; ++e) s[t * E + e] = v[e];
-  __syncthreads();
-}
-
-// shared-memory bitonic sort for any power-of-two n (used below 256 keys)
+// shared-memory bitonic sort for any power-of-two n (a row's distinct targets)
 template <int NT>
 __device__ void bitonic_sort(uint32_t *s, int n) {
   // n is a power of two; ascending
@@ -141,18 +89,75 @@ __device__ void bitonic_sort(uint32_t *s, int n) {
   }
 }
 
-__global__ void __launch_bounds__(kThreads) count_kernel(AsmParams P, int64_t *counts,
-                                                         uint32_t *sorted) {
+constexpr int kWarps = kThreads / 32;
+
+// exclusive prefix sum of v[0 .. n) in shared memory, in place; called by
+// every thread after v is written, returns after a barrier
+__device__ void block_exclusive_scan(int *v, int n, int *warp_tot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int chunk = (n + kThreads - 1) / kThreads;
+  const int b = min(n, (int)threadIdx.x * chunk), e = min(n, b + chunk);
+  int s = 0;
+  for (int k = b; k < e; ++k) s += v[k];
+  int incl = s;
+  for (int d = 1; d < 32; d <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += u;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  int run = incl - s;
+  for (int w = 0; w < warp; ++w) run += warp_tot[w];
+  for (int k = b; k < e; ++k) {
+    const int t = v[k];
+    v[k] = run;
+    run += t;
+  }
+  __syncthreads();
+}
+
+// insert a key into a shared hash set of 2^bits slots (multiplicative hash,
+// linear probing; the set has at least twice as many slots as keys): true
+// if the key was not there yet
+__device__ __forceinline__ bool set_insert(uint32_t *table, int bits, uint32_t key) {
+  const uint32_t mask = (1u << bits) - 1u;
+  uint32_t h = (key * 2654435761u) >> (32 - bits);
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    const uint32_t old = atomicCAS(&table[h], kInvalid, key);
+    if (old == kInvalid) return true;
+    if (old == key) return false;
+    h = (h + 1) & mask;
+  }
+  return false;
+}
+
+// Count pass of one source cell (R = np2 / kThreads nodes per thread; node
+// n = warp * 32 R + k * 32 + lane, so each warp holds consecutive nodes).
+// Every node is binned; the distinct targets go into a shared hash set and
+// are sorted (a row has tens to a few hundred); each node takes its
+// target's rank by binary search; then a stable counting sort places the
+// nodes rank by rank in node order: within a warp by warp-match, across
+// warps by per-(warp, rank) counts.  The result, the packed keys
+// (target << nbits | node) in ascending order, is the one a full sort of
+// the keys gives, at a cost linear in the node count.
+template <int R>
+__global__ void __launch_bounds__(kThreads) count_kernel(AsmParams P, int64_t *counts, uint32_t *sorted) {
   extern __shared__ __align__(16) unsigned char smem[];
   long long *pe2 = reinterpret_cast<long long *>(smem);
   long long *qe2 = pe2 + (P.N + 1);
   BinConst *abk = reinterpret_cast<BinConst *>(qe2 + (P.M + 1));  // per (a, b)
   double *ys = reinterpret_cast<double *>(abk + P.n_p * P.n_q);
-  uint32_t *keys = reinterpret_cast<uint32_t *>(ys + P.n_x);
-  __shared__ int red[kThreads / 32];
+  // 4 np2 words: the hash set (2 np2 slots), then the per-warp counts
+  uint32_t *table = reinterpret_cast<uint32_t *>(ys + P.n_x);
+  uint16_t *wc = reinterpret_cast<uint16_t *>(table);  // [kWarps][np2]
+  uint32_t *keys = table + 4 * P.np2;                   // distinct targets, then the sorted keys
+  int *off = reinterpret_cast<int *>(keys + P.np2);     // per-rank node counts, then offsets
+  __shared__ int n_distinct, n_fill, n_valid, warp_tot[kWarps];
 
   const int c = blockIdx.x;
   const int i = c / P.M, j = c % P.M;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int np2 = P.np2;
   for (int k = threadIdx.x; k <= P.N; k += kThreads) pe2[k] = __double_as_longlong(P.pe2[k]);
   for (int k = threadIdx.x; k <= P.M; k += kThreads) qe2[k] = __double_as_longlong(P.qe2[k]);
   for (int ab = threadIdx.x; ab < P.n_p * P.n_q; ab += kThreads) {
@@ -166,46 +171,142 @@ __global__ void __launch_bounds__(kThreads) count_kernel(AsmParams P, int64_t *c
     abk[ab] = BinConst{A, Bp, C, D};
   }
   for (int x = threadIdx.x; x < P.n_x; x += kThreads) ys[x] = P.yn[x];
-  __syncthreads();
-  const long long pmax2 = pe2[P.N], qmax2 = qe2[P.M];
-  for (int n = threadIdx.x; n < P.np2; n += kThreads) {
-    uint32_t key = kInvalid;
-    if (n < P.n_nodes) {
-      const BinConst k = abk[n / P.n_x];
-      const double y = ys[n % P.n_x];
-      long long ip2 = __double_as_longlong(__fma_rn(k.A, y, k.Bp));
-      long long iq2 = __double_as_longlong(__fma_rn(k.C, y, k.D));
-      if (ip2 <= pmax2 && iq2 <= qmax2) {
-        int ib = bin_search(pe2, P.N, ip2);
-        int jb = bin_search(qe2, P.M, iq2);
-        key = ((uint32_t)(ib * P.M + jb) << P.nbits) | (uint32_t)n;
-      }
-    }
-    keys[n] = key;
-  }
-  __syncthreads();
-  switch (P.np2 / kThreads) {  // keys per thread
-    case 1: bitonic_sort_reg<1>(keys, P.np2); break;
-    case 2: bitonic_sort_reg<2>(keys, P.np2); break;
-    case 4: bitonic_sort_reg<4>(keys, P.np2); break;
-    case 8: bitonic_sort_reg<8>(keys, P.np2); break;
-    case 16: bitonic_sort_reg<16>(keys, P.np2); break;
-    default: bitonic_sort<kThreads>(keys, P.np2); break;
-  }
-  int local = 0;
-  for (int n = threadIdx.x; n < P.np2; n += kThreads) {
-    uint32_t k = keys[n];
-    if (k != kInvalid && (n == 0 || (keys[n - 1] >> P.nbits) != (k >> P.nbits))) ++local;
-    sorted[(size_t)c * P.np2 + n] = k;
-  }
-  for (int o = 16; o > 0; o >>= 1) local += __shfl_down_sync(0xffffffffu, local, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
-  __syncthreads();
+  for (int k = threadIdx.x; k < 2 * np2; k += kThreads) table[k] = kInvalid;
   if (threadIdx.x == 0) {
-    int s = 0;
-    for (int w = 0; w < kThreads / 32; ++w) s += red[w];
-    counts[c] = s;
+    n_distinct = 0;
+    n_fill = 0;
+    n_valid = 0;
   }
+  __syncthreads();
+  // bin the nodes: the recoupled squares of all R nodes first, then the
+  // binary searches over the squared edges in lock step (2 R independent
+  // shared-memory chains per thread instead of one chain at a time)
+  const long long pmax2 = pe2[P.N], qmax2 = qe2[P.M];
+  const int bits = P.nbits + 1;
+  long long xp[R], xq[R];
+  int ib[R], jb[R];
+  bool in[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    const int n = warp * 32 * R + k * 32 + lane;
+    in[k] = false;
+    xp[k] = xq[k] = 0;
+    if (n < P.n_nodes) {
+      const int ab = div_magic(n, P.nx_magic);
+      const BinConst bc = abk[ab];
+      const double y = ys[n - ab * P.n_x];
+      xp[k] = __double_as_longlong(__fma_rn(bc.A, y, bc.Bp));
+      xq[k] = __double_as_longlong(__fma_rn(bc.C, y, bc.D));
+      in[k] = xp[k] <= pmax2 && xq[k] <= qmax2;
+    }
+    ib[k] = jb[k] = 0;
+  }
+  // number of interior squared edges e2[1 .. n-1] that are <= x (as bin_search)
+  int sp = 1, sq = 1;
+  while (sp * 2 <= P.N - 1) sp *= 2;
+  while (sq * 2 <= P.M - 1) sq *= 2;
+  for (; sp >= 1; sp >>= 1)
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int cand = ib[k] + sp;
+      ib[k] = (cand <= P.N - 1 && pe2[cand] <= xp[k]) ? cand : ib[k];
+    }
+  for (; sq >= 1; sq >>= 1)
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int cand = jb[k] + sq;
+      jb[k] = (cand <= P.M - 1 && qe2[cand] <= xq[k]) ? cand : jb[k];
+    }
+  // collect the distinct targets
+  uint32_t tgt[R];
+  int my_valid = 0;
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    uint32_t t = kInvalid;
+    if (in[k]) {
+      t = (uint32_t)(ib[k] * P.M + jb[k]);
+      ++my_valid;
+      if (set_insert(table, bits, t)) atomicAdd(&n_distinct, 1);
+    }
+    tgt[k] = t;
+  }
+  if (my_valid) atomicAdd(&n_valid, my_valid);
+  __syncthreads();
+  // the distinct targets, ascending
+  const int nr = n_distinct;
+  for (int k = threadIdx.x; k < 2 * np2; k += kThreads) {
+    const uint32_t v = table[k];
+    if (v != kInvalid) keys[atomicAdd(&n_fill, 1)] = v;
+  }
+  int np2r = 1;
+  while (np2r < nr) np2r <<= 1;
+  __syncthreads();
+  for (int k = nr + threadIdx.x; k < np2r; k += kThreads) keys[k] = kInvalid;
+  __syncthreads();
+  bitonic_sort<kThreads>(keys, np2r);
+  // each node's rank: the position of its target among them
+  int rk[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    int r = -1;
+    if (tgt[k] != kInvalid) {
+      int lo = 0, hi = nr - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (keys[mid] < tgt[k])
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      r = lo;
+    }
+    rk[k] = r;
+  }
+  // the hash set is dead: per-warp counts per rank in its place
+  for (int r = threadIdx.x; r < nr; r += kThreads)
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) wc[w * np2 + r] = 0;
+  __syncthreads();
+  // within the warp: nodes of one rank in lane order, k by k
+  const unsigned lower = (1u << lane) - 1u;
+  int lp[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    const int r = rk[k];
+    const unsigned peers = __match_any_sync(0xffffffffu, r);
+    const int base = r >= 0 ? (int)wc[warp * np2 + r] : 0;
+    __syncwarp();
+    if (r >= 0 && (peers & lower) == 0) wc[warp * np2 + r] = (uint16_t)(base + __popc(peers));
+    __syncwarp();
+    lp[k] = base + __popc(peers & lower);
+  }
+  __syncthreads();
+  // per rank: the offsets of the warps within the rank, and its node count
+  for (int r = threadIdx.x; r < nr; r += kThreads) {
+    int s = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const int t = wc[w * np2 + r];
+      wc[w * np2 + r] = (uint16_t)s;
+      s += t;
+    }
+    off[r] = s;
+  }
+  __syncthreads();
+  block_exclusive_scan(off, nr, warp_tot);
+  // place the keys; the invalid nodes fill the tail
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    const int r = rk[k];
+    if (r >= 0) {
+      const int n = warp * 32 * R + k * 32 + lane;
+      keys[off[r] + wc[warp * np2 + r] + lp[k]] = (tgt[k] << P.nbits) | (uint32_t)n;
+    }
+  }
+  for (int k = n_valid + threadIdx.x; k < np2; k += kThreads) keys[k] = kInvalid;
+  __syncthreads();
+  for (int k = threadIdx.x; k < np2; k += kThreads) sorted[(size_t)c * np2 + k] = keys[k];
+  if (threadIdx.x == 0) counts[c] = nr;
 }
 
 // single-CTA exclusive scan of n counts into row_ptr[n + 1]
@@ -297,6 +398,29 @@ __device__ __forceinline__ void legendre_n(real y, real *P) {
     P[n + 1] = (real(2 * n + 1) / real(n + 1)) * y * P[n] - (real(n) / real(n + 1)) * P[n - 1];
 }
 
+// W P_0 .. W P_{NCH-1} at y (the weight folded into the recurrence)
+template <typename real, int NCH>
+__device__ __forceinline__ void legendre_w(real y, real W, real *P) {
+  P[0] = W;
+  if (NCH > 1) P[1] = W * y;
+#pragma unroll
+  for (int n = 1; n + 1 < NCH; ++n)
+    P[n + 1] = (real(2 * n + 1) / real(n + 1)) * y * P[n] - (real(n) / real(n + 1)) * P[n - 1];
+}
+
+// 1/sqrt(d) for d > 0 in FP64 by one Newton-Raphson step r <- r + r (1 -
+// d r^2) / 2 from the FP32 reciprocal square root of d rounded to FP32:
+// for a seed with relative error e the step leaves about 1.5 e^2 (the seed
+// is within 3e-7, so the result within about 2e-13); d outside the FP32
+// range takes the FP64 rsqrt
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  const float f = __double2float_rn(d);
+  if (!(f >= 1e-30f && f <= 1e30f)) return rsqrt(d);
+  const double r = (double)rsqrtf(f);
+  const double e = fma(-(d * r), r, 1.0);  // 1 - d r^2
+  return fma(0.5 * r, e, r);
+}
+
 // Per (p, q) node pair constants of one source cell (FP64):
 //   p'^2 = A y + Bp,  q'^2 = C y + D,  p'.q' = nA y + nB,  and the weight
 //   wp wq.  Shared by the n_x y-nodes of the pair.
@@ -304,8 +428,35 @@ struct PairConst {
   double A, Bp, C, D, nA, nB, W;
 };
 
+// The FP32C form: each FP64 constant as an unevaluated float pair hi + lo
+// (hi the nearest float, lo the nearest float to the rest: 48 bits)
+struct PairConstF {
+  float Ah, Al, Bh, Bl, Ch, Cl, Dh, Dl, nAh, nAl, nBh, nBl, W;
+};
+
+__device__ __forceinline__ float2 split_ff(double v) {
+  const float h = __double2float_rn(v);
+  return make_float2(h, __double2float_rn(v - (double)h));
+}
+
+// a y + b for float pairs a, y, b, rounded to a float: the product of the
+// high parts exactly (Dekker's TwoProduct by FMA), its sum with b's high
+// part exactly (Knuth's TwoSum), then the small terms; the result is the
+// FP64-class value rounded once to FP32 (intrinsics: no contraction)
+__device__ __forceinline__ float ff_mad(float ah, float al, float yh, float yl, float bh, float bl) {
+  const float ph = __fmul_rn(ah, yh);
+  const float pl = __fmaf_rn(ah, yh, -ph);
+  const float sh = __fadd_rn(ph, bh);
+  const float bb = __fsub_rn(sh, ph);
+  const float e = __fadd_rn(__fsub_rn(ph, __fsub_rn(sh, bb)), __fsub_rn(bh, bb));
+  float t = __fmaf_rn(ah, yl, pl);
+  t = __fmaf_rn(al, yh, t);
+  t = __fadd_rn(t, __fadd_rn(bl, e));
+  return __fadd_rn(sh, t);
+}
+
 template <bool F64, int NCH>
-__global__ void __launch_bounds__(kThreads) fill_kernel(AsmParams P, const uint32_t *sorted,
+__global__ void __launch_bounds__(kFill) fill_kernel(AsmParams P, const uint32_t *sorted,
                                                         const int64_t *row_ptr, int32_t *col,
                                                         typename NodeVal<F64>::real *val,
                                                         int64_t nnz) {
@@ -313,21 +464,23 @@ __global__ void __launch_bounds__(kThreads) fill_kernel(AsmParams P, const uint3
   using Acc = typename NodeVal<F64>::Acc;
   constexpr int NPAIR = pair_count(NCH);
   extern __shared__ __align__(16) unsigned char smem[];
-  PairConst *pc = reinterpret_cast<PairConst *>(smem);           // [n_p * n_q]
-  real *Pyw = reinterpret_cast<real *>(pc + P.n_p * P.n_q);     // w_y P_l(y) [n_x][NCH]
+  PairConst *pc = reinterpret_cast<PairConst *>(smem);            // [n_p * n_q] (FP64)
+  PairConstF *pcf = reinterpret_cast<PairConstF *>(smem);         // [n_p * n_q] (FP32C)
+  float2 *ysp = reinterpret_cast<float2 *>(pc + P.n_p * P.n_q);   // y as a float pair [n_x]
+  real *Pyw = reinterpret_cast<real *>(ysp + P.n_x);               // w_y P_l(y) [n_x][NCH]
   uint32_t *keys = reinterpret_cast<uint32_t *>(Pyw + P.n_x * NCH + 2);  // [np2]
-  __shared__ Acc wtot[kThreads / 32][NPAIR];
-  __shared__ int wflag[kThreads / 32];
-  __shared__ int whead[kThreads / 32];
+  __shared__ Acc wtot[kFill / 32][NPAIR];
+  __shared__ int wflag[kFill / 32];
+  __shared__ int whead[kFill / 32];
 
   const int c = blockIdx.x;
   const int i = c / P.M, j = c % P.M;
-  const int R = P.np2 / kThreads;  // consecutive sorted elements per thread
+  const int R = P.np2 / kFill;  // consecutive sorted elements per thread
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t mask = (1u << P.nbits) - 1u;
   const int nbits = P.nbits;
 
-  for (int ab = threadIdx.x; ab < P.n_p * P.n_q; ab += kThreads) {
+  for (int ab = threadIdx.x; ab < P.n_p * P.n_q; ab += kFill) {
     int a = ab / P.n_q, b = ab % P.n_q;
     double p = P.pn[i * P.n_p + a], q = P.qn[j * P.n_q + b];
     PairConst k;
@@ -338,15 +491,34 @@ __global__ void __launch_bounds__(kThreads) fill_kernel(AsmParams P, const uint3
     k.nA = -0.5 * p * q;
     k.nB = 0.375 * q * q - 0.5 * p * p;
     k.W = P.wp[i * P.n_p + a] * P.wq[j * P.n_q + b];
-    pc[ab] = k;
+    if (F64) {
+      pc[ab] = k;
+    } else {
+      PairConstF f;
+      float2 t = split_ff(k.A);
+      f.Ah = t.x, f.Al = t.y;
+      t = split_ff(k.Bp);
+      f.Bh = t.x, f.Bl = t.y;
+      t = split_ff(k.C);
+      f.Ch = t.x, f.Cl = t.y;
+      t = split_ff(k.D);
+      f.Dh = t.x, f.Dl = t.y;
+      t = split_ff(k.nA);
+      f.nAh = t.x, f.nAl = t.y;
+      t = split_ff(k.nB);
+      f.nBh = t.x, f.nBl = t.y;
+      f.W = (float)k.W;
+      pcf[ab] = f;
+    }
   }
-  for (int x = threadIdx.x; x < P.n_x; x += kThreads) {
+  for (int x = threadIdx.x; x < P.n_x; x += kFill) {
     real Pl[NCH];
     legendre_n<real, NCH>((real)P.yn[x], Pl);
 #pragma unroll
     for (int l = 0; l < NCH; ++l) Pyw[x * NCH + l] = (real)P.wy[x] * Pl[l];
+    ysp[x] = split_ff(P.yn[x]);
   }
-  for (int n = threadIdx.x; n < P.np2; n += kThreads) keys[n] = sorted[(size_t)c * P.np2 + n];
+  for (int n = threadIdx.x; n < P.np2; n += kFill) keys[n] = sorted[(size_t)c * P.np2 + n];
   __syncthreads();
 
   auto is_head = [&](int e) {
@@ -359,33 +531,35 @@ __global__ void __launch_bounds__(kThreads) fill_kernel(AsmParams P, const uint3
            (e + 1 == P.np2 || keys[e + 1] == kInvalid || (keys[e + 1] >> nbits) != (k >> nbits));
   };
   // add the contributions of sorted element e to every (l, l') pair:
-  // acc[m] += (W_pq w_y P_l(y)) P_l'(y'), the first factor per l
+  // acc[m] += (w_y P_l(y)) (W_pq P_l'(y')), the first factor from a table
   auto accumulate = [&](int e, Acc *acc) {
-    int node = (int)(keys[e] & mask);
-    int x = node % P.n_x;
-    const PairConst &k = pc[node / P.n_x];
-    double y = P.yn[x];
-    real yp;
+    const int node = (int)(keys[e] & mask);
+    const int ab = div_magic(node, P.nx_magic), x = node - ab * P.n_x;
+    real yp, W;
     if (F64) {
+      const PairConst &k = pc[ab];
+      const double y = P.yn[x];
       double p2 = fma(k.A, y, k.Bp), q2 = fma(k.C, y, k.D), num = fma(k.nA, y, k.nB);
-      double den2 = p2 * q2;  // both >= 0 up to rounding; guarded below
-      yp = den2 > 0.0 ? num * rsqrt(den2) : 0.0;
+      double den2 = p2 * q2;  // both >= 0 up to rounding; guarded below (sign by the bits)
+      yp = __double_as_longlong(den2) > 0 ? num * rsqrt_newton(den2) : 0.0;
+      W = k.W;
     } else {
-      // recoupled squares and p'.q' in FP64 (three FMAs), the rest in FP32
-      float p2 = (float)fma(k.A, y, k.Bp), q2 = (float)fma(k.C, y, k.D);
-      float num = (float)fma(k.nA, y, k.nB);
+      // recoupled squares and p'.q' to FP64-class accuracy from float pairs
+      // (no FP64 instruction), each rounded once to FP32; the rest in FP32
+      const PairConstF &k = pcf[ab];
+      const float2 y = ysp[x];
+      const float p2 = ff_mad(k.Ah, k.Al, y.x, y.y, k.Bh, k.Bl);
+      const float q2 = ff_mad(k.Ch, k.Cl, y.x, y.y, k.Dh, k.Dl);
+      const float num = ff_mad(k.nAh, k.nAl, y.x, y.y, k.nBh, k.nBl);
       float den2 = p2 * q2;
       float cc = den2 > 0.f ? num * rsqrtf(den2) : 0.f;
       yp = (real)fminf(1.f, fmaxf(-1.f, cc));
+      W = k.W;
     }
-    real Pl2[NCH];
-    legendre_n<real, NCH>(yp, Pl2);
-    real wl[NCH];
-    const real W = (real)k.W;
+    real WPl2[NCH];  // W_pq P_l'(y')
+    legendre_w<real, NCH>(yp, W, WPl2);
 #pragma unroll
-    for (int l = 0; l < NCH; ++l) wl[l] = W * Pyw[x * NCH + l];
-#pragma unroll
-    for (int m = 0; m < NPAIR; ++m) acc[m].fma(wl[pair_first(NCH, m)], Pl2[pair_second(NCH, m)]);
+    for (int m = 0; m < NPAIR; ++m) acc[m].fma(Pyw[x * NCH + pair_first(NCH, m)], WPl2[pair_second(NCH, m)]);
   };
 
   // step A: segment ranks from an integer scan of the head flags
@@ -502,13 +676,22 @@ __global__ void __launch_bounds__(kThreads) fill_kernel(AsmParams P, const uint3
   }
 }
 
+template <int R>
+cudaError_t launch_count(const AsmParams &P, int n_cells, size_t smem, cudaStream_t s, int64_t *counts,
+                         uint32_t *sorted) {
+  cudaError_t e = cudaFuncSetAttribute(count_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  count_kernel<R><<<n_cells, kThreads, smem, s>>>(P, counts, sorted);
+  return cudaGetLastError();
+}
+
 template <bool F64, int NCH>
 void launch_fill(const AsmParams &P, int n_cells, size_t smem, cudaStream_t s, const uint32_t *sorted,
                  const int64_t *row_ptr, int32_t *col, void *val, int64_t nnz) {
   using real = typename NodeVal<F64>::real;
   auto kern = fill_kernel<F64, NCH>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  kern<<<n_cells, kThreads, smem, s>>>(P, sorted, row_ptr, col, reinterpret_cast<real *>(val), nnz);
+  kern<<<n_cells, kFill, smem, s>>>(P, sorted, row_ptr, col, reinterpret_cast<real *>(val), nnz);
 }
 
 template <bool F64>
@@ -539,6 +722,7 @@ wpcd_status assemble(wpcd_grid *g, int n_ch, int prec, cudaStream_t s, wpcd_P **
   P.n_q = g->n_q;
   P.n_x = g->n_x;
   P.n_nodes = g->n_p * g->n_q * g->n_x;
+  P.nx_magic = ((1ull << 32) + (uint64_t)g->n_x - 1) / (uint64_t)g->n_x;
   int np2 = kThreads;
   while (np2 < P.n_nodes) np2 *= 2;
   P.np2 = np2;
@@ -600,10 +784,20 @@ wpcd_status assemble(wpcd_grid *g, int n_ch, int prec, cudaStream_t s, wpcd_P **
   if ((e = dev_malloc(&Pm->row_ptr, sizeof(int64_t) * (n_cells + 1))) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc row_ptr"));
 
   cudaEventRecord(ev0, s);
-  size_t smem_count = sizeof(long long) * (P.N + P.M + 2) + sizeof(BinConst) * P.n_p * P.n_q +
-                      sizeof(double) * P.n_x + sizeof(uint32_t) * np2;
-  cudaFuncSetAttribute(count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_count);
-  count_kernel<<<n_cells, kThreads, smem_count, s>>>(P, counts, sorted);
+  // edges, node constants, y nodes; hash set / per-warp counts (4 np2
+  // words), keys (np2), per-rank offsets (np2)
+  const size_t smem_count = sizeof(long long) * (P.N + P.M + 2) + sizeof(BinConst) * P.n_p * P.n_q +
+                            sizeof(double) * P.n_x + sizeof(uint32_t) * 6 * (size_t)np2;
+  if (smem_count > 227 * 1024) return fail(set_error(WPCD_EINVAL, "lattice edges and node count exceed shared memory"));
+  switch (np2 / kThreads) {
+    case 1: e = launch_count<1>(P, n_cells, smem_count, s, counts, sorted); break;
+    case 2: e = launch_count<2>(P, n_cells, smem_count, s, counts, sorted); break;
+    case 4: e = launch_count<4>(P, n_cells, smem_count, s, counts, sorted); break;
+    case 8: e = launch_count<8>(P, n_cells, smem_count, s, counts, sorted); break;
+    case 16: e = launch_count<16>(P, n_cells, smem_count, s, counts, sorted); break;
+    default: e = launch_count<32>(P, n_cells, smem_count, s, counts, sorted); break;
+  }
+  if (e != cudaSuccess) return fail(cuda_error(e, "count pass launch"));
   cudaEventRecord(evc, s);
   scan_kernel<<<1, 1024, 0, s>>>(counts, n_cells, Pm->row_ptr);
   cudaEventRecord(evs, s);
@@ -625,7 +819,7 @@ wpcd_status assemble(wpcd_grid *g, int n_ch, int prec, cudaStream_t s, wpcd_P **
     val = Pm->val32;
   }
   size_t rsz = prec == WPCD_FP64 ? sizeof(double) : sizeof(float);
-  size_t smem_fill = sizeof(double) * 7 * (size_t)P.n_p * P.n_q +
+  size_t smem_fill = sizeof(double) * 7 * (size_t)P.n_p * P.n_q + sizeof(float2) * P.n_x +
                      rsz * ((size_t)P.n_x * P.n_ch + 2) + sizeof(uint32_t) * np2;
   smem_fill = (smem_fill + 15) & ~(size_t)15;
   wpcd_status st = prec == WPCD_FP64
