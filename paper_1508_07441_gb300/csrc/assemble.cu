@@ -1,18 +1,21 @@
 // Step 2 of the numerical scheme (Sec. 3.3; Sec. 4.2): the lattice
 // permutation matrix P0 of Eq. perm / Eq. gal, assembled on the device by
-// quadrature-node binning, in two passes with no atomics.
+// quadrature-node binning, in two passes.  Values are summed in a fixed
+// order (no floating-point atomics), so the result is bit-reproducible.
 //
 //   count pass  one CTA per source cell c = (i, j).  Every GL node (a, b, x)
 //               of the cell is mapped through the recoupled momenta
 //                 p'^2 = fma((0.75 p) q, y, (p p) 0.25 + (q q) 0.5625)
 //                 q'^2 = fma(-(p q),     y, (p p) + (q q) 0.25)
-//               (FP64, each product rounded on its own) and binned by a
-//               branch-free binary search over the squared edges held in
-//               shared memory (compared as int64 bit patterns: the order of
-//               non-negative doubles).  The packed keys (target << nb | node)
-//               are sorted in shared memory (bitonic network), the distinct
-//               targets counted (the paper's pre-selection), and the sorted
-//               keys kept in global memory for the fill pass.
+//               (FP64, each product rounded on its own) and binned against
+//               the squared edges held in shared memory (compared as int64
+//               bit patterns: the order of non-negative doubles), by binary
+//               search for the first y node of each (p, q) pair and short
+//               walks for the rest (p'^2, q'^2 are monotone in y).  The
+//               distinct targets (the paper's pre-selection) are counted in
+//               a shared hash set and ranked; a stable counting sort by rank
+//               leaves the packed keys (target << nbits | node) in ascending
+//               order in global memory for the fill pass.
 //   scan        exclusive scan of the counts -> row_ptr.
 //   fill pass   one CTA per source cell.  The sorted keys are re-read; each
 //               node's value w p^2 q^2 P_l(y) P_l'(y') is formed for every
@@ -21,8 +24,9 @@
 //               sqrt((2l+1)(2l'+1)) / sqrt(B_i Bq_j B_i' Bq_j') and written
 //               to block-CSR (pair-major values).
 //
-// FP64 mode computes y' and the node values in FP64.  FP32C mode computes
-// them in FP32 and accumulates with error-free transformations (TwoSum
+// FP64 mode computes y' and the node values in FP64.  FP32C mode forms the
+// recoupled squares from float pairs (FP64-class, rounded once to FP32),
+// the rest in FP32, and accumulates with error-free transformations (TwoSum
 // float-float pairs); only the binning uses FP64.
 #include <cuda_runtime.h>
 
@@ -68,27 +72,6 @@ struct BinConst {
   double A, Bp, C, D;
 };
 
-// shared-memory bitonic sort for any power-of-two n (a row's distinct targets)
-template <int NT>
-__device__ void bitonic_sort(uint32_t *s, int n) {
-  // n is a power of two; ascending
-  for (int k = 2; k <= n; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int t = threadIdx.x; t < n / 2; t += NT) {
-        int i = 2 * j * (t / j) + (t % j);
-        int l = i + j;
-        uint32_t a = s[i], b = s[l];
-        bool up = (i & k) == 0;
-        if ((a > b) == up) {
-          s[i] = b;
-          s[l] = a;
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
-
 constexpr int kWarps = kThreads / 32;
 
 // exclusive prefix sum of v[0 .. n) in shared memory, in place; called by
@@ -117,29 +100,34 @@ __device__ void block_exclusive_scan(int *v, int n, int *warp_tot) {
 }
 
 // insert a key into a shared hash set of 2^bits slots (multiplicative hash,
-// linear probing; the set has at least twice as many slots as keys): true
-// if the key was not there yet
-__device__ __forceinline__ bool set_insert(uint32_t *table, int bits, uint32_t key) {
+// linear probing; the set has at least twice as many slots as keys): the
+// key's slot, fresh if it was not there yet
+__device__ __forceinline__ int set_insert(uint32_t *table, int bits, uint32_t key, bool &fresh) {
   const uint32_t mask = (1u << bits) - 1u;
   uint32_t h = (key * 2654435761u) >> (32 - bits);
+  fresh = false;
   for (uint32_t probe = 0; probe <= mask; ++probe) {
     const uint32_t old = atomicCAS(&table[h], kInvalid, key);
-    if (old == kInvalid) return true;
-    if (old == key) return false;
+    if (old == kInvalid) {
+      fresh = true;
+      return (int)h;
+    }
+    if (old == key) return (int)h;
     h = (h + 1) & mask;
   }
-  return false;
+  return -1;
 }
 
-// Count pass of one source cell (R = np2 / kThreads nodes per thread; node
-// n = warp * 32 R + k * 32 + lane, so each warp holds consecutive nodes).
-// Every node is binned; the distinct targets go into a shared hash set and
-// are sorted (a row has tens to a few hundred); each node takes its
-// target's rank by binary search; then a stable counting sort places the
-// nodes rank by rank in node order: within a warp by warp-match, across
-// warps by per-(warp, rank) counts.  The result, the packed keys
+// Count pass of one source cell (R = np2 / kThreads nodes per thread).
+// Every node is binned (thread t: nodes t R .. t R + R - 1, a binary search
+// for the first node of each (p, q) pair, then walks along its y nodes);
+// the distinct targets go into a shared hash set, each node keeping its
+// target's slot; a target's rank is the number of smaller distinct targets;
+// then a stable counting sort places the nodes rank by rank in node order
+// (node n = warp * 32 R + k * 32 + lane here: within a warp by warp-match,
+// across warps by per-(warp, rank) counts).  The result, the packed keys
 // (target << nbits | node) in ascending order, is the one a full sort of
-// the keys gives, at a cost linear in the node count.
+// the keys gives, without sorting them.
 template <int R>
 __global__ void __launch_bounds__(kThreads) count_kernel(AsmParams P, int64_t *counts, uint32_t *sorted) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -178,90 +166,86 @@ __global__ void __launch_bounds__(kThreads) count_kernel(AsmParams P, int64_t *c
     n_valid = 0;
   }
   __syncthreads();
-  // bin the nodes: the recoupled squares of all R nodes first, then the
-  // binary searches over the squared edges in lock step (2 R independent
-  // shared-memory chains per thread instead of one chain at a time)
+  // bin the nodes, thread t taking nodes t R .. t R + R - 1: consecutive y
+  // nodes of one (p, q) pair, along which p'^2 and q'^2 are monotone, so
+  // after a binary search for the first node of each pair the bins follow
+  // by short walks (both directions: the y order is not assumed)
   const long long pmax2 = pe2[P.N], qmax2 = qe2[P.M];
   const int bits = P.nbits + 1;
-  long long xp[R], xq[R];
-  int ib[R], jb[R];
-  bool in[R];
-#pragma unroll
-  for (int k = 0; k < R; ++k) {
-    const int n = warp * 32 * R + k * 32 + lane;
-    in[k] = false;
-    xp[k] = xq[k] = 0;
-    if (n < P.n_nodes) {
-      const int ab = div_magic(n, P.nx_magic);
-      const BinConst bc = abk[ab];
-      const double y = ys[n - ab * P.n_x];
-      xp[k] = __double_as_longlong(__fma_rn(bc.A, y, bc.Bp));
-      xq[k] = __double_as_longlong(__fma_rn(bc.C, y, bc.D));
-      in[k] = xp[k] <= pmax2 && xq[k] <= qmax2;
+  uint32_t *tg = reinterpret_cast<uint32_t *>(off);  // targets by node index
+  {
+    int bp = 0, bq = 0, prev_ab = -1;
+#pragma unroll 1
+    for (int k = 0; k < R; ++k) {
+      const int n = (int)threadIdx.x * R + k;
+      uint32_t t = kInvalid;
+      if (n < P.n_nodes) {
+        const int ab = div_magic(n, P.nx_magic);
+        const BinConst bc = abk[ab];
+        const double y = ys[n - ab * P.n_x];
+        const long long xp = __double_as_longlong(__fma_rn(bc.A, y, bc.Bp));
+        const long long xq = __double_as_longlong(__fma_rn(bc.C, y, bc.D));
+        if (ab != prev_ab) {
+          bp = bin_search(pe2, P.N, xp);
+          bq = bin_search(qe2, P.M, xq);
+          prev_ab = ab;
+        } else {
+          while (bp < P.N - 1 && pe2[bp + 1] <= xp) ++bp;
+          while (bp > 0 && pe2[bp] > xp) --bp;
+          while (bq < P.M - 1 && qe2[bq + 1] <= xq) ++bq;
+          while (bq > 0 && qe2[bq] > xq) --bq;
+        }
+        if (xp <= pmax2 && xq <= qmax2) t = (uint32_t)(bp * P.M + bq);
+      }
+      tg[n] = t;
     }
-    ib[k] = jb[k] = 0;
   }
-  // number of interior squared edges e2[1 .. n-1] that are <= x (as bin_search)
-  int sp = 1, sq = 1;
-  while (sp * 2 <= P.N - 1) sp *= 2;
-  while (sq * 2 <= P.M - 1) sq *= 2;
-  for (; sp >= 1; sp >>= 1)
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-      const int cand = ib[k] + sp;
-      ib[k] = (cand <= P.N - 1 && pe2[cand] <= xp[k]) ? cand : ib[k];
-    }
-  for (; sq >= 1; sq >>= 1)
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-      const int cand = jb[k] + sq;
-      jb[k] = (cand <= P.M - 1 && qe2[cand] <= xq[k]) ? cand : jb[k];
-    }
-  // collect the distinct targets
+  __syncthreads();
+  // collect the distinct targets (node n = warp * 32 R + k * 32 + lane from
+  // here on, so that each warp holds consecutive nodes); each node keeps
+  // its target's hash slot
   uint32_t tgt[R];
+  int slot[R];
   int my_valid = 0;
 #pragma unroll
   for (int k = 0; k < R; ++k) {
-    uint32_t t = kInvalid;
-    if (in[k]) {
-      t = (uint32_t)(ib[k] * P.M + jb[k]);
+    const uint32_t t = tg[warp * 32 * R + k * 32 + lane];
+    slot[k] = -1;
+    if (t != kInvalid) {
       ++my_valid;
-      if (set_insert(table, bits, t)) atomicAdd(&n_distinct, 1);
+      bool fresh;
+      slot[k] = set_insert(table, bits, t, fresh);
+      if (fresh) atomicAdd(&n_distinct, 1);
     }
     tgt[k] = t;
   }
   if (my_valid) atomicAdd(&n_valid, my_valid);
   __syncthreads();
-  // the distinct targets, ascending
+  // the distinct targets (list) with their slots; the rank of each is the
+  // number of smaller ones (a row has tens to a few hundred), stored by slot
   const int nr = n_distinct;
+  uint32_t *rank_of = table + 2 * np2;  // by slot
+  int *lslot = off;                      // the targets by node index are in registers now
   for (int k = threadIdx.x; k < 2 * np2; k += kThreads) {
     const uint32_t v = table[k];
-    if (v != kInvalid) keys[atomicAdd(&n_fill, 1)] = v;
+    if (v != kInvalid) {
+      const int at = atomicAdd(&n_fill, 1);
+      keys[at] = v;
+      lslot[at] = k;
+    }
   }
-  int np2r = 1;
-  while (np2r < nr) np2r <<= 1;
   __syncthreads();
-  for (int k = nr + threadIdx.x; k < np2r; k += kThreads) keys[k] = kInvalid;
+  for (int m = threadIdx.x; m < nr; m += kThreads) {
+    const uint32_t v = keys[m];
+    int r = 0;
+    for (int q = 0; q < nr; ++q) r += keys[q] < v ? 1 : 0;
+    rank_of[lslot[m]] = (uint32_t)r;
+  }
   __syncthreads();
-  bitonic_sort<kThreads>(keys, np2r);
-  // each node's rank: the position of its target among them
   int rk[R];
 #pragma unroll
-  for (int k = 0; k < R; ++k) {
-    int r = -1;
-    if (tgt[k] != kInvalid) {
-      int lo = 0, hi = nr - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (keys[mid] < tgt[k])
-          lo = mid + 1;
-        else
-          hi = mid;
-      }
-      r = lo;
-    }
-    rk[k] = r;
-  }
+  for (int k = 0; k < R; ++k) rk[k] = slot[k] >= 0 ? (int)rank_of[slot[k]] : -1;
+  __syncthreads();
   // the hash set is dead: per-warp counts per rank in its place
   for (int r = threadIdx.x; r < nr; r += kThreads)
 #pragma unroll
