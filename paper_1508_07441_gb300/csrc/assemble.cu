@@ -45,6 +45,7 @@ constexpr uint32_t kInvalid = 0xFFFFFFFFu;
 struct AsmParams {
   int N, M, n_p, n_q, n_x, n_nodes, np2, nbits, n_ch, n_pairs;
   uint64_t nx_magic;  // ceil(2^32 / n_x): node / n_x by a multiply and a shift
+  int stage_rows;     // fill: rows staged in shared memory (the longest row), 0: direct writes
   int pl[kMaxPairs], plp[kMaxPairs];
   double cnorm[kMaxPairs];  // sqrt((2l+1)(2l'+1))
   const double *pe2, *qe2, *pn, *wp, *qn, *wq, *yn, *wy, *rsb;
@@ -290,7 +291,10 @@ __global__ void __launch_bounds__(kThreads) count_kernel(AsmParams P, int64_t *c
   for (int k = n_valid + threadIdx.x; k < np2; k += kThreads) keys[k] = kInvalid;
   __syncthreads();
   for (int k = threadIdx.x; k < np2; k += kThreads) sorted[(size_t)c * np2 + k] = keys[k];
-  if (threadIdx.x == 0) counts[c] = nr;
+  if (threadIdx.x == 0) {
+    counts[c] = nr;
+    atomicMax(reinterpret_cast<unsigned long long *>(counts + P.N * P.M), (unsigned long long)nr);  // longest row
+  }
 }
 
 // single-CTA exclusive scan of n counts into row_ptr[n + 1]
@@ -324,6 +328,7 @@ struct Acc64 {
   __device__ void fma(double a, double b) { v = ::fma(a, b, v); }
   __device__ void add(const Acc64 &o) { v += o.v; }
   __device__ double value() const { return v; }
+  __device__ double result() const { return v; }
   __device__ Acc64 shfl_up(int d) const { Acc64 r; r.v = __shfl_up_sync(0xffffffffu, v, d); return r; }
 };
 
@@ -351,6 +356,7 @@ struct AccFF {
     two_sum(s, e, hi, lo);
   }
   __device__ double value() const { return (double)hi + (double)lo; }
+  __device__ float result() const { return __fadd_rn(hi, lo); }  // rounded once to FP32
   __device__ AccFF shfl_up(int d) const {
     AccFF r;
     r.hi = __shfl_up_sync(0xffffffffu, hi, d);
@@ -382,13 +388,19 @@ __device__ __forceinline__ void legendre_n(real y, real *P) {
     P[n + 1] = (real(2 * n + 1) / real(n + 1)) * y * P[n] - (real(n) / real(n + 1)) * P[n - 1];
 }
 
-// W P_0 .. W P_{NCH-1} at y (the weight folded into the recurrence)
+// a b + c in the operands' own precision (no promotion of floats to double)
+__device__ __forceinline__ float fma_r(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_r(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// W P_0 .. W P_{NCH-1} at y (the weight folded into the recurrence; hW =
+// W / 2, the term P_0 / 2 of the first step, given)
 template <typename real, int NCH>
-__device__ __forceinline__ void legendre_w(real y, real W, real *P) {
+__device__ __forceinline__ void legendre_w(real y, real W, real hW, real *P) {
   P[0] = W;
   if (NCH > 1) P[1] = W * y;
+  if (NCH > 2) P[2] = fma_r(real(1.5) * y, P[1], -hW);
 #pragma unroll
-  for (int n = 1; n + 1 < NCH; ++n)
+  for (int n = 2; n + 1 < NCH; ++n)
     P[n + 1] = (real(2 * n + 1) / real(n + 1)) * y * P[n] - (real(n) / real(n + 1)) * P[n - 1];
 }
 
@@ -408,14 +420,14 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
 // Per (p, q) node pair constants of one source cell (FP64):
 //   p'^2 = A y + Bp,  q'^2 = C y + D,  p'.q' = nA y + nB,  and the weight
 //   wp wq.  Shared by the n_x y-nodes of the pair.
-struct PairConst {
-  double A, Bp, C, D, nA, nB, W;
+struct __align__(16) PairConst {
+  double A, Bp, C, D, nA, nB, W, hW;  // hW = W / 2
 };
 
 // The FP32C form: each FP64 constant as an unevaluated float pair hi + lo
 // (hi the nearest float, lo the nearest float to the rest: 48 bits)
-struct PairConstF {
-  float Ah, Al, Bh, Bl, Ch, Cl, Dh, Dl, nAh, nAl, nBh, nBl, W;
+struct __align__(16) PairConstF {
+  float Ah, Al, Bh, Bl, Ch, Cl, Dh, Dl, nAh, nAl, nBh, nBl, W, hW, pad[2];
 };
 
 __device__ __forceinline__ float2 split_ff(double v) {
@@ -453,6 +465,9 @@ __global__ void __launch_bounds__(kFill) fill_kernel(AsmParams P, const uint32_t
   float2 *ysp = reinterpret_cast<float2 *>(pc + P.n_p * P.n_q);   // y as a float pair [n_x]
   real *Pyw = reinterpret_cast<real *>(ysp + P.n_x);               // w_y P_l(y) [n_x][NCH]
   uint32_t *keys = reinterpret_cast<uint32_t *>(Pyw + P.n_x * NCH + 2);  // [np2]
+  // the row's staged sums [stage_rows][NPAIR] and targets [stage_rows]
+  real *st_val = reinterpret_cast<real *>((reinterpret_cast<uintptr_t>(keys + P.np2) + 15) & ~(uintptr_t)15);
+  int32_t *st_col = reinterpret_cast<int32_t *>(st_val + (size_t)P.stage_rows * NPAIR);
   __shared__ Acc wtot[kFill / 32][NPAIR];
   __shared__ int wflag[kFill / 32];
   __shared__ int whead[kFill / 32];
@@ -475,6 +490,7 @@ __global__ void __launch_bounds__(kFill) fill_kernel(AsmParams P, const uint32_t
     k.nA = -0.5 * p * q;
     k.nB = 0.375 * q * q - 0.5 * p * p;
     k.W = P.wp[i * P.n_p + a] * P.wq[j * P.n_q + b];
+    k.hW = 0.5 * k.W;
     if (F64) {
       pc[ab] = k;
     } else {
@@ -492,6 +508,7 @@ __global__ void __launch_bounds__(kFill) fill_kernel(AsmParams P, const uint32_t
       t = split_ff(k.nB);
       f.nBh = t.x, f.nBl = t.y;
       f.W = (float)k.W;
+      f.hW = 0.5f * f.W;
       pcf[ab] = f;
     }
   }
@@ -509,17 +526,12 @@ __global__ void __launch_bounds__(kFill) fill_kernel(AsmParams P, const uint32_t
     uint32_t k = keys[e];
     return k != kInvalid && (e == 0 || (keys[e - 1] >> nbits) != (k >> nbits));
   };
-  auto is_tail = [&](int e) {
-    uint32_t k = keys[e];
-    return k != kInvalid &&
-           (e + 1 == P.np2 || keys[e + 1] == kInvalid || (keys[e + 1] >> nbits) != (k >> nbits));
-  };
   // add the contributions of sorted element e to every (l, l') pair:
   // acc[m] += (w_y P_l(y)) (W_pq P_l'(y')), the first factor from a table
   auto accumulate = [&](int e, Acc *acc) {
     const int node = (int)(keys[e] & mask);
     const int ab = div_magic(node, P.nx_magic), x = node - ab * P.n_x;
-    real yp, W;
+    real yp, W, hW;
     if (F64) {
       const PairConst &k = pc[ab];
       const double y = P.yn[x];
@@ -527,6 +539,7 @@ __global__ void __launch_bounds__(kFill) fill_kernel(AsmParams P, const uint32_t
       double den2 = p2 * q2;  // both >= 0 up to rounding; guarded below (sign by the bits)
       yp = __double_as_longlong(den2) > 0 ? num * rsqrt_newton(den2) : 0.0;
       W = k.W;
+      hW = k.hW;
     } else {
       // recoupled squares and p'.q' to FP64-class accuracy from float pairs
       // (no FP64 instruction), each rounded once to FP32; the rest in FP32
@@ -539,9 +552,10 @@ __global__ void __launch_bounds__(kFill) fill_kernel(AsmParams P, const uint32_t
       float cc = den2 > 0.f ? num * rsqrtf(den2) : 0.f;
       yp = (real)fminf(1.f, fmaxf(-1.f, cc));
       W = k.W;
+      hW = k.hW;
     }
     real WPl2[NCH];  // W_pq P_l'(y')
-    legendre_w<real, NCH>(yp, W, WPl2);
+    legendre_w<real, NCH>(yp, W, hW, WPl2);
 #pragma unroll
     for (int m = 0; m < NPAIR; ++m) acc[m].fma(Pyw[x * NCH + pair_first(NCH, m)], WPl2[pair_second(NCH, m)]);
   };
@@ -564,9 +578,16 @@ __global__ void __launch_bounds__(kFill) fill_kernel(AsmParams P, const uint32_t
   const int64_t lim = row_ptr[c + 1];
   const double rs_src = P.rsb[c];
 
+  const bool staged = P.stage_rows > 0;
   auto write_seg = [&](int seg, uint32_t k, const Acc *sum) {
     int64_t o = base + seg;
-    if (o < lim) {
+    if (staged) {
+      if (o < lim) {
+        st_col[seg] = (int32_t)(k >> nbits);
+#pragma unroll
+        for (int m = 0; m < NPAIR; ++m) st_val[seg * NPAIR + m] = sum[m].result();
+      }
+    } else if (o < lim) {
       int t = (int)(k >> nbits);
       col[o] = t;
       double nrm = rs_src * P.rsb[t];
@@ -585,18 +606,21 @@ __global__ void __launch_bounds__(kFill) fill_kernel(AsmParams P, const uint32_t
   }
   int flag = 0, local_heads = 0, lead_tail = 0;
   uint32_t lead_key = 0;
+  // a window of (previous, current) keys: one shared-memory load per element
+  uint32_t kprev = e0 > 0 ? keys[e0 - 1] : kInvalid, k = keys[e0];
   for (int r = 0; r < R; ++r) {
     const int e = e0 + r;
-    const uint32_t k = keys[e];
     if (k == kInvalid) break;
-    if (is_head(e)) {
+    const uint32_t knext = e + 1 < P.np2 ? keys[e + 1] : kInvalid;
+    const uint32_t tk = k >> nbits;
+    if (e == 0 || (kprev >> nbits) != tk) {
       flag = 1;
       ++local_heads;
 #pragma unroll
       for (int m = 0; m < NPAIR; ++m) run[m].zero();
     }
     accumulate(e, run);
-    if (is_tail(e)) {
+    if (knext == kInvalid || (knext >> nbits) != tk) {
       if (flag) {
         write_seg(seg0 + local_heads - 1, k, run);
       } else {
@@ -606,6 +630,8 @@ __global__ void __launch_bounds__(kFill) fill_kernel(AsmParams P, const uint32_t
         lead_key = k;
       }
     }
+    kprev = k;
+    k = knext;
   }
   // step C: segmented scan of (flag, sum of the segment open at my end)
   Acc agg[NPAIR];
@@ -657,6 +683,16 @@ __global__ void __launch_bounds__(kFill) fill_kernel(AsmParams P, const uint32_t
 #pragma unroll
     for (int m = 0; m < NPAIR; ++m) lead[m].add(excl[m]);
     write_seg(seg0 - 1, lead_key, lead);
+  }
+  if (!staged) return;  // uniform over the CTA
+  // normalise and write the row: consecutive threads, consecutive elements
+  __syncthreads();
+  const int n_seg = (int)(lim - base);
+  for (int sg = threadIdx.x; sg < n_seg; sg += kFill) col[base + sg] = st_col[sg];
+  for (int idx = threadIdx.x; idx < n_seg * NPAIR; idx += kFill) {
+    const int m = idx / n_seg, sg = idx - m * n_seg;
+    const double scale = rs_src * P.rsb[st_col[sg]] * P.cnorm[m];
+    val[(size_t)m * nnz + base + sg] = (real)((double)st_val[sg * NPAIR + m] * scale);
   }
 }
 
@@ -763,7 +799,11 @@ wpcd_status assemble(wpcd_grid *g, int n_ch, int prec, cudaStream_t s, wpcd_P **
     return st;
   };
   cudaError_t e;
-  if ((e = dev_malloc(&counts, sizeof(int64_t) * n_cells)) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc counts"));
+  // counts[n_cells]: the longest row
+  if ((e = dev_malloc(&counts, sizeof(int64_t) * (n_cells + 1))) != cudaSuccess)
+    return fail(cuda_error(e, "cudaMalloc counts"));
+  if ((e = cudaMemsetAsync(counts + n_cells, 0, sizeof(int64_t), s)) != cudaSuccess)
+    return fail(cuda_error(e, "counts clear"));
   if ((e = dev_malloc(&sorted, sizeof(uint32_t) * (size_t)n_cells * np2)) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc sorted keys"));
   if ((e = dev_malloc(&Pm->row_ptr, sizeof(int64_t) * (n_cells + 1))) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc row_ptr"));
 
@@ -787,8 +827,9 @@ wpcd_status assemble(wpcd_grid *g, int n_ch, int prec, cudaStream_t s, wpcd_P **
   cudaEventRecord(evs, s);
   count_launches(2);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_error(e, "count/scan launch"));
-  int64_t nnz = 0;
-  if ((e = cudaMemcpyAsync(&nnz, Pm->row_ptr + n_cells, sizeof(int64_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+  int64_t nnz = 0, longest = 0;
+  if ((e = cudaMemcpyAsync(&nnz, Pm->row_ptr + n_cells, sizeof(int64_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&longest, counts + n_cells, sizeof(int64_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return fail(cuda_error(e, "nnz readback"));
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(cuda_error(e, "count pass"));
   Pm->nnz = nnz;
@@ -803,9 +844,14 @@ wpcd_status assemble(wpcd_grid *g, int n_ch, int prec, cudaStream_t s, wpcd_P **
     val = Pm->val32;
   }
   size_t rsz = prec == WPCD_FP64 ? sizeof(double) : sizeof(float);
-  size_t smem_fill = sizeof(double) * 7 * (size_t)P.n_p * P.n_q + sizeof(float2) * P.n_x +
+  size_t smem_fill = sizeof(PairConst) * (size_t)P.n_p * P.n_q + sizeof(float2) * P.n_x +
                      rsz * ((size_t)P.n_x * P.n_ch + 2) + sizeof(uint32_t) * np2;
   smem_fill = (smem_fill + 15) & ~(size_t)15;
+  // each row's sums staged in shared memory (values, target), then
+  // normalised and written by all threads together, when the longest fits
+  const size_t stage = 16 + (size_t)longest * ((size_t)P.n_pairs * rsz + sizeof(int32_t));
+  P.stage_rows = smem_fill + stage <= 200 * 1024 ? (int)longest : 0;
+  if (P.stage_rows) smem_fill += stage;
   wpcd_status st = prec == WPCD_FP64
                        ? dispatch_fill<true>(P, n_cells, smem_fill, s, sorted, Pm->row_ptr, Pm->col, val, nnz)
                        : dispatch_fill<false>(P, n_cells, smem_fill, s, sorted, Pm->row_ptr, Pm->col, val, nnz);
