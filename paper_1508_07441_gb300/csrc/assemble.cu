@@ -46,6 +46,8 @@ struct AsmParams {
   int N, M, n_p, n_q, n_x, n_nodes, np2, nbits, n_ch, n_pairs;
   uint64_t nx_magic;  // ceil(2^32 / n_x): node / n_x by a multiply and a shift
   int stage_rows;     // fill: rows staged in shared memory (the longest row), 0: direct writes
+  int warp_runs;      // n_x a multiple of 32 and the y nodes ascending: a warp step is one
+                      // (p, q) pair's consecutive y nodes, with monotone targets
   int pl[kMaxPairs], plp[kMaxPairs];
   double cnorm[kMaxPairs];  // sqrt((2l+1)(2l'+1))
   const double *pe2, *qe2, *pn, *wp, *qn, *wq, *yn, *wy, *rsb;
@@ -173,9 +175,13 @@ __global__ void __launch_bounds__(kThreads) count_kernel(AsmParams P, int64_t *c
   // by short walks (both directions: the y order is not assumed)
   const long long pmax2 = pe2[P.N], qmax2 = qe2[P.M];
   const int bits = P.nbits + 1;
+  // the distinct targets go into the hash set here too (once per run of
+  // equal targets along the thread's nodes); each node keeps its slot
   uint32_t *tg = reinterpret_cast<uint32_t *>(off);  // targets by node index
+  int *ts = reinterpret_cast<int *>(keys);           // their hash slots by node index
   {
-    int bp = 0, bq = 0, prev_ab = -1;
+    int bp = 0, bq = 0, prev_ab = -1, prev_slot = -1, my_valid = 0;
+    uint32_t prev_t = kInvalid;
 #pragma unroll 1
     for (int k = 0; k < R; ++k) {
       const int n = (int)threadIdx.x * R + k;
@@ -198,29 +204,34 @@ __global__ void __launch_bounds__(kThreads) count_kernel(AsmParams P, int64_t *c
         }
         if (xp <= pmax2 && xq <= qmax2) t = (uint32_t)(bp * P.M + bq);
       }
+      int sl = -1;
+      if (t != kInvalid) {
+        ++my_valid;
+        if (t == prev_t) {
+          sl = prev_slot;
+        } else {
+          bool fresh;
+          sl = set_insert(table, bits, t, fresh);
+          if (fresh) atomicAdd(&n_distinct, 1);
+        }
+      }
+      prev_t = t;
+      prev_slot = sl;
       tg[n] = t;
+      ts[n] = sl;
     }
+    if (my_valid) atomicAdd(&n_valid, my_valid);
   }
   __syncthreads();
-  // collect the distinct targets (node n = warp * 32 R + k * 32 + lane from
-  // here on, so that each warp holds consecutive nodes); each node keeps
-  // its target's hash slot
+  // node n = warp * 32 R + k * 32 + lane from here on, so that each warp
+  // holds consecutive nodes
   uint32_t tgt[R];
   int slot[R];
-  int my_valid = 0;
 #pragma unroll
   for (int k = 0; k < R; ++k) {
-    const uint32_t t = tg[warp * 32 * R + k * 32 + lane];
-    slot[k] = -1;
-    if (t != kInvalid) {
-      ++my_valid;
-      bool fresh;
-      slot[k] = set_insert(table, bits, t, fresh);
-      if (fresh) atomicAdd(&n_distinct, 1);
-    }
-    tgt[k] = t;
+    tgt[k] = tg[warp * 32 * R + k * 32 + lane];
+    slot[k] = ts[warp * 32 * R + k * 32 + lane];
   }
-  if (my_valid) atomicAdd(&n_valid, my_valid);
   __syncthreads();
   // the distinct targets (list) with their slots; the rank of each is the
   // number of smaller ones (a row has tens to a few hundred), stored by slot
@@ -252,13 +263,28 @@ __global__ void __launch_bounds__(kThreads) count_kernel(AsmParams P, int64_t *c
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) wc[w * np2 + r] = 0;
   __syncthreads();
-  // within the warp: nodes of one rank in lane order, k by k
+  // within the warp: nodes of one rank in lane order, k by k.  When n_x is
+  // a multiple of 32 the lanes of a step are consecutive y nodes of one
+  // (p, q) pair, whose targets are monotone, so the lanes of one rank are
+  // contiguous and found from the run heads; else by warp-match
   const unsigned lower = (1u << lane) - 1u;
+  const bool contiguous = P.warp_runs != 0;
   int lp[R];
 #pragma unroll
   for (int k = 0; k < R; ++k) {
     const int r = rk[k];
-    const unsigned peers = __match_any_sync(0xffffffffu, r);
+    unsigned peers;
+    if (contiguous) {
+      const int up = __shfl_up_sync(0xffffffffu, r, 1);
+      const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || up != r);
+      const unsigned le = lower | (1u << lane);
+      const int h = 31 - __clz(heads & le);                       // my run's head
+      const unsigned after = heads & ~le;                           // heads after me
+      const int e = after ? __ffs(after) - 1 : 32;                  // next run's head
+      peers = (e >= 32 ? 0xffffffffu : ((1u << e) - 1u)) & ~((1u << h) - 1u);
+    } else {
+      peers = __match_any_sync(0xffffffffu, r);
+    }
     const int base = r >= 0 ? (int)wc[warp * np2 + r] : 0;
     __syncwarp();
     if (r >= 0 && (peers & lower) == 0) wc[warp * np2 + r] = (uint16_t)(base + __popc(peers));
@@ -743,6 +769,7 @@ wpcd_status assemble(wpcd_grid *g, int n_ch, int prec, cudaStream_t s, wpcd_P **
   P.n_x = g->n_x;
   P.n_nodes = g->n_p * g->n_q * g->n_x;
   P.nx_magic = ((1ull << 32) + (uint64_t)g->n_x - 1) / (uint64_t)g->n_x;
+  P.warp_runs = g->n_x % 32 == 0 && g->y_ascending;
   int np2 = kThreads;
   while (np2 < P.n_nodes) np2 *= 2;
   P.np2 = np2;

@@ -250,6 +250,8 @@ static wpcd_status grid_create(const wpcd_grid_desc *d, wpcd_grid **out) {
   gauss_legendre(d->n_p, tp.data(), wp.data());
   gauss_legendre(d->n_q, tq.data(), wq.data());
   gauss_legendre(d->n_x, ty.data(), wy.data());
+  g->y_ascending = true;
+  for (int x = 1; x < d->n_x; ++x) g->y_ascending = g->y_ascending && ty[x] > ty[x - 1];
   std::vector<double> pn((size_t)N * d->n_p), pw((size_t)N * d->n_p), qn((size_t)M * d->n_q),
       qw((size_t)M * d->n_q), pe2(N + 1), qe2(M + 1), rsb((size_t)N * M);
   for (int i = 0; i < N; ++i) {

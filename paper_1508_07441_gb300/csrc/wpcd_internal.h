@@ -128,6 +128,7 @@ struct wpcd_grid {
   double *yn = nullptr, *wy = nullptr;          // y nodes / weights [n_x]
   double *rsb = nullptr;                        // 1/sqrt(B_i Bq_j) per cell [N*M]
   double *qe_d = nullptr;                       // q edges [M+1]
+  bool y_ascending = false;                     // the y nodes strictly increase
   std::atomic<int> refs{1};
 };
 

@@ -69,6 +69,10 @@ CASES = [
     (12, 14, (3, 5, 7), 3, None),
     (17, 23, (4, 6, 12), 2, 11),
     (26, 22, (8, 8, 32), 5, 21),
+    # n_x a multiple of 32 (a warp step is one (p, q) pair's y nodes):
+    # 64 y nodes, and a node count that is not a power of two
+    (14, 18, (3, 2, 64), 3, 5),
+    (19, 13, (3, 5, 32), 2, None),
     (50, 50, (4, 4, 16), 1, None),  # the s-wave benchmark lattice
 ]
 
