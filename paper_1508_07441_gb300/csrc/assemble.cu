@@ -53,6 +53,11 @@ struct AsmParams {
   const double *pe2, *qe2, *pn, *wp, *qn, *wq, *yn, *wy, *rsb;
 };
 
+// shared-memory index of element n of a per-node array read both as runs of
+// R consecutive elements per thread and as 32 consecutive elements per warp:
+// one pad word per 32 puts the runs of the 32 lanes on distinct banks
+__device__ __forceinline__ int pad32(int n) { return n + (n >> 5); }
+
 // n / d for 0 <= n < 2^13 and d <= 2^13 from magic = ceil(2^32 / d): with
 // magic d = 2^32 + r, 0 <= r < d, the product n magic / 2^32 exceeds n / d by
 // n r / (d 2^32) < 1 / d, too little to reach the next integer
@@ -142,7 +147,7 @@ __global__ void __launch_bounds__(kThreads) count_kernel(AsmParams P, int64_t *c
   uint32_t *table = reinterpret_cast<uint32_t *>(ys + P.n_x);
   uint16_t *wc = reinterpret_cast<uint16_t *>(table);  // [kWarps][np2]
   uint32_t *keys = table + 4 * P.np2;                   // distinct targets, then the sorted keys
-  int *off = reinterpret_cast<int *>(keys + P.np2);     // per-rank node counts, then offsets
+  int *off = reinterpret_cast<int *>(keys + P.np2 + P.np2 / 32);  // per-rank counts, then offsets
   __shared__ int n_distinct, n_fill, n_valid, warp_tot[kWarps];
 
   const int c = blockIdx.x;
@@ -217,8 +222,8 @@ __global__ void __launch_bounds__(kThreads) count_kernel(AsmParams P, int64_t *c
       }
       prev_t = t;
       prev_slot = sl;
-      tg[n] = t;
-      ts[n] = sl;
+      tg[pad32(n)] = t;
+      ts[pad32(n)] = sl;
     }
     if (my_valid) atomicAdd(&n_valid, my_valid);
   }
@@ -229,8 +234,8 @@ __global__ void __launch_bounds__(kThreads) count_kernel(AsmParams P, int64_t *c
   int slot[R];
 #pragma unroll
   for (int k = 0; k < R; ++k) {
-    tgt[k] = tg[warp * 32 * R + k * 32 + lane];
-    slot[k] = ts[warp * 32 * R + k * 32 + lane];
+    tgt[k] = tg[pad32(warp * 32 * R + k * 32 + lane)];
+    slot[k] = ts[pad32(warp * 32 * R + k * 32 + lane)];
   }
   __syncthreads();
   // the distinct targets (list) with their slots; the rank of each is the
@@ -414,6 +419,9 @@ __device__ __forceinline__ void legendre_n(real y, real *P) {
     P[n + 1] = (real(2 * n + 1) / real(n + 1)) * y * P[n] - (real(n) / real(n + 1)) * P[n - 1];
 }
 
+__device__ __forceinline__ float mul_r(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_r(double a, double b) { return __dmul_rn(a, b); }
+
 // a b + c in the operands' own precision (no promotion of floats to double)
 __device__ __forceinline__ float fma_r(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_r(double a, double b, double c) { return __fma_rn(a, b, c); }
@@ -461,6 +469,31 @@ __device__ __forceinline__ float2 split_ff(double v) {
   return make_float2(h, __double2float_rn(v - (double)h));
 }
 
+// float-pair arithmetic (hi + lo, |lo| <= ulp(hi) / 2; intrinsics, so no
+// contraction): products by Dekker's TwoProduct (FMA), sums by Knuth's TwoSum
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  const float e = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, __fmaf_rn(a.x, b.x, -p)));
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ float2 ff_mul_f(float2 a, float b) {
+  const float p = __fmul_rn(a.x, b);
+  return fast_two_sum(p, __fmaf_rn(a.y, b, __fmaf_rn(a.x, b, -p)));
+}
+__device__ __forceinline__ float2 ff_scale2(float2 a, float pow2) {  // exact
+  return make_float2(a.x * pow2, a.y * pow2);
+}
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float bb = __fsub_rn(s, a.x);
+  const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+  return fast_two_sum(s, __fadd_rn(e, __fadd_rn(a.y, b.y)));
+}
+
 // a y + b for float pairs a, y, b, rounded to a float: the product of the
 // high parts exactly (Dekker's TwoProduct by FMA), its sum with b's high
 // part exactly (Knuth's TwoSum), then the small terms; the result is the
@@ -492,7 +525,8 @@ __global__ void __launch_bounds__(kFill) fill_kernel(AsmParams P, const uint32_t
   real *Pyw = reinterpret_cast<real *>(ysp + P.n_x);               // w_y P_l(y) [n_x][NCH]
   uint32_t *keys = reinterpret_cast<uint32_t *>(Pyw + P.n_x * NCH + 2);  // [np2]
   // the row's staged sums [stage_rows][NPAIR] and targets [stage_rows]
-  real *st_val = reinterpret_cast<real *>((reinterpret_cast<uintptr_t>(keys + P.np2) + 15) & ~(uintptr_t)15);
+  real *st_val =
+      reinterpret_cast<real *>((reinterpret_cast<uintptr_t>(keys + P.np2 + P.np2 / 32) + 15) & ~(uintptr_t)15);
   int32_t *st_col = reinterpret_cast<int32_t *>(st_val + (size_t)P.stage_rows * NPAIR);
   __shared__ Acc wtot[kFill / 32][NPAIR];
   __shared__ int wflag[kFill / 32];
@@ -508,6 +542,27 @@ __global__ void __launch_bounds__(kFill) fill_kernel(AsmParams P, const uint32_t
   for (int ab = threadIdx.x; ab < P.n_p * P.n_q; ab += kFill) {
     int a = ab / P.n_q, b = ab % P.n_q;
     double p = P.pn[i * P.n_p + a], q = P.qn[j * P.n_q + b];
+    if (!F64) {
+      // the same constants in float-pair arithmetic from p and q split
+      // once (FP64-class, a handful of FP64 instructions per pair)
+      const float2 pf = split_ff(p), qf = split_ff(q);
+      const float2 pp = ff_mul(pf, pf), qq = ff_mul(qf, qf), pq = ff_mul(pf, qf);
+      const float2 A = ff_mul_f(pq, 0.75f);
+      const float2 Bp = ff_add(ff_scale2(pp, 0.25f), ff_mul_f(qq, 0.5625f));
+      const float2 D = ff_add(pp, ff_scale2(qq, 0.25f));
+      const float2 nB = ff_add(ff_mul_f(qq, 0.375f), ff_scale2(pp, -0.5f));
+      PairConstF f;
+      f.Ah = A.x, f.Al = A.y;
+      f.Bh = Bp.x, f.Bl = Bp.y;
+      f.Ch = -pq.x, f.Cl = -pq.y;
+      f.Dh = D.x, f.Dl = D.y;
+      f.nAh = -0.5f * pq.x, f.nAl = -0.5f * pq.y;
+      f.nBh = nB.x, f.nBl = nB.y;
+      f.W = (float)P.wp[i * P.n_p + a] * (float)P.wq[j * P.n_q + b];
+      f.hW = 0.5f * f.W;
+      pcf[ab] = f;
+      continue;
+    }
     PairConst k;
     k.A = __dmul_rn(__dmul_rn(0.75, p), q);
     k.Bp = __dadd_rn(__dmul_rn(__dmul_rn(p, p), 0.25), __dmul_rn(__dmul_rn(q, q), 0.5625));
@@ -517,26 +572,7 @@ __global__ void __launch_bounds__(kFill) fill_kernel(AsmParams P, const uint32_t
     k.nB = 0.375 * q * q - 0.5 * p * p;
     k.W = P.wp[i * P.n_p + a] * P.wq[j * P.n_q + b];
     k.hW = 0.5 * k.W;
-    if (F64) {
-      pc[ab] = k;
-    } else {
-      PairConstF f;
-      float2 t = split_ff(k.A);
-      f.Ah = t.x, f.Al = t.y;
-      t = split_ff(k.Bp);
-      f.Bh = t.x, f.Bl = t.y;
-      t = split_ff(k.C);
-      f.Ch = t.x, f.Cl = t.y;
-      t = split_ff(k.D);
-      f.Dh = t.x, f.Dl = t.y;
-      t = split_ff(k.nA);
-      f.nAh = t.x, f.nAl = t.y;
-      t = split_ff(k.nB);
-      f.nBh = t.x, f.nBl = t.y;
-      f.W = (float)k.W;
-      f.hW = 0.5f * f.W;
-      pcf[ab] = f;
-    }
+    pc[ab] = k;
   }
   for (int x = threadIdx.x; x < P.n_x; x += kFill) {
     real Pl[NCH];
@@ -545,17 +581,19 @@ __global__ void __launch_bounds__(kFill) fill_kernel(AsmParams P, const uint32_t
     for (int l = 0; l < NCH; ++l) Pyw[x * NCH + l] = (real)P.wy[x] * Pl[l];
     ysp[x] = split_ff(P.yn[x]);
   }
-  for (int n = threadIdx.x; n < P.np2; n += kFill) keys[n] = sorted[(size_t)c * P.np2 + n];
+  // keys at pad32(n): each thread reads a run of R consecutive keys
+  for (int n = threadIdx.x; n < P.np2; n += kFill) keys[pad32(n)] = sorted[(size_t)c * P.np2 + n];
   __syncthreads();
 
   auto is_head = [&](int e) {
-    uint32_t k = keys[e];
-    return k != kInvalid && (e == 0 || (keys[e - 1] >> nbits) != (k >> nbits));
+    uint32_t k = keys[pad32(e)];
+    return k != kInvalid && (e == 0 || (keys[pad32(e - 1)] >> nbits) != (k >> nbits));
   };
   // add the contributions of sorted element e to every (l, l') pair:
   // acc[m] += (w_y P_l(y)) (W_pq P_l'(y')), the first factor from a table
-  auto accumulate = [&](int e, Acc *acc) {
-    const int node = (int)(keys[e] & mask);
+  // the two factors of every pair's term of element e: Pyw row x, W P_l'(y')
+  auto factors = [&](int e, real *WPl2) -> int {
+    const int node = (int)(keys[pad32(e)] & mask);
     const int ab = div_magic(node, P.nx_magic), x = node - ab * P.n_x;
     real yp, W, hW;
     if (F64) {
@@ -580,10 +618,21 @@ __global__ void __launch_bounds__(kFill) fill_kernel(AsmParams P, const uint32_t
       W = k.W;
       hW = k.hW;
     }
-    real WPl2[NCH];  // W_pq P_l'(y')
     legendre_w<real, NCH>(yp, W, hW, WPl2);
+    return x;
+  };
+  auto accumulate = [&](int e, Acc *acc) {
+    real WPl2[NCH];  // W_pq P_l'(y')
+    const int x = factors(e, WPl2);
 #pragma unroll
     for (int m = 0; m < NPAIR; ++m) acc[m].fma(Pyw[x * NCH + pair_first(NCH, m)], WPl2[pair_second(NCH, m)]);
+  };
+  // FP32C: the rounded products of element e (AccFF::fma adds the same)
+  auto products = [&](int e, real *v) {
+    real WPl2[NCH];
+    const int x = factors(e, WPl2);
+#pragma unroll
+    for (int m = 0; m < NPAIR; ++m) v[m] = mul_r(Pyw[x * NCH + pair_first(NCH, m)], WPl2[pair_second(NCH, m)]);
   };
 
   // step A: segment ranks from an integer scan of the head flags
@@ -633,19 +682,33 @@ __global__ void __launch_bounds__(kFill) fill_kernel(AsmParams P, const uint32_t
   int flag = 0, local_heads = 0, lead_tail = 0;
   uint32_t lead_key = 0;
   // a window of (previous, current) keys: one shared-memory load per element
-  uint32_t kprev = e0 > 0 ? keys[e0 - 1] : kInvalid, k = keys[e0];
+  uint32_t kprev = e0 > 0 ? keys[pad32(e0 - 1)] : kInvalid, k = keys[pad32(e0)];
+  // FP32C: the next element's products are formed while the current one is
+  // added (independent work for the scheduler); same sums as AccFF::fma
+  real v_cur[NPAIR], v_nxt[NPAIR];
+  if constexpr (!F64) {
+    if (k != kInvalid) products(e0, v_cur);
+  }
   for (int r = 0; r < R; ++r) {
     const int e = e0 + r;
     if (k == kInvalid) break;
-    const uint32_t knext = e + 1 < P.np2 ? keys[e + 1] : kInvalid;
+    const uint32_t knext = e + 1 < P.np2 ? keys[pad32(e + 1)] : kInvalid;
     const uint32_t tk = k >> nbits;
+    if constexpr (!F64) {
+      if (r + 1 < R && knext != kInvalid) products(e + 1, v_nxt);
+    }
     if (e == 0 || (kprev >> nbits) != tk) {
       flag = 1;
       ++local_heads;
 #pragma unroll
       for (int m = 0; m < NPAIR; ++m) run[m].zero();
     }
-    accumulate(e, run);
+    if constexpr (F64) {
+      accumulate(e, run);
+    } else {
+#pragma unroll
+      for (int m = 0; m < NPAIR; ++m) run[m].add(v_cur[m]);
+    }
     if (knext == kInvalid || (knext >> nbits) != tk) {
       if (flag) {
         write_seg(seg0 + local_heads - 1, k, run);
@@ -658,6 +721,10 @@ __global__ void __launch_bounds__(kFill) fill_kernel(AsmParams P, const uint32_t
     }
     kprev = k;
     k = knext;
+    if constexpr (!F64) {
+#pragma unroll
+      for (int m = 0; m < NPAIR; ++m) v_cur[m] = v_nxt[m];
+    }
   }
   // step C: segmented scan of (flag, sum of the segment open at my end)
   Acc agg[NPAIR];
@@ -838,7 +905,7 @@ wpcd_status assemble(wpcd_grid *g, int n_ch, int prec, cudaStream_t s, wpcd_P **
   // edges, node constants, y nodes; hash set / per-warp counts (4 np2
   // words), keys (np2), per-rank offsets (np2)
   const size_t smem_count = sizeof(long long) * (P.N + P.M + 2) + sizeof(BinConst) * P.n_p * P.n_q +
-                            sizeof(double) * P.n_x + sizeof(uint32_t) * 6 * (size_t)np2;
+                            sizeof(double) * P.n_x + sizeof(uint32_t) * (6 * (size_t)np2 + np2 / 16);
   if (smem_count > 227 * 1024) return fail(set_error(WPCD_EINVAL, "lattice edges and node count exceed shared memory"));
   switch (np2 / kThreads) {
     case 1: e = launch_count<1>(P, n_cells, smem_count, s, counts, sorted); break;
@@ -872,7 +939,7 @@ wpcd_status assemble(wpcd_grid *g, int n_ch, int prec, cudaStream_t s, wpcd_P **
   }
   size_t rsz = prec == WPCD_FP64 ? sizeof(double) : sizeof(float);
   size_t smem_fill = sizeof(PairConst) * (size_t)P.n_p * P.n_q + sizeof(float2) * P.n_x +
-                     rsz * ((size_t)P.n_x * P.n_ch + 2) + sizeof(uint32_t) * np2;
+                     rsz * ((size_t)P.n_x * P.n_ch + 2) + sizeof(uint32_t) * (np2 + np2 / 32);
   smem_fill = (smem_fill + 15) & ~(size_t)15;
   // each row's sums staged in shared memory (values, target), then
   // normalised and written by all threads together, when the longest fits
