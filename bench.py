@@ -144,12 +144,12 @@ def fill_flops_per_node(n_ch: int, n_pairs: int) -> int:
 # of the kernel as it stands (profiles/ names the capture); None where no
 # capture of the current kernel exists
 NCU_TRAFFIC = {
-    "fill_kernel<FP64,3>": 435.6e6,
-    "spmm_sacc_kernel<FP32>": 377.8e6,
-    "tc_gemm_kernel<TF32x3> (Vt, G1)": 329.2e6,
-    "tc_gemm_kernel<TF32x3> (O)": 331.5e6,
-    "spmm_df_kernel": 961.9e6,
-    "oz_gemm_kernel (digit planes)": 450.4e6,
+    "fill_kernel<FP64,3>": 435.0e6,
+    "spmm_tile_kernel<FP32>": 331.4e6,
+    "tc_gemm_kernel<TF32x3> (Vt, G1)": 328.9e6,
+    "tc_gemm_kernel<TF32x3> (O)": 331.6e6,
+    "spmm_df_kernel": 759.3e6,
+    "oz_gemm_kernel (digit planes)": 323.3e6,
     "gemm_df_kernel": 903.6e6,
 }
 
@@ -371,7 +371,7 @@ def kernel_rooflines(W, pr, w, phases, n_nodes, n_e, stream, flush, peaks, f_sm,
     # FP32 inner cycles: P0 SpMM and the two tensor-core channel products
     ms = _time_kernel(stream, flush, lambda: pr.wpcd_spmm(P, x32, y32, n_e, mode=W.WPCD_SPMM_FP32, stream=stream,
                                                            timed=True))
-    entry("spmm_sacc_kernel<FP32>", "alu", spmm_flops / (ms * 1e-3) / 1e12, fp32, "TFLOP/s", ms, n32,
+    entry("spmm_tile_kernel<FP32>", "alu", spmm_flops / (ms * 1e-3) / 1e12, fp32, "TFLOP/s", ms, n32,
           f"4 n_pairs nnz B = {spmm_flops:.3e} FP32 flops (one real-by-complex multiply-add per block entry and "
           "energy)", src32)
     tc_bytes = 3.0 * 8 * dim * n_e
@@ -417,7 +417,7 @@ def kernel_rooflines(W, pr, w, phases, n_nodes, n_e, stream, flush, peaks, f_sm,
                                                            timed=True))
     spmv_bytes = P.nnz * (4 + 8 * pr.n_pairs) + 8 * (N * M + 1) + 2 * 16 * dim
     spmv_flops = 4.0 * pr.n_pairs * P.nnz
-    entry("spmm_kernel<double> (1 RHS)", "alu", spmv_flops / (ms * 1e-3) / 1e12, fp64, "TFLOP/s", ms, 0,
+    entry("spmv_kernel<FP64> (1 RHS)", "alu", spmv_flops / (ms * 1e-3) / 1e12, fp64, "TFLOP/s", ms, 0,
           f"{spmv_flops:.3e} FP64 flops, {spmv_bytes:.3e} B (HBM fraction "
           f"{spmv_bytes / (ms * 1e-3) / 1e9 / hbm:.3f}): at 0.45 flop/B it sits above GB300's FP64 ridge "
           f"({fp64 * 1e3 / hbm:.2f} flop/B), so the FP64 pipe, not HBM, bounds it", src64)
@@ -428,7 +428,7 @@ def kernel_rooflines(W, pr, w, phases, n_nodes, n_e, stream, flush, peaks, f_sm,
     ms = _time_kernel(stream, flush, lambda: pr.wpcd_spmm(P, x1f, y1f, 1, mode=W.WPCD_SPMM_FP32, stream=stream,
                                                            timed=True), reps=5)
     spmv32_bytes = P.nnz * (4 + 4 * pr.n_pairs) + 8 * (N * M + 1) + 2 * 8 * dim
-    entry("spmm_sacc_kernel<FP32> (1 RHS)", "hbm", spmv32_bytes / (ms * 1e-3) / 1e9, hbm, "GB/s", ms, 0,
+    entry("spmv_kernel<FP32> (1 RHS)", "hbm", spmv32_bytes / (ms * 1e-3) / 1e9, hbm, "GB/s", ms, 0,
           f"{spmv32_bytes:.3e} B: columns and FP32 values read once, row pointers, y read and z written "
           "once (FP32 complex)", "measured HBM copy (hbm_gbs)")
     ms = _time_kernel(stream, flush, lambda: pr.wpcd_channel_gemm(1, W.WPCD_GEMM_FP64, None, x1, y1, 1,
