@@ -162,6 +162,11 @@ __global__ void __launch_bounds__(TL_THREADS, 2) spmm_tile_kernel(TileParams T, 
         for (int q = 0; q < EPT; ++q) part[k][l][q][0] = part[k][l][q][1] = 0.f;
     const int64_t u0 = T.tptr[t], u1 = T.tptr[t + 1];
     int nb = 0;
+    // unrolled so that the next columns' value and y loads issue before this
+    // column's FMAs (2-row tiles: 4 columns; 4-row tiles have no registers
+    // to spare)
+    constexpr int UNR = R == 2 ? 4 : 1;
+#pragma unroll UNR
     for (int64_t u = u0; u < u1; ++u) {
       const int c = __ldg(T.ucol + u);
       float v[VS];
