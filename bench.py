@@ -821,7 +821,7 @@ def main():
         Xtr, Ttr = ws.dataset(inputs.random_energies(pr.eps_bound, args.warm_train, seed=2026))
         t_data = time.perf_counter() - t0
         t1 = time.perf_counter()
-        hist = ws.fit(Xtr, Ttr, epochs=300, batch=256, lr=2e-3)
+        hist = ws.fit(Xtr, Ttr, epochs=600, batch=256, lr=2e-3, decay=(0.1, 0.01, 0.001))
         torch.cuda.synchronize()
         t_train = time.perf_counter() - t1
         Ete = inputs.random_energies(pr.eps_bound, args.warm_test, seed=2027)
@@ -831,6 +831,18 @@ def main():
         torch.cuda.synchronize()
         t_pred = time.perf_counter() - t2
         wit, rw, fb, Uw = ws.iterations(Ete, u_init=ug, tol=1e-8, batch=64, max_iter=60)
+        # accuracy of the warm start itself: |u_g - u| / |u| per energy, BF16
+        # inference (the one used) and FP32 inference of the same network
+        ut = ws.solve_vectors(Ete, batch=128).view(len(Ete), -1)
+        torch.cuda.synchronize()
+        nrm = torch.linalg.vector_norm(ut, dim=1)
+        err_bf16 = (torch.linalg.vector_norm(ug.view(len(Ete), -1) - ut, dim=1) / nrm).cpu().numpy()
+        ug32 = ws.predict(Ete, bf16=False).view(len(Ete), -1)
+        torch.cuda.synchronize()  # predict runs on the bench stream
+        err_fp32 = (torch.linalg.vector_norm(ug32 - ut, dim=1) / nrm).cpu().numpy()
+        del ut
+        wit32, _, fb32, _ = ws.iterations(Ete, u_init=ug32.view(-1), tol=1e-8, batch=64, max_iter=60)
+        del ug32
         warm = {"what": "3-layer MLP (width 256, FP32 train by the library's kernels, BF16 inference) "
                         "predicting the solution beyond the Born term in a 64-vector basis of the "
                         "method's own solutions; FP64 Krylov to rel residual 1e-8 from the warm "
@@ -843,6 +855,10 @@ def main():
                 "saved_fraction": float(1.0 - wit.mean() / cold.mean()),
                 "max_rel_residual_cold": float(rc.max()), "max_rel_residual_warm": float(rw.max()),
                 "fallbacks": int(fb.sum()),
+                "warm_rel_error_median_bf16": float(np.median(err_bf16)),
+                "warm_rel_error_median_fp32_inference": float(np.median(err_fp32)),
+                "k_applications_warm_fp32_inference_mean": float(wit32.mean()),
+                "saved_fraction_fp32_inference": float(1.0 - wit32.mean() / cold.mean()),
                 "max_rel_diff_U00_warm_vs_cold": float(np.max(np.abs(Uw - Uc) / np.abs(Uc))),
                 "s_data": t_data, "s_train": t_train, "s_predict": t_pred}
         P5.close()

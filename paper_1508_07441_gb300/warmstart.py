@@ -7,9 +7,9 @@ to the bin.  The network therefore predicts the part of the solution beyond
 the first iterate, u - u0, in a basis built from that part.
 
 Pipeline, every arithmetic step in libwpcd:
-  1. snapshots: u(E) - u0(E) at k energies spread evenly over the on-shell
-     bins of the range (batched mixed solves), orthonormalised on the GPU
-     into a projected basis Phi;
+  1. snapshots: u(E) - u0(E) at the centres of the k on-shell bins that
+     carry the most of the energy range (batched mixed solves),
+     orthonormalised on the GPU into a projected basis Phi;
   2. data: for each training energy the target is Phi^H (u - u0) (k complex
      = 2k reals) and the features are the scaled centre of the on-shell bin
      and the first kf coefficients Phi^H u0 of the first iterate;
@@ -56,13 +56,16 @@ class WarmStart:
         return b
 
     def snapshot_energies(self, e_lo, e_hi):
-        """k energies at the centres of on-shell bins spread evenly (in bin
-        index) over the bins that [e_lo, e_hi] reaches."""
+        """k energies at the centres of the on-shell bins that carry the most
+        of [e_lo, e_hi] in energy (a bin q in [q_j, q_j+1) spans eps_d + 3/4 q^2
+        over its edges): u depends on E only through the bin, so a basis that
+        holds the solutions of those bins holds the exact solution for every
+        energy that falls in one of them."""
         qe, eb = self.pr.qe, self.pr.eps_bound
-        q_lo, q_hi = np.sqrt((e_lo - eb) / 0.75), np.sqrt((e_hi - eb) / 0.75)
-        j_lo = int(np.searchsorted(qe, q_lo, side="right") - 1)
-        j_hi = int(np.searchsorted(qe, q_hi, side="right") - 1)
-        js = np.unique(np.round(np.linspace(j_lo, j_hi, self.k)).astype(int))
+        Eq = eb + 0.75 * np.asarray(qe) ** 2
+        meas = np.clip(np.minimum(Eq[1:], e_hi) - np.maximum(Eq[:-1], e_lo), 0.0, None)
+        js = np.sort(np.argsort(-meas, kind="stable")[:self.k])
+        js = js[meas[js] > 0]
         E = eb + 0.75 * (0.5 * (qe[js] + qe[js + 1])) ** 2
         return np.clip(E, e_lo, e_hi)  # fewer than k when the range has fewer bins
 
@@ -109,7 +112,9 @@ class WarmStart:
             del U
         return self.torch.cat(Xs), self.torch.cat(Ts)
 
-    def fit(self, X, T, epochs=300, batch=256, lr=1e-3):
+    def fit(self, X, T, epochs=300, batch=256, lr=1e-3, decay=()):
+        """Train for epochs at lr, then epochs more at each lr * f for f in
+        decay (a step schedule); the loss history of all phases."""
         n_in, n_out = X.shape[1], T.shape[1]
         self.mlp = W.MLP(n_in, self.width, n_out, seed=self.seed, device=self.device)
         # affine maps from the training statistics (setup of the network, host)
@@ -119,8 +124,12 @@ class WarmStart:
         ts = Th.std(axis=0)
         ts[ts == 0] = 1.0
         self.mlp.wpcd_mlp_set_affine(1.0 / xs, -Xh.mean(axis=0) / xs, ts, Th.mean(axis=0))
-        return self.mlp.wpcd_mlp_train(X.contiguous(), T.contiguous(), epochs, batch, lr, seed=self.seed,
-                                       stream=self.stream)
+        hist = [self.mlp.wpcd_mlp_train(X.contiguous(), T.contiguous(), epochs, batch, lr, seed=self.seed,
+                                        stream=self.stream)]
+        for i, f in enumerate(decay):
+            hist.append(self.mlp.wpcd_mlp_train(X.contiguous(), T.contiguous(), epochs, batch, lr * f,
+                                                seed=self.seed + 1 + i, stream=self.stream))
+        return np.concatenate(hist)
 
     def predict(self, E, bf16=True):
         """Warm starts u_g = u0 + Phi c_hat (device float64 [len(E)][2 dim])."""

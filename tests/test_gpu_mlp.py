@@ -94,14 +94,17 @@ def test_warm_start_saves_iterations(W, orc):
     ws.e_lo, ws.e_hi = lo, hi
     ws.build_basis(ws.snapshot_energies(lo, hi))
     X, T = ws.dataset(inputs.random_energies(pr.eps_bound, 384, seed=2026))
-    hist = ws.fit(X, T, epochs=400, batch=128, lr=2e-3)
+    hist = ws.fit(X, T, epochs=400, batch=128, lr=2e-3, decay=(0.1, 0.01))
     assert hist[-1] < 0.2 * hist[0]
     E = inputs.random_energies(pr.eps_bound, 48, seed=2027)
     cold, rc, _, Uc = ws.iterations(E, tol=1e-8)
     ug = ws.predict(E)
     warm, rw, fb, Uw = ws.iterations(E, u_init=ug, tol=1e-8)
     assert np.all(rc <= 1e-8) and np.all(rw <= 1e-8)   # equal residual
-    assert warm.mean() < cold.mean(), (warm.mean(), cold.mean())
+    print(f"warm start: {cold.mean():.2f} -> {warm.mean():.2f} K applications, fallbacks {fb.sum()}")
+    # measured 12.85 -> 11.44 (11 %); the snapshots hold the solutions of the
+    # bins that carry most of the energy range
+    assert warm.mean() < 0.95 * cold.mean(), (warm.mean(), cold.mean())
     assert np.max(np.abs(Uw - Uc) / np.abs(Uc)) < 1e-6
     opr = orc.Problem(dict(pe=pe, qe=qe, n_p=4, n_q=4, n_x=16, n_ch=3, V=[-3.0], a=[1.0], n_pair_nodes=8))
     for k in (0, 17, 47):
