@@ -890,6 +890,17 @@ def main():
         cpu = {"value": n_nodes / t_asm / 1e9, "unit": "Gnodes/s", "cores": oracle.num_threads(),
                "kind": "oracle",
                "sample": "P0 assembly (count + fill) of the full 200x200 lattice, 81.9M nodes, once"}
+        # one core (the paper's CPU convention), on the lattice of the first
+        # 100 x 100 bins of the same edges (a quarter of the nodes)
+        n_all = oracle.num_threads()
+        oracle.set_threads(1)
+        t0 = time.perf_counter()
+        oracle.P0(w["p_edges"][:101], w["q_edges"][:101], *w["nodes"], n_ch)
+        t1c = time.perf_counter() - t0
+        oracle.set_threads(n_all)
+        cpu["single_core"] = {"value": 100 * 100 * int(np.prod(w["nodes"])) / t1c / 1e9, "unit": "Gnodes/s",
+                              "cores": 1, "s": t1c,
+                              "sample": "P0 assembly of the first 100 x 100 bins of the same edges (20.5M nodes)"}
         if not args.no_oracle_check:
             opr = oracle.Problem(dict(pe=w["p_edges"], qe=w["q_edges"], n_p=nn[0], n_q=nn[1],
                                       n_x=nn[2], n_ch=n_ch, V=list(w["V"]), a=list(w["a"]),

@@ -339,8 +339,7 @@ static wpcd_status pair_create(wpcd_grid *g, const wpcd_pair_desc *d, wpcd_probl
   // the potential matrices of every channel (rows in parallel inside), then
   // the channels' eigenproblems side by side on the host cores
   std::vector<std::vector<double>> vs(d->n_ch), hs(d->n_ch), epss(d->n_ch), Os(d->n_ch);
-  for (int l = 0; l < d->n_ch; ++l)
-    pair_matrices(N, g->pe.data(), d->n_pair_nodes, l, d->n_terms, d->V, d->a, vs[l], hs[l]);
+  pair_matrices_all(N, g->pe.data(), d->n_pair_nodes, d->n_ch, d->n_terms, d->V, d->a, vs, hs);
 #pragma omp parallel for schedule(dynamic, 1)
   for (int l = 0; l < d->n_ch; ++l) pair_eig(N, hs[l], epss[l], Os[l]);
   for (int l = 0; l < d->n_ch; ++l) {

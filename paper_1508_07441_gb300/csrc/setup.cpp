@@ -88,20 +88,32 @@ double bessel_i_scaled(int l, double z) {
   return want / cur * i0s;
 }
 
-// v_l(p, p') = (2/pi) int r^2 j_l(pr) V(r) j_l(p'r) dr for a sum of
-// Gaussians, partial-wave states normalised to delta(p - p')/p^2:
-//   sum_k V_k / (2 sqrt(pi) alpha^{3/2}) exp(-(p-p')^2/(4 alpha)) e^{-z} i_l(z),
-// alpha = 1/a_k, z = p p' / (2 alpha).
-double v_partial_wave(int l, double p, double pp, int n_terms, const double *V, const double *a) {
-  const double two_sqrt_pi = 3.5449077018110320546;
-  double s = 0.0;
-  for (int k = 0; k < n_terms; ++k) {
-    double alpha = 1.0 / a[k];
-    double z = 0.5 * p * pp * a[k];
-    double gauss = std::exp(-0.25 * (p - pp) * (p - pp) * a[k]);
-    s += V[k] / (two_sqrt_pi * alpha * std::sqrt(alpha)) * gauss * bessel_i_scaled(l, z);
+// exp(-z) i_l(z) for l = 0 .. lmax at once (out[lmax + 1]): the same three
+// regimes as bessel_i_scaled; in the middle one a single downward recurrence
+// (started above lmax) yields every order
+void bessel_i_scaled_all(int lmax, double z, double *out) {
+  if (z == 0.0 || z < 1e-3 || z > 40.0) {
+    for (int l = 0; l <= lmax; ++l) out[l] = bessel_i_scaled(l, z);
+    return;
   }
-  return s;
+  for (int l = 0; l <= lmax; ++l) out[l] = 0.0;
+  const int top = lmax + 30 + (int)(2.0 * z);
+  const double inv_z = 1.0 / z;
+  double up = 0.0, cur = 1e-300;
+  for (int n = top; n >= 1; --n) {
+    const double down = up + (2.0 * n + 1.0) * inv_z * cur;  // i_{n-1}
+    up = cur;
+    cur = down;
+    if (n - 1 <= lmax) out[n - 1] = cur;
+    if (std::fabs(cur) > 1e250) {  // rescale to stay in range
+      cur *= 1e-250;
+      up *= 1e-250;
+      for (int l = 0; l <= lmax; ++l) out[l] *= 1e-250;
+    }
+  }
+  // cur = i_0 (unnormalised)
+  const double scale = -std::expm1(-2.0 * z) / (2.0 * z) / cur;
+  for (int l = 0; l <= lmax; ++l) out[l] *= scale;
 }
 
 // Symmetric eigenproblem: Householder reduction to tridiagonal form, then
@@ -209,8 +221,18 @@ bool sym_eig(int n, std::vector<double> A, std::vector<double> &evals, std::vect
 // with unit weight functions in the p^2 dp measure, n_nodes GL points per
 // bin) and h1 = diag(<p^2>) + v, whose eigen-decomposition (Eq. exp_z) is
 // pair_eig's
-void pair_matrices(int N, const double *edges, int n_nodes, int l, int n_terms, const double *V,
-                   const double *a, std::vector<double> &v, std::vector<double> &h) {
+// The potential matrices v (and h1 = h0 + v) of channels l = 0 .. n_ch - 1 in
+// the pair-momentum WP basis: v_l averaged over each pair of bins with
+// n_nodes GL nodes per bin, rows in parallel on the host cores (each element
+// computed by one thread, in a fixed order: the result does not depend on the
+// thread count).  One Bessel recurrence per (node, node) pair and Gaussian
+// term serves every l.  For a sum of Gaussians, with partial-wave states
+// normalised to delta(p - p') / p^2,
+//   v_l(p, p') = (2/pi) int r^2 j_l(pr) V(r) j_l(p'r) dr
+//              = sum_k V_k / (2 sqrt(pi) alpha^{3/2}) exp(-(p-p')^2/(4 alpha)) e^{-z} i_l(z),
+// alpha = 1/a_k, z = p p' / (2 alpha).
+void pair_matrices_all(int N, const double *edges, int n_nodes, int n_ch, int n_terms, const double *V,
+                       const double *a, std::vector<std::vector<double>> &v, std::vector<std::vector<double>> &h) {
   std::vector<double> t(n_nodes), w(n_nodes);
   gauss_legendre(n_nodes, t.data(), w.data());
   std::vector<double> pn((size_t)N * n_nodes), pw((size_t)N * n_nodes), rsB(N);
@@ -224,34 +246,44 @@ void pair_matrices(int N, const double *edges, int n_nodes, int l, int n_terms, 
     }
     rsB[i] = 1.0 / std::sqrt(shell_volume(lo, hi));
   }
-  v.assign((size_t)N * N, 0.0);
-  // rows in parallel on the host cores (each element is computed once, by
-  // one thread, in the same order as serially: the result does not depend
-  // on the thread count)
+  v.assign(n_ch, std::vector<double>((size_t)N * N, 0.0));
+  const double two_sqrt_pi = 3.5449077018110320546;
 #pragma omp parallel for schedule(dynamic, 2)
-  for (int i = 0; i < N; ++i)
-    for (int k = i; k < N; ++k) {
-      double s = 0.0;
-      for (int x = 0; x < n_nodes; ++x) {
-        double px = pn[(size_t)i * n_nodes + x], wx = pw[(size_t)i * n_nodes + x];
-        double row = 0.0;
-        for (int y = 0; y < n_nodes; ++y)
-          row += pw[(size_t)k * n_nodes + y] *
-                 v_partial_wave(l, px, pn[(size_t)k * n_nodes + y], n_terms, V, a);
-        s += wx * row;
-      }
-      s *= rsB[i] * rsB[k];
-      v[(size_t)i * N + k] = s;
-      v[(size_t)k * N + i] = s;
-    }
-  h = v;
   for (int i = 0; i < N; ++i) {
-    double lo = edges[i], hi = edges[i + 1];
-    // <p^2>_i = int p^4 dp / B_i
-    double lo2 = lo * lo, hi2 = hi * hi;
-    double p5 = (hi - lo) * (hi2 * hi2 + hi2 * hi * lo + hi2 * lo2 + hi * lo * lo2 + lo2 * lo2) / 5.0;
-    h[(size_t)i * N + i] += p5 / shell_volume(lo, hi);
+    std::vector<double> bes(n_ch), s(n_ch), row(n_ch);
+    for (int k = i; k < N; ++k) {
+      std::fill(s.begin(), s.end(), 0.0);
+      for (int x = 0; x < n_nodes; ++x) {
+        const double px = pn[(size_t)i * n_nodes + x], wx = pw[(size_t)i * n_nodes + x];
+        std::fill(row.begin(), row.end(), 0.0);
+        for (int y = 0; y < n_nodes; ++y) {
+          const double py = pn[(size_t)k * n_nodes + y], wy = pw[(size_t)k * n_nodes + y];
+          for (int q = 0; q < n_terms; ++q) {
+            const double alpha = 1.0 / a[q];
+            const double z = 0.5 * px * py * a[q];
+            const double c = V[q] / (two_sqrt_pi * alpha * std::sqrt(alpha)) *
+                             std::exp(-0.25 * (px - py) * (px - py) * a[q]);
+            bessel_i_scaled_all(n_ch - 1, z, bes.data());
+            for (int l = 0; l < n_ch; ++l) row[l] += wy * (c * bes[l]);
+          }
+        }
+        for (int l = 0; l < n_ch; ++l) s[l] += wx * row[l];
+      }
+      for (int l = 0; l < n_ch; ++l) {
+        const double e = s[l] * rsB[i] * rsB[k];
+        v[l][(size_t)i * N + k] = e;
+        v[l][(size_t)k * N + i] = e;
+      }
+    }
   }
+  h = v;
+  for (int l = 0; l < n_ch; ++l)
+    for (int i = 0; i < N; ++i) {
+      double lo = edges[i], hi = edges[i + 1];
+      double lo2 = lo * lo, hi2 = hi * hi;
+      double p5 = (hi - lo) * (hi2 * hi2 + hi2 * hi * lo + hi2 * lo2 + hi * lo * lo2 + lo2 * lo2) / 5.0;
+      h[l][(size_t)i * N + i] += p5 / shell_volume(lo, hi);
+    }
 }
 
 // eps, O (eigenvectors as rows) of h1; empty on failure

@@ -82,12 +82,12 @@ void clear_error();
 // ---- host mathematics of step 1 (setup.cpp) -------------------------------
 void gauss_legendre(int n, double *t, double *w);
 double bessel_i_scaled(int l, double z);  // exp(-z) i_l(z)
-double v_partial_wave(int l, double p, double pp, int n_terms, const double *V, const double *a);
+void bessel_i_scaled_all(int lmax, double z, double *out);  // l = 0 .. lmax
 // symmetric eigensolver: A (n x n, row-major) -> eigenvalues ascending,
 // vectors as rows with the largest-magnitude component positive.
 bool sym_eig(int n, std::vector<double> A, std::vector<double> &evals, std::vector<double> &rows);
-void pair_matrices(int N, const double *edges, int n_nodes, int l, int n_terms, const double *V,
-                   const double *a, std::vector<double> &v, std::vector<double> &h);
+void pair_matrices_all(int N, const double *edges, int n_nodes, int n_ch, int n_terms, const double *V,
+                       const double *a, std::vector<std::vector<double>> &v, std::vector<std::vector<double>> &h);
 void pair_eig(int N, const std::vector<double> &h, std::vector<double> &eps, std::vector<double> &O);
 inline double shell_volume(double lo, double hi) {
   // int_lo^hi p^2 dp, written to avoid cancellation for narrow bins
