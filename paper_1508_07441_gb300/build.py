@@ -30,7 +30,7 @@ def nvcc() -> str:
 
 
 def _flags():
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3",
                    "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 
 
@@ -40,7 +40,7 @@ def _stale(obj: str, src: str) -> bool:
     t = os.path.getmtime(obj)
     deps = [src, os.path.join(CSRC, "wpcd_internal.h"), os.path.join(CSRC, "common.cuh"),
             os.path.join(CSRC, "df_common.cuh"), os.path.join(CSRC, "tc_ptx.cuh"),
-            os.path.join(ROOT, "include", "wpcd.h")]
+            os.path.join(ROOT, "include", "wpcd.h"), os.path.abspath(__file__)]  # flags live here
     return any(os.path.getmtime(d) > t for d in deps)
 
 

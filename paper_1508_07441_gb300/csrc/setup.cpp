@@ -158,6 +158,12 @@ bool sym_eig(int n, std::vector<double> A, std::vector<double> &evals, std::vect
       for (int j = k + 1; j < n; ++j) q(i, j) -= s * u[j];
     }
   }
+  // the QR steps rotate pairs of columns of Q: keep Q transposed so that
+  // each rotation runs over two contiguous rows
+  std::vector<double> QT((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) QT[(size_t)j * n + i] = q(i, j);
+  auto qt = [&](int k, int i) -> double & { return QT[(size_t)k * n + i]; };
   std::vector<double> d(n), e(n, 0.0);
   for (int i = 0; i < n; ++i) d[i] = a(i, i);
   for (int i = 0; i + 1 < n; ++i) e[i] = a(i + 1, i);
@@ -192,10 +198,11 @@ bool sym_eig(int n, std::vector<double> A, std::vector<double> &evals, std::vect
         z = s * e[k + 1];
         e[k + 1] *= c;
       }
+      double *r0 = &qt(k, 0), *r1 = &qt(k + 1, 0);
       for (int i = 0; i < n; ++i) {
-        double qk = q(i, k), qk1 = q(i, k + 1);
-        q(i, k) = c * qk + s * qk1;
-        q(i, k + 1) = -s * qk + c * qk1;
+        const double qk = r0[i], qk1 = r1[i];
+        r0[i] = c * qk + s * qk1;
+        r1[i] = -s * qk + c * qk1;
       }
     }
   }
@@ -210,19 +217,17 @@ bool sym_eig(int n, std::vector<double> A, std::vector<double> &evals, std::vect
     int imax = 0;
     double big = -1.0;
     for (int i = 0; i < n; ++i)
-      if (std::fabs(q(i, c)) > big) { big = std::fabs(q(i, c)); imax = i; }
-    double sg = q(imax, c) < 0 ? -1.0 : 1.0;
-    for (int i = 0; i < n; ++i) rows[(size_t)k * n + i] = sg * q(i, c);
+      if (std::fabs(qt(c, i)) > big) { big = std::fabs(qt(c, i)); imax = i; }
+    double sg = qt(c, imax) < 0 ? -1.0 : 1.0;
+    for (int i = 0; i < n; ++i) rows[(size_t)k * n + i] = sg * qt(c, i);
   }
   return true;
 }
 
-// Pair matrices of channel l: the free-packet potential matrix v (Eq. vpot
-// with unit weight functions in the p^2 dp measure, n_nodes GL points per
-// bin) and h1 = diag(<p^2>) + v, whose eigen-decomposition (Eq. exp_z) is
-// pair_eig's
-// The potential matrices v (and h1 = h0 + v) of channels l = 0 .. n_ch - 1 in
-// the pair-momentum WP basis: v_l averaged over each pair of bins with
+// The pair matrices of channels l = 0 .. n_ch - 1: the free-packet potential
+// matrix v (Eq. vpot with unit weight functions in the p^2 dp measure) and
+// h1 = diag(<p^2>) + v, whose eigen-decomposition (Eq. exp_z) is pair_eig's.
+// v_l is averaged over each pair of bins with
 // n_nodes GL nodes per bin, rows in parallel on the host cores (each element
 // computed by one thread, in a fixed order: the result does not depend on the
 // thread count).  One Bessel recurrence per (node, node) pair and Gaussian
