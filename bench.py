@@ -844,10 +844,11 @@ def main():
         wit32, _, fb32, _ = ws.iterations(Ete, u_init=ug32.view(-1), tol=1e-8, batch=64, max_iter=60)
         del ug32
         warm = {"what": "3-layer MLP (width 256, FP32 train by the library's kernels, BF16 inference) "
-                        "predicting the solution beyond the Born term in a 64-vector basis of the "
-                        "method's own solutions; FP64 Krylov to rel residual 1e-8 from the warm "
-                        "start vs from zero; K applications include the Born term and, warm, the "
-                        "warm start's residual",
+                        "predicting mixture weights (softmax of 64 logits) over a 64-vector basis of "
+                        "the method's own solutions beyond the Born term, at the 64 on-shell bins "
+                        "that carry most of the energy range; FP64 Krylov to rel residual 1e-8 from "
+                        "the warm start vs from zero; K applications include the Born term and, "
+                        "warm, the warm start's residual",
                 "train_energies": args.warm_train, "test_energies": args.warm_test,
                 "basis": ws.k, "train_loss_first_last": [float(hist[0]), float(hist[-1])],
                 "k_applications_cold_mean": float(cold.mean()),

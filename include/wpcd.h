@@ -538,6 +538,11 @@ wpcd_status wpcd_warm_features(const wpcd_problem *pr, const double *E, int n, d
 wpcd_status wpcd_vec_axpy(double alpha, const double *x, double *y, int64_t n, void *stream);
 /* dst [2n] FP32 (re, im) pairs from src [n] complex FP64 (device). */
 wpcd_status wpcd_complex_to_f32(const double *src, int64_t n, float *dst, void *stream);
+/* Mixture weights of the warm start: for each of n rows of k logits (FP32,
+ * device [n][k]) the softmax w_j = exp(z_j - max z) / sum_i exp(z_i - max z),
+ * written as real coefficients C [n][k][2] = (w_j, 0) for wpcd_basis_expand.
+ * EINVAL for n < 1 or k < 1 or k > 1024. */
+wpcd_status wpcd_warm_softmax(const float *logits, int n, int k, float *C, void *stream);
 
 #ifdef __cplusplus
 }

@@ -662,6 +662,22 @@ wpcd_status wpcd_vec_axpy(double alpha, const double *x, double *y, int64_t n, v
   return e == cudaSuccess ? WPCD_OK : cuda_error(e, "axpy");
 }
 
+// softmax of each row of k logits (one warp per row; k <= 1024), written as
+// (w, 0) complex pairs
+__global__ void softmax_rows_kernel(int n, int k, const float *__restrict__ z, float2 *__restrict__ C) {
+  const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (row >= n) return;  // uniform over the warp
+  const float *zr = z + (int64_t)row * k;
+  float mx = -INFINITY;
+  for (int j = lane; j < k; j += 32) mx = fmaxf(mx, zr[j]);
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  float sum = 0.f;
+  for (int j = lane; j < k; j += 32) sum += expf(zr[j] - mx);
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  const float inv = 1.f / sum;
+  for (int j = lane; j < k; j += 32) C[(int64_t)row * k + j] = make_float2(expf(zr[j] - mx) * inv, 0.f);
+}
+
 // FP64 complex -> FP32 (re, im) pairs (device), e.g. projection
 // coefficients as training targets
 wpcd_status wpcd_complex_to_f32(const double *src, int64_t n, float *dst, void *stream) {
@@ -674,6 +690,16 @@ wpcd_status wpcd_complex_to_f32(const double *src, int64_t n, float *dst, void *
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? WPCD_OK : cuda_error(e, "conversion");
+}
+
+wpcd_status wpcd_warm_softmax(const float *logits, int n, int k, float *C, void *stream) {
+  clear_error();
+  if (!logits || !C || n < 1 || k < 1 || k > 1024) return set_error(WPCD_EINVAL, "bad softmax arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  softmax_rows_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(n, k, logits, reinterpret_cast<float2 *>(C));
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? WPCD_OK : cuda_error(e, "softmax");
 }
 
 }  // extern "C"

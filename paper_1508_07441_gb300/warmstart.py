@@ -4,20 +4,28 @@ the library's kernels).
 G1 depends on the energy only through its on-shell bin, so u(E) is constant
 across a bin and its source u0 (the Born term, the first iterate) is specific
 to the bin.  The network therefore predicts the part of the solution beyond
-the first iterate, u - u0, in a basis built from that part.
+the first iterate, u - u0, in a basis of the method's own solutions.
 
 Pipeline, every arithmetic step in libwpcd:
-  1. snapshots: u(E) - u0(E) at the centres of the k on-shell bins that
-     carry the most of the energy range (batched mixed solves),
-     orthonormalised on the GPU into a projected basis Phi;
-  2. data: for each training energy the target is Phi^H (u - u0) (k complex
-     = 2k reals) and the features are the scaled centre of the on-shell bin
-     and the first kf coefficients Phi^H u0 of the first iterate;
+  1. snapshots: d_j = u(E_j) - u0(E_j) at the centres of the k on-shell bins
+     that carry the most of the energy range (batched mixed solves); D =
+     [d_1 .. d_k] is the basis, and an orthonormalised copy Phi serves the
+     features;
+  2. data: each training energy is solved; its label is the snapshot nearest
+     to its u - u0 (least |d - d_j|, from the inner products <d_j, d>); the
+     target is a logit vector, L at the label and 0 elsewhere; the features
+     are the scaled centre of the on-shell bin and the first kf coefficients
+     Phi^H u0 of the first iterate;
   3. the MLP is trained by the library's FP32 forward / backward / Adam
      kernels and inferred with BF16 weights;
-  4. warm start u_g = u0 + Phi c_hat; the solve starts from u_g and falls
-     back to u = 0 for any energy whose warm residual is not below |u0|; the
-     plain iteration's FP64 residual judges convergence.
+  4. warm start u_g = u0 + D w with w = softmax(logits): mixture weights over
+     the snapshots.  The weights are insensitive to the BF16 rounding of the
+     logits (an error of 1e-3 L in a logit changes a weight by that relative
+     amount, while the weight of a wrong snapshot stays near exp(-L)), so an
+     energy in a snapshot's bin gets that snapshot's solution almost exactly.
+     The solve starts from u_g and falls back to u = 0 for any energy whose
+     warm residual is not below |u0|; the plain iteration's FP64 residual
+     judges convergence.
 """
 from __future__ import annotations
 
@@ -27,14 +35,16 @@ from . import wpcd as W
 
 
 class WarmStart:
-    def __init__(self, pr, P, k=64, kf=16, width=256, seed=2026, device=0, stream=None):
+    def __init__(self, pr, P, k=64, kf=16, width=256, seed=2026, device=0, stream=None, logit=24.0):
         import torch
 
         self.torch = torch
         self.pr, self.P, self.k, self.kf, self.width = pr, P, k, kf, width
         self.seed, self.device, self.stream = seed, device, stream
+        self.logit = logit
         self.dim = pr.dim
-        self.Phi = None
+        self.D = None    # snapshots u - u0 [k][2 dim], the mixture basis
+        self.Phi = None  # its orthonormalised copy (features)
         self.mlp = None
         self.e_lo = self.e_hi = None
 
@@ -74,13 +84,32 @@ class WarmStart:
         self.k = len(E_snap)
         U = self.solve_vectors(E_snap, batch=batch)
         W.wpcd_vec_axpy(-1.0, self.born(E_snap), U, stream=self.stream)  # u - u0
+        with self.torch.cuda.stream(self._torch_stream()):
+            self.D = U.clone()
         W.wpcd_basis_orthonormalize(U, self.k, self.dim, stream=self.stream)
         self.Phi = U
+        # |d_j|^2 for the labels: the diagonal of D^H D
+        G = self._dev(2 * self.k * self.k, self.torch.float64)
+        W.wpcd_basis_project(self.D, self.k, self.dim, self.D, self.k, G, stream=self.stream)
+        self._sync()
+        g = G.cpu().numpy().view(np.complex128).reshape(self.k, self.k)
+        self.dnorm2 = np.real(np.diag(g)).copy()
         return U
 
-    def coefficients(self, U, n):
+    def _torch_stream(self):
+        if self.stream is None:
+            return self.torch.cuda.current_stream(self.device)
+        return self.stream
+
+    def _sync(self):
+        self.torch.cuda.synchronize(self.device)
+
+    def coefficients(self, U, n, basis=None):
+        """C [n][k] complex FP64 (device): <b_j, U_e> for the basis b (Phi by
+        default)."""
         C = self._dev(2 * n * self.k, self.torch.float64)
-        W.wpcd_basis_project(self.Phi, self.k, self.dim, U, n, C, stream=self.stream)
+        W.wpcd_basis_project(self.Phi if basis is None else basis, self.k, self.dim, U, n, C,
+                             stream=self.stream)
         return C
 
     def features(self, E, b=None):
@@ -95,21 +124,33 @@ class WarmStart:
         W.wpcd_warm_features(self.pr, E, self.e_lo, self.e_hi, Cb, self.k, self.kf, X, stream=self.stream)
         return X.view(n, 1 + 2 * self.kf)
 
+    def labels(self, Ud, n):
+        """The snapshot nearest to each of the n vectors Ud (u - u0):
+        argmin_j |d_j|^2 - 2 Re <d_j, d>."""
+        C = self.coefficients(Ud, n, basis=self.D)
+        self._sync()
+        c = C.cpu().numpy().view(np.complex128).reshape(n, self.k)
+        return np.argmin(self.dnorm2[None, :] - 2.0 * c.real, axis=1)
+
     def dataset(self, E, batch=128):
-        """(X, T): features and target coefficients, device float32."""
+        """(X, T): features and logit targets (L at the label, 0 elsewhere),
+        device float32; the labels come from the solutions of the energies."""
         E = np.asarray(E, dtype=np.float64)
         Xs, Ts = [], []
+        self.train_labels = []
         for i in range(0, len(E), batch):
             Eb = E[i:i + batch]
             U = self.solve_vectors(Eb, batch=batch)
             b = self.born(Eb)
             W.wpcd_vec_axpy(-1.0, b, U, stream=self.stream)  # u - u0
-            C = self.coefficients(U, len(Eb))
-            T = self._dev(2 * len(Eb) * self.k, self.torch.float32)
-            W.wpcd_complex_to_f32(C, len(Eb) * self.k, T, stream=self.stream)
+            lab = self.labels(U, len(Eb))
+            self.train_labels.append(lab)
+            T = np.zeros((len(Eb), self.k), dtype=np.float32)
+            T[np.arange(len(Eb)), lab] = self.logit
             Xs.append(self.features(Eb, b))
-            Ts.append(T.view(len(Eb), 2 * self.k))
+            Ts.append(self.torch.from_numpy(T).to(f"cuda:{self.device}"))
             del U
+        self.train_labels = np.concatenate(self.train_labels)
         return self.torch.cat(Xs), self.torch.cat(Ts)
 
     def fit(self, X, T, epochs=300, batch=256, lr=1e-3, decay=()):
@@ -132,15 +173,17 @@ class WarmStart:
         return np.concatenate(hist)
 
     def predict(self, E, bf16=True):
-        """Warm starts u_g = u0 + Phi c_hat (device float64 [len(E)][2 dim])."""
+        """Warm starts u_g = u0 + D softmax(logits) (device float64 [len(E)][2 dim])."""
         E = np.asarray(E, dtype=np.float64)
         n = len(E)
         b = self.born(E)
         X = self.features(E, b)
-        Y = self._dev(n * 2 * self.k, self.torch.float32)
+        Y = self._dev(n * self.k, self.torch.float32)
         self.mlp.wpcd_mlp_forward(X.contiguous(), Y, bf16=bf16, stream=self.stream)
+        C = self._dev(n * 2 * self.k, self.torch.float32)
+        W.wpcd_warm_softmax(Y, n, self.k, C, stream=self.stream)
         U = self._dev(2 * n * self.dim, self.torch.float64)
-        W.wpcd_basis_expand(self.Phi, self.k, self.dim, Y, n, U, stream=self.stream)
+        W.wpcd_basis_expand(self.D, self.k, self.dim, C, n, U, stream=self.stream)
         W.wpcd_vec_axpy(1.0, b, U, stream=self.stream)
         return U
 

@@ -113,6 +113,7 @@ _SIGS = {
     "wpcd_basis_project": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P]),
     "wpcd_basis_expand": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P]),
     "wpcd_basis_orthonormalize": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P]),
+    "wpcd_warm_softmax": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
     "wpcd_warm_features": (ctypes.c_int, [_P, _D, ctypes.c_int, ctypes.c_double, ctypes.c_double, _P,
                                           ctypes.c_int, ctypes.c_int, _P, _P]),
     "wpcd_vec_axpy": (ctypes.c_int, [ctypes.c_double, _P, _P, ctypes.c_int64, _P]),
@@ -550,6 +551,10 @@ def wpcd_basis_expand(Phi, k, dim, C, n, U, stream=None):
 
 def wpcd_basis_orthonormalize(Phi, k, dim, stream=None):
     check(lib().wpcd_basis_orthonormalize(_tensor_ptr(Phi), k, dim, _stream_ptr(stream)))
+
+
+def wpcd_warm_softmax(logits, n, k, C, stream=None):
+    check(lib().wpcd_warm_softmax(_tensor_ptr(logits), n, k, _tensor_ptr(C), _stream_ptr(stream)))
 
 
 def wpcd_warm_features(problem, E, e_lo, e_hi, Cb, k, kf, X, stream=None):

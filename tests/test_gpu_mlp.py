@@ -102,9 +102,10 @@ def test_warm_start_saves_iterations(W, orc):
     warm, rw, fb, Uw = ws.iterations(E, u_init=ug, tol=1e-8)
     assert np.all(rc <= 1e-8) and np.all(rw <= 1e-8)   # equal residual
     print(f"warm start: {cold.mean():.2f} -> {warm.mean():.2f} K applications, fallbacks {fb.sum()}")
-    # measured 12.85 -> 11.44 (11 %); the snapshots hold the solutions of the
-    # bins that carry most of the energy range
-    assert warm.mean() < 0.95 * cold.mean(), (warm.mean(), cold.mean())
+    # measured 12.85 -> 2.54 (80 % fewer): the snapshots hold the solutions
+    # of the bins that carry most of the energy range, and the mixture
+    # weights pick the energy's own bin
+    assert warm.mean() < 0.5 * cold.mean(), (warm.mean(), cold.mean())
     assert np.max(np.abs(Uw - Uc) / np.abs(Uc)) < 1e-6
     opr = orc.Problem(dict(pe=pe, qe=qe, n_p=4, n_q=4, n_x=16, n_ch=3, V=[-3.0], a=[1.0], n_pair_nodes=8))
     for k in (0, 17, 47):
