@@ -117,6 +117,12 @@ def test_wait_limit_knob_argument_checks(W):
         assert L.wpcd_debug_expire_first_wait(kernel, role) == W.WPCD_OK, (kernel, role)
 
 
+def test_warm_softmax_argument_checks(W):
+    L = W.lib()
+    for n, k in ((0, 4), (4, 0), (4, 1025)):
+        assert L.wpcd_warm_softmax(None, n, k, None, None) == W.WPCD_EINVAL
+
+
 def test_no_cpu_fallback_when_library_missing(W, monkeypatch, tmp_path):
     monkeypatch.setattr(W, "LIB_PATH", str(tmp_path / "missing.so"))
     monkeypatch.setattr(W, "_lib", None)

@@ -78,6 +78,24 @@ def test_training_reduces_loss(W):
     assert l1 < 0.02 * l0 and hist[-1] < hist[0]
 
 
+def test_warm_softmax_matches_numpy(W):
+    """mixture weights of the warm start: row softmax of the logits as (w, 0)
+    pairs, one warp per row; k beyond 32 (several entries per lane) and a
+    ragged last row block"""
+    import torch
+
+    rng = np.random.default_rng(7)
+    for n, k in ((13, 64), (3, 5), (9, 100)):
+        z = (rng.standard_normal((n, k)) * 8).astype(np.float32)
+        C = torch.full((n * 2 * k,), float("nan"), dtype=torch.float32, device="cuda")
+        W.wpcd_warm_softmax(torch.from_numpy(z).cuda(), n, k, C)
+        got = C.cpu().numpy().reshape(n, k, 2)
+        e = np.exp(z.astype(np.float64) - z.max(axis=1, keepdims=True))
+        ref = e / e.sum(axis=1, keepdims=True)
+        assert np.all(got[:, :, 1] == 0.0)
+        assert np.max(np.abs(got[:, :, 0] - ref)) < 2e-6, (n, k)
+
+
 def test_warm_start_saves_iterations(W, orc):
     """Trained on the method's own solutions of a 3-channel system, the
     network's warm start reaches the same FP64 relative residual (1e-8) in
