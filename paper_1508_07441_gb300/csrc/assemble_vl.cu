@@ -182,47 +182,75 @@ __global__ void __launch_bounds__(VL_THREADS) vl_rows_kernel(VlParams P, int64_t
   }
 }
 
-// P_l(x) for l = 0 .. lmax by the three-term recurrence
-__device__ __forceinline__ void legendre_all(int lmax, double x, double *Pl) {
+// P_0 .. P_{NCH-1} at x by the three-term recurrence (constant coefficients)
+template <int NCH>
+__device__ __forceinline__ void legendre_t(double x, double *Pl) {
   Pl[0] = 1.0;
-  if (lmax >= 1) Pl[1] = x;
-  for (int n = 1; n < lmax; ++n) Pl[n + 1] = ((2.0 * n + 1.0) * x * Pl[n] - n * Pl[n - 1]) / (n + 1.0);
+  if (NCH > 1) Pl[1] = x;
+#pragma unroll
+  for (int n = 1; n + 1 < NCH; ++n)
+    Pl[n + 1] = (double(2 * n + 1) / double(n + 1)) * x * Pl[n] - (double(n) / double(n + 1)) * Pl[n - 1];
 }
 
-// one thread per nonzero of row c (CTA c): sum over the cell's nodes
+// 1/sqrt(d) for d > 0: an FP32 seed refined by one Newton-Raphson step in
+// FP64 (relative error about 1.5 e^2 for the seed's e < 3e-7: below 2e-13);
+// d outside the FP32 range takes the FP64 rsqrt
+__device__ __forceinline__ double vl_rsqrt(double d) {
+  const float f = __double2float_rn(d);
+  if (!(f >= 1e-30f && f <= 1e30f)) return rsqrt(d);
+  const double r = (double)rsqrtf(f);
+  const double e = fma(-(d * r), r, 1.0);
+  return fma(0.5 * r, e, r);
+}
+
+// one thread per nonzero of row c (CTA c): sum over the cell's nodes, in a
+// fixed order, of the GL integral over the node's y-interval for the target
+template <int NCH>
 __global__ void __launch_bounds__(VL_THREADS) vl_value_kernel(VlParams P, const int64_t *row_ptr,
                                                              const int32_t *cols, int64_t nnz, double *val) {
+  constexpr int NPAIR = pair_count(NCH);
   const int c = blockIdx.x, i = c / P.M, j = c % P.M;
   const int64_t b0 = row_ptr[c], b1 = row_ptr[c + 1];
   for (int64_t o = b0 + threadIdx.x; o < b1; o += blockDim.x) {
     const int t = cols[o], it = t / P.M, jt = t % P.M;
-    double sum[kMaxPairs];
-    for (int m = 0; m < P.n_pairs; ++m) sum[m] = 0.0;
+    double sum[NPAIR];
+#pragma unroll
+    for (int m = 0; m < NPAIR; ++m) sum[m] = 0.0;
     for (int a = 0; a < P.n_p; ++a)
       for (int b = 0; b < P.n_q; ++b) {
         const double p = P.pn[i * P.n_p + a], q = P.qn[j * P.n_q + b];
         const VlNode nd(p, q);
         double lo, hi;
         if (!vl_interval(P, nd, it, jt, lo, hi)) continue;
-        const double Wpq = P.wp[i * P.n_p + a] * P.wq[j * P.n_q + b];
         const double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
+        const double hW = P.wp[i * P.n_p + a] * P.wq[j * P.n_q + b] * half;
+        // p'.q' = nA y + nB = -p^2/2 - p q y / 2 + 3 q^2 / 8
+        const double nA = -0.5 * p * q, nB = 0.375 * q * q - 0.5 * p * p;
         for (int x = 0; x < P.n_x; ++x) {
-          const double y = mid + half * P.yn[x];
-          const double W = Wpq * (half * P.wy[x]);
-          // y' = p'.q' / (|p'| |q'|), p'.q' = -p^2/2 - p q y / 2 + 3 q^2 / 8
-          const double p2 = fma(nd.A, y, nd.Bp), q2 = fma(nd.C, y, nd.Dq);
-          const double num = -0.5 * p * p - 0.5 * p * q * y + 0.375 * q * q;
-          const double den = sqrt(fmax(p2, 0.0) * fmax(q2, 0.0));
-          const double yp = den > 0.0 ? fmin(1.0, fmax(-1.0, num / den)) : 0.0;
-          double Py[kMaxCh], Pyp[kMaxCh];
-          legendre_all(P.n_ch - 1, y, Py);
-          legendre_all(P.n_ch - 1, yp, Pyp);
-          for (int m = 0; m < P.n_pairs; ++m) sum[m] += W * Py[P.pl[m]] * Pyp[P.plp[m]];
+          const double y = fma(half, P.yn[x], mid);
+          const double W = hW * P.wy[x];
+          const double p2 = fma(nd.A, y, nd.Bp), q2 = fma(nd.C, y, nd.Dq), num = fma(nA, y, nB);
+          const double den2 = fmax(p2, 0.0) * fmax(q2, 0.0);
+          const double yp = den2 > 0.0 ? fmin(1.0, fmax(-1.0, num * vl_rsqrt(den2))) : 0.0;
+          double Py[NCH], Pyp[NCH];
+          legendre_t<NCH>(y, Py);
+          legendre_t<NCH>(yp, Pyp);
+#pragma unroll
+          for (int l = 0; l < NCH; ++l) Py[l] *= W;
+#pragma unroll
+          for (int m = 0; m < NPAIR; ++m) sum[m] = fma(Py[pair_first(NCH, m)], Pyp[pair_second(NCH, m)], sum[m]);
         }
       }
     const double nrm = P.rsb[c] * P.rsb[t];
-    for (int m = 0; m < P.n_pairs; ++m) val[(size_t)m * nnz + o] = sum[m] * nrm * P.cnorm[m];
+#pragma unroll
+    for (int m = 0; m < NPAIR; ++m) val[(size_t)m * nnz + o] = sum[m] * nrm * P.cnorm[m];
   }
+}
+
+template <int NCH>
+void launch_vl_value(const VlParams &P, int n_cells, cudaStream_t s, const int64_t *row_ptr, const int32_t *cols,
+                     int64_t nnz, double *val) {
+  vl_value_kernel<NCH><<<n_cells, VL_THREADS, 0, s>>>(P, row_ptr, cols, nnz, val);
 }
 
 }  // namespace
@@ -332,7 +360,13 @@ wpcd_status assemble_vl(wpcd_grid *g, int n_ch, cudaStream_t s, wpcd_P **out) {
   if ((e = dev_malloc(&Pm->val64, sizeof(double) * (nz > 0 ? nz : 1) * P.n_pairs)) != cudaSuccess)
     return fail(cuda_error(e, "cudaMalloc val"));
   vl_rows_kernel<<<n_cells, VL_THREADS, vl_smem, s>>>(P, nullptr, Pm->row_ptr, Pm->col, err, nullptr);
-  vl_value_kernel<<<n_cells, VL_THREADS, 0, s>>>(P, Pm->row_ptr, Pm->col, nz, Pm->val64);
+  switch (n_ch) {
+    case 1: launch_vl_value<1>(P, n_cells, s, Pm->row_ptr, Pm->col, nz, Pm->val64); break;
+    case 2: launch_vl_value<2>(P, n_cells, s, Pm->row_ptr, Pm->col, nz, Pm->val64); break;
+    case 3: launch_vl_value<3>(P, n_cells, s, Pm->row_ptr, Pm->col, nz, Pm->val64); break;
+    case 4: launch_vl_value<4>(P, n_cells, s, Pm->row_ptr, Pm->col, nz, Pm->val64); break;
+    default: launch_vl_value<5>(P, n_cells, s, Pm->row_ptr, Pm->col, nz, Pm->val64); break;
+  }
   count_launches(2);
   cudaEventRecord(ev1, s);
   if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaEventSynchronize(ev1)) != cudaSuccess)
