@@ -46,6 +46,8 @@ struct AsmParams {
   int N, M, n_p, n_q, n_x, n_nodes, np2, nbits, n_ch, n_pairs;
   uint64_t nx_magic;  // ceil(2^32 / n_x): node / n_x by a multiply and a shift
   int stage_rows;     // fill: rows staged in shared memory (the longest row), 0: direct writes
+  int slot_bits;      // count pass: hash set of 2^slot_bits slots, filled to half at most
+  int *err;           // count pass: set when a cell's distinct targets overflow the set
   int warp_runs;      // n_x a multiple of 32 and the y nodes ascending: a warp step is one
                       // (p, q) pair's consecutive y nodes, with monotone targets
   int pl[kMaxPairs], plp[kMaxPairs];
@@ -143,12 +145,14 @@ __global__ void __launch_bounds__(kThreads) count_kernel(AsmParams P, int64_t *c
   long long *qe2 = pe2 + (P.N + 1);
   BinConst *abk = reinterpret_cast<BinConst *>(qe2 + (P.M + 1));  // per (a, b)
   double *ys = reinterpret_cast<double *>(abk + P.n_p * P.n_q);
-  // 4 np2 words: the hash set (2 np2 slots), then the per-warp counts
+  // 2 S words: the hash set (S slots) and the ranks by slot, then the
+  // per-warp counts [kWarps][S / 2] (a cell has at most S / 2 distinct targets)
+  const int S = 1 << P.slot_bits, WS = S / 2;
   uint32_t *table = reinterpret_cast<uint32_t *>(ys + P.n_x);
-  uint16_t *wc = reinterpret_cast<uint16_t *>(table);  // [kWarps][np2]
-  uint32_t *keys = table + 4 * P.np2;                   // distinct targets, then the sorted keys
+  uint16_t *wc = reinterpret_cast<uint16_t *>(table);
+  uint32_t *keys = table + 2 * S;                       // distinct targets, then the sorted keys
   int *off = reinterpret_cast<int *>(keys + P.np2 + P.np2 / 32);  // per-rank counts, then offsets
-  __shared__ int n_distinct, n_fill, n_valid, warp_tot[kWarps];
+  __shared__ int n_distinct, n_fill, n_valid, overflow, warp_tot[kWarps];
 
   const int c = blockIdx.x;
   const int i = c / P.M, j = c % P.M;
@@ -167,11 +171,12 @@ __global__ void __launch_bounds__(kThreads) count_kernel(AsmParams P, int64_t *c
     abk[ab] = BinConst{A, Bp, C, D};
   }
   for (int x = threadIdx.x; x < P.n_x; x += kThreads) ys[x] = P.yn[x];
-  for (int k = threadIdx.x; k < 2 * np2; k += kThreads) table[k] = kInvalid;
+  for (int k = threadIdx.x; k < S; k += kThreads) table[k] = kInvalid;
   if (threadIdx.x == 0) {
     n_distinct = 0;
     n_fill = 0;
     n_valid = 0;
+    overflow = 0;
   }
   __syncthreads();
   // bin the nodes, thread t taking nodes t R .. t R + R - 1: consecutive y
@@ -179,7 +184,7 @@ __global__ void __launch_bounds__(kThreads) count_kernel(AsmParams P, int64_t *c
   // after a binary search for the first node of each pair the bins follow
   // by short walks (both directions: the y order is not assumed)
   const long long pmax2 = pe2[P.N], qmax2 = qe2[P.M];
-  const int bits = P.nbits + 1;
+  const int bits = P.slot_bits;
   // the distinct targets go into the hash set here too (once per run of
   // equal targets along the thread's nodes); each node keeps its slot
   uint32_t *tg = reinterpret_cast<uint32_t *>(off);  // targets by node index
@@ -218,6 +223,7 @@ __global__ void __launch_bounds__(kThreads) count_kernel(AsmParams P, int64_t *c
           bool fresh;
           sl = set_insert(table, bits, t, fresh);
           if (fresh) atomicAdd(&n_distinct, 1);
+          if (sl < 0) overflow = 1;
         }
       }
       prev_t = t;
@@ -241,9 +247,16 @@ __global__ void __launch_bounds__(kThreads) count_kernel(AsmParams P, int64_t *c
   // the distinct targets (list) with their slots; the rank of each is the
   // number of smaller ones (a row has tens to a few hundred), stored by slot
   const int nr = n_distinct;
-  uint32_t *rank_of = table + 2 * np2;  // by slot
+  if (overflow || nr > WS) {  // uniform (shared values after a barrier): the host reruns with a larger set
+    if (threadIdx.x == 0) {
+      atomicOr(P.err, 1);
+      counts[c] = 0;
+    }
+    return;
+  }
+  uint32_t *rank_of = table + S;  // by slot
   int *lslot = off;                      // the targets by node index are in registers now
-  for (int k = threadIdx.x; k < 2 * np2; k += kThreads) {
+  for (int k = threadIdx.x; k < S; k += kThreads) {
     const uint32_t v = table[k];
     if (v != kInvalid) {
       const int at = atomicAdd(&n_fill, 1);
@@ -266,7 +279,7 @@ __global__ void __launch_bounds__(kThreads) count_kernel(AsmParams P, int64_t *c
   // the hash set is dead: per-warp counts per rank in its place
   for (int r = threadIdx.x; r < nr; r += kThreads)
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) wc[w * np2 + r] = 0;
+    for (int w = 0; w < kWarps; ++w) wc[w * WS + r] = 0;
   __syncthreads();
   // within the warp: nodes of one rank in lane order, k by k.  When n_x is
   // a multiple of 32 the lanes of a step are consecutive y nodes of one
@@ -290,9 +303,9 @@ __global__ void __launch_bounds__(kThreads) count_kernel(AsmParams P, int64_t *c
     } else {
       peers = __match_any_sync(0xffffffffu, r);
     }
-    const int base = r >= 0 ? (int)wc[warp * np2 + r] : 0;
+    const int base = r >= 0 ? (int)wc[warp * WS + r] : 0;
     __syncwarp();
-    if (r >= 0 && (peers & lower) == 0) wc[warp * np2 + r] = (uint16_t)(base + __popc(peers));
+    if (r >= 0 && (peers & lower) == 0) wc[warp * WS + r] = (uint16_t)(base + __popc(peers));
     __syncwarp();
     lp[k] = base + __popc(peers & lower);
   }
@@ -302,8 +315,8 @@ __global__ void __launch_bounds__(kThreads) count_kernel(AsmParams P, int64_t *c
     int s = 0;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) {
-      const int t = wc[w * np2 + r];
-      wc[w * np2 + r] = (uint16_t)s;
+      const int t = wc[w * WS + r];
+      wc[w * WS + r] = (uint16_t)s;
       s += t;
     }
     off[r] = s;
@@ -316,7 +329,7 @@ __global__ void __launch_bounds__(kThreads) count_kernel(AsmParams P, int64_t *c
     const int r = rk[k];
     if (r >= 0) {
       const int n = warp * 32 * R + k * 32 + lane;
-      keys[off[r] + wc[warp * np2 + r] + lp[k]] = (tgt[k] << P.nbits) | (uint32_t)n;
+      keys[off[r] + wc[warp * WS + r] + lp[k]] = (tgt[k] << P.nbits) | (uint32_t)n;
     }
   }
   for (int k = n_valid + threadIdx.x; k < np2; k += kThreads) keys[k] = kInvalid;
@@ -893,39 +906,60 @@ wpcd_status assemble(wpcd_grid *g, int n_ch, int prec, cudaStream_t s, wpcd_P **
     return st;
   };
   cudaError_t e;
-  // counts[n_cells]: the longest row
-  if ((e = dev_malloc(&counts, sizeof(int64_t) * (n_cells + 1))) != cudaSuccess)
+  // counts[n_cells]: the longest row; counts[n_cells + 1]: the overflow word
+  if ((e = dev_malloc(&counts, sizeof(int64_t) * (n_cells + 2))) != cudaSuccess)
     return fail(cuda_error(e, "cudaMalloc counts"));
-  if ((e = cudaMemsetAsync(counts + n_cells, 0, sizeof(int64_t), s)) != cudaSuccess)
-    return fail(cuda_error(e, "counts clear"));
   if ((e = dev_malloc(&sorted, sizeof(uint32_t) * (size_t)n_cells * np2)) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc sorted keys"));
   if ((e = dev_malloc(&Pm->row_ptr, sizeof(int64_t) * (n_cells + 1))) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc row_ptr"));
 
   cudaEventRecord(ev0, s);
-  // edges, node constants, y nodes; hash set / per-warp counts (4 np2
-  // words), keys (np2), per-rank offsets (np2)
-  const size_t smem_count = sizeof(long long) * (P.N + P.M + 2) + sizeof(BinConst) * P.n_p * P.n_q +
-                            sizeof(double) * P.n_x + sizeof(uint32_t) * (6 * (size_t)np2 + np2 / 16);
-  if (smem_count > 227 * 1024) return fail(set_error(WPCD_EINVAL, "lattice edges and node count exceed shared memory"));
-  switch (np2 / kThreads) {
-    case 1: e = launch_count<1>(P, n_cells, smem_count, s, counts, sorted); break;
-    case 2: e = launch_count<2>(P, n_cells, smem_count, s, counts, sorted); break;
-    case 4: e = launch_count<4>(P, n_cells, smem_count, s, counts, sorted); break;
-    case 8: e = launch_count<8>(P, n_cells, smem_count, s, counts, sorted); break;
-    case 16: e = launch_count<16>(P, n_cells, smem_count, s, counts, sorted); break;
-    default: e = launch_count<32>(P, n_cells, smem_count, s, counts, sorted); break;
-  }
-  if (e != cudaSuccess) return fail(cuda_error(e, "count pass launch"));
-  cudaEventRecord(evc, s);
-  scan_kernel<<<1, 1024, 0, s>>>(counts, n_cells, Pm->row_ptr);
-  cudaEventRecord(evs, s);
-  count_launches(2);
-  if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_error(e, "count/scan launch"));
+  // the count pass's hash set: 4 (N + M) slots (at least 512), which the
+  // distinct targets of a cell fill to half at most in practice; a cell
+  // that overflows it sets the error word and the pass runs again with
+  // 2 np2 slots, which no cell can overflow (it has at most np2 targets)
+  int full_bits = 1;
+  while ((1 << full_bits) < 2 * np2) ++full_bits;
+  int bits0 = 9;
+  while ((1 << bits0) < 4 * (P.N + P.M) && bits0 < full_bits) ++bits0;
+  if (bits0 > full_bits) bits0 = full_bits;
+  P.err = reinterpret_cast<int *>(counts + n_cells + 1);
   int64_t nnz = 0, longest = 0;
-  if ((e = cudaMemcpyAsync(&nnz, Pm->row_ptr + n_cells, sizeof(int64_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(&longest, counts + n_cells, sizeof(int64_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-    return fail(cuda_error(e, "nnz readback"));
-  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(cuda_error(e, "count pass"));
+  for (int attempt = 0;; ++attempt) {
+    P.slot_bits = attempt == 0 ? bits0 : full_bits;
+    // edges, node constants, y nodes; hash set and ranks (2 S words, then
+    // the per-warp counts), keys and per-rank offsets (np2 + np2 / 32 each)
+    const size_t smem_count = sizeof(long long) * (P.N + P.M + 2) + sizeof(BinConst) * P.n_p * P.n_q +
+                              sizeof(double) * P.n_x +
+                              sizeof(uint32_t) * (2 * ((size_t)1 << P.slot_bits) + 2 * (size_t)np2 + np2 / 16);
+    if (smem_count > 227 * 1024)
+      return fail(set_error(WPCD_EINVAL, "lattice edges and node count exceed shared memory"));
+    if ((e = cudaMemsetAsync(counts + n_cells, 0, 2 * sizeof(int64_t), s)) != cudaSuccess)
+      return fail(cuda_error(e, "counts clear"));
+    switch (np2 / kThreads) {
+      case 1: e = launch_count<1>(P, n_cells, smem_count, s, counts, sorted); break;
+      case 2: e = launch_count<2>(P, n_cells, smem_count, s, counts, sorted); break;
+      case 4: e = launch_count<4>(P, n_cells, smem_count, s, counts, sorted); break;
+      case 8: e = launch_count<8>(P, n_cells, smem_count, s, counts, sorted); break;
+      case 16: e = launch_count<16>(P, n_cells, smem_count, s, counts, sorted); break;
+      default: e = launch_count<32>(P, n_cells, smem_count, s, counts, sorted); break;
+    }
+    if (e != cudaSuccess) return fail(cuda_error(e, "count pass launch"));
+    cudaEventRecord(evc, s);
+    scan_kernel<<<1, 1024, 0, s>>>(counts, n_cells, Pm->row_ptr);
+    cudaEventRecord(evs, s);
+    count_launches(2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_error(e, "count/scan launch"));
+    int64_t flag = 0;
+    if ((e = cudaMemcpyAsync(&nnz, Pm->row_ptr + n_cells, sizeof(int64_t), cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(&longest, counts + n_cells, sizeof(int64_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&flag, counts + n_cells + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess)
+      return fail(cuda_error(e, "nnz readback"));
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(cuda_error(e, "count pass"));
+    if (!flag) break;
+    if (P.slot_bits == full_bits) return fail(set_error(WPCD_ECUDA, "count pass: hash set overflow"));
+  }
   Pm->nnz = nnz;
   size_t nz = nnz > 0 ? (size_t)nnz : 1;
   if ((e = dev_malloc(&Pm->col, sizeof(int32_t) * nz)) != cudaSuccess) return fail(cuda_error(e, "cudaMalloc col"));

@@ -95,6 +95,25 @@ def test_assemble_matches_oracle(W, orc, N, M, nodes, n_ch, jit, prec):
     assert st["n_abs_only"] <= (0.01 if prec == "fp32c" else 0.005) * st["n"], st
 
 
+def test_assemble_rows_beyond_first_hash_set(W, orc):
+    """60 fine bins and one coarse outer bin, 16 x 16 x 32 nodes per cell (the
+    8192-node maximum): rows of the coarse cells reach 327 targets, more than
+    half the count pass's first hash set (512 slots for N + M = 122), so the
+    pass runs again with the full set; the result matches the oracle as
+    everywhere else"""
+    pe = np.concatenate([np.linspace(0.0, 4.0, 61), [8.0]])
+    nodes, n_ch = (16, 16, 32), 1
+    pr = W.Problem(pe, pe, *nodes, n_ch, (-6.0,), (1.0,))
+    ref = orc.P0(pe, pe, *nodes, n_ch, with_abs=True)
+    assert np.diff(ref["row_ptr"]).max() > 256
+    for prec in ("fp64", "fp32c"):
+        P = pr.wpcd_assemble_P(W.WPCD_FP64 if prec == "fp64" else W.WPCD_FP32C)
+        rp, col, val = P.wpcd_P_export()
+        assert np.array_equal(rp, ref["row_ptr"])
+        assert np.array_equal(col, ref["col"])
+        assert _excess(val.T, ref["val"], ref["absval"], prec) <= 1.0
+
+
 def test_assemble_deterministic(W):
     pe, qe = _inputs(30, 30)
     pr = W.Problem(pe, qe, 8, 8, 32, 3, (-6.0,), (1.0,))
