@@ -452,16 +452,24 @@ __device__ __forceinline__ void legendre_w(real y, real W, real hW, real *P) {
 }
 
 // 1/sqrt(d) for d > 0 in FP64 by one Newton-Raphson step r <- r + r (1 -
-// d r^2) / 2 from the FP32 reciprocal square root of d rounded to FP32:
-// for a seed with relative error e the step leaves about 1.5 e^2 (the seed
-// is within 3e-7, so the result within about 2e-13); d outside the FP32
-// range takes the FP64 rsqrt
+// d r^2) / 2 from the FP32 reciprocal square root of d: for a seed with
+// relative error e the step leaves about 1.5 e^2 (the seed is within 3e-7,
+// so the result within about 2e-13).  The seed's float is formed from d's
+// exponent and leading mantissa bits, and the FP32 result widened, by
+// integer operations, so that no conversion occupies the FP64 pipe; d
+// outside 2^-99 .. 2^99 takes the FP64 rsqrt
 __device__ __forceinline__ double rsqrt_newton(double d) {
-  const float f = __double2float_rn(d);
-  if (!(f >= 1e-30f && f <= 1e30f)) return rsqrt(d);
-  const double r = (double)rsqrtf(f);
+  const long long b = __double_as_longlong(d);
+  const int ex = (int)((b >> 52) & 0x7ff) - 1023;
+  if (ex < -99 || ex > 99) return rsqrt(d);
+  const unsigned fb = ((unsigned)(ex + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff);
+  const unsigned rb = __float_as_uint(rsqrtf(__uint_as_float(fb)));
+  const double r = __longlong_as_double(((long long)((int)((rb >> 23) & 0xff) - 127 + 1023) << 52) |
+                                        ((long long)(rb & 0x7fffff) << 29));
   const double e = fma(-(d * r), r, 1.0);  // 1 - d r^2
-  return fma(0.5 * r, e, r);
+  // r / 2 by decrementing the exponent (r is normal): no FP64 multiply
+  const double half_r = __longlong_as_double(__double_as_longlong(r) - (1LL << 52));
+  return fma(half_r, e, r);
 }
 
 // Per (p, q) node pair constants of one source cell (FP64):

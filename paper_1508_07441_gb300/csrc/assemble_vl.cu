@@ -194,13 +194,21 @@ __device__ __forceinline__ void legendre_t(double x, double *Pl) {
 
 // 1/sqrt(d) for d > 0: an FP32 seed refined by one Newton-Raphson step in
 // FP64 (relative error about 1.5 e^2 for the seed's e < 3e-7: below 2e-13);
-// d outside the FP32 range takes the FP64 rsqrt
+// the seed's float is cut from d's bits and the result widened by integer
+// operations (no conversion on the FP64 pipe); d outside 2^-99 .. 2^99 takes
+// the FP64 rsqrt
 __device__ __forceinline__ double vl_rsqrt(double d) {
-  const float f = __double2float_rn(d);
-  if (!(f >= 1e-30f && f <= 1e30f)) return rsqrt(d);
-  const double r = (double)rsqrtf(f);
+  const long long b = __double_as_longlong(d);
+  const int ex = (int)((b >> 52) & 0x7ff) - 1023;
+  if (ex < -99 || ex > 99) return rsqrt(d);
+  const unsigned fb = ((unsigned)(ex + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff);
+  const unsigned rb = __float_as_uint(rsqrtf(__uint_as_float(fb)));
+  const double r = __longlong_as_double(((long long)((int)((rb >> 23) & 0xff) - 127 + 1023) << 52) |
+                                        ((long long)(rb & 0x7fffff) << 29));
   const double e = fma(-(d * r), r, 1.0);
-  return fma(0.5 * r, e, r);
+  // r / 2 by decrementing the exponent (r is normal): no FP64 multiply
+  const double half_r = __longlong_as_double(__double_as_longlong(r) - (1LL << 52));
+  return fma(half_r, e, r);
 }
 
 // one thread per nonzero of row c (CTA c): sum over the cell's nodes, in a
