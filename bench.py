@@ -640,6 +640,7 @@ def run_kernel(args):
     flush = L2Flush()
     mode = W.WPCD_SPMM_FP32 if fp32 else W.WPCD_SPMM_FP64
     pr.wpcd_spmm(P, y, z, B, mode=mode)  # tuning (and the FP32 value copy)
+    shape = pr.wpcd_tune_spmm(P, B, fp32=fp32)  # the cached choice, before the timed launches
     ms = []
     for _ in range(args.kernel_reps):
         flush.fill_(1)
@@ -649,7 +650,7 @@ def run_kernel(args):
     nbytes = P.nnz * (4 + s_val * pr.n_pairs) + 8 * (pr.N * pr.M + 1) + 2 * 2 * s_val * pr.dim * B
     print(json.dumps({"kernel": args.kernel, "n_rhs": B, "ms": ms, "ms_mean": float(np.mean(ms[1:] or ms)),
                       "bytes": nbytes, "GB_per_s": nbytes / (float(np.mean(ms[1:] or ms)) * 1e-3) / 1e9,
-                      "flops": 4.0 * pr.n_pairs * P.nnz * B, "shape": pr.wpcd_tune_spmm(P, B, fp32=fp32)}))
+                      "flops": 4.0 * pr.n_pairs * P.nnz * B, "shape": shape}))
     return 0
 
 
