@@ -144,8 +144,8 @@ def fill_flops_per_node(n_ch: int, n_pairs: int) -> int:
 # of the kernel as it stands (profiles/ names the capture); None where no
 # capture of the current kernel exists
 NCU_TRAFFIC = {
-    "fill_kernel<FP64,3>": 435.0e6,
-    "spmm_tile_kernel<FP32>": 331.4e6,
+    "fill_kernel<FP64,3>": 438.8e6,
+    "spmm_tile_kernel<FP32>": 335.5e6,
     "tc_gemm_kernel<TF32x3> (Vt, G1)": 328.9e6,
     "tc_gemm_kernel<TF32x3> (O)": 331.6e6,
     "spmm_df_kernel": 759.3e6,
