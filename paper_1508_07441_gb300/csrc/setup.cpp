@@ -120,49 +120,78 @@ void bessel_i_scaled_all(int lmax, double z, double *out) {
 // implicit symmetric QR steps with Wilkinson shifts on the tridiagonal,
 // accumulating the orthogonal transformations.
 bool sym_eig(int n, std::vector<double> A, std::vector<double> &evals, std::vector<double> &rows) {
-  std::vector<double> Q((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
   auto a = [&](int i, int j) -> double & { return A[(size_t)i * n + j]; };
-  auto q = [&](int i, int j) -> double & { return Q[(size_t)i * n + j]; };
-  std::vector<double> u(n), pvec(n), kvec(n);
-  // Householder: zero column k below the subdiagonal, A <- H A H, Q <- Q H
+  // Householder: zero column k below the subdiagonal, A <- H_k A H_k with
+  // H_k = 1 - beta_k u_k u_k^T; the u_k are kept for Q = H_0 H_1 .. H_{n-3}
+  std::vector<double> Us((size_t)n * n, 0.0), betas(n, 0.0), pvec(n), kvec(n);
   for (int k = 0; k + 2 < n; ++k) {
+    double *u = &Us[(size_t)k * n];
     double alpha = 0.0;
     for (int i = k + 1; i < n; ++i) alpha += a(i, k) * a(i, k);
     alpha = std::sqrt(alpha);
     if (alpha == 0.0) continue;
     if (a(k + 1, k) > 0) alpha = -alpha;
-    std::fill(u.begin(), u.end(), 0.0);
     u[k + 1] = a(k + 1, k) - alpha;
     for (int i = k + 2; i < n; ++i) u[i] = a(i, k);
     double unorm2 = 0.0;
     for (int i = k + 1; i < n; ++i) unorm2 += u[i] * u[i];
     if (unorm2 == 0.0) continue;
-    double beta = 2.0 / unorm2;
-    // p = beta A u ; K = p - (beta/2)(u.p) u ; A <- A - u K^T - K u^T
-    double up = 0.0;
-    for (int i = k; i < n; ++i) {
-      double s = 0.0;
-      for (int j = k + 1; j < n; ++j) s += a(i, j) * u[j];
-      pvec[i] = beta * s;
+    const double beta = 2.0 / unorm2;
+    betas[k] = beta;
+    // p = beta A u ; K = p - (beta/2)(u.p) u ; A <- A - u K^T - K u^T.
+    // A is symmetric, so A u is a sum of the rows a(j, .) weighted by u[j],
+    // four rows per pass: independent lanes over i, a quarter of the stores
+    std::fill(pvec.begin() + k, pvec.end(), 0.0);
+    int j = k + 1;
+    for (; j + 3 < n; j += 4) {
+      const double u0 = u[j], u1 = u[j + 1], u2 = u[j + 2], u3 = u[j + 3];
+      const double *a0 = &a(j, 0), *a1 = &a(j + 1, 0), *a2 = &a(j + 2, 0), *a3 = &a(j + 3, 0);
+      for (int i = k; i < n; ++i) pvec[i] += (a0[i] * u0 + a1[i] * u1) + (a2[i] * u2 + a3[i] * u3);
     }
-    for (int i = 0; i < k; ++i) pvec[i] = 0.0;
+    for (; j < n; ++j) {
+      const double uj = u[j], *aj = &a(j, 0);
+      for (int i = k; i < n; ++i) pvec[i] += aj[i] * uj;
+    }
+    for (int i = k; i < n; ++i) pvec[i] *= beta;
+    double up = 0.0;
     for (int i = k + 1; i < n; ++i) up += u[i] * pvec[i];
     for (int i = k; i < n; ++i) kvec[i] = pvec[i] - 0.5 * beta * up * u[i];
+    // the rank-2 update on the upper triangle, mirrored: A stays exactly
+    // symmetric
+    for (int i = k; i < n; ++i) {
+      const double ui = u[i], ki = kvec[i];
+      for (int c = i; c < n; ++c) a(i, c) -= ui * kvec[c] + ki * u[c];
+    }
     for (int i = k; i < n; ++i)
-      for (int j = k; j < n; ++j) a(i, j) -= u[i] * kvec[j] + kvec[i] * u[j];
-    for (int i = 0; i < n; ++i) {
-      double s = 0.0;
-      for (int j = k + 1; j < n; ++j) s += q(i, j) * u[j];
-      s *= beta;
-      for (int j = k + 1; j < n; ++j) q(i, j) -= s * u[j];
+      for (int c = i + 1; c < n; ++c) a(c, i) = a(i, c);
+  }
+  // Q by backward accumulation: Q <- H_k Q for k = n-3 .. 0, starting from
+  // the identity.  H_{k+1} .. H_{n-3} touch only indices above k + 1, so
+  // each step works on the trailing block of rows and columns k + 1 .. n-1:
+  // t = u_k^T Q (a sum of rows of Q), then Q <- Q - beta_k u_k t
+  std::vector<double> Q((size_t)n * n, 0.0), t(n);
+  for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
+  for (int k = n - 3; k >= 0; --k) {
+    const double beta = betas[k];
+    if (beta == 0.0) continue;
+    const double *u = &Us[(size_t)k * n];
+    std::fill(t.begin() + k + 1, t.end(), 0.0);
+    for (int i = k + 1; i < n; ++i) {
+      const double ui = u[i], *qi = &Q[(size_t)i * n];
+      for (int c = k + 1; c < n; ++c) t[c] += ui * qi[c];
+    }
+    for (int c = k + 1; c < n; ++c) t[c] *= beta;
+    for (int i = k + 1; i < n; ++i) {
+      const double ui = u[i];
+      double *qi = &Q[(size_t)i * n];
+      for (int c = k + 1; c < n; ++c) qi[c] -= ui * t[c];
     }
   }
   // the QR steps rotate pairs of columns of Q: keep Q transposed so that
   // each rotation runs over two contiguous rows
   std::vector<double> QT((size_t)n * n);
   for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) QT[(size_t)j * n + i] = q(i, j);
+    for (int c = 0; c < n; ++c) QT[(size_t)c * n + i] = Q[(size_t)i * n + c];
   auto qt = [&](int k, int i) -> double & { return QT[(size_t)k * n + i]; };
   std::vector<double> d(n), e(n, 0.0);
   for (int i = 0; i < n; ++i) d[i] = a(i, i);
