@@ -18,7 +18,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwpcd.so")
 SOURCES = ["capi.cpp", "setup.cpp", "assemble.cu", "solve.cu", "group.cu", "tc_gemm.cu", "df.cu", "mlp.cu",
            "kapply_noalloc.cu", "spmm_tile.cu", "oz_gemm.cu", "spmv.cu",
-           "assemble_vl.cu"]
+           "assemble_vl.cu", "pair.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -39,7 +39,7 @@ def _stale(obj: str, src: str) -> bool:
         return True
     t = os.path.getmtime(obj)
     deps = [src, os.path.join(CSRC, "wpcd_internal.h"), os.path.join(CSRC, "common.cuh"),
-            os.path.join(CSRC, "df_common.cuh"), os.path.join(CSRC, "tc_ptx.cuh"),
+            os.path.join(CSRC, "df_common.cuh"), os.path.join(CSRC, "tc_ptx.cuh"), os.path.join(CSRC, "bessel.h"),
             os.path.join(ROOT, "include", "wpcd.h"), os.path.abspath(__file__)]  # flags live here
     return any(os.path.getmtime(d) > t for d in deps)
 

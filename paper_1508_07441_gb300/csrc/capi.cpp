@@ -336,10 +336,15 @@ static wpcd_status pair_create(wpcd_grid *g, const wpcd_pair_desc *d, wpcd_probl
   pr->O.assign((size_t)d->n_ch * N * N, 0.0);
   pr->v.assign((size_t)d->n_ch * N * N, 0.0);
   pr->Vt.assign((size_t)d->n_ch * N * N, 0.0);
-  // the potential matrices of every channel (rows in parallel inside), then
-  // the channels' eigenproblems side by side on the host cores
+  // the potential matrices of every channel on the device, then the
+  // channels' eigenproblems side by side on the host cores
   std::vector<std::vector<double>> vs(d->n_ch), hs(d->n_ch), epss(d->n_ch), Os(d->n_ch);
-  pair_matrices_all(N, g->pe.data(), d->n_pair_nodes, d->n_ch, d->n_terms, d->V, d->a, vs, hs);
+  wpcd_status pst = pair_matrices_gpu(g->device, N, g->pe.data(), d->n_pair_nodes, d->n_ch, d->n_terms, d->V, d->a, vs);
+  if (pst != WPCD_OK) {
+    delete pr;
+    return pst;
+  }
+  pair_h(N, g->pe.data(), d->n_ch, vs, hs);
 #pragma omp parallel for schedule(dynamic, 1)
   for (int l = 0; l < d->n_ch; ++l) pair_eig(N, hs[l], epss[l], Os[l]);
   for (int l = 0; l < d->n_ch; ++l) {

@@ -47,75 +47,6 @@ void gauss_legendre(int n, double *t, double *w) {
   }
 }
 
-// exp(-z) i_l(z) for the modified spherical Bessel function i_l.
-// Small z: leading power-series terms.  Moderate z: Miller's downward
-// recurrence i_{n-1} = i_{n+1} + (2n+1)/z i_n (stable: i_n is the minimal
-// solution) normalised by exp(-z) i_0 = (1 - exp(-2z)) / (2z).  Large z: the
-// terminating expansion of i_l in powers of 1/(2z).
-double bessel_i_scaled(int l, double z) {
-  if (z == 0.0) return l == 0 ? 1.0 : 0.0;
-  if (z < 1e-3) {
-    double df = 1.0;
-    for (int m = 3; m <= 2 * l + 1; m += 2) df *= m;
-    double lead = std::pow(z, l) / df;
-    return lead * (1.0 + z * z / (2.0 * (2 * l + 3))) * std::exp(-z);
-  }
-  if (z > 40.0) {
-    double inv = 1.0 / (2.0 * z), term = 1.0, s_alt = 0.0, s_pos = 0.0;
-    for (int k = 0; k <= l; ++k) {
-      if (k > 0) term *= (double)(l + k) * (l - k + 1) / k * inv;  // (l+k)!/(k!(l-k)!) (2z)^-k
-      s_alt += (k % 2 ? -term : term);
-      s_pos += term;
-    }
-    double tail = ((l + 1) % 2 ? -1.0 : 1.0) * std::exp(-2.0 * z) * s_pos;
-    return (s_alt + tail) / (2.0 * z);
-  }
-  int top = l + 30 + (int)(2.0 * z);
-  double up = 0.0, cur = 1e-300, want = 0.0;
-  for (int n = top; n >= 1; --n) {
-    double down = up + (2.0 * n + 1.0) / z * cur;  // i_{n-1}
-    up = cur;
-    cur = down;
-    if (n - 1 == l) want = cur;
-    if (std::fabs(cur) > 1e250) {  // rescale to stay in range
-      cur *= 1e-250;
-      up *= 1e-250;
-      want *= 1e-250;
-    }
-  }
-  // cur = i_0 (unnormalised)
-  double i0s = -std::expm1(-2.0 * z) / (2.0 * z);
-  return want / cur * i0s;
-}
-
-// exp(-z) i_l(z) for l = 0 .. lmax at once (out[lmax + 1]): the same three
-// regimes as bessel_i_scaled; in the middle one a single downward recurrence
-// (started above lmax) yields every order
-void bessel_i_scaled_all(int lmax, double z, double *out) {
-  if (z == 0.0 || z < 1e-3 || z > 40.0) {
-    for (int l = 0; l <= lmax; ++l) out[l] = bessel_i_scaled(l, z);
-    return;
-  }
-  for (int l = 0; l <= lmax; ++l) out[l] = 0.0;
-  const int top = lmax + 30 + (int)(2.0 * z);
-  const double inv_z = 1.0 / z;
-  double up = 0.0, cur = 1e-300;
-  for (int n = top; n >= 1; --n) {
-    const double down = up + (2.0 * n + 1.0) * inv_z * cur;  // i_{n-1}
-    up = cur;
-    cur = down;
-    if (n - 1 <= lmax) out[n - 1] = cur;
-    if (std::fabs(cur) > 1e250) {  // rescale to stay in range
-      cur *= 1e-250;
-      up *= 1e-250;
-      for (int l = 0; l <= lmax; ++l) out[l] *= 1e-250;
-    }
-  }
-  // cur = i_0 (unnormalised)
-  const double scale = -std::expm1(-2.0 * z) / (2.0 * z) / cur;
-  for (int l = 0; l <= lmax; ++l) out[l] *= scale;
-}
-
 // Symmetric eigenproblem: Householder reduction to tridiagonal form, then
 // implicit symmetric QR steps with Wilkinson shifts on the tridiagonal,
 // accumulating the orthogonal transformations.
@@ -253,69 +184,39 @@ bool sym_eig(int n, std::vector<double> A, std::vector<double> &evals, std::vect
   return true;
 }
 
-// The pair matrices of channels l = 0 .. n_ch - 1: the free-packet potential
-// matrix v (Eq. vpot with unit weight functions in the p^2 dp measure) and
-// h1 = diag(<p^2>) + v, whose eigen-decomposition (Eq. exp_z) is pair_eig's.
-// v_l is averaged over each pair of bins with
-// n_nodes GL nodes per bin, rows in parallel on the host cores (each element
-// computed by one thread, in a fixed order: the result does not depend on the
-// thread count).  One Bessel recurrence per (node, node) pair and Gaussian
-// term serves every l.  For a sum of Gaussians, with partial-wave states
-// normalised to delta(p - p') / p^2,
-//   v_l(p, p') = (2/pi) int r^2 j_l(pr) V(r) j_l(p'r) dr
-//              = sum_k V_k / (2 sqrt(pi) alpha^{3/2}) exp(-(p-p')^2/(4 alpha)) e^{-z} i_l(z),
-// alpha = 1/a_k, z = p p' / (2 alpha).
-void pair_matrices_all(int N, const double *edges, int n_nodes, int n_ch, int n_terms, const double *V,
-                       const double *a, std::vector<std::vector<double>> &v, std::vector<std::vector<double>> &h) {
+// Node tables of the pair matrices (Sec. 2.2 Eq. vpot with unit weight
+// functions in the p^2 dp measure): n_nodes GL nodes per p bin, their
+// weights times p^2, and 1/sqrt(bin volume).  The matrices themselves are
+// formed on the device (pair.cu).
+void pair_nodes(int N, const double *edges, int n_nodes, std::vector<double> &pn, std::vector<double> &pw,
+                std::vector<double> &rsB) {
   std::vector<double> t(n_nodes), w(n_nodes);
   gauss_legendre(n_nodes, t.data(), w.data());
-  std::vector<double> pn((size_t)N * n_nodes), pw((size_t)N * n_nodes), rsB(N);
+  pn.assign((size_t)N * n_nodes, 0.0);
+  pw.assign((size_t)N * n_nodes, 0.0);
+  rsB.assign(N, 0.0);
   for (int i = 0; i < N; ++i) {
-    double lo = edges[i], hi = edges[i + 1];
-    double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
+    const double lo = edges[i], hi = edges[i + 1];
+    const double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
     for (int a_ = 0; a_ < n_nodes; ++a_) {
-      double p = mid + half * t[a_];
+      const double p = mid + half * t[a_];
       pn[(size_t)i * n_nodes + a_] = p;
       pw[(size_t)i * n_nodes + a_] = half * w[a_] * p * p;
     }
     rsB[i] = 1.0 / std::sqrt(shell_volume(lo, hi));
   }
-  v.assign(n_ch, std::vector<double>((size_t)N * N, 0.0));
-  const double two_sqrt_pi = 3.5449077018110320546;
-#pragma omp parallel for schedule(dynamic, 2)
-  for (int i = 0; i < N; ++i) {
-    std::vector<double> bes(n_ch), s(n_ch), row(n_ch);
-    for (int k = i; k < N; ++k) {
-      std::fill(s.begin(), s.end(), 0.0);
-      for (int x = 0; x < n_nodes; ++x) {
-        const double px = pn[(size_t)i * n_nodes + x], wx = pw[(size_t)i * n_nodes + x];
-        std::fill(row.begin(), row.end(), 0.0);
-        for (int y = 0; y < n_nodes; ++y) {
-          const double py = pn[(size_t)k * n_nodes + y], wy = pw[(size_t)k * n_nodes + y];
-          for (int q = 0; q < n_terms; ++q) {
-            const double alpha = 1.0 / a[q];
-            const double z = 0.5 * px * py * a[q];
-            const double c = V[q] / (two_sqrt_pi * alpha * std::sqrt(alpha)) *
-                             std::exp(-0.25 * (px - py) * (px - py) * a[q]);
-            bessel_i_scaled_all(n_ch - 1, z, bes.data());
-            for (int l = 0; l < n_ch; ++l) row[l] += wy * (c * bes[l]);
-          }
-        }
-        for (int l = 0; l < n_ch; ++l) s[l] += wx * row[l];
-      }
-      for (int l = 0; l < n_ch; ++l) {
-        const double e = s[l] * rsB[i] * rsB[k];
-        v[l][(size_t)i * N + k] = e;
-        v[l][(size_t)k * N + i] = e;
-      }
-    }
-  }
+}
+
+// h1 = diag(<p^2>) + v of every channel, <p^2> the bin average of p^2 in the
+// p^2 dp measure
+void pair_h(int N, const double *edges, int n_ch, const std::vector<std::vector<double>> &v,
+            std::vector<std::vector<double>> &h) {
   h = v;
   for (int l = 0; l < n_ch; ++l)
     for (int i = 0; i < N; ++i) {
-      double lo = edges[i], hi = edges[i + 1];
-      double lo2 = lo * lo, hi2 = hi * hi;
-      double p5 = (hi - lo) * (hi2 * hi2 + hi2 * hi * lo + hi2 * lo2 + hi * lo * lo2 + lo2 * lo2) / 5.0;
+      const double lo = edges[i], hi = edges[i + 1];
+      const double lo2 = lo * lo, hi2 = hi * hi;
+      const double p5 = (hi - lo) * (hi2 * hi2 + hi2 * hi * lo + hi2 * lo2 + hi * lo * lo2 + lo2 * lo2) / 5.0;
       h[l][(size_t)i * N + i] += p5 / shell_volume(lo, hi);
     }
 }

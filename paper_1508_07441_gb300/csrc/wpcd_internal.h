@@ -81,13 +81,17 @@ void clear_error();
 
 // ---- host mathematics of step 1 (setup.cpp) -------------------------------
 void gauss_legendre(int n, double *t, double *w);
-double bessel_i_scaled(int l, double z);  // exp(-z) i_l(z)
-void bessel_i_scaled_all(int lmax, double z, double *out);  // l = 0 .. lmax
 // symmetric eigensolver: A (n x n, row-major) -> eigenvalues ascending,
 // vectors as rows with the largest-magnitude component positive.
 bool sym_eig(int n, std::vector<double> A, std::vector<double> &evals, std::vector<double> &rows);
-void pair_matrices_all(int N, const double *edges, int n_nodes, int n_ch, int n_terms, const double *V,
-                       const double *a, std::vector<std::vector<double>> &v, std::vector<std::vector<double>> &h);
+void pair_nodes(int N, const double *edges, int n_nodes, std::vector<double> &pn, std::vector<double> &pw,
+                std::vector<double> &rsB);
+void pair_h(int N, const double *edges, int n_ch, const std::vector<std::vector<double>> &v,
+            std::vector<std::vector<double>> &h);
+// the potential matrices v_l of every channel on the device (pair.cu), read
+// back to the host; synchronous
+wpcd_status pair_matrices_gpu(int device, int N, const double *edges, int n_nodes, int n_ch, int n_terms,
+                              const double *V, const double *a, std::vector<std::vector<double>> &v);
 void pair_eig(int N, const std::vector<double> &h, std::vector<double> &eps, std::vector<double> &O);
 inline double shell_volume(double lo, double hi) {
   // int_lo^hi p^2 dp, written to avoid cancellation for narrow bins
