@@ -145,7 +145,7 @@ def test_spmm_matches_oracle_P0(W, orc, B):
     n_ch = 3
     pr = W.Problem(pe, qe, 4, 4, 16, n_ch, (-6.0,), (1.0,))
     P = pr.wpcd_assemble_P(W.WPCD_FP64)
-    ref_P = orc.P0(pe, qe, 4, 4, 16, n_ch)
+    ref_P = orc.P0(pe, qe, 4, 4, 16, n_ch, with_abs=True)
     n_cells = 26 * 22
     y = inputs.random_complex(n_ch * n_cells * B, 77 + B).reshape(n_ch, n_cells, B)
     ref = np.zeros_like(y)
@@ -153,7 +153,12 @@ def test_spmm_matches_oracle_P0(W, orc, B):
     for m, (l, lp) in enumerate(orc.pair_list(n_ch)):
         A = sp.csr_matrix((ref_P["val"][:, m], ref_P["col"], ref_P["row_ptr"]), shape=(n_cells, n_cells))
         ref[l] += A @ y[lp]
-        mag[l] += abs(A) @ np.abs(y[lp])
+        # the term-magnitude sums of P0's elements: an element that is a
+        # cancelling sum of node terms carries FP64 rounding relative to its
+        # terms (the assembly's bar: 1e-10 |ref| + 1e-13 of that sum), not to
+        # its own small value
+        S = sp.csr_matrix((ref_P["absval"][:, m], ref_P["col"], ref_P["row_ptr"]), shape=(n_cells, n_cells))
+        mag[l] += (abs(A) + S) @ np.abs(y[lp])
     # FP32: plain blocked sums, bounded by n 2^-24 of the magnitude sum with n
     # the terms of the longest row (nonzero cells x channel pairs)
     n_terms = int(np.max(np.diff(ref_P["row_ptr"]))) * len(orc.pair_list(n_ch))
@@ -198,14 +203,19 @@ def test_spmv_one_rhs_every_shape(W, orc, tmp_path, monkeypatch, N, M, rpw, cps)
     pe, qe = inputs.tangent_edges(N, 20.0), inputs.tangent_edges(M, 20.0)
     pr = W.Problem(pe, qe, 4, 4, 16, n_ch, (-6.0,), (1.0,))
     P = pr.wpcd_assemble_P(W.WPCD_FP64)
-    ref_P = orc.P0(pe, qe, 4, 4, 16, n_ch)
+    ref_P = orc.P0(pe, qe, 4, 4, 16, n_ch, with_abs=True)
     n_cells = N * M
     y = inputs.random_complex(n_ch * n_cells, 5 + N).reshape(n_ch, n_cells, 1)
     ref, mag = np.zeros_like(y), np.zeros(y.shape)
     for m, (l, lp) in enumerate(orc.pair_list(n_ch)):
         A = sp.csr_matrix((ref_P["val"][:, m], ref_P["col"], ref_P["row_ptr"]), shape=(n_cells, n_cells))
         ref[l] += A @ y[lp]
-        mag[l] += abs(A) @ np.abs(y[lp])
+        # the term-magnitude sums of P0's elements: an element that is a
+        # cancelling sum of node terms carries FP64 rounding relative to its
+        # terms (the assembly's bar: 1e-10 |ref| + 1e-13 of that sum), not to
+        # its own small value
+        S = sp.csr_matrix((ref_P["absval"][:, m], ref_P["col"], ref_P["row_ptr"]), shape=(n_cells, n_cells))
+        mag[l] += (abs(A) + S) @ np.abs(y[lp])
     n_terms = int(np.max(np.diff(ref_P["row_ptr"]))) * len(orc.pair_list(n_ch))
     for fp32, dt, tol in ((False, np.complex128, 1e-9), (True, np.complex64, max(3e-6, n_terms * 2.0**-24))):
         yd = torch.from_numpy(y.astype(dt).reshape(-1).view(np.float32 if fp32 else np.float64)).cuda()
@@ -238,14 +248,19 @@ def test_spmm_tiled_every_shape(W, orc, tmp_path, monkeypatch, N, M, B, tile, ep
     pe, qe = inputs.tangent_edges(N, 20.0), inputs.tangent_edges(M, 20.0)
     pr = W.Problem(pe, qe, 4, 4, 16, n_ch, (-6.0,), (1.0,))
     P = pr.wpcd_assemble_P(W.WPCD_FP64)
-    ref_P = orc.P0(pe, qe, 4, 4, 16, n_ch)
+    ref_P = orc.P0(pe, qe, 4, 4, 16, n_ch, with_abs=True)
     n_cells = N * M
     y = inputs.random_complex(n_ch * n_cells * B, 900 + B).reshape(n_ch, n_cells, B)
     ref, mag = np.zeros_like(y), np.zeros(y.shape)
     for m, (l, lp) in enumerate(orc.pair_list(n_ch)):
         A = sp.csr_matrix((ref_P["val"][:, m], ref_P["col"], ref_P["row_ptr"]), shape=(n_cells, n_cells))
         ref[l] += A @ y[lp]
-        mag[l] += abs(A) @ np.abs(y[lp])
+        # the term-magnitude sums of P0's elements: an element that is a
+        # cancelling sum of node terms carries FP64 rounding relative to its
+        # terms (the assembly's bar: 1e-10 |ref| + 1e-13 of that sum), not to
+        # its own small value
+        S = sp.csr_matrix((ref_P["absval"][:, m], ref_P["col"], ref_P["row_ptr"]), shape=(n_cells, n_cells))
+        mag[l] += (abs(A) + S) @ np.abs(y[lp])
     n_terms = int(np.max(np.diff(ref_P["row_ptr"]))) * len(orc.pair_list(n_ch))
     yd = torch.from_numpy(y.astype(np.complex64).reshape(-1).view(np.float32)).cuda()
     zd = torch.full_like(yd, float("nan"))
