@@ -377,44 +377,59 @@ __global__ void __launch_bounds__(V_THREADS) bdot_kernel(int rows, int B, int nv
 // The FP32 dots with B even: as bdot_kernel, two adjacent energies per
 // thread in 16-byte loads (a warp reads 512 contiguous bytes of each
 // vector per row); the block sums in FP32, the cross-block sums (breduce)
-// in FP64
+// in FP64.  JCT basis vectors per pass over w and U rows per thread per
+// iteration, their loads issued together: few vectors leave few loads in
+// flight per row, so those launches take more rows at once (the dispatch
+// picks U from nv; 1 vector at U = 1 ran at a third of HBM bandwidth, at
+// U = 8 at 6.4 TB/s).
+template <int JCT, int U>
 __global__ void __launch_bounds__(V_THREADS) bdot2_kernel(int rows, int B, int nv, const float4 *__restrict__ V,
                                                           size_t ld2, const float4 *__restrict__ w,
                                                           double2 *__restrict__ partial) {
-  __shared__ float4 red[JC][V_THREADS];
+  __shared__ float4 red[JCT][V_THREADS];
   const int EL = blockDim.x;  // energy-pair lanes (<= 32)
   const int RB = blockDim.y;  // row lanes
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * EL + tx;
   const int B2 = B / 2;
   const int e2 = blockIdx.y * EL + tx;
   const int nblk = gridDim.x;
-  for (int j0 = 0; j0 < nv; j0 += JC) {
-    float4 acc[JC];
+  const int rstep = nblk * RB;
+  for (int j0 = 0; j0 < nv; j0 += JCT) {
+    float4 acc[JCT];
 #pragma unroll
-    for (int c = 0; c < JC; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int c = 0; c < JCT; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (e2 < B2) {
-      for (int r = blockIdx.x * RB + ty; r < rows; r += nblk * RB) {
-        const size_t f = (size_t)r * B2 + e2;
-        const float4 b = w[f];
+      for (int r = blockIdx.x * RB + ty; r < rows; r += U * rstep) {
+        float4 b[U], a[U][JCT];
 #pragma unroll
-        for (int c = 0; c < JC; ++c) {
-          if (j0 + c < nv) {
-            const float4 a = V[(size_t)(j0 + c) * ld2 + f];
-            acc[c].x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc[c].x));
-            acc[c].y = fmaf(a.x, b.y, fmaf(-a.y, b.x, acc[c].y));
-            acc[c].z = fmaf(a.z, b.z, fmaf(a.w, b.w, acc[c].z));
-            acc[c].w = fmaf(a.z, b.w, fmaf(-a.w, b.z, acc[c].w));
-          }
+        for (int u = 0; u < U; ++u) {
+          const int rr = r + u * rstep;
+          const bool ok = rr < rows;
+          const size_t f = (size_t)rr * B2 + e2;
+          b[u] = ok ? w[f] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int c = 0; c < JCT; ++c)
+            a[u][c] = ok && j0 + c < nv ? V[(size_t)(j0 + c) * ld2 + f] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int c = 0; c < JCT; ++c) {
+            const float4 av = a[u][c], bv = b[u];
+            acc[c].x = fmaf(av.x, bv.x, fmaf(av.y, bv.y, acc[c].x));
+            acc[c].y = fmaf(av.x, bv.y, fmaf(-av.y, bv.x, acc[c].y));
+            acc[c].z = fmaf(av.z, bv.z, fmaf(av.w, bv.w, acc[c].z));
+            acc[c].w = fmaf(av.z, bv.w, fmaf(-av.w, bv.z, acc[c].w));
+          }
       }
     }
 #pragma unroll
-    for (int c = 0; c < JC; ++c) red[c][tid] = acc[c];
+    for (int c = 0; c < JCT; ++c) red[c][tid] = acc[c];
     __syncthreads();
     for (int h = RB / 2; h > 0; h >>= 1) {
       if (ty < h)
 #pragma unroll
-        for (int c = 0; c < JC; ++c) {
+        for (int c = 0; c < JCT; ++c) {
           const float4 o = red[c][(ty + h) * EL + tx];
           red[c][tid].x += o.x;
           red[c][tid].y += o.y;
@@ -425,7 +440,7 @@ __global__ void __launch_bounds__(V_THREADS) bdot2_kernel(int rows, int B, int n
     }
     if (ty == 0 && e2 < B2)
 #pragma unroll
-      for (int c = 0; c < JC; ++c)
+      for (int c = 0; c < JCT; ++c)
         if (j0 + c < nv) {
           const float4 v = red[c][tx];
           double2 *o = partial + ((size_t)(j0 + c) * nblk + blockIdx.x) * B + 2 * e2;
@@ -549,6 +564,17 @@ __global__ void baxpy2_kernel(int64_t n2, int B2, int nv, const float4 *__restri
       a.w = fmaf(cj.z, v.w, fmaf(cj.w, v.z, a.w));
     }
     w[f] = a;
+  }
+}
+
+// the FP32 scaling with B even: two adjacent energies per thread in 16-byte
+// loads, 32-bit index arithmetic (n2 = n / 2 < 2^31)
+__global__ void bscale2_kernel(int n2, int B2, const float4 *__restrict__ src, const float2 *__restrict__ inv,
+                               float4 *__restrict__ dst) {
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < n2; f += gridDim.x * blockDim.x) {
+    const float2 sc = inv[f % B2];
+    const float4 a = src[f];
+    dst[f] = make_float4(a.x * sc.x, a.y * sc.x, a.z * sc.y, a.w * sc.y);
   }
 }
 
@@ -1227,8 +1253,24 @@ struct Krylov {
       int el = 1;
       while (el < B / 2 && el < 32) el *= 2;
       const dim3 blk(el, V_THREADS / el), grd(nblk, (B / 2 + el - 1) / el);
-      bdot2_kernel<<<grd, blk, 0, s>>>((int)dim, B, nv, reinterpret_cast<const float4 *>(base), ld / 2,
-                                       reinterpret_cast<const float4 *>(x), partial);
+      const float4 *Vb = reinterpret_cast<const float4 *>(base), *xb = reinterpret_cast<const float4 *>(x);
+      if (nv == 1)
+        bdot2_kernel<1, 8><<<grd, blk, 0, s>>>((int)dim, B, nv, Vb, ld / 2, xb, partial);
+      else if (nv == 2)
+        bdot2_kernel<2, 4><<<grd, blk, 0, s>>>((int)dim, B, nv, Vb, ld / 2, xb, partial);
+      else if (nv <= 4)
+        bdot2_kernel<4, 2><<<grd, blk, 0, s>>>((int)dim, B, nv, Vb, ld / 2, xb, partial);
+      else if (nv <= 6)
+        bdot2_kernel<6, 2><<<grd, blk, 0, s>>>((int)dim, B, nv, Vb, ld / 2, xb, partial);
+      // more vectors: passes of at most six, w re-read per pass (one pass over
+      // eleven or eight vectors, 12 or 9 streams per thread, ran at 3.5-4.2
+      // TB/s against 6.5 for six); 7-8 vectors as two passes of four (185,
+      // 200 us against 213, 219 as six + rest), 9-10 as six + rest (226, 235
+      // us against 240, 251 as two passes of five)
+      else if (nv <= 8)
+        bdot2_kernel<4, 2><<<grd, blk, 0, s>>>((int)dim, B, nv, Vb, ld / 2, xb, partial);
+      else
+        bdot2_kernel<6, 2><<<grd, blk, 0, s>>>((int)dim, B, nv, Vb, ld / 2, xb, partial);
     } else {
       bdot_kernel<U><<<dot_grid(), dot_block(), 0, s>>>((int)dim, B, nv, base, ld, x, partial);
     }
@@ -1271,7 +1313,12 @@ struct Krylov {
       count_launches(2);
     }
     norms<T>(wv(), s, true);
-    bscale_kernel<T><<<vg, 256, 0, s>>>(n, B, wv(), inv, vec(k + 1));
+    if (sizeof(T) == 4 && B % 2 == 0 && n / 2 < INT32_MAX)
+      bscale2_kernel<<<grid_for(n / 2, 256), 256, 0, s>>>((int)(n / 2), B / 2, reinterpret_cast<const float4 *>(wv()),
+                                                         reinterpret_cast<const float2 *>(inv),
+                                                         reinterpret_cast<float4 *>(vec(k + 1)));
+    else
+      bscale_kernel<T><<<vg, 256, 0, s>>>(n, B, wv(), inv, vec(k + 1));
     bgivens_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, m, k, h, nrm, H, cs, sn, bet, resid, bnorm);
     count_launches(3);
   }
