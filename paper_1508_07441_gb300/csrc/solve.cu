@@ -546,7 +546,6 @@ __global__ void baxpy_kernel(int64_t n, int B, int nv, const typename Cx<T>::t *
   }
 }
 
-// dst[f] = src[f] * inv[e]
 // the FP32 axpy with B even: two adjacent energies of one row per thread,
 // in 16-byte loads of the vectors and of the coefficients (n2 = n / 2)
 __global__ void baxpy2_kernel(int64_t n2, int B2, int nv, const float4 *__restrict__ V, size_t ld2,
@@ -567,6 +566,34 @@ __global__ void baxpy2_kernel(int64_t n2, int B2, int nv, const float4 *__restri
   }
 }
 
+// the same with the vector count bounded by NVT: every vector's load for the
+// element is issued before the multiply-adds (the runtime loop waits on one
+// load per vector: 4.8-5.0 TB/s at 8-10 vectors), the sums in the same order;
+// 32-bit index arithmetic (n2 < 2^31)
+template <int NVT>
+__global__ void __launch_bounds__(256) baxpy2t_kernel(int n2, int B2, int nv, const float4 *__restrict__ V,
+                                                      size_t ld2, const float4 *__restrict__ c,
+                                                      float4 *__restrict__ w) {
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < n2; f += gridDim.x * blockDim.x) {
+    const int e2 = f % B2;
+    float4 v[NVT];
+#pragma unroll
+    for (int j = 0; j < NVT; ++j) v[j] = j < nv ? V[(size_t)j * ld2 + f] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 a = w[f];
+#pragma unroll
+    for (int j = 0; j < NVT; ++j)
+      if (j < nv) {
+        const float4 cj = c[j * B2 + e2];
+        a.x = fmaf(cj.x, v[j].x, fmaf(-cj.y, v[j].y, a.x));
+        a.y = fmaf(cj.x, v[j].y, fmaf(cj.y, v[j].x, a.y));
+        a.z = fmaf(cj.z, v[j].z, fmaf(-cj.w, v[j].w, a.z));
+        a.w = fmaf(cj.z, v[j].w, fmaf(cj.w, v[j].z, a.w));
+      }
+    w[f] = a;
+  }
+}
+
+// dst[f] = src[f] * inv[e]
 // the FP32 scaling with B even: two adjacent energies per thread in 16-byte
 // loads, 32-bit index arithmetic (n2 = n / 2 < 2^31)
 __global__ void bscale2_kernel(int n2, int B2, const float4 *__restrict__ src, const float2 *__restrict__ inv,
@@ -1289,7 +1316,22 @@ struct Krylov {
   // w += sum_{j < nv} hc_j V_j (FP32 with B even: two energies per thread)
   void axpy(int nv, cudaStream_t s) {
     const int64_t n = (int64_t)dim * B;
-    if (sizeof(T) == 4 && B % 2 == 0)
+    // the unrolled form except at three vectors (112 against 103 us there;
+    // 47-256 against 58-292 us elsewhere up to ten)
+    if (sizeof(T) == 4 && B % 2 == 0 && nv <= 12 && nv != 3 && n / 2 < INT32_MAX) {
+      const int n2 = (int)(n / 2), g = grid_for(n2, 256);
+      const float4 *Vv = reinterpret_cast<const float4 *>(V), *cc = reinterpret_cast<const float4 *>(hc);
+      float4 *ww = reinterpret_cast<float4 *>(w);
+      const size_t ld2 = dim * B / 2;
+      if (nv <= 2)
+        baxpy2t_kernel<2><<<g, 256, 0, s>>>(n2, B / 2, nv, Vv, ld2, cc, ww);
+      else if (nv <= 4)
+        baxpy2t_kernel<4><<<g, 256, 0, s>>>(n2, B / 2, nv, Vv, ld2, cc, ww);
+      else if (nv <= 8)
+        baxpy2t_kernel<8><<<g, 256, 0, s>>>(n2, B / 2, nv, Vv, ld2, cc, ww);
+      else
+        baxpy2t_kernel<12><<<g, 256, 0, s>>>(n2, B / 2, nv, Vv, ld2, cc, ww);
+    } else if (sizeof(T) == 4 && B % 2 == 0)
       baxpy2_kernel<<<grid_for(n / 2, 256), 256, 0, s>>>(n / 2, B / 2, nv, reinterpret_cast<const float4 *>(V),
                                                          dim * B / 2, reinterpret_cast<const float4 *>(hc),
                                                          reinterpret_cast<float4 *>(w));
