@@ -520,6 +520,9 @@ __global__ void gaxpy_kernel(const GMeta *__restrict__ gm, int64_t len, int nv,
 
 // the FP32 axpy of an even group (every B_g and segment offset even): two
 // adjacent energies of one row per thread in 16-byte loads; len2 = len / 2
+// (NVT > 0: at most NVT vectors, every vector's load for the element issued
+// before the multiply-adds, the sums in the same order)
+template <int NVT>
 __global__ void gaxpy2_kernel(const GMeta *__restrict__ gm, int64_t len2, int nv, const float4 *__restrict__ V,
                               size_t ld2, const float4 *__restrict__ c, float4 *__restrict__ w) {
   __shared__ SegSmem sm;
@@ -529,13 +532,21 @@ __global__ void gaxpy2_kernel(const GMeta *__restrict__ gm, int64_t len2, int nv
        f += (int64_t)gridDim.x * blockDim.x) {
     const int s2 = system_of(sm, n, 2 * f) / 2;  // even system of the pair
     float4 a = w[f];
-    for (int j = 0; j < nv; ++j) {
-      const float4 v = V[(size_t)j * ld2 + f];
-      const float4 cj = c[(size_t)j * S2 + s2];
+    const auto mac = [&](const float4 &v, const float4 &cj) {
       a.x = fmaf(cj.x, v.x, fmaf(-cj.y, v.y, a.x));
       a.y = fmaf(cj.x, v.y, fmaf(cj.y, v.x, a.y));
       a.z = fmaf(cj.z, v.z, fmaf(-cj.w, v.w, a.z));
       a.w = fmaf(cj.z, v.w, fmaf(cj.w, v.z, a.w));
+    };
+    if constexpr (NVT > 0) {
+      float4 v[NVT];
+#pragma unroll
+      for (int j = 0; j < NVT; ++j) v[j] = j < nv ? V[(size_t)j * ld2 + f] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < NVT; ++j)
+        if (j < nv) mac(v[j], c[(size_t)j * S2 + s2]);
+    } else {
+      for (int j = 0; j < nv; ++j) mac(V[(size_t)j * ld2 + f], c[(size_t)j * S2 + s2]);
     }
     w[f] = a;
   }
@@ -952,12 +963,23 @@ struct GKrylov {
   }
   // w += sum_{j < nv} hc_j V_j (FP32 in an even group: two energies per thread)
   void axpy(int nv, cudaStream_t s) {
-    if (sizeof(T) == 4 && gr->even)
-      gaxpy2_kernel<<<grid_for(L / 2, 256), 256, 0, s>>>(gr->d_meta, L / 2, nv, reinterpret_cast<const float4 *>(V),
-                                                         (size_t)L / 2, reinterpret_cast<const float4 *>(hc),
-                                                         reinterpret_cast<float4 *>(w));
-    else
+    if (sizeof(T) == 4 && gr->even) {
+      const float4 *Vv = reinterpret_cast<const float4 *>(V), *cc = reinterpret_cast<const float4 *>(hc);
+      float4 *ww = reinterpret_cast<float4 *>(w);
+      const int g = grid_for(L / 2, 256);
+      if (nv <= 2)
+        gaxpy2_kernel<2><<<g, 256, 0, s>>>(gr->d_meta, L / 2, nv, Vv, (size_t)L / 2, cc, ww);
+      else if (nv <= 4)
+        gaxpy2_kernel<4><<<g, 256, 0, s>>>(gr->d_meta, L / 2, nv, Vv, (size_t)L / 2, cc, ww);
+      else if (nv <= 8)
+        gaxpy2_kernel<8><<<g, 256, 0, s>>>(gr->d_meta, L / 2, nv, Vv, (size_t)L / 2, cc, ww);
+      else if (nv <= 12)
+        gaxpy2_kernel<12><<<g, 256, 0, s>>>(gr->d_meta, L / 2, nv, Vv, (size_t)L / 2, cc, ww);
+      else
+        gaxpy2_kernel<0><<<g, 256, 0, s>>>(gr->d_meta, L / 2, nv, Vv, (size_t)L / 2, cc, ww);
+    } else {
       gaxpy_kernel<T><<<grid_for(L, 256), 256, 0, s>>>(gr->d_meta, L, nv, vec(0), (size_t)L, hc, wv());
+    }
   }
   // one Arnoldi step from column k (w = (I - K) v_k on entry); classical
   // Gram-Schmidt with a second pass (reorth) or a single pass

@@ -143,12 +143,17 @@ def test_assemble_full_size_3_channels(W, orc):
         assert st["n_abs_only"] <= (0.002 if name == "fp32c" else 0.0005) * st["n"], st
 
 
-def test_pair_setup_matches_oracle(W, orc):
-    pe, qe = _inputs(60, 40)
-    pr = W.Problem(pe, qe, 4, 4, 16, 3, (-3.0,), (1.0,), n_pair_nodes=8)
-    for l in range(3):
+# the potential matrices are formed on the device (a thread per bin pair,
+# the Bessel recurrence per node pair serving every l), the eigenproblems on
+# the host: one Gaussian and three channels, and the short-range repulsive
+# sum of two Gaussians with five channels (l up to 4, large z = p p' a / 2)
+@pytest.mark.parametrize("N,n_ch,V,a", [(60, 3, (-3.0,), (1.0,)), (50, 5, (-6.0, 2.0), (0.5, 0.1))])
+def test_pair_setup_matches_oracle(W, orc, N, n_ch, V, a):
+    pe, qe = _inputs(N, 40)
+    pr = W.Problem(pe, qe, 4, 4, 16, n_ch, V, a, n_pair_nodes=8)
+    for l in range(n_ch):
         eps, O, v = pr.wpcd_problem_pair(l)
-        v2, _, eps2, O2 = orc.pair(pe, 8, l, [-3.0], [1.0])
+        v2, _, eps2, O2 = orc.pair(pe, 8, l, list(V), list(a))
         assert np.max(np.abs(eps - eps2)) < 1e-12 * np.abs(eps2).max()
         assert np.max(np.abs(v - v2)) < 1e-12 * np.abs(v2).max()
         assert np.max(np.abs(O - O2)) < 1e-8
