@@ -643,7 +643,6 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
             if (SCALE_G) gv[it][qq] = in ? rg[kl * (WS_BN / 2) + (nn >> 1)] : make_float2(0.f, 0.f);
           }
         }
-        mbar_arrive(&bars.r_empty[sr]);
         if (q >= p.nsb && !(ok = ws_wait(&bars.b_empty[sb], (uint32_t)(q / p.nsb - 1) & 1, &abort_flag, p.err, lim.next())))
           break;
         unsigned char *bhi = b_ring + (size_t)sb * WS_B_STAGE, *blo = bhi + WS_B_HALF;
@@ -679,6 +678,12 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
         // generic-proxy stores -> visible to the tensor core (async proxy)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&bars.b_full[sb]);
+        // the raw slot is released only now that the values read from it
+        // have been stored: released right after the reads, it was refilled
+        // under them whenever the producer ran ahead on raw slots (one raw
+        // slot, or more A stages than raw slots), and products differed from
+        // run to run
+        mbar_arrive(&bars.r_empty[sr]);
       }
     }
   } else {
