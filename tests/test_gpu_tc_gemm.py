@@ -49,6 +49,56 @@ def _reference(A, x, g, N, M, B):
 # (40, 160, 64) gives 480 column tiles, so each persistent CTA takes three or
 # four tiles and the stage rings and accumulator buffers wrap; (450, 40, 8)
 # has four row tiles (one accumulator buffer)
+# the persistent kernel's rings hand every panel chunk from the TMA producer
+# to the converters and every operand stage to the MMA thread; a slot released
+# too early shows as products that differ from call to call.  Repeated calls
+# must agree bit for bit: 200 rows (three A stages, four raw chunks) and 450
+# rows (two A stages, two raw chunks with G1, one accumulator buffer), each
+# over enough column tiles that every ring wraps many times
+@pytest.mark.parametrize("N,M,B", [(200, 40, 64), (450, 40, 16)])
+@pytest.mark.parametrize("which", [0, 1])
+def test_tensor_core_gemm_bit_identical_across_calls(W, N, M, B, which):
+    import torch
+
+    pr = _problem(W, N, M)
+    n = pr.n_ch * N * M * B
+    gen = torch.Generator().manual_seed(N + which)
+    x = torch.randn(2 * n, generator=gen, dtype=torch.float32).cuda()
+    g = torch.randn(2 * n, generator=gen, dtype=torch.float32).cuda() if which == 0 else None
+    outs = []
+    for _ in range(4):
+        y = torch.full((2 * n,), float("nan"), dtype=torch.float32, device="cuda")
+        pr.wpcd_channel_gemm(which, W.WPCD_GEMM_TF32X3, g, x, y, B)
+        outs.append(y)
+    assert torch.isfinite(outs[0]).all()
+    for y in outs[1:]:
+        assert torch.equal(y, outs[0])
+    pr.close()
+
+
+# the same for the digit-plane product (bf16 planes on the tensor cores, FP64
+# in and out; A digits by bulk copy ahead of the MMAs)
+@pytest.mark.parametrize("which", [0, 1])
+def test_digit_plane_gemm_bit_identical_across_calls(W, which):
+    import torch
+
+    N, M, B = 200, 40, 16
+    pr = _problem(W, N, M)
+    n = pr.n_ch * N * M * B
+    gen = torch.Generator().manual_seed(7 + which)
+    x = torch.randn(2 * n, generator=gen, dtype=torch.float64).cuda()
+    g = torch.randn(2 * n, generator=gen, dtype=torch.float64).cuda() if which == 0 else None
+    outs = []
+    for _ in range(4):
+        y = torch.full((2 * n,), float("nan"), dtype=torch.float64, device="cuda")
+        pr.wpcd_channel_gemm(which, W.WPCD_GEMM_DIGITS, g, x, y, B)
+        outs.append(y)
+    assert torch.isfinite(outs[0]).all()
+    for y in outs[1:]:
+        assert torch.equal(y, outs[0])
+    pr.close()
+
+
 @pytest.mark.parametrize("N,M,B", [(30, 28, 3), (130, 20, 5), (200, 16, 8), (300, 12, 2), (40, 15, 3),
                                    (40, 160, 64), (450, 40, 8)])
 @pytest.mark.parametrize("which", [0, 1])
