@@ -109,6 +109,86 @@ __global__ void __launch_bounds__(TL_THREADS) tile_merge_kernel(int N, int M, in
   }
 }
 
+// the same merge for 2-cell tiles, a warp per tile: the merged position of
+// a column of one row is its index there plus the number of the other row's
+// columns below it (a binary search) less the number of shared columns
+// before it (a warp prefix count); shared columns are written from the first
+// row.  The result is the thread-per-tile kernel's, element for element.
+__device__ __forceinline__ int t2_lower_bound(const int32_t *__restrict__ a, int n, int x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(a + mid) < x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(TL_THREADS) tile2_merge_warp_kernel(int N, int M, int npair,
+                                                                     const int64_t *__restrict__ row_ptr,
+                                                                     const int32_t *__restrict__ col,
+                                                                     const float *__restrict__ val, int64_t nnz,
+                                                                     int64_t *__restrict__ cnt_or_ptr,
+                                                                     int32_t *__restrict__ ucol,
+                                                                     float *__restrict__ tval) {
+  const int n_tiles = tile_count<2>(N, M);
+  const int vs = tile_vs(2, npair);
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < n_tiles; t += (gridDim.x * blockDim.x) >> 5) {
+    int r[2];
+    tile_rows<2>(t, N, M, r);
+    const int64_t a0 = row_ptr[r[0]], na = row_ptr[r[0] + 1] - a0;
+    const int64_t b0 = r[1] >= 0 ? row_ptr[r[1]] : 0, nb = r[1] >= 0 ? row_ptr[r[1] + 1] - b0 : 0;
+    const int32_t *A = col + a0, *Bc = col + b0;
+    const int64_t u0 = FILL ? cnt_or_ptr[t] : 0;
+    // the first row's columns (and the shared ones)
+    int common = 0;
+    for (int i0 = 0; i0 < na; i0 += 32) {
+      const int i = i0 + lane;
+      const bool in = i < na;
+      const int x = in ? __ldg(A + i) : 0;
+      const int lb = in ? t2_lower_bound(Bc, (int)nb, x) : 0;
+      const bool shared_col = in && lb < nb && __ldg(Bc + lb) == x;
+      const unsigned m = __ballot_sync(0xffffffffu, shared_col);
+      if (FILL && in) {
+        const int64_t u = u0 + i + lb - (common + __popc(m & below));
+        ucol[u] = x;
+        float *v = tval + u * vs;
+        for (int q = 0; q < npair; ++q) {
+          v[q * 2] = val[(size_t)q * nnz + a0 + i];
+          v[q * 2 + 1] = shared_col ? val[(size_t)q * nnz + b0 + lb] : 0.f;
+        }
+        for (int q = 2 * npair; q < vs; ++q) v[q] = 0.f;
+      }
+      common += __popc(m);
+    }
+    // the second row's columns that the first row lacks
+    int common_b = 0;
+    for (int j0 = 0; j0 < nb; j0 += 32) {
+      const int j = j0 + lane;
+      const bool in = j < nb;
+      const int x = in ? __ldg(Bc + j) : 0;
+      const int lb = in ? t2_lower_bound(A, (int)na, x) : 0;
+      const bool shared_col = in && lb < na && __ldg(A + lb) == x;
+      const unsigned m = __ballot_sync(0xffffffffu, shared_col);
+      if (FILL && in && !shared_col) {
+        const int64_t u = u0 + j + lb - (common_b + __popc(m & below));
+        ucol[u] = x;
+        float *v = tval + u * vs;
+        for (int q = 0; q < npair; ++q) {
+          v[q * 2] = 0.f;
+          v[q * 2 + 1] = val[(size_t)q * nnz + b0 + j];
+        }
+        for (int q = 2 * npair; q < vs; ++q) v[q] = 0.f;
+      }
+      common_b += __popc(m);
+    }
+    if (!FILL && lane == 0) cnt_or_ptr[t] = na + nb - common;
+  }
+}
+
 struct TileParams {
   int n_cells, n_tiles, N, M, B;
   const int64_t *tptr;
@@ -243,8 +323,14 @@ wpcd_status tile_prepare_r(const wpcd_problem *pr, wpcd_P *P, const float *v32, 
   int64_t *ptr = nullptr;
   WPCD_CUDA_TRY(dev_malloc(&ptr, sizeof(int64_t) * (n_tiles + 1)));
   const int grid = grid_for(n_tiles, TL_THREADS);
-  tile_merge_kernel<R, false><<<grid, TL_THREADS, 0, s>>>(N, M, npair, P->row_ptr, P->col, v32, P->nnz, ptr,
-                                                           nullptr, nullptr);
+  // 2-cell tiles: a warp per tile (640 K threads at 200 x 200, against 20 K)
+  const int wgrid = grid_for((int64_t)n_tiles * 32, TL_THREADS, 152 * 16);
+  if constexpr (R == 2)
+    tile2_merge_warp_kernel<false><<<wgrid, TL_THREADS, 0, s>>>(N, M, npair, P->row_ptr, P->col, v32, P->nnz, ptr,
+                                                                 nullptr, nullptr);
+  else
+    tile_merge_kernel<R, false><<<grid, TL_THREADS, 0, s>>>(N, M, npair, P->row_ptr, P->col, v32, P->nnz, ptr,
+                                                             nullptr, nullptr);
   count_launches(1);
   // exclusive prefix sum of the tile sizes on the host (once per matrix)
   std::vector<int64_t> h(n_tiles + 1, 0);
@@ -262,8 +348,12 @@ wpcd_status tile_prepare_r(const wpcd_problem *pr, wpcd_P *P, const float *v32, 
   if (e == cudaSuccess) e = dev_malloc(&ucol, sizeof(int32_t) * std::max<int64_t>(total, 1));
   if (e == cudaSuccess) e = dev_malloc(&tval, sizeof(float) * tile_vs(R, npair) * std::max<int64_t>(total, 1));
   if (e == cudaSuccess) {
-    tile_merge_kernel<R, true><<<grid, TL_THREADS, 0, s>>>(N, M, npair, P->row_ptr, P->col, v32, P->nnz, ptr, ucol,
-                                                            tval);
+    if constexpr (R == 2)
+      tile2_merge_warp_kernel<true><<<wgrid, TL_THREADS, 0, s>>>(N, M, npair, P->row_ptr, P->col, v32, P->nnz, ptr,
+                                                                  ucol, tval);
+    else
+      tile_merge_kernel<R, true><<<grid, TL_THREADS, 0, s>>>(N, M, npair, P->row_ptr, P->col, v32, P->nnz, ptr, ucol,
+                                                              tval);
     count_launches(1);
     e = cudaGetLastError();
   }
