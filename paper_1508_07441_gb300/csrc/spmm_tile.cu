@@ -10,8 +10,8 @@
 // a column once per nonzero; here a warp takes a tile of R cells and gathers
 // the y row of each column of the tile once, into registers, and applies it
 // to all R rows.  The tile structure is built once per matrix on the device
-// (tile_merge_kernel counting, a host prefix sum, tile_merge_kernel
-// filling): for tile t the
+// (a counting pass, a host prefix sum, a filling pass: tile2_merge_warp_kernel
+// for 2-cell tiles, tile_merge_kernel for 4-cell ones): for tile t the
 // merged, ascending column list of its rows, and per column an R-row block
 // of values for every (l, l') pair, zero where a row lacks the column.
 //
