@@ -538,6 +538,13 @@ wpcd_status wpcd_warm_features(const wpcd_problem *pr, const double *E, int n, d
 wpcd_status wpcd_vec_axpy(double alpha, const double *x, double *y, int64_t n, void *stream);
 /* dst [2n] FP32 (re, im) pairs from src [n] complex FP64 (device). */
 wpcd_status wpcd_complex_to_f32(const double *src, int64_t n, float *dst, void *stream);
+/* The float-float split of the mixed solve's FP64-class residual (Sec. 4.1
+ * precision): for n FP64 values x (device), hi = x rounded to the nearest
+ * float (ties to even) and lo = (x - hi) rounded likewise, so hi + lo carries
+ * x to about 2^-48; values whose part lies below the float normal range
+ * (2^-126) give zero there instead of a subnormal.  hi, lo device [n] FP32,
+ * caller-owned.  EINVAL for null pointers or n < 0.  Enqueued on stream. */
+wpcd_status wpcd_split_f64(const double *x, int64_t n, float *hi, float *lo, void *stream);
 /* Mixture weights of the warm start: for each of n rows of k logits (FP32,
  * device [n][k]) the softmax w_j = exp(z_j - max z) / sum_i exp(z_i - max z),
  * written as real coefficients C [n][k][2] = (w_j, 0) for wpcd_basis_expand.

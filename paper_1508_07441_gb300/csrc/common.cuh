@@ -20,6 +20,42 @@ namespace {
 
 constexpr double kPi = 3.141592653589793238462643383279502884;
 
+// FP64 <-> FP32 conversions by integer operations.  On GB300 a conversion
+// instruction occupies an FP64-pipe slot like a multiply-add, and the
+// splitting kernels below are bound by that pipe; these take the integer
+// pipe instead.  f64_to_f32_rn rounds to nearest, ties to even (IEEE 754),
+// for results in the float normal range; |v| below 2^-126 gives a signed
+// zero (no float subnormals: those magnitudes are far below every value these
+// kernels handle), beyond the float range an infinity, a NaN stays a NaN.
+__device__ __forceinline__ float f64_to_f32_rn(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7FF);
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  if (e < 897) return __uint_as_float(sign);
+  if (e == 2047) return __uint_as_float(sign | (m ? 0x7FC00000u : 0x7F800000u));
+  if (e > 1150) return __uint_as_float(sign | 0x7F800000u);
+  // the float's exponent and mantissa fields before rounding; the 29 bits
+  // dropped decide the rounding, and a carry out of the mantissa raises the
+  // exponent (to infinity past the largest float)
+  unsigned r = ((unsigned)(e - 896) << 23) | (unsigned)(m >> 29);
+  const unsigned rem = (unsigned)(m & 0x1FFFFFFFull);
+  r += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;
+  return __uint_as_float(sign | r);
+}
+
+// exact widening of a float that f64_to_f32_rn produced (zero or normal;
+// infinities and NaNs keep their class)
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned fe = (u >> 23) & 0xFFu;
+  const unsigned long long man = (unsigned long long)(u & 0x7FFFFFu) << 29;
+  if (fe == 0) return __longlong_as_double((long long)sign);
+  if (fe == 255) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull | man));
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(fe + 896) << 52) | man));
+}
+
 template <typename T>
 struct Cx;
 template <>

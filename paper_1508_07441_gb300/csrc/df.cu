@@ -314,3 +314,20 @@ wpcd_status df_born(const wpcd_problem *pr, const wpcd_P *P, const int *r0, int 
 }
 
 }  // namespace wpcd
+
+using namespace wpcd;
+
+extern "C" {
+
+wpcd_status wpcd_split_f64(const double *x, int64_t n, float *hi, float *lo, void *stream) {
+  clear_error();
+  if (!x || !hi || !lo || n < 0) return set_error(WPCD_EINVAL, "bad split arguments");
+  if (n == 0) return WPCD_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  df_split_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, x, hi, lo);
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? WPCD_OK : cuda_error(e, "split");
+}
+
+}  // extern "C"

@@ -42,9 +42,9 @@ __global__ void df_split_kernel(int64_t n, const double *__restrict__ x, float *
                                 float *__restrict__ lo) {
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n; f += (int64_t)gridDim.x * blockDim.x) {
     const double v = x[f];
-    const float h = (float)v;
+    const float h = f64_to_f32_rn(v);
     hi[f] = h;
-    lo[f] = (float)(v - (double)h);
+    lo[f] = f64_to_f32_rn(v - f32_to_f64(h));
   }
 }
 
@@ -58,9 +58,10 @@ __global__ void df_split_scaled_kernel(int64_t nc, const double2 *__restrict__ x
       const double2 b = g[f];
       v = make_double2(b.x * a.x - b.y * a.y, b.x * a.y + b.y * a.x);
     }
-    const float hr = (float)v.x, hm = (float)v.y;
+    const float hr = f64_to_f32_rn(v.x), hm = f64_to_f32_rn(v.y);
     reinterpret_cast<float2 *>(hi)[f] = make_float2(hr, hm);
-    reinterpret_cast<float2 *>(lo)[f] = make_float2((float)(v.x - (double)hr), (float)(v.y - (double)hm));
+    reinterpret_cast<float2 *>(lo)[f] =
+        make_float2(f64_to_f32_rn(v.x - f32_to_f64(hr)), f64_to_f32_rn(v.y - f32_to_f64(hm)));
   }
 }
 

@@ -574,7 +574,7 @@ __global__ void gnormalize_f32_kernel(const GMeta *__restrict__ gm, int64_t len,
   const int n = gm->n;
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < len; f += (int64_t)gridDim.x * blockDim.x) {
     const double sc = inv[system_of(sm, n, f)];
-    dst[f] = make_float2((float)(src[f].x * sc), (float)(src[f].y * sc));
+    dst[f] = make_float2(f64_to_f32_rn(src[f].x * sc), f64_to_f32_rn(src[f].y * sc));
   }
 }
 
@@ -622,7 +622,7 @@ __global__ void gborn_vt_kernel(const GMeta *__restrict__ gm, const GProb *__res
 
 __global__ void gd2f_kernel(int64_t n, const double *__restrict__ src, float *__restrict__ dst) {
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n; f += (int64_t)gridDim.x * blockDim.x)
-    dst[f] = (float)src[f];
+    dst[f] = f64_to_f32_rn(src[f]);
 }
 
 // S = 1 - 2 pi i U00 / D and the paper's A per system; out[s * 6 + ...]

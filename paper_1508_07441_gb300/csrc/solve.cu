@@ -671,14 +671,14 @@ __global__ void bnormalize_f32_kernel(int64_t n, int B, const double2 *src, cons
        f += (int64_t)gridDim.x * blockDim.x) {
     const double sc = inv[(int)(f % B)];
     const double2 v = src[f];
-    dst[f] = make_float2((float)(v.x * sc), (float)(v.y * sc));
+    dst[f] = make_float2(f64_to_f32_rn(v.x * sc), f64_to_f32_rn(v.y * sc));
   }
 }
 
 __global__ void d2f_kernel(int64_t n, const double *src, float *dst) {
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n;
        f += (int64_t)gridDim.x * blockDim.x)
-    dst[f] = (float)src[f];
+    dst[f] = f64_to_f32_rn(src[f]);
 }
 
 // unit vectors: X[r0[e] * B + e] = 1

@@ -118,6 +118,7 @@ _SIGS = {
                                           ctypes.c_int, ctypes.c_int, _P, _P]),
     "wpcd_vec_axpy": (ctypes.c_int, [ctypes.c_double, _P, _P, ctypes.c_int64, _P]),
     "wpcd_complex_to_f32": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P]),
+    "wpcd_split_f64": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P]),
 }
 
 _lib = None
@@ -551,6 +552,11 @@ def wpcd_basis_expand(Phi, k, dim, C, n, U, stream=None):
 
 def wpcd_basis_orthonormalize(Phi, k, dim, stream=None):
     check(lib().wpcd_basis_orthonormalize(_tensor_ptr(Phi), k, dim, _stream_ptr(stream)))
+
+
+def wpcd_split_f64(x, hi, lo, stream=None):
+    """Float-float split of device float64 tensor x into float32 tensors hi, lo."""
+    check(lib().wpcd_split_f64(_tensor_ptr(x), x.numel(), _tensor_ptr(hi), _tensor_ptr(lo), _stream_ptr(stream)))
 
 
 def wpcd_warm_softmax(logits, n, k, C, stream=None):

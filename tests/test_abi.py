@@ -123,6 +123,13 @@ def test_warm_softmax_argument_checks(W):
         assert L.wpcd_warm_softmax(None, n, k, None, None) == W.WPCD_EINVAL
 
 
+def test_split_argument_checks(W):
+    L = W.lib()
+    assert L.wpcd_split_f64(None, 4, None, None, None) == W.WPCD_EINVAL
+    assert L.wpcd_split_f64(1, -1, 1, 1, None) == W.WPCD_EINVAL
+    assert L.wpcd_split_f64(1, 0, 1, 1, None) == W.WPCD_OK  # nothing to do, nothing launched
+
+
 def test_no_cpu_fallback_when_library_missing(W, monkeypatch, tmp_path):
     monkeypatch.setattr(W, "LIB_PATH", str(tmp_path / "missing.so"))
     monkeypatch.setattr(W, "_lib", None)
