@@ -570,10 +570,15 @@ __global__ void baxpy2_kernel(int64_t n2, int B2, int nv, const float4 *__restri
 // element is issued before the multiply-adds (the runtime loop waits on one
 // load per vector: 4.8-5.0 TB/s at 8-10 vectors), the sums in the same order;
 // 32-bit index arithmetic (n2 < 2^31)
-template <int NVT>
+// NORM: the norm pass of the Arnoldi step folded in: each thread sums the
+// squares of its two energies' new values (the grid stride is a multiple of
+// B2, so a thread keeps its energies), and the block writes
+// partial[blk * B + e] = (sum, 0) as the norm kernel does
+template <int NVT, bool NORM>
 __global__ void __launch_bounds__(256) baxpy2t_kernel(int n2, int B2, int nv, const float4 *__restrict__ V,
                                                       size_t ld2, const float4 *__restrict__ c,
-                                                      float4 *__restrict__ w) {
+                                                      float4 *__restrict__ w, double2 *__restrict__ partial) {
+  float s0 = 0.f, s1 = 0.f;
   for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < n2; f += gridDim.x * blockDim.x) {
     const int e2 = f % B2;
     float4 v[NVT];
@@ -590,6 +595,26 @@ __global__ void __launch_bounds__(256) baxpy2t_kernel(int n2, int B2, int nv, co
         a.w = fmaf(cj.z, v[j].w, fmaf(cj.w, v[j].z, a.w));
       }
     w[f] = a;
+    if (NORM) {
+      s0 = fmaf(a.x, a.x, fmaf(a.y, a.y, s0));
+      s1 = fmaf(a.z, a.z, fmaf(a.w, a.w, s1));
+    }
+  }
+  if (NORM) {
+    __shared__ double red[2][256];
+    const int tid = threadIdx.x;
+    red[0][tid] = s0;
+    red[1][tid] = s1;
+    __syncthreads();
+    if (tid < B2) {  // threads tid, tid + B2, ... hold energies 2 tid, 2 tid + 1
+      double t0 = 0.0, t1 = 0.0;
+      for (int q = tid; q < 256; q += B2) {
+        t0 += red[0][q];
+        t1 += red[1][q];
+      }
+      partial[(size_t)blockIdx.x * 2 * B2 + 2 * tid] = make_double2(t0, 0.0);
+      partial[(size_t)blockIdx.x * 2 * B2 + 2 * tid + 1] = make_double2(t1, 0.0);
+    }
   }
 }
 
@@ -1313,30 +1338,45 @@ struct Krylov {
                                                       scale ? inv : nullptr);
     count_launches(2);
   }
-  // w += sum_{j < nv} hc_j V_j (FP32 with B even: two energies per thread)
-  void axpy(int nv, cudaStream_t s) {
+  template <bool NORM>
+  void axpy2t(int nv, int g, cudaStream_t s) {
+    const int n2 = (int)((int64_t)dim * B / 2);
+    const float4 *Vv = reinterpret_cast<const float4 *>(V), *cc = reinterpret_cast<const float4 *>(hc);
+    float4 *ww = reinterpret_cast<float4 *>(w);
+    const size_t ld2 = dim * B / 2;
+    if (nv <= 2)
+      baxpy2t_kernel<2, NORM><<<g, 256, 0, s>>>(n2, B / 2, nv, Vv, ld2, cc, ww, partial);
+    else if (nv <= 4)
+      baxpy2t_kernel<4, NORM><<<g, 256, 0, s>>>(n2, B / 2, nv, Vv, ld2, cc, ww, partial);
+    else if (nv <= 8)
+      baxpy2t_kernel<8, NORM><<<g, 256, 0, s>>>(n2, B / 2, nv, Vv, ld2, cc, ww, partial);
+    else
+      baxpy2t_kernel<12, NORM><<<g, 256, 0, s>>>(n2, B / 2, nv, Vv, ld2, cc, ww, partial);
+  }
+  // w += sum_{j < nv} hc_j V_j (FP32 with B even: two energies per thread).
+  // With with_norm, where the shape allows (FP32, B / 2 dividing 256, the
+  // partial buffer holding a block partial per block of the axpy's grid),
+  // the norm pass's block partials of the new w come out of the same kernel;
+  // returns their block count (0: not done)
+  int axpy(int nv, cudaStream_t s, bool with_norm = false) {
     const int64_t n = (int64_t)dim * B;
+    const bool t_ok = sizeof(T) == 4 && B % 2 == 0 && nv <= 12 && n / 2 < INT32_MAX;
+    const int g = grid_for(n / 2, 256);
+    if (with_norm && t_ok && 256 % (B / 2) == 0 && g <= (m + 1) * nblk) {
+      axpy2t<true>(nv, g, s);
+      return g;
+    }
     // the unrolled form except at three vectors (112 against 103 us there;
     // 47-256 against 58-292 us elsewhere up to ten)
-    if (sizeof(T) == 4 && B % 2 == 0 && nv <= 12 && nv != 3 && n / 2 < INT32_MAX) {
-      const int n2 = (int)(n / 2), g = grid_for(n2, 256);
-      const float4 *Vv = reinterpret_cast<const float4 *>(V), *cc = reinterpret_cast<const float4 *>(hc);
-      float4 *ww = reinterpret_cast<float4 *>(w);
-      const size_t ld2 = dim * B / 2;
-      if (nv <= 2)
-        baxpy2t_kernel<2><<<g, 256, 0, s>>>(n2, B / 2, nv, Vv, ld2, cc, ww);
-      else if (nv <= 4)
-        baxpy2t_kernel<4><<<g, 256, 0, s>>>(n2, B / 2, nv, Vv, ld2, cc, ww);
-      else if (nv <= 8)
-        baxpy2t_kernel<8><<<g, 256, 0, s>>>(n2, B / 2, nv, Vv, ld2, cc, ww);
-      else
-        baxpy2t_kernel<12><<<g, 256, 0, s>>>(n2, B / 2, nv, Vv, ld2, cc, ww);
+    if (t_ok && nv != 3) {
+      axpy2t<false>(nv, g, s);
     } else if (sizeof(T) == 4 && B % 2 == 0)
       baxpy2_kernel<<<grid_for(n / 2, 256), 256, 0, s>>>(n / 2, B / 2, nv, reinterpret_cast<const float4 *>(V),
                                                          dim * B / 2, reinterpret_cast<const float4 *>(hc),
                                                          reinterpret_cast<float4 *>(w));
     else
       baxpy_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(n, B, nv, vec(0), dim * B, hc, wv());
+    return 0;
   }
   // one Arnoldi step from column k (w holds (I - K) v_k on entry); classical
   // Gram-Schmidt with a second pass (reorth = true) or a single pass
@@ -1345,7 +1385,7 @@ struct Krylov {
     const size_t ld = dim * B;
     const int vg = grid_for(n, 256);
     dots<T>(k + 1, vec(0), ld, wv(), h, 0, s, true);
-    axpy(k + 1, s);
+    const int normed = axpy(k + 1, s, !reorth);
     if (reorth) {
       dots<T>(k + 1, vec(0), ld, wv(), h2, 0, s, true);
       axpy(k + 1, s);
@@ -1354,7 +1394,12 @@ struct Krylov {
                                                                    nullptr);
       count_launches(2);
     }
-    norms<T>(wv(), s, true);
+    if (normed) {  // the axpy left the norm partials of its `normed` blocks
+      breduce_kernel<T><<<breduce_blocks(B), 256, 0, s>>>(1, normed, B, partial, nrm, 0, nullptr, -1.0, inv);
+      count_launches(1);
+    } else {
+      norms<T>(wv(), s, true);
+    }
     if (sizeof(T) == 4 && B % 2 == 0 && n / 2 < INT32_MAX)
       bscale2_kernel<<<grid_for(n / 2, 256), 256, 0, s>>>((int)(n / 2), B / 2, reinterpret_cast<const float4 *>(wv()),
                                                          reinterpret_cast<const float2 *>(inv),
